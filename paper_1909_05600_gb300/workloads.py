@@ -1,0 +1,167 @@
+"""Seeded synthetic inputs shaped like the paper's workloads (numpy only).
+
+This module holds no part of the method's arithmetic: it only draws point clouds,
+weights and densities.  Both the CUDA path's tests/bench and the CPU oracle take their
+inputs from here.  Seeds follow one convention: X from `seed`, Y from `seed + 1000`,
+u from `seed + 2000`.
+
+Shapes:
+  * random points on the unit sphere (Sec. 4.1, the paper's scalability runs), drawn as
+    normalised standard normal vectors;
+  * uniform points on the surface of the unit cube [0,1]^3;
+  * uniform points in the unit cube;
+  * a mixture of 8 isotropic Gaussians (sigma = 0.05, centres uniform in [0,1]^3).
+"""
+from dataclasses import dataclass, field
+import math
+
+import numpy as np
+
+LAPLACE, HELMHOLTZ = 0, 1
+
+
+def sphere_surface(n, seed):
+    p = np.random.default_rng(seed).standard_normal((n, 3))
+    return p / np.linalg.norm(p, axis=1, keepdims=True)
+
+
+def cube_surface(n, seed):
+    rng = np.random.default_rng(seed)
+    face = rng.integers(0, 6, n)
+    a = rng.random((n, 2))
+    p = np.empty((n, 3))
+    axis = face % 3
+    side = (face // 3).astype(np.float64)
+    for d in range(3):
+        on = axis == d
+        others = [e for e in range(3) if e != d]
+        p[on, d] = side[on]
+        p[on, others[0]] = a[on, 0]
+        p[on, others[1]] = a[on, 1]
+    return p
+
+
+def cube_volume(n, seed):
+    return np.random.default_rng(seed).random((n, 3))
+
+
+def gaussian_mixture(n, seed, centres_seed=7, ncomp=8, sigma=0.05):
+    centres = np.random.default_rng(centres_seed).random((ncomp, 3))
+    rng = np.random.default_rng(seed)
+    comp = rng.integers(0, ncomp, n)
+    return centres[comp] + sigma * rng.standard_normal((n, 3))
+
+
+GEOMETRIES = {"sphere": sphere_surface, "cube_surface": cube_surface, "cube_volume": cube_volume}
+AREA = {"sphere": 4.0 * math.pi, "cube_surface": 6.0, "cube_volume": 1.0}
+
+
+def wavenumber_ppw(n, geometry, ppw=10.0):
+    """k giving `ppw` points per wavelength: dx = sqrt(area/n) on a surface,
+    (volume/n)^(1/3) in a volume, k = 2 pi / (ppw dx)."""
+    if geometry == "cube_volume":
+        dx = (1.0 / n) ** (1.0 / 3.0)
+    else:
+        dx = math.sqrt(AREA[geometry] / n)
+    return 2.0 * math.pi / (ppw * dx)
+
+
+@dataclass
+class Problem:
+    name: str
+    X: np.ndarray
+    Y: np.ndarray
+    u: np.ndarray          # (ny,) or (ny, nrhs); float64/float32/complex64
+    w: np.ndarray          # (ny,) quadrature weights
+    kind: int
+    k: float
+    eps: float
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def n(self):
+        return max(self.X.shape[0], self.Y.shape[0])
+
+
+def laplace_sphere(n=20000, seed=1, eps=1e-3):
+    """Laplace 1/(4 pi r), X and Y independent uniform draws on the unit sphere,
+    w = 4 pi / n, u ~ N(0, 1) float64."""
+    X = sphere_surface(n, seed)
+    Y = sphere_surface(n, seed + 1000)
+    u = np.random.default_rng(seed + 2000).standard_normal(n)
+    w = np.full(n, 4.0 * math.pi / n)
+    return Problem("laplace_sphere_%d" % n, X, Y, u, w, LAPLACE, 0.0, eps)
+
+
+def helmholtz_sphere(n=1_000_000, seed=1, eps=1e-3, ppw=10.0):
+    """Helmholtz e^{ikr}/(4 pi r), X and Y independent on the unit sphere, k at `ppw`
+    points per wavelength, u complex64 with N(0,1) parts, w = 4 pi / n."""
+    X = sphere_surface(n, seed)
+    Y = sphere_surface(n, seed + 1000)
+    rng = np.random.default_rng(seed + 2000)
+    u = (rng.standard_normal(n) + 1j * rng.standard_normal(n)).astype(np.complex64)
+    w = np.full(n, 4.0 * math.pi / n)
+    k = wavenumber_ppw(n, "sphere", ppw)
+    return Problem("helmholtz_sphere_%d" % n, X, Y, u, w, HELMHOLTZ, k, eps)
+
+
+def helmholtz_cube_multirhs(n=200_000, nrhs=64, seed=1, eps=1e-4, ppw=10.0):
+    """Helmholtz on the unit-cube surface with X = Y, nrhs plane-wave densities
+    u_m(y) = e^{ik d_m . y} with directions d_m uniform on the sphere, complex64."""
+    X = cube_surface(n, seed)
+    k = wavenumber_ppw(n, "cube_surface", ppw)
+    d = sphere_surface(nrhs, seed + 2000)
+    u = np.exp(1j * k * (X @ d.T)).astype(np.complex64)
+    w = np.full(n, 6.0 / n)
+    return Problem("helmholtz_cube_%dx%d" % (n, nrhs), X, X.copy(), u, w, HELMHOLTZ, k, eps)
+
+
+def laplace_clustered(n=100_000_000, seed=1, eps=1e-3):
+    """Laplace on a mixture of 8 Gaussians (sigma 0.05, shared centres), X and Y
+    independent, u ~ U(-1, 1) float32, w = 1/n."""
+    X = gaussian_mixture(n, seed)
+    Y = gaussian_mixture(n, seed + 1000)
+    u = np.random.default_rng(seed + 2000).uniform(-1.0, 1.0, n).astype(np.float32)
+    w = np.full(n, 1.0 / n)
+    return Problem("laplace_clustered_%d" % n, X, Y, u, w, LAPLACE, 0.0, eps)
+
+
+def serving_stream(nreq=500, seed=7, nmin=10_000, nmax=2_000_000, rate_hz=10.0):
+    """Request descriptors for the serving stream: Poisson arrivals, N log-uniform in
+    [nmin, nmax], kernel 50/50, geometry uniform over three shapes, eps in {1e-3, 1e-4}."""
+    rng = np.random.default_rng(seed)
+    t = np.cumsum(rng.exponential(1.0 / rate_hz, nreq))
+    ns = np.exp(rng.uniform(math.log(nmin), math.log(nmax), nreq)).astype(np.int64)
+    kinds = rng.integers(0, 2, nreq)
+    geos = rng.integers(0, 3, nreq)
+    epss = np.where(rng.integers(0, 2, nreq) == 0, 1e-3, 1e-4)
+    names = list(GEOMETRIES)
+    out = []
+    for i in range(nreq):
+        g = names[geos[i]]
+        out.append({"id": i, "t_arrival": float(t[i]), "n": int(ns[i]), "kind": int(kinds[i]), "geometry": g,
+                    "eps": float(epss[i]), "seed": int(seed * 100000 + i)})
+    return out
+
+
+def serving_problem(req):
+    """Materialise one serving request: X = Y drawn independently per set."""
+    g = req["geometry"]
+    n = req["n"]
+    X = GEOMETRIES[g](n, req["seed"])
+    Y = GEOMETRIES[g](n, req["seed"] + 1000)
+    rng = np.random.default_rng(req["seed"] + 2000)
+    w = np.full(n, AREA[g] / n)
+    if req["kind"] == LAPLACE:
+        u = rng.standard_normal(n).astype(np.float32)
+        return Problem("req%d" % req["id"], X, Y, u, w, LAPLACE, 0.0, req["eps"])
+    u = (rng.standard_normal(n) + 1j * rng.standard_normal(n)).astype(np.complex64)
+    k = wavenumber_ppw(n, g)
+    return Problem("req%d" % req["id"], X, Y, u, w, HELMHOLTZ, k, req["eps"])
+
+
+def sample_targets(nx, count=4096, seed=12345):
+    """Seeded random subset of target indices for error measurement at large N."""
+    if nx <= count:
+        return np.arange(nx, dtype=np.int64)
+    return np.sort(np.random.default_rng(seed).choice(nx, count, replace=False)).astype(np.int64)

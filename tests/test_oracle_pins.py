@@ -1,0 +1,394 @@
+"""Pins of the FP64 CPU oracle against facts that do not come from the oracle itself:
+closed-form potentials, library special functions, invariants of the convolution, exact
+reproduction of a polynomial kernel, and the transfer counts printed in the paper.
+All CPU-only."""
+import math
+
+import numpy as np
+import pytest
+from scipy.special import spherical_jn, spherical_yn, eval_legendre, gamma
+
+from oracle import oracle as O
+from paper_1909_05600_gb300 import workloads as W
+
+
+def _unit_dirs(n, seed):
+    return W.sphere_surface(n, seed)
+
+
+# ----------------------------------------------------------- O1 closed forms
+
+def test_direct_laplace_charged_sphere():
+    """int_{S^2} dS_y / (4 pi |x - y|) = 1 inside the unit sphere and 1/|x| outside
+    (potential of a uniformly charged sphere); Y is the oracle's own sphere quadrature."""
+    s, w = O.sphere_quad(40)
+    radii = np.array([0.0, 0.3, 0.55, 0.8, 1.25, 2.0, 5.0])
+    dirs = _unit_dirs(len(radii), 3)
+    X = dirs * radii[:, None]
+    v = O.direct(X, s, np.ones(len(w)), O.LAPLACE, w=w)[:, 0]
+    exact = np.where(radii < 1, 1.0, 1.0 / np.maximum(radii, 1e-300))
+    assert np.max(np.abs(v.real - exact)) < 1e-8
+    assert np.max(np.abs(v.imag)) == 0.0
+
+
+@pytest.mark.parametrize("k", [0.7, 5.0, 12.0])
+def test_direct_helmholtz_sphere_single_layer(k):
+    """int_{S^2} e^{ik|x-y|}/(4 pi |x-y|) dS_y = e^{ik} sin(k|x|)/(k|x|) for |x| < 1 and
+    sin(k) e^{ik|x|}/(k|x|) for |x| > 1 (addition theorem: only n = 0 survives)."""
+    s, w = O.sphere_quad(48)
+    radii = np.array([0.2, 0.5, 0.8, 1.25, 1.7, 3.0])
+    X = _unit_dirs(len(radii), 4) * radii[:, None]
+    v = O.direct(X, s, np.ones(len(w)), O.HELMHOLTZ, k, w=w)[:, 0]
+    inside = np.exp(1j * k) * np.sin(k * radii) / (k * radii)
+    outside = np.sin(k) * np.exp(1j * k * radii) / (k * radii)
+    exact = np.where(radii < 1, inside, outside)
+    assert np.max(np.abs(v - exact)) < 1e-8
+
+
+def test_direct_helmholtz_plane_wave_density():
+    """Funk-Hecke: for u(y) = e^{ik d.y} on the unit sphere and |x| < 1,
+    v(x) = sum_n i^n (2n+1) ik j_n(k) h_n(k) j_n(k|x|) P_n(x.d/|x|)."""
+    k = 4.0
+    s, w = O.sphere_quad(48)
+    d = np.array([0.36, -0.48, 0.8])
+    u = np.exp(1j * k * (s @ d))
+    radii = np.array([0.25, 0.6, 0.8])
+    X = _unit_dirs(3, 9) * radii[:, None]
+    v = O.direct(X, s, u, O.HELMHOLTZ, k, w=w)[:, 0]
+    n = np.arange(60)
+    jk = spherical_jn(n, k)
+    hk = jk + 1j * spherical_yn(n, k)
+    for i in range(3):
+        r = radii[i]
+        c = X[i] @ d / r
+        ex = np.sum((1j ** n) * (2 * n + 1) * 1j * k * jk * hk * spherical_jn(n, k * r) * eval_legendre(n, c))
+        assert abs(v[i] - ex) < 1e-8 * max(1.0, abs(ex))
+
+
+def test_direct_reciprocity_and_linearity():
+    """G(x, y) = G(y, x) with no conjugation: a^T (G_XY b) = b^T (G_YX a); the sum is
+    linear in u."""
+    rng = np.random.default_rng(0)
+    X = rng.random((150, 3))
+    Y = rng.random((170, 3)) + 0.3
+    a = rng.standard_normal(150) + 1j * rng.standard_normal(150)
+    b = rng.standard_normal(170) + 1j * rng.standard_normal(170)
+    k = 7.5
+    lhs = a @ O.direct(X, Y, b, O.HELMHOLTZ, k)[:, 0]
+    rhs = b @ O.direct(Y, X, a, O.HELMHOLTZ, k)[:, 0]
+    assert abs(lhs - rhs) < 1e-12 * abs(lhs)
+    c = rng.standard_normal(170)
+    v1 = O.direct(X, Y, 2.0 * b - 3.0 * c, O.HELMHOLTZ, k)
+    v2 = 2.0 * O.direct(X, Y, b, O.HELMHOLTZ, k) - 3.0 * O.direct(X, Y, c, O.HELMHOLTZ, k)
+    assert O.rel_l2(v1, v2) < 1e-13
+
+
+def test_direct_coincident_points_contribute_zero():
+    X = np.array([[0.1, 0.2, 0.3]])
+    v = O.direct(X, X, np.ones(1), O.LAPLACE)
+    assert v[0, 0] == 0.0
+    v = O.direct(X, X, np.ones(1), O.HELMHOLTZ, 3.0)
+    assert v[0, 0] == 0.0
+
+
+# ------------------------------------------------- O2 components, textbook pins
+
+@pytest.mark.parametrize("n", [1, 2, 5, 17, 64, 161])
+def test_gauss_legendre_matches_numpy(n):
+    x, w = O.gauss_legendre(n)
+    xr, wr = np.polynomial.legendre.leggauss(n)
+    assert np.max(np.abs(x - xr)) < 1e-13
+    assert np.max(np.abs(w - wr)) < 1e-13
+
+
+@pytest.mark.parametrize("L", [1, 4, 11, 30])
+def test_sphere_quadrature_integrates_monomials(L):
+    """Quadrature of eq. 17: weights sum to 4 pi and monomials x^a y^b z^c of total
+    degree < 2L integrate exactly: int = 2 G((a+1)/2) G((b+1)/2) G((c+1)/2) / G((a+b+c+3)/2)
+    for even a, b, c, zero otherwise."""
+    s, w = O.sphere_quad(L)
+    assert len(w) == 2 * L * (L + 1)
+    assert abs(w.sum() - 4 * math.pi) < 1e-12
+    for (a, b, c) in [(2, 0, 0), (0, 2, 2), (1, 1, 0), (4, 2, 0), (0, 0, 6), (2, 2, 2), (3, 0, 1)]:
+        if a + b + c >= 2 * L:
+            continue
+        num = np.sum(w * s[:, 0] ** a * s[:, 1] ** b * s[:, 2] ** c)
+        if a % 2 or b % 2 or c % 2:
+            ex = 0.0
+        else:
+            ex = 2 * gamma((a + 1) / 2) * gamma((b + 1) / 2) * gamma((c + 1) / 2) / gamma((a + b + c + 3) / 2)
+        assert abs(num - ex) < 1e-12
+
+
+@pytest.mark.parametrize("z", [0.5, 3.0, 17.0, 250.0])
+def test_hankel_matches_scipy(z):
+    L = 60
+    h = O.hankel(L, z)
+    p = np.arange(L + 1)
+    ref = spherical_jn(p, z) + 1j * spherical_yn(p, z)
+    rel = np.abs(h - ref) / np.abs(ref)
+    assert np.max(rel) < 1e-10
+
+
+@pytest.mark.parametrize("kd,offset,eps", [
+    (2.0, (2, 0, 0), 1e-3), (5.0, (2, 1, 0), 1e-3), (20.0, (2, 2, 2), 1e-3),
+    (60.0, (3, -2, 1), 1e-3), (8.0, (-2, 0, 1), 1e-4), (30.0, (0, 2, -3), 1e-4)])
+def test_plane_wave_single_pair(kd, offset, eps):
+    """Eqs. 10-16 with the readings p from 0, box-centred phases (no r0 phase), natural-log
+    rank and the (L+1) x 2L quadrature reproduce e^{ik|x-y|}/(4 pi |x-y|) to eps for a
+    box pair at the admissibility distance."""
+    d = 1.0
+    k = kd / d
+    L = O.pw_rank(k, d, eps)
+    rng = np.random.default_rng(int(kd * 10))
+    y0 = np.zeros(3)
+    x0 = np.array(offset, dtype=float) * d
+    worst = 0.0
+    for _ in range(6):
+        x = x0 + (rng.random(3) - 0.5) * d
+        y = y0 + (rng.random(3) - 0.5) * d
+        r = np.linalg.norm(x - y)
+        exact = np.exp(1j * k * r) / (4 * math.pi * r)
+        worst = max(worst, abs(O.pw_pair(k, L, x, y, x0, y0) - exact) / abs(exact))
+    assert worst < eps
+
+
+def test_plane_wave_series_from_p1_misses_eps():
+    """Eq. 12 as printed sums from p = 1. Dropping the p = 0 term removes
+    ik h_0(k r0) j_0(k |r_xy|) / (4 pi) from the single-pair approximation (the quadrature
+    integrates e^{ik s.r_xy} to 4 pi j_0 exactly), and the result misses eps by far."""
+    k, d, eps = 10.0, 1.0, 1e-3
+    L = O.pw_rank(k, d, eps)
+    x0 = np.array([2.0, 0.0, 0.0])
+    y0 = np.zeros(3)
+    x = x0 + np.array([0.2, -0.1, 0.3])
+    y = y0 + np.array([-0.25, 0.1, 0.05])
+    r = np.linalg.norm(x - y)
+    exact = np.exp(1j * k * r) / (4 * math.pi * r)
+    good = O.pw_pair(k, L, x, y, x0, y0)
+    assert abs(good - exact) < eps * abs(exact)
+    rxy = np.linalg.norm((x - x0) - (y - y0))
+    h0 = O.hankel(0, k * np.linalg.norm(x0 - y0))[0]
+    monopole = 1j * k * h0 * spherical_jn(0, k * rxy) / (4 * math.pi)
+    assert abs(good - monopole - exact) > 10 * eps * abs(exact)
+
+
+def test_r1_table_matches_calibration():
+    from oracle.calibrate_r1 import calibrate, round_up
+    cal = calibrate()
+    for name, kind in (("laplace", O.LAPLACE), ("helmholtz_kd2", O.HELMHOLTZ)):
+        tab = O.r1_table(kind)
+        for r1, e in zip(range(2, 11), cal[name]):
+            assert tab[r1] == pytest.approx(round_up(e), rel=1e-12)
+    assert O.r1_rule(O.LAPLACE, 1e-3) == 4
+    assert O.r1_rule(O.LAPLACE, 1e-4) == 6
+
+
+def test_morton_interleave():
+    assert O.morton(1, 0, 0) == 4
+    assert O.morton(0, 1, 0) == 2
+    assert O.morton(0, 0, 1) == 1
+    # bit b of gx -> 3b+2, of gy -> 3b+1, of gz -> 3b
+    gx, gy, gz = 0b1011, 0b0110, 0b1101
+    ref = 0
+    for b in range(4):
+        ref |= ((gx >> b) & 1) << (3 * b + 2) | ((gy >> b) & 1) << (3 * b + 1) | ((gz >> b) & 1) << (3 * b)
+    assert O.morton(gx, gy, gz) == ref
+
+
+# --------------------------------------------------- O2 descent / transfer counts
+
+def test_admissibility_is_non_strict_max_norm():
+    z = np.zeros(3)
+    assert O.admissible(z, 3, [2, 0, 0])
+    assert O.admissible(z, 3, [-2, 1, 1])
+    assert not O.admissible(z, 3, [1, 1, 1])
+    assert O.admissible(z, 3, [2, 2, 2])
+    # shifted trees: the offset is sigma*2^l + m
+    sig = np.array([0.25 / 8, 0.0, 0.0])
+    assert not O.admissible(sig, 3, [1, 0, 0])   # 1.25
+    assert O.admissible(sig, 3, [-3, 0, 0])      # -2.75
+    assert not O.admissible(sig, 3, [-2, 0, 0])  # -1.75
+
+
+def _pairs_per_target(pairs):
+    _, c = np.unique(pairs[:, 0], return_counts=True)
+    return c
+
+
+def test_quadtree_transfer_counts_match_paper():
+    """Planar points with X = Y (aligned quadtrees, Sec. 3.1 proof of Prop. 1): an interior
+    box has 27 admissible partners and a level holds at most 7^2 - 3^2 = 40 distinct
+    transfers."""
+    rng = np.random.default_rng(11)
+    P = np.zeros((20000, 3))
+    P[:, :2] = rng.random((20000, 2))
+    plan = O.Plan(P, P, O.LAPLACE, 0.0, 1e-3)
+    st = plan.stats()
+    assert st["l_stop"] >= 4
+    for l in range(2, st["l_stop"] + 1):
+        assert st["n_trans"][l] == 40
+        if l >= 3:
+            assert _pairs_per_target(plan.pairs(l, "adm")).max() == 27
+
+
+def test_octree_transfer_counts():
+    """Volume points with X = Y: at most 7^3 - 3^3 = 316 distinct transfers per level and
+    6^3 - 3^3 = 189 admissible partners for an interior box."""
+    P = W.cube_volume(60000, 5)
+    plan = O.Plan(P, P, O.LAPLACE, 0.0, 1e-3, n_leaf=16)
+    st = plan.stats()
+    for l in range(3, st["l_stop"] + 1):
+        assert st["n_trans"][l] == 316
+        assert _pairs_per_target(plan.pairs(l, "adm")).max() == 189
+
+
+def test_stop_rule_mean_occupancy():
+    prob = W.laplace_sphere(20000)
+    plan = O.Plan(prob.X, prob.Y, O.LAPLACE, 0.0, 1e-3)
+    st = plan.stats()
+    ls = st["l_stop"]
+    tot = prob.X.shape[0] + prob.Y.shape[0]
+    assert tot < 64 * (st["nboxX"][ls] + st["nboxY"][ls])
+    assert tot >= 64 * (st["nboxX"][ls - 1] + st["nboxY"][ls - 1])
+
+
+# ------------------------------------------------------------ O2 versus O1
+
+def test_ffm_small_n_is_the_direct_sum():
+    """With no more points than one leaf holds the descent stops at the roots and the FFM
+    is the dense product."""
+    rng = np.random.default_rng(3)
+    X = rng.random((40, 3))
+    Y = rng.random((50, 3))
+    u = rng.standard_normal(50) + 1j * rng.standard_normal(50)
+    plan = O.Plan(X, Y, O.HELMHOLTZ, 9.0, 1e-3)
+    assert plan.stats()["l_stop"] == 0
+    v = plan.apply(u)
+    ref = O.direct(X, Y, u, O.HELMHOLTZ, 9.0)
+    assert O.rel_l2(v, ref) < 1e-14
+
+
+def test_ffm_lagrange_reproduces_polynomial_kernel():
+    """Tensor Lagrange interpolation with r1 = 4 is exact for a kernel of degree <= 3 per
+    coordinate: anterpolation, transfer and interpolation then make no error at all."""
+    P = W.cube_volume(6000, 21)
+    Q = W.cube_volume(5000, 22) * 0.9 + 0.07
+    u = np.random.default_rng(23).standard_normal(5000)
+    plan = O.Plan(P, Q, O.POLY, 0.0, 1e-3, r1_override=4, n_leaf=16)
+    st = plan.stats()
+    assert sum(st["n_adm"]) > 1000
+    v = plan.apply(u)
+    ref = O.direct(P, Q, u, O.POLY)
+    assert O.rel_l2(v, ref) < 1e-11
+
+
+def test_ffm_laplace_sphere_meets_eps():
+    prob = W.laplace_sphere(20000)
+    v = O.ffm(prob.X, prob.Y, prob.u, O.LAPLACE, 0.0, prob.eps, w=prob.w)
+    ref = O.direct(prob.X, prob.Y, prob.u, O.LAPLACE, w=prob.w)
+    err = O.rel_l2(v, ref)
+    # within eps, and in the band of Table 1 (8e-5 .. 3.5e-4 at eps = 1e-3) to a factor 10
+    assert 1e-6 < err < prob.eps
+
+
+@pytest.mark.parametrize("n", [8000, 30000])
+def test_ffm_helmholtz_sphere_meets_eps(n):
+    prob = W.helmholtz_sphere(n)
+    plan = O.Plan(prob.X, prob.Y, O.HELMHOLTZ, prob.k, prob.eps)
+    st = plan.stats()
+    assert any(m == O.MODE_PLANEWAVE for m in st["mode"])
+    v = plan.apply(prob.u.astype(np.complex128), prob.w)
+    t = W.sample_targets(n, 1500)
+    ref = O.direct(prob.X, prob.Y, prob.u.astype(np.complex128), O.HELMHOLTZ, prob.k, w=prob.w, targets=t)
+    assert O.rel_l2(v[t], ref) < prob.eps
+
+
+def test_ffm_helmholtz_low_frequency_lagrange_levels():
+    """Helmholtz with k d_l below the switch at every level: Lagrange interpolation of the
+    oscillatory kernel (complex transfer)."""
+    prob = W.helmholtz_sphere(12000, ppw=60.0)
+    plan = O.Plan(prob.X, prob.Y, O.HELMHOLTZ, 1.5, 1e-3)
+    st = plan.stats()
+    assert all(m != O.MODE_PLANEWAVE for m in st["mode"]) and any(m == O.MODE_LAGRANGE for m in st["mode"])
+    u = prob.u.astype(np.complex128)
+    v = plan.apply(u, prob.w)
+    t = W.sample_targets(12000, 1500)
+    ref = O.direct(prob.X, prob.Y, u, O.HELMHOLTZ, 1.5, w=prob.w, targets=t)
+    assert O.rel_l2(v[t], ref) < 1e-3
+
+
+def test_ffm_mixed_levels_and_coincident_sets():
+    """X = Y on the cube surface (pairs at distance 0 skipped) with plane-wave levels above
+    Lagrange levels, eps = 1e-4."""
+    n = 15000
+    X = W.cube_surface(n, 31)
+    k = 12.0
+    u = np.exp(1j * k * X @ np.array([0.0, 0.6, 0.8]))
+    plan = O.Plan(X, X, O.HELMHOLTZ, k, 1e-4)
+    st = plan.stats()
+    modes = [m for m in st["mode"] if m]
+    assert O.MODE_PLANEWAVE in modes and O.MODE_LAGRANGE in modes
+    v = plan.apply(u, np.full(n, 6.0 / n))
+    t = W.sample_targets(n, 1500)
+    ref = O.direct(X, X, u, O.HELMHOLTZ, k, w=np.full(n, 6.0 / n), targets=t)
+    assert O.rel_l2(v[t], ref) < 1e-4
+
+
+@pytest.mark.parametrize("kind,k", [(O.LAPLACE, 0.0), (O.HELMHOLTZ, 10.0)])
+def test_ffm_far_separated_roots(kind, k):
+    """Roots already admissible (centres 5 d0 apart): one far-field interaction at level 0."""
+    rng = np.random.default_rng(8)
+    X = rng.random((3000, 3))
+    Y = rng.random((2500, 3)) + np.array([5.0, 0.5, -0.2])
+    u = rng.standard_normal(2500)
+    plan = O.Plan(X, Y, kind, k, 1e-3)
+    st = plan.stats()
+    assert st["root_admissible"] == 1 and st["n_adm"][0] == 1 and st["l_stop"] == 0
+    v = plan.apply(u)
+    ref = O.direct(X, Y, u, kind, k)
+    assert O.rel_l2(v, ref) < 1e-3
+
+
+def test_ffm_linearity_multirhs_and_reciprocity():
+    prob = W.helmholtz_sphere(6000, eps=1e-4)
+    u = prob.u.astype(np.complex128)
+    rng = np.random.default_rng(44)
+    u2 = rng.standard_normal(6000) + 0j
+    U = np.stack([u, u2, 2 * u - 3j * u2], 1)
+    plan = O.Plan(prob.X, prob.Y, O.HELMHOLTZ, prob.k, 1e-4)
+    V = plan.apply(U)
+    assert O.rel_l2(V[:, 2], 2 * V[:, 0] - 3j * V[:, 1]) < 1e-12
+    assert O.rel_l2(V[:, :1], plan.apply(u)) < 1e-14
+    # reciprocity a^T G_XY b = b^T G_YX a holds to eps through the FFM
+    plan_t = O.Plan(prob.Y, prob.X, O.HELMHOLTZ, prob.k, 1e-4)
+    a = rng.standard_normal(6000)
+    lhs = a @ V[:, 1]
+    rhs = u2 @ plan_t.apply(a)[:, 0]
+    assert abs(lhs - rhs) < 1e-4 * abs(lhs)
+
+
+def test_ffm_translation_and_scaling_invariance():
+    prob = W.laplace_sphere(8000)
+    v = O.ffm(prob.X, prob.Y, prob.u, O.LAPLACE, 0.0, 1e-3)
+    s = np.array([0.5, -0.25, 0.125])
+    vt = O.ffm(prob.X + s, prob.Y + s, prob.u, O.LAPLACE, 0.0, 1e-3)
+    assert O.rel_l2(vt, v) < 1e-10
+    vs = O.ffm(2.0 * prob.X, 2.0 * prob.Y, prob.u, O.LAPLACE, 0.0, 1e-3)
+    assert O.rel_l2(2.0 * vs, v) < 1e-13
+    hp = W.helmholtz_sphere(8000)
+    u = hp.u.astype(np.complex128)
+    vh = O.ffm(hp.X, hp.Y, u, O.HELMHOLTZ, hp.k, 1e-3)
+    vhs = O.ffm(2.0 * hp.X, 2.0 * hp.Y, u, O.HELMHOLTZ, hp.k / 2.0, 1e-3)
+    assert O.rel_l2(2.0 * vhs, vh) < 1e-13
+
+
+def test_ffm_degenerate_inputs():
+    one = np.array([[0.3, 0.3, 0.3]])
+    plan = O.Plan(one, one, O.LAPLACE, 0.0, 1e-3)
+    assert plan.stats()["d0"] == 1.0
+    assert plan.apply(np.ones(1))[0, 0] == 0.0
+    with pytest.raises(ValueError):
+        O.Plan(one, one, O.LAPLACE, 0.0, 0.0)
+    with pytest.raises(ValueError):
+        O.Plan(one, one, O.HELMHOLTZ, -1.0, 1e-3)
