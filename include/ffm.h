@@ -1,0 +1,155 @@
+/*
+ * ffm.h -- C ABI of the GB300 (sm_103a) Fast Free Memory library, libffm_gb300.so.
+ *
+ * The library evaluates the discrete convolution of Sec. 1, eqs. 3-4 of Aussal & Bakry,
+ * "The Fast and Free Memory Method for the efficient computation of convolution
+ * kernels" (arXiv:1909.05600):
+ *
+ *     v_i = sum_j  w_j G(x_i - y_j) u_j ,      i.e.  v = G W u ,
+ *
+ * for the Laplace kernel G = 1/(4 pi |x-y|) (Sec. 4.1, eq. 19) and the Helmholtz kernel
+ * G = e^{ik|x-y|}/(4 pi |x-y|) (Sec. 2.2.3, eq. 9), by the FFM of Sec. 2: two cubic
+ * octrees of equal edge (Sec. 2.2.1), a descent-only traversal with the admissibility
+ * test of Sec. 2.2.2, far fields by Chebyshev-Lagrange interpolation (Sec. 2.2.2) or by
+ * the Gegenbauer plane-wave expansion (Sec. 2.2.3), and a dense near field at the level
+ * where the stopping criterion of Sec. 2.2.4 holds.  Pairs of coincident points
+ * (|x-y| = 0) contribute nothing.
+ *
+ * Every step runs in CUDA kernels on the current device; no CPU fallback exists.
+ *
+ * Conventions
+ *   - Point sets are N x 3 row-major arrays (x0,y0,z0,x1,...) of float or double.
+ *   - Densities u (length N_Y per right-hand side) and results v (length N_X per
+ *     right-hand side) are column-major with nrhs columns: u[j + N_Y*m].  Complex values
+ *     are interleaved (re, im).
+ *   - Any array argument may live in device memory or in host memory (pageable or
+ *     pinned); host arrays are staged through device memory on the given stream.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls return after
+ *     enqueueing their work except where noted; ffm_plan synchronises its stream a
+ *     few times (pair counts decide allocation sizes).
+ *   - Functions return an ffm_status; no exception crosses the ABI.  On failure, output
+ *     handles are set to NULL and ffm_last_error() describes the cause.
+ */
+#ifndef FFM_GB300_H
+#define FFM_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ffm_plan_s ffm_plan_t;
+
+typedef enum {
+    FFM_OK = 0,
+    FFM_EINVAL = 1,      /* bad argument: N <= 0, eps outside (0,1), k < 0, NaN input, bad dtype */
+    FFM_ENOMEM = 2,      /* device allocation failed; nothing is leaked, no plan is returned */
+    FFM_ECUDA = 3,       /* a CUDA runtime call or kernel launch failed */
+    FFM_ETIMEOUT = 4,    /* a bounded device-side wait gave up */
+    FFM_EUNSUPPORTED = 5 /* valid request outside what this build implements */
+} ffm_status;
+
+typedef enum { FFM_LAPLACE = 0, FFM_HELMHOLTZ = 1 } ffm_kernel;
+
+typedef enum {
+    FFM_F32 = 0,  /* float */
+    FFM_F64 = 1,  /* double */
+    FFM_C64 = 2,  /* interleaved complex float */
+    FFM_C128 = 3  /* interleaved complex double */
+} ffm_dtype;
+
+/* Plan options.  Zero-initialise and set what you need; a NULL opts pointer means all
+ * defaults.  The defaults are the plan constants of the method (readings of the paper
+ * where it is silent): n_leaf = 64, l_cap = 21, kappa_switch = 2.0, r1 from the
+ * calibrated Lagrange error table. */
+typedef struct {
+    int n_leaf;           /* stop refining once the mean number of points per non-empty
+                             box (both trees) drops below n_leaf (Sec. 2.2.4); 0 -> 64 */
+    int l_cap;            /* deepest level (<= 21); 0 -> 21 */
+    double kappa_switch;  /* Helmholtz: plane waves at level l iff k d_l >= kappa_switch,
+                             Lagrange otherwise (Sec. 2.2.3); 0 -> 2.0 */
+    int r1_override;      /* Chebyshev nodes per axis for Lagrange levels (2..8); 0 -> rule */
+    int precision;        /* reserved, 0 */
+    const void *weights;  /* quadrature weights w_j (N_Y entries), host or device; NULL -> 1 */
+    ffm_dtype weights_dtype; /* FFM_F32 or FFM_F64 */
+} ffm_opts;
+
+/* Build a plan for targets X (nx points) and sources Y (ny points) (Sec. 2.2.1-2.2.4):
+ * bounding cubes, Morton sort of both sets, per-level box tables, the descent-only
+ * admissible / near pair lists, and the per-level transfer operators (one per distinct
+ * box translation, Sec. 3.1 proof of Prop. 1).
+ *   X, Y      : N x 3 row-major, dtype xdt / ydt in {FFM_F32, FFM_F64}; copied, so the
+ *               caller may free them when the call returns.
+ *   kernel, k : FFM_LAPLACE (k ignored) or FFM_HELMHOLTZ with wavenumber k >= 0.
+ *   eps       : requested accuracy, 0 < eps < 1 (sets the Lagrange rank and the
+ *               plane-wave rank L of eq. 13).
+ *   opts      : NULL or options (the weights are copied).
+ *   stream    : cudaStream_t for all work.
+ *   out       : receives the plan (NULL on failure).
+ * Errors: FFM_EINVAL on bad arguments or non-finite coordinates, FFM_ENOMEM, FFM_ECUDA,
+ * FFM_EUNSUPPORTED (eps needs r1 > 8). */
+ffm_status ffm_plan(const void *X, ffm_dtype xdt, int64_t nx, const void *Y, ffm_dtype ydt, int64_t ny,
+                    ffm_kernel kernel, double k, double eps, const ffm_opts *opts, void *stream,
+                    ffm_plan_t **out);
+
+/* v = G W u through the plan (Sec. 2.2, Fig. of the descent): far field of every level
+ * with admissible pairs, near field at the stop level, FP64 accumulation per target.
+ *   u   : N_Y x nrhs column-major; Laplace: FFM_F32 or FFM_F64; Helmholtz: FFM_C64 or
+ *         FFM_C128.
+ *   v   : N_X x nrhs column-major, same dtype as u; overwritten (not accumulated).
+ *   nrhs: number of right-hand sides, >= 1.
+ * Works on `stream`; returns once the work is enqueued (device u, v) or after the
+ * result has been copied back (host v).  The plan is read-only here, so concurrent
+ * applies on different streams are allowed.
+ * Errors: FFM_EINVAL (NULL plan, bad dtype, nrhs < 1), FFM_ENOMEM, FFM_ECUDA. */
+ffm_status ffm_apply(ffm_plan_t *plan, const void *u, ffm_dtype udt, int nrhs, void *v, void *stream);
+
+/* Release a plan and all its device memory.  NULL-safe.  Synchronises the plan's
+ * stream first. */
+void ffm_destroy(ffm_plan_t *plan);
+
+/* Device bytes held by the plan (for admission by memory footprint). */
+ffm_status ffm_plan_bytes(const ffm_plan_t *plan, size_t *bytes);
+
+/* Per-level description of a plan, for tests and reports.  Arrays are indexed by the
+ * level l = 0..21. mode: 0 no far field, 1 Lagrange, 2 plane waves. */
+typedef struct {
+    int l_stop;                /* level of the near field (leaf level) */
+    int root_admissible;       /* 1 if the two roots are already far apart (level-0 far field) */
+    double d0;                 /* common edge of the two root cubes */
+    double oX[3], oY[3];       /* lower corners of the root cubes */
+    int64_t nboxX[22], nboxY[22]; /* non-empty boxes per level (0 beyond the levels built) */
+    int64_t n_adm[22];         /* admissible pairs handled at each level */
+    int64_t n_near[22];        /* near pairs left after each level */
+    int64_t n_trans[22];       /* distinct box translations among the admissible pairs */
+    int mode[22];
+    int r1[22];                /* Chebyshev nodes per axis (Lagrange levels) */
+    int L[22];                 /* Gegenbauer rank (plane-wave levels) */
+    int nQ[22];                /* quadrature directions 2L(L+1) (plane-wave levels) */
+    int64_t nx, ny;
+} ffm_info;
+
+ffm_status ffm_plan_info(const ffm_plan_t *plan, ffm_info *info);
+
+/* Copy plan contents to host memory, for tests.
+ *   what = FFM_EXPORT_PERM_X / _PERM_Y: sorted position -> original index (int64, N).
+ *   what = FFM_EXPORT_ADM: admissible pairs of `level` as (X box id, Y box id) Morton ids
+ *          at that level (uint64 pairs, 2*count values).
+ *   what = FFM_EXPORT_NEAR: near pairs at the stop level, same format.
+ * With host_out NULL only *count is set.  Blocks until the copy is done. */
+enum { FFM_EXPORT_PERM_X = 0, FFM_EXPORT_PERM_Y = 1, FFM_EXPORT_ADM = 2, FFM_EXPORT_NEAR = 3 };
+ffm_status ffm_plan_export(const ffm_plan_t *plan, int what, int level, void *host_out, int64_t *count);
+
+/* Number of kernels this library has launched in this process (all threads). */
+uint64_t ffm_launch_count(void);
+
+/* Human-readable status name, and the message of the last failure in this thread. */
+const char *ffm_status_str(ffm_status s);
+const char *ffm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FFM_GB300_H */

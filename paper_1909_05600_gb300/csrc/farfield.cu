@@ -1,0 +1,534 @@
+// Far field of one level, computed on the fly from the plan's per-translation tables.
+//
+// Lagrange levels (Sec. 2.2.2):      u~_b = L_Y(b) (w u)_b ;  v~_a = sum_b T_t(a,b) u~_b ;
+//                                    v_a += L_X(a)^T v~_a
+// Plane-wave levels (Sec. 2.2.3):    u~_b(q) = sum_{j in b} e^{-ik s_q.(y_j - y0_b)} (w u)_j
+//                                    v~_a(q) = sum_b D_t(a,b)(q) u~_b(q)
+//                                    v_i    += sum_q e^{ik s_q.(x_i - x0_a)} v~_a(q)
+//
+// Plane-wave phases are split at the leaf: y - y0_b = (y - c_leaf) + (c_leaf - y0_b).
+// The first factor has a small argument (|k s.(y - c_leaf)| <= k sqrt(3) d_leaf / 2) and
+// is evaluated per (point, direction) with the FP32 special-function unit; the second
+// is a product of tabulated octant factors, one per level between the box and the leaf,
+// so that no large phase is ever rounded to FP32.  This only re-associates the sums of
+// Sec. 2.2.3 (e^{a+b} = e^a e^b); the F matrices are still applied exactly, without
+// NUFFT.
+#include "ffm_internal.cuh"
+
+namespace ffm {
+
+// ----------------------------------------------------------- helpers
+
+struct Cheb {
+    float t[R1MAX];  // Chebyshev nodes cos((2a+1) pi / (2 r1))
+    float w[R1MAX];  // 1 / prod_{b != a} (t_a - t_b)
+    int r1;
+};
+
+static Cheb make_cheb(int r1) {
+    Cheb c{};
+    c.r1 = r1;
+    double t[R1MAX];
+    for (int a = 0; a < r1; ++a) t[a] = std::cos((2.0 * a + 1.0) * PI / (2.0 * r1));
+    for (int a = 0; a < r1; ++a) {
+        double d = 1.0;
+        for (int b = 0; b < r1; ++b)
+            if (b != a) d *= t[a] - t[b];
+        c.t[a] = (float)t[a];
+        c.w[a] = (float)(1.0 / d);
+    }
+    return c;
+}
+
+// 1-D Lagrange basis at xi via prefix / suffix products.
+__device__ __forceinline__ void lag1d(const Cheb &c, float xi, float *out) {
+    float pre[R1MAX], suf[R1MAX];
+    float acc = 1.f;
+#pragma unroll
+    for (int a = 0; a < R1MAX; ++a) {
+        if (a < c.r1) {
+            pre[a] = acc;
+            acc *= xi - c.t[a];
+        }
+    }
+    acc = 1.f;
+#pragma unroll
+    for (int a = R1MAX - 1; a >= 0; --a) {
+        if (a < c.r1) {
+            suf[a] = acc;
+            acc *= xi - c.t[a];
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < R1MAX; ++a)
+        if (a < c.r1) out[a] = c.w[a] * pre[a] * suf[a];
+}
+
+// Offset of a leaf centre from the centre of its ancestor at level l, per axis:
+// d_ls * ((g_leaf + 1/2) - (g_box + 1/2) 2^(ls-l)).
+__device__ __forceinline__ float3 leaf_offset(int4 gl, int4 gb, int shift, float dls) {
+    float half = 0.5f * (float)(1 << shift);
+    return make_float3(dls * ((float)(gl.x - (gb.x << shift)) + 0.5f - half),
+                       dls * ((float)(gl.y - (gb.y << shift)) + 0.5f - half),
+                       dls * ((float)(gl.z - (gb.z << shift)) + 0.5f - half));
+}
+
+template <bool CPLX>
+struct QT;
+template <>
+struct QT<false> {
+    typedef float T;
+};
+template <>
+struct QT<true> {
+    typedef float2 T;
+};
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ float2 cmulc(float2 a, float2 b) {  // a * conj(b)
+    return make_float2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+
+struct LevelArgs {
+    // boxes of the level and the leaves
+    const uint32_t *box_start;
+    const int4 *box_g;
+    const uint32_t *leaf_start;
+    const int4 *leaf_g;
+    const float4 *eps;
+    int shift;  // l_stop - l
+    float dls;  // leaf edge
+    float inv_half_dl;  // 2 / d_l
+};
+
+// ========================================================= Lagrange kernels
+
+constexpr int LAG_T = 256;
+
+template <bool CPLX>
+__global__ void __launch_bounds__(LAG_T) k_lag_anterp(LevelArgs A, const uint32_t *__restrict__ src, Cheb cb,
+                                                      const typename QT<CPLX>::T *__restrict__ q, int64_t ny,
+                                                      int nrhs, typename QT<CPLX>::T *__restrict__ ut) {
+    typedef typename QT<CPLX>::T Q;
+    __shared__ float sl[LAG_T][3 * R1MAX + 1];
+    __shared__ Q sq[LAG_T];
+    int b = src[blockIdx.x], m = blockIdx.y;
+    int r1 = cb.r1, r = r1 * r1 * r1;
+    uint32_t s0 = A.box_start[b], s1 = A.box_start[b + 1];
+    int4 gb = A.box_g[b];
+    float accr[2] = {0.f, 0.f}, acci[2] = {0.f, 0.f};
+    for (uint32_t base = s0; base < s1; base += LAG_T) {
+        uint32_t j = base + threadIdx.x;
+        if (j < s1) {
+            float4 e = A.eps[j];
+            int4 gl = A.leaf_g[__float_as_uint(e.w)];
+            float3 o = leaf_offset(gl, gb, A.shift, A.dls);
+            lag1d(cb, (o.x + e.x) * A.inv_half_dl, &sl[threadIdx.x][0]);
+            lag1d(cb, (o.y + e.y) * A.inv_half_dl, &sl[threadIdx.x][R1MAX]);
+            lag1d(cb, (o.z + e.z) * A.inv_half_dl, &sl[threadIdx.x][2 * R1MAX]);
+            sq[threadIdx.x] = q[(int64_t)m * ny + j];
+        }
+        __syncthreads();
+        int cnt = min((uint32_t)LAG_T, s1 - base);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            int a = threadIdx.x + h * LAG_T;
+            if (a < r) {
+                int ia = a / (r1 * r1), ib = (a / r1) % r1, ic = a % r1;
+                for (int jj = 0; jj < cnt; ++jj) {
+                    float L = sl[jj][ia] * sl[jj][R1MAX + ib] * sl[jj][2 * R1MAX + ic];
+                    if constexpr (CPLX) {
+                        accr[h] = fmaf(L, sq[jj].x, accr[h]);
+                        acci[h] = fmaf(L, sq[jj].y, acci[h]);
+                    } else {
+                        accr[h] = fmaf(L, sq[jj], accr[h]);
+                    }
+                }
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        int a = threadIdx.x + h * LAG_T;
+        if (a < r) {
+            size_t o = ((size_t)b * nrhs + m) * r + a;
+            if constexpr (CPLX)
+                ut[o] = make_float2(accr[h], acci[h]);
+            else
+                ut[o] = accr[h];
+        }
+    }
+}
+
+// v~_a[i] = sum_e sum_j T[t_e][j][i] u~_{b_e}[j]; one thread per control node i.
+template <bool CPLX>
+__global__ void k_lag_transfer(const uint32_t *__restrict__ tgt, const uint32_t *__restrict__ off,
+                               const uint32_t *__restrict__ asrc, const uint32_t *__restrict__ at,
+                               const float *__restrict__ T, int r, int nrhs,
+                               const typename QT<CPLX>::T *__restrict__ ut, typename QT<CPLX>::T *__restrict__ vt) {
+    typedef typename QT<CPLX>::T Q;
+    extern __shared__ unsigned char smraw[];
+    Q *su = reinterpret_cast<Q *>(smraw);
+    int x = blockIdx.x, m = blockIdx.y;
+    int a = tgt[x];
+    float ar = 0.f, ai = 0.f;
+    for (uint32_t e = off[x]; e < off[x + 1]; ++e) {
+        uint32_t b = asrc[e], t = at[e];
+        __syncthreads();
+        for (int j = threadIdx.x; j < r; j += blockDim.x) su[j] = ut[((size_t)b * nrhs + m) * r + j];
+        __syncthreads();
+        int i = threadIdx.x;
+        if (i < r) {
+            if constexpr (CPLX) {
+                const float2 *Tt = reinterpret_cast<const float2 *>(T) + (size_t)t * r * r + i;
+                for (int j = 0; j < r; ++j) {
+                    float2 tv = Tt[(size_t)j * r];
+                    float2 uv = su[j];
+                    ar = fmaf(tv.x, uv.x, fmaf(-tv.y, uv.y, ar));
+                    ai = fmaf(tv.x, uv.y, fmaf(tv.y, uv.x, ai));
+                }
+            } else {
+                const float *Tt = T + (size_t)t * r * r + i;
+                for (int j = 0; j < r; ++j) ar = fmaf(Tt[(size_t)j * r], su[j], ar);
+            }
+        }
+    }
+    int i = threadIdx.x;
+    if (i < r) {
+        size_t o = ((size_t)a * nrhs + m) * r + i;
+        if constexpr (CPLX)
+            vt[o] = make_float2(ar, ai);
+        else
+            vt[o] = ar;
+    }
+}
+
+template <bool CPLX>
+__global__ void __launch_bounds__(128) k_lag_interp(LevelArgs A, const uint32_t *__restrict__ tgt, Cheb cb,
+                                                    const typename QT<CPLX>::T *__restrict__ vt, int nrhs,
+                                                    int64_t nx, double2 *__restrict__ acc) {
+    typedef typename QT<CPLX>::T Q;
+    __shared__ Q sv[R1MAX * R1MAX * R1MAX];
+    int a = tgt[blockIdx.x], m = blockIdx.y;
+    int r1 = cb.r1, r = r1 * r1 * r1;
+    for (int i = threadIdx.x; i < r; i += blockDim.x) sv[i] = vt[((size_t)a * nrhs + m) * r + i];
+    __syncthreads();
+    uint32_t s0 = A.box_start[a], s1 = A.box_start[a + 1];
+    int4 gb = A.box_g[a];
+    for (uint32_t i = s0 + threadIdx.x; i < s1; i += blockDim.x) {
+        float4 e = A.eps[i];
+        int4 gl = A.leaf_g[__float_as_uint(e.w)];
+        float3 o = leaf_offset(gl, gb, A.shift, A.dls);
+        float lx[R1MAX], ly[R1MAX], lz[R1MAX];
+        lag1d(cb, (o.x + e.x) * A.inv_half_dl, lx);
+        lag1d(cb, (o.y + e.y) * A.inv_half_dl, ly);
+        lag1d(cb, (o.z + e.z) * A.inv_half_dl, lz);
+        float sr = 0.f, si = 0.f;
+        for (int ia = 0; ia < r1; ++ia)
+            for (int ib = 0; ib < r1; ++ib) {
+                float lab = lx[ia] * ly[ib];
+                const Q *row = sv + (ia * r1 + ib) * r1;
+                for (int ic = 0; ic < r1; ++ic) {
+                    float L = lab * lz[ic];
+                    if constexpr (CPLX) {
+                        sr = fmaf(L, row[ic].x, sr);
+                        si = fmaf(L, row[ic].y, si);
+                    } else {
+                        sr = fmaf(L, row[ic], sr);
+                    }
+                }
+            }
+        double2 &dst = acc[(int64_t)m * nx + i];
+        dst.x += (double)sr;
+        dst.y += (double)si;
+    }
+}
+
+static LevelArgs level_args(const ffm_plan_s *p, const BoxLevel &B, const BoxLevel &Lf, const float4 *eps, int l) {
+    LevelArgs A;
+    A.box_start = B.start;
+    A.box_g = B.g;
+    A.leaf_start = Lf.start;
+    A.leaf_g = Lf.g;
+    A.eps = eps;
+    A.shift = p->l_stop - l;
+    A.dls = (float)std::ldexp(p->d0, -p->l_stop);
+    A.inv_half_dl = (float)(2.0 / std::ldexp(p->d0, -l));
+    return A;
+}
+
+void far_lagrange(const ffm_plan_s *p, int l, const void *q, int nrhs, double2 *acc, Alloc &tmp, cudaStream_t s) {
+    const FarLevel &F = p->far[l];
+    int ls = p->l_stop;
+    int r = F.r1 * F.r1 * F.r1;
+    Cheb cb = make_cheb(F.r1);
+    LevelArgs AY = level_args(p, p->by[l], p->by[ls], p->epsY, l);
+    LevelArgs AX = level_args(p, p->bx[l], p->bx[ls], p->epsX, l);
+    bool cplx = p->kind == FFM_HELMHOLTZ;
+    size_t esz = cplx ? sizeof(float2) : sizeof(float);
+    void *ut = tmp.raw(esz * r * nrhs * (size_t)p->by[l].nb);
+    void *vt = tmp.raw(esz * r * nrhs * (size_t)p->bx[l].nb);
+    dim3 gs((unsigned)F.n_src, nrhs), gt((unsigned)F.n_tgt, nrhs);
+    int tb = ((r + 31) / 32) * 32;
+    if (cplx) {
+        FFM_LAUNCH(k_lag_anterp<true>, gs, LAG_T, 0, s, AY, F.src, cb, (const float2 *)q, p->ny, nrhs, (float2 *)ut);
+        FFM_LAUNCH(k_lag_transfer<true>, gt, tb, r * sizeof(float2), s, F.tgt, F.adm_off, F.adm_src, F.adm_t, F.T, r,
+                   nrhs, (const float2 *)ut, (float2 *)vt);
+        FFM_LAUNCH(k_lag_interp<true>, gt, 128, 0, s, AX, F.tgt, cb, (const float2 *)vt, nrhs, p->nx, acc);
+    } else {
+        FFM_LAUNCH(k_lag_anterp<false>, gs, LAG_T, 0, s, AY, F.src, cb, (const float *)q, p->ny, nrhs, (float *)ut);
+        FFM_LAUNCH(k_lag_transfer<false>, gt, tb, r * sizeof(float), s, F.tgt, F.adm_off, F.adm_src, F.adm_t, F.T, r,
+                   nrhs, (const float *)ut, (float *)vt);
+        FFM_LAUNCH(k_lag_interp<false>, gt, 128, 0, s, AX, F.tgt, cb, (const float *)vt, nrhs, p->nx, acc);
+    }
+}
+
+// ======================================================= plane-wave kernels
+
+constexpr int PW_QPT = 2;     // directions per thread in the forward transform
+constexpr int PW_CHUNK = 256; // staged points per block iteration
+constexpr int PW_MAXD = 16;   // deepest supported level gap between box and leaf
+
+// Cody-Waite reduction of a phase to [-pi, pi] (two-term 2 pi), then FP32 sincos.
+template <bool REDUCE>
+__device__ __forceinline__ void phase_sincos(float ph, float &s, float &c) {
+    if constexpr (REDUCE) {
+        float n = rintf(ph * 0.15915494309189535f);
+        ph = fmaf(-n, 6.28318548202514648f, ph);
+        ph = fmaf(-n, -1.7484555314695172e-07f, ph);
+    }
+    __sincosf(ph, &s, &c);
+}
+
+struct PwArgs {
+    LevelArgs A;
+    const float4 *ks;
+    const float2 *E;  // [depth][oct][q]
+    int nQ;
+};
+
+// Leaf factor prod_{depth} E[depth][oct(depth)][q] (conjugated when CONJ).
+template <bool CONJ>
+__device__ __forceinline__ float2 leaf_factor(const PwArgs &P, int4 gl, int q) {
+    float2 f = make_float2(1.f, 0.f);
+    for (int d = 0; d < P.A.shift; ++d) {
+        int sh = P.A.shift - 1 - d;  // depth l+1+d sits sh levels above the leaf
+        int oct = (((gl.x >> sh) & 1) << 2) | (((gl.y >> sh) & 1) << 1) | ((gl.z >> sh) & 1);
+        float2 e = __ldg(&P.E[((size_t)d * 8 + oct) * P.nQ + q]);
+        f = CONJ ? cmulc(f, e) : cmul(f, e);
+    }
+    return f;
+}
+
+// Forward transform: u~_b(q) for a chunk of directions of one source box.
+template <bool REDUCE>
+__global__ void __launch_bounds__(128) k_pw_forward(PwArgs P, const uint32_t *__restrict__ src,
+                                                    const float2 *__restrict__ q, int64_t ny, int nrhs,
+                                                    float2 *__restrict__ ut) {
+    __shared__ float4 se[PW_CHUNK];
+    __shared__ float2 sq[PW_CHUNK];
+    int b = src[blockIdx.x], m = blockIdx.z;
+    int q0 = (blockIdx.y * blockDim.x + threadIdx.x) * PW_QPT;
+    float3 k3[PW_QPT];
+    bool on[PW_QPT];
+#pragma unroll
+    for (int t = 0; t < PW_QPT; ++t) {
+        on[t] = q0 + t < P.nQ;
+        float4 v = on[t] ? P.ks[q0 + t] : make_float4(0.f, 0.f, 0.f, 0.f);
+        k3[t] = make_float3(v.x, v.y, v.z);
+    }
+    float2 acc[PW_QPT], S[PW_QPT];
+#pragma unroll
+    for (int t = 0; t < PW_QPT; ++t) acc[t] = S[t] = make_float2(0.f, 0.f);
+    uint32_t s0 = P.A.box_start[b], s1 = P.A.box_start[b + 1];
+    uint32_t cur = 0xffffffffu;
+    for (uint32_t base = s0; base < s1; base += PW_CHUNK) {
+        int cnt = (int)min((uint32_t)PW_CHUNK, s1 - base);
+        __syncthreads();
+        for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
+            se[j] = P.A.eps[base + j];
+            sq[j] = q[(int64_t)m * ny + base + j];
+        }
+        __syncthreads();
+        for (int j = 0; j < cnt; ++j) {
+            float4 e = se[j];
+            uint32_t leaf = __float_as_uint(e.w);
+            if (leaf != cur) {
+                if (cur != 0xffffffffu) {
+                    int4 gl = P.A.leaf_g[cur];
+#pragma unroll
+                    for (int t = 0; t < PW_QPT; ++t) {
+                        float2 f = on[t] ? leaf_factor<false>(P, gl, q0 + t) : make_float2(0.f, 0.f);
+                        float2 v = cmul(f, S[t]);
+                        acc[t].x += v.x;
+                        acc[t].y += v.y;
+                        S[t] = make_float2(0.f, 0.f);
+                    }
+                }
+                cur = leaf;
+            }
+            float2 w = sq[j];
+#pragma unroll
+            for (int t = 0; t < PW_QPT; ++t) {
+                float ph = fmaf(k3[t].x, e.x, fmaf(k3[t].y, e.y, k3[t].z * e.z));
+                float sn, cs;
+                phase_sincos<REDUCE>(ph, sn, cs);
+                // e^{-i ph} w
+                S[t].x = fmaf(cs, w.x, fmaf(sn, w.y, S[t].x));
+                S[t].y = fmaf(cs, w.y, fmaf(-sn, w.x, S[t].y));
+            }
+        }
+    }
+    if (cur != 0xffffffffu) {
+        int4 gl = P.A.leaf_g[cur];
+#pragma unroll
+        for (int t = 0; t < PW_QPT; ++t) {
+            float2 f = on[t] ? leaf_factor<false>(P, gl, q0 + t) : make_float2(0.f, 0.f);
+            float2 v = cmul(f, S[t]);
+            acc[t].x += v.x;
+            acc[t].y += v.y;
+        }
+    }
+#pragma unroll
+    for (int t = 0; t < PW_QPT; ++t)
+        if (on[t]) ut[((size_t)b * nrhs + m) * P.nQ + q0 + t] = acc[t];
+}
+
+// Diagonal transfer: v~_a(q) = sum_{b adm a} D_t(q) u~_b(q).
+__global__ void k_pw_transfer(const uint32_t *__restrict__ tgt, const uint32_t *__restrict__ off,
+                              const uint32_t *__restrict__ asrc, const uint32_t *__restrict__ at,
+                              const float2 *__restrict__ D, int nQ, int nrhs, const float2 *__restrict__ ut,
+                              float2 *__restrict__ vt) {
+    int x = blockIdx.x, m = blockIdx.z;
+    int q = blockIdx.y * blockDim.x + threadIdx.x;
+    if (q >= nQ) return;
+    float ar = 0.f, ai = 0.f;
+    for (uint32_t e = off[x]; e < off[x + 1]; ++e) {
+        uint32_t b = asrc[e], t = at[e];
+        float2 d = D[(size_t)t * nQ + q];
+        float2 u = ut[((size_t)b * nrhs + m) * nQ + q];
+        ar = fmaf(d.x, u.x, fmaf(-d.y, u.y, ar));
+        ai = fmaf(d.x, u.y, fmaf(d.y, u.x, ai));
+    }
+    vt[((size_t)tgt[x] * nrhs + m) * nQ + q] = make_float2(ar, ai);
+}
+
+constexpr int PW_QC = 512;  // directions staged per block iteration in the backward transform
+
+// Backward transform for one target leaf: v_i += sum_q e^{ik s_q.(x_i - c_leaf)} W(q),
+// W(q) = v~_a(q) prod conj(E) (the leaf's octant path up to its level-l ancestor a).
+template <bool REDUCE>
+__global__ void __launch_bounds__(128) k_pw_backward(PwArgs P, const uint32_t *__restrict__ box_fine,
+                                                     int64_t nbox, const uint32_t *__restrict__ leaf_fine,
+                                                     const int *__restrict__ slot, const float2 *__restrict__ vt,
+                                                     int nrhs, int64_t nx, double2 *__restrict__ acc) {
+    __shared__ float4 sk[PW_QC];
+    __shared__ float2 sw[PW_QC];
+    __shared__ float2 red[128];
+    int leaf = blockIdx.x, m = blockIdx.z;
+    // ancestor at level l: last box whose first deep box index <= the leaf's
+    uint32_t lf = leaf_fine[leaf];
+    int64_t lo = 0, hi = nbox - 1;
+    while (lo < hi) {
+        int64_t mid = (lo + hi + 1) >> 1;
+        if (box_fine[mid] <= lf)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    int a = (int)lo;
+    if (slot[a] < 0) return;
+    uint32_t p0 = P.A.leaf_start[leaf], p1 = P.A.leaf_start[leaf + 1];
+    int np = (int)(p1 - p0);
+    int pr = np < 128 ? np : 128;
+    int G = 128 / pr;
+    int grp = threadIdx.x / pr, pi = threadIdx.x % pr;
+    bool active = grp < G;
+    int4 gl = P.A.leaf_g[leaf];
+    const float2 *va = vt + ((size_t)a * nrhs + m) * P.nQ;
+    for (int pb = 0; pb < np; pb += pr) {
+        bool valid = active && pb + pi < np;
+        float4 e = valid ? P.A.eps[p0 + pb + pi] : make_float4(0.f, 0.f, 0.f, 0.f);
+        float sr = 0.f, si = 0.f;
+        for (int qb = 0; qb < P.nQ; qb += PW_QC) {
+            int qc = min(PW_QC, P.nQ - qb);
+            __syncthreads();
+            for (int j = threadIdx.x; j < qc; j += blockDim.x) {
+                float4 k4 = P.ks[qb + j];
+                sk[j] = k4;
+                sw[j] = cmul(va[qb + j], leaf_factor<true>(P, gl, qb + j));
+            }
+            __syncthreads();
+            if (valid) {
+                for (int j = grp; j < qc; j += G) {
+                    float4 k4 = sk[j];
+                    float ph = fmaf(k4.x, e.x, fmaf(k4.y, e.y, k4.z * e.z));
+                    float sn, cs;
+                    phase_sincos<REDUCE>(ph, sn, cs);
+                    float2 w = sw[j];
+                    sr = fmaf(cs, w.x, fmaf(-sn, w.y, sr));
+                    si = fmaf(cs, w.y, fmaf(sn, w.x, si));
+                }
+            }
+        }
+        __syncthreads();
+        red[threadIdx.x] = make_float2(sr, si);
+        __syncthreads();
+        if (valid && grp == 0) {
+            float tr = 0.f, ti = 0.f;
+            for (int g = 0; g < G; ++g) {
+                tr += red[g * pr + pi].x;
+                ti += red[g * pr + pi].y;
+            }
+            double2 &dst = acc[(int64_t)m * nx + p0 + pb + pi];
+            dst.x += (double)tr;
+            dst.y += (double)ti;
+        }
+    }
+}
+
+__global__ void k_slot_init(int *slot, int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) slot[i] = -1;
+}
+__global__ void k_slot_set(const uint32_t *__restrict__ tgt, int64_t n, int *slot) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) slot[tgt[i]] = (int)i;
+}
+
+void far_planewave(const ffm_plan_s *p, int l, const float2 *q, int nrhs, double2 *acc, Alloc &tmp,
+                   cudaStream_t s) {
+    const FarLevel &F = p->far[l];
+    int ls = p->l_stop;
+    if (ls - l > PW_MAXD) fail(FFM_EUNSUPPORTED, "more than 16 levels between a plane-wave level and the leaves");
+    PwArgs PY{level_args(p, p->by[l], p->by[ls], p->epsY, l), F.ks, F.E, F.nQ};
+    PwArgs PX{level_args(p, p->bx[l], p->bx[ls], p->epsX, l), F.ks, F.E, F.nQ};
+    float2 *ut = tmp.get<float2>((size_t)p->by[l].nb * nrhs * F.nQ);
+    float2 *vt = tmp.get<float2>((size_t)p->bx[l].nb * nrhs * F.nQ);
+    // largest leaf-local phase: k sqrt(3) d_leaf / 2
+    bool reduce = p->k * std::sqrt(3.0) * std::ldexp(p->d0, -ls) * 0.5 > 3.0;
+    int fwd_per_block = 128 * PW_QPT;
+    dim3 gf((unsigned)F.n_src, cdiv(F.nQ, fwd_per_block), nrhs);
+    if (reduce)
+        FFM_LAUNCH(k_pw_forward<true>, gf, 128, 0, s, PY, F.src, q, p->ny, nrhs, ut);
+    else
+        FFM_LAUNCH(k_pw_forward<false>, gf, 128, 0, s, PY, F.src, q, p->ny, nrhs, ut);
+    dim3 gt((unsigned)F.n_tgt, cdiv(F.nQ, 128), nrhs);
+    FFM_LAUNCH(k_pw_transfer, gt, 128, 0, s, F.tgt, F.adm_off, F.adm_src, F.adm_t, F.D, F.nQ, nrhs, ut, vt);
+    int64_t nbx = p->bx[l].nb;
+    int *slot = tmp.get<int>(nbx);
+    FFM_LAUNCH(k_slot_init, cdiv(nbx, 256), 256, 0, s, slot, nbx);
+    FFM_LAUNCH(k_slot_set, cdiv(F.n_tgt, 256), 256, 0, s, F.tgt, F.n_tgt, slot);
+    dim3 gb((unsigned)p->bx[ls].nb, 1, nrhs);
+    if (reduce)
+        FFM_LAUNCH(k_pw_backward<true>, gb, 128, 0, s, PX, p->bx[l].fine, nbx, p->bx[ls].fine, slot, vt, nrhs, p->nx,
+                   acc);
+    else
+        FFM_LAUNCH(k_pw_backward<false>, gb, 128, 0, s, PX, p->bx[l].fine, nbx, p->bx[ls].fine, slot, vt, nrhs, p->nx,
+                   acc);
+}
+
+}  // namespace ffm

@@ -1,0 +1,144 @@
+// Internal declarations shared by the CUDA translation units of libffm_gb300.so.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+#include <string>
+#include <vector>
+
+#include "../../include/ffm.h"
+
+namespace ffm {
+
+constexpr int LMAX = 21;         // finest level of the Morton keys (3 x 21 bits)
+constexpr int R1MAX = 8;         // largest Chebyshev node count per axis
+constexpr double PI = 3.14159265358979323846;
+
+// ---------------------------------------------------------------- errors
+
+struct Error {
+    ffm_status status;
+    std::string msg;
+};
+
+[[noreturn]] void fail(ffm_status s, const std::string &msg);
+void check_cuda(cudaError_t e, const char *what);
+
+#define FFM_CUDA(call) ::ffm::check_cuda((call), #call)
+
+extern std::atomic<uint64_t> g_launches;
+
+// Every kernel launch goes through this: counts it and checks the launch status.
+template <class... KArgs, class... Args>
+inline void launch_kernel(const char *name, void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                          cudaStream_t s, Args &&...args) {
+    if (grid.x == 0 || grid.y == 0 || grid.z == 0) return;
+    k<<<grid, block, smem, s>>>(static_cast<KArgs>(args)...);
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    check_cuda(cudaGetLastError(), name);
+}
+
+#define FFM_LAUNCH(kernel, grid, block, smem, stream, ...) \
+    ::ffm::launch_kernel(#kernel, kernel, dim3(grid), dim3(block), (size_t)(smem), (stream), __VA_ARGS__)
+
+// ------------------------------------------------------- device memory
+
+// Stream-ordered device allocation owned by a scope or a plan.
+struct Alloc {
+    std::vector<void *> ptrs;
+    cudaStream_t stream = nullptr;
+    size_t bytes = 0;
+    void *raw(size_t n);
+    template <class T>
+    T *get(size_t count) {
+        return static_cast<T *>(raw(sizeof(T) * (count > 0 ? count : 1)));
+    }
+    void release();
+    ~Alloc() { release(); }
+};
+
+inline unsigned cdiv(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b); }
+
+// --------------------------------------------------- primitives (tree.cu)
+
+// Exclusive scan of n uint32 values (in may alias out); total written to *d_total if
+// non-null.  Temporaries from `al`.
+void scan_u32(const uint32_t *in, uint32_t *out, int64_t n, uint32_t *d_total, Alloc &al, cudaStream_t s);
+
+// Stable LSD radix sort of (key, val) by the key bits [0, nbits).  Buffers are
+// ping-ponged; the sorted data ends in (keys, vals) on return.
+void radix_sort_u64(uint64_t *keys, uint32_t *vals, int64_t n, int nbits, Alloc &al, cudaStream_t s);
+void radix_sort_u32(uint32_t *keys, uint32_t *vals, int64_t n, int nbits, Alloc &al, cudaStream_t s);
+
+// ----------------------------------------------------------- the plan
+
+struct BoxLevel {
+    int64_t nb = 0;             // number of non-empty boxes
+    uint32_t *start = nullptr;  // nb+1 sorted-position offsets (within the set)
+    int4 *g = nullptr;          // integer box coordinates at this level
+    uint32_t *first_leaf = nullptr;  // nb+1: first leaf (stop-level box) of each box
+    uint32_t *first_child = nullptr; // nb+1: first child in the next level (descent only)
+    uint32_t *fine = nullptr;   // nb: index of the first box of the deepest table
+};
+
+struct FarLevel {
+    int mode = 0;        // 0 none, 1 Lagrange, 2 plane waves
+    int r1 = 0, L = 0, nQ = 0;
+    int64_t n_adm = 0;
+    int n_trans = 0;
+    int64_t n_tgt = 0, n_src = 0;   // boxes with at least one admissible pair
+    uint32_t *tgt = nullptr;        // n_tgt target box indices
+    uint32_t *src = nullptr;        // n_src source box indices
+    uint32_t *adm_off = nullptr;    // n_tgt+1 CSR offsets (per listed target)
+    uint32_t *adm_src = nullptr;    // n_adm source box per pair
+    uint32_t *adm_t = nullptr;      // n_adm translation index per pair
+    int4 *trans_m = nullptr;        // n_trans integer offsets gX - gY
+    std::vector<int4> h_trans_m;
+    // Lagrange
+    float *T = nullptr;             // n_trans * r * r (real) or float2 (complex), [t][j][i]
+    // plane waves
+    float4 *ks = nullptr;           // nQ: k * s_q (x, y, z, 0)
+    float2 *D = nullptr;            // n_trans * nQ
+    float2 *E = nullptr;            // (l_stop - l) * 8 * nQ: octant phase factors
+};
+
+}  // namespace ffm
+
+struct ffm_plan_s {
+    int64_t nx = 0, ny = 0;
+    int kind = 0;
+    double k = 0, eps = 0;
+    int n_leaf = 64, l_cap = ffm::LMAX;
+    double kappa = 2.0;
+    int r1_override = 0;
+    double d0 = 1, oX[3] = {0, 0, 0}, oY[3] = {0, 0, 0}, sigma[3] = {0, 0, 0};
+    int l_stop = 0, root_adm = 0;
+    cudaStream_t stream = nullptr;
+    ffm::Alloc mem;                     // everything the plan owns
+    uint32_t *permX = nullptr, *permY = nullptr;  // sorted position -> original index
+    float4 *epsX = nullptr, *epsY = nullptr;      // leaf-relative coords; .w = leaf index bits
+    double *wY = nullptr;                          // sorted weights (or null)
+    uint64_t *keyX = nullptr, *keyY = nullptr;     // sorted Morton keys (exports)
+    ffm::BoxLevel bx[ffm::LMAX + 1], by[ffm::LMAX + 1];
+    ffm::FarLevel far[ffm::LMAX + 1];
+    int64_t n_near = 0;
+    uint32_t *near_off = nullptr;   // nbx(l_stop)+1 CSR over all target leaves
+    uint32_t *near_src = nullptr;   // n_near source leaf per pair
+    ffm_info info{};
+};
+
+namespace ffm {
+// tree.cu
+void build_plan(ffm_plan_s *p, const void *X, ffm_dtype xdt, const void *Y, ffm_dtype ydt, const void *w,
+                ffm_dtype wdt, Alloc &tmp);
+// tables.cu
+void build_tables(ffm_plan_s *p, int l, Alloc &tmp);
+int r1_rule(int kind, double eps);
+// farfield.cu / nearfield.cu
+void far_lagrange(const ffm_plan_s *p, int l, const void *q, int nrhs, double2 *acc, Alloc &tmp, cudaStream_t s);
+void far_planewave(const ffm_plan_s *p, int l, const float2 *q, int nrhs, double2 *acc, Alloc &tmp,
+                   cudaStream_t s);
+void near_field(const ffm_plan_s *p, const void *q, int nrhs, double2 *acc, cudaStream_t s);
+}  // namespace ffm

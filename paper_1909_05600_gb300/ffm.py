@@ -1,0 +1,214 @@
+"""Python binding of libffm_gb300.so (C ABI in include/ffm.h): argument marshalling only.
+
+Every step of the computation runs in the library's CUDA kernels.  There is no CPU path:
+if the shared library is missing or a CUDA device is not available, calls raise.
+
+Arrays may be torch tensors (CUDA or CPU) or numpy arrays (host memory); host arrays are
+staged to the device by the library.  Densities are laid out (nrhs, N) row-major, which
+is the ABI's column-major N x nrhs.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+try:
+    import torch
+except ImportError:  # pragma: no cover - torch is part of the environment
+    torch = None
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libffm_gb300.so")
+
+LAPLACE, HELMHOLTZ = 0, 1
+F32, F64, C64, C128 = 0, 1, 2, 3
+EXPORT_PERM_X, EXPORT_PERM_Y, EXPORT_ADM, EXPORT_NEAR = 0, 1, 2, 3
+STATUS = {0: "FFM_OK", 1: "FFM_EINVAL", 2: "FFM_ENOMEM", 3: "FFM_ECUDA", 4: "FFM_ETIMEOUT", 5: "FFM_EUNSUPPORTED"}
+
+# Every symbol include/ffm.h declares.
+ABI_SYMBOLS = ("ffm_plan", "ffm_apply", "ffm_destroy", "ffm_plan_bytes", "ffm_plan_info", "ffm_plan_export",
+               "ffm_launch_count", "ffm_status_str", "ffm_last_error")
+
+
+class FFMError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS.get(status, status), msg))
+        self.status = status
+
+
+class Opts(C.Structure):
+    _fields_ = [("n_leaf", C.c_int), ("l_cap", C.c_int), ("kappa_switch", C.c_double), ("r1_override", C.c_int),
+                ("precision", C.c_int), ("weights", C.c_void_p), ("weights_dtype", C.c_int)]
+
+
+class Info(C.Structure):
+    _fields_ = [("l_stop", C.c_int), ("root_admissible", C.c_int), ("d0", C.c_double), ("oX", C.c_double * 3),
+                ("oY", C.c_double * 3), ("nboxX", C.c_int64 * 22), ("nboxY", C.c_int64 * 22),
+                ("n_adm", C.c_int64 * 22), ("n_near", C.c_int64 * 22), ("n_trans", C.c_int64 * 22),
+                ("mode", C.c_int * 22), ("r1", C.c_int * 22), ("L", C.c_int * 22), ("nQ", C.c_int * 22),
+                ("nx", C.c_int64), ("ny", C.c_int64)]
+
+    def as_dict(self):
+        d = {"l_stop": self.l_stop, "root_admissible": self.root_admissible, "d0": self.d0, "oX": list(self.oX),
+             "oY": list(self.oY), "nx": self.nx, "ny": self.ny}
+        for f in ("nboxX", "nboxY", "n_adm", "n_near", "n_trans", "mode", "r1", "L", "nQ"):
+            d[f] = list(getattr(self, f))
+        return d
+
+
+_lib = None
+
+
+def lib():
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libffm_gb300.so is not built (run __graft_entry__.build() or "
+                               "python -m paper_1909_05600_gb300.build); there is no CPU fallback")
+        L = C.CDLL(LIB_PATH)
+        vp, i64 = C.c_void_p, C.c_int64
+        L.ffm_plan.argtypes = [vp, C.c_int, i64, vp, C.c_int, i64, C.c_int, C.c_double, C.c_double, C.POINTER(Opts),
+                               vp, C.POINTER(vp)]
+        L.ffm_plan.restype = C.c_int
+        L.ffm_apply.argtypes = [vp, vp, C.c_int, C.c_int, vp, vp]
+        L.ffm_apply.restype = C.c_int
+        L.ffm_destroy.argtypes = [vp]
+        L.ffm_destroy.restype = None
+        L.ffm_plan_bytes.argtypes = [vp, C.POINTER(C.c_size_t)]
+        L.ffm_plan_bytes.restype = C.c_int
+        L.ffm_plan_info.argtypes = [vp, C.POINTER(Info)]
+        L.ffm_plan_info.restype = C.c_int
+        L.ffm_plan_export.argtypes = [vp, C.c_int, C.c_int, vp, C.POINTER(i64)]
+        L.ffm_plan_export.restype = C.c_int
+        L.ffm_launch_count.restype = C.c_uint64
+        L.ffm_status_str.argtypes = [C.c_int]
+        L.ffm_status_str.restype = C.c_char_p
+        L.ffm_last_error.restype = C.c_char_p
+        _lib = L
+    return _lib
+
+
+def _check(rc):
+    if rc != 0:
+        raise FFMError(rc, lib().ffm_last_error().decode())
+
+
+def launch_count():
+    return int(lib().ffm_launch_count())
+
+
+_TORCH_DT = None
+
+
+def _dtype_code(a):
+    global _TORCH_DT
+    if torch is not None and isinstance(a, torch.Tensor):
+        if _TORCH_DT is None:
+            _TORCH_DT = {torch.float32: F32, torch.float64: F64, torch.complex64: C64, torch.complex128: C128}
+        return _TORCH_DT[a.dtype]
+    return {np.dtype(np.float32): F32, np.dtype(np.float64): F64, np.dtype(np.complex64): C64,
+            np.dtype(np.complex128): C128}[a.dtype]
+
+
+def _ptr(a):
+    if torch is not None and isinstance(a, torch.Tensor):
+        assert a.is_contiguous(), "tensors must be contiguous"
+        return a.data_ptr()
+    assert a.flags["C_CONTIGUOUS"], "arrays must be C-contiguous"
+    return a.ctypes.data
+
+
+def _stream_of(*arrays, stream=None):
+    if stream is not None:
+        return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    if torch is not None:
+        for a in arrays:
+            if isinstance(a, torch.Tensor) and a.is_cuda:
+                return torch.cuda.current_stream(a.device).cuda_stream
+    return 0
+
+
+class Plan:
+    """ffm_plan / ffm_apply / ffm_destroy.
+
+    X: (nx, 3), Y: (ny, 3) float32/float64; kernel LAPLACE or HELMHOLTZ; eps in (0, 1);
+    weights: (ny,) float32/float64 or None.
+    """
+
+    def __init__(self, X, Y, kernel, k=0.0, eps=1e-3, weights=None, stream=None, n_leaf=0, l_cap=0,
+                 kappa_switch=0.0, r1_override=0):
+        self._h = None
+        self._keep = (X, Y, weights)
+        o = Opts(n_leaf, l_cap, float(kappa_switch), r1_override, 0, None, F64)
+        if weights is not None:
+            o.weights = _ptr(weights)
+            o.weights_dtype = _dtype_code(weights)
+        self.stream = _stream_of(X, Y, stream=stream)
+        self.nx, self.ny = int(X.shape[0]), int(Y.shape[0])
+        self.kernel = kernel
+        h = C.c_void_p()
+        _check(lib().ffm_plan(_ptr(X), _dtype_code(X), self.nx, _ptr(Y), _dtype_code(Y), self.ny, kernel, float(k),
+                              float(eps), C.byref(o), self.stream, C.byref(h)))
+        self._h = h
+        self._keep = None
+
+    def close(self):
+        if self._h:
+            lib().ffm_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def apply(self, u, out=None, stream=None):
+        """v = G W u.  u: (ny,) or (nrhs, ny); returns (nx,) or (nrhs, nx) of u's dtype,
+        on u's device (torch) or as a numpy array (numpy input)."""
+        one = u.ndim == 1
+        nrhs = 1 if one else int(u.shape[0])
+        shape = (self.nx,) if one else (nrhs, self.nx)
+        if out is None:
+            if torch is not None and isinstance(u, torch.Tensor):
+                out = torch.empty(shape, dtype=u.dtype, device=u.device)
+            else:
+                out = np.empty(shape, dtype=u.dtype)
+        s = _stream_of(u, out, stream=stream)
+        _check(lib().ffm_apply(self._h, _ptr(u), _dtype_code(u), nrhs, _ptr(out), s))
+        return out
+
+    def info(self):
+        inf = Info()
+        _check(lib().ffm_plan_info(self._h, C.byref(inf)))
+        return inf.as_dict()
+
+    def bytes(self):
+        b = C.c_size_t()
+        _check(lib().ffm_plan_bytes(self._h, C.byref(b)))
+        return int(b.value)
+
+    def perm(self, which):
+        what = EXPORT_PERM_X if which == "X" else EXPORT_PERM_Y
+        n = C.c_int64()
+        _check(lib().ffm_plan_export(self._h, what, 0, None, C.byref(n)))
+        out = np.zeros(n.value, np.int64)
+        _check(lib().ffm_plan_export(self._h, what, 0, out.ctypes.data, C.byref(n)))
+        return out
+
+    def pairs(self, level, which):
+        """(n, 2) uint64 Morton box ids (X box, Y box): which='adm' at `level`, 'near' at the stop level."""
+        what = EXPORT_ADM if which == "adm" else EXPORT_NEAR
+        n = C.c_int64()
+        _check(lib().ffm_plan_export(self._h, what, level, None, C.byref(n)))
+        out = np.zeros((n.value, 2), np.uint64)
+        if n.value:
+            _check(lib().ffm_plan_export(self._h, what, level, out.ctypes.data, C.byref(n)))
+        return out
