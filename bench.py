@@ -1,0 +1,341 @@
+"""Benchmark of the FFM hot path on one or more GB300s (one process per GPU).
+
+A step is one whole FFM product through the C ABI, ffm_plan + ffm_apply + ffm_destroy
+(bounding cubes, Morton sort, box tables, descent, per-level operators, far field of every
+level, near field, accumulation), on inputs already resident in HBM.  The default workload
+is the Helmholtz kernel on 1,000,000 + 1,000,000 independent uniform points on the unit
+sphere, k at 10 points per wavelength (k = 177.2), complex64 densities, eps = 1e-3.
+
+Prints one JSON line (rank 0).  `value` is FFM products per second over all ranks;
+`e2e` is the same metric through the same API with host buffers (copies included);
+`roofline` is the dominant kernel against its pipe's peak; `cpu_baseline` is the FP64 CPU
+oracle (direct sum) timed on this host on a bounded sample of targets, which also gives
+the rel-L2 error of the GPU result on those targets.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ffm|reference]
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+SM_COUNT = 152
+MUFU_PER_SM_CLK = 16          # special-function unit results per SM per clock
+FP32_PER_SM_CLK = 128         # FP32 FMA lanes per SM per clock
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ffm", choices=["ffm", "reference"])
+    ap.add_argument("--workload", default="helmholtz_sphere_1M",
+                    choices=["helmholtz_sphere_1M", "laplace_sphere_20k"])
+    ap.add_argument("--cpu-targets", type=int, default=4096)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def make_problem(name, seed):
+    from paper_1909_05600_gb300 import workloads as W
+    if name == "helmholtz_sphere_1M":
+        return W.helmholtz_sphere(1_000_000, seed=seed)
+    return W.laplace_sphere(20000, seed=seed)
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.Q, "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.index)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def rejected(clk):
+    bad = {"hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown"}
+    if bad & set(clk.get("reasons", [])):
+        return True
+    if clk.get("sm_mhz") and clk.get("sm_max_mhz") and clk["sm_mhz"] < 0.5 * clk["sm_max_mhz"] \
+            and "sw_power_cap" not in clk.get("reasons", []):
+        return True
+    return False
+
+
+def cpu_direct_sample(prob, ntargets, seed=12345):
+    """The FP64 CPU oracle's direct sum (eq. 3) for a seeded subset of targets."""
+    from oracle import oracle as O
+    from paper_1909_05600_gb300 import workloads as W
+    t = W.sample_targets(prob.X.shape[0], ntargets, seed)
+    u = prob.u.astype(np.complex128) if np.iscomplexobj(prob.u) else prob.u.astype(np.float64)
+    t0 = time.perf_counter()
+    ref = O.direct(prob.X, prob.Y, u, prob.kind, prob.k, w=prob.w, targets=t)[:, 0]
+    dt = time.perf_counter() - t0
+    return t, ref, dt, O.nthreads()
+
+
+def run_reference(args, rank):
+    """The oracle as it stands, timed on this host's cores: each step is the FP64 direct
+    sum over all sources for a bounded sample of targets, scaled to the full product."""
+    if rank != 0:
+        return
+    prob = make_problem(args.workload, 1)
+    n = prob.X.shape[0]
+    ns = min(n, 1024 if args.workload == "helmholtz_sphere_1M" else n)
+    for _ in range(args.warmup):
+        cpu_direct_sample(prob, ns)
+    dts = []
+    cores = 0
+    for _ in range(args.steps):
+        _, _, dt, cores = cpu_direct_sample(prob, ns)
+        dts.append(dt * n / ns)
+    tot = sum(dts)
+    value = args.steps / tot
+    line = {"impl": "reference", "metric": "FFM applies/s", "value": value, "unit": "applies/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "n": n, "k": prob.k, "eps": prob.eps},
+            "cpu_baseline": {"value": value, "unit": "applies/s", "cores": cores, "kind": "oracle",
+                             "sample": "FP64 direct sum over all %d sources for %d seeded targets per step, "
+                                       "scaled to %d targets" % (n, ns, n)},
+            "e2e": {"value": value, "unit": "applies/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def roofline(prof, info, steps, clk, pk, pk_kind):
+    """Dominant kernel of the timed region against its pipe.  Plane-wave transforms and
+    the Helmholtz near field are bound by the special-function (MUFU) pipe: each
+    point-direction pair costs one sin and one cos; each Helmholtz near pair one rsqrt,
+    one sin and one cos; each Laplace near pair one rsqrt."""
+    name, (nl, ms) = max(prof.items(), key=lambda kv: kv[1][1])
+    mhz = pk.get("sm_max_mhz", 2070.0)
+    mufu_peak = SM_COUNT * MUFU_PER_SM_CLK * mhz * 1e6 / 1e12  # Tops/s
+    helm = any(m == 2 for m in info["mode"])
+    units = None
+    if "k_pw_forward" in name:
+        units = 2.0 * sum(info["src_points"][l] * info["nQ"][l] for l in range(22) if info["mode"][l] == 2)
+    elif "k_pw_backward" in name:
+        units = 2.0 * sum(info["tgt_points"][l] * info["nQ"][l] for l in range(22) if info["mode"][l] == 2)
+    elif "k_p2p" in name:
+        units = (3.0 if helm else 1.0) * info["p2p_pairs"]
+    out = {"kernel": name, "launches_per_step": nl / steps, "ms_per_step": ms / steps}
+    if units is None:
+        out.update({"bound": "alu", "achieved": None, "peak": None, "unit": None, "frac": None, "traffic": None})
+        return out
+    achieved = units * steps / (ms * 1e-3) / 1e12
+    out.update({"bound": "alu", "pipe": "MUFU", "achieved": achieved, "peak": mufu_peak, "unit": "Tops/s",
+                "frac": achieved / mufu_peak, "traffic": None,
+                "peak_basis": "%d SMs x %d MUFU results/clk x %.0f MHz (max SM clock, %s peaks file)"
+                              % (SM_COUNT, MUFU_PER_SM_CLK, mhz, pk_kind),
+                "units_per_step": units})
+    return out
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("gloo", rank=rank, world_size=world)
+    if args.impl == "reference":
+        run_reference(args, rank)
+        if dist:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+
+    import torch
+    from paper_1909_05600_gb300 import build, ffm
+
+    build.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    prob = make_problem(args.workload, 1 + rank)
+    n = max(prob.X.shape[0], prob.Y.shape[0])
+    X = torch.as_tensor(prob.X, device=dev)
+    Y = torch.as_tensor(prob.Y, device=dev)
+    w = torch.as_tensor(prob.w, device=dev)
+    u = torch.as_tensor(prob.u, device=dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(events=None):
+        if events:
+            events[0].record(stream)
+        p = ffm.Plan(X, Y, prob.kind, prob.k, prob.eps, weights=w)
+        if events:
+            events[1].record(stream)
+        v = p.apply(u)
+        if events:
+            events[2].record(stream)
+        p.close()
+        return v, p
+
+    info = None
+    for _ in range(args.warmup):
+        flush.zero_()
+        v, _ = step()
+    torch.cuda.synchronize()
+    with ffm.Plan(X, Y, prob.kind, prob.k, prob.eps, weights=w) as p0:
+        info = p0.info()
+
+    def timed():
+        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+        clocks = Clocks(local)
+        ffm.profile_reset()
+        l0 = ffm.launch_count()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        clocks.start()
+        vlast = None
+        for i in range(args.steps):
+            flush.zero_()  # L2 flush between steps, outside the step's events
+            ffm.profile_enable(True)
+            vlast, _ = step(ev[i])
+            ffm.profile_enable(False)
+        torch.cuda.synchronize()
+        clk = clocks.stop()
+        if dist:
+            dist.barrier()
+        launches = ffm.launch_count() - l0
+        t_plan = sum(e[0].elapsed_time(e[1]) for e in ev)
+        t_apply = sum(e[1].elapsed_time(e[2]) for e in ev)
+        return vlast, t_plan, t_apply, clk, launches, ffm.profile_read()
+
+    vlast, t_plan, t_apply, clk, launches, prof = timed()
+    note = None
+    if rejected(clk):
+        note = "first timed run rejected (clock reasons %s); re-measured" % clk.get("reasons")
+        vlast, t_plan, t_apply, clk, launches, prof = timed()
+    t_step = t_plan + t_apply  # ms over all steps (device time between the step's events)
+    if dist:
+        import torch.distributed as tdist
+        tt = torch.tensor([t_step, t_plan, t_apply], dtype=torch.float64)
+        tdist.all_reduce(tt, op=tdist.ReduceOp.MAX)
+        t_step, t_plan, t_apply = tt.tolist()
+    value = args.steps * world / (t_step * 1e-3)
+    pk, pk_kind = peaks()
+
+    e2e = None
+    if not args.no_e2e:
+        Xh = torch.as_tensor(prob.X).pin_memory()
+        Yh = torch.as_tensor(prob.Y).pin_memory()
+        wh = torch.as_tensor(prob.w).pin_memory()
+        uh = torch.as_tensor(prob.u).pin_memory()
+        vh = torch.empty(prob.X.shape[0], dtype=uh.dtype).pin_memory()
+        ke = max(2, args.steps // 2)
+        ts = []
+        for i in range(ke + 1):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            with ffm.Plan(Xh, Yh, prob.kind, prob.k, prob.eps, weights=wh, stream=stream) as ph:
+                ph.apply(uh, out=vh, stream=stream)
+            torch.cuda.synchronize()
+            if i:
+                ts.append(time.perf_counter() - t0)
+        h2d = Xh.numel() * Xh.element_size() + Yh.numel() * Yh.element_size() + wh.numel() * wh.element_size() \
+            + uh.numel() * uh.element_size()
+        e2e = {"value": world * len(ts) / sum(ts), "unit": "applies/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": vh.numel() * vh.element_size(), "steps": len(ts),
+               "api": "ffm_plan(host X, Y, w) + ffm_apply(host u -> host v) + ffm_destroy"}
+
+    cpu = None
+    err = None
+    if rank == 0 and not args.no_cpu_baseline:
+        vg = vlast.cpu().numpy()
+        t, ref, dt, cores = cpu_direct_sample(prob, args.cpu_targets)
+        err = float(np.linalg.norm(vg[t] - ref) / np.linalg.norm(ref))
+        cpu = {"value": 1.0 / (dt * prob.X.shape[0] / len(t)), "unit": "applies/s", "cores": cores, "kind": "oracle",
+               "sample": "FP64 direct sum over all %d sources for %d seeded targets (%.1f s), scaled to %d targets"
+                         % (prob.Y.shape[0], len(t), dt, prob.X.shape[0])}
+
+    if rank == 0:
+        rl = roofline(prof, info, args.steps, clk, pk, pk_kind)
+        kernels = {k: {"launches_per_step": v[0] / args.steps, "ms_per_step": v[1] / args.steps}
+                   for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}
+        line = {
+            "metric": "FFM applies/s", "value": value, "unit": "applies/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_step / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": args.workload, "n_x": int(prob.X.shape[0]), "n_y": int(prob.Y.shape[0]),
+                       "kernel": "helmholtz" if prob.kind == 1 else "laplace", "k": prob.k, "eps": prob.eps,
+                       "u_dtype": str(prob.u.dtype), "step": "ffm_plan + ffm_apply + ffm_destroy",
+                       "l2": "flushed between steps (512 MiB write, outside the step events)",
+                       "replicas": world},
+            "mpoints_per_s": n * value / 1e6,
+            "t_plan_ms": t_plan / args.steps, "t_apply_ms": t_apply / args.steps,
+            "apply_only_per_s": args.steps * world / (t_apply * 1e-3),
+            "err_vs_fp64_direct": err, "err_targets": args.cpu_targets if err is not None else None,
+            "roofline": rl, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": launches,
+            "kernels": kernels,
+            "plan": {"l_stop": info["l_stop"], "mode": info["mode"][:info["l_stop"] + 1],
+                     "L": info["L"][:info["l_stop"] + 1], "nQ": info["nQ"][:info["l_stop"] + 1],
+                     "n_adm": info["n_adm"][:info["l_stop"] + 1], "p2p_pairs": info["p2p_pairs"]},
+        }
+        if note:
+            line["note"] = note
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

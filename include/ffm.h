@@ -129,6 +129,9 @@ typedef struct {
     int L[22];                 /* Gegenbauer rank (plane-wave levels) */
     int nQ[22];                /* quadrature directions 2L(L+1) (plane-wave levels) */
     int64_t nx, ny;
+    int64_t src_points[22];    /* source points in boxes with admissible pairs (per level) */
+    int64_t tgt_points[22];    /* target points in boxes with admissible pairs (per level) */
+    int64_t p2p_pairs;         /* point pairs of the near field, sum over near leaf pairs of n_a n_b */
 } ffm_info;
 
 ffm_status ffm_plan_info(const ffm_plan_t *plan, ffm_info *info);
@@ -144,6 +147,17 @@ ffm_status ffm_plan_export(const ffm_plan_t *plan, int what, int level, void *ho
 
 /* Number of kernels this library has launched in this process (all threads). */
 uint64_t ffm_launch_count(void);
+
+/* Per-kernel device timing, for measurement.  While enabled, each kernel launch of this
+ * library is bracketed by two CUDA events on its stream; ffm_profile_read synchronises on
+ * those events and returns, per kernel name, the number of launches and the summed
+ * device time in milliseconds since the last reset.
+ *   names: buffer for up to `cap` NUL-terminated names, 64 bytes each (cap*64 bytes);
+ *   launches, ms: arrays of `cap` entries.  Returns the number of entries written.
+ * Not thread-safe with respect to concurrent launches from other threads. */
+void ffm_profile_enable(int on);
+void ffm_profile_reset(void);
+int ffm_profile_read(char *names, uint64_t *launches, double *ms, int cap);
 
 /* Human-readable status name, and the message of the last failure in this thread. */
 const char *ffm_status_str(ffm_status s);

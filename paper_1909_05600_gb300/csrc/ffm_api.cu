@@ -13,6 +13,48 @@ namespace ffm {
 std::atomic<uint64_t> g_launches{0};
 static thread_local std::string g_last_error;
 
+// ------------------------------------------------------------- profiling
+
+bool g_profile = false;
+struct ProfRec {
+    std::string name;
+    cudaEvent_t e0, e1;
+};
+static std::vector<ProfRec> g_prof_open;
+static std::vector<std::pair<std::string, std::pair<uint64_t, double>>> g_prof_tot;
+
+void profile_begin(const char *name, cudaStream_t s) {
+    ProfRec r;
+    r.name = name;
+    cudaEventCreate(&r.e0);
+    cudaEventCreate(&r.e1);
+    cudaEventRecord(r.e0, s);
+    g_prof_open.push_back(r);
+}
+
+void profile_end(cudaStream_t s) { cudaEventRecord(g_prof_open.back().e1, s); }
+
+static void profile_flush() {
+    for (ProfRec &r : g_prof_open) {
+        cudaEventSynchronize(r.e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, r.e0, r.e1);
+        cudaEventDestroy(r.e0);
+        cudaEventDestroy(r.e1);
+        bool found = false;
+        for (auto &t : g_prof_tot)
+            if (t.first == r.name) {
+                t.second.first += 1;
+                t.second.second += ms;
+                found = true;
+                break;
+            }
+        if (!found) g_prof_tot.push_back({r.name, {1, (double)ms}});
+    }
+    g_prof_open.clear();
+    cudaGetLastError();
+}
+
 void fail(ffm_status s, const std::string &msg) { throw Error{s, msg}; }
 
 void check_cuda(cudaError_t e, const char *what) {
@@ -338,6 +380,32 @@ ffm_status ffm_plan_export(const ffm_plan_t *plan, int what, int level, void *ho
 }
 
 uint64_t ffm_launch_count(void) { return g_launches.load(); }
+
+void ffm_profile_enable(int on) {
+    if (!on) profile_flush();
+    g_profile = on != 0;
+}
+
+void ffm_profile_reset(void) {
+    profile_flush();
+    g_prof_tot.clear();
+}
+
+int ffm_profile_read(char *names, uint64_t *launches, double *ms, int cap) {
+    profile_flush();
+    int n = 0;
+    for (auto &t : g_prof_tot) {
+        if (n >= cap) break;
+        if (names) {
+            std::strncpy(names + 64 * n, t.first.c_str(), 63);
+            names[64 * n + 63] = 0;
+        }
+        if (launches) launches[n] = t.second.first;
+        if (ms) ms[n] = t.second.second;
+        ++n;
+    }
+    return n;
+}
 
 const char *ffm_status_str(ffm_status s) {
     switch (s) {

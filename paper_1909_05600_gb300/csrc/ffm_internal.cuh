@@ -29,13 +29,18 @@ void check_cuda(cudaError_t e, const char *what);
 #define FFM_CUDA(call) ::ffm::check_cuda((call), #call)
 
 extern std::atomic<uint64_t> g_launches;
+extern bool g_profile;
+void profile_begin(const char *name, cudaStream_t s);
+void profile_end(cudaStream_t s);
 
 // Every kernel launch goes through this: counts it and checks the launch status.
 template <class... KArgs, class... Args>
 inline void launch_kernel(const char *name, void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem,
                           cudaStream_t s, Args &&...args) {
     if (grid.x == 0 || grid.y == 0 || grid.z == 0) return;
+    if (g_profile) profile_begin(name, s);
     k<<<grid, block, smem, s>>>(static_cast<KArgs>(args)...);
+    if (g_profile) profile_end(s);
     g_launches.fetch_add(1, std::memory_order_relaxed);
     check_cuda(cudaGetLastError(), name);
 }
@@ -118,7 +123,8 @@ struct ffm_plan_s {
     cudaStream_t stream = nullptr;
     ffm::Alloc mem;                     // everything the plan owns
     uint32_t *permX = nullptr, *permY = nullptr;  // sorted position -> original index
-    float4 *epsX = nullptr, *epsY = nullptr;      // leaf-relative coords; .w = leaf index bits
+    float4 *epsX = nullptr, *epsY = nullptr;      // leaf-relative coords (hi part); .w = leaf index bits
+    float4 *epsXlo = nullptr, *epsYlo = nullptr;  // FP32 residual of the leaf-relative coords (lo part)
     double *wY = nullptr;                          // sorted weights (or null)
     uint64_t *keyX = nullptr, *keyY = nullptr;     // sorted Morton keys (exports)
     ffm::BoxLevel bx[ffm::LMAX + 1], by[ffm::LMAX + 1];

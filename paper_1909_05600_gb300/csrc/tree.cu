@@ -546,6 +546,34 @@ __global__ void k_list_marked(const uint32_t *__restrict__ used, const uint32_t 
     if (i < n && used[i]) out[pos[i]] = (uint32_t)i;
 }
 
+// sum over listed boxes of their point counts
+__global__ void k_sum_sizes(const uint32_t *__restrict__ list, int64_t n, const uint32_t *__restrict__ start,
+                            unsigned long long *__restrict__ out) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned long long v = 0;
+    if (i < n) v = start[list[i] + 1] - start[list[i]];
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0 && v) atomicAdd(out, v);
+}
+
+// sum over pairs (a, b) of n_a * n_b
+__global__ void k_sum_pair_sizes(const uint32_t *__restrict__ a, const uint32_t *__restrict__ b, int64_t n,
+                                 const uint32_t *__restrict__ sa, const uint32_t *__restrict__ sb,
+                                 unsigned long long *__restrict__ out) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned long long v = 0;
+    if (i < n) v = (unsigned long long)(sa[a[i] + 1] - sa[a[i]]) * (sb[b[i] + 1] - sb[b[i]]);
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0 && v) atomicAdd(out, v);
+}
+
+static int64_t read_u64(const unsigned long long *d, cudaStream_t s) {
+    unsigned long long h;
+    FFM_CUDA(cudaMemcpyAsync(&h, d, sizeof h, cudaMemcpyDeviceToHost, s));
+    FFM_CUDA(cudaStreamSynchronize(s));
+    return (int64_t)h;
+}
+
 __global__ void k_hist_u32(const uint32_t *__restrict__ a, int64_t n, uint32_t *__restrict__ cnt) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) atomicAdd(&cnt[a[i]], 1u);
@@ -556,25 +584,28 @@ __global__ void k_hist_u32(const uint32_t *__restrict__ a, int64_t n, uint32_t *
 template <class T>
 __global__ void k_leaf_eps(const T *__restrict__ P, const uint32_t *__restrict__ perm,
                            const uint64_t *__restrict__ key, const uint32_t *__restrict__ lstart, int64_t nleaf,
-                           int64_t n, D3 o, double dls, int ls, float4 *__restrict__ eps) {
+                           int64_t n, D3 o, double dls, int ls, float4 *__restrict__ eps, float4 *__restrict__ lo) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     uint64_t k = key[i];
     int sh = LMAX - ls;
     double g0 = (double)(compact3(k >> 2) >> sh), g1 = (double)(compact3(k >> 1) >> sh), g2 = (double)(compact3(k) >> sh);
     uint32_t j = perm[i];
-    float e0 = (float)((double)P[3 * (int64_t)j] - (o.v[0] + (g0 + 0.5) * dls));
-    float e1 = (float)((double)P[3 * (int64_t)j + 1] - (o.v[1] + (g1 + 0.5) * dls));
-    float e2 = (float)((double)P[3 * (int64_t)j + 2] - (o.v[2] + (g2 + 0.5) * dls));
-    int64_t lo = 0, hi = nleaf - 1;  // last leaf with start <= i
-    while (lo < hi) {
-        int64_t mid = (lo + hi + 1) >> 1;
+    // leaf-relative coordinates as an unevaluated FP32 pair hi + lo
+    double d0 = (double)P[3 * (int64_t)j] - (o.v[0] + (g0 + 0.5) * dls);
+    double d1 = (double)P[3 * (int64_t)j + 1] - (o.v[1] + (g1 + 0.5) * dls);
+    double d2 = (double)P[3 * (int64_t)j + 2] - (o.v[2] + (g2 + 0.5) * dls);
+    float e0 = (float)d0, e1 = (float)d1, e2 = (float)d2;
+    int64_t lo_ = 0, hi_ = nleaf - 1;  // last leaf with start <= i
+    while (lo_ < hi_) {
+        int64_t mid = (lo_ + hi_ + 1) >> 1;
         if (lstart[mid] <= (uint32_t)i)
-            lo = mid;
+            lo_ = mid;
         else
-            hi = mid - 1;
+            hi_ = mid - 1;
     }
-    eps[i] = make_float4(e0, e1, e2, __uint_as_float((uint32_t)lo));
+    eps[i] = make_float4(e0, e1, e2, __uint_as_float((uint32_t)lo_));
+    lo[i] = make_float4((float)(d0 - (double)e0), (float)(d1 - (double)e1), (float)(d2 - (double)e2), 0.f);
 }
 
 template <class T>
@@ -624,9 +655,10 @@ static void launch_bbox(const void *P, int64_t n, unsigned long long *out, cudaS
 template <class T>
 static void launch_leaf_eps(const void *P, const uint32_t *perm, const uint64_t *key, const uint32_t *lstart,
                             int64_t nleaf, int64_t n, const double o[3], double dls, int ls, float4 *eps,
-                            cudaStream_t s) {
+                            float4 *lo, cudaStream_t s) {
     D3 oo{{o[0], o[1], o[2]}};
-    FFM_LAUNCH(k_leaf_eps<T>, cdiv(n, 256), 256, 0, s, (const T *)P, perm, key, lstart, nleaf, n, oo, dls, ls, eps);
+    FFM_LAUNCH(k_leaf_eps<T>, cdiv(n, 256), 256, 0, s, (const T *)P, perm, key, lstart, nleaf, n, oo, dls, ls, eps,
+               lo);
 }
 
 static uint32_t read_u32(const uint32_t *d, cudaStream_t s) {
@@ -756,6 +788,12 @@ static void finish_far_level(ffm_plan_s *p, int l, uint32_t *aa, uint32_t *ab, i
     F.n_src = read_u32(tot, s);
     F.src = p->mem.get<uint32_t>(F.n_src);
     FFM_LAUNCH(k_list_marked, cdiv(nby, 256), 256, 0, s, su, spos, nby, F.src);
+    unsigned long long *sums = tmp.get<unsigned long long>(2);
+    FFM_CUDA(cudaMemsetAsync(sums, 0, 2 * sizeof(unsigned long long), s));
+    FFM_LAUNCH(k_sum_sizes, cdiv(F.n_src, 256), 256, 0, s, F.src, F.n_src, p->by[l].start, sums);
+    FFM_LAUNCH(k_sum_sizes, cdiv(F.n_tgt, 256), 256, 0, s, F.tgt, F.n_tgt, p->bx[l].start, sums + 1);
+    p->info.src_points[l] = read_u64(sums, s);
+    p->info.tgt_points[l] = read_u64(sums + 1, s);
     p->info.mode[l] = F.mode;
     if (F.mode == 1) {
         F.r1 = p->r1_override > 0 ? p->r1_override : r1_rule(p->kind, p->eps);
@@ -930,6 +968,11 @@ void build_plan(ffm_plan_s *p, const void *X, ffm_dtype xdt, const void *Y, ffm_
         FFM_CUDA(cudaMemsetAsync(h, 0, sizeof(uint32_t) * (nleafX + 1), s));
         FFM_LAUNCH(k_hist_u32, cdiv(nnear, 256), 256, 0, s, c.a, nnear, h);
         scan_u32(h, p->near_off, nleafX + 1, nullptr, tmp, s);
+        unsigned long long *pp = tmp.get<unsigned long long>(1);
+        FFM_CUDA(cudaMemsetAsync(pp, 0, sizeof(unsigned long long), s));
+        FFM_LAUNCH(k_sum_pair_sizes, cdiv(nnear, 256), 256, 0, s, c.a, c.b, nnear, p->bx[ls].start, p->by[ls].start,
+                   pp);
+        p->info.p2p_pairs = read_u64(pp, s);
     } else {
         FFM_CUDA(cudaMemsetAsync(p->near_off, 0, sizeof(uint32_t) * (nleafX + 1), s));
     }
@@ -945,14 +988,16 @@ void build_plan(ffm_plan_s *p, const void *X, ffm_dtype xdt, const void *Y, ffm_
     double dls = std::ldexp(d0, -ls);
     p->epsX = p->mem.get<float4>(nx);
     p->epsY = p->mem.get<float4>(ny);
+    p->epsXlo = p->mem.get<float4>(nx);
+    p->epsYlo = p->mem.get<float4>(ny);
     if (xdt == FFM_F64)
-        launch_leaf_eps<double>(dX, p->permX, p->keyX, p->bx[ls].start, p->bx[ls].nb, nx, p->oX, dls, ls, p->epsX, s);
+        launch_leaf_eps<double>(dX, p->permX, p->keyX, p->bx[ls].start, p->bx[ls].nb, nx, p->oX, dls, ls, p->epsX, p->epsXlo, s);
     else
-        launch_leaf_eps<float>(dX, p->permX, p->keyX, p->bx[ls].start, p->bx[ls].nb, nx, p->oX, dls, ls, p->epsX, s);
+        launch_leaf_eps<float>(dX, p->permX, p->keyX, p->bx[ls].start, p->bx[ls].nb, nx, p->oX, dls, ls, p->epsX, p->epsXlo, s);
     if (ydt == FFM_F64)
-        launch_leaf_eps<double>(dY, p->permY, p->keyY, p->by[ls].start, p->by[ls].nb, ny, p->oY, dls, ls, p->epsY, s);
+        launch_leaf_eps<double>(dY, p->permY, p->keyY, p->by[ls].start, p->by[ls].nb, ny, p->oY, dls, ls, p->epsY, p->epsYlo, s);
     else
-        launch_leaf_eps<float>(dY, p->permY, p->keyY, p->by[ls].start, p->by[ls].nb, ny, p->oY, dls, ls, p->epsY, s);
+        launch_leaf_eps<float>(dY, p->permY, p->keyY, p->by[ls].start, p->by[ls].nb, ny, p->oY, dls, ls, p->epsY, p->epsYlo, s);
     if (w) {
         const void *dw = to_device(w, (wdt == FFM_F64 ? 8 : 4) * (size_t)ny, tmp, s);
         p->wY = p->mem.get<double>(ny);

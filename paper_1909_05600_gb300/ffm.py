@@ -27,7 +27,8 @@ STATUS = {0: "FFM_OK", 1: "FFM_EINVAL", 2: "FFM_ENOMEM", 3: "FFM_ECUDA", 4: "FFM
 
 # Every symbol include/ffm.h declares.
 ABI_SYMBOLS = ("ffm_plan", "ffm_apply", "ffm_destroy", "ffm_plan_bytes", "ffm_plan_info", "ffm_plan_export",
-               "ffm_launch_count", "ffm_status_str", "ffm_last_error")
+               "ffm_launch_count", "ffm_profile_enable", "ffm_profile_reset", "ffm_profile_read", "ffm_status_str",
+               "ffm_last_error")
 
 
 class FFMError(RuntimeError):
@@ -46,12 +47,14 @@ class Info(C.Structure):
                 ("oY", C.c_double * 3), ("nboxX", C.c_int64 * 22), ("nboxY", C.c_int64 * 22),
                 ("n_adm", C.c_int64 * 22), ("n_near", C.c_int64 * 22), ("n_trans", C.c_int64 * 22),
                 ("mode", C.c_int * 22), ("r1", C.c_int * 22), ("L", C.c_int * 22), ("nQ", C.c_int * 22),
-                ("nx", C.c_int64), ("ny", C.c_int64)]
+                ("nx", C.c_int64), ("ny", C.c_int64), ("src_points", C.c_int64 * 22),
+                ("tgt_points", C.c_int64 * 22), ("p2p_pairs", C.c_int64)]
 
     def as_dict(self):
         d = {"l_stop": self.l_stop, "root_admissible": self.root_admissible, "d0": self.d0, "oX": list(self.oX),
-             "oY": list(self.oY), "nx": self.nx, "ny": self.ny}
-        for f in ("nboxX", "nboxY", "n_adm", "n_near", "n_trans", "mode", "r1", "L", "nQ"):
+             "oY": list(self.oY), "nx": self.nx, "ny": self.ny, "p2p_pairs": self.p2p_pairs}
+        for f in ("nboxX", "nboxY", "n_adm", "n_near", "n_trans", "mode", "r1", "L", "nQ", "src_points",
+                  "tgt_points"):
             d[f] = list(getattr(self, f))
         return d
 
@@ -82,6 +85,11 @@ def lib():
         L.ffm_plan_export.argtypes = [vp, C.c_int, C.c_int, vp, C.POINTER(i64)]
         L.ffm_plan_export.restype = C.c_int
         L.ffm_launch_count.restype = C.c_uint64
+        L.ffm_profile_enable.argtypes = [C.c_int]
+        L.ffm_profile_enable.restype = None
+        L.ffm_profile_reset.restype = None
+        L.ffm_profile_read.argtypes = [C.c_char_p, C.POINTER(C.c_uint64), C.POINTER(C.c_double), C.c_int]
+        L.ffm_profile_read.restype = C.c_int
         L.ffm_status_str.argtypes = [C.c_int]
         L.ffm_status_str.restype = C.c_char_p
         L.ffm_last_error.restype = C.c_char_p
@@ -96,6 +104,28 @@ def _check(rc):
 
 def launch_count():
     return int(lib().ffm_launch_count())
+
+
+def profile_enable(on=True):
+    """Bracket every kernel launch of the library with CUDA events (per-kernel device time)."""
+    lib().ffm_profile_enable(1 if on else 0)
+
+
+def profile_reset():
+    lib().ffm_profile_reset()
+
+
+def profile_read(cap=256):
+    """{kernel name: (launches, total device ms)} since the last reset."""
+    names = C.create_string_buffer(64 * cap)
+    n_l = (C.c_uint64 * cap)()
+    ms = (C.c_double * cap)()
+    n = lib().ffm_profile_read(names, n_l, ms, cap)
+    out = {}
+    for i in range(n):
+        nm = names.raw[64 * i:64 * (i + 1)].split(b"\0", 1)[0].decode()
+        out[nm] = (int(n_l[i]), float(ms[i]))
+    return out
 
 
 _TORCH_DT = None
