@@ -132,6 +132,8 @@ typedef struct {
     int64_t src_points[22];    /* source points in boxes with admissible pairs (per level) */
     int64_t tgt_points[22];    /* target points in boxes with admissible pairs (per level) */
     int64_t p2p_pairs;         /* point pairs of the near field, sum over near leaf pairs of n_a n_b */
+    int pw64[22];              /* 1 if the level's plane-wave kernels run in FP64 */
+    double cancel[22];         /* cancellation ratio of the level's quadrature sum (closest pair) */
 } ffm_info;
 
 ffm_status ffm_plan_info(const ffm_plan_t *plan, ffm_info *info);

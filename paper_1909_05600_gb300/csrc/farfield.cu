@@ -291,6 +291,34 @@ void far_lagrange(const ffm_plan_s *p, int l, const void *q, int nrhs, double2 *
 constexpr int PW_QPT = 2;     // directions per thread in the forward transform
 constexpr int PW_CHUNK = 256; // staged points per block iteration
 constexpr int PW_MAXD = 16;   // deepest supported level gap between box and leaf
+constexpr int PW_QC = 512;    // directions staged per block iteration in the backward transform
+
+// Scalar-type traits: FP32 levels use float tables and MUFU sincos; FP64 levels (large
+// cancellation in the quadrature sum) use double tables, leaf coordinates hi + lo and
+// FP64 sincos.
+template <class R>
+struct PwT;
+template <>
+struct PwT<float> {
+    typedef float2 C;
+    typedef float4 K;
+};
+template <>
+struct PwT<double> {
+    typedef double2 C;
+    typedef D4 K;
+};
+
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ double2 cmulc(double2 a, double2 b) {
+    return make_double2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+__device__ __forceinline__ float2 czero(float) { return make_float2(0.f, 0.f); }
+__device__ __forceinline__ double2 czero(double) { return make_double2(0.0, 0.0); }
+__device__ __forceinline__ float2 cone(float) { return make_float2(1.f, 0.f); }
+__device__ __forceinline__ double2 cone(double) { return make_double2(1.0, 0.0); }
 
 // Cody-Waite reduction of a phase to [-pi, pi] (two-term 2 pi), then FP32 sincos.
 template <bool REDUCE>
@@ -302,47 +330,79 @@ __device__ __forceinline__ void phase_sincos(float ph, float &s, float &c) {
     }
     __sincosf(ph, &s, &c);
 }
+template <bool REDUCE>
+__device__ __forceinline__ void phase_sincos(double ph, double &s, double &c) {
+    sincos(ph, &s, &c);
+}
 
+// Leaf-relative coordinates of a point in the level's scalar type (hi part only in FP32,
+// hi + lo in FP64).
+template <class R>
+struct Coord;
+template <>
+struct Coord<float> {
+    static __device__ __forceinline__ float3 get(const float4 &hi, const float4 *, uint32_t) {
+        return make_float3(hi.x, hi.y, hi.z);
+    }
+};
+template <>
+struct Coord<double> {
+    static __device__ __forceinline__ double3 get(const float4 &hi, const float4 *lo, uint32_t i) {
+        float4 l = lo[i];
+        return make_double3((double)hi.x + (double)l.x, (double)hi.y + (double)l.y, (double)hi.z + (double)l.z);
+    }
+};
+
+template <class R>
 struct PwArgs {
     LevelArgs A;
-    const float4 *ks;
-    const float2 *E;  // [depth][oct][q]
+    const float4 *eps_lo;  // lo parts of the leaf-relative coordinates (FP64 levels)
+    const typename PwT<R>::K *ks;
+    const typename PwT<R>::C *E;  // [depth][oct][q]
     int nQ;
 };
 
 // Leaf factor prod_{depth} E[depth][oct(depth)][q] (conjugated when CONJ).
-template <bool CONJ>
-__device__ __forceinline__ float2 leaf_factor(const PwArgs &P, int4 gl, int q) {
-    float2 f = make_float2(1.f, 0.f);
+template <bool CONJ, class R>
+__device__ __forceinline__ typename PwT<R>::C leaf_factor(const PwArgs<R> &P, int4 gl, int q) {
+    typename PwT<R>::C f = cone(R(0));
     for (int d = 0; d < P.A.shift; ++d) {
         int sh = P.A.shift - 1 - d;  // depth l+1+d sits sh levels above the leaf
         int oct = (((gl.x >> sh) & 1) << 2) | (((gl.y >> sh) & 1) << 1) | ((gl.z >> sh) & 1);
-        float2 e = __ldg(&P.E[((size_t)d * 8 + oct) * P.nQ + q]);
+        typename PwT<R>::C e = P.E[((size_t)d * 8 + oct) * P.nQ + q];
         f = CONJ ? cmulc(f, e) : cmul(f, e);
     }
     return f;
 }
 
-// Forward transform: u~_b(q) for a chunk of directions of one source box.
-template <bool REDUCE>
-__global__ void __launch_bounds__(128) k_pw_forward(PwArgs P, const uint32_t *__restrict__ src,
+// Forward transform: u~_b(q) for a chunk of directions of one source box.  The points of
+// the box are streamed through shared memory in Morton order; each leaf's partial sum
+// (leaf-centred phases) is moved to the box centre by its octant factor.
+template <class R, bool REDUCE>
+__global__ void __launch_bounds__(128) k_pw_forward(PwArgs<R> P, const uint32_t *__restrict__ src,
                                                     const float2 *__restrict__ q, int64_t ny, int nrhs,
-                                                    float2 *__restrict__ ut) {
+                                                    typename PwT<R>::C *__restrict__ ut) {
+    typedef typename PwT<R>::C C2;
     __shared__ float4 se[PW_CHUNK];
+    __shared__ float4 sl[sizeof(R) == 8 ? PW_CHUNK : 1];
     __shared__ float2 sq[PW_CHUNK];
     int b = src[blockIdx.x], m = blockIdx.z;
     int q0 = (blockIdx.y * blockDim.x + threadIdx.x) * PW_QPT;
-    float3 k3[PW_QPT];
+    R kx[PW_QPT], ky[PW_QPT], kz[PW_QPT];
     bool on[PW_QPT];
 #pragma unroll
     for (int t = 0; t < PW_QPT; ++t) {
         on[t] = q0 + t < P.nQ;
-        float4 v = on[t] ? P.ks[q0 + t] : make_float4(0.f, 0.f, 0.f, 0.f);
-        k3[t] = make_float3(v.x, v.y, v.z);
+        kx[t] = ky[t] = kz[t] = R(0);
+        if (on[t]) {
+            kx[t] = P.ks[q0 + t].x;
+            ky[t] = P.ks[q0 + t].y;
+            kz[t] = P.ks[q0 + t].z;
+        }
     }
-    float2 acc[PW_QPT], S[PW_QPT];
+    C2 acc[PW_QPT], S[PW_QPT];
 #pragma unroll
-    for (int t = 0; t < PW_QPT; ++t) acc[t] = S[t] = make_float2(0.f, 0.f);
+    for (int t = 0; t < PW_QPT; ++t) acc[t] = S[t] = czero(R(0));
     uint32_t s0 = P.A.box_start[b], s1 = P.A.box_start[b + 1];
     uint32_t cur = 0xffffffffu;
     for (uint32_t base = s0; base < s1; base += PW_CHUNK) {
@@ -350,35 +410,37 @@ __global__ void __launch_bounds__(128) k_pw_forward(PwArgs P, const uint32_t *__
         __syncthreads();
         for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
             se[j] = P.A.eps[base + j];
+            if constexpr (sizeof(R) == 8) sl[j] = P.eps_lo[base + j];
             sq[j] = q[(int64_t)m * ny + base + j];
         }
         __syncthreads();
         for (int j = 0; j < cnt; ++j) {
-            float4 e = se[j];
-            uint32_t leaf = __float_as_uint(e.w);
+            float4 eh = se[j];
+            uint32_t leaf = __float_as_uint(eh.w);
             if (leaf != cur) {
                 if (cur != 0xffffffffu) {
                     int4 gl = P.A.leaf_g[cur];
 #pragma unroll
                     for (int t = 0; t < PW_QPT; ++t) {
-                        float2 f = on[t] ? leaf_factor<false>(P, gl, q0 + t) : make_float2(0.f, 0.f);
-                        float2 v = cmul(f, S[t]);
+                        C2 f = on[t] ? leaf_factor<false>(P, gl, q0 + t) : czero(R(0));
+                        C2 v = cmul(f, S[t]);
                         acc[t].x += v.x;
                         acc[t].y += v.y;
-                        S[t] = make_float2(0.f, 0.f);
+                        S[t] = czero(R(0));
                     }
                 }
                 cur = leaf;
             }
+            auto e = Coord<R>::get(eh, sl, (uint32_t)j);
             float2 w = sq[j];
 #pragma unroll
             for (int t = 0; t < PW_QPT; ++t) {
-                float ph = fmaf(k3[t].x, e.x, fmaf(k3[t].y, e.y, k3[t].z * e.z));
-                float sn, cs;
+                R ph = kx[t] * e.x + ky[t] * e.y + kz[t] * e.z;
+                R sn, cs;
                 phase_sincos<REDUCE>(ph, sn, cs);
                 // e^{-i ph} w
-                S[t].x = fmaf(cs, w.x, fmaf(sn, w.y, S[t].x));
-                S[t].y = fmaf(cs, w.y, fmaf(-sn, w.x, S[t].y));
+                S[t].x += cs * (R)w.x + sn * (R)w.y;
+                S[t].y += cs * (R)w.y - sn * (R)w.x;
             }
         }
     }
@@ -386,8 +448,8 @@ __global__ void __launch_bounds__(128) k_pw_forward(PwArgs P, const uint32_t *__
         int4 gl = P.A.leaf_g[cur];
 #pragma unroll
         for (int t = 0; t < PW_QPT; ++t) {
-            float2 f = on[t] ? leaf_factor<false>(P, gl, q0 + t) : make_float2(0.f, 0.f);
-            float2 v = cmul(f, S[t]);
+            C2 f = on[t] ? leaf_factor<false>(P, gl, q0 + t) : czero(R(0));
+            C2 v = cmul(f, S[t]);
             acc[t].x += v.x;
             acc[t].y += v.y;
         }
@@ -398,36 +460,40 @@ __global__ void __launch_bounds__(128) k_pw_forward(PwArgs P, const uint32_t *__
 }
 
 // Diagonal transfer: v~_a(q) = sum_{b adm a} D_t(q) u~_b(q).
+template <class C2>
 __global__ void k_pw_transfer(const uint32_t *__restrict__ tgt, const uint32_t *__restrict__ off,
                               const uint32_t *__restrict__ asrc, const uint32_t *__restrict__ at,
-                              const float2 *__restrict__ D, int nQ, int nrhs, const float2 *__restrict__ ut,
-                              float2 *__restrict__ vt) {
+                              const C2 *__restrict__ D, int nQ, int nrhs, const C2 *__restrict__ ut,
+                              C2 *__restrict__ vt) {
     int x = blockIdx.x, m = blockIdx.z;
     int q = blockIdx.y * blockDim.x + threadIdx.x;
     if (q >= nQ) return;
-    float ar = 0.f, ai = 0.f;
+    C2 a;
+    a.x = 0;
+    a.y = 0;
     for (uint32_t e = off[x]; e < off[x + 1]; ++e) {
         uint32_t b = asrc[e], t = at[e];
-        float2 d = D[(size_t)t * nQ + q];
-        float2 u = ut[((size_t)b * nrhs + m) * nQ + q];
-        ar = fmaf(d.x, u.x, fmaf(-d.y, u.y, ar));
-        ai = fmaf(d.x, u.y, fmaf(d.y, u.x, ai));
+        C2 d = D[(size_t)t * nQ + q];
+        C2 u = ut[((size_t)b * nrhs + m) * nQ + q];
+        a.x += d.x * u.x - d.y * u.y;
+        a.y += d.x * u.y + d.y * u.x;
     }
-    vt[((size_t)tgt[x] * nrhs + m) * nQ + q] = make_float2(ar, ai);
+    vt[((size_t)tgt[x] * nrhs + m) * nQ + q] = a;
 }
-
-constexpr int PW_QC = 512;  // directions staged per block iteration in the backward transform
 
 // Backward transform for one target leaf: v_i += sum_q e^{ik s_q.(x_i - c_leaf)} W(q),
 // W(q) = v~_a(q) prod conj(E) (the leaf's octant path up to its level-l ancestor a).
-template <bool REDUCE>
-__global__ void __launch_bounds__(128) k_pw_backward(PwArgs P, const uint32_t *__restrict__ box_fine,
+template <class R, bool REDUCE>
+__global__ void __launch_bounds__(128) k_pw_backward(PwArgs<R> P, const uint32_t *__restrict__ box_fine,
                                                      int64_t nbox, const uint32_t *__restrict__ leaf_fine,
-                                                     const int *__restrict__ slot, const float2 *__restrict__ vt,
-                                                     int nrhs, int64_t nx, double2 *__restrict__ acc) {
-    __shared__ float4 sk[PW_QC];
-    __shared__ float2 sw[PW_QC];
-    __shared__ float2 red[128];
+                                                     const int *__restrict__ slot,
+                                                     const typename PwT<R>::C *__restrict__ vt, int nrhs, int64_t nx,
+                                                     double2 *__restrict__ acc) {
+    typedef typename PwT<R>::C C2;
+    typedef typename PwT<R>::K K4;
+    __shared__ K4 sk[PW_QC];
+    __shared__ C2 sw[PW_QC];
+    __shared__ C2 red[128];
     int leaf = blockIdx.x, m = blockIdx.z;
     // ancestor at level l: last box whose first deep box index <= the leaf's
     uint32_t lf = leaf_fine[leaf];
@@ -448,37 +514,38 @@ __global__ void __launch_bounds__(128) k_pw_backward(PwArgs P, const uint32_t *_
     int grp = threadIdx.x / pr, pi = threadIdx.x % pr;
     bool active = grp < G;
     int4 gl = P.A.leaf_g[leaf];
-    const float2 *va = vt + ((size_t)a * nrhs + m) * P.nQ;
+    const C2 *va = vt + ((size_t)a * nrhs + m) * P.nQ;
     for (int pb = 0; pb < np; pb += pr) {
         bool valid = active && pb + pi < np;
-        float4 e = valid ? P.A.eps[p0 + pb + pi] : make_float4(0.f, 0.f, 0.f, 0.f);
-        float sr = 0.f, si = 0.f;
+        float4 eh = valid ? P.A.eps[p0 + pb + pi] : make_float4(0.f, 0.f, 0.f, 0.f);
+        auto e = Coord<R>::get(eh, P.eps_lo, valid ? p0 + pb + pi : 0u);
+        R sr = 0, si = 0;
         for (int qb = 0; qb < P.nQ; qb += PW_QC) {
             int qc = min(PW_QC, P.nQ - qb);
             __syncthreads();
             for (int j = threadIdx.x; j < qc; j += blockDim.x) {
-                float4 k4 = P.ks[qb + j];
-                sk[j] = k4;
+                sk[j] = P.ks[qb + j];
                 sw[j] = cmul(va[qb + j], leaf_factor<true>(P, gl, qb + j));
             }
             __syncthreads();
             if (valid) {
                 for (int j = grp; j < qc; j += G) {
-                    float4 k4 = sk[j];
-                    float ph = fmaf(k4.x, e.x, fmaf(k4.y, e.y, k4.z * e.z));
-                    float sn, cs;
+                    K4 k4 = sk[j];
+                    R ph = k4.x * e.x + k4.y * e.y + k4.z * e.z;
+                    R sn, cs;
                     phase_sincos<REDUCE>(ph, sn, cs);
-                    float2 w = sw[j];
-                    sr = fmaf(cs, w.x, fmaf(-sn, w.y, sr));
-                    si = fmaf(cs, w.y, fmaf(sn, w.x, si));
+                    C2 w = sw[j];
+                    sr += cs * w.x - sn * w.y;
+                    si += cs * w.y + sn * w.x;
                 }
             }
         }
         __syncthreads();
-        red[threadIdx.x] = make_float2(sr, si);
+        red[threadIdx.x].x = sr;
+        red[threadIdx.x].y = si;
         __syncthreads();
         if (valid && grp == 0) {
-            float tr = 0.f, ti = 0.f;
+            R tr = 0, ti = 0;
             for (int g = 0; g < G; ++g) {
                 tr += red[g * pr + pi].x;
                 ti += red[g * pr + pi].y;
@@ -499,36 +566,48 @@ __global__ void k_slot_set(const uint32_t *__restrict__ tgt, int64_t n, int *slo
     if (i < n) slot[tgt[i]] = (int)i;
 }
 
-void far_planewave(const ffm_plan_s *p, int l, const float2 *q, int nrhs, double2 *acc, Alloc &tmp,
-                   cudaStream_t s) {
+template <class R>
+static void planewave_level(const ffm_plan_s *p, int l, const float2 *q, int nrhs, double2 *acc, Alloc &tmp,
+                            cudaStream_t s, const typename PwT<R>::K *ks, const typename PwT<R>::C *D,
+                            const typename PwT<R>::C *E) {
+    typedef typename PwT<R>::C C2;
     const FarLevel &F = p->far[l];
     int ls = p->l_stop;
-    if (ls - l > PW_MAXD) fail(FFM_EUNSUPPORTED, "more than 16 levels between a plane-wave level and the leaves");
-    PwArgs PY{level_args(p, p->by[l], p->by[ls], p->epsY, l), F.ks, F.E, F.nQ};
-    PwArgs PX{level_args(p, p->bx[l], p->bx[ls], p->epsX, l), F.ks, F.E, F.nQ};
-    float2 *ut = tmp.get<float2>((size_t)p->by[l].nb * nrhs * F.nQ);
-    float2 *vt = tmp.get<float2>((size_t)p->bx[l].nb * nrhs * F.nQ);
+    PwArgs<R> PY{level_args(p, p->by[l], p->by[ls], p->epsY, l), p->epsYlo, ks, E, F.nQ};
+    PwArgs<R> PX{level_args(p, p->bx[l], p->bx[ls], p->epsX, l), p->epsXlo, ks, E, F.nQ};
+    C2 *ut = tmp.get<C2>((size_t)p->by[l].nb * nrhs * F.nQ);
+    C2 *vt = tmp.get<C2>((size_t)p->bx[l].nb * nrhs * F.nQ);
     // largest leaf-local phase: k sqrt(3) d_leaf / 2
     bool reduce = p->k * std::sqrt(3.0) * std::ldexp(p->d0, -ls) * 0.5 > 3.0;
-    int fwd_per_block = 128 * PW_QPT;
-    dim3 gf((unsigned)F.n_src, cdiv(F.nQ, fwd_per_block), nrhs);
+    dim3 gf((unsigned)F.n_src, cdiv(F.nQ, 128 * PW_QPT), nrhs);
     if (reduce)
-        FFM_LAUNCH(k_pw_forward<true>, gf, 128, 0, s, PY, F.src, q, p->ny, nrhs, ut);
+        FFM_LAUNCH((k_pw_forward<R, true>), gf, 128, 0, s, PY, F.src, q, p->ny, nrhs, ut);
     else
-        FFM_LAUNCH(k_pw_forward<false>, gf, 128, 0, s, PY, F.src, q, p->ny, nrhs, ut);
+        FFM_LAUNCH((k_pw_forward<R, false>), gf, 128, 0, s, PY, F.src, q, p->ny, nrhs, ut);
     dim3 gt((unsigned)F.n_tgt, cdiv(F.nQ, 128), nrhs);
-    FFM_LAUNCH(k_pw_transfer, gt, 128, 0, s, F.tgt, F.adm_off, F.adm_src, F.adm_t, F.D, F.nQ, nrhs, ut, vt);
+    FFM_LAUNCH(k_pw_transfer<C2>, gt, 128, 0, s, F.tgt, F.adm_off, F.adm_src, F.adm_t, D, F.nQ, nrhs,
+               (const C2 *)ut, vt);
     int64_t nbx = p->bx[l].nb;
     int *slot = tmp.get<int>(nbx);
     FFM_LAUNCH(k_slot_init, cdiv(nbx, 256), 256, 0, s, slot, nbx);
     FFM_LAUNCH(k_slot_set, cdiv(F.n_tgt, 256), 256, 0, s, F.tgt, F.n_tgt, slot);
     dim3 gb((unsigned)p->bx[ls].nb, 1, nrhs);
     if (reduce)
-        FFM_LAUNCH(k_pw_backward<true>, gb, 128, 0, s, PX, p->bx[l].fine, nbx, p->bx[ls].fine, slot, vt, nrhs, p->nx,
-                   acc);
+        FFM_LAUNCH((k_pw_backward<R, true>), gb, 128, 0, s, PX, p->bx[l].fine, nbx, p->bx[ls].fine, slot,
+                   (const C2 *)vt, nrhs, p->nx, acc);
     else
-        FFM_LAUNCH(k_pw_backward<false>, gb, 128, 0, s, PX, p->bx[l].fine, nbx, p->bx[ls].fine, slot, vt, nrhs, p->nx,
-                   acc);
+        FFM_LAUNCH((k_pw_backward<R, false>), gb, 128, 0, s, PX, p->bx[l].fine, nbx, p->bx[ls].fine, slot,
+                   (const C2 *)vt, nrhs, p->nx, acc);
+}
+
+void far_planewave(const ffm_plan_s *p, int l, const float2 *q, int nrhs, double2 *acc, Alloc &tmp,
+                   cudaStream_t s) {
+    const FarLevel &F = p->far[l];
+    if (p->l_stop - l > PW_MAXD) fail(FFM_EUNSUPPORTED, "more than 16 levels between a plane-wave level and the leaves");
+    if (F.pw64)
+        planewave_level<double>(p, l, q, nrhs, acc, tmp, s, F.ksd, F.Dd, F.Ed);
+    else
+        planewave_level<float>(p, l, q, nrhs, acc, tmp, s, F.ks, F.D, F.E);
 }
 
 }  // namespace ffm

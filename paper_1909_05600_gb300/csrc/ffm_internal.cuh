@@ -66,6 +66,10 @@ struct Alloc {
 
 inline unsigned cdiv(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b); }
 
+struct alignas(32) D4 {
+    double x, y, z, w;
+};
+
 // --------------------------------------------------- primitives (tree.cu)
 
 // Exclusive scan of n uint32 values (in may alias out); total written to *d_total if
@@ -103,10 +107,16 @@ struct FarLevel {
     std::vector<int4> h_trans_m;
     // Lagrange
     float *T = nullptr;             // n_trans * r * r (real) or float2 (complex), [t][j][i]
-    // plane waves
+    // plane waves: FP32 tables, or FP64 tables when pw64 (large cancellation in the
+    // quadrature sum, see tables.cu)
+    int pw64 = 0;
+    double cancel = 0;              // sum_q |D(q)| / |sum_q D(q)| for the closest translation
     float4 *ks = nullptr;           // nQ: k * s_q (x, y, z, 0)
     float2 *D = nullptr;            // n_trans * nQ
     float2 *E = nullptr;            // (l_stop - l) * 8 * nQ: octant phase factors
+    D4 *ksd = nullptr;
+    double2 *Dd = nullptr;
+    double2 *Ed = nullptr;
 };
 
 }  // namespace ffm

@@ -13,10 +13,6 @@
 
 namespace ffm {
 
-struct alignas(32) Dir4 {
-    double x, y, z, w;
-};
-
 // Worst-pair relative error of the tensor Chebyshev-Lagrange interpolation per r1 (index
 // r1 = 2..10), for the Laplace kernel and for the Helmholtz kernel at k d = 2.  These are
 // plan constants: the smallest r1 whose error is <= eps is used.
@@ -85,46 +81,104 @@ __global__ void k_lag_table(const int4 *__restrict__ m, int ntrans, LagGeo geo, 
     }
 }
 
-// D_t(q) = (i k w_q / (4 pi)) sum_{p=0}^{L} c_t[p] P_p(s_q . rhat_t)
-__global__ void k_pw_table(const Dir4 *__restrict__ sw, int nQ, const double2 *__restrict__ coef, int L,
-                           const Dir4 *__restrict__ rhat, double k, float2 *__restrict__ D) {
-    int q = blockIdx.x * blockDim.x + threadIdx.x;
+// ---- double-float arithmetic (unevaluated sums hi + lo of two floats, FMA-based)
+
+struct dflt {
+    float hi, lo;
+};
+
+__device__ __forceinline__ dflt df_fast_two_sum(float a, float b) {
+    float s = a + b;
+    return {s, b - (s - a)};
+}
+__device__ __forceinline__ dflt df_two_sum(float a, float b) {
+    float s = a + b;
+    float bb = s - a;
+    return {s, (a - (s - bb)) + (b - bb)};
+}
+__device__ __forceinline__ dflt df_mul(dflt a, dflt b) {
+    float p = a.hi * b.hi;
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, e));
+    return df_fast_two_sum(p, e);
+}
+__device__ __forceinline__ dflt df_add(dflt a, dflt b) {
+    dflt s = df_two_sum(a.hi, b.hi);
+    return df_fast_two_sum(s.hi, s.lo + (a.lo + b.lo));
+}
+__device__ __forceinline__ dflt df_split(double x) {
+    float h = (float)x;
+    return {h, (float)(x - (double)h)};
+}
+
+// D_t(q) = (i k w_q / (4 pi)) sum_{p=0}^{L} c_t[p] P_p(s_q . rhat_t).
+// The Legendre recurrence P_{p+1} = x P_p + p/(p+1) (x P_p - P_{p-1}) and the sum run in
+// double-float arithmetic on the FP32 pipe (FP64 throughput on this part is a small
+// fraction of FP32), giving ~2^-44 relative accuracy before the final rounding.
+// coef: per translation L+1 complex coefficients split as (re.hi, re.lo, im.hi, im.lo);
+// beta: L entries p/(p+1) split as (hi, lo).
+template <class OUT>
+__global__ void __launch_bounds__(256) k_pw_table(const D4 *__restrict__ sw, int nQ, const float4 *__restrict__ coef,
+                                                  const float2 *__restrict__ beta, int L,
+                                                  const D4 *__restrict__ rhat, double k, OUT *__restrict__ D) {
+    extern __shared__ float4 sm[];
+    float4 *sc = sm;                                  // L+1 coefficients
+    float2 *sb = reinterpret_cast<float2 *>(sm + L + 1);  // L betas
     int t = blockIdx.y;
+    for (int i = threadIdx.x; i <= L; i += blockDim.x) sc[i] = coef[(size_t)t * (L + 1) + i];
+    for (int i = threadIdx.x; i < L; i += blockDim.x) sb[i] = beta[i];
+    __syncthreads();
+    int q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= nQ) return;
-    Dir4 s = sw[q];
-    Dir4 rh = rhat[t];
-    double x = s.x * rh.x + s.y * rh.y + s.z * rh.z;
-    const double2 *c = coef + (size_t)t * (L + 1);
-    double p0 = 1.0, p1 = x;
-    double ar = c[0].x, ai = c[0].y;
+    D4 s = sw[q];
+    D4 rh = rhat[t];
+    dflt x = df_split(s.x * rh.x + s.y * rh.y + s.z * rh.z);
+    dflt p0 = {1.f, 0.f}, p1 = x;
+    float4 c0 = sc[0];
+    dflt sr = {c0.x, c0.y}, si = {c0.z, c0.w};
     if (L >= 1) {
-        ar += c[1].x * x;
-        ai += c[1].y * x;
+        float4 c1 = sc[1];
+        sr = df_add(sr, df_mul({c1.x, c1.y}, x));
+        si = df_add(si, df_mul({c1.z, c1.w}, x));
     }
     for (int p = 1; p < L; ++p) {
-        double p2 = ((2.0 * p + 1.0) * x * p1 - p * p0) / (p + 1.0);
+        dflt xp = df_mul(x, p1);
+        dflt diff = df_add(xp, {-p0.hi, -p0.lo});
+        float2 b = sb[p];
+        dflt p2 = df_add(xp, df_mul({b.x, b.y}, diff));
+        float4 c = sc[p + 1];
+        sr = df_add(sr, df_mul({c.x, c.y}, p2));
+        si = df_add(si, df_mul({c.z, c.w}, p2));
         p0 = p1;
         p1 = p2;
-        ar += c[p + 1].x * p2;
-        ai += c[p + 1].y * p2;
     }
     double f = k * s.w / (4.0 * PI);
-    D[(size_t)t * nQ + q] = make_float2((float)(-f * ai), (float)(f * ar));
+    double tr = (double)sr.hi + (double)sr.lo, ti = (double)si.hi + (double)si.lo;
+    size_t o = (size_t)t * nQ + q;
+    if constexpr (sizeof(OUT) == sizeof(float2))
+        D[o] = make_float2((float)(-f * ti), (float)(f * tr));
+    else
+        D[o] = make_double2(-f * ti, f * tr);
 }
 
 // E[d][oct][q] = e^{-ik s_q . delta}, delta_axis = (bit - 1/2) d_m for depth m = l+1+d.
-__global__ void k_pw_octants(const Dir4 *__restrict__ sw, int nQ, double k, double d_first, int ndepth,
-                             float2 *__restrict__ E) {
+template <class OUT>
+__global__ void k_pw_octants(const D4 *__restrict__ sw, int nQ, double k, double d_first, int ndepth,
+                             OUT *__restrict__ E) {
     int q = blockIdx.x * blockDim.x + threadIdx.x;
     int d = blockIdx.y, oct = blockIdx.z;
     if (q >= nQ || d >= ndepth) return;
     double dm = ldexp(d_first, -d);
-    Dir4 s = sw[q];
+    D4 s = sw[q];
     double bx = ((oct >> 2) & 1) - 0.5, by = ((oct >> 1) & 1) - 0.5, bz = (oct & 1) - 0.5;
     double ph = -k * dm * (s.x * bx + s.y * by + s.z * bz);
     double sn, cs;
     sincos(ph, &sn, &cs);
-    E[((size_t)d * 8 + oct) * nQ + q] = make_float2((float)cs, (float)sn);
+    size_t o = ((size_t)d * 8 + oct) * nQ + q;
+    if constexpr (sizeof(OUT) == sizeof(float2))
+        E[o] = make_float2((float)cs, (float)sn);
+    else
+        E[o] = make_double2(cs, sn);
 }
 
 // Gauss-Legendre nodes (ascending) and weights of order n by Newton's method on P_n.
@@ -198,54 +252,116 @@ void build_tables(ffm_plan_s *p, int l, Alloc &tmp) {
     int L = F.L, nQ = F.nQ, np = 2 * L;
     std::vector<double> mu, wg;
     gauss_legendre(L + 1, mu, wg);
-    std::vector<Dir4> sw(nQ);
-    std::vector<float4> ks(nQ);
+    std::vector<D4> sw(nQ);
     for (int i = 0; i <= L; ++i) {
         double st = std::sqrt(1.0 - mu[i] * mu[i]);
         for (int j = 0; j < np; ++j) {
             double ph = j * PI / L;
-            int q = i * np + j;
-            sw[q] = Dir4{st * std::cos(ph), st * std::sin(ph), mu[i], wg[i] * PI / L};
-            ks[q] = make_float4((float)(p->k * sw[q].x), (float)(p->k * sw[q].y), (float)(p->k * sw[q].z), 0.f);
+            sw[i * np + j] = D4{st * std::cos(ph), st * std::sin(ph), mu[i], wg[i] * PI / L};
         }
     }
     // Gegenbauer coefficients c_t[p] = (2p+1) i^p h_p(k |r0_t|) / (4 pi) and r0 directions
     int nt = F.n_trans;
-    std::vector<double2> coef((size_t)nt * (L + 1));
-    std::vector<Dir4> rhat(nt);
+    std::vector<double> cr((size_t)nt * (L + 1)), ci((size_t)nt * (L + 1));
+    std::vector<D4> rhat(nt);
     std::vector<double> hr, hi;
+    int tmin = 0;
     for (int t = 0; t < nt; ++t) {
         int4 m = F.h_trans_m[t];
         double r0[3] = {oxy[0] + m.x * dl, oxy[1] + m.y * dl, oxy[2] + m.z * dl};
         double R = std::sqrt(r0[0] * r0[0] + r0[1] * r0[1] + r0[2] * r0[2]);
-        rhat[t] = Dir4{r0[0] / R, r0[1] / R, r0[2] / R, R};
+        rhat[t] = D4{r0[0] / R, r0[1] / R, r0[2] / R, R};
+        if (R < rhat[tmin].w) tmin = t;
         hankel1(L, p->k * R, hr, hi);
         for (int q = 0; q <= L; ++q) {
             double ipr = (q % 4 == 0) ? 1.0 : (q % 4 == 2 ? -1.0 : 0.0);
             double ipi = (q % 4 == 1) ? 1.0 : (q % 4 == 3 ? -1.0 : 0.0);
             double f = (2.0 * q + 1.0) / (4.0 * PI);
-            coef[(size_t)t * (L + 1) + q] = make_double2(f * (ipr * hr[q] - ipi * hi[q]), f * (ipr * hi[q] + ipi * hr[q]));
+            cr[(size_t)t * (L + 1) + q] = f * (ipr * hr[q] - ipi * hi[q]);
+            ci[(size_t)t * (L + 1) + q] = f * (ipr * hi[q] + ipi * hr[q]);
         }
     }
-    Dir4 *d_sw = tmp.get<Dir4>(nQ);
-    double2 *d_coef = tmp.get<double2>(coef.size());
-    Dir4 *d_rhat = tmp.get<Dir4>(nt);
-    FFM_CUDA(cudaMemcpyAsync(d_sw, sw.data(), sizeof(Dir4) * nQ, cudaMemcpyHostToDevice, s));
-    FFM_CUDA(cudaMemcpyAsync(d_coef, coef.data(), sizeof(double2) * coef.size(), cudaMemcpyHostToDevice, s));
-    FFM_CUDA(cudaMemcpyAsync(d_rhat, rhat.data(), sizeof(Dir4) * nt, cudaMemcpyHostToDevice, s));
-    F.ks = p->mem.get<float4>(nQ);
-    FFM_CUDA(cudaMemcpyAsync(F.ks, ks.data(), sizeof(float4) * nQ, cudaMemcpyHostToDevice, s));
-    F.D = p->mem.get<float2>((size_t)nt * nQ);
-    dim3 g1(cdiv(nQ, 128), nt);
-    FFM_LAUNCH(k_pw_table, g1, 128, 0, s, d_sw, nQ, d_coef, L, d_rhat, p->k, F.D);
-    int ndepth = p->l_stop - l;
-    if (ndepth > 0) {
-        F.E = p->mem.get<float2>((size_t)ndepth * 8 * nQ);
-        dim3 g2(cdiv(nQ, 128), ndepth, 8);
-        FFM_LAUNCH(k_pw_octants, g2, 128, 0, s, d_sw, nQ, p->k, std::ldexp(p->d0, -(l + 1)), ndepth, F.E);
+    // Cancellation of the quadrature sum for the closest translation:
+    // C = sum_q |D(q)| / |sum_q D(q)|.  FP32 loses about C * 2.6e-8 relative on a pair at
+    // that distance, so levels with C > 250 (low k d_l, where the Hankel terms with
+    // p > k |r0| grow) run their plane-wave kernels in FP64.
+    F.cancel = 0.0;
+    if (L > 1.1 * p->k * rhat[tmin].w) {
+        double sa = 0.0, ar = 0.0, ai = 0.0;
+        const D4 &rh = rhat[tmin];
+        for (int q = 0; q < nQ; ++q) {
+            double x = sw[q].x * rh.x + sw[q].y * rh.y + sw[q].z * rh.z;
+            double p0 = 1.0, p1 = x, tr = cr[(size_t)tmin * (L + 1)], ti = ci[(size_t)tmin * (L + 1)];
+            tr += cr[(size_t)tmin * (L + 1) + 1] * x;
+            ti += ci[(size_t)tmin * (L + 1) + 1] * x;
+            for (int pp = 1; pp < L; ++pp) {
+                double p2 = ((2.0 * pp + 1.0) * x * p1 - pp * p0) / (pp + 1.0);
+                p0 = p1;
+                p1 = p2;
+                tr += cr[(size_t)tmin * (L + 1) + pp + 1] * p2;
+                ti += ci[(size_t)tmin * (L + 1) + pp + 1] * p2;
+            }
+            sa += sw[q].w * std::sqrt(tr * tr + ti * ti);
+            ar += sw[q].w * tr;
+            ai += sw[q].w * ti;
+        }
+        F.cancel = sa / std::sqrt(ar * ar + ai * ai);
     }
-    // host vectors die here: wait for the copies that read them
-    FFM_CUDA(cudaStreamSynchronize(s));
+    F.pw64 = F.cancel > 250.0 ? 1 : 0;
+    p->info.pw64[l] = F.pw64;
+    p->info.cancel[l] = F.cancel;
+    std::vector<float4> coef((size_t)nt * (L + 1));
+    for (size_t i = 0; i < coef.size(); ++i) {
+        float a = (float)cr[i], b = (float)ci[i];
+        coef[i] = make_float4(a, (float)(cr[i] - (double)a), b, (float)(ci[i] - (double)b));
+    }
+    std::vector<float2> beta(L > 0 ? L : 1);
+    for (int q = 0; q < L; ++q) {
+        double bq = (double)q / (q + 1.0);
+        float h = (float)bq;
+        beta[q] = make_float2(h, (float)(bq - (double)h));
+    }
+    D4 *d_sw = tmp.get<D4>(nQ);
+    float4 *d_coef = tmp.get<float4>(coef.size());
+    float2 *d_beta = tmp.get<float2>(beta.size());
+    D4 *d_rhat = tmp.get<D4>(nt);
+    FFM_CUDA(cudaMemcpyAsync(d_sw, sw.data(), sizeof(D4) * nQ, cudaMemcpyHostToDevice, s));
+    FFM_CUDA(cudaMemcpyAsync(d_coef, coef.data(), sizeof(float4) * coef.size(), cudaMemcpyHostToDevice, s));
+    FFM_CUDA(cudaMemcpyAsync(d_beta, beta.data(), sizeof(float2) * beta.size(), cudaMemcpyHostToDevice, s));
+    FFM_CUDA(cudaMemcpyAsync(d_rhat, rhat.data(), sizeof(D4) * nt, cudaMemcpyHostToDevice, s));
+    dim3 g1(cdiv(nQ, 256), nt);
+    size_t sm1 = sizeof(float4) * (L + 1) + sizeof(float2) * L;
+    int ndepth = p->l_stop - l;
+    dim3 g2(cdiv(nQ, 128), ndepth, 8);
+    if (F.pw64) {
+        std::vector<D4> ks(nQ);
+        for (int q = 0; q < nQ; ++q) ks[q] = D4{p->k * sw[q].x, p->k * sw[q].y, p->k * sw[q].z, 0.0};
+        F.ksd = p->mem.get<D4>(nQ);
+        FFM_CUDA(cudaMemcpyAsync(F.ksd, ks.data(), sizeof(D4) * nQ, cudaMemcpyHostToDevice, s));
+        F.Dd = p->mem.get<double2>((size_t)nt * nQ);
+        FFM_LAUNCH(k_pw_table<double2>, g1, 256, sm1, s, d_sw, nQ, d_coef, d_beta, L, d_rhat, p->k, F.Dd);
+        if (ndepth > 0) {
+            F.Ed = p->mem.get<double2>((size_t)ndepth * 8 * nQ);
+            FFM_LAUNCH(k_pw_octants<double2>, g2, 128, 0, s, d_sw, nQ, p->k, std::ldexp(p->d0, -(l + 1)), ndepth,
+                       F.Ed);
+        }
+        FFM_CUDA(cudaStreamSynchronize(s));
+    } else {
+        std::vector<float4> ks(nQ);
+        for (int q = 0; q < nQ; ++q)
+            ks[q] = make_float4((float)(p->k * sw[q].x), (float)(p->k * sw[q].y), (float)(p->k * sw[q].z), 0.f);
+        F.ks = p->mem.get<float4>(nQ);
+        FFM_CUDA(cudaMemcpyAsync(F.ks, ks.data(), sizeof(float4) * nQ, cudaMemcpyHostToDevice, s));
+        F.D = p->mem.get<float2>((size_t)nt * nQ);
+        FFM_LAUNCH(k_pw_table<float2>, g1, 256, sm1, s, d_sw, nQ, d_coef, d_beta, L, d_rhat, p->k, F.D);
+        if (ndepth > 0) {
+            F.E = p->mem.get<float2>((size_t)ndepth * 8 * nQ);
+            FFM_LAUNCH(k_pw_octants<float2>, g2, 128, 0, s, d_sw, nQ, p->k, std::ldexp(p->d0, -(l + 1)), ndepth,
+                       F.E);
+        }
+        // host vectors die here: wait for the copies that read them
+        FFM_CUDA(cudaStreamSynchronize(s));
+    }
 }
 
 }  // namespace ffm

@@ -48,13 +48,14 @@ class Info(C.Structure):
                 ("n_adm", C.c_int64 * 22), ("n_near", C.c_int64 * 22), ("n_trans", C.c_int64 * 22),
                 ("mode", C.c_int * 22), ("r1", C.c_int * 22), ("L", C.c_int * 22), ("nQ", C.c_int * 22),
                 ("nx", C.c_int64), ("ny", C.c_int64), ("src_points", C.c_int64 * 22),
-                ("tgt_points", C.c_int64 * 22), ("p2p_pairs", C.c_int64)]
+                ("tgt_points", C.c_int64 * 22), ("p2p_pairs", C.c_int64), ("pw64", C.c_int * 22),
+                ("cancel", C.c_double * 22)]
 
     def as_dict(self):
         d = {"l_stop": self.l_stop, "root_admissible": self.root_admissible, "d0": self.d0, "oX": list(self.oX),
              "oY": list(self.oY), "nx": self.nx, "ny": self.ny, "p2p_pairs": self.p2p_pairs}
         for f in ("nboxX", "nboxY", "n_adm", "n_near", "n_trans", "mode", "r1", "L", "nQ", "src_points",
-                  "tgt_points"):
+                  "tgt_points", "pw64", "cancel"):
             d[f] = list(getattr(self, f))
         return d
 
