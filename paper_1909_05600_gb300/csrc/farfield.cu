@@ -95,6 +95,7 @@ struct LevelArgs {
     // boxes of the level and the leaves
     const uint32_t *box_start;
     const int4 *box_g;
+    const uint32_t *box_leaf;   // first leaf of each box (nb + 1)
     const uint32_t *leaf_start;
     const int4 *leaf_g;
     const float4 *eps;
@@ -251,6 +252,7 @@ static LevelArgs level_args(const ffm_plan_s *p, const BoxLevel &B, const BoxLev
     LevelArgs A;
     A.box_start = B.start;
     A.box_g = B.g;
+    A.box_leaf = B.first_leaf;
     A.leaf_start = Lf.start;
     A.leaf_g = Lf.g;
     A.eps = eps;
@@ -362,23 +364,30 @@ struct PwArgs {
     int nQ;
 };
 
-// Leaf factor prod_{depth} E[depth][oct(depth)][q] (conjugated when CONJ).
+// Octant path of a leaf: oct[d] = octant of its ancestor at depth l+1+d within its parent.
+__device__ __forceinline__ int leaf_octant(int4 gl, int shift, int d) {
+    int sh = shift - 1 - d;  // depth l+1+d sits sh levels above the leaf
+    return (((gl.x >> sh) & 1) << 2) | (((gl.y >> sh) & 1) << 1) | ((gl.z >> sh) & 1);
+}
+
+// Leaf factor prod_d E[d][oct[d]][q] (conjugated when CONJ), octant path from shared memory.
 template <bool CONJ, class R>
-__device__ __forceinline__ typename PwT<R>::C leaf_factor(const PwArgs<R> &P, int4 gl, int q) {
+__device__ __forceinline__ typename PwT<R>::C leaf_factor(const PwArgs<R> &P, const int *oct, int q) {
     typename PwT<R>::C f = cone(R(0));
     for (int d = 0; d < P.A.shift; ++d) {
-        int sh = P.A.shift - 1 - d;  // depth l+1+d sits sh levels above the leaf
-        int oct = (((gl.x >> sh) & 1) << 2) | (((gl.y >> sh) & 1) << 1) | ((gl.z >> sh) & 1);
-        typename PwT<R>::C e = P.E[((size_t)d * 8 + oct) * P.nQ + q];
+        typename PwT<R>::C e = P.E[((size_t)d * 8 + oct[d]) * P.nQ + q];
         f = CONJ ? cmulc(f, e) : cmul(f, e);
     }
     return f;
 }
 
-// Forward transform: u~_b(q) for a chunk of directions of one source box.  The points of
-// the box are streamed through shared memory in Morton order; each leaf's partial sum
-// (leaf-centred phases) is moved to the box centre by its octant factor.
-template <class R, bool REDUCE>
+// Forward transform: u~_b(q) for a chunk of direction pairs of one source box.  The
+// leaves of the box are visited in order; each leaf's points are staged in shared memory
+// and summed with leaf-centred phases in a tight loop, then the leaf sum is moved to the
+// box centre by its octant factor.  Directions h and h + nQ/2 are antipodal, so one
+// sincos of k s_h . e gives e^{-i phase} for h and its conjugate for h + nQ/2.  Each
+// thread owns QPT pairs.
+template <class R, bool REDUCE, int QPT>
 __global__ void __launch_bounds__(128) k_pw_forward(PwArgs<R> P, const uint32_t *__restrict__ src,
                                                     const float2 *__restrict__ q, int64_t ny, int nrhs,
                                                     typename PwT<R>::C *__restrict__ ut) {
@@ -386,77 +395,78 @@ __global__ void __launch_bounds__(128) k_pw_forward(PwArgs<R> P, const uint32_t 
     __shared__ float4 se[PW_CHUNK];
     __shared__ float4 sl[sizeof(R) == 8 ? PW_CHUNK : 1];
     __shared__ float2 sq[PW_CHUNK];
+    __shared__ int soct[PW_MAXD];
     int b = src[blockIdx.x], m = blockIdx.z;
-    int q0 = (blockIdx.y * blockDim.x + threadIdx.x) * PW_QPT;
-    R kx[PW_QPT], ky[PW_QPT], kz[PW_QPT];
-    bool on[PW_QPT];
+    int nH = P.nQ / 2;
+    int h0 = blockIdx.y * blockDim.x * QPT + threadIdx.x;  // pairs h0 + t * blockDim.x
+    R kx[QPT], ky[QPT], kz[QPT];
+    bool on[QPT];
 #pragma unroll
-    for (int t = 0; t < PW_QPT; ++t) {
-        on[t] = q0 + t < P.nQ;
-        kx[t] = ky[t] = kz[t] = R(0);
-        if (on[t]) {
-            kx[t] = P.ks[q0 + t].x;
-            ky[t] = P.ks[q0 + t].y;
-            kz[t] = P.ks[q0 + t].z;
-        }
+    for (int t = 0; t < QPT; ++t) {
+        int hh = h0 + t * blockDim.x;
+        on[t] = hh < nH;
+        int hc = on[t] ? hh : 0;
+        kx[t] = P.ks[hc].x;
+        ky[t] = P.ks[hc].y;
+        kz[t] = P.ks[hc].z;
     }
-    C2 acc[PW_QPT], S[PW_QPT];
+    C2 acc[QPT], acb[QPT];
 #pragma unroll
-    for (int t = 0; t < PW_QPT; ++t) acc[t] = S[t] = czero(R(0));
-    uint32_t s0 = P.A.box_start[b], s1 = P.A.box_start[b + 1];
-    uint32_t cur = 0xffffffffu;
-    for (uint32_t base = s0; base < s1; base += PW_CHUNK) {
-        int cnt = (int)min((uint32_t)PW_CHUNK, s1 - base);
-        __syncthreads();
-        for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
-            se[j] = P.A.eps[base + j];
-            if constexpr (sizeof(R) == 8) sl[j] = P.eps_lo[base + j];
-            sq[j] = q[(int64_t)m * ny + base + j];
-        }
-        __syncthreads();
-        for (int j = 0; j < cnt; ++j) {
-            float4 eh = se[j];
-            uint32_t leaf = __float_as_uint(eh.w);
-            if (leaf != cur) {
-                if (cur != 0xffffffffu) {
-                    int4 gl = P.A.leaf_g[cur];
+    for (int t = 0; t < QPT; ++t) acc[t] = acb[t] = czero(R(0));
+    const float2 *qm = q + (int64_t)m * ny;
+    uint32_t lf0 = P.A.box_leaf[b], lf1 = P.A.box_leaf[b + 1];
+    for (uint32_t leaf = lf0; leaf < lf1; ++leaf) {
+        uint32_t p0 = P.A.leaf_start[leaf], p1 = P.A.leaf_start[leaf + 1];
+        C2 S[QPT], Sb[QPT];
 #pragma unroll
-                    for (int t = 0; t < PW_QPT; ++t) {
-                        C2 f = on[t] ? leaf_factor<false>(P, gl, q0 + t) : czero(R(0));
-                        C2 v = cmul(f, S[t]);
-                        acc[t].x += v.x;
-                        acc[t].y += v.y;
-                        S[t] = czero(R(0));
-                    }
+        for (int t = 0; t < QPT; ++t) S[t] = Sb[t] = czero(R(0));
+        for (uint32_t base = p0; base < p1; base += PW_CHUNK) {
+            int cnt = (int)min((uint32_t)PW_CHUNK, p1 - base);
+            __syncthreads();
+            for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
+                se[j] = P.A.eps[base + j];
+                if constexpr (sizeof(R) == 8) sl[j] = P.eps_lo[base + j];
+                sq[j] = qm[base + j];
+            }
+            if (base == p0 && threadIdx.x < P.A.shift) soct[threadIdx.x] = leaf_octant(P.A.leaf_g[leaf], P.A.shift, threadIdx.x);
+            __syncthreads();
+#pragma unroll 2
+            for (int j = 0; j < cnt; ++j) {
+                auto e = Coord<R>::get(se[j], sl, (uint32_t)j);
+                float2 w = sq[j];
+#pragma unroll
+                for (int t = 0; t < QPT; ++t) {
+                    R ph = fma(kx[t], e.x, fma(ky[t], e.y, kz[t] * e.z));
+                    R sn, cs;
+                    phase_sincos<REDUCE>(ph, sn, cs);
+                    // direction h: e^{-i ph} w; antipode h + nQ/2: e^{+i ph} w
+                    S[t].x = fma(cs, (R)w.x, fma(sn, (R)w.y, S[t].x));
+                    S[t].y = fma(cs, (R)w.y, fma(-sn, (R)w.x, S[t].y));
+                    Sb[t].x = fma(cs, (R)w.x, fma(-sn, (R)w.y, Sb[t].x));
+                    Sb[t].y = fma(cs, (R)w.y, fma(sn, (R)w.x, Sb[t].y));
                 }
-                cur = leaf;
-            }
-            auto e = Coord<R>::get(eh, sl, (uint32_t)j);
-            float2 w = sq[j];
-#pragma unroll
-            for (int t = 0; t < PW_QPT; ++t) {
-                R ph = kx[t] * e.x + ky[t] * e.y + kz[t] * e.z;
-                R sn, cs;
-                phase_sincos<REDUCE>(ph, sn, cs);
-                // e^{-i ph} w
-                S[t].x += cs * (R)w.x + sn * (R)w.y;
-                S[t].y += cs * (R)w.y - sn * (R)w.x;
             }
         }
-    }
-    if (cur != 0xffffffffu) {
-        int4 gl = P.A.leaf_g[cur];
 #pragma unroll
-        for (int t = 0; t < PW_QPT; ++t) {
-            C2 f = on[t] ? leaf_factor<false>(P, gl, q0 + t) : czero(R(0));
-            C2 v = cmul(f, S[t]);
+        for (int t = 0; t < QPT; ++t) {
+            if (!on[t]) continue;
+            int hh = h0 + t * blockDim.x;
+            C2 v = cmul(leaf_factor<false>(P, soct, hh), S[t]);
+            C2 vb = cmul(leaf_factor<false>(P, soct, hh + nH), Sb[t]);
             acc[t].x += v.x;
             acc[t].y += v.y;
+            acb[t].x += vb.x;
+            acb[t].y += vb.y;
         }
     }
 #pragma unroll
-    for (int t = 0; t < PW_QPT; ++t)
-        if (on[t]) ut[((size_t)b * nrhs + m) * P.nQ + q0 + t] = acc[t];
+    for (int t = 0; t < QPT; ++t)
+        if (on[t]) {
+            int hh = h0 + t * blockDim.x;
+            C2 *o = ut + ((size_t)b * nrhs + m) * P.nQ;
+            o[hh] = acc[t];
+            o[hh + nH] = acb[t];
+        }
 }
 
 // Diagonal transfer: v~_a(q) = sum_{b adm a} D_t(q) u~_b(q).
@@ -475,15 +485,17 @@ __global__ void k_pw_transfer(const uint32_t *__restrict__ tgt, const uint32_t *
         uint32_t b = asrc[e], t = at[e];
         C2 d = D[(size_t)t * nQ + q];
         C2 u = ut[((size_t)b * nrhs + m) * nQ + q];
-        a.x += d.x * u.x - d.y * u.y;
-        a.y += d.x * u.y + d.y * u.x;
+        a.x = fma(d.x, u.x, fma(-d.y, u.y, a.x));
+        a.y = fma(d.x, u.y, fma(d.y, u.x, a.y));
     }
     vt[((size_t)tgt[x] * nrhs + m) * nQ + q] = a;
 }
 
 // Backward transform for one target leaf: v_i += sum_q e^{ik s_q.(x_i - c_leaf)} W(q),
 // W(q) = v~_a(q) prod conj(E) (the leaf's octant path up to its level-l ancestor a).
-template <class R, bool REDUCE>
+// Each thread owns PPT points of the leaf (one shared-memory read of a direction serves
+// PPT phasors); thread groups split the directions when the leaf is small.
+template <class R, bool REDUCE, int PPT>
 __global__ void __launch_bounds__(128) k_pw_backward(PwArgs<R> P, const uint32_t *__restrict__ box_fine,
                                                      int64_t nbox, const uint32_t *__restrict__ leaf_fine,
                                                      const int *__restrict__ slot,
@@ -491,9 +503,11 @@ __global__ void __launch_bounds__(128) k_pw_backward(PwArgs<R> P, const uint32_t
                                                      double2 *__restrict__ acc) {
     typedef typename PwT<R>::C C2;
     typedef typename PwT<R>::K K4;
-    __shared__ K4 sk[PW_QC];
-    __shared__ C2 sw[PW_QC];
-    __shared__ C2 red[128];
+    constexpr int QC = sizeof(R) == 8 ? PW_QC / 4 : PW_QC;  // direction pairs per chunk
+    __shared__ K4 sk[QC];
+    __shared__ C2 sw[QC];
+    __shared__ C2 swb[QC];
+    __shared__ C2 red[128 * PPT];
     int leaf = blockIdx.x, m = blockIdx.z;
     // ancestor at level l: last box whose first deep box index <= the leaf's
     uint32_t lf = leaf_fine[leaf];
@@ -509,50 +523,76 @@ __global__ void __launch_bounds__(128) k_pw_backward(PwArgs<R> P, const uint32_t
     if (slot[a] < 0) return;
     uint32_t p0 = P.A.leaf_start[leaf], p1 = P.A.leaf_start[leaf + 1];
     int np = (int)(p1 - p0);
-    int pr = np < 128 ? np : 128;
-    int G = 128 / pr;
+    int slots = (np + PPT - 1) / PPT;        // thread slots needed for the whole leaf
+    int pr = slots < 128 ? slots : 128;      // threads per group
+    int G = 128 / pr;                        // groups splitting the directions
     int grp = threadIdx.x / pr, pi = threadIdx.x % pr;
     bool active = grp < G;
-    int4 gl = P.A.leaf_g[leaf];
+    __shared__ int soct[PW_MAXD];
+    if (threadIdx.x < P.A.shift) soct[threadIdx.x] = leaf_octant(P.A.leaf_g[leaf], P.A.shift, threadIdx.x);
     const C2 *va = vt + ((size_t)a * nrhs + m) * P.nQ;
-    for (int pb = 0; pb < np; pb += pr) {
-        bool valid = active && pb + pi < np;
-        float4 eh = valid ? P.A.eps[p0 + pb + pi] : make_float4(0.f, 0.f, 0.f, 0.f);
-        auto e = Coord<R>::get(eh, P.eps_lo, valid ? p0 + pb + pi : 0u);
-        R sr = 0, si = 0;
-        for (int qb = 0; qb < P.nQ; qb += PW_QC) {
-            int qc = min(PW_QC, P.nQ - qb);
+    for (int pb = 0; pb < np; pb += pr * PPT) {
+        decltype(Coord<R>::get(float4(), nullptr, 0u)) e[PPT];
+        bool valid[PPT];
+        R sr[PPT], si[PPT];
+#pragma unroll
+        for (int u = 0; u < PPT; ++u) {
+            int idx = pb + pi + u * pr;
+            valid[u] = active && idx < np;
+            float4 eh = valid[u] ? P.A.eps[p0 + idx] : make_float4(0.f, 0.f, 0.f, 0.f);
+            e[u] = Coord<R>::get(eh, P.eps_lo, valid[u] ? p0 + idx : 0u);
+            sr[u] = si[u] = 0;
+        }
+        int nH = P.nQ / 2;
+        for (int qb = 0; qb < nH; qb += QC) {
+            int qc = min(QC, nH - qb);
             __syncthreads();
             for (int j = threadIdx.x; j < qc; j += blockDim.x) {
                 sk[j] = P.ks[qb + j];
-                sw[j] = cmul(va[qb + j], leaf_factor<true>(P, gl, qb + j));
+                sw[j] = cmul(va[qb + j], leaf_factor<true>(P, soct, qb + j));
+                swb[j] = cmul(va[qb + j + nH], leaf_factor<true>(P, soct, qb + j + nH));
             }
             __syncthreads();
-            if (valid) {
-                for (int j = grp; j < qc; j += G) {
+            if (active) {
+                int j0 = grp * qc / G, j1 = (grp + 1) * qc / G;  // this group's slice
+#pragma unroll 2
+                for (int j = j0; j < j1; ++j) {
                     K4 k4 = sk[j];
-                    R ph = k4.x * e.x + k4.y * e.y + k4.z * e.z;
-                    R sn, cs;
-                    phase_sincos<REDUCE>(ph, sn, cs);
-                    C2 w = sw[j];
-                    sr += cs * w.x - sn * w.y;
-                    si += cs * w.y + sn * w.x;
+                    C2 w = sw[j], wb = swb[j];
+#pragma unroll
+                    for (int u = 0; u < PPT; ++u) {
+                        R ph = fma(k4.x, e[u].x, fma(k4.y, e[u].y, k4.z * e[u].z));
+                        R sn, cs;
+                        phase_sincos<REDUCE>(ph, sn, cs);
+                        // e^{+i ph} W_h + e^{-i ph} W_{h + nQ/2}
+                        sr[u] = fma(cs, w.x, fma(-sn, w.y, sr[u]));
+                        si[u] = fma(cs, w.y, fma(sn, w.x, si[u]));
+                        sr[u] = fma(cs, wb.x, fma(sn, wb.y, sr[u]));
+                        si[u] = fma(cs, wb.y, fma(-sn, wb.x, si[u]));
+                    }
                 }
             }
         }
         __syncthreads();
-        red[threadIdx.x].x = sr;
-        red[threadIdx.x].y = si;
+#pragma unroll
+        for (int u = 0; u < PPT; ++u) {
+            red[threadIdx.x * PPT + u].x = sr[u];
+            red[threadIdx.x * PPT + u].y = si[u];
+        }
         __syncthreads();
-        if (valid && grp == 0) {
-            R tr = 0, ti = 0;
-            for (int g = 0; g < G; ++g) {
-                tr += red[g * pr + pi].x;
-                ti += red[g * pr + pi].y;
+        if (active && grp == 0) {
+#pragma unroll
+            for (int u = 0; u < PPT; ++u) {
+                if (!valid[u]) continue;
+                R tr = 0, ti = 0;
+                for (int g = 0; g < G; ++g) {
+                    tr += red[(g * pr + pi) * PPT + u].x;
+                    ti += red[(g * pr + pi) * PPT + u].y;
+                }
+                double2 &dst = acc[(int64_t)m * nx + p0 + pb + pi + u * pr];
+                dst.x += (double)tr;
+                dst.y += (double)ti;
             }
-            double2 &dst = acc[(int64_t)m * nx + p0 + pb + pi];
-            dst.x += (double)tr;
-            dst.y += (double)ti;
         }
     }
 }
@@ -577,13 +617,20 @@ static void planewave_level(const ffm_plan_s *p, int l, const float2 *q, int nrh
     PwArgs<R> PX{level_args(p, p->bx[l], p->bx[ls], p->epsX, l), p->epsXlo, ks, E, F.nQ};
     C2 *ut = tmp.get<C2>((size_t)p->by[l].nb * nrhs * F.nQ);
     C2 *vt = tmp.get<C2>((size_t)p->bx[l].nb * nrhs * F.nQ);
-    // largest leaf-local phase: k sqrt(3) d_leaf / 2
-    bool reduce = p->k * std::sqrt(3.0) * std::ldexp(p->d0, -ls) * 0.5 > 3.0;
-    dim3 gf((unsigned)F.n_src, cdiv(F.nQ, 128 * PW_QPT), nrhs);
+    // largest leaf-local phase k sqrt(3) d_leaf / 2: reduce to [-pi, pi] only beyond 2 pi
+    bool reduce = p->k * std::sqrt(3.0) * std::ldexp(p->d0, -ls) * 0.5 > 2.0 * PI;
+    constexpr int QPT = 4;
+    // threads per forward block: 128 unless the ragged tail of the direction range wastes
+    // more than 10% of the lanes
+    int tb = 128;
+    int nH = F.nQ / 2;
+    for (int cand : {64, 32})
+        if ((double)cdiv(nH, tb * QPT) * tb * QPT > 1.1 * nH) tb = cand;
+    dim3 gf((unsigned)F.n_src, cdiv(nH, tb * QPT), nrhs);
     if (reduce)
-        FFM_LAUNCH((k_pw_forward<R, true>), gf, 128, 0, s, PY, F.src, q, p->ny, nrhs, ut);
+        FFM_LAUNCH((k_pw_forward<R, true, QPT>), gf, tb, 0, s, PY, F.src, q, p->ny, nrhs, ut);
     else
-        FFM_LAUNCH((k_pw_forward<R, false>), gf, 128, 0, s, PY, F.src, q, p->ny, nrhs, ut);
+        FFM_LAUNCH((k_pw_forward<R, false, QPT>), gf, tb, 0, s, PY, F.src, q, p->ny, nrhs, ut);
     dim3 gt((unsigned)F.n_tgt, cdiv(F.nQ, 128), nrhs);
     FFM_LAUNCH(k_pw_transfer<C2>, gt, 128, 0, s, F.tgt, F.adm_off, F.adm_src, F.adm_t, D, F.nQ, nrhs,
                (const C2 *)ut, vt);
@@ -592,11 +639,12 @@ static void planewave_level(const ffm_plan_s *p, int l, const float2 *q, int nrh
     FFM_LAUNCH(k_slot_init, cdiv(nbx, 256), 256, 0, s, slot, nbx);
     FFM_LAUNCH(k_slot_set, cdiv(F.n_tgt, 256), 256, 0, s, F.tgt, F.n_tgt, slot);
     dim3 gb((unsigned)p->bx[ls].nb, 1, nrhs);
+    constexpr int PPT = 2;
     if (reduce)
-        FFM_LAUNCH((k_pw_backward<R, true>), gb, 128, 0, s, PX, p->bx[l].fine, nbx, p->bx[ls].fine, slot,
+        FFM_LAUNCH((k_pw_backward<R, true, PPT>), gb, 128, 0, s, PX, p->bx[l].fine, nbx, p->bx[ls].fine, slot,
                    (const C2 *)vt, nrhs, p->nx, acc);
     else
-        FFM_LAUNCH((k_pw_backward<R, false>), gb, 128, 0, s, PX, p->bx[l].fine, nbx, p->bx[ls].fine, slot,
+        FFM_LAUNCH((k_pw_backward<R, false, PPT>), gb, 128, 0, s, PX, p->bx[l].fine, nbx, p->bx[ls].fine, slot,
                    (const C2 *)vt, nrhs, p->nx, acc);
 }
 

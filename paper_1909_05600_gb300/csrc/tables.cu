@@ -248,17 +248,27 @@ void build_tables(ffm_plan_s *p, int l, Alloc &tmp) {
         FFM_LAUNCH(k_lag_table, F.n_trans, 256, 0, s, F.trans_m, F.n_trans, g, F.T);
         return;
     }
-    // plane waves: quadrature of eq. 17
-    int L = F.L, nQ = F.nQ, np = 2 * L;
+    // plane waves: quadrature of eq. 17, (L+1) Gauss-Legendre nodes in cos(theta) times 2L
+    // azimuths phi_j = j pi / L.  The set is antipodally symmetric (mu_{L-i} = -mu_i,
+    // phi_{j+L} = phi_j + pi); it is ordered so that direction h + nQ/2 is exactly -s_h,
+    // which lets the transforms derive both phasors of a pair from one sincos.
+    int L = F.L, nQ = F.nQ, np = 2 * L, nH = nQ / 2;
     std::vector<double> mu, wg;
     gauss_legendre(L + 1, mu, wg);
     std::vector<D4> sw(nQ);
-    for (int i = 0; i <= L; ++i) {
-        double st = std::sqrt(1.0 - mu[i] * mu[i]);
-        for (int j = 0; j < np; ++j) {
+    {
+        int h = 0;
+        auto put = [&](int i, int j) {
+            double st = std::sqrt(1.0 - mu[i] * mu[i]);
             double ph = j * PI / L;
-            sw[i * np + j] = D4{st * std::cos(ph), st * std::sin(ph), mu[i], wg[i] * PI / L};
-        }
+            sw[h] = D4{st * std::cos(ph), st * std::sin(ph), mu[i], wg[i] * PI / L};
+            sw[h + nH] = D4{-sw[h].x, -sw[h].y, -sw[h].z, sw[h].w};
+            ++h;
+        };
+        for (int i = 0; i < (L + 1) / 2; ++i)
+            for (int j = 0; j < np; ++j) put(i, j);
+        if (L % 2 == 0)
+            for (int j = 0; j < L; ++j) put(L / 2, j);  // equator: phi_j and phi_j + pi pair up
     }
     // Gegenbauer coefficients c_t[p] = (2p+1) i^p h_p(k |r0_t|) / (4 pi) and r0 directions
     int nt = F.n_trans;
