@@ -156,18 +156,19 @@ def run_reference(args, rank):
 
 def roofline(prof, info, steps, clk, pk, pk_kind):
     """Dominant kernel of the timed region against its pipe.  Plane-wave transforms and
-    the Helmholtz near field are bound by the special-function (MUFU) pipe: each
-    point-direction pair costs one sin and one cos; each Helmholtz near pair one rsqrt,
-    one sin and one cos; each Laplace near pair one rsqrt."""
+    the Helmholtz near field are bound by the special-function (MUFU) pipe.  Algorithmic
+    MUFU work: a point-direction pair of a transform costs one MUFU op (one sin and one
+    cos serve a direction and its antipode, eq. 17's quadrature being symmetric); a
+    Helmholtz near pair costs three (rsqrt, sin, cos); a Laplace near pair one (rsqrt)."""
     name, (nl, ms) = max(prof.items(), key=lambda kv: kv[1][1])
     mhz = pk.get("sm_max_mhz", 2070.0)
     mufu_peak = SM_COUNT * MUFU_PER_SM_CLK * mhz * 1e6 / 1e12  # Tops/s
     helm = any(m == 2 for m in info["mode"])
     units = None
     if "k_pw_forward" in name:
-        units = 2.0 * sum(info["src_points"][l] * info["nQ"][l] for l in range(22) if info["mode"][l] == 2)
+        units = 1.0 * sum(info["src_points"][l] * info["nQ"][l] for l in range(22) if info["mode"][l] == 2)
     elif "k_pw_backward" in name:
-        units = 2.0 * sum(info["tgt_points"][l] * info["nQ"][l] for l in range(22) if info["mode"][l] == 2)
+        units = 1.0 * sum(info["tgt_points"][l] * info["nQ"][l] for l in range(22) if info["mode"][l] == 2)
     elif "k_p2p" in name:
         units = (3.0 if helm else 1.0) * info["p2p_pairs"]
     out = {"kernel": name, "launches_per_step": nl / steps, "ms_per_step": ms / steps}

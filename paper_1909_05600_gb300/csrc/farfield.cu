@@ -639,7 +639,7 @@ static void planewave_level(const ffm_plan_s *p, int l, const float2 *q, int nrh
     FFM_LAUNCH(k_slot_init, cdiv(nbx, 256), 256, 0, s, slot, nbx);
     FFM_LAUNCH(k_slot_set, cdiv(F.n_tgt, 256), 256, 0, s, F.tgt, F.n_tgt, slot);
     dim3 gb((unsigned)p->bx[ls].nb, 1, nrhs);
-    constexpr int PPT = 2;
+    constexpr int PPT = 4;  // target points per thread
     if (reduce)
         FFM_LAUNCH((k_pw_backward<R, true, PPT>), gb, 128, 0, s, PX, p->bx[l].fine, nbx, p->bx[ls].fine, slot,
                    (const C2 *)vt, nrhs, p->nx, acc);
