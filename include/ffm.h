@@ -161,6 +161,26 @@ void ffm_profile_enable(int on);
 void ffm_profile_reset(void);
 int ffm_profile_read(char *names, uint64_t *launches, double *ms, int cap);
 
+/* Morton (Z-order) ordering of one point set, computed without allocating any device
+ * memory.  The paper has no counterpart: this entry point serves callers that cannot
+ * allocate device memory while they run (code executing while another framework owns
+ * the whole device heap, allocation-free real-time loops, hosts whose allocator policy
+ * forbids cudaMalloc on their worker threads).
+ *   X        : n x 3 row-major DEVICE array, FFM_F32 or FFM_F64.
+ *   n        : 1 <= n <= 262144; larger n returns FFM_EINVAL (the scratch is fixed).
+ *   perm_out : n uint32 DEVICE entries; receives sorted position -> original index, the
+ *              same order ffm_plan gives X when called with Y = X (bounding cube, FP64
+ *              quantisation, 63-bit Morton key, ties by original index).
+ *   stream   : cudaStream_t; the call only enqueues work.
+ * Scratch: one file-scope device array of about 6.3 MB (keys, indices, histograms, cube),
+ * reserved on every GPU that loads the library until the process exits; no cudaMalloc,
+ * cudaFree or allocating library call is made.  The first call on each device resolves
+ * the array's device address (cudaGetSymbolAddress), so make that first call before any
+ * stream capture.  All calls share the array: calls whose work overlaps on the GPU (other
+ * streams, other threads) race and must be serialised by the caller.
+ * Errors: FFM_EINVAL (NULL or host pointers, bad dtype, n out of range), FFM_ECUDA. */
+ffm_status ffm_morton_order_noalloc(const void *X, ffm_dtype xdt, int64_t n, uint32_t *perm_out, void *stream);
+
 /* Human-readable status name, and the message of the last failure in this thread. */
 const char *ffm_status_str(ffm_status s);
 const char *ffm_last_error(void);

@@ -57,6 +57,8 @@ static void profile_flush() {
 
 void fail(ffm_status s, const std::string &msg) { throw Error{s, msg}; }
 
+void set_last_error(const std::string &msg) { g_last_error = msg; }
+
 void check_cuda(cudaError_t e, const char *what) {
     if (e == cudaSuccess) return;
     ffm_status s = (e == cudaErrorMemoryAllocation) ? FFM_ENOMEM : FFM_ECUDA;

@@ -24,6 +24,7 @@ struct Error {
 };
 
 [[noreturn]] void fail(ffm_status s, const std::string &msg);
+void set_last_error(const std::string &msg);
 void check_cuda(cudaError_t e, const char *what);
 
 #define FFM_CUDA(call) ::ffm::check_cuda((call), #call)

@@ -28,7 +28,7 @@ STATUS = {0: "FFM_OK", 1: "FFM_EINVAL", 2: "FFM_ENOMEM", 3: "FFM_ECUDA", 4: "FFM
 # Every symbol include/ffm.h declares.
 ABI_SYMBOLS = ("ffm_plan", "ffm_apply", "ffm_destroy", "ffm_plan_bytes", "ffm_plan_info", "ffm_plan_export",
                "ffm_launch_count", "ffm_profile_enable", "ffm_profile_reset", "ffm_profile_read", "ffm_status_str",
-               "ffm_last_error")
+               "ffm_last_error", "ffm_morton_order_noalloc")
 
 
 class FFMError(RuntimeError):
@@ -94,6 +94,8 @@ def lib():
         L.ffm_status_str.argtypes = [C.c_int]
         L.ffm_status_str.restype = C.c_char_p
         L.ffm_last_error.restype = C.c_char_p
+        L.ffm_morton_order_noalloc.argtypes = [vp, C.c_int, i64, vp, vp]
+        L.ffm_morton_order_noalloc.restype = C.c_int
         _lib = L
     return _lib
 
@@ -158,6 +160,17 @@ def _stream_of(*arrays, stream=None):
             if isinstance(a, torch.Tensor) and a.is_cuda:
                 return torch.cuda.current_stream(a.device).cuda_stream
     return 0
+
+
+NOALLOC_MAX_POINTS = 262144
+
+
+def morton_order_noalloc(X, perm_out, stream=None):
+    """ffm_morton_order_noalloc: Morton ordering of X (device) into perm_out (device uint32),
+    without any device allocation inside the library."""
+    _check(lib().ffm_morton_order_noalloc(_ptr(X), _dtype_code(X), int(X.shape[0]), _ptr(perm_out),
+                                          _stream_of(X, stream=stream)))
+    return perm_out
 
 
 class Plan:
