@@ -21,7 +21,7 @@ def lib():
     return ffm.lib()
 
 
-def test_header_declares_the_north_star_calls():
+def test_header_declares_plan_apply_destroy():
     names = _declared()
     for n in ("ffm_plan", "ffm_apply", "ffm_destroy"):
         assert n in names
