@@ -40,17 +40,27 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ffm", choices=["ffm", "reference"])
     ap.add_argument("--workload", default="helmholtz_sphere_1M",
-                    choices=["helmholtz_sphere_1M", "laplace_sphere_20k"])
+                    choices=["helmholtz_sphere_1M", "laplace_sphere_20k", "helmholtz_cube_200k_64rhs",
+                             "laplace_clustered"])
+    ap.add_argument("--n", type=int, default=0, help="points per set for the clustered workload")
+    ap.add_argument("--serving", action="store_true",
+                    help="serving stream: Poisson arrivals of mixed requests, p50/p99 latency and throughput")
+    ap.add_argument("--requests", type=int, default=500)
+    ap.add_argument("--workers", type=int, default=4)
     ap.add_argument("--cpu-targets", type=int, default=4096)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
 
 
-def make_problem(name, seed):
+def make_problem(name, seed, n=0):
     from paper_1909_05600_gb300 import workloads as W
     if name == "helmholtz_sphere_1M":
         return W.helmholtz_sphere(1_000_000, seed=seed)
+    if name == "helmholtz_cube_200k_64rhs":
+        return W.helmholtz_cube_multirhs(200_000, nrhs=64, seed=seed, eps=1e-4)
+    if name == "laplace_clustered":
+        return W.laplace_clustered(n or 100_000_000, seed=seed)
     return W.laplace_sphere(20000, seed=seed)
 
 
@@ -119,7 +129,8 @@ def cpu_direct_sample(prob, ntargets, seed=12345):
     from oracle import oracle as O
     from paper_1909_05600_gb300 import workloads as W
     t = W.sample_targets(prob.X.shape[0], ntargets, seed)
-    u = prob.u.astype(np.complex128) if np.iscomplexobj(prob.u) else prob.u.astype(np.float64)
+    u0 = prob.u[:, 0] if prob.u.ndim == 2 else prob.u
+    u = u0.astype(np.complex128) if np.iscomplexobj(u0) else u0.astype(np.float64)
     t0 = time.perf_counter()
     ref = O.direct(prob.X, prob.Y, u, prob.kind, prob.k, w=prob.w, targets=t)[:, 0]
     dt = time.perf_counter() - t0
@@ -131,7 +142,7 @@ def run_reference(args, rank):
     sum over all sources for a bounded sample of targets, scaled to the full product."""
     if rank != 0:
         return
-    prob = make_problem(args.workload, 1)
+    prob = make_problem(args.workload, 1, args.n)
     n = prob.X.shape[0]
     ns = min(n, 1024 if args.workload == "helmholtz_sphere_1M" else n)
     for _ in range(args.warmup):
@@ -184,6 +195,79 @@ def roofline(prof, info, steps, clk, pk, pk_kind):
     return out
 
 
+def run_serving(args):
+    """Serving stream: requests with N log-uniform in [1e4, 2e6], Laplace or Helmholtz,
+    three geometries, eps in {1e-3, 1e-4}.  Three passes over the same requests (inputs
+    resident in HBM): the plain path (one stream, ffm_plan + ffm_apply + ffm_destroy in turn),
+    the server with every request queued at once (throughput), and the server fed by Poisson
+    arrivals at 0.8 x the plain path's capacity (latency p50 / p99)."""
+    import torch
+    from paper_1909_05600_gb300 import build, ffm, workloads as W
+    from paper_1909_05600_gb300.serving import Request, Server, latency_stats
+    build.build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    descs = W.serving_stream(args.requests)
+    t0 = time.perf_counter()
+    reqs = []
+    for d in descs:
+        pr = W.serving_problem(d)
+        t = lambda a: torch.as_tensor(np.ascontiguousarray(a), device=dev)
+        reqs.append(dict(rid=d["id"], key=(d["seed"], pr.kind, pr.k, pr.eps), nx=pr.X.shape[0], ny=pr.Y.shape[0],
+                         kind=pr.kind, k=pr.k, eps=pr.eps, X=t(pr.X), Y=t(pr.Y), w=t(pr.w), u=t(pr.u)))
+    t_gen = time.perf_counter() - t0
+    n_pts = sum(r["nx"] for r in reqs)
+    # plain path: one stream, requests in arrival order
+    stream = torch.cuda.current_stream(dev)
+    l0 = ffm.launch_count()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    lat_plain = []
+    for r in reqs:
+        tq = time.perf_counter()
+        with ffm.Plan(r["X"], r["Y"], r["kind"], r["k"], r["eps"], weights=r["w"]) as p:
+            p.apply(r["u"])
+        torch.cuda.synchronize()
+        lat_plain.append(1e3 * (time.perf_counter() - tq))
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    t_plain = ev0.elapsed_time(ev1) * 1e-3
+    cap = len(reqs) / t_plain
+
+    def serve(rate):
+        rng = np.random.default_rng(7)
+        arrivals = np.zeros(len(reqs)) if rate is None else np.cumsum(rng.exponential(1.0 / rate, len(reqs)))
+        objs = [Request(**r) for r in reqs]
+        srv = Server(device=0, workers=args.workers)
+        try:
+            t_start = time.perf_counter()
+            for o, ta in zip(objs, arrivals):
+                while time.perf_counter() - t_start < ta:
+                    time.sleep(0.0005)
+                o.t_arrival = time.perf_counter()
+                srv.submit(o)
+            srv.drain(len(objs), timeout=1800)
+        finally:
+            srv.close()
+        return latency_stats(objs), objs
+
+    st_sat, _ = serve(None)
+    st_08, objs = serve(0.8 * cap)
+    launches = ffm.launch_count() - l0
+    line = {"metric": "serving requests/s", "value": st_sat["throughput_rps"], "unit": "requests/s", "n_gpus": 1,
+            "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "serving_stream", "requests": len(reqs), "n_points_total": n_pts,
+                       "workers": args.workers, "generation_s": t_gen},
+            "plain": {"throughput_rps": cap, "p50_ms": float(np.percentile(lat_plain, 50)),
+                      "p99_ms": float(np.percentile(lat_plain, 99)),
+                      "path": "one stream, ffm_plan + ffm_apply + ffm_destroy per request"},
+            "served_saturated": st_sat, "served_at_0.8_capacity": dict(st_08, rate_rps=0.8 * cap),
+            "speedup_vs_plain": st_sat["throughput_rps"] / cap, "gpu_launches": launches,
+            "failed": [o.error for o in objs if o.error][:3]}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -194,6 +278,13 @@ def main():
         import torch.distributed as dist
         os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
         dist.init_process_group("gloo", rank=rank, world_size=world)
+    if args.serving and args.impl == "ffm":
+        if rank == 0:
+            run_serving(args)
+        if dist:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
     if args.impl == "reference":
         run_reference(args, rank)
         if dist:
@@ -207,12 +298,14 @@ def main():
     build.build()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    prob = make_problem(args.workload, 1 + rank)
+    prob = make_problem(args.workload, 1 + rank, args.n)
     n = max(prob.X.shape[0], prob.Y.shape[0])
     X = torch.as_tensor(prob.X, device=dev)
     Y = torch.as_tensor(prob.Y, device=dev)
     w = torch.as_tensor(prob.w, device=dev)
-    u = torch.as_tensor(prob.u, device=dev)
+    u_host = np.ascontiguousarray(prob.u.T) if prob.u.ndim == 2 else prob.u  # (nrhs, n) for several RHS
+    nrhs = 1 if prob.u.ndim == 1 else prob.u.shape[1]
+    u = torch.as_tensor(u_host, device=dev)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
 
@@ -279,8 +372,8 @@ def main():
         Xh = torch.as_tensor(prob.X).pin_memory()
         Yh = torch.as_tensor(prob.Y).pin_memory()
         wh = torch.as_tensor(prob.w).pin_memory()
-        uh = torch.as_tensor(prob.u).pin_memory()
-        vh = torch.empty(prob.X.shape[0], dtype=uh.dtype).pin_memory()
+        uh = torch.as_tensor(u_host).pin_memory()
+        vh = torch.empty(tuple(uh.shape[:-1]) + (prob.X.shape[0],), dtype=uh.dtype).pin_memory()
         ke = max(2, args.steps // 2)
         ts = []
         for i in range(ke + 1):
@@ -301,11 +394,15 @@ def main():
     err = None
     if rank == 0 and not args.no_cpu_baseline:
         vg = vlast.cpu().numpy()
+        if vg.ndim == 2:
+            vg = vg[0]
         t, ref, dt, cores = cpu_direct_sample(prob, args.cpu_targets)
         err = float(np.linalg.norm(vg[t] - ref) / np.linalg.norm(ref))
-        cpu = {"value": 1.0 / (dt * prob.X.shape[0] / len(t)), "unit": "applies/s", "cores": cores, "kind": "oracle",
-               "sample": "FP64 direct sum over all %d sources for %d seeded targets (%.1f s), scaled to %d targets"
-                         % (prob.Y.shape[0], len(t), dt, prob.X.shape[0])}
+        cpu = {"value": 1.0 / (dt * prob.X.shape[0] / len(t) * nrhs), "unit": "applies/s", "cores": cores,
+               "kind": "oracle",
+               "sample": "FP64 direct sum over all %d sources for %d seeded targets and 1 of %d right-hand sides "
+                         "(%.1f s), scaled to %d targets and %d right-hand sides"
+                         % (prob.Y.shape[0], len(t), nrhs, dt, prob.X.shape[0], nrhs)}
 
     if rank == 0:
         rl = roofline(prof, info, args.steps, clk, pk, pk_kind)
@@ -319,8 +416,8 @@ def main():
                        "kernel": "helmholtz" if prob.kind == 1 else "laplace", "k": prob.k, "eps": prob.eps,
                        "u_dtype": str(prob.u.dtype), "step": "ffm_plan + ffm_apply + ffm_destroy",
                        "l2": "flushed between steps (512 MiB write, outside the step events)",
-                       "replicas": world},
-            "mpoints_per_s": n * value / 1e6,
+                       "replicas": world, "nrhs": nrhs},
+            "mpoints_per_s": n * value / 1e6, "rhs_per_s": value * nrhs,
             "t_plan_ms": t_plan / args.steps, "t_apply_ms": t_apply / args.steps,
             "apply_only_per_s": args.steps * world / (t_apply * 1e-3),
             "err_vs_fp64_direct": err, "err_targets": args.cpu_targets if err is not None else None,

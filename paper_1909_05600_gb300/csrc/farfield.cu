@@ -164,46 +164,101 @@ __global__ void __launch_bounds__(LAG_T) k_lag_anterp(LevelArgs A, const uint32_
     }
 }
 
-// v~_a[i] = sum_e sum_j T[t_e][j][i] u~_{b_e}[j]; one thread per control node i.
+// Transfer as one GEMM per translation (Sec. 2.2.2, T depends only on the box offset):
+// C(i, p) = sum_j T_t(i, j) u~_{src(p)}(j) for the pairs p of a column tile of translation t,
+// then v~_{tgt(p)}(i) += C(i, p).  A tile is BM control nodes x BN pairs; K runs over the r
+// source nodes in steps of BK.  Source columns are gathered from u~ by pair; the result is
+// scatter-added with FP32 atomics (a target box receives from up to 316-665 translations).
+constexpr int LG_BM = 64, LG_BK = 16, LG_T = 256;
 template <bool CPLX>
-__global__ void k_lag_transfer(const uint32_t *__restrict__ tgt, const uint32_t *__restrict__ off,
-                               const uint32_t *__restrict__ asrc, const uint32_t *__restrict__ at,
-                               const float *__restrict__ T, int r, int nrhs,
-                               const typename QT<CPLX>::T *__restrict__ ut, typename QT<CPLX>::T *__restrict__ vt) {
+__global__ void __launch_bounds__(LG_T) k_lag_gemm(const uint32_t *__restrict__ tile_t,
+                                                   const uint32_t *__restrict__ tile_p0,
+                                                   const uint32_t *__restrict__ bt_off,
+                                                   const uint32_t *__restrict__ bt_src,
+                                                   const uint32_t *__restrict__ bt_tgt, const float *__restrict__ T,
+                                                   int r, int nrhs, const typename QT<CPLX>::T *__restrict__ ut,
+                                                   typename QT<CPLX>::T *__restrict__ vt) {
     typedef typename QT<CPLX>::T Q;
-    extern __shared__ unsigned char smraw[];
-    Q *su = reinterpret_cast<Q *>(smraw);
-    int x = blockIdx.x, m = blockIdx.y;
-    int a = tgt[x];
-    float ar = 0.f, ai = 0.f;
-    for (uint32_t e = off[x]; e < off[x + 1]; ++e) {
-        uint32_t b = asrc[e], t = at[e];
+    constexpr int BN = LAG_GEMM_BN;
+    __shared__ Q As[LG_BK][LG_BM];
+    __shared__ Q Bs[LG_BK][BN];
+    __shared__ uint32_t s_src[BN], s_tgt[BN];
+    int t = tile_t[blockIdx.x];
+    uint32_t p0 = tile_p0[blockIdx.x];
+    int np = (int)min((uint32_t)BN, bt_off[t + 1] - p0);
+    int i0 = blockIdx.y * LG_BM, m = blockIdx.z;
+    int tid = threadIdx.x;
+    if (tid < BN) {
+        s_src[tid] = tid < np ? bt_src[p0 + tid] : 0u;
+        s_tgt[tid] = tid < np ? bt_tgt[p0 + tid] : 0u;
+    }
+    int ti = tid % 16, tp = tid / 16;  // 4 rows x 2 columns per thread
+    float cr[4][2], ci[4][2];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b) cr[a][b] = ci[a][b] = 0.f;
+    const Q *Tt = reinterpret_cast<const Q *>(T) + (size_t)t * r * r;
+    __syncthreads();
+    for (int j0 = 0; j0 < r; j0 += LG_BK) {
+        for (int e = tid; e < LG_BK * LG_BM; e += LG_T) {
+            int jj = e / LG_BM, ii = e % LG_BM;
+            int j = j0 + jj, i = i0 + ii;
+            Q v;
+            if constexpr (CPLX)
+                v = (j < r && i < r) ? Tt[(size_t)j * r + i] : make_float2(0.f, 0.f);
+            else
+                v = (j < r && i < r) ? Tt[(size_t)j * r + i] : 0.f;
+            As[jj][ii] = v;
+        }
+        for (int e = tid; e < LG_BK * BN; e += LG_T) {
+            int jj = e % LG_BK, pp = e / LG_BK;
+            int j = j0 + jj;
+            Q v;
+            if constexpr (CPLX)
+                v = (j < r && pp < np) ? ut[((size_t)s_src[pp] * nrhs + m) * r + j] : make_float2(0.f, 0.f);
+            else
+                v = (j < r && pp < np) ? ut[((size_t)s_src[pp] * nrhs + m) * r + j] : 0.f;
+            Bs[jj][pp] = v;
+        }
         __syncthreads();
-        for (int j = threadIdx.x; j < r; j += blockDim.x) su[j] = ut[((size_t)b * nrhs + m) * r + j];
-        __syncthreads();
-        int i = threadIdx.x;
-        if (i < r) {
-            if constexpr (CPLX) {
-                const float2 *Tt = reinterpret_cast<const float2 *>(T) + (size_t)t * r * r + i;
-                for (int j = 0; j < r; ++j) {
-                    float2 tv = Tt[(size_t)j * r];
-                    float2 uv = su[j];
-                    ar = fmaf(tv.x, uv.x, fmaf(-tv.y, uv.y, ar));
-                    ai = fmaf(tv.x, uv.y, fmaf(tv.y, uv.x, ai));
+#pragma unroll
+        for (int kk = 0; kk < LG_BK; ++kk) {
+            Q a[4], b[2];
+#pragma unroll
+            for (int x = 0; x < 4; ++x) a[x] = As[kk][ti * 4 + x];
+#pragma unroll
+            for (int y = 0; y < 2; ++y) b[y] = Bs[kk][tp * 2 + y];
+#pragma unroll
+            for (int x = 0; x < 4; ++x)
+#pragma unroll
+                for (int y = 0; y < 2; ++y) {
+                    if constexpr (CPLX) {
+                        cr[x][y] = fmaf(a[x].x, b[y].x, fmaf(-a[x].y, b[y].y, cr[x][y]));
+                        ci[x][y] = fmaf(a[x].x, b[y].y, fmaf(a[x].y, b[y].x, ci[x][y]));
+                    } else {
+                        cr[x][y] = fmaf(a[x], b[y], cr[x][y]);
+                    }
                 }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int y = 0; y < 2; ++y) {
+        int pp = tp * 2 + y;
+        if (pp >= np) continue;
+        Q *dst = vt + ((size_t)s_tgt[pp] * nrhs + m) * r;
+#pragma unroll
+        for (int x = 0; x < 4; ++x) {
+            int i = i0 + ti * 4 + x;
+            if (i >= r) continue;
+            if constexpr (CPLX) {
+                atomicAdd(&dst[i].x, cr[x][y]);
+                atomicAdd(&dst[i].y, ci[x][y]);
             } else {
-                const float *Tt = T + (size_t)t * r * r + i;
-                for (int j = 0; j < r; ++j) ar = fmaf(Tt[(size_t)j * r], su[j], ar);
+                atomicAdd(&dst[i], cr[x][y]);
             }
         }
-    }
-    int i = threadIdx.x;
-    if (i < r) {
-        size_t o = ((size_t)a * nrhs + m) * r + i;
-        if constexpr (CPLX)
-            vt[o] = make_float2(ar, ai);
-        else
-            vt[o] = ar;
     }
 }
 
@@ -274,15 +329,16 @@ void far_lagrange(const ffm_plan_s *p, int l, const void *q, int nrhs, double2 *
     void *ut = tmp.raw(esz * r * nrhs * (size_t)p->by[l].nb);
     void *vt = tmp.raw(esz * r * nrhs * (size_t)p->bx[l].nb);
     dim3 gs((unsigned)F.n_src, nrhs), gt((unsigned)F.n_tgt, nrhs);
-    int tb = ((r + 31) / 32) * 32;
+    dim3 gg((unsigned)F.n_tiles, cdiv(r, LG_BM), nrhs);
+    FFM_CUDA(cudaMemsetAsync(vt, 0, esz * r * nrhs * (size_t)p->bx[l].nb, s));
     if (cplx) {
         FFM_LAUNCH(k_lag_anterp<true>, gs, LAG_T, 0, s, AY, F.src, cb, (const float2 *)q, p->ny, nrhs, (float2 *)ut);
-        FFM_LAUNCH(k_lag_transfer<true>, gt, tb, r * sizeof(float2), s, F.tgt, F.adm_off, F.adm_src, F.adm_t, F.T, r,
+        FFM_LAUNCH(k_lag_gemm<true>, gg, LG_T, 0, s, F.tile_t, F.tile_p0, F.bt_off, F.bt_src, F.bt_tgt, F.T, r,
                    nrhs, (const float2 *)ut, (float2 *)vt);
         FFM_LAUNCH(k_lag_interp<true>, gt, 128, 0, s, AX, F.tgt, cb, (const float2 *)vt, nrhs, p->nx, acc);
     } else {
         FFM_LAUNCH(k_lag_anterp<false>, gs, LAG_T, 0, s, AY, F.src, cb, (const float *)q, p->ny, nrhs, (float *)ut);
-        FFM_LAUNCH(k_lag_transfer<false>, gt, tb, r * sizeof(float), s, F.tgt, F.adm_off, F.adm_src, F.adm_t, F.T, r,
+        FFM_LAUNCH(k_lag_gemm<false>, gg, LG_T, 0, s, F.tile_t, F.tile_p0, F.bt_off, F.bt_src, F.bt_tgt, F.T, r,
                    nrhs, (const float *)ut, (float *)vt);
         FFM_LAUNCH(k_lag_interp<false>, gt, 128, 0, s, AX, F.tgt, cb, (const float *)vt, nrhs, p->nx, acc);
     }
@@ -469,26 +525,36 @@ __global__ void __launch_bounds__(128) k_pw_forward(PwArgs<R> P, const uint32_t 
         }
 }
 
-// Diagonal transfer: v~_a(q) = sum_{b adm a} D_t(q) u~_b(q).
-template <class C2>
+// Diagonal transfer: v~_a(q) = sum_{b adm a} D_t(q) u~_b(q), all right-hand sides of a
+// direction in one thread so that D_t(q) is read once per pair.
+template <class C2, int MR>
 __global__ void k_pw_transfer(const uint32_t *__restrict__ tgt, const uint32_t *__restrict__ off,
                               const uint32_t *__restrict__ asrc, const uint32_t *__restrict__ at,
                               const C2 *__restrict__ D, int nQ, int nrhs, const C2 *__restrict__ ut,
                               C2 *__restrict__ vt) {
-    int x = blockIdx.x, m = blockIdx.z;
+    int x = blockIdx.x;
     int q = blockIdx.y * blockDim.x + threadIdx.x;
     if (q >= nQ) return;
-    C2 a;
-    a.x = 0;
-    a.y = 0;
-    for (uint32_t e = off[x]; e < off[x + 1]; ++e) {
-        uint32_t b = asrc[e], t = at[e];
-        C2 d = D[(size_t)t * nQ + q];
-        C2 u = ut[((size_t)b * nrhs + m) * nQ + q];
-        a.x = fma(d.x, u.x, fma(-d.y, u.y, a.x));
-        a.y = fma(d.x, u.y, fma(d.y, u.x, a.y));
+    for (int m0 = 0; m0 < nrhs; m0 += MR) {
+        C2 a[MR];
+#pragma unroll
+        for (int m = 0; m < MR; ++m) a[m].x = a[m].y = 0;
+        for (uint32_t e = off[x]; e < off[x + 1]; ++e) {
+            uint32_t b = asrc[e], t = at[e];
+            C2 d = D[(size_t)t * nQ + q];
+            const C2 *ub = ut + ((size_t)b * nrhs + m0) * nQ + q;
+#pragma unroll
+            for (int m = 0; m < MR; ++m)
+                if (m0 + m < nrhs) {
+                    C2 u = ub[(size_t)m * nQ];
+                    a[m].x = fma(d.x, u.x, fma(-d.y, u.y, a[m].x));
+                    a[m].y = fma(d.x, u.y, fma(d.y, u.x, a[m].y));
+                }
+        }
+#pragma unroll
+        for (int m = 0; m < MR; ++m)
+            if (m0 + m < nrhs) vt[((size_t)tgt[x] * nrhs + m0 + m) * nQ + q] = a[m];
     }
-    vt[((size_t)tgt[x] * nrhs + m) * nQ + q] = a;
 }
 
 // Backward transform for one target leaf: v_i += sum_q e^{ik s_q.(x_i - c_leaf)} W(q),
@@ -597,6 +663,162 @@ __global__ void __launch_bounds__(128) k_pw_backward(PwArgs<R> P, const uint32_t
     }
 }
 
+// ---- several right-hand sides: each phasor is computed once and applied to MC densities
+
+// Forward transform for MC right-hand sides m0..m0+MC-1.  Thread owns one direction pair
+// (h, h + nQ/2).  The leaf factor is folded into the phasor, e = F_leaf(h) e^{-i k s_h.e}, and
+// the antipode's phasor is conj(e) (the whole of F is conjugate-symmetric under s -> -s).
+template <class R, bool REDUCE, int MC>
+__global__ void __launch_bounds__(128) k_pw_forward_mr(PwArgs<R> P, const uint32_t *__restrict__ src,
+                                                       const float2 *__restrict__ q, int64_t ny, int nrhs,
+                                                       typename PwT<R>::C *__restrict__ ut) {
+    typedef typename PwT<R>::C C2;
+    constexpr int CH = 128;
+    __shared__ float4 se[CH];
+    __shared__ float4 sl[sizeof(R) == 8 ? CH : 1];
+    __shared__ float2 sq[CH][MC];
+    __shared__ int soct[PW_MAXD];
+    int b = src[blockIdx.x], m0 = blockIdx.z * MC;
+    int nH = P.nQ / 2;
+    int h = blockIdx.y * blockDim.x + threadIdx.x;
+    bool on = h < nH;
+    int hc = on ? h : 0;
+    R kx = P.ks[hc].x, ky = P.ks[hc].y, kz = P.ks[hc].z;
+    C2 acc[MC], acb[MC];
+#pragma unroll
+    for (int m = 0; m < MC; ++m) acc[m] = acb[m] = czero(R(0));
+    uint32_t lf0 = P.A.box_leaf[b], lf1 = P.A.box_leaf[b + 1];
+    for (uint32_t leaf = lf0; leaf < lf1; ++leaf) {
+        uint32_t p0 = P.A.leaf_start[leaf], p1 = P.A.leaf_start[leaf + 1];
+        C2 f = cone(R(0));
+        for (uint32_t base = p0; base < p1; base += CH) {
+            int cnt = (int)min((uint32_t)CH, p1 - base);
+            __syncthreads();
+            for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
+                se[j] = P.A.eps[base + j];
+                if constexpr (sizeof(R) == 8) sl[j] = P.eps_lo[base + j];
+            }
+            for (int e = threadIdx.x; e < cnt * MC; e += blockDim.x) {
+                int j = e % cnt, m = e / cnt;
+                sq[j][m] = (m0 + m < nrhs) ? q[(int64_t)(m0 + m) * ny + base + j] : make_float2(0.f, 0.f);
+            }
+            if (base == p0 && threadIdx.x < P.A.shift) soct[threadIdx.x] = leaf_octant(P.A.leaf_g[leaf], P.A.shift, threadIdx.x);
+            __syncthreads();
+            if (base == p0) f = leaf_factor<false>(P, soct, hc);
+            for (int j = 0; j < cnt; ++j) {
+                auto e3 = Coord<R>::get(se[j], sl, (uint32_t)j);
+                R ph = fma(kx, e3.x, fma(ky, e3.y, kz * e3.z));
+                R sn, cs;
+                phase_sincos<REDUCE>(ph, sn, cs);
+                // e = f e^{-i ph}
+                R er = fma(f.x, cs, f.y * sn), ei = fma(f.y, cs, -f.x * sn);
+#pragma unroll
+                for (int m = 0; m < MC; ++m) {
+                    float2 w = sq[j][m];
+                    acc[m].x = fma(er, (R)w.x, fma(-ei, (R)w.y, acc[m].x));
+                    acc[m].y = fma(er, (R)w.y, fma(ei, (R)w.x, acc[m].y));
+                    acb[m].x = fma(er, (R)w.x, fma(ei, (R)w.y, acb[m].x));
+                    acb[m].y = fma(er, (R)w.y, fma(-ei, (R)w.x, acb[m].y));
+                }
+            }
+        }
+    }
+    if (on)
+#pragma unroll
+        for (int m = 0; m < MC; ++m)
+            if (m0 + m < nrhs) {
+                C2 *o = ut + ((size_t)b * nrhs + m0 + m) * P.nQ;
+                o[h] = acc[m];
+                o[h + nH] = acb[m];
+            }
+}
+
+// Backward transform for MC right-hand sides: one block per target leaf, one thread per
+// target point (looping over the leaf), direction pairs staged in shared memory with
+// W(h) = v~_a(h) conj(F_leaf(h)) and W(h + nQ/2) = v~_a(h + nQ/2) F_leaf(h).
+template <class R, bool REDUCE, int MC>
+__global__ void __launch_bounds__(128) k_pw_backward_mr(PwArgs<R> P, const uint32_t *__restrict__ box_fine,
+                                                        int64_t nbox, const uint32_t *__restrict__ leaf_fine,
+                                                        const int *__restrict__ slot,
+                                                        const typename PwT<R>::C *__restrict__ vt, int nrhs,
+                                                        int64_t nx, double2 *__restrict__ acc) {
+    typedef typename PwT<R>::C C2;
+    typedef typename PwT<R>::K K4;
+    constexpr int QC = 64;
+    __shared__ K4 sk[QC];
+    __shared__ C2 sw[QC][MC];
+    __shared__ C2 swb[QC][MC];
+    __shared__ int soct[PW_MAXD];
+    int leaf = blockIdx.x, m0 = blockIdx.z * MC;
+    uint32_t lf = leaf_fine[leaf];
+    int64_t lo = 0, hi = nbox - 1;
+    while (lo < hi) {
+        int64_t mid = (lo + hi + 1) >> 1;
+        if (box_fine[mid] <= lf)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    int a = (int)lo;
+    if (slot[a] < 0) return;
+    if (threadIdx.x < P.A.shift) soct[threadIdx.x] = leaf_octant(P.A.leaf_g[leaf], P.A.shift, threadIdx.x);
+    uint32_t p0 = P.A.leaf_start[leaf], p1 = P.A.leaf_start[leaf + 1];
+    int np = (int)(p1 - p0);
+    int nH = P.nQ / 2;
+    for (int pb = 0; pb < np; pb += blockDim.x) {
+        bool valid = pb + (int)threadIdx.x < np;
+        float4 eh = valid ? P.A.eps[p0 + pb + threadIdx.x] : make_float4(0.f, 0.f, 0.f, 0.f);
+        auto e3 = Coord<R>::get(eh, P.eps_lo, valid ? p0 + pb + threadIdx.x : 0u);
+        C2 o[MC];
+#pragma unroll
+        for (int m = 0; m < MC; ++m) o[m] = czero(R(0));
+        for (int qb = 0; qb < nH; qb += QC) {
+            int qc = min(QC, nH - qb);
+            __syncthreads();
+            for (int e = threadIdx.x; e < qc * MC; e += blockDim.x) {
+                int j = e % qc, m = e / qc;
+                C2 fconj = leaf_factor<true>(P, soct, qb + j);
+                if (m0 + m < nrhs) {
+                    const C2 *va = vt + ((size_t)a * nrhs + m0 + m) * P.nQ;
+                    sw[j][m] = cmul(va[qb + j], fconj);
+                    C2 fb;
+                    fb.x = fconj.x;
+                    fb.y = -fconj.y;
+                    swb[j][m] = cmul(va[qb + j + nH], fb);
+                } else {
+                    sw[j][m] = czero(R(0));
+                    swb[j][m] = czero(R(0));
+                }
+                if (m == 0) sk[j] = P.ks[qb + j];
+            }
+            __syncthreads();
+            if (valid) {
+                for (int j = 0; j < qc; ++j) {
+                    K4 k4 = sk[j];
+                    R ph = fma(k4.x, e3.x, fma(k4.y, e3.y, k4.z * e3.z));
+                    R sn, cs;
+                    phase_sincos<REDUCE>(ph, sn, cs);
+#pragma unroll
+                    for (int m = 0; m < MC; ++m) {
+                        C2 w = sw[j][m], wb = swb[j][m];
+                        // e^{+i ph} W_h + e^{-i ph} W_{h + nQ/2}
+                        o[m].x = fma(cs, w.x + wb.x, fma(sn, wb.y - w.y, o[m].x));
+                        o[m].y = fma(cs, w.y + wb.y, fma(sn, w.x - wb.x, o[m].y));
+                    }
+                }
+            }
+        }
+        if (valid)
+#pragma unroll
+            for (int m = 0; m < MC; ++m)
+                if (m0 + m < nrhs) {
+                    double2 &dst = acc[(int64_t)(m0 + m) * nx + p0 + pb + threadIdx.x];
+                    dst.x += (double)o[m].x;
+                    dst.y += (double)o[m].y;
+                }
+    }
+}
+
 __global__ void k_slot_init(int *slot, int64_t n) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) slot[i] = -1;
@@ -626,25 +848,49 @@ static void planewave_level(const ffm_plan_s *p, int l, const float2 *q, int nrh
     int nH = F.nQ / 2;
     for (int cand : {64, 32})
         if ((double)cdiv(nH, tb * QPT) * tb * QPT > 1.1 * nH) tb = cand;
-    dim3 gf((unsigned)F.n_src, cdiv(nH, tb * QPT), nrhs);
-    if (reduce)
-        FFM_LAUNCH((k_pw_forward<R, true, QPT>), gf, tb, 0, s, PY, F.src, q, p->ny, nrhs, ut);
+    constexpr int MC = 8;  // right-hand sides per thread in the multi-RHS kernels
+    bool multi = nrhs > 1;
+    if (multi) {
+        dim3 gm((unsigned)F.n_src, cdiv(nH, 128), cdiv(nrhs, MC));
+        if (reduce)
+            FFM_LAUNCH_NAMED(sizeof(R) == 8 ? "k_pw_forward_mr<f64>" : "k_pw_forward_mr<f32>", (k_pw_forward_mr<R, true, MC>), gm, 128, 0, s, PY, F.src, q, p->ny, nrhs, ut);
+        else
+            FFM_LAUNCH_NAMED(sizeof(R) == 8 ? "k_pw_forward_mr<f64>" : "k_pw_forward_mr<f32>", (k_pw_forward_mr<R, false, MC>), gm, 128, 0, s, PY, F.src, q, p->ny, nrhs, ut);
+    } else {
+        dim3 gf((unsigned)F.n_src, cdiv(nH, tb * QPT), 1);
+        if (reduce)
+            FFM_LAUNCH_NAMED(sizeof(R) == 8 ? "k_pw_forward<f64>" : "k_pw_forward<f32>", (k_pw_forward<R, true, QPT>), gf, tb, 0, s, PY, F.src, q, p->ny, nrhs, ut);
+        else
+            FFM_LAUNCH_NAMED(sizeof(R) == 8 ? "k_pw_forward<f64>" : "k_pw_forward<f32>", (k_pw_forward<R, false, QPT>), gf, tb, 0, s, PY, F.src, q, p->ny, nrhs, ut);
+    }
+    dim3 gt((unsigned)F.n_tgt, cdiv(F.nQ, 128), 1);
+    if (nrhs == 1)
+        FFM_LAUNCH_NAMED(sizeof(R) == 8 ? "k_pw_transfer<f64>" : "k_pw_transfer<f32>", (k_pw_transfer<C2, 1>), gt, 128,
+                         0, s, F.tgt, F.adm_off, F.adm_src, F.adm_t, D, F.nQ, nrhs, (const C2 *)ut, vt);
     else
-        FFM_LAUNCH((k_pw_forward<R, false, QPT>), gf, tb, 0, s, PY, F.src, q, p->ny, nrhs, ut);
-    dim3 gt((unsigned)F.n_tgt, cdiv(F.nQ, 128), nrhs);
-    FFM_LAUNCH(k_pw_transfer<C2>, gt, 128, 0, s, F.tgt, F.adm_off, F.adm_src, F.adm_t, D, F.nQ, nrhs,
-               (const C2 *)ut, vt);
+        FFM_LAUNCH_NAMED(sizeof(R) == 8 ? "k_pw_transfer<f64>" : "k_pw_transfer<f32>", (k_pw_transfer<C2, 8>), gt, 128,
+                         0, s, F.tgt, F.adm_off, F.adm_src, F.adm_t, D, F.nQ, nrhs, (const C2 *)ut, vt);
     int64_t nbx = p->bx[l].nb;
     int *slot = tmp.get<int>(nbx);
     FFM_LAUNCH(k_slot_init, cdiv(nbx, 256), 256, 0, s, slot, nbx);
     FFM_LAUNCH(k_slot_set, cdiv(F.n_tgt, 256), 256, 0, s, F.tgt, F.n_tgt, slot);
-    dim3 gb((unsigned)p->bx[ls].nb, 1, nrhs);
+    if (multi) {
+        dim3 gm((unsigned)p->bx[ls].nb, 1, cdiv(nrhs, MC));
+        if (reduce)
+            FFM_LAUNCH_NAMED(sizeof(R) == 8 ? "k_pw_backward_mr<f64>" : "k_pw_backward_mr<f32>", (k_pw_backward_mr<R, true, MC>), gm, 128, 0, s, PX, p->bx[l].fine, nbx, p->bx[ls].fine, slot,
+                       (const C2 *)vt, nrhs, p->nx, acc);
+        else
+            FFM_LAUNCH_NAMED(sizeof(R) == 8 ? "k_pw_backward_mr<f64>" : "k_pw_backward_mr<f32>", (k_pw_backward_mr<R, false, MC>), gm, 128, 0, s, PX, p->bx[l].fine, nbx, p->bx[ls].fine, slot,
+                       (const C2 *)vt, nrhs, p->nx, acc);
+        return;
+    }
+    dim3 gb((unsigned)p->bx[ls].nb, 1, 1);
     constexpr int PPT = 4;  // target points per thread
     if (reduce)
-        FFM_LAUNCH((k_pw_backward<R, true, PPT>), gb, 128, 0, s, PX, p->bx[l].fine, nbx, p->bx[ls].fine, slot,
+        FFM_LAUNCH_NAMED(sizeof(R) == 8 ? "k_pw_backward<f64>" : "k_pw_backward<f32>", (k_pw_backward<R, true, PPT>), gb, 128, 0, s, PX, p->bx[l].fine, nbx, p->bx[ls].fine, slot,
                    (const C2 *)vt, nrhs, p->nx, acc);
     else
-        FFM_LAUNCH((k_pw_backward<R, false, PPT>), gb, 128, 0, s, PX, p->bx[l].fine, nbx, p->bx[ls].fine, slot,
+        FFM_LAUNCH_NAMED(sizeof(R) == 8 ? "k_pw_backward<f64>" : "k_pw_backward<f32>", (k_pw_backward<R, false, PPT>), gb, 128, 0, s, PX, p->bx[l].fine, nbx, p->bx[ls].fine, slot,
                    (const C2 *)vt, nrhs, p->nx, acc);
 }
 

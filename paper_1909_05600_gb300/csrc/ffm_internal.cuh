@@ -14,6 +14,9 @@ namespace ffm {
 
 constexpr int LMAX = 21;         // finest level of the Morton keys (3 x 21 bits)
 constexpr int R1MAX = 8;         // largest Chebyshev node count per axis
+constexpr int LAG_GEMM_BN = 32;  // pairs (GEMM columns) per tile of the Lagrange transfer
+constexpr int P2P_TCHUNK = 128;  // targets per near-field work item
+constexpr int P2P_SMAX = 4096;   // source points per near-field work item (a larger single leaf stays whole)
 constexpr double PI = 3.14159265358979323846;
 
 // ---------------------------------------------------------------- errors
@@ -48,6 +51,9 @@ inline void launch_kernel(const char *name, void (*k)(KArgs...), dim3 grid, dim3
 
 #define FFM_LAUNCH(kernel, grid, block, smem, stream, ...) \
     ::ffm::launch_kernel(#kernel, kernel, dim3(grid), dim3(block), (size_t)(smem), (stream), __VA_ARGS__)
+// Same, with an explicit name for per-kernel timing (e.g. to tell FP32 and FP64 variants apart).
+#define FFM_LAUNCH_NAMED(name, kernel, grid, block, smem, stream, ...) \
+    ::ffm::launch_kernel(name, kernel, dim3(grid), dim3(block), (size_t)(smem), (stream), __VA_ARGS__)
 
 // ------------------------------------------------------- device memory
 
@@ -108,6 +114,12 @@ struct FarLevel {
     std::vector<int4> h_trans_m;
     // Lagrange
     float *T = nullptr;             // n_trans * r * r (real) or float2 (complex), [t][j][i]
+    uint32_t *bt_off = nullptr;     // n_trans+1: pairs grouped by translation (CSR)
+    uint32_t *bt_src = nullptr;     // n_adm source box per pair, grouped by translation
+    uint32_t *bt_tgt = nullptr;     // n_adm target box per pair, grouped by translation
+    int64_t n_tiles = 0;            // GEMM column tiles over all translations
+    uint32_t *tile_t = nullptr;     // per tile: translation
+    uint32_t *tile_p0 = nullptr;    // per tile: first pair (index into bt_*)
     // plane waves: FP32 tables, or FP64 tables when pw64 (large cancellation in the
     // quadrature sum, see tables.cu)
     int pw64 = 0;
@@ -143,6 +155,8 @@ struct ffm_plan_s {
     int64_t n_near = 0;
     uint32_t *near_off = nullptr;   // nbx(l_stop)+1 CSR over all target leaves
     uint32_t *near_src = nullptr;   // n_near source leaf per pair
+    int64_t n_items = 0;            // near-field work items (target chunk x bounded source range)
+    int4 *items = nullptr;          // (target leaf, first target in the leaf, first pair, end pair)
     ffm_info info{};
 };
 

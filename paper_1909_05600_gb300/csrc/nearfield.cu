@@ -2,13 +2,16 @@
 // leaf pairs left by the descent, v_i += sum_{j in near leaves} G(x_i - y_j) (w u)_j,
 // with pairs at distance 0 skipped.
 //
-// One block per target leaf.  Coordinates are leaf-relative unevaluated FP32 pairs
-// (hi + lo).  Source points of the near leaves are staged in shared memory relative to
-// the target leaf centre (re-split in FP64 from their own leaf frame), and a difference is
-// formed as (x_hi - y_hi) + (x_lo - y_lo): the hi difference is exact for nearby points
-// (Sterbenz), so |x - y| keeps ~2^-48 relative accuracy exactly where the 1/|x - y|
-// terms are largest.  Small target leaves are served by several thread groups that split
-// the staged sources and are reduced in shared memory.
+// Work is split into items of at most P2P_TCHUNK targets of one leaf times a range of its
+// near pairs holding at most P2P_SMAX source points, so that clustered inputs with very
+// uneven leaves still spread over the whole GPU; items add into the FP64 accumulators with
+// atomics.  Coordinates are leaf-relative unevaluated FP32 pairs (hi + lo).  Source points
+// are staged in shared memory relative to the target leaf centre: the offset between the
+// two leaf centres is formed in FP64 once per source leaf, split into hi + lo, and added to
+// each point with an FP32 TwoSum.  A difference is then (x_hi - y_hi) + (x_lo - y_lo), whose
+// hi part is exact for nearby points (Sterbenz), so |x - y| keeps about 2^-44 relative
+// accuracy exactly where the 1/|x - y| terms are largest.  Small chunks are served by
+// several thread groups that split the staged sources and are reduced in shared memory.
 #include "ffm_internal.cuh"
 
 namespace ffm {
@@ -22,10 +25,36 @@ struct NearArgs {
     const float4 *epsX, *epsY;            // hi parts (.w: leaf index bits)
     const float4 *epsXlo, *epsYlo;        // lo parts
     const uint32_t *off, *src;            // CSR over target leaves
+    const int4 *items;                    // (target leaf, first target, first pair, end pair)
     double dls;                           // leaf edge
     double oyx[3];                        // oY - oX
     float k;
 };
+
+// y (hi + lo, own leaf frame) plus the leaf-centre offset (oh + ol): an FP32 TwoSum of the
+// hi parts, the lo parts added to the rounding error.
+__device__ __forceinline__ void stage_coord(float yh, float yl, float oh, float ol, float &hi, float &lo) {
+    float s = yh + oh;
+    float bb = s - yh;
+    float err = (yh - (s - bb)) + (oh - bb);
+    hi = s;
+    lo = err + (yl + ol);
+}
+
+struct Off3 {
+    float h[3], l[3];
+};
+
+__device__ __forceinline__ Off3 leaf_offset3(const NearArgs &N, int4 ga, int4 gb) {
+    double o[3] = {N.oyx[0] + N.dls * (double)(gb.x - ga.x), N.oyx[1] + N.dls * (double)(gb.y - ga.y),
+                   N.oyx[2] + N.dls * (double)(gb.z - ga.z)};
+    Off3 r;
+    for (int d = 0; d < 3; ++d) {
+        r.h[d] = (float)o[d];
+        r.l[d] = (float)(o[d] - (double)r.h[d]);
+    }
+    return r;
+}
 
 // Accumulate the staged sources [grp, fill) step G into (sr, si) for target x = xh + xl.
 // Staged source j: sy[j] = (hi.x, hi.y, hi.z, lo.x), syl[j] = (lo.y, lo.z).
@@ -66,79 +95,164 @@ __global__ void __launch_bounds__(P2P_T) k_p2p(NearArgs N, const void *__restric
     __shared__ float2 syl[P2P_SB];
     __shared__ float2 sq[P2P_SB];
     __shared__ float2 red[P2P_T];
-    int a = blockIdx.x, m = blockIdx.y;
-    uint32_t e0 = N.off[a], e1 = N.off[a + 1];
-    if (e0 == e1) return;
-    uint32_t p0 = N.xl_start[a], p1 = N.xl_start[a + 1];
-    int np = (int)(p1 - p0);
-    int pr = np < P2P_T ? np : P2P_T;
-    int G = P2P_T / pr;
-    int grp = threadIdx.x / pr, pi = threadIdx.x % pr;
-    bool active = grp < G;
+    int4 it = N.items[blockIdx.x];
+    int a = it.x, m = blockIdx.y;
+    uint32_t e0 = (uint32_t)it.z, e1 = (uint32_t)it.w;
+    uint32_t p0 = N.xl_start[a] + (uint32_t)it.y;
+    int np = min(P2P_TCHUNK, (int)(N.xl_start[a + 1] - p0));
+    int G = P2P_T / np;
+    int grp = threadIdx.x / np, pi = threadIdx.x % np;
+    bool valid = grp < G;
     int4 ga = N.xl_g[a];
     const float *qr = reinterpret_cast<const float *>(qv) + (int64_t)m * ny;
     const float2 *qc = reinterpret_cast<const float2 *>(qv) + (int64_t)m * ny;
-    for (int pb = 0; pb < np; pb += pr) {
-        bool valid = active && pb + pi < np;
-        float4 x = valid ? N.epsX[p0 + pb + pi] : make_float4(0.f, 0.f, 0.f, 0.f);
-        float4 xl = valid ? N.epsXlo[p0 + pb + pi] : make_float4(0.f, 0.f, 0.f, 0.f);
-        float sr = 0.f, si = 0.f;
-        int fill = 0;
+    float4 x = valid ? N.epsX[p0 + pi] : make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 xl = valid ? N.epsXlo[p0 + pi] : make_float4(0.f, 0.f, 0.f, 0.f);
+    float sr = 0.f, si = 0.f;
+    int fill = 0;
+    for (uint32_t e = e0; e < e1; ++e) {
+        uint32_t b = N.src[e];
+        uint32_t s0 = N.yl_start[b];
+        int cnt = (int)(N.yl_start[b + 1] - s0);
+        Off3 oc = leaf_offset3(N, ga, N.yl_g[b]);
+        for (int c0 = 0; c0 < cnt;) {
+            int take = min(cnt - c0, P2P_SB - fill);
+            for (int j = threadIdx.x; j < take; j += P2P_T) {
+                float4 y = N.epsY[s0 + c0 + j];
+                float4 yl = N.epsYlo[s0 + c0 + j];
+                float hx, lx, hy, ly, hz, lz;
+                stage_coord(y.x, yl.x, oc.h[0], oc.l[0], hx, lx);
+                stage_coord(y.y, yl.y, oc.h[1], oc.l[1], hy, ly);
+                stage_coord(y.z, yl.z, oc.h[2], oc.l[2], hz, lz);
+                sy[fill + j] = make_float4(hx, hy, hz, lx);
+                syl[fill + j] = make_float2(ly, lz);
+                if constexpr (HELM)
+                    sq[fill + j] = qc[s0 + c0 + j];
+                else
+                    sq[fill + j] = make_float2(qr[s0 + c0 + j], 0.f);
+            }
+            fill += take;
+            c0 += take;
+            if (fill == P2P_SB) {
+                __syncthreads();
+                if (valid) interact<HELM>(sy, syl, sq, fill, grp, G, x, xl, N.k, sr, si);
+                __syncthreads();
+                fill = 0;
+            }
+        }
+    }
+    __syncthreads();
+    if (valid) interact<HELM>(sy, syl, sq, fill, grp, G, x, xl, N.k, sr, si);
+    red[threadIdx.x] = make_float2(sr, si);
+    __syncthreads();
+    if (valid && grp == 0) {
+        float tr = 0.f, ti = 0.f;
+        for (int g = 0; g < G; ++g) {
+            tr += red[g * np + pi].x;
+            ti += red[g * np + pi].y;
+        }
+        const double c = 0.079577471545947667884;  // 1 / (4 pi)
+        double2 *dst = &acc[(int64_t)m * nx + p0 + pi];
+        atomicAdd(&dst->x, (double)tr * c);
+        atomicAdd(&dst->y, (double)ti * c);
+    }
+}
+
+// Several right-hand sides: each kernel value G(x_i - y_j) is computed once and applied
+// to MC densities.  One thread per target point of the leaf.
+template <bool HELM, int MC>
+__global__ void __launch_bounds__(P2P_T) k_p2p_mr(NearArgs N, const void *__restrict__ qv, int64_t ny, int nrhs,
+                                                  int64_t nx, double2 *__restrict__ acc) {
+    constexpr int SB = 128;
+    __shared__ float4 sy[SB];
+    __shared__ float2 syl[SB];
+    __shared__ float2 sq[SB][MC];
+    int4 it = N.items[blockIdx.x];
+    int a = it.x, m0 = blockIdx.y * MC;
+    uint32_t e0 = (uint32_t)it.z, e1 = (uint32_t)it.w;
+    uint32_t p0 = N.xl_start[a] + (uint32_t)it.y;
+    int np = min(P2P_TCHUNK, (int)(N.xl_start[a + 1] - p0));
+    int4 ga = N.xl_g[a];
+    const float *qr = reinterpret_cast<const float *>(qv);
+    const float2 *qc = reinterpret_cast<const float2 *>(qv);
+    for (int pb = 0; pb < np; pb += P2P_T) {
+        bool valid = pb + (int)threadIdx.x < np;
+        float4 x = valid ? N.epsX[p0 + pb + threadIdx.x] : make_float4(0.f, 0.f, 0.f, 0.f);
+        float4 xl = valid ? N.epsXlo[p0 + pb + threadIdx.x] : make_float4(0.f, 0.f, 0.f, 0.f);
+        float2 o[MC];
+#pragma unroll
+        for (int m = 0; m < MC; ++m) o[m] = make_float2(0.f, 0.f);
         for (uint32_t e = e0; e < e1; ++e) {
             uint32_t b = N.src[e];
             uint32_t s0 = N.yl_start[b];
             int cnt = (int)(N.yl_start[b + 1] - s0);
-            int4 gb = N.yl_g[b];
-            double ox = N.oyx[0] + N.dls * (double)(gb.x - ga.x);
-            double oy = N.oyx[1] + N.dls * (double)(gb.y - ga.y);
-            double oz = N.oyx[2] + N.dls * (double)(gb.z - ga.z);
-            for (int c0 = 0; c0 < cnt;) {
-                int take = min(cnt - c0, P2P_SB - fill);
+            Off3 oc = leaf_offset3(N, ga, N.yl_g[b]);
+            for (int c0 = 0; c0 < cnt; c0 += SB) {
+                int take = min(cnt - c0, SB);
+                __syncthreads();
                 for (int j = threadIdx.x; j < take; j += P2P_T) {
                     float4 y = N.epsY[s0 + c0 + j];
                     float4 yl = N.epsYlo[s0 + c0 + j];
-                    double rx = ((double)y.x + (double)yl.x) + ox;
-                    double ry = ((double)y.y + (double)yl.y) + oy;
-                    double rz = ((double)y.z + (double)yl.z) + oz;
-                    float hx = (float)rx, hy = (float)ry, hz = (float)rz;
-                    sy[fill + j] = make_float4(hx, hy, hz, (float)(rx - (double)hx));
-                    syl[fill + j] = make_float2((float)(ry - (double)hy), (float)(rz - (double)hz));
-                    if constexpr (HELM)
-                        sq[fill + j] = qc[s0 + c0 + j];
-                    else
-                        sq[fill + j] = make_float2(qr[s0 + c0 + j], 0.f);
+                    float hx, lx, hy, ly, hz, lz;
+                    stage_coord(y.x, yl.x, oc.h[0], oc.l[0], hx, lx);
+                    stage_coord(y.y, yl.y, oc.h[1], oc.l[1], hy, ly);
+                    stage_coord(y.z, yl.z, oc.h[2], oc.l[2], hz, lz);
+                    sy[j] = make_float4(hx, hy, hz, lx);
+                    syl[j] = make_float2(ly, lz);
                 }
-                fill += take;
-                c0 += take;
-                if (fill == P2P_SB) {
-                    __syncthreads();
-                    if (valid) interact<HELM>(sy, syl, sq, fill, grp, G, x, xl, N.k, sr, si);
-                    __syncthreads();
-                    fill = 0;
+                for (int t = threadIdx.x; t < take * MC; t += P2P_T) {
+                    int j = t % take, m = t / take;
+                    int64_t idx = (int64_t)(m0 + m) * ny + s0 + c0 + j;
+                    float2 w = make_float2(0.f, 0.f);
+                    if (m0 + m < nrhs) w = HELM ? qc[idx] : make_float2(qr[idx], 0.f);
+                    sq[j][m] = w;
+                }
+                __syncthreads();
+                if (valid) {
+                    for (int j = 0; j < take; ++j) {
+                        float4 y = sy[j];
+                        float2 yl2 = syl[j];
+                        float dx = (x.x - y.x) + (xl.x - y.w);
+                        float dy = (x.y - y.y) + (xl.y - yl2.x);
+                        float dz = (x.z - y.z) + (xl.z - yl2.y);
+                        float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                        float inv = r2 > 0.f ? rsqrtf(r2) : 0.f;
+                        float gr = inv, gi = 0.f;
+                        if constexpr (HELM) {
+                            float ph = N.k * (r2 * inv);
+                            float n = rintf(ph * 0.15915494309189535f);
+                            ph = fmaf(-n, 6.28318548202514648f, ph);
+                            ph = fmaf(-n, -1.7484555314695172e-07f, ph);
+                            float sn, cs;
+                            __sincosf(ph, &sn, &cs);
+                            gr = cs * inv;
+                            gi = sn * inv;
+                        }
+#pragma unroll
+                        for (int m = 0; m < MC; ++m) {
+                            float2 w = sq[j][m];
+                            o[m].x = fmaf(gr, w.x, fmaf(-gi, w.y, o[m].x));
+                            o[m].y = fmaf(gr, w.y, fmaf(gi, w.x, o[m].y));
+                        }
+                    }
                 }
             }
         }
-        __syncthreads();
-        if (valid) interact<HELM>(sy, syl, sq, fill, grp, G, x, xl, N.k, sr, si);
-        red[threadIdx.x] = make_float2(sr, si);
-        __syncthreads();
-        if (valid && grp == 0) {
-            float tr = 0.f, ti = 0.f;
-            for (int g = 0; g < G; ++g) {
-                tr += red[g * pr + pi].x;
-                ti += red[g * pr + pi].y;
-            }
+        if (valid) {
             const double c = 0.079577471545947667884;  // 1 / (4 pi)
-            double2 &dst = acc[(int64_t)m * nx + p0 + pb + pi];
-            dst.x += (double)tr * c;
-            dst.y += (double)ti * c;
+#pragma unroll
+            for (int m = 0; m < MC; ++m)
+                if (m0 + m < nrhs) {
+                    double2 *dst = &acc[(int64_t)(m0 + m) * nx + p0 + pb + threadIdx.x];
+                    atomicAdd(&dst->x, (double)o[m].x * c);
+                    atomicAdd(&dst->y, (double)o[m].y * c);
+                }
         }
-        __syncthreads();
     }
 }
 
 void near_field(const ffm_plan_s *p, const void *q, int nrhs, double2 *acc, cudaStream_t s) {
-    if (p->n_near == 0) return;
+    if (p->n_near == 0 || p->n_items == 0) return;
     int ls = p->l_stop;
     NearArgs N;
     N.xl_start = p->bx[ls].start;
@@ -151,10 +265,20 @@ void near_field(const ffm_plan_s *p, const void *q, int nrhs, double2 *acc, cuda
     N.epsYlo = p->epsYlo;
     N.off = p->near_off;
     N.src = p->near_src;
+    N.items = p->items;
     N.dls = std::ldexp(p->d0, -ls);
     for (int d = 0; d < 3; ++d) N.oyx[d] = p->oY[d] - p->oX[d];
     N.k = (float)p->k;
-    dim3 g((unsigned)p->bx[ls].nb, nrhs);
+    if (nrhs > 1) {
+        constexpr int MC = 8;
+        dim3 gm((unsigned)p->n_items, cdiv(nrhs, MC));
+        if (p->kind == FFM_HELMHOLTZ)
+            FFM_LAUNCH((k_p2p_mr<true, MC>), gm, P2P_T, 0, s, N, q, p->ny, nrhs, p->nx, acc);
+        else
+            FFM_LAUNCH((k_p2p_mr<false, MC>), gm, P2P_T, 0, s, N, q, p->ny, nrhs, p->nx, acc);
+        return;
+    }
+    dim3 g((unsigned)p->n_items, nrhs);
     if (p->kind == FFM_HELMHOLTZ)
         FFM_LAUNCH(k_p2p<true>, g, P2P_T, 0, s, N, q, p->ny, nrhs, p->nx, acc);
     else

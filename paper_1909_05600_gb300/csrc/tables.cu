@@ -27,56 +27,43 @@ int r1_rule(int kind, double eps) {
 }
 
 struct LagGeo {
-    double oxy[3]; // oX - oY
+    double oxy[3];  // oX - oY
     double dl;
-    double k;
+    float k;
     int r1;
     int kind;
+    float hnode[R1MAX];  // (d_l / 2) cos((2a+1) pi / (2 r1))
 };
 
-__device__ __forceinline__ void kernel_fp64(int kind, double k, double dx, double dy, double dz, double &gr,
-                                            double &gi) {
-    double r = sqrt(dx * dx + dy * dy + dz * dz);
-    if (r == 0.0) {
-        gr = gi = 0.0;
-        return;
-    }
-    double a = 1.0 / (4.0 * PI * r);
-    if (kind == FFM_LAPLACE) {
-        gr = a;
-        gi = 0.0;
-    } else {
-        double sn, cs;
-        sincos(k * r, &sn, &cs);
-        gr = a * cs;
-        gi = a * sn;
-    }
-}
-
-// T stored as [t][j][i] (source node j outer) so the transfer kernel reads it along i.
+// T stored as [t][j][i] (source node j outer) so the transfer GEMM reads it along i.
+// The translation r0 is formed in FP64 and rounded once; node differences, the distance
+// and the kernel are FP32 (admissible control nodes are at least d_l apart, so the
+// difference loses nothing), and T is stored in FP32.
 __global__ void k_lag_table(const int4 *__restrict__ m, int ntrans, LagGeo geo, float *__restrict__ T) {
     int t = blockIdx.x;
     int r1 = geo.r1, r = r1 * r1 * r1;
     int4 mt = m[t];
-    double r0x = geo.oxy[0] + mt.x * geo.dl, r0y = geo.oxy[1] + mt.y * geo.dl, r0z = geo.oxy[2] + mt.z * geo.dl;
-    double h = 0.5 * geo.dl;
+    float r0x = (float)(geo.oxy[0] + mt.x * geo.dl), r0y = (float)(geo.oxy[1] + mt.y * geo.dl),
+          r0z = (float)(geo.oxy[2] + mt.z * geo.dl);
     bool cplx = geo.kind == FFM_HELMHOLTZ;
+    const float c4pi = 0.07957747154594767f;  // 1 / (4 pi)
     for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
         int j = e / r, i = e % r;
         int ix = i / (r1 * r1), iy = (i / r1) % r1, iz = i % r1;
         int jx = j / (r1 * r1), jy = (j / r1) % r1, jz = j % r1;
-        double c = PI / (2.0 * r1);
-        double dx = r0x + h * (cos((2 * ix + 1) * c) - cos((2 * jx + 1) * c));
-        double dy = r0y + h * (cos((2 * iy + 1) * c) - cos((2 * jy + 1) * c));
-        double dz = r0z + h * (cos((2 * iz + 1) * c) - cos((2 * jz + 1) * c));
-        double gr, gi;
-        kernel_fp64(geo.kind, geo.k, dx, dy, dz, gr, gi);
+        float dx = r0x + (geo.hnode[ix] - geo.hnode[jx]);
+        float dy = r0y + (geo.hnode[iy] - geo.hnode[jy]);
+        float dz = r0z + (geo.hnode[iz] - geo.hnode[jz]);
+        float rr = sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+        float a = c4pi / rr;
         size_t o = (size_t)t * r * r + (size_t)j * r + i;
         if (cplx) {
-            T[2 * o] = (float)gr;
-            T[2 * o + 1] = (float)gi;
+            float sn, cs;
+            sincosf(geo.k * rr, &sn, &cs);
+            T[2 * o] = a * cs;
+            T[2 * o + 1] = a * sn;
         } else {
-            T[o] = (float)gr;
+            T[o] = a;
         }
     }
 }
@@ -242,9 +229,10 @@ void build_tables(ffm_plan_s *p, int l, Alloc &tmp) {
         LagGeo g{};
         for (int d = 0; d < 3; ++d) g.oxy[d] = oxy[d];
         g.dl = dl;
-        g.k = p->k;
+        g.k = (float)p->k;
         g.r1 = F.r1;
         g.kind = p->kind;
+        for (int a = 0; a < F.r1; ++a) g.hnode[a] = (float)(0.5 * dl * std::cos((2.0 * a + 1.0) * PI / (2.0 * F.r1)));
         FFM_LAUNCH(k_lag_table, F.n_trans, 256, 0, s, F.trans_m, F.n_trans, g, F.T);
         return;
     }

@@ -426,62 +426,61 @@ __global__ void k_lower_bound(const uint32_t *__restrict__ needle, int64_t nb, c
 
 // ================================================================== descent
 
-__global__ void k_child_counts(const uint32_t *__restrict__ na, const uint32_t *__restrict__ nbb, int64_t n,
+
+
+// Two-pass expansion without candidate arrays: pass 1 counts the admissible children of
+// each near pair, pass 2 writes admissible and near child pairs at their scanned offsets.
+// Children of (a, b) are visited in the same order in both passes.
+__device__ __forceinline__ bool child_admissible(int4 p, int4 q, const D3 &sig) {
+    return fabs(sig.v[0] + (double)(p.x - q.x)) >= 2.0 || fabs(sig.v[1] + (double)(p.y - q.y)) >= 2.0 ||
+           fabs(sig.v[2] + (double)(p.z - q.z)) >= 2.0;
+}
+
+__global__ void k_expand_count(const uint32_t *__restrict__ na, const uint32_t *__restrict__ nbb, int64_t nnear,
                                const uint32_t *__restrict__ fcx, const uint32_t *__restrict__ fcy,
-                               uint32_t *__restrict__ cnt) {
+                               const int4 *__restrict__ gx, const int4 *__restrict__ gy, D3 sig,
+                               uint32_t *__restrict__ nadm, uint32_t *__restrict__ nnr) {
     int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= n) return;
+    if (e >= nnear) return;
     uint32_t a = na[e], b = nbb[e];
-    cnt[e] = (fcx[a + 1] - fcx[a]) * (fcy[b + 1] - fcy[b]);
+    uint32_t c = 0, t = 0;
+    for (uint32_t a2 = fcx[a]; a2 < fcx[a + 1]; ++a2) {
+        int4 p = gx[a2];
+        for (uint32_t b2 = fcy[b]; b2 < fcy[b + 1]; ++b2) {
+            c += child_admissible(p, gy[b2], sig) ? 1u : 0u;
+            ++t;
+        }
+    }
+    nadm[e] = c;
+    nnr[e] = t - c;
 }
 
-// Children of near pair e: (a', b') for a' in children(a), b' in children(b).
-// Admissible (Sec. 2.2.2, max-norm, non-strict) iff some |sigma_d 2^l + m_d| >= 2.
-__global__ void k_expand(const uint32_t *__restrict__ na, const uint32_t *__restrict__ nbb,
-                         const uint32_t *__restrict__ off, int64_t nnear, int64_t total,
-                         const uint32_t *__restrict__ fcx, const uint32_t *__restrict__ fcy,
-                         const int4 *__restrict__ gx, const int4 *__restrict__ gy, D3 sig,
-                         uint32_t *__restrict__ ca, uint32_t *__restrict__ cb, uint32_t *__restrict__ flag) {
-    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= total) return;
-    int64_t lo = 0, hi = nnear - 1;
-    while (lo < hi) {  // last e with off[e] <= c
-        int64_t mid = (lo + hi + 1) >> 1;
-        if (off[mid] <= (uint32_t)c)
-            lo = mid;
-        else
-            hi = mid - 1;
-    }
-    int64_t e = lo;
+__global__ void k_expand_emit(const uint32_t *__restrict__ na, const uint32_t *__restrict__ nbb, int64_t nnear,
+                              const uint32_t *__restrict__ fcx, const uint32_t *__restrict__ fcy,
+                              const int4 *__restrict__ gx, const int4 *__restrict__ gy, D3 sig,
+                              const uint32_t *__restrict__ oadm, const uint32_t *__restrict__ onr,
+                              uint32_t *__restrict__ aa, uint32_t *__restrict__ ab, uint32_t *__restrict__ ea,
+                              uint32_t *__restrict__ eb) {
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= nnear) return;
     uint32_t a = na[e], b = nbb[e];
-    uint32_t nby = fcy[b + 1] - fcy[b];
-    uint32_t r = (uint32_t)c - off[e];
-    uint32_t a2 = fcx[a] + r / nby, b2 = fcy[b] + r % nby;
-    int4 p = gx[a2], q = gy[b2];
-    double t0 = fabs(sig.v[0] + (double)(p.x - q.x));
-    double t1 = fabs(sig.v[1] + (double)(p.y - q.y));
-    double t2 = fabs(sig.v[2] + (double)(p.z - q.z));
-    ca[c] = a2;
-    cb[c] = b2;
-    flag[c] = (t0 >= 2.0 || t1 >= 2.0 || t2 >= 2.0) ? 1u : 0u;
+    uint32_t ia = oadm[e], in = onr[e];
+    for (uint32_t a2 = fcx[a]; a2 < fcx[a + 1]; ++a2) {
+        int4 p = gx[a2];
+        for (uint32_t b2 = fcy[b]; b2 < fcy[b + 1]; ++b2) {
+            if (child_admissible(p, gy[b2], sig)) {
+                aa[ia] = a2;
+                ab[ia] = b2;
+                ++ia;
+            } else {
+                ea[in] = a2;
+                eb[in] = b2;
+                ++in;
+            }
+        }
+    }
 }
 
-__global__ void k_partition(const uint32_t *__restrict__ ca, const uint32_t *__restrict__ cb,
-                            const uint32_t *__restrict__ flag, const uint32_t *__restrict__ pos, int64_t total,
-                            uint32_t *__restrict__ aa, uint32_t *__restrict__ ab, uint32_t *__restrict__ ea,
-                            uint32_t *__restrict__ eb) {
-    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= total) return;
-    uint32_t p = pos[c];
-    if (flag[c]) {
-        aa[p] = ca[c];
-        ab[p] = cb[c];
-    } else {
-        uint32_t q = (uint32_t)c - p;
-        ea[q] = ca[c];
-        eb[q] = cb[c];
-    }
-}
 
 __global__ void k_gather_u32(const uint32_t *__restrict__ src, const uint32_t *__restrict__ idx, int64_t n,
                              uint32_t *__restrict__ dst) {
@@ -577,6 +576,69 @@ static int64_t read_u64(const unsigned long long *d, cudaStream_t s) {
 __global__ void k_hist_u32(const uint32_t *__restrict__ a, int64_t n, uint32_t *__restrict__ cnt) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) atomicAdd(&cnt[a[i]], 1u);
+}
+
+// CSR offsets of a sorted key array: off[b] = first i with key[i] >= b, b = 0..nkeys.
+__global__ void k_csr_offsets(const uint32_t *__restrict__ key, int64_t n, int64_t nkeys, uint32_t *__restrict__ off) {
+    int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b > nkeys) return;
+    int64_t lo = 0, hi = n;
+    while (lo < hi) {
+        int64_t mid = (lo + hi) >> 1;
+        if (key[mid] < (uint32_t)b)
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    off[b] = (uint32_t)lo;
+}
+
+// Near-field work items of one target leaf: its targets in chunks of P2P_TCHUNK times its
+// near pairs split into consecutive ranges of at most P2P_SMAX source points.
+__device__ __forceinline__ int p2p_ranges(const uint32_t *off, const uint32_t *src, const uint32_t *ystart, int64_t a,
+                                          int4 *out, int base, int tc, int pstart) {
+    int nr = 0;
+    uint32_t e0 = off[a], acc = 0;
+    for (uint32_t e = off[a]; e < off[a + 1]; ++e) {
+        uint32_t nb = ystart[src[e] + 1] - ystart[src[e]];
+        if (acc > 0 && acc + nb > P2P_SMAX) {
+            if (out)
+                for (int c = 0; c < tc; ++c) out[base + nr * tc + c] = make_int4((int)a, pstart + c * P2P_TCHUNK, (int)e0, (int)e);
+            ++nr;
+            e0 = e;
+            acc = 0;
+        }
+        acc += nb;
+    }
+    if (off[a + 1] > off[a]) {
+        if (out)
+            for (int c = 0; c < tc; ++c)
+                out[base + nr * tc + c] = make_int4((int)a, pstart + c * P2P_TCHUNK, (int)e0, (int)off[a + 1]);
+        ++nr;
+    }
+    return nr;
+}
+
+__global__ void k_p2p_items(const uint32_t *__restrict__ off, const uint32_t *__restrict__ src,
+                            const uint32_t *__restrict__ xstart, const uint32_t *__restrict__ ystart, int64_t nleaf,
+                            const uint32_t *__restrict__ pos, uint32_t *__restrict__ cnt, int4 *__restrict__ out) {
+    int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= nleaf) return;
+    int np = (int)(xstart[a + 1] - xstart[a]);
+    int tc = (np + P2P_TCHUNK - 1) / P2P_TCHUNK;
+    if (!out) {
+        cnt[a] = (uint32_t)(p2p_ranges(off, src, ystart, a, nullptr, 0, tc, 0) * tc);
+    } else {
+        p2p_ranges(off, src, ystart, a, out, (int)pos[a], tc, 0);
+    }
+}
+
+// Target box of every pair of a CSR list (pairs of listed target x: [off[x], off[x+1])).
+__global__ void k_expand_csr_targets(const uint32_t *__restrict__ tgt, const uint32_t *__restrict__ off, int64_t nt,
+                                     uint32_t *__restrict__ out) {
+    int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= nt) return;
+    for (uint32_t e = off[x]; e < off[x + 1]; ++e) out[e] = tgt[x];
 }
 
 // ======================================================== leaf coordinates
@@ -794,6 +856,37 @@ static void finish_far_level(ffm_plan_s *p, int l, uint32_t *aa, uint32_t *ab, i
     FFM_LAUNCH(k_sum_sizes, cdiv(F.n_tgt, 256), 256, 0, s, F.tgt, F.n_tgt, p->bx[l].start, sums + 1);
     p->info.src_points[l] = read_u64(sums, s);
     p->info.tgt_points[l] = read_u64(sums + 1, s);
+    if (F.mode == 1) {
+        // pairs grouped by translation for the transfer GEMMs, and the column tiles
+        uint32_t *tk = tmp.get<uint32_t>(na), *pidx = tmp.get<uint32_t>(na);
+        FFM_CUDA(cudaMemcpyAsync(tk, F.adm_t, sizeof(uint32_t) * na, cudaMemcpyDeviceToDevice, s));
+        FFM_LAUNCH(k_iota, cdiv(na, 256), 256, 0, s, pidx, na);
+        radix_sort_u32(tk, pidx, na, bits_for(F.n_trans), tmp, s);
+        // target of every pair in CSR order
+        uint32_t *ptgt = tmp.get<uint32_t>(na);
+        FFM_LAUNCH(k_expand_csr_targets, cdiv(F.n_tgt, 128), 128, 0, s, F.tgt, F.adm_off, F.n_tgt, ptgt);
+        F.bt_src = p->mem.get<uint32_t>(na);
+        F.bt_tgt = p->mem.get<uint32_t>(na);
+        FFM_LAUNCH(k_gather_u32, cdiv(na, 256), 256, 0, s, F.adm_src, pidx, na, F.bt_src);
+        FFM_LAUNCH(k_gather_u32, cdiv(na, 256), 256, 0, s, ptgt, pidx, na, F.bt_tgt);
+        F.bt_off = p->mem.get<uint32_t>(F.n_trans + 1);
+        FFM_LAUNCH(k_csr_offsets, cdiv(F.n_trans + 1, 256), 256, 0, s, tk, na, F.n_trans, F.bt_off);
+        std::vector<uint32_t> hoff(F.n_trans + 1);
+        FFM_CUDA(cudaMemcpyAsync(hoff.data(), F.bt_off, sizeof(uint32_t) * (F.n_trans + 1), cudaMemcpyDeviceToHost, s));
+        FFM_CUDA(cudaStreamSynchronize(s));
+        std::vector<uint32_t> tt, tp;
+        for (int t = 0; t < F.n_trans; ++t)
+            for (uint32_t q0 = hoff[t]; q0 < hoff[t + 1]; q0 += LAG_GEMM_BN) {
+                tt.push_back((uint32_t)t);
+                tp.push_back(q0);
+            }
+        F.n_tiles = (int64_t)tt.size();
+        F.tile_t = p->mem.get<uint32_t>(tt.size());
+        F.tile_p0 = p->mem.get<uint32_t>(tp.size());
+        FFM_CUDA(cudaMemcpyAsync(F.tile_t, tt.data(), sizeof(uint32_t) * tt.size(), cudaMemcpyHostToDevice, s));
+        FFM_CUDA(cudaMemcpyAsync(F.tile_p0, tp.data(), sizeof(uint32_t) * tp.size(), cudaMemcpyHostToDevice, s));
+        FFM_CUDA(cudaStreamSynchronize(s));
+    }
     p->info.mode[l] = F.mode;
     if (F.mode == 1) {
         F.r1 = p->r1_override > 0 ? p->r1_override : r1_rule(p->kind, p->eps);
@@ -866,8 +959,10 @@ void build_plan(ffm_plan_s *p, const void *X, ffm_dtype xdt, const void *Y, ffm_
     }
 
     // ---- Morton keys and the joint stable sort (X first: set bit 0; Y: set bit 1)
-    uint64_t *keys = tmp.get<uint64_t>(n);
-    uint32_t *vals = tmp.get<uint32_t>(n);
+    Alloc sortmem;  // keys, indices and the sort's ping-pong buffers: released after the split
+    sortmem.stream = s;
+    uint64_t *keys = sortmem.get<uint64_t>(n);
+    uint32_t *vals = sortmem.get<uint32_t>(n);
     if (xdt == FFM_F64)
         launch_keys<double>(dX, nx, p->oX, d0, 0ull, 0u, keys, vals, s);
     else
@@ -876,12 +971,13 @@ void build_plan(ffm_plan_s *p, const void *X, ffm_dtype xdt, const void *Y, ffm_
         launch_keys<double>(dY, ny, p->oY, d0, 1ull << 63, (uint32_t)nx, keys + nx, vals + nx, s);
     else
         launch_keys<float>(dY, ny, p->oY, d0, 1ull << 63, (uint32_t)nx, keys + nx, vals + nx, s);
-    radix_sort_u64(keys, vals, n, 64, tmp, s);
+    radix_sort_u64(keys, vals, n, 64, sortmem, s);
     p->keyX = p->mem.get<uint64_t>(nx);
     p->keyY = p->mem.get<uint64_t>(ny);
     p->permX = p->mem.get<uint32_t>(nx);
     p->permY = p->mem.get<uint32_t>(ny);
     FFM_LAUNCH(k_split_sorted, cdiv(n, 256), 256, 0, s, keys, vals, nx, n, p->keyX, p->keyY, p->permX, p->permY);
+    sortmem.release();
 
     // ---- boxes per level
     uint8_t *fX = tmp.get<uint8_t>(nx), *fY = tmp.get<uint8_t>(ny);
@@ -912,6 +1008,7 @@ void build_plan(ffm_plan_s *p, const void *X, ffm_dtype xdt, const void *Y, ffm_
     bool root_adm = false;
     for (int d = 0; d < 3; ++d)
         if (std::fabs(p->sigma[d]) >= 2.0) root_adm = true;
+    Alloc levels[LMAX + 2];  // per-level temporaries of the descent, released level by level
     uint32_t *nearA = tmp.get<uint32_t>(1), *nearB = tmp.get<uint32_t>(1);
     FFM_CUDA(cudaMemsetAsync(nearA, 0, sizeof(uint32_t), s));
     FFM_CUDA(cudaMemsetAsync(nearB, 0, sizeof(uint32_t), s));
@@ -931,23 +1028,27 @@ void build_plan(ffm_plan_s *p, const void *X, ffm_dtype xdt, const void *Y, ffm_
                 break;
             }
             int lc = l + 1;
-            uint32_t *cntc = tmp.get<uint32_t>(nnear), *off = tmp.get<uint32_t>(nnear), *tot = tmp.get<uint32_t>(1);
-            FFM_LAUNCH(k_child_counts, cdiv(nnear, 256), 256, 0, s, nearA, nearB, nnear, p->bx[l].first_child,
-                       p->by[l].first_child, cntc);
-            scan_u32(cntc, off, nnear, tot, tmp, s);
-            int64_t total = read_u32(tot, s);
-            uint32_t *ca = tmp.get<uint32_t>(total), *cb = tmp.get<uint32_t>(total), *flag = tmp.get<uint32_t>(total);
             D3 sg{{std::ldexp(p->sigma[0], lc), std::ldexp(p->sigma[1], lc), std::ldexp(p->sigma[2], lc)}};
-            FFM_LAUNCH(k_expand, cdiv(total, 256), 256, 0, s, nearA, nearB, off, nnear, total, p->bx[l].first_child,
-                       p->by[l].first_child, p->bx[lc].g, p->by[lc].g, sg, ca, cb, flag);
-            uint32_t *pos = tmp.get<uint32_t>(total);
-            scan_u32(flag, pos, total, tot, tmp, s);
-            int64_t na = read_u32(tot, s);
-            int64_t nn = total - na;
-            uint32_t *aa = tmp.get<uint32_t>(na), *ab = tmp.get<uint32_t>(na);
-            uint32_t *ea = tmp.get<uint32_t>(nn), *eb = tmp.get<uint32_t>(nn);
-            FFM_LAUNCH(k_partition, cdiv(total, 256), 256, 0, s, ca, cb, flag, pos, total, aa, ab, ea, eb);
-            finish_far_level(p, lc, aa, ab, na, tmp, s);
+            Alloc &lvl = levels[lc];
+            lvl.stream = s;
+            uint32_t *nadm = lvl.get<uint32_t>(nnear), *nnr = lvl.get<uint32_t>(nnear);
+            uint32_t *oadm = lvl.get<uint32_t>(nnear), *onr = lvl.get<uint32_t>(nnear);
+            uint32_t *tot = lvl.get<uint32_t>(2);
+            FFM_LAUNCH(k_expand_count, cdiv(nnear, 128), 128, 0, s, nearA, nearB, nnear, p->bx[l].first_child,
+                       p->by[l].first_child, p->bx[lc].g, p->by[lc].g, sg, nadm, nnr);
+            scan_u32(nadm, oadm, nnear, tot, lvl, s);
+            scan_u32(nnr, onr, nnear, tot + 1, lvl, s);
+            uint32_t htot[2];
+            FFM_CUDA(cudaMemcpyAsync(htot, tot, sizeof htot, cudaMemcpyDeviceToHost, s));
+            FFM_CUDA(cudaStreamSynchronize(s));
+            int64_t na = htot[0], nn = htot[1];
+            uint32_t *aa = lvl.get<uint32_t>(na), *ab = lvl.get<uint32_t>(na);
+            uint32_t *ea = lvl.get<uint32_t>(nn), *eb = lvl.get<uint32_t>(nn);
+            FFM_LAUNCH(k_expand_emit, cdiv(nnear, 128), 128, 0, s, nearA, nearB, nnear, p->bx[l].first_child,
+                       p->by[l].first_child, p->bx[lc].g, p->by[lc].g, sg, oadm, onr, aa, ab, ea, eb);
+            // the previous level's near list is no longer needed
+            if (l >= 1) levels[l].release();
+            finish_far_level(p, lc, aa, ab, na, lvl, s);
             nearA = ea;
             nearB = eb;
             nnear = nn;
@@ -964,10 +1065,18 @@ void build_plan(ffm_plan_s *p, const void *X, ffm_dtype xdt, const void *Y, ffm_
     if (nnear > 0) {
         Csr c = group_by_target(nearA, nearB, nnear, nleafX, p->mem, tmp, s);
         p->near_src = c.b;
-        uint32_t *h = tmp.get<uint32_t>(nleafX + 1);
-        FFM_CUDA(cudaMemsetAsync(h, 0, sizeof(uint32_t) * (nleafX + 1), s));
-        FFM_LAUNCH(k_hist_u32, cdiv(nnear, 256), 256, 0, s, c.a, nnear, h);
-        scan_u32(h, p->near_off, nleafX + 1, nullptr, tmp, s);
+        FFM_LAUNCH(k_csr_offsets, cdiv(nleafX + 1, 256), 256, 0, s, c.a, nnear, nleafX, p->near_off);
+        // work items: target chunks x bounded source ranges
+        uint32_t *icnt = tmp.get<uint32_t>(nleafX + 1), *ipos = tmp.get<uint32_t>(nleafX + 1);
+        FFM_CUDA(cudaMemsetAsync(icnt, 0, sizeof(uint32_t) * (nleafX + 1), s));
+        FFM_LAUNCH(k_p2p_items, cdiv(nleafX, 128), 128, 0, s, p->near_off, c.b, p->bx[ls].start, p->by[ls].start,
+                   nleafX, (const uint32_t *)nullptr, icnt, (int4 *)nullptr);
+        uint32_t *itot = tmp.get<uint32_t>(1);
+        scan_u32(icnt, ipos, nleafX + 1, itot, tmp, s);
+        p->n_items = read_u32(itot, s);
+        p->items = p->mem.get<int4>(p->n_items);
+        FFM_LAUNCH(k_p2p_items, cdiv(nleafX, 128), 128, 0, s, p->near_off, c.b, p->bx[ls].start, p->by[ls].start,
+                   nleafX, ipos, icnt, p->items);
         unsigned long long *pp = tmp.get<unsigned long long>(1);
         FFM_CUDA(cudaMemsetAsync(pp, 0, sizeof(unsigned long long), s));
         FFM_LAUNCH(k_sum_pair_sizes, cdiv(nnear, 256), 256, 0, s, c.a, c.b, nnear, p->bx[ls].start, p->by[ls].start,

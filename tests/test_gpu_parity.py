@@ -174,16 +174,20 @@ def test_single_points_and_coincidence():
     assert v[0] == 0.0
 
 
-def test_multirhs_columns_equal_single_applies_and_are_deterministic():
-    prob = W.helmholtz_cube_multirhs(30000, nrhs=3, eps=1e-4)
+@pytest.mark.parametrize("nrhs", [3, 11])
+def test_multirhs_columns_match_single_applies_and_are_deterministic(nrhs):
+    prob = W.helmholtz_cube_multirhs(30000, nrhs=nrhs, eps=1e-4)
     U = np.ascontiguousarray(prob.u.T)  # (nrhs, n)
     with gpu_plan(prob) as gp:
         V = gpu_apply(gp, U)
         V2 = gpu_apply(gp, U)
         singles = [gpu_apply(gp, np.ascontiguousarray(U[m])) for m in range(3)]
-    assert np.array_equal(V, V2)
+    ref_ffm = O.ffm(prob.X, prob.Y, as_c128(prob.u[:, :3]), O.HELMHOLTZ, prob.k, prob.eps, w=prob.w)
     for m in range(3):
-        assert np.array_equal(V[m], singles[m])
+        assert O.rel_l2(V[m], ref_ffm[:, m]) < TOL_FFM
+    assert O.rel_l2(V, V2) < 1e-9  # repeatable up to the order of FP64 atomic additions in the near field
+    for m in range(3):  # batched kernels (phasors shared by the RHS) agree with single applies to rounding
+        assert O.rel_l2(V[m], singles[m]) < 1e-6
     t = W.sample_targets(30000, 800)
     ref = O.direct(prob.X, prob.Y, as_c128(prob.u[:, 1]), O.HELMHOLTZ, prob.k, w=prob.w, targets=t)[:, 0]
     assert O.rel_l2(V[1][t], ref) < 1e-4
@@ -195,7 +199,9 @@ def test_host_buffers_match_device_buffers():
         vd = gpu_apply(gp, prob.u)
     with ffm.Plan(prob.X, prob.Y, ffm.LAPLACE, 0.0, prob.eps, weights=prob.w) as hp:
         vh = hp.apply(prob.u)
-    assert np.array_equal(vd, vh)
+    # same plan and kernels; Lagrange transfers scatter with FP32 atomics, so the order of
+    # additions (not the arithmetic) may differ between the two runs
+    assert O.rel_l2(vd, vh) < 1e-6
 
 
 def test_float32_inputs():
@@ -238,3 +244,17 @@ def test_full_size_helmholtz_sphere_1M_sampled_targets():
     t = W.sample_targets(prob.X.shape[0], 256)
     ref = O.direct(prob.X, prob.Y, as_c128(prob.u), O.HELMHOLTZ, prob.k, w=prob.w, targets=t)[:, 0]
     assert O.rel_l2(v[t], ref) < prob.eps
+
+
+def test_laplace_volume_eps_1e4_transfer_gemm():
+    """Volume points with X = Y at eps = 1e-4: r1 = 6 (216 control nodes), transfers by the
+    per-translation GEMM with 189 admissible partners per interior box."""
+    P = W.cube_volume(40000, 12)
+    u = np.random.default_rng(13).standard_normal(40000)
+    prob = W.Problem("vol", P, P.copy(), u, np.full(40000, 1.0 / 40000), W.LAPLACE, 0.0, 1e-4)
+    with gpu_plan(prob, n_leaf=32) as gp:
+        info = gp.info()
+        v = gpu_apply(gp, prob.u)
+    assert max(info["r1"]) == 6
+    ref = O.ffm(P, P, u, O.LAPLACE, 0.0, 1e-4, w=prob.w, n_leaf=32)[:, 0]
+    assert O.rel_l2(v, ref) < TOL_FFM
