@@ -134,6 +134,7 @@ typedef struct {
     int64_t p2p_pairs;         /* point pairs of the near field, sum over near leaf pairs of n_a n_b */
     int pw64[22];              /* 1 if the level's plane-wave kernels run in FP64 */
     double cancel[22];         /* cancellation ratio of the level's quadrature sum (closest pair) */
+    int device_errors;         /* nonzero if a bounded device-side wait gave up (results invalid) */
 } ffm_info;
 
 ffm_status ffm_plan_info(const ffm_plan_t *plan, ffm_info *info);

@@ -206,9 +206,9 @@ __global__ void __launch_bounds__(LG_T) k_lag_gemm(const uint32_t *__restrict__ 
             int j = j0 + jj, i = i0 + ii;
             Q v;
             if constexpr (CPLX)
-                v = (j < r && i < r) ? Tt[(size_t)j * r + i] : make_float2(0.f, 0.f);
+                v = (j < r && i < r) ? Tt[(size_t)i * r + j] : make_float2(0.f, 0.f);
             else
-                v = (j < r && i < r) ? Tt[(size_t)j * r + i] : 0.f;
+                v = (j < r && i < r) ? Tt[(size_t)i * r + j] : 0.f;
             As[jj][ii] = v;
         }
         for (int e = tid; e < LG_BK * BN; e += LG_T) {
@@ -260,6 +260,196 @@ __global__ void __launch_bounds__(LG_T) k_lag_gemm(const uint32_t *__restrict__ 
             }
         }
     }
+}
+
+// ---- tensor-core transfer (5th-generation tensor cores, tcgen05, TF32 with hi/lo split)
+//
+// D(p, i) = sum_j u~_{src(p)}(j) T_t(i, j) for a tile of 128 pairs p of translation t:
+// A = gathered u~ columns (M = 128 pairs, K = r, K-major), B = T_t (N = r padded to a
+// multiple of 16, K-major), accumulator in TMEM (lane = pair, column = i).  Each operand is
+// split into hi + lo TF32 parts (hi: low 13 mantissa bits cleared, lo = x - hi exactly), and
+// D += A_hi B_hi + A_hi B_lo + A_lo B_hi in FP32, about 2^-21 relative per product.
+// Operands use the no-swizzle K-major layout of 8-row x 16-byte core matrices: core matrix
+// (g, c) at byte (g * KT/4 + c) * 128, leading-dimension (K) stride 128 B, 8-row-group stride
+// KT/4 * 128 B.  One thread issues the MMAs; completion is tracked by an mbarrier with a
+// bounded wait that raises a device error flag instead of hanging.
+constexpr int TC_M = 128;
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint32_t kmajor_off(int row, int k, int KT) {
+    return (uint32_t)((((row >> 3) * (KT >> 2) + (k >> 2)) << 7) + ((row & 7) << 4) + ((k & 3) << 2));
+}
+
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
+}
+
+__device__ __forceinline__ void tf32_split(float x, float &hi, float &lo) {
+    hi = __uint_as_float(__float_as_uint(x) & 0xffffe000u);
+    lo = x - hi;
+}
+
+template <int KT>
+__global__ void __launch_bounds__(256) k_lag_gemm_tc(const uint32_t *__restrict__ tile_t,
+                                                     const uint32_t *__restrict__ tile_p0,
+                                                     const uint32_t *__restrict__ bt_off,
+                                                     const uint32_t *__restrict__ bt_src,
+                                                     const uint32_t *__restrict__ bt_tgt, const float *__restrict__ T,
+                                                     int r, int npad, int tcols, int nrhs,
+                                                     const float *__restrict__ ut, float *__restrict__ vt,
+                                                     int *__restrict__ err) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    float *sAh = reinterpret_cast<float *>(smem);
+    float *sAl = sAh + TC_M * KT;
+    float *sBh = sAl + TC_M * KT;
+    float *sBl = sBh + npad * KT;
+    __shared__ uint32_t s_tmem;
+    __shared__ __align__(8) uint64_t s_mbar;
+    __shared__ uint32_t s_src[TC_M], s_tgt[TC_M];
+    int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    int t = tile_t[blockIdx.x], m = blockIdx.y;
+    uint32_t p0 = tile_p0[blockIdx.x];
+    int np = (int)min((uint32_t)TC_M, bt_off[t + 1] - p0);
+    if (tid < TC_M) {
+        s_src[tid] = tid < np ? bt_src[p0 + tid] : 0u;
+        s_tgt[tid] = tid < np ? bt_tgt[p0 + tid] : 0u;
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&s_tmem)),
+                     "r"(tcols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&s_mbar)));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    uint32_t tmem = s_tmem;
+    const float *Tt = T + (size_t)t * r * r;
+    const bool r4 = (r & 3) == 0;  // rows of u~ and T start on 16-byte boundaries
+    const uint32_t lbo = 128, sbo = (KT / 4) * 128;
+    const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(npad >> 3) << 17) | ((uint32_t)(TC_M >> 4) << 24);
+    bool ok = true;
+    int phase = 0;
+    for (int k0 = 0; k0 < r; k0 += KT) {
+        // A: row p = pair, K = source node j (gathered u~ column of the pair's source box).
+        // Each thread moves 4 consecutive K elements = one 16-byte row of a core matrix.
+        constexpr int C4 = KT / 4;
+        for (int e = tid; e < TC_M * C4; e += blockDim.x) {
+            int p = e / C4, c = e % C4;
+            int j = k0 + 4 * c;
+            const float *src = ut + ((size_t)s_src[p] * nrhs + m) * r + j;
+            float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (p < np) {
+                if (r4 && j + 4 <= r) {
+                    x = *reinterpret_cast<const float4 *>(src);
+                } else {
+                    x.x = j < r ? src[0] : 0.f;
+                    x.y = j + 1 < r ? src[1] : 0.f;
+                    x.z = j + 2 < r ? src[2] : 0.f;
+                    x.w = j + 3 < r ? src[3] : 0.f;
+                }
+            }
+            float4 h, l;
+            tf32_split(x.x, h.x, l.x);
+            tf32_split(x.y, h.y, l.y);
+            tf32_split(x.z, h.z, l.z);
+            tf32_split(x.w, h.w, l.w);
+            uint32_t o = kmajor_off(p, 4 * c, KT) >> 2;
+            *reinterpret_cast<float4 *>(sAh + o) = h;
+            *reinterpret_cast<float4 *>(sAl + o) = l;
+        }
+        // B: row n = target node i, K = source node j (rows of T_t)
+        for (int e = tid; e < npad * C4; e += blockDim.x) {
+            int i = e / C4, c = e % C4;
+            int j = k0 + 4 * c;
+            const float *src = Tt + (size_t)i * r + j;
+            float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (i < r) {
+                if (r4 && j + 4 <= r) {
+                    x = *reinterpret_cast<const float4 *>(src);
+                } else {
+                    x.x = j < r ? src[0] : 0.f;
+                    x.y = j + 1 < r ? src[1] : 0.f;
+                    x.z = j + 2 < r ? src[2] : 0.f;
+                    x.w = j + 3 < r ? src[3] : 0.f;
+                }
+            }
+            float4 h, l;
+            tf32_split(x.x, h.x, l.x);
+            tf32_split(x.y, h.y, l.y);
+            tf32_split(x.z, h.z, l.z);
+            tf32_split(x.w, h.w, l.w);
+            uint32_t o = kmajor_off(i, 4 * c, KT) >> 2;
+            *reinterpret_cast<float4 *>(sBh + o) = h;
+            *reinterpret_cast<float4 *>(sBl + o) = l;
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            for (int ks = 0; ks < KT / 8; ++ks) {
+                uint64_t ah = umma_desc(smem_addr(sAh) + ks * 256, lbo, sbo);
+                uint64_t al = umma_desc(smem_addr(sAl) + ks * 256, lbo, sbo);
+                uint64_t bh = umma_desc(smem_addr(sBh) + ks * 256, lbo, sbo);
+                uint64_t bl = umma_desc(smem_addr(sBl) + ks * 256, lbo, sbo);
+                uint32_t acc0 = (k0 > 0 || ks > 0) ? 1u : 0u;
+                asm volatile(
+                    "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                    "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                    "l"(ah), "l"(bh), "r"(idesc), "r"(acc0));
+                asm volatile("tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, 1;\n" ::"r"(tmem), "l"(ah), "l"(bl),
+                             "r"(idesc));
+                asm volatile("tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, 1;\n" ::"r"(tmem), "l"(al), "l"(bh),
+                             "r"(idesc));
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             smem_addr(&s_mbar))
+                         : "memory");
+        }
+        // bounded wait for this K tile's MMAs before the buffers are refilled or D is read
+        uint32_t done = 0;
+        for (int it = 0; it < (1 << 24) && !done; ++it)
+            asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+                         : "=r"(done)
+                         : "r"(smem_addr(&s_mbar)), "r"(phase));
+        if (!done) ok = false;
+        phase ^= 1;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        __syncthreads();
+    }
+    if (!ok && tid == 0) atomicOr(err, 1);
+    // epilogue: warps 0-3 hold TMEM lanes 32w..32w+31 = pairs; columns = target nodes i.
+    // Warps 4-7 (the second warpgroup) take the odd column chunks of the same lanes.
+    int quarter = warp & 3;
+    int p = quarter * 32 + lane;
+    float *dst = vt + ((size_t)s_tgt[p] * nrhs + m) * r;
+    for (int c0 = (warp >> 2) * 8; c0 < npad; c0 += 16) {
+        uint32_t v[8];
+        uint32_t addr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c0;
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                     : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+                     : "r"(addr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (ok && p < np) {
+            if ((r & 3) == 0 && c0 + 8 <= r) {
+                atomicAdd(reinterpret_cast<float4 *>(dst + c0),
+                          make_float4(__uint_as_float(v[0]), __uint_as_float(v[1]), __uint_as_float(v[2]), __uint_as_float(v[3])));
+                atomicAdd(reinterpret_cast<float4 *>(dst + c0 + 4),
+                          make_float4(__uint_as_float(v[4]), __uint_as_float(v[5]), __uint_as_float(v[6]), __uint_as_float(v[7])));
+            } else {
+#pragma unroll
+                for (int q = 0; q < 8; ++q)
+                    if (c0 + q < r) atomicAdd(dst + c0 + q, __uint_as_float(v[q]));
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tcols));
 }
 
 template <bool CPLX>
@@ -338,8 +528,26 @@ void far_lagrange(const ffm_plan_s *p, int l, const void *q, int nrhs, double2 *
         FFM_LAUNCH(k_lag_interp<true>, gt, 128, 0, s, AX, F.tgt, cb, (const float2 *)vt, nrhs, p->nx, acc);
     } else {
         FFM_LAUNCH(k_lag_anterp<false>, gs, LAG_T, 0, s, AY, F.src, cb, (const float *)q, p->ny, nrhs, (float *)ut);
-        FFM_LAUNCH(k_lag_gemm<false>, gg, LG_T, 0, s, F.tile_t, F.tile_p0, F.bt_off, F.bt_src, F.bt_tgt, F.T, r,
-                   nrhs, (const float *)ut, (float *)vt);
+        int npad = (r + 15) / 16 * 16;
+        if (npad <= 256 && F.tc_tiles > 0) {
+            // tensor cores: 128-pair tiles, K tiles of KT source nodes
+            constexpr int KT = 64;
+            int tcols = 32;
+            while (tcols < npad) tcols <<= 1;
+            size_t smem = (size_t)(2 * TC_M * KT + 2 * npad * KT) * sizeof(float);
+            static bool attr = false;
+            if (!attr) {
+                FFM_CUDA(cudaFuncSetAttribute(k_lag_gemm_tc<KT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)(2 * TC_M * KT + 2 * 256 * KT) * (int)sizeof(float)));
+                attr = true;
+            }
+            dim3 gtc((unsigned)F.tc_tiles, nrhs);
+            FFM_LAUNCH(k_lag_gemm_tc<KT>, gtc, 256, smem, s, F.tc_tile_t, F.tc_tile_p0, F.bt_off, F.bt_src, F.bt_tgt,
+                       F.T, r, npad, tcols, nrhs, (const float *)ut, (float *)vt, p->dev_err);
+        } else {
+            FFM_LAUNCH(k_lag_gemm<false>, gg, LG_T, 0, s, F.tile_t, F.tile_p0, F.bt_off, F.bt_src, F.bt_tgt, F.T, r,
+                       nrhs, (const float *)ut, (float *)vt);
+        }
         FFM_LAUNCH(k_lag_interp<false>, gt, 128, 0, s, AX, F.tgt, cb, (const float *)vt, nrhs, p->nx, acc);
     }
 }

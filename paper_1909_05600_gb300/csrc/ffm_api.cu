@@ -317,7 +317,13 @@ ffm_status ffm_plan_bytes(const ffm_plan_t *plan, size_t *bytes) {
 ffm_status ffm_plan_info(const ffm_plan_t *plan, ffm_info *info) {
     if (!plan || !info) return FFM_EINVAL;
     *info = plan->info;
-    return FFM_OK;
+    int err = 0;
+    if (cudaMemcpy(&err, plan->dev_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) {
+        cudaGetLastError();
+        return FFM_ECUDA;
+    }
+    info->device_errors = err;
+    return err ? FFM_ETIMEOUT : FFM_OK;
 }
 
 ffm_status ffm_plan_export(const ffm_plan_t *plan, int what, int level, void *host_out, int64_t *count) {

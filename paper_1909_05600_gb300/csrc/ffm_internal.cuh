@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <atomic>
+#include <cstring>
 #include <string>
 #include <vector>
 
@@ -113,13 +114,16 @@ struct FarLevel {
     int4 *trans_m = nullptr;        // n_trans integer offsets gX - gY
     std::vector<int4> h_trans_m;
     // Lagrange
-    float *T = nullptr;             // n_trans * r * r (real) or float2 (complex), [t][j][i]
+    float *T = nullptr;             // n_trans * r * r (real) or float2 (complex), [t][i][j]
     uint32_t *bt_off = nullptr;     // n_trans+1: pairs grouped by translation (CSR)
     uint32_t *bt_src = nullptr;     // n_adm source box per pair, grouped by translation
     uint32_t *bt_tgt = nullptr;     // n_adm target box per pair, grouped by translation
     int64_t n_tiles = 0;            // GEMM column tiles over all translations
     uint32_t *tile_t = nullptr;     // per tile: translation
     uint32_t *tile_p0 = nullptr;    // per tile: first pair (index into bt_*)
+    int64_t tc_tiles = 0;           // 128-pair tiles for the tensor-core transfer
+    uint32_t *tc_tile_t = nullptr;
+    uint32_t *tc_tile_p0 = nullptr;
     // plane waves: FP32 tables, or FP64 tables when pw64 (large cancellation in the
     // quadrature sum, see tables.cu)
     int pw64 = 0;
@@ -157,6 +161,7 @@ struct ffm_plan_s {
     uint32_t *near_src = nullptr;   // n_near source leaf per pair
     int64_t n_items = 0;            // near-field work items (target chunk x bounded source range)
     int4 *items = nullptr;          // (target leaf, first target in the leaf, first pair, end pair)
+    int *dev_err = nullptr;         // device-side error flags (bounded waits that gave up)
     ffm_info info{};
 };
 
@@ -165,7 +170,30 @@ namespace ffm {
 void build_plan(ffm_plan_s *p, const void *X, ffm_dtype xdt, const void *Y, ffm_dtype ydt, const void *w,
                 ffm_dtype wdt, Alloc &tmp);
 // tables.cu
-void build_tables(ffm_plan_s *p, int l, Alloc &tmp);
+// Host staging buffers that must outlive the asynchronous copies reading them.
+struct HostKeep {
+    std::vector<std::vector<char>> bufs;
+    template <class T>
+    const T *hold(std::vector<T> &&v) {
+        std::vector<char> b(sizeof(T) * v.size());
+        if (!v.empty()) memcpy(b.data(), v.data(), b.size());
+        bufs.push_back(std::move(b));
+        return reinterpret_cast<const T *>(bufs.back().data());
+    }
+};
+// Operator tables of each level are enqueued as soon as the level's translations are known.
+// They run in order on the plan's stream: a concurrent side stream was measured slower,
+// since the table kernels fill every SM and the descent's small kernels queue behind them.
+struct TableJob {
+    cudaStream_t side;
+    Alloc tmp;
+    HostKeep keep;
+    D4 *d_sw[LMAX + 1] = {};
+    explicit TableJob(cudaStream_t main);
+    ~TableJob();
+};
+void build_tables(ffm_plan_s *p, int l, TableJob &tj);   // once level l's translations are known
+void build_octants(ffm_plan_s *p, int l, TableJob &tj);  // once the stop level is known
 int r1_rule(int kind, double eps);
 // farfield.cu / nearfield.cu
 void far_lagrange(const ffm_plan_s *p, int l, const void *q, int nrhs, double2 *acc, Alloc &tmp, cudaStream_t s);

@@ -7,6 +7,8 @@
 //     factors e^{-ik s_q . delta} that move a leaf-centred sum to its ancestor's centre.
 // Tables are computed in FP64 and stored in FP32.
 #include <cmath>
+#include <map>
+#include <tuple>
 #include <vector>
 
 #include "ffm_internal.cuh"
@@ -35,7 +37,8 @@ struct LagGeo {
     float hnode[R1MAX];  // (d_l / 2) cos((2a+1) pi / (2 r1))
 };
 
-// T stored as [t][j][i] (source node j outer) so the transfer GEMM reads it along i.
+// T stored as [t][i][j] (source node j innermost): rows of T are K-major operands of the
+// transfer GEMMs.
 // The translation r0 is formed in FP64 and rounded once; node differences, the distance
 // and the kernel are FP32 (admissible control nodes are at least d_l apart, so the
 // difference loses nothing), and T is stored in FP32.
@@ -48,7 +51,7 @@ __global__ void k_lag_table(const int4 *__restrict__ m, int ntrans, LagGeo geo, 
     bool cplx = geo.kind == FFM_HELMHOLTZ;
     const float c4pi = 0.07957747154594767f;  // 1 / (4 pi)
     for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
-        int j = e / r, i = e % r;
+        int i = e / r, j = e % r;
         int ix = i / (r1 * r1), iy = (i / r1) % r1, iz = i % r1;
         int jx = j / (r1 * r1), jy = (j / r1) % r1, jz = j % r1;
         float dx = r0x + (geo.hnode[ix] - geo.hnode[jx]);
@@ -56,7 +59,7 @@ __global__ void k_lag_table(const int4 *__restrict__ m, int ntrans, LagGeo geo, 
         float dz = r0z + (geo.hnode[iz] - geo.hnode[jz]);
         float rr = sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
         float a = c4pi / rr;
-        size_t o = (size_t)t * r * r + (size_t)j * r + i;
+        size_t o = (size_t)t * r * r + (size_t)i * r + j;
         if (cplx) {
             float sn, cs;
             sincosf(geo.k * rr, &sn, &cs);
@@ -105,47 +108,83 @@ __device__ __forceinline__ dflt df_split(double x) {
 // coef: per translation L+1 complex coefficients split as (re.hi, re.lo, im.hi, im.lo);
 // beta: L entries p/(p+1) split as (hi, lo).
 template <class OUT>
-__global__ void __launch_bounds__(256) k_pw_table(const D4 *__restrict__ sw, int nQ, const float4 *__restrict__ coef,
+__device__ __forceinline__ void put_d(OUT *D, size_t o, double f, dflt r, dflt i) {
+    // D = i f (sum_re + i sum_im)
+    double tr = (double)r.hi + (double)r.lo, ti = (double)i.hi + (double)i.lo;
+    if constexpr (sizeof(OUT) == sizeof(float2))
+        D[o] = make_float2((float)(-f * ti), (float)(f * tr));
+    else
+        D[o] = make_double2(-f * ti, f * tr);
+}
+
+// One Legendre recurrence serves four table entries.  With x = s_h . rhat_t, the sum splits
+// into even-degree and odd-degree parts E(x) + O(x); direction h + nQ/2 is -s_h, where the
+// sum is E - O.  A translation -m with the same length (the two root boxes share their
+// centre) has rhat = -rhat_t, so its entries are the same two values with the directions
+// swapped.  pairs[c] = (t, partner of t or -1).
+template <class OUT>
+__global__ void __launch_bounds__(256) k_pw_table(const D4 *__restrict__ sw, int nH, const float4 *__restrict__ coef,
                                                   const float2 *__restrict__ beta, int L,
-                                                  const D4 *__restrict__ rhat, double k, OUT *__restrict__ D) {
+                                                  const D4 *__restrict__ rhat, const int2 *__restrict__ pairs,
+                                                  double k, OUT *__restrict__ D) {
     extern __shared__ float4 sm[];
     float4 *sc = sm;                                  // L+1 coefficients
     float2 *sb = reinterpret_cast<float2 *>(sm + L + 1);  // L betas
-    int t = blockIdx.y;
+    int2 tp = pairs[blockIdx.y];
+    int t = tp.x;
     for (int i = threadIdx.x; i <= L; i += blockDim.x) sc[i] = coef[(size_t)t * (L + 1) + i];
     for (int i = threadIdx.x; i < L; i += blockDim.x) sb[i] = beta[i];
     __syncthreads();
     int q = blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= nQ) return;
+    if (q >= nH) return;
     D4 s = sw[q];
     D4 rh = rhat[t];
     dflt x = df_split(s.x * rh.x + s.y * rh.y + s.z * rh.z);
     dflt p0 = {1.f, 0.f}, p1 = x;
     float4 c0 = sc[0];
-    dflt sr = {c0.x, c0.y}, si = {c0.z, c0.w};
+    dflt er = {c0.x, c0.y}, ei = {c0.z, c0.w}, orr = {0.f, 0.f}, oi = {0.f, 0.f};
     if (L >= 1) {
         float4 c1 = sc[1];
-        sr = df_add(sr, df_mul({c1.x, c1.y}, x));
-        si = df_add(si, df_mul({c1.z, c1.w}, x));
+        orr = df_mul({c1.x, c1.y}, x);
+        oi = df_mul({c1.z, c1.w}, x);
     }
-    for (int p = 1; p < L; ++p) {
+    // P_{p+1} = x P_p + (p/(p+1)) (x P_p - P_{p-1}); degree p+1 is even for odd p
+    auto step = [&](int pp) {
         dflt xp = df_mul(x, p1);
         dflt diff = df_add(xp, {-p0.hi, -p0.lo});
-        float2 b = sb[p];
+        float2 b = sb[pp];
         dflt p2 = df_add(xp, df_mul({b.x, b.y}, diff));
-        float4 c = sc[p + 1];
-        sr = df_add(sr, df_mul({c.x, c.y}, p2));
-        si = df_add(si, df_mul({c.z, c.w}, p2));
         p0 = p1;
         p1 = p2;
+        return p2;
+    };
+    int pp = 1;
+    for (; pp + 1 < L; pp += 2) {
+        dflt pe = step(pp);
+        float4 c = sc[pp + 1];
+        er = df_add(er, df_mul({c.x, c.y}, pe));
+        ei = df_add(ei, df_mul({c.z, c.w}, pe));
+        dflt po = step(pp + 1);
+        float4 d = sc[pp + 2];
+        orr = df_add(orr, df_mul({d.x, d.y}, po));
+        oi = df_add(oi, df_mul({d.z, d.w}, po));
+    }
+    if (pp < L) {
+        dflt pe = step(pp);
+        float4 c = sc[pp + 1];
+        er = df_add(er, df_mul({c.x, c.y}, pe));
+        ei = df_add(ei, df_mul({c.z, c.w}, pe));
     }
     double f = k * s.w / (4.0 * PI);
-    double tr = (double)sr.hi + (double)sr.lo, ti = (double)si.hi + (double)si.lo;
-    size_t o = (size_t)t * nQ + q;
-    if constexpr (sizeof(OUT) == sizeof(float2))
-        D[o] = make_float2((float)(-f * ti), (float)(f * tr));
-    else
-        D[o] = make_double2(-f * ti, f * tr);
+    dflt pr = df_add(er, orr), pi = df_add(ei, oi);
+    dflt mr = df_add(er, {-orr.hi, -orr.lo}), mi = df_add(ei, {-oi.hi, -oi.lo});
+    size_t nQ = 2 * (size_t)nH;
+    put_d(D, (size_t)t * nQ + q, f, pr, pi);
+    put_d(D, (size_t)t * nQ + q + nH, f, mr, mi);
+    if (tp.y >= 0) {
+        put_d(D, (size_t)tp.y * nQ + q, f, mr, mi);
+        put_d(D, (size_t)tp.y * nQ + q + nH, f, pr, pi);
+    }
 }
 
 // E[d][oct][q] = e^{-ik s_q . delta}, delta_axis = (bit - 1/2) d_m for depth m = l+1+d.
@@ -216,17 +255,26 @@ static void hankel1(int L, double z, std::vector<double> &hr, std::vector<double
     }
 }
 
-void build_tables(ffm_plan_s *p, int l, Alloc &tmp) {
+TableJob::TableJob(cudaStream_t main) : side(main) { tmp.stream = main; }
+
+TableJob::~TableJob() {
+    // host staging buffers may still be read by queued copies
+    cudaStreamSynchronize(side);
+    tmp.release();
+}
+
+void build_tables(ffm_plan_s *p, int l, TableJob &tj) {
     FarLevel &F = p->far[l];
-    cudaStream_t s = p->stream;
+    cudaStream_t s = tj.side;
+    Alloc &tmp = tj.tmp;
+    if (F.mode == 1 && F.r1 > R1MAX) fail(FFM_EUNSUPPORTED, "eps needs more than 8 Chebyshev nodes per axis");
     double dl = std::ldexp(p->d0, -l);
     double oxy[3] = {p->oX[0] - p->oY[0], p->oX[1] - p->oY[1], p->oX[2] - p->oY[2]};
     if (F.mode == 1) {
-        if (F.r1 > R1MAX) fail(FFM_EUNSUPPORTED, "eps needs more than 8 Chebyshev nodes per axis");
         int r = F.r1 * F.r1 * F.r1;
         bool cplx = p->kind == FFM_HELMHOLTZ;
         F.T = p->mem.get<float>((size_t)F.n_trans * r * r * (cplx ? 2 : 1));
-        LagGeo g{};
+            LagGeo g{};
         for (int d = 0; d < 3; ++d) g.oxy[d] = oxy[d];
         g.dl = dl;
         g.k = (float)p->k;
@@ -319,47 +367,77 @@ void build_tables(ffm_plan_s *p, int l, Alloc &tmp) {
         float h = (float)bq;
         beta[q] = make_float2(h, (float)(bq - (double)h));
     }
+    // canonical translations: t with its partner -m (when the root centres coincide the
+    // set of translations is symmetric and -m has the same coefficients)
+    std::vector<int2> pairs;
+    {
+        bool same_centre = oxy[0] == 0.0 && oxy[1] == 0.0 && oxy[2] == 0.0;
+        std::map<std::tuple<int, int, int>, int> idx;
+        if (same_centre)
+            for (int t = 0; t < nt; ++t) idx[{F.h_trans_m[t].x, F.h_trans_m[t].y, F.h_trans_m[t].z}] = t;
+        for (int t = 0; t < nt; ++t) {
+            int partner = -1;
+            if (same_centre) {
+                auto it = idx.find({-F.h_trans_m[t].x, -F.h_trans_m[t].y, -F.h_trans_m[t].z});
+                if (it != idx.end()) partner = it->second;
+            }
+            if (partner >= 0 && partner < t) continue;  // done with its partner
+            pairs.push_back(make_int2(t, partner == t ? -1 : partner));
+        }
+    }
+    int npairs = (int)pairs.size();
+    dim3 g1(cdiv(nH, 256), npairs);
+    size_t sm1 = sizeof(float4) * (L + 1) + sizeof(float2) * L;
+    if (F.pw64) {
+        F.ksd = p->mem.get<D4>(nQ);
+        F.Dd = p->mem.get<double2>((size_t)nt * nQ);
+    } else {
+        F.ks = p->mem.get<float4>(nQ);
+        F.D = p->mem.get<float2>((size_t)nt * nQ);
+    }
     D4 *d_sw = tmp.get<D4>(nQ);
+    tj.d_sw[l] = d_sw;
     float4 *d_coef = tmp.get<float4>(coef.size());
     float2 *d_beta = tmp.get<float2>(beta.size());
     D4 *d_rhat = tmp.get<D4>(nt);
-    FFM_CUDA(cudaMemcpyAsync(d_sw, sw.data(), sizeof(D4) * nQ, cudaMemcpyHostToDevice, s));
-    FFM_CUDA(cudaMemcpyAsync(d_coef, coef.data(), sizeof(float4) * coef.size(), cudaMemcpyHostToDevice, s));
-    FFM_CUDA(cudaMemcpyAsync(d_beta, beta.data(), sizeof(float2) * beta.size(), cudaMemcpyHostToDevice, s));
-    FFM_CUDA(cudaMemcpyAsync(d_rhat, rhat.data(), sizeof(D4) * nt, cudaMemcpyHostToDevice, s));
-    dim3 g1(cdiv(nQ, 256), nt);
-    size_t sm1 = sizeof(float4) * (L + 1) + sizeof(float2) * L;
-    int ndepth = p->l_stop - l;
-    dim3 g2(cdiv(nQ, 128), ndepth, 8);
+    int2 *d_pairs = tmp.get<int2>(npairs);
+    HostKeep &keep = tj.keep;
+    const D4 *h_sw = keep.hold(std::vector<D4>(sw));
+    size_t ncoef = coef.size(), nbeta = beta.size();
+    FFM_CUDA(cudaMemcpyAsync(d_sw, h_sw, sizeof(D4) * nQ, cudaMemcpyHostToDevice, s));
+    FFM_CUDA(cudaMemcpyAsync(d_coef, keep.hold(std::move(coef)), sizeof(float4) * ncoef, cudaMemcpyHostToDevice, s));
+    FFM_CUDA(cudaMemcpyAsync(d_beta, keep.hold(std::move(beta)), sizeof(float2) * nbeta, cudaMemcpyHostToDevice, s));
+    FFM_CUDA(cudaMemcpyAsync(d_rhat, keep.hold(std::move(rhat)), sizeof(D4) * nt, cudaMemcpyHostToDevice, s));
+    FFM_CUDA(cudaMemcpyAsync(d_pairs, keep.hold(std::move(pairs)), sizeof(int2) * npairs, cudaMemcpyHostToDevice, s));
     if (F.pw64) {
         std::vector<D4> ks(nQ);
         for (int q = 0; q < nQ; ++q) ks[q] = D4{p->k * sw[q].x, p->k * sw[q].y, p->k * sw[q].z, 0.0};
-        F.ksd = p->mem.get<D4>(nQ);
-        FFM_CUDA(cudaMemcpyAsync(F.ksd, ks.data(), sizeof(D4) * nQ, cudaMemcpyHostToDevice, s));
-        F.Dd = p->mem.get<double2>((size_t)nt * nQ);
-        FFM_LAUNCH(k_pw_table<double2>, g1, 256, sm1, s, d_sw, nQ, d_coef, d_beta, L, d_rhat, p->k, F.Dd);
-        if (ndepth > 0) {
-            F.Ed = p->mem.get<double2>((size_t)ndepth * 8 * nQ);
-            FFM_LAUNCH(k_pw_octants<double2>, g2, 128, 0, s, d_sw, nQ, p->k, std::ldexp(p->d0, -(l + 1)), ndepth,
-                       F.Ed);
-        }
-        FFM_CUDA(cudaStreamSynchronize(s));
+        FFM_CUDA(cudaMemcpyAsync(F.ksd, keep.hold(std::move(ks)), sizeof(D4) * nQ, cudaMemcpyHostToDevice, s));
+        FFM_LAUNCH(k_pw_table<double2>, g1, 256, sm1, s, d_sw, nH, d_coef, d_beta, L, d_rhat, d_pairs, p->k, F.Dd);
     } else {
         std::vector<float4> ks(nQ);
         for (int q = 0; q < nQ; ++q)
             ks[q] = make_float4((float)(p->k * sw[q].x), (float)(p->k * sw[q].y), (float)(p->k * sw[q].z), 0.f);
-        F.ks = p->mem.get<float4>(nQ);
-        FFM_CUDA(cudaMemcpyAsync(F.ks, ks.data(), sizeof(float4) * nQ, cudaMemcpyHostToDevice, s));
-        F.D = p->mem.get<float2>((size_t)nt * nQ);
-        FFM_LAUNCH(k_pw_table<float2>, g1, 256, sm1, s, d_sw, nQ, d_coef, d_beta, L, d_rhat, p->k, F.D);
-        if (ndepth > 0) {
-            F.E = p->mem.get<float2>((size_t)ndepth * 8 * nQ);
-            FFM_LAUNCH(k_pw_octants<float2>, g2, 128, 0, s, d_sw, nQ, p->k, std::ldexp(p->d0, -(l + 1)), ndepth,
-                       F.E);
-        }
-        // host vectors die here: wait for the copies that read them
-        FFM_CUDA(cudaStreamSynchronize(s));
+        FFM_CUDA(cudaMemcpyAsync(F.ks, keep.hold(std::move(ks)), sizeof(float4) * nQ, cudaMemcpyHostToDevice, s));
+        FFM_LAUNCH(k_pw_table<float2>, g1, 256, sm1, s, d_sw, nH, d_coef, d_beta, L, d_rhat, d_pairs, p->k, F.D);
     }
+}
+
+void build_octants(ffm_plan_s *p, int l, TableJob &tj) {
+    FarLevel &F = p->far[l];
+    int ndepth = p->l_stop - l;
+    if (F.mode != 2 || ndepth <= 0) return;
+    int nQ = F.nQ;
+    dim3 g2(cdiv(nQ, 128), ndepth, 8);
+    double half = std::ldexp(p->d0, -(l + 1));
+    if (F.pw64)
+        F.Ed = p->mem.get<double2>((size_t)ndepth * 8 * nQ);
+    else
+        F.E = p->mem.get<float2>((size_t)ndepth * 8 * nQ);
+    if (F.pw64)
+        FFM_LAUNCH(k_pw_octants<double2>, g2, 128, 0, tj.side, tj.d_sw[l], nQ, p->k, half, ndepth, F.Ed);
+    else
+        FFM_LAUNCH(k_pw_octants<float2>, g2, 128, 0, tj.side, tj.d_sw[l], nQ, p->k, half, ndepth, F.E);
 }
 
 }  // namespace ffm

@@ -874,17 +874,27 @@ static void finish_far_level(ffm_plan_s *p, int l, uint32_t *aa, uint32_t *ab, i
         std::vector<uint32_t> hoff(F.n_trans + 1);
         FFM_CUDA(cudaMemcpyAsync(hoff.data(), F.bt_off, sizeof(uint32_t) * (F.n_trans + 1), cudaMemcpyDeviceToHost, s));
         FFM_CUDA(cudaStreamSynchronize(s));
-        std::vector<uint32_t> tt, tp;
-        for (int t = 0; t < F.n_trans; ++t)
+        std::vector<uint32_t> tt, tp, ct, cp;
+        for (int t = 0; t < F.n_trans; ++t) {
             for (uint32_t q0 = hoff[t]; q0 < hoff[t + 1]; q0 += LAG_GEMM_BN) {
                 tt.push_back((uint32_t)t);
                 tp.push_back(q0);
             }
+            for (uint32_t q0 = hoff[t]; q0 < hoff[t + 1]; q0 += 128) {
+                ct.push_back((uint32_t)t);
+                cp.push_back(q0);
+            }
+        }
         F.n_tiles = (int64_t)tt.size();
         F.tile_t = p->mem.get<uint32_t>(tt.size());
         F.tile_p0 = p->mem.get<uint32_t>(tp.size());
+        F.tc_tiles = (int64_t)ct.size();
+        F.tc_tile_t = p->mem.get<uint32_t>(ct.size());
+        F.tc_tile_p0 = p->mem.get<uint32_t>(cp.size());
         FFM_CUDA(cudaMemcpyAsync(F.tile_t, tt.data(), sizeof(uint32_t) * tt.size(), cudaMemcpyHostToDevice, s));
         FFM_CUDA(cudaMemcpyAsync(F.tile_p0, tp.data(), sizeof(uint32_t) * tp.size(), cudaMemcpyHostToDevice, s));
+        FFM_CUDA(cudaMemcpyAsync(F.tc_tile_t, ct.data(), sizeof(uint32_t) * ct.size(), cudaMemcpyHostToDevice, s));
+        FFM_CUDA(cudaMemcpyAsync(F.tc_tile_p0, cp.data(), sizeof(uint32_t) * cp.size(), cudaMemcpyHostToDevice, s));
         FFM_CUDA(cudaStreamSynchronize(s));
     }
     p->info.mode[l] = F.mode;
@@ -905,6 +915,9 @@ void build_plan(ffm_plan_s *p, const void *X, ffm_dtype xdt, const void *Y, ffm_
     int64_t nx = p->nx, ny = p->ny, n = nx + ny;
     size_t xb = (xdt == FFM_F64 ? 8 : 4) * 3 * (size_t)nx, yb = (ydt == FFM_F64 ? 8 : 4) * 3 * (size_t)ny;
     const void *dX = to_device(X, xb, tmp, s), *dY = to_device(Y, yb, tmp, s);
+
+    p->dev_err = p->mem.get<int>(4);
+    FFM_CUDA(cudaMemsetAsync(p->dev_err, 0, 4 * sizeof(int), s));
 
     // ---- root cubes (Sec. 2.2.1)
     unsigned long long *bb = tmp.get<unsigned long long>(14);
@@ -1009,6 +1022,7 @@ void build_plan(ffm_plan_s *p, const void *X, ffm_dtype xdt, const void *Y, ffm_
     for (int d = 0; d < 3; ++d)
         if (std::fabs(p->sigma[d]) >= 2.0) root_adm = true;
     Alloc levels[LMAX + 2];  // per-level temporaries of the descent, released level by level
+    TableJob tj(s);
     uint32_t *nearA = tmp.get<uint32_t>(1), *nearB = tmp.get<uint32_t>(1);
     FFM_CUDA(cudaMemsetAsync(nearA, 0, sizeof(uint32_t), s));
     FFM_CUDA(cudaMemsetAsync(nearB, 0, sizeof(uint32_t), s));
@@ -1018,6 +1032,7 @@ void build_plan(ffm_plan_s *p, const void *X, ffm_dtype xdt, const void *Y, ffm_
         p->root_adm = 1;
         p->info.root_admissible = 1;
         finish_far_level(p, 0, nearA, nearB, 1, tmp, s);
+        if (p->far[0].n_adm > 0) build_tables(p, 0, tj);
         nnear = 0;
     } else {
         p->info.n_near[0] = 1;
@@ -1049,6 +1064,7 @@ void build_plan(ffm_plan_s *p, const void *X, ffm_dtype xdt, const void *Y, ffm_
             // the previous level's near list is no longer needed
             if (l >= 1) levels[l].release();
             finish_far_level(p, lc, aa, ab, na, lvl, s);
+            if (p->far[lc].n_adm > 0) build_tables(p, lc, tj);
             nearA = ea;
             nearB = eb;
             nnear = nn;
@@ -1116,7 +1132,7 @@ void build_plan(ffm_plan_s *p, const void *X, ffm_dtype xdt, const void *Y, ffm_
             FFM_LAUNCH(k_sorted_weights<float>, cdiv(ny, 256), 256, 0, s, (const float *)dw, p->permY, ny, p->wY);
     }
     for (int l = 0; l <= ls; ++l)
-        if (p->far[l].n_adm > 0) build_tables(p, l, tmp);
+        if (p->far[l].n_adm > 0) build_octants(p, l, tj);
     FFM_CUDA(cudaStreamSynchronize(s));
 }
 

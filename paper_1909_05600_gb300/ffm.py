@@ -49,11 +49,12 @@ class Info(C.Structure):
                 ("mode", C.c_int * 22), ("r1", C.c_int * 22), ("L", C.c_int * 22), ("nQ", C.c_int * 22),
                 ("nx", C.c_int64), ("ny", C.c_int64), ("src_points", C.c_int64 * 22),
                 ("tgt_points", C.c_int64 * 22), ("p2p_pairs", C.c_int64), ("pw64", C.c_int * 22),
-                ("cancel", C.c_double * 22)]
+                ("cancel", C.c_double * 22), ("device_errors", C.c_int)]
 
     def as_dict(self):
         d = {"l_stop": self.l_stop, "root_admissible": self.root_admissible, "d0": self.d0, "oX": list(self.oX),
-             "oY": list(self.oY), "nx": self.nx, "ny": self.ny, "p2p_pairs": self.p2p_pairs}
+             "oY": list(self.oY), "nx": self.nx, "ny": self.ny, "p2p_pairs": self.p2p_pairs,
+             "device_errors": self.device_errors}
         for f in ("nboxX", "nboxY", "n_adm", "n_near", "n_trans", "mode", "r1", "L", "nQ", "src_points",
                   "tgt_points", "pw64", "cancel"):
             d[f] = list(getattr(self, f))
