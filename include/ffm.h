@@ -60,6 +60,19 @@ typedef enum {
     FFM_C128 = 3  /* interleaved complex double */
 } ffm_dtype;
 
+/* Arithmetic of the plane-wave levels (forward transform, transfer, backward transform).
+ * The quadrature sum of a level cancels by the ratio C = sum_q |D(q)| / |sum_q D(q)|
+ * (closest translation), which amplifies rounding errors by up to C; it is large at low
+ * k d_l and small eps.  FFM_PREC_AUTO picks FP32 for C <= 250, compensated FP32 (own
+ * accurate sincos, TwoSum accumulation of the direction and translation sums) for
+ * C <= 4e3, FP64 above, which keeps the rounding error below ~6e-6 relative. */
+typedef enum {
+    FFM_PREC_AUTO = 0,
+    FFM_PREC_F32 = 1,   /* FP32, hardware sincos approximation */
+    FFM_PREC_F32C = 2,  /* FP32 with accurate sincos and compensated sums */
+    FFM_PREC_F64 = 3    /* FP64 */
+} ffm_precision;
+
 /* Plan options.  Zero-initialise and set what you need; a NULL opts pointer means all
  * defaults.  The defaults are the plan constants of the method (readings of the paper
  * where it is silent): n_leaf = 64, l_cap = 21, kappa_switch = 2.0, r1 from the
@@ -71,7 +84,8 @@ typedef struct {
     double kappa_switch;  /* Helmholtz: plane waves at level l iff k d_l >= kappa_switch,
                              Lagrange otherwise (Sec. 2.2.3); 0 -> 2.0 */
     int r1_override;      /* Chebyshev nodes per axis for Lagrange levels (2..8); 0 -> rule */
-    int precision;        /* reserved, 0 */
+    int precision;        /* plane-wave level arithmetic, one of ffm_precision; 0 -> chosen
+                             per level from the quadrature's cancellation ratio */
     const void *weights;  /* quadrature weights w_j (N_Y entries), host or device; NULL -> 1 */
     ffm_dtype weights_dtype; /* FFM_F32 or FFM_F64 */
 } ffm_opts;
@@ -132,7 +146,7 @@ typedef struct {
     int64_t src_points[22];    /* source points in boxes with admissible pairs (per level) */
     int64_t tgt_points[22];    /* target points in boxes with admissible pairs (per level) */
     int64_t p2p_pairs;         /* point pairs of the near field, sum over near leaf pairs of n_a n_b */
-    int pw64[22];              /* 1 if the level's plane-wave kernels run in FP64 */
+    int pw_prec[22];           /* plane-wave levels: the ffm_precision they run in (0 otherwise) */
     double cancel[22];         /* cancellation ratio of the level's quadrature sum (closest pair) */
     int device_errors;         /* nonzero if a bounded device-side wait gave up (results invalid) */
 } ffm_info;

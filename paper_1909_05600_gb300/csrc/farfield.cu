@@ -586,20 +586,67 @@ __device__ __forceinline__ double2 czero(double) { return make_double2(0.0, 0.0)
 __device__ __forceinline__ float2 cone(float) { return make_float2(1.f, 0.f); }
 __device__ __forceinline__ double2 cone(double) { return make_double2(1.0, 0.0); }
 
-// Cody-Waite reduction of a phase to [-pi, pi] (two-term 2 pi), then FP32 sincos.
-template <bool REDUCE>
-__device__ __forceinline__ void phase_sincos(float ph, float &s, float &c) {
-    if constexpr (REDUCE) {
-        float n = rintf(ph * 0.15915494309189535f);
-        ph = fmaf(-n, 6.28318548202514648f, ph);
-        ph = fmaf(-n, -1.7484555314695172e-07f, ph);
-    }
-    __sincosf(ph, &s, &c);
+// Phasor modes of the FP32 levels: the hardware sincos approximation on the phase as is
+// (PH_MUFU) or after Cody-Waite reduction to [-pi, pi] (PH_MUFU_RED), or the accurate
+// sincos below (PH_ACC, compensated levels).  FP64 levels ignore the mode.
+constexpr int PH_MUFU = 0, PH_MUFU_RED = 1, PH_ACC = 2;
+
+// sin and cos to about one FP32 ulp: x = n pi/2 + r with |r| <= pi/4 (Cody and Waite's
+// reduction, pi/2 split in two FP32 terms), then the Taylor series of sin r to r^9 and of
+// cos r to r^10, whose first omitted terms are below 3e-9, and the quadrant's symmetry.
+__device__ __forceinline__ void sincos_acc(float x, float &s, float &c) {
+    constexpr double PIO2 = 1.5707963267948966;
+    constexpr float PIO2_HI = (float)PIO2;
+    constexpr float PIO2_LO = (float)(PIO2 - (double)PIO2_HI);
+    constexpr float TWO_OVER_PI = (float)(2.0 / 3.14159265358979323846);
+    // n = nearest integer of x 2/pi by the 1.5 2^23 shifter; its low bits give the quadrant
+    float t = fmaf(x, TWO_OVER_PI, 12582912.f);
+    float n = t - 12582912.f;
+    float r = fmaf(-n, PIO2_HI, x);
+    r = fmaf(-n, PIO2_LO, r);
+    float r2 = r * r;
+    // coefficients (-1)^j / (2j+1)! and (-1)^j / (2j)!
+    float ps = fmaf(r2, (float)(1.0 / 362880.0), (float)(-1.0 / 5040.0));
+    ps = fmaf(r2, ps, (float)(1.0 / 120.0));
+    ps = fmaf(r2, ps, (float)(-1.0 / 6.0));
+    float sr = fmaf(r * r2, ps, r);
+    float pc = fmaf(r2, (float)(-1.0 / 3628800.0), (float)(1.0 / 40320.0));
+    pc = fmaf(r2, pc, (float)(-1.0 / 720.0));
+    pc = fmaf(r2, pc, (float)(1.0 / 24.0));
+    pc = fmaf(r2, pc, -0.5f);
+    float cr = fmaf(r2, pc, 1.0f);
+    int q = __float_as_int(t) & 3;
+    float a = (q & 1) ? cr : sr, b = (q & 1) ? sr : cr;
+    s = (q & 2) ? -a : a;
+    c = ((q + 1) & 2) ? -b : b;
 }
-template <bool REDUCE>
+
+template <int PH>
+__device__ __forceinline__ void phase_sincos(float ph, float &s, float &c) {
+    if constexpr (PH == PH_ACC) {
+        sincos_acc(ph, s, c);
+    } else {
+        if constexpr (PH == PH_MUFU_RED) {
+            float n = rintf(ph * 0.15915494309189535f);
+            ph = fmaf(-n, 6.28318548202514648f, ph);
+            ph = fmaf(-n, -1.7484555314695172e-07f, ph);
+        }
+        __sincosf(ph, &s, &c);
+    }
+}
+template <int PH>
 __device__ __forceinline__ void phase_sincos(double ph, double &s, double &c) {
     sincos(ph, &s, &c);
 }
+
+// hi + t with the rounding error carried into lo (Knuth's TwoSum; no ordering assumption)
+__device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float t) {
+    float sum = hi + t;
+    float bb = sum - hi;
+    lo += (hi - (sum - bb)) + (t - bb);
+    hi = sum;
+}
+__device__ __forceinline__ void two_sum_acc(double &hi, double &, double t) { hi += t; }
 
 // Leaf-relative coordinates of a point in the level's scalar type (hi part only in FP32,
 // hi + lo in FP64).
@@ -649,9 +696,10 @@ __device__ __forceinline__ typename PwT<R>::C leaf_factor(const PwArgs<R> &P, co
 // leaves of the box are visited in order; each leaf's points are staged in shared memory
 // and summed with leaf-centred phases in a tight loop, then the leaf sum is moved to the
 // box centre by its octant factor.  Directions h and h + nQ/2 are antipodal, so one
-// sincos of k s_h . e gives e^{-i phase} for h and its conjugate for h + nQ/2.  Each
-// thread owns QPT pairs.
-template <class R, bool REDUCE, int QPT>
+// sincos of k s_h . e serves both: with P = sum cos(ph) w and Q = sum sin(ph) w, the leaf
+// sums are P - iQ (direction h, phasor e^{-i ph}) and P + iQ (its antipode).  Each thread
+// owns QPT pairs.
+template <class R, int PH, int QPT>
 __global__ void __launch_bounds__(128) k_pw_forward(PwArgs<R> P, const uint32_t *__restrict__ src,
                                                     const float2 *__restrict__ q, int64_t ny, int nrhs,
                                                     typename PwT<R>::C *__restrict__ ut) {
@@ -681,9 +729,9 @@ __global__ void __launch_bounds__(128) k_pw_forward(PwArgs<R> P, const uint32_t 
     uint32_t lf0 = P.A.box_leaf[b], lf1 = P.A.box_leaf[b + 1];
     for (uint32_t leaf = lf0; leaf < lf1; ++leaf) {
         uint32_t p0 = P.A.leaf_start[leaf], p1 = P.A.leaf_start[leaf + 1];
-        C2 S[QPT], Sb[QPT];
+        C2 Pc[QPT], Qs[QPT];
 #pragma unroll
-        for (int t = 0; t < QPT; ++t) S[t] = Sb[t] = czero(R(0));
+        for (int t = 0; t < QPT; ++t) Pc[t] = Qs[t] = czero(R(0));
         for (uint32_t base = p0; base < p1; base += PW_CHUNK) {
             int cnt = (int)min((uint32_t)PW_CHUNK, p1 - base);
             __syncthreads();
@@ -702,12 +750,11 @@ __global__ void __launch_bounds__(128) k_pw_forward(PwArgs<R> P, const uint32_t 
                 for (int t = 0; t < QPT; ++t) {
                     R ph = fma(kx[t], e.x, fma(ky[t], e.y, kz[t] * e.z));
                     R sn, cs;
-                    phase_sincos<REDUCE>(ph, sn, cs);
-                    // direction h: e^{-i ph} w; antipode h + nQ/2: e^{+i ph} w
-                    S[t].x = fma(cs, (R)w.x, fma(sn, (R)w.y, S[t].x));
-                    S[t].y = fma(cs, (R)w.y, fma(-sn, (R)w.x, S[t].y));
-                    Sb[t].x = fma(cs, (R)w.x, fma(-sn, (R)w.y, Sb[t].x));
-                    Sb[t].y = fma(cs, (R)w.y, fma(sn, (R)w.x, Sb[t].y));
+                    phase_sincos<PH>(ph, sn, cs);
+                    Pc[t].x = fma(cs, (R)w.x, Pc[t].x);
+                    Pc[t].y = fma(cs, (R)w.y, Pc[t].y);
+                    Qs[t].x = fma(sn, (R)w.x, Qs[t].x);
+                    Qs[t].y = fma(sn, (R)w.y, Qs[t].y);
                 }
             }
         }
@@ -715,8 +762,14 @@ __global__ void __launch_bounds__(128) k_pw_forward(PwArgs<R> P, const uint32_t 
         for (int t = 0; t < QPT; ++t) {
             if (!on[t]) continue;
             int hh = h0 + t * blockDim.x;
-            C2 v = cmul(leaf_factor<false>(P, soct, hh), S[t]);
-            C2 vb = cmul(leaf_factor<false>(P, soct, hh + nH), Sb[t]);
+            C2 S, Sb;
+            S.x = Pc[t].x + Qs[t].y;
+            S.y = Pc[t].y - Qs[t].x;
+            Sb.x = Pc[t].x - Qs[t].y;
+            Sb.y = Pc[t].y + Qs[t].x;
+            // the antipode's octant factor is the conjugate of direction h's
+            C2 f = leaf_factor<false>(P, soct, hh);
+            C2 v = cmul(f, S), vb = cmulc(Sb, f);
             acc[t].x += v.x;
             acc[t].y += v.y;
             acb[t].x += vb.x;
@@ -734,8 +787,9 @@ __global__ void __launch_bounds__(128) k_pw_forward(PwArgs<R> P, const uint32_t 
 }
 
 // Diagonal transfer: v~_a(q) = sum_{b adm a} D_t(q) u~_b(q), all right-hand sides of a
-// direction in one thread so that D_t(q) is read once per pair.
-template <class C2, int MR>
+// direction in one thread so that D_t(q) is read once per pair.  COMP: the sum over the
+// admissible sources is compensated (TwoSum).
+template <class C2, int MR, bool COMP>
 __global__ void k_pw_transfer(const uint32_t *__restrict__ tgt, const uint32_t *__restrict__ off,
                               const uint32_t *__restrict__ asrc, const uint32_t *__restrict__ at,
                               const C2 *__restrict__ D, int nQ, int nrhs, const C2 *__restrict__ ut,
@@ -744,9 +798,9 @@ __global__ void k_pw_transfer(const uint32_t *__restrict__ tgt, const uint32_t *
     int q = blockIdx.y * blockDim.x + threadIdx.x;
     if (q >= nQ) return;
     for (int m0 = 0; m0 < nrhs; m0 += MR) {
-        C2 a[MR];
+        C2 a[MR], al[MR];
 #pragma unroll
-        for (int m = 0; m < MR; ++m) a[m].x = a[m].y = 0;
+        for (int m = 0; m < MR; ++m) a[m].x = a[m].y = al[m].x = al[m].y = 0;
         for (uint32_t e = off[x]; e < off[x + 1]; ++e) {
             uint32_t b = asrc[e], t = at[e];
             C2 d = D[(size_t)t * nQ + q];
@@ -755,21 +809,46 @@ __global__ void k_pw_transfer(const uint32_t *__restrict__ tgt, const uint32_t *
             for (int m = 0; m < MR; ++m)
                 if (m0 + m < nrhs) {
                     C2 u = ub[(size_t)m * nQ];
-                    a[m].x = fma(d.x, u.x, fma(-d.y, u.y, a[m].x));
-                    a[m].y = fma(d.x, u.y, fma(d.y, u.x, a[m].y));
+                    if constexpr (COMP) {
+                        two_sum_acc(a[m].x, al[m].x, fma(d.x, u.x, -d.y * u.y));
+                        two_sum_acc(a[m].y, al[m].y, fma(d.x, u.y, d.y * u.x));
+                    } else {
+                        a[m].x = fma(d.x, u.x, fma(-d.y, u.y, a[m].x));
+                        a[m].y = fma(d.x, u.y, fma(d.y, u.x, a[m].y));
+                    }
                 }
         }
 #pragma unroll
         for (int m = 0; m < MR; ++m)
-            if (m0 + m < nrhs) vt[((size_t)tgt[x] * nrhs + m0 + m) * nQ + q] = a[m];
+            if (m0 + m < nrhs) {
+                C2 r = a[m];
+                if constexpr (COMP) {
+                    r.x += al[m].x;
+                    r.y += al[m].y;
+                }
+                vt[((size_t)tgt[x] * nrhs + m0 + m) * nQ + q] = r;
+            }
     }
+}
+
+// Staged backward weights of direction pair h: with W_h = v~_a(h) conj(F_leaf(h)) and
+// W_b = v~_a(h + nQ/2) F_leaf(h), the pair contributes
+// e^{+i ph} W_h + e^{-i ph} W_b = cos(ph) A + sin(ph) B, A = W_h + W_b, B = i (W_h - W_b).
+template <class C2>
+__device__ __forceinline__ void backward_weights(C2 vh, C2 vb, C2 f, C2 &A, C2 &B) {
+    C2 wh = cmulc(vh, f), wb = cmul(vb, f);
+    A.x = wh.x + wb.x;
+    A.y = wh.y + wb.y;
+    B.x = wb.y - wh.y;
+    B.y = wh.x - wb.x;
 }
 
 // Backward transform for one target leaf: v_i += sum_q e^{ik s_q.(x_i - c_leaf)} W(q),
 // W(q) = v~_a(q) prod conj(E) (the leaf's octant path up to its level-l ancestor a).
 // Each thread owns PPT points of the leaf (one shared-memory read of a direction serves
-// PPT phasors); thread groups split the directions when the leaf is small.
-template <class R, bool REDUCE, int PPT>
+// PPT phasors); thread groups split the directions when the leaf is small.  In the
+// compensated mode the sum over directions carries its rounding error (TwoSum).
+template <class R, int PH, int PPT>
 __global__ void __launch_bounds__(128) k_pw_backward(PwArgs<R> P, const uint32_t *__restrict__ box_fine,
                                                      int64_t nbox, const uint32_t *__restrict__ leaf_fine,
                                                      const int *__restrict__ slot,
@@ -777,11 +856,13 @@ __global__ void __launch_bounds__(128) k_pw_backward(PwArgs<R> P, const uint32_t
                                                      double2 *__restrict__ acc) {
     typedef typename PwT<R>::C C2;
     typedef typename PwT<R>::K K4;
+    constexpr bool COMP = PH == PH_ACC && sizeof(R) == 4;
     constexpr int QC = sizeof(R) == 8 ? PW_QC / 4 : PW_QC;  // direction pairs per chunk
     __shared__ K4 sk[QC];
-    __shared__ C2 sw[QC];
-    __shared__ C2 swb[QC];
+    __shared__ C2 sA[QC];
+    __shared__ C2 sB[QC];
     __shared__ C2 red[128 * PPT];
+    __shared__ C2 redl[COMP ? 128 * PPT : 1];
     int leaf = blockIdx.x, m = blockIdx.z;
     // ancestor at level l: last box whose first deep box index <= the leaf's
     uint32_t lf = leaf_fine[leaf];
@@ -808,14 +889,14 @@ __global__ void __launch_bounds__(128) k_pw_backward(PwArgs<R> P, const uint32_t
     for (int pb = 0; pb < np; pb += pr * PPT) {
         decltype(Coord<R>::get(float4(), nullptr, 0u)) e[PPT];
         bool valid[PPT];
-        R sr[PPT], si[PPT];
+        R sr[PPT], si[PPT], lr[PPT], li[PPT];
 #pragma unroll
         for (int u = 0; u < PPT; ++u) {
             int idx = pb + pi + u * pr;
             valid[u] = active && idx < np;
             float4 eh = valid[u] ? P.A.eps[p0 + idx] : make_float4(0.f, 0.f, 0.f, 0.f);
             e[u] = Coord<R>::get(eh, P.eps_lo, valid[u] ? p0 + idx : 0u);
-            sr[u] = si[u] = 0;
+            sr[u] = si[u] = lr[u] = li[u] = 0;
         }
         int nH = P.nQ / 2;
         for (int qb = 0; qb < nH; qb += QC) {
@@ -823,8 +904,7 @@ __global__ void __launch_bounds__(128) k_pw_backward(PwArgs<R> P, const uint32_t
             __syncthreads();
             for (int j = threadIdx.x; j < qc; j += blockDim.x) {
                 sk[j] = P.ks[qb + j];
-                sw[j] = cmul(va[qb + j], leaf_factor<true>(P, soct, qb + j));
-                swb[j] = cmul(va[qb + j + nH], leaf_factor<true>(P, soct, qb + j + nH));
+                backward_weights(va[qb + j], va[qb + j + nH], leaf_factor<false>(P, soct, qb + j), sA[j], sB[j]);
             }
             __syncthreads();
             if (active) {
@@ -832,17 +912,19 @@ __global__ void __launch_bounds__(128) k_pw_backward(PwArgs<R> P, const uint32_t
 #pragma unroll 2
                 for (int j = j0; j < j1; ++j) {
                     K4 k4 = sk[j];
-                    C2 w = sw[j], wb = swb[j];
+                    C2 A = sA[j], B = sB[j];
 #pragma unroll
                     for (int u = 0; u < PPT; ++u) {
                         R ph = fma(k4.x, e[u].x, fma(k4.y, e[u].y, k4.z * e[u].z));
                         R sn, cs;
-                        phase_sincos<REDUCE>(ph, sn, cs);
-                        // e^{+i ph} W_h + e^{-i ph} W_{h + nQ/2}
-                        sr[u] = fma(cs, w.x, fma(-sn, w.y, sr[u]));
-                        si[u] = fma(cs, w.y, fma(sn, w.x, si[u]));
-                        sr[u] = fma(cs, wb.x, fma(sn, wb.y, sr[u]));
-                        si[u] = fma(cs, wb.y, fma(-sn, wb.x, si[u]));
+                        phase_sincos<PH>(ph, sn, cs);
+                        if constexpr (COMP) {
+                            two_sum_acc(sr[u], lr[u], fma(cs, A.x, sn * B.x));
+                            two_sum_acc(si[u], li[u], fma(cs, A.y, sn * B.y));
+                        } else {
+                            sr[u] = fma(cs, A.x, fma(sn, B.x, sr[u]));
+                            si[u] = fma(cs, A.y, fma(sn, B.y, si[u]));
+                        }
                     }
                 }
             }
@@ -852,20 +934,28 @@ __global__ void __launch_bounds__(128) k_pw_backward(PwArgs<R> P, const uint32_t
         for (int u = 0; u < PPT; ++u) {
             red[threadIdx.x * PPT + u].x = sr[u];
             red[threadIdx.x * PPT + u].y = si[u];
+            if constexpr (COMP) {
+                redl[threadIdx.x * PPT + u].x = lr[u];
+                redl[threadIdx.x * PPT + u].y = li[u];
+            }
         }
         __syncthreads();
         if (active && grp == 0) {
 #pragma unroll
             for (int u = 0; u < PPT; ++u) {
                 if (!valid[u]) continue;
-                R tr = 0, ti = 0;
+                double tr = 0, ti = 0;
                 for (int g = 0; g < G; ++g) {
-                    tr += red[(g * pr + pi) * PPT + u].x;
-                    ti += red[(g * pr + pi) * PPT + u].y;
+                    tr += (double)red[(g * pr + pi) * PPT + u].x;
+                    ti += (double)red[(g * pr + pi) * PPT + u].y;
+                    if constexpr (COMP) {
+                        tr += (double)redl[(g * pr + pi) * PPT + u].x;
+                        ti += (double)redl[(g * pr + pi) * PPT + u].y;
+                    }
                 }
                 double2 &dst = acc[(int64_t)m * nx + p0 + pb + pi + u * pr];
-                dst.x += (double)tr;
-                dst.y += (double)ti;
+                dst.x += tr;
+                dst.y += ti;
             }
         }
     }
@@ -874,9 +964,10 @@ __global__ void __launch_bounds__(128) k_pw_backward(PwArgs<R> P, const uint32_t
 // ---- several right-hand sides: each phasor is computed once and applied to MC densities
 
 // Forward transform for MC right-hand sides m0..m0+MC-1.  Thread owns one direction pair
-// (h, h + nQ/2).  The leaf factor is folded into the phasor, e = F_leaf(h) e^{-i k s_h.e}, and
-// the antipode's phasor is conj(e) (the whole of F is conjugate-symmetric under s -> -s).
-template <class R, bool REDUCE, int MC>
+// (h, h + nQ/2).  The leaf factor is folded into the phasor, e = F_leaf(h) e^{-i k s_h.e},
+// and the antipode's phasor is conj(e) (the whole of F is conjugate-symmetric under
+// s -> -s): with P = sum Re(e) w and Q = sum Im(e) w the two sums are P + iQ and P - iQ.
+template <class R, int PH, int MC>
 __global__ void __launch_bounds__(128) k_pw_forward_mr(PwArgs<R> P, const uint32_t *__restrict__ src,
                                                        const float2 *__restrict__ q, int64_t ny, int nrhs,
                                                        typename PwT<R>::C *__restrict__ ut) {
@@ -892,9 +983,9 @@ __global__ void __launch_bounds__(128) k_pw_forward_mr(PwArgs<R> P, const uint32
     bool on = h < nH;
     int hc = on ? h : 0;
     R kx = P.ks[hc].x, ky = P.ks[hc].y, kz = P.ks[hc].z;
-    C2 acc[MC], acb[MC];
+    C2 Pc[MC], Qs[MC];
 #pragma unroll
-    for (int m = 0; m < MC; ++m) acc[m] = acb[m] = czero(R(0));
+    for (int m = 0; m < MC; ++m) Pc[m] = Qs[m] = czero(R(0));
     uint32_t lf0 = P.A.box_leaf[b], lf1 = P.A.box_leaf[b + 1];
     for (uint32_t leaf = lf0; leaf < lf1; ++leaf) {
         uint32_t p0 = P.A.leaf_start[leaf], p1 = P.A.leaf_start[leaf + 1];
@@ -917,16 +1008,16 @@ __global__ void __launch_bounds__(128) k_pw_forward_mr(PwArgs<R> P, const uint32
                 auto e3 = Coord<R>::get(se[j], sl, (uint32_t)j);
                 R ph = fma(kx, e3.x, fma(ky, e3.y, kz * e3.z));
                 R sn, cs;
-                phase_sincos<REDUCE>(ph, sn, cs);
+                phase_sincos<PH>(ph, sn, cs);
                 // e = f e^{-i ph}
                 R er = fma(f.x, cs, f.y * sn), ei = fma(f.y, cs, -f.x * sn);
 #pragma unroll
                 for (int m = 0; m < MC; ++m) {
                     float2 w = sq[j][m];
-                    acc[m].x = fma(er, (R)w.x, fma(-ei, (R)w.y, acc[m].x));
-                    acc[m].y = fma(er, (R)w.y, fma(ei, (R)w.x, acc[m].y));
-                    acb[m].x = fma(er, (R)w.x, fma(ei, (R)w.y, acb[m].x));
-                    acb[m].y = fma(er, (R)w.y, fma(-ei, (R)w.x, acb[m].y));
+                    Pc[m].x = fma(er, (R)w.x, Pc[m].x);
+                    Pc[m].y = fma(er, (R)w.y, Pc[m].y);
+                    Qs[m].x = fma(ei, (R)w.x, Qs[m].x);
+                    Qs[m].y = fma(ei, (R)w.y, Qs[m].y);
                 }
             }
         }
@@ -936,15 +1027,20 @@ __global__ void __launch_bounds__(128) k_pw_forward_mr(PwArgs<R> P, const uint32
         for (int m = 0; m < MC; ++m)
             if (m0 + m < nrhs) {
                 C2 *o = ut + ((size_t)b * nrhs + m0 + m) * P.nQ;
-                o[h] = acc[m];
-                o[h + nH] = acb[m];
+                C2 v, vb;
+                v.x = Pc[m].x - Qs[m].y;
+                v.y = Pc[m].y + Qs[m].x;
+                vb.x = Pc[m].x + Qs[m].y;
+                vb.y = Pc[m].y - Qs[m].x;
+                o[h] = v;
+                o[h + nH] = vb;
             }
 }
 
 // Backward transform for MC right-hand sides: one block per target leaf, one thread per
-// target point (looping over the leaf), direction pairs staged in shared memory with
-// W(h) = v~_a(h) conj(F_leaf(h)) and W(h + nQ/2) = v~_a(h + nQ/2) F_leaf(h).
-template <class R, bool REDUCE, int MC>
+// target point (looping over the leaf), direction pairs staged in shared memory as the
+// (A, B) weights of backward_weights.  Compensated mode: TwoSum over the directions.
+template <class R, int PH, int MC>
 __global__ void __launch_bounds__(128) k_pw_backward_mr(PwArgs<R> P, const uint32_t *__restrict__ box_fine,
                                                         int64_t nbox, const uint32_t *__restrict__ leaf_fine,
                                                         const int *__restrict__ slot,
@@ -952,10 +1048,11 @@ __global__ void __launch_bounds__(128) k_pw_backward_mr(PwArgs<R> P, const uint3
                                                         int64_t nx, double2 *__restrict__ acc) {
     typedef typename PwT<R>::C C2;
     typedef typename PwT<R>::K K4;
+    constexpr bool COMP = PH == PH_ACC && sizeof(R) == 4;
     constexpr int QC = 64;
     __shared__ K4 sk[QC];
-    __shared__ C2 sw[QC][MC];
-    __shared__ C2 swb[QC][MC];
+    __shared__ C2 sA[QC][MC];
+    __shared__ C2 sB[QC][MC];
     __shared__ int soct[PW_MAXD];
     int leaf = blockIdx.x, m0 = blockIdx.z * MC;
     uint32_t lf = leaf_fine[leaf];
@@ -977,25 +1074,21 @@ __global__ void __launch_bounds__(128) k_pw_backward_mr(PwArgs<R> P, const uint3
         bool valid = pb + (int)threadIdx.x < np;
         float4 eh = valid ? P.A.eps[p0 + pb + threadIdx.x] : make_float4(0.f, 0.f, 0.f, 0.f);
         auto e3 = Coord<R>::get(eh, P.eps_lo, valid ? p0 + pb + threadIdx.x : 0u);
-        C2 o[MC];
+        C2 o[MC], ol[MC];
 #pragma unroll
-        for (int m = 0; m < MC; ++m) o[m] = czero(R(0));
+        for (int m = 0; m < MC; ++m) o[m] = ol[m] = czero(R(0));
         for (int qb = 0; qb < nH; qb += QC) {
             int qc = min(QC, nH - qb);
             __syncthreads();
             for (int e = threadIdx.x; e < qc * MC; e += blockDim.x) {
                 int j = e % qc, m = e / qc;
-                C2 fconj = leaf_factor<true>(P, soct, qb + j);
                 if (m0 + m < nrhs) {
                     const C2 *va = vt + ((size_t)a * nrhs + m0 + m) * P.nQ;
-                    sw[j][m] = cmul(va[qb + j], fconj);
-                    C2 fb;
-                    fb.x = fconj.x;
-                    fb.y = -fconj.y;
-                    swb[j][m] = cmul(va[qb + j + nH], fb);
+                    backward_weights(va[qb + j], va[qb + j + nH], leaf_factor<false>(P, soct, qb + j), sA[j][m],
+                                     sB[j][m]);
                 } else {
-                    sw[j][m] = czero(R(0));
-                    swb[j][m] = czero(R(0));
+                    sA[j][m] = czero(R(0));
+                    sB[j][m] = czero(R(0));
                 }
                 if (m == 0) sk[j] = P.ks[qb + j];
             }
@@ -1005,13 +1098,17 @@ __global__ void __launch_bounds__(128) k_pw_backward_mr(PwArgs<R> P, const uint3
                     K4 k4 = sk[j];
                     R ph = fma(k4.x, e3.x, fma(k4.y, e3.y, k4.z * e3.z));
                     R sn, cs;
-                    phase_sincos<REDUCE>(ph, sn, cs);
+                    phase_sincos<PH>(ph, sn, cs);
 #pragma unroll
                     for (int m = 0; m < MC; ++m) {
-                        C2 w = sw[j][m], wb = swb[j][m];
-                        // e^{+i ph} W_h + e^{-i ph} W_{h + nQ/2}
-                        o[m].x = fma(cs, w.x + wb.x, fma(sn, wb.y - w.y, o[m].x));
-                        o[m].y = fma(cs, w.y + wb.y, fma(sn, w.x - wb.x, o[m].y));
+                        C2 A = sA[j][m], B = sB[j][m];
+                        if constexpr (COMP) {
+                            two_sum_acc(o[m].x, ol[m].x, fma(cs, A.x, sn * B.x));
+                            two_sum_acc(o[m].y, ol[m].y, fma(cs, A.y, sn * B.y));
+                        } else {
+                            o[m].x = fma(cs, A.x, fma(sn, B.x, o[m].x));
+                            o[m].y = fma(cs, A.y, fma(sn, B.y, o[m].y));
+                        }
                     }
                 }
             }
@@ -1021,8 +1118,8 @@ __global__ void __launch_bounds__(128) k_pw_backward_mr(PwArgs<R> P, const uint3
             for (int m = 0; m < MC; ++m)
                 if (m0 + m < nrhs) {
                     double2 &dst = acc[(int64_t)(m0 + m) * nx + p0 + pb + threadIdx.x];
-                    dst.x += (double)o[m].x;
-                    dst.y += (double)o[m].y;
+                    dst.x += (double)o[m].x + (COMP ? (double)ol[m].x : 0.0);
+                    dst.y += (double)o[m].y + (COMP ? (double)ol[m].y : 0.0);
                 }
     }
 }
@@ -1036,19 +1133,24 @@ __global__ void k_slot_set(const uint32_t *__restrict__ tgt, int64_t n, int *slo
     if (i < n) slot[tgt[i]] = (int)i;
 }
 
-template <class R>
+template <class R, int PH>
 static void planewave_level(const ffm_plan_s *p, int l, const float2 *q, int nrhs, double2 *acc, Alloc &tmp,
                             cudaStream_t s, const typename PwT<R>::K *ks, const typename PwT<R>::C *D,
                             const typename PwT<R>::C *E) {
     typedef typename PwT<R>::C C2;
+    constexpr bool COMP = PH == PH_ACC;
+    const char *tag = sizeof(R) == 8 ? "f64" : COMP ? "f32c" : "f32";
+    auto name = [&](const char *k) {
+        static thread_local char buf[64];
+        snprintf(buf, sizeof buf, "%s<%s>", k, tag);
+        return (const char *)buf;
+    };
     const FarLevel &F = p->far[l];
     int ls = p->l_stop;
     PwArgs<R> PY{level_args(p, p->by[l], p->by[ls], p->epsY, l), p->epsYlo, ks, E, F.nQ};
     PwArgs<R> PX{level_args(p, p->bx[l], p->bx[ls], p->epsX, l), p->epsXlo, ks, E, F.nQ};
     C2 *ut = tmp.get<C2>((size_t)p->by[l].nb * nrhs * F.nQ);
     C2 *vt = tmp.get<C2>((size_t)p->bx[l].nb * nrhs * F.nQ);
-    // largest leaf-local phase k sqrt(3) d_leaf / 2: reduce to [-pi, pi] only beyond 2 pi
-    bool reduce = p->k * std::sqrt(3.0) * std::ldexp(p->d0, -ls) * 0.5 > 2.0 * PI;
     constexpr int QPT = 4;
     // threads per forward block: 128 unless the ragged tail of the direction range wastes
     // more than 10% of the lanes
@@ -1060,56 +1162,51 @@ static void planewave_level(const ffm_plan_s *p, int l, const float2 *q, int nrh
     bool multi = nrhs > 1;
     if (multi) {
         dim3 gm((unsigned)F.n_src, cdiv(nH, 128), cdiv(nrhs, MC));
-        if (reduce)
-            FFM_LAUNCH_NAMED(sizeof(R) == 8 ? "k_pw_forward_mr<f64>" : "k_pw_forward_mr<f32>", (k_pw_forward_mr<R, true, MC>), gm, 128, 0, s, PY, F.src, q, p->ny, nrhs, ut);
-        else
-            FFM_LAUNCH_NAMED(sizeof(R) == 8 ? "k_pw_forward_mr<f64>" : "k_pw_forward_mr<f32>", (k_pw_forward_mr<R, false, MC>), gm, 128, 0, s, PY, F.src, q, p->ny, nrhs, ut);
+        FFM_LAUNCH_NAMED(name("k_pw_forward_mr"), (k_pw_forward_mr<R, PH, MC>), gm, 128, 0, s, PY, F.src, q, p->ny,
+                         nrhs, ut);
     } else {
         dim3 gf((unsigned)F.n_src, cdiv(nH, tb * QPT), 1);
-        if (reduce)
-            FFM_LAUNCH_NAMED(sizeof(R) == 8 ? "k_pw_forward<f64>" : "k_pw_forward<f32>", (k_pw_forward<R, true, QPT>), gf, tb, 0, s, PY, F.src, q, p->ny, nrhs, ut);
-        else
-            FFM_LAUNCH_NAMED(sizeof(R) == 8 ? "k_pw_forward<f64>" : "k_pw_forward<f32>", (k_pw_forward<R, false, QPT>), gf, tb, 0, s, PY, F.src, q, p->ny, nrhs, ut);
+        FFM_LAUNCH_NAMED(name("k_pw_forward"), (k_pw_forward<R, PH, QPT>), gf, tb, 0, s, PY, F.src, q, p->ny, nrhs,
+                         ut);
     }
     dim3 gt((unsigned)F.n_tgt, cdiv(F.nQ, 128), 1);
     if (nrhs == 1)
-        FFM_LAUNCH_NAMED(sizeof(R) == 8 ? "k_pw_transfer<f64>" : "k_pw_transfer<f32>", (k_pw_transfer<C2, 1>), gt, 128,
-                         0, s, F.tgt, F.adm_off, F.adm_src, F.adm_t, D, F.nQ, nrhs, (const C2 *)ut, vt);
+        FFM_LAUNCH_NAMED(name("k_pw_transfer"), (k_pw_transfer<C2, 1, COMP>), gt, 128, 0, s, F.tgt, F.adm_off,
+                         F.adm_src, F.adm_t, D, F.nQ, nrhs, (const C2 *)ut, vt);
     else
-        FFM_LAUNCH_NAMED(sizeof(R) == 8 ? "k_pw_transfer<f64>" : "k_pw_transfer<f32>", (k_pw_transfer<C2, 8>), gt, 128,
-                         0, s, F.tgt, F.adm_off, F.adm_src, F.adm_t, D, F.nQ, nrhs, (const C2 *)ut, vt);
+        FFM_LAUNCH_NAMED(name("k_pw_transfer"), (k_pw_transfer<C2, 8, COMP>), gt, 128, 0, s, F.tgt, F.adm_off,
+                         F.adm_src, F.adm_t, D, F.nQ, nrhs, (const C2 *)ut, vt);
     int64_t nbx = p->bx[l].nb;
     int *slot = tmp.get<int>(nbx);
     FFM_LAUNCH(k_slot_init, cdiv(nbx, 256), 256, 0, s, slot, nbx);
     FFM_LAUNCH(k_slot_set, cdiv(F.n_tgt, 256), 256, 0, s, F.tgt, F.n_tgt, slot);
     if (multi) {
         dim3 gm((unsigned)p->bx[ls].nb, 1, cdiv(nrhs, MC));
-        if (reduce)
-            FFM_LAUNCH_NAMED(sizeof(R) == 8 ? "k_pw_backward_mr<f64>" : "k_pw_backward_mr<f32>", (k_pw_backward_mr<R, true, MC>), gm, 128, 0, s, PX, p->bx[l].fine, nbx, p->bx[ls].fine, slot,
-                       (const C2 *)vt, nrhs, p->nx, acc);
-        else
-            FFM_LAUNCH_NAMED(sizeof(R) == 8 ? "k_pw_backward_mr<f64>" : "k_pw_backward_mr<f32>", (k_pw_backward_mr<R, false, MC>), gm, 128, 0, s, PX, p->bx[l].fine, nbx, p->bx[ls].fine, slot,
-                       (const C2 *)vt, nrhs, p->nx, acc);
+        FFM_LAUNCH_NAMED(name("k_pw_backward_mr"), (k_pw_backward_mr<R, PH, MC>), gm, 128, 0, s, PX, p->bx[l].fine,
+                         nbx, p->bx[ls].fine, slot, (const C2 *)vt, nrhs, p->nx, acc);
         return;
     }
     dim3 gb((unsigned)p->bx[ls].nb, 1, 1);
     constexpr int PPT = 4;  // target points per thread
-    if (reduce)
-        FFM_LAUNCH_NAMED(sizeof(R) == 8 ? "k_pw_backward<f64>" : "k_pw_backward<f32>", (k_pw_backward<R, true, PPT>), gb, 128, 0, s, PX, p->bx[l].fine, nbx, p->bx[ls].fine, slot,
-                   (const C2 *)vt, nrhs, p->nx, acc);
-    else
-        FFM_LAUNCH_NAMED(sizeof(R) == 8 ? "k_pw_backward<f64>" : "k_pw_backward<f32>", (k_pw_backward<R, false, PPT>), gb, 128, 0, s, PX, p->bx[l].fine, nbx, p->bx[ls].fine, slot,
-                   (const C2 *)vt, nrhs, p->nx, acc);
+    FFM_LAUNCH_NAMED(name("k_pw_backward"), (k_pw_backward<R, PH, PPT>), gb, 128, 0, s, PX, p->bx[l].fine, nbx,
+                     p->bx[ls].fine, slot, (const C2 *)vt, nrhs, p->nx, acc);
 }
 
 void far_planewave(const ffm_plan_s *p, int l, const float2 *q, int nrhs, double2 *acc, Alloc &tmp,
                    cudaStream_t s) {
     const FarLevel &F = p->far[l];
     if (p->l_stop - l > PW_MAXD) fail(FFM_EUNSUPPORTED, "more than 16 levels between a plane-wave level and the leaves");
-    if (F.pw64)
-        planewave_level<double>(p, l, q, nrhs, acc, tmp, s, F.ksd, F.Dd, F.Ed);
+    // largest leaf-local phase k sqrt(3) d_leaf / 2: the hardware sincos gets the phase
+    // reduced to [-pi, pi] only beyond 2 pi
+    bool reduce = p->k * std::sqrt(3.0) * std::ldexp(p->d0, -p->l_stop) * 0.5 > 2.0 * PI;
+    if (F.prec == FFM_PREC_F64)
+        planewave_level<double, PH_MUFU>(p, l, q, nrhs, acc, tmp, s, F.ksd, F.Dd, F.Ed);
+    else if (F.prec == FFM_PREC_F32C)
+        planewave_level<float, PH_ACC>(p, l, q, nrhs, acc, tmp, s, F.ks, F.D, F.E);
+    else if (reduce)
+        planewave_level<float, PH_MUFU_RED>(p, l, q, nrhs, acc, tmp, s, F.ks, F.D, F.E);
     else
-        planewave_level<float>(p, l, q, nrhs, acc, tmp, s, F.ks, F.D, F.E);
+        planewave_level<float, PH_MUFU>(p, l, q, nrhs, acc, tmp, s, F.ks, F.D, F.E);
 }
 
 }  // namespace ffm

@@ -124,9 +124,9 @@ struct FarLevel {
     int64_t tc_tiles = 0;           // 128-pair tiles for the tensor-core transfer
     uint32_t *tc_tile_t = nullptr;
     uint32_t *tc_tile_p0 = nullptr;
-    // plane waves: FP32 tables, or FP64 tables when pw64 (large cancellation in the
-    // quadrature sum, see tables.cu)
-    int pw64 = 0;
+    // plane waves: arithmetic (FFM_PREC_F32 / _F32C with FP32 tables, FFM_PREC_F64 with
+    // FP64 tables), chosen from the cancellation of the quadrature sum (tables.cu)
+    int prec = 0;
     double cancel = 0;              // sum_q |D(q)| / |sum_q D(q)| for the closest translation
     float4 *ks = nullptr;           // nQ: k * s_q (x, y, z, 0)
     float2 *D = nullptr;            // n_trans * nQ
@@ -145,6 +145,7 @@ struct ffm_plan_s {
     int n_leaf = 64, l_cap = ffm::LMAX;
     double kappa = 2.0;
     int r1_override = 0;
+    int precision = 0;  // ffm_precision for the plane-wave levels, 0 = by cancellation
     double d0 = 1, oX[3] = {0, 0, 0}, oY[3] = {0, 0, 0}, sigma[3] = {0, 0, 0};
     int l_stop = 0, root_adm = 0;
     cudaStream_t stream = nullptr;

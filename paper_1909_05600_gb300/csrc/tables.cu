@@ -328,9 +328,11 @@ void build_tables(ffm_plan_s *p, int l, TableJob &tj) {
         }
     }
     // Cancellation of the quadrature sum for the closest translation:
-    // C = sum_q |D(q)| / |sum_q D(q)|.  FP32 loses about C * 2.6e-8 relative on a pair at
-    // that distance, so levels with C > 250 (low k d_l, where the Hankel terms with
-    // p > k |r0| grow) run their plane-wave kernels in FP64.
+    // C = sum_q |D(q)| / |sum_q D(q)|, large at low k d_l where the Hankel terms with
+    // p > k |r0| grow.  Rounding errors of the FP32 kernels are amplified by about C:
+    // measured on ill-conditioned cube surfaces, the result moves by up to ~2.3e-9 C with
+    // the hardware sincos and ~1.3e-9 C with the compensated kernels.  The level runs
+    // FP32 for C <= 250, compensated FP32 for C <= 4e3 (both below 6e-6), FP64 above.
     F.cancel = 0.0;
     if (L > 1.1 * p->k * rhat[tmin].w) {
         double sa = 0.0, ar = 0.0, ai = 0.0;
@@ -353,8 +355,12 @@ void build_tables(ffm_plan_s *p, int l, TableJob &tj) {
         }
         F.cancel = sa / std::sqrt(ar * ar + ai * ai);
     }
-    F.pw64 = F.cancel > 250.0 ? 1 : 0;
-    p->info.pw64[l] = F.pw64;
+    if (p->precision != FFM_PREC_AUTO)
+        F.prec = p->precision;
+    else
+        F.prec = F.cancel <= 250.0 ? FFM_PREC_F32 : F.cancel <= 4e3 ? FFM_PREC_F32C : FFM_PREC_F64;
+    p->info.pw_prec[l] = F.prec;
+    bool dbl = F.prec == FFM_PREC_F64;
     p->info.cancel[l] = F.cancel;
     std::vector<float4> coef((size_t)nt * (L + 1));
     for (size_t i = 0; i < coef.size(); ++i) {
@@ -388,7 +394,7 @@ void build_tables(ffm_plan_s *p, int l, TableJob &tj) {
     int npairs = (int)pairs.size();
     dim3 g1(cdiv(nH, 256), npairs);
     size_t sm1 = sizeof(float4) * (L + 1) + sizeof(float2) * L;
-    if (F.pw64) {
+    if (dbl) {
         F.ksd = p->mem.get<D4>(nQ);
         F.Dd = p->mem.get<double2>((size_t)nt * nQ);
     } else {
@@ -409,7 +415,7 @@ void build_tables(ffm_plan_s *p, int l, TableJob &tj) {
     FFM_CUDA(cudaMemcpyAsync(d_beta, keep.hold(std::move(beta)), sizeof(float2) * nbeta, cudaMemcpyHostToDevice, s));
     FFM_CUDA(cudaMemcpyAsync(d_rhat, keep.hold(std::move(rhat)), sizeof(D4) * nt, cudaMemcpyHostToDevice, s));
     FFM_CUDA(cudaMemcpyAsync(d_pairs, keep.hold(std::move(pairs)), sizeof(int2) * npairs, cudaMemcpyHostToDevice, s));
-    if (F.pw64) {
+    if (dbl) {
         std::vector<D4> ks(nQ);
         for (int q = 0; q < nQ; ++q) ks[q] = D4{p->k * sw[q].x, p->k * sw[q].y, p->k * sw[q].z, 0.0};
         FFM_CUDA(cudaMemcpyAsync(F.ksd, keep.hold(std::move(ks)), sizeof(D4) * nQ, cudaMemcpyHostToDevice, s));
@@ -430,11 +436,11 @@ void build_octants(ffm_plan_s *p, int l, TableJob &tj) {
     int nQ = F.nQ;
     dim3 g2(cdiv(nQ, 128), ndepth, 8);
     double half = std::ldexp(p->d0, -(l + 1));
-    if (F.pw64)
+    if (F.prec == FFM_PREC_F64)
         F.Ed = p->mem.get<double2>((size_t)ndepth * 8 * nQ);
     else
         F.E = p->mem.get<float2>((size_t)ndepth * 8 * nQ);
-    if (F.pw64)
+    if (F.prec == FFM_PREC_F64)
         FFM_LAUNCH(k_pw_octants<double2>, g2, 128, 0, tj.side, tj.d_sw[l], nQ, p->k, half, ndepth, F.Ed);
     else
         FFM_LAUNCH(k_pw_octants<float2>, g2, 128, 0, tj.side, tj.d_sw[l], nQ, p->k, half, ndepth, F.E);

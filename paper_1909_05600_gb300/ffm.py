@@ -22,6 +22,8 @@ LIB_PATH = os.path.join(HERE, "libffm_gb300.so")
 
 LAPLACE, HELMHOLTZ = 0, 1
 F32, F64, C64, C128 = 0, 1, 2, 3
+# plane-wave level arithmetic (ffm_precision)
+PREC_AUTO, PREC_F32, PREC_F32C, PREC_F64 = 0, 1, 2, 3
 EXPORT_PERM_X, EXPORT_PERM_Y, EXPORT_ADM, EXPORT_NEAR = 0, 1, 2, 3
 STATUS = {0: "FFM_OK", 1: "FFM_EINVAL", 2: "FFM_ENOMEM", 3: "FFM_ECUDA", 4: "FFM_ETIMEOUT", 5: "FFM_EUNSUPPORTED"}
 
@@ -48,7 +50,7 @@ class Info(C.Structure):
                 ("n_adm", C.c_int64 * 22), ("n_near", C.c_int64 * 22), ("n_trans", C.c_int64 * 22),
                 ("mode", C.c_int * 22), ("r1", C.c_int * 22), ("L", C.c_int * 22), ("nQ", C.c_int * 22),
                 ("nx", C.c_int64), ("ny", C.c_int64), ("src_points", C.c_int64 * 22),
-                ("tgt_points", C.c_int64 * 22), ("p2p_pairs", C.c_int64), ("pw64", C.c_int * 22),
+                ("tgt_points", C.c_int64 * 22), ("p2p_pairs", C.c_int64), ("pw_prec", C.c_int * 22),
                 ("cancel", C.c_double * 22), ("device_errors", C.c_int)]
 
     def as_dict(self):
@@ -56,7 +58,7 @@ class Info(C.Structure):
              "oY": list(self.oY), "nx": self.nx, "ny": self.ny, "p2p_pairs": self.p2p_pairs,
              "device_errors": self.device_errors}
         for f in ("nboxX", "nboxY", "n_adm", "n_near", "n_trans", "mode", "r1", "L", "nQ", "src_points",
-                  "tgt_points", "pw64", "cancel"):
+                  "tgt_points", "pw_prec", "cancel"):
             d[f] = list(getattr(self, f))
         return d
 
@@ -182,10 +184,10 @@ class Plan:
     """
 
     def __init__(self, X, Y, kernel, k=0.0, eps=1e-3, weights=None, stream=None, n_leaf=0, l_cap=0,
-                 kappa_switch=0.0, r1_override=0):
+                 kappa_switch=0.0, r1_override=0, precision=PREC_AUTO):
         self._h = None
         self._keep = (X, Y, weights)
-        o = Opts(n_leaf, l_cap, float(kappa_switch), r1_override, 0, None, F64)
+        o = Opts(n_leaf, l_cap, float(kappa_switch), r1_override, int(precision), None, F64)
         if weights is not None:
             o.weights = _ptr(weights)
             o.weights_dtype = _dtype_code(weights)
