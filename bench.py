@@ -42,7 +42,7 @@ def parse():
     ap.add_argument("--workload", default="helmholtz_sphere_1M",
                     choices=["helmholtz_sphere_1M", "laplace_sphere_20k", "helmholtz_cube_200k_64rhs",
                              "laplace_clustered"])
-    ap.add_argument("--n", type=int, default=0, help="points per set for the clustered workload")
+    ap.add_argument("--n", type=int, default=0, help="points per set (0: the workload's own size)")
     ap.add_argument("--serving", action="store_true",
                     help="serving stream: Poisson arrivals of mixed requests, p50/p99 latency and throughput")
     ap.add_argument("--requests", type=int, default=500)
@@ -50,18 +50,22 @@ def parse():
     ap.add_argument("--cpu-targets", type=int, default=4096)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="default kernel variants instead of ffm_autotune's picks")
     return ap.parse_args()
 
 
 def make_problem(name, seed, n=0):
+    """The named workload; n > 0 overrides its point count (same generator, k kept at 10
+    points per wavelength), for profiling runs on smaller cases."""
     from paper_1909_05600_gb300 import workloads as W
     if name == "helmholtz_sphere_1M":
-        return W.helmholtz_sphere(1_000_000, seed=seed)
+        return W.helmholtz_sphere(n or 1_000_000, seed=seed)
     if name == "helmholtz_cube_200k_64rhs":
-        return W.helmholtz_cube_multirhs(200_000, nrhs=64, seed=seed, eps=1e-4)
+        return W.helmholtz_cube_multirhs(n or 200_000, nrhs=64, seed=seed, eps=1e-4)
     if name == "laplace_clustered":
         return W.laplace_clustered(n or 100_000_000, seed=seed)
-    return W.laplace_sphere(20000, seed=seed)
+    return W.laplace_sphere(n or 20000, seed=seed)
 
 
 def peaks():
@@ -129,12 +133,44 @@ def cpu_direct_sample(prob, ntargets, seed=12345):
     from oracle import oracle as O
     from paper_1909_05600_gb300 import workloads as W
     t = W.sample_targets(prob.X.shape[0], ntargets, seed)
-    u0 = prob.u[:, 0] if prob.u.ndim == 2 else prob.u
-    u = u0.astype(np.complex128) if np.iscomplexobj(u0) else u0.astype(np.float64)
+    u = prob.u.astype(np.complex128) if np.iscomplexobj(prob.u) else prob.u.astype(np.float64)
     t0 = time.perf_counter()
-    ref = O.direct(prob.X, prob.Y, u, prob.kind, prob.k, w=prob.w, targets=t)[:, 0]
+    ref = O.direct(prob.X, prob.Y, u, prob.kind, prob.k, w=prob.w, targets=t)  # (targets, nrhs)
     dt = time.perf_counter() - t0
     return t, ref, dt, O.nthreads()
+
+
+def reference_targets(prob):
+    """Targets per timed oracle step: about 1.2e9 target-source pairs, at most all targets."""
+    return int(min(prob.X.shape[0], max(64, 1.2e9 // prob.Y.shape[0])))
+
+
+def repeat_applies(ffm, torch, prob, X, Y, w, u, flush, stream, reps, tune_cache=None):
+    """Repeated products with one resident plan (an iterative solver's use): eager
+    ffm_apply calls against launches of the same apply captured as a CUDA graph.  Device
+    time per product with an L2 flush before each one (outside its events)."""
+    out = torch.empty_like(u)
+    with ffm.Plan(X, Y, prob.kind, prob.k, prob.eps, weights=w, autotune_cache=tune_cache) as p:
+        def run(fn):
+            fn()
+            torch.cuda.synchronize()
+            tot = 0.0
+            for _ in range(reps):
+                flush.zero_()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                fn()
+                e1.record(stream)
+                e1.synchronize()
+                tot += e0.elapsed_time(e1)
+            return reps / (tot * 1e-3)
+        eager = run(lambda: p.apply(u, out=out))
+        with p.graph(u, out) as g:
+            graph = run(lambda: g.launch())
+            kernels = g.kernels
+    return {"eager_applies_per_s": eager, "graph_applies_per_s": graph, "kernels_per_apply": kernels,
+            "reps": reps, "note": "plan built once; ffm_apply vs one CUDA graph launch per product"}
 
 
 def run_reference(args, rank):
@@ -144,7 +180,7 @@ def run_reference(args, rank):
         return
     prob = make_problem(args.workload, 1, args.n)
     n = prob.X.shape[0]
-    ns = min(n, 1024 if args.workload == "helmholtz_sphere_1M" else n)
+    ns = reference_targets(prob)
     for _ in range(args.warmup):
         cpu_direct_sample(prob, ns)
     dts = []
@@ -309,10 +345,25 @@ def main():
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
 
+    # kernel variants: ffm_autotune times them once on a plan of this workload, before the
+    # timed region; every plan below takes the picks from the cache file (no timing)
+    tune_cache, tune = None, None
+    if not args.no_autotune:
+        import tempfile
+        fd, tune_cache = tempfile.mkstemp(prefix="ffm_tune_", suffix=".txt")
+        os.close(fd)
+        t0 = time.perf_counter()
+        with ffm.Plan(X, Y, prob.kind, prob.k, prob.eps, weights=w) as pt:
+            ti = pt.autotune(nrhs=nrhs, cache_path=tune_cache)
+        tune = {"seconds": time.perf_counter() - t0, "p2p_tchunk": ti["p2p_tchunk"], "p2p_smax": ti["p2p_smax"],
+                "tune_tc": [ti["tune_tc"][l] for l in range(ti["l_stop"] + 1)],
+                "tune_pw": [ti["tune_pw"][l] for l in range(ti["l_stop"] + 1)],
+                "note": "picked once before the timed region; each timed plan reads them from the cache"}
+
     def step(events=None):
         if events:
             events[0].record(stream)
-        p = ffm.Plan(X, Y, prob.kind, prob.k, prob.eps, weights=w)
+        p = ffm.Plan(X, Y, prob.kind, prob.k, prob.eps, weights=w, autotune_cache=tune_cache)
         if events:
             events[1].record(stream)
         v = p.apply(u)
@@ -326,7 +377,7 @@ def main():
         flush.zero_()
         v, _ = step()
     torch.cuda.synchronize()
-    with ffm.Plan(X, Y, prob.kind, prob.k, prob.eps, weights=w) as p0:
+    with ffm.Plan(X, Y, prob.kind, prob.k, prob.eps, weights=w, autotune_cache=tune_cache) as p0:
         info = p0.info()
 
     def timed():
@@ -354,6 +405,7 @@ def main():
         return vlast, t_plan, t_apply, clk, launches, ffm.profile_read()
 
     vlast, t_plan, t_apply, clk, launches, prof = timed()
+    rep = repeat_applies(ffm, torch, prob, X, Y, w, u, flush, stream, max(3, args.steps), tune_cache)
     note = None
     if rejected(clk):
         note = "first timed run rejected (clock reasons %s); re-measured" % clk.get("reasons")
@@ -379,7 +431,8 @@ def main():
         for i in range(ke + 1):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            with ffm.Plan(Xh, Yh, prob.kind, prob.k, prob.eps, weights=wh, stream=stream) as ph:
+            with ffm.Plan(Xh, Yh, prob.kind, prob.k, prob.eps, weights=wh, stream=stream,
+                          autotune_cache=tune_cache) as ph:
                 ph.apply(uh, out=vh, stream=stream)
             torch.cuda.synchronize()
             if i:
@@ -397,12 +450,13 @@ def main():
         if vg.ndim == 2:
             vg = vg[0]
         t, ref, dt, cores = cpu_direct_sample(prob, args.cpu_targets)
+        ref = ref[:, 0]
         err = float(np.linalg.norm(vg[t] - ref) / np.linalg.norm(ref))
-        cpu = {"value": 1.0 / (dt * prob.X.shape[0] / len(t) * nrhs), "unit": "applies/s", "cores": cores,
+        cpu = {"value": 1.0 / (dt * prob.X.shape[0] / len(t)), "unit": "applies/s", "cores": cores,
                "kind": "oracle",
-               "sample": "FP64 direct sum over all %d sources for %d seeded targets and 1 of %d right-hand sides "
-                         "(%.1f s), scaled to %d targets and %d right-hand sides"
-                         % (prob.Y.shape[0], len(t), nrhs, dt, prob.X.shape[0], nrhs)}
+               "sample": "FP64 direct sum over all %d sources for %d seeded targets and all %d right-hand sides "
+                         "(%.1f s), scaled to %d targets"
+                         % (prob.Y.shape[0], len(t), nrhs, dt, prob.X.shape[0])}
 
     if rank == 0:
         rl = roofline(prof, info, args.steps, clk, pk, pk_kind)
@@ -420,6 +474,7 @@ def main():
             "mpoints_per_s": n * value / 1e6, "rhs_per_s": value * nrhs,
             "t_plan_ms": t_plan / args.steps, "t_apply_ms": t_apply / args.steps,
             "apply_only_per_s": args.steps * world / (t_apply * 1e-3),
+            "repeat_apply": rep, "autotune": tune,
             "err_vs_fp64_direct": err, "err_targets": args.cpu_targets if err is not None else None,
             "roofline": rl, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": launches,
             "kernels": kernels,
@@ -430,6 +485,8 @@ def main():
         if note:
             line["note"] = note
         print(json.dumps(line), flush=True)
+    if tune_cache:
+        os.remove(tune_cache)
     if dist:
         dist.barrier()
         dist.destroy_process_group()

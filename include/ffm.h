@@ -88,6 +88,9 @@ typedef struct {
                              per level from the quadrature's cancellation ratio */
     const void *weights;  /* quadrature weights w_j (N_Y entries), host or device; NULL -> 1 */
     ffm_dtype weights_dtype; /* FFM_F32 or FFM_F64 */
+    const char *autotune_cache; /* NULL, or a file written by ffm_autotune: the plan takes the
+                                   picks stored for its sizes (single right-hand side picks;
+                                   several-RHS picks from 64, else 8 RHS), timing nothing */
 } ffm_opts;
 
 /* Build a plan for targets X (nx points) and sources Y (ny points) (Sec. 2.2.1-2.2.4):
@@ -149,6 +152,12 @@ typedef struct {
     int pw_prec[22];           /* plane-wave levels: the ffm_precision they run in (0 otherwise) */
     double cancel[22];         /* cancellation ratio of the level's quadrature sum (closest pair) */
     int device_errors;         /* nonzero if a bounded device-side wait gave up (results invalid) */
+    /* kernel variants in use (ffm_autotune's picks, else the defaults) */
+    int autotuned;             /* 1 after ffm_autotune */
+    int p2p_tchunk, p2p_smax;  /* near-field work items: targets, source points per item */
+    int tune_tc[22];           /* Lagrange levels: transfer on tensor cores (1) or CUDA cores (0) */
+    int tune_pw[22][3];        /* plane-wave levels: direction pairs per thread (forward), points
+                                  per thread (backward), right-hand sides per thread (several) */
 } ffm_info;
 
 ffm_status ffm_plan_info(const ffm_plan_t *plan, ffm_info *info);
@@ -162,7 +171,38 @@ ffm_status ffm_plan_info(const ffm_plan_t *plan, ffm_info *info);
 enum { FFM_EXPORT_PERM_X = 0, FFM_EXPORT_PERM_Y = 1, FFM_EXPORT_ADM = 2, FFM_EXPORT_NEAR = 3 };
 ffm_status ffm_plan_export(const ffm_plan_t *plan, int what, int level, void *host_out, int64_t *count);
 
-/* Number of kernels this library has launched in this process (all threads). */
+/* Pick kernel variants for this plan by timing them on its own data, for products with
+ * `nrhs` right-hand sides: the near-field work-item shape (targets and source points per
+ * item, which balance clustered leaves), the Lagrange transfer GEMM (tcgen05 tiles of 128
+ * box pairs, or CUDA-core tiles of 32), and per plane-wave level the direction pairs and
+ * points per thread of the transforms (or right-hand sides per thread).  Costs a few
+ * applies of GPU time; results change only by rounding.
+ *   cache_path : NULL, or a text file of earlier picks keyed by device, kernel, level
+ *                sizes and nrhs; keys found there are not timed again, new picks are
+ *                appended (the file is created if missing).
+ *   stream     : cudaStream_t for the timing runs; the call returns when they are done.
+ * Errors: FFM_EINVAL, FFM_ENOMEM, FFM_ECUDA. */
+ffm_status ffm_autotune(ffm_plan_t *plan, int nrhs, const char *cache_path, void *stream);
+
+/* A captured apply, for iterative solvers that multiply by the same matrix many times
+ * with the same buffers (Sec. 4.3's BEM solves: about ten products per GMRES iteration).
+ * ffm_graph_create records one ffm_apply(plan, u, udt, nrhs, v) into a CUDA graph and
+ * instantiates it; nothing runs.  Each ffm_graph_launch then recomputes v from the current
+ * contents of u with one graph launch instead of one launch per kernel (a few hundred for
+ * a million-point Helmholtz product), its temporaries being graph-owned allocations.
+ *   u, v : DEVICE buffers as for ffm_apply; the graph keeps their addresses, so they must
+ *          stay allocated (and the plan alive) until ffm_graph_destroy.
+ *   stream (launch): cudaStream_t; the call only enqueues work.
+ * Errors: FFM_EINVAL (NULL or host buffers, bad dtype or nrhs), FFM_ENOMEM, FFM_ECUDA. */
+typedef struct ffm_graph_s ffm_graph_t;
+ffm_status ffm_graph_create(ffm_plan_t *plan, const void *u, ffm_dtype udt, int nrhs, void *v, ffm_graph_t **out);
+ffm_status ffm_graph_launch(ffm_graph_t *graph, void *stream);
+/* Kernels one launch of the graph runs (they count towards ffm_launch_count). */
+int64_t ffm_graph_kernels(const ffm_graph_t *graph);
+void ffm_graph_destroy(ffm_graph_t *graph);
+
+/* Number of kernels this library has launched in this process (all threads); a graph
+ * launch adds the kernels it contains. */
 uint64_t ffm_launch_count(void);
 
 /* Per-kernel device timing, for measurement.  While enabled, each kernel launch of this

@@ -108,16 +108,24 @@ struct LevelArgs {
 
 constexpr int LAG_T = 256;
 
-template <bool CPLX>
-__global__ void __launch_bounds__(LAG_T) k_lag_anterp(LevelArgs A, const uint32_t *__restrict__ src, Cheb cb,
+// Source step of a Lagrange level (L_Y u of eq. 8): u~_b(abc) = sum_{j in b} L_a(x_j) L_b(y_j) L_c(z_j) q_j.
+// One block per chunk of at most LAG_CHUNK points of a box; each thread owns up to two
+// control nodes.  A box split into several chunks adds its partial sums with atomics
+// (u~ is zeroed first); a single-chunk box stores them.
+template <bool CPLX, int R1>
+__global__ void __launch_bounds__(LAG_T) k_lag_anterp(LevelArgs A, const uint2 *__restrict__ chunks, Cheb cb,
                                                       const typename QT<CPLX>::T *__restrict__ q, int64_t ny,
                                                       int nrhs, typename QT<CPLX>::T *__restrict__ ut) {
     typedef typename QT<CPLX>::T Q;
-    __shared__ float sl[LAG_T][3 * R1MAX + 1];
-    __shared__ Q sq[LAG_T];
-    int b = src[blockIdx.x], m = blockIdx.y;
-    int r1 = cb.r1, r = r1 * r1 * r1;
-    uint32_t s0 = A.box_start[b], s1 = A.box_start[b + 1];
+    constexpr int r = R1 * R1 * R1;
+    // per staged point: x weights (times q for real densities), y and z weights
+    __shared__ float sl[LAG_T][3 * R1 + 1];
+    __shared__ Q sq[CPLX ? LAG_T : 1];
+    uint2 ck = chunks[blockIdx.x];
+    int b = (int)ck.x, m = blockIdx.y;
+    uint32_t s0 = ck.y, bend = A.box_start[b + 1];
+    uint32_t s1 = min(bend, s0 + (uint32_t)LAG_CHUNK);
+    bool sole = s0 == A.box_start[b] && s1 == bend;
     int4 gb = A.box_g[b];
     float accr[2] = {0.f, 0.f}, acci[2] = {0.f, 0.f};
     for (uint32_t base = s0; base < s1; base += LAG_T) {
@@ -126,25 +134,37 @@ __global__ void __launch_bounds__(LAG_T) k_lag_anterp(LevelArgs A, const uint32_
             float4 e = A.eps[j];
             int4 gl = A.leaf_g[__float_as_uint(e.w)];
             float3 o = leaf_offset(gl, gb, A.shift, A.dls);
-            lag1d(cb, (o.x + e.x) * A.inv_half_dl, &sl[threadIdx.x][0]);
-            lag1d(cb, (o.y + e.y) * A.inv_half_dl, &sl[threadIdx.x][R1MAX]);
-            lag1d(cb, (o.z + e.z) * A.inv_half_dl, &sl[threadIdx.x][2 * R1MAX]);
-            sq[threadIdx.x] = q[(int64_t)m * ny + j];
+            float lx[R1MAX], ly[R1MAX], lz[R1MAX];
+            lag1d(cb, (o.x + e.x) * A.inv_half_dl, lx);
+            lag1d(cb, (o.y + e.y) * A.inv_half_dl, ly);
+            lag1d(cb, (o.z + e.z) * A.inv_half_dl, lz);
+            Q w = q[(int64_t)m * ny + j];
+#pragma unroll
+            for (int a = 0; a < R1; ++a) {
+                if constexpr (CPLX)
+                    sl[threadIdx.x][a] = lx[a];
+                else
+                    sl[threadIdx.x][a] = lx[a] * w;
+                sl[threadIdx.x][R1 + a] = ly[a];
+                sl[threadIdx.x][2 * R1 + a] = lz[a];
+            }
+            if constexpr (CPLX) sq[threadIdx.x] = w;
         }
         __syncthreads();
-        int cnt = min((uint32_t)LAG_T, s1 - base);
+        int cnt = (int)min((uint32_t)LAG_T, s1 - base);
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             int a = threadIdx.x + h * LAG_T;
             if (a < r) {
-                int ia = a / (r1 * r1), ib = (a / r1) % r1, ic = a % r1;
+                int ia = a / (R1 * R1), ib = (a / R1) % R1, ic = a % R1;
                 for (int jj = 0; jj < cnt; ++jj) {
-                    float L = sl[jj][ia] * sl[jj][R1MAX + ib] * sl[jj][2 * R1MAX + ic];
+                    float L = sl[jj][ia] * sl[jj][R1 + ib];
                     if constexpr (CPLX) {
+                        L *= sl[jj][2 * R1 + ic];
                         accr[h] = fmaf(L, sq[jj].x, accr[h]);
                         acci[h] = fmaf(L, sq[jj].y, acci[h]);
                     } else {
-                        accr[h] = fmaf(L, sq[jj], accr[h]);
+                        accr[h] = fmaf(L, sl[jj][2 * R1 + ic], accr[h]);
                     }
                 }
             }
@@ -156,10 +176,19 @@ __global__ void __launch_bounds__(LAG_T) k_lag_anterp(LevelArgs A, const uint32_
         int a = threadIdx.x + h * LAG_T;
         if (a < r) {
             size_t o = ((size_t)b * nrhs + m) * r + a;
-            if constexpr (CPLX)
-                ut[o] = make_float2(accr[h], acci[h]);
-            else
-                ut[o] = accr[h];
+            if constexpr (CPLX) {
+                if (sole) {
+                    ut[o] = make_float2(accr[h], acci[h]);
+                } else {
+                    atomicAdd(&ut[o].x, accr[h]);
+                    atomicAdd(&ut[o].y, acci[h]);
+                }
+            } else {
+                if (sole)
+                    ut[o] = accr[h];
+                else
+                    atomicAdd(&ut[o], accr[h]);
+            }
         }
     }
 }
@@ -452,17 +481,20 @@ __global__ void __launch_bounds__(256) k_lag_gemm_tc(const uint32_t *__restrict_
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tcols));
 }
 
-template <bool CPLX>
-__global__ void __launch_bounds__(128) k_lag_interp(LevelArgs A, const uint32_t *__restrict__ tgt, Cheb cb,
+// Target step of a Lagrange level (L_X^T v~ of eq. 8): v_i += sum_abc L_a(x_i) L_b(y_i) L_c(z_i) v~_a(abc),
+// one block per chunk of at most LAG_CHUNK points of a target box, added in FP32 into accf.
+template <bool CPLX, int R1>
+__global__ void __launch_bounds__(128) k_lag_interp(LevelArgs A, const uint2 *__restrict__ chunks, Cheb cb,
                                                     const typename QT<CPLX>::T *__restrict__ vt, int nrhs,
-                                                    int64_t nx, double2 *__restrict__ acc) {
+                                                    int64_t nx, float2 *__restrict__ accf) {
     typedef typename QT<CPLX>::T Q;
-    __shared__ Q sv[R1MAX * R1MAX * R1MAX];
-    int a = tgt[blockIdx.x], m = blockIdx.y;
-    int r1 = cb.r1, r = r1 * r1 * r1;
+    constexpr int r = R1 * R1 * R1;
+    __shared__ Q sv[r];
+    uint2 ck = chunks[blockIdx.x];
+    int a = (int)ck.x, m = blockIdx.y;
     for (int i = threadIdx.x; i < r; i += blockDim.x) sv[i] = vt[((size_t)a * nrhs + m) * r + i];
     __syncthreads();
-    uint32_t s0 = A.box_start[a], s1 = A.box_start[a + 1];
+    uint32_t s0 = ck.y, s1 = min(A.box_start[a + 1], s0 + (uint32_t)LAG_CHUNK);
     int4 gb = A.box_g[a];
     for (uint32_t i = s0 + threadIdx.x; i < s1; i += blockDim.x) {
         float4 e = A.eps[i];
@@ -473,23 +505,28 @@ __global__ void __launch_bounds__(128) k_lag_interp(LevelArgs A, const uint32_t 
         lag1d(cb, (o.y + e.y) * A.inv_half_dl, ly);
         lag1d(cb, (o.z + e.z) * A.inv_half_dl, lz);
         float sr = 0.f, si = 0.f;
-        for (int ia = 0; ia < r1; ++ia)
-            for (int ib = 0; ib < r1; ++ib) {
+#pragma unroll
+        for (int ia = 0; ia < R1; ++ia)
+#pragma unroll
+            for (int ib = 0; ib < R1; ++ib) {
                 float lab = lx[ia] * ly[ib];
-                const Q *row = sv + (ia * r1 + ib) * r1;
-                for (int ic = 0; ic < r1; ++ic) {
-                    float L = lab * lz[ic];
+                const Q *row = sv + (ia * R1 + ib) * R1;
+                float pr = 0.f, pi = 0.f;
+#pragma unroll
+                for (int ic = 0; ic < R1; ++ic) {
                     if constexpr (CPLX) {
-                        sr = fmaf(L, row[ic].x, sr);
-                        si = fmaf(L, row[ic].y, si);
+                        pr = fmaf(lz[ic], row[ic].x, pr);
+                        pi = fmaf(lz[ic], row[ic].y, pi);
                     } else {
-                        sr = fmaf(L, row[ic], sr);
+                        pr = fmaf(lz[ic], row[ic], pr);
                     }
                 }
+                sr = fmaf(lab, pr, sr);
+                if constexpr (CPLX) si = fmaf(lab, pi, si);
             }
-        double2 &dst = acc[(int64_t)m * nx + i];
-        dst.x += (double)sr;
-        dst.y += (double)si;
+        float2 &dst = accf[(int64_t)m * nx + i];
+        dst.x += sr;
+        if constexpr (CPLX) dst.y += si;
     }
 }
 
@@ -507,7 +544,37 @@ static LevelArgs level_args(const ffm_plan_s *p, const BoxLevel &B, const BoxLev
     return A;
 }
 
-void far_lagrange(const ffm_plan_s *p, int l, const void *q, int nrhs, double2 *acc, Alloc &tmp, cudaStream_t s) {
+template <bool CPLX, int R1>
+static void lagrange_points(const ffm_plan_s *p, const FarLevel &F, const LevelArgs &A, const Cheb &cb, bool anterp,
+                            const void *in, int nrhs, void *out, cudaStream_t s) {
+    typedef typename QT<CPLX>::T Q;
+    if (anterp) {
+        dim3 g((unsigned)F.n_src_chunks, nrhs);
+        FFM_LAUNCH((k_lag_anterp<CPLX, R1>), g, LAG_T, 0, s, A, F.src_chunks, cb, (const Q *)in, p->ny, nrhs,
+                   (Q *)out);
+    } else {
+        dim3 g((unsigned)F.n_tgt_chunks, nrhs);
+        FFM_LAUNCH((k_lag_interp<CPLX, R1>), g, 128, 0, s, A, F.tgt_chunks, cb, (const Q *)in, nrhs, p->nx,
+                   (float2 *)out);
+    }
+}
+
+template <bool CPLX>
+static void lagrange_points_r1(const ffm_plan_s *p, const FarLevel &F, const LevelArgs &A, const Cheb &cb,
+                               bool anterp, const void *in, int nrhs, void *out, cudaStream_t s) {
+    switch (F.r1) {
+        case 2: lagrange_points<CPLX, 2>(p, F, A, cb, anterp, in, nrhs, out, s); break;
+        case 3: lagrange_points<CPLX, 3>(p, F, A, cb, anterp, in, nrhs, out, s); break;
+        case 4: lagrange_points<CPLX, 4>(p, F, A, cb, anterp, in, nrhs, out, s); break;
+        case 5: lagrange_points<CPLX, 5>(p, F, A, cb, anterp, in, nrhs, out, s); break;
+        case 6: lagrange_points<CPLX, 6>(p, F, A, cb, anterp, in, nrhs, out, s); break;
+        case 7: lagrange_points<CPLX, 7>(p, F, A, cb, anterp, in, nrhs, out, s); break;
+        case 8: lagrange_points<CPLX, 8>(p, F, A, cb, anterp, in, nrhs, out, s); break;
+        default: fail(FFM_EUNSUPPORTED, "Chebyshev nodes per axis outside 2..8");
+    }
+}
+
+void far_lagrange(const ffm_plan_s *p, int l, const void *q, int nrhs, float2 *accf, Alloc &tmp, cudaStream_t s) {
     const FarLevel &F = p->far[l];
     int ls = p->l_stop;
     int r = F.r1 * F.r1 * F.r1;
@@ -516,20 +583,21 @@ void far_lagrange(const ffm_plan_s *p, int l, const void *q, int nrhs, double2 *
     LevelArgs AX = level_args(p, p->bx[l], p->bx[ls], p->epsX, l);
     bool cplx = p->kind == FFM_HELMHOLTZ;
     size_t esz = cplx ? sizeof(float2) : sizeof(float);
-    void *ut = tmp.raw(esz * r * nrhs * (size_t)p->by[l].nb);
-    void *vt = tmp.raw(esz * r * nrhs * (size_t)p->bx[l].nb);
-    dim3 gs((unsigned)F.n_src, nrhs), gt((unsigned)F.n_tgt, nrhs);
+    size_t ub = esz * r * nrhs * (size_t)p->by[l].nb, vb = esz * r * nrhs * (size_t)p->bx[l].nb;
+    void *ut = tmp.raw(ub);
+    void *vt = tmp.raw(vb);
     dim3 gg((unsigned)F.n_tiles, cdiv(r, LG_BM), nrhs);
-    FFM_CUDA(cudaMemsetAsync(vt, 0, esz * r * nrhs * (size_t)p->bx[l].nb, s));
+    FFM_CUDA(cudaMemsetAsync(ut, 0, ub, s));
+    FFM_CUDA(cudaMemsetAsync(vt, 0, vb, s));
     if (cplx) {
-        FFM_LAUNCH(k_lag_anterp<true>, gs, LAG_T, 0, s, AY, F.src, cb, (const float2 *)q, p->ny, nrhs, (float2 *)ut);
+        lagrange_points_r1<true>(p, F, AY, cb, true, q, nrhs, ut, s);
         FFM_LAUNCH(k_lag_gemm<true>, gg, LG_T, 0, s, F.tile_t, F.tile_p0, F.bt_off, F.bt_src, F.bt_tgt, F.T, r,
                    nrhs, (const float2 *)ut, (float2 *)vt);
-        FFM_LAUNCH(k_lag_interp<true>, gt, 128, 0, s, AX, F.tgt, cb, (const float2 *)vt, nrhs, p->nx, acc);
+        lagrange_points_r1<true>(p, F, AX, cb, false, vt, nrhs, accf, s);
     } else {
-        FFM_LAUNCH(k_lag_anterp<false>, gs, LAG_T, 0, s, AY, F.src, cb, (const float *)q, p->ny, nrhs, (float *)ut);
+        lagrange_points_r1<false>(p, F, AY, cb, true, q, nrhs, ut, s);
         int npad = (r + 15) / 16 * 16;
-        if (npad <= 256 && F.tc_tiles > 0) {
+        if (npad <= 256 && F.tc_tiles > 0 && F.tune_tc != 0) {
             // tensor cores: 128-pair tiles, K tiles of KT source nodes
             constexpr int KT = 64;
             int tcols = 32;
@@ -548,13 +616,12 @@ void far_lagrange(const ffm_plan_s *p, int l, const void *q, int nrhs, double2 *
             FFM_LAUNCH(k_lag_gemm<false>, gg, LG_T, 0, s, F.tile_t, F.tile_p0, F.bt_off, F.bt_src, F.bt_tgt, F.T, r,
                        nrhs, (const float *)ut, (float *)vt);
         }
-        FFM_LAUNCH(k_lag_interp<false>, gt, 128, 0, s, AX, F.tgt, cb, (const float *)vt, nrhs, p->nx, acc);
+        lagrange_points_r1<false>(p, F, AX, cb, false, vt, nrhs, accf, s);
     }
 }
 
 // ======================================================= plane-wave kernels
 
-constexpr int PW_QPT = 2;     // directions per thread in the forward transform
 constexpr int PW_CHUNK = 256; // staged points per block iteration
 constexpr int PW_MAXD = 16;   // deepest supported level gap between box and leaf
 constexpr int PW_QC = 512;    // directions staged per block iteration in the backward transform
@@ -1151,23 +1218,34 @@ static void planewave_level(const ffm_plan_s *p, int l, const float2 *q, int nrh
     PwArgs<R> PX{level_args(p, p->bx[l], p->bx[ls], p->epsX, l), p->epsXlo, ks, E, F.nQ};
     C2 *ut = tmp.get<C2>((size_t)p->by[l].nb * nrhs * F.nQ);
     C2 *vt = tmp.get<C2>((size_t)p->bx[l].nb * nrhs * F.nQ);
-    constexpr int QPT = 4;
+    // kernel variants (autotuned; FP64 levels keep the defaults)
+    constexpr bool dbl = sizeof(R) == 8;
+    const int qpt = dbl ? 4 : F.pw_qpt, ppt = dbl ? 4 : F.pw_ppt, mc = dbl ? 8 : F.pw_mc;
     // threads per forward block: 128 unless the ragged tail of the direction range wastes
     // more than 10% of the lanes
     int tb = 128;
     int nH = F.nQ / 2;
     for (int cand : {64, 32})
-        if ((double)cdiv(nH, tb * QPT) * tb * QPT > 1.1 * nH) tb = cand;
-    constexpr int MC = 8;  // right-hand sides per thread in the multi-RHS kernels
+        if ((double)cdiv(nH, tb * qpt) * tb * qpt > 1.1 * nH) tb = cand;
     bool multi = nrhs > 1;
     if (multi) {
-        dim3 gm((unsigned)F.n_src, cdiv(nH, 128), cdiv(nrhs, MC));
-        FFM_LAUNCH_NAMED(name("k_pw_forward_mr"), (k_pw_forward_mr<R, PH, MC>), gm, 128, 0, s, PY, F.src, q, p->ny,
-                         nrhs, ut);
+        if (!dbl && mc == 4) {
+            dim3 gm((unsigned)F.n_src, cdiv(nH, 128), cdiv(nrhs, 4));
+            FFM_LAUNCH_NAMED(name("k_pw_forward_mr"), (k_pw_forward_mr<R, PH, dbl ? 8 : 4>), gm, 128, 0, s, PY, F.src,
+                             q, p->ny, nrhs, ut);
+        } else {
+            dim3 gm((unsigned)F.n_src, cdiv(nH, 128), cdiv(nrhs, 8));
+            FFM_LAUNCH_NAMED(name("k_pw_forward_mr"), (k_pw_forward_mr<R, PH, 8>), gm, 128, 0, s, PY, F.src, q,
+                             p->ny, nrhs, ut);
+        }
     } else {
-        dim3 gf((unsigned)F.n_src, cdiv(nH, tb * QPT), 1);
-        FFM_LAUNCH_NAMED(name("k_pw_forward"), (k_pw_forward<R, PH, QPT>), gf, tb, 0, s, PY, F.src, q, p->ny, nrhs,
-                         ut);
+        dim3 gf((unsigned)F.n_src, cdiv(nH, tb * qpt), 1);
+        if (!dbl && qpt == 2)
+            FFM_LAUNCH_NAMED(name("k_pw_forward"), (k_pw_forward<R, PH, dbl ? 4 : 2>), gf, tb, 0, s, PY, F.src, q,
+                             p->ny, nrhs, ut);
+        else
+            FFM_LAUNCH_NAMED(name("k_pw_forward"), (k_pw_forward<R, PH, 4>), gf, tb, 0, s, PY, F.src, q, p->ny, nrhs,
+                             ut);
     }
     dim3 gt((unsigned)F.n_tgt, cdiv(F.nQ, 128), 1);
     if (nrhs == 1)
@@ -1181,15 +1259,24 @@ static void planewave_level(const ffm_plan_s *p, int l, const float2 *q, int nrh
     FFM_LAUNCH(k_slot_init, cdiv(nbx, 256), 256, 0, s, slot, nbx);
     FFM_LAUNCH(k_slot_set, cdiv(F.n_tgt, 256), 256, 0, s, F.tgt, F.n_tgt, slot);
     if (multi) {
-        dim3 gm((unsigned)p->bx[ls].nb, 1, cdiv(nrhs, MC));
-        FFM_LAUNCH_NAMED(name("k_pw_backward_mr"), (k_pw_backward_mr<R, PH, MC>), gm, 128, 0, s, PX, p->bx[l].fine,
-                         nbx, p->bx[ls].fine, slot, (const C2 *)vt, nrhs, p->nx, acc);
+        if (!dbl && mc == 4) {
+            dim3 gm((unsigned)p->bx[ls].nb, 1, cdiv(nrhs, 4));
+            FFM_LAUNCH_NAMED(name("k_pw_backward_mr"), (k_pw_backward_mr<R, PH, dbl ? 8 : 4>), gm, 128, 0, s, PX,
+                             p->bx[l].fine, nbx, p->bx[ls].fine, slot, (const C2 *)vt, nrhs, p->nx, acc);
+        } else {
+            dim3 gm((unsigned)p->bx[ls].nb, 1, cdiv(nrhs, 8));
+            FFM_LAUNCH_NAMED(name("k_pw_backward_mr"), (k_pw_backward_mr<R, PH, 8>), gm, 128, 0, s, PX,
+                             p->bx[l].fine, nbx, p->bx[ls].fine, slot, (const C2 *)vt, nrhs, p->nx, acc);
+        }
         return;
     }
     dim3 gb((unsigned)p->bx[ls].nb, 1, 1);
-    constexpr int PPT = 4;  // target points per thread
-    FFM_LAUNCH_NAMED(name("k_pw_backward"), (k_pw_backward<R, PH, PPT>), gb, 128, 0, s, PX, p->bx[l].fine, nbx,
-                     p->bx[ls].fine, slot, (const C2 *)vt, nrhs, p->nx, acc);
+    if (!dbl && ppt == 2)
+        FFM_LAUNCH_NAMED(name("k_pw_backward"), (k_pw_backward<R, PH, dbl ? 4 : 2>), gb, 128, 0, s, PX,
+                         p->bx[l].fine, nbx, p->bx[ls].fine, slot, (const C2 *)vt, nrhs, p->nx, acc);
+    else
+        FFM_LAUNCH_NAMED(name("k_pw_backward"), (k_pw_backward<R, PH, 4>), gb, 128, 0, s, PX, p->bx[l].fine, nbx,
+                         p->bx[ls].fine, slot, (const C2 *)vt, nrhs, p->nx, acc);
 }
 
 void far_planewave(const ffm_plan_s *p, int l, const float2 *q, int nrhs, double2 *acc, Alloc &tmp,

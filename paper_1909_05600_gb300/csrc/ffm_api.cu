@@ -7,6 +7,7 @@
 #include <string>
 
 #include "ffm_internal.cuh"
+#include <memory>
 
 namespace ffm {
 
@@ -16,18 +17,28 @@ static thread_local std::string g_last_error;
 // ------------------------------------------------------------- profiling
 
 bool g_profile = false;
+thread_local int64_t *g_capture_count = nullptr;
 struct ProfRec {
     std::string name;
     cudaEvent_t e0, e1;
 };
+// Open records, and a pool of event pairs reused after each flush, so that a profiled
+// launch costs two event records on the host and no event creation.
 static std::vector<ProfRec> g_prof_open;
+static std::vector<std::pair<cudaEvent_t, cudaEvent_t>> g_prof_pool;
 static std::vector<std::pair<std::string, std::pair<uint64_t, double>>> g_prof_tot;
 
 void profile_begin(const char *name, cudaStream_t s) {
     ProfRec r;
     r.name = name;
-    cudaEventCreate(&r.e0);
-    cudaEventCreate(&r.e1);
+    if (!g_prof_pool.empty()) {
+        r.e0 = g_prof_pool.back().first;
+        r.e1 = g_prof_pool.back().second;
+        g_prof_pool.pop_back();
+    } else {
+        cudaEventCreate(&r.e0);
+        cudaEventCreate(&r.e1);
+    }
     cudaEventRecord(r.e0, s);
     g_prof_open.push_back(r);
 }
@@ -39,8 +50,7 @@ static void profile_flush() {
         cudaEventSynchronize(r.e1);
         float ms = 0.f;
         cudaEventElapsedTime(&ms, r.e0, r.e1);
-        cudaEventDestroy(r.e0);
-        cudaEventDestroy(r.e1);
+        g_prof_pool.push_back({r.e0, r.e1});
         bool found = false;
         for (auto &t : g_prof_tot)
             if (t.first == r.name) {
@@ -78,6 +88,15 @@ void *Alloc::raw(size_t n) {
     ptrs.push_back(p);
     bytes += n;
     return p;
+}
+
+void Alloc::drop(void *p) {
+    for (size_t i = 0; i < ptrs.size(); ++i)
+        if (ptrs[i] == p) {
+            cudaFreeAsync(p, stream);
+            ptrs.erase(ptrs.begin() + (long)i);
+            return;
+        }
 }
 
 void Alloc::release() {
@@ -128,13 +147,18 @@ __global__ void k_gather_q(const UT *__restrict__ u, const uint32_t *__restrict_
     }
 }
 
+// v = near field and plane-wave levels (FP64 accumulators) + Lagrange levels (FP32), summed
+// in FP64 per target, back in the caller's order.
 template <class VT, bool CPLX>
-__global__ void k_scatter_v(const double2 *__restrict__ acc, const uint32_t *__restrict__ perm, int64_t nx, int nrhs,
-                            VT *__restrict__ v) {
+__global__ void k_scatter_v(const double2 *__restrict__ acc, const float2 *__restrict__ accf,
+                            const uint32_t *__restrict__ perm, int64_t nx, int nrhs, VT *__restrict__ v) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int m = blockIdx.y;
     if (i >= nx) return;
     double2 a = acc[(int64_t)m * nx + i];
+    float2 f = accf[(int64_t)m * nx + i];
+    a.x += (double)f.x;
+    a.y += (double)f.y;
     int64_t o = (int64_t)perm[i] + (int64_t)m * nx;
     if constexpr (CPLX) {
         v[2 * o] = (VT)a.x;
@@ -173,6 +197,8 @@ static void apply_impl(ffm_plan_s *p, const void *u, ffm_dtype udt, int nrhs, vo
     void *q = tmp.raw((helm ? 8 : 4) * (size_t)ny * nrhs);
     double2 *acc = tmp.get<double2>((size_t)nx * nrhs);
     FFM_CUDA(cudaMemsetAsync(acc, 0, sizeof(double2) * (size_t)nx * nrhs, s));
+    float2 *accf = tmp.get<float2>((size_t)nx * nrhs);
+    FFM_CUDA(cudaMemsetAsync(accf, 0, sizeof(float2) * (size_t)nx * nrhs, s));
     dim3 gy(cdiv(ny, 256), nrhs), gx(cdiv(nx, 256), nrhs);
     switch (udt) {
         case FFM_F32: FFM_LAUNCH((k_gather_q<float, false>), gy, 256, 0, s, (const float *)du, p->permY, p->wY, ny, nrhs, q); break;
@@ -184,16 +210,16 @@ static void apply_impl(ffm_plan_s *p, const void *u, ffm_dtype udt, int nrhs, vo
         const FarLevel &F = p->far[l];
         if (F.n_adm == 0) continue;
         if (F.mode == 1)
-            far_lagrange(p, l, q, nrhs, acc, tmp, s);
+            far_lagrange(p, l, q, nrhs, accf, tmp, s);
         else
             far_planewave(p, l, (const float2 *)q, nrhs, acc, tmp, s);
     }
     near_field(p, q, nrhs, acc, s);
     switch (udt) {
-        case FFM_F32: FFM_LAUNCH((k_scatter_v<float, false>), gx, 256, 0, s, acc, p->permX, nx, nrhs, (float *)dv); break;
-        case FFM_F64: FFM_LAUNCH((k_scatter_v<double, false>), gx, 256, 0, s, acc, p->permX, nx, nrhs, (double *)dv); break;
-        case FFM_C64: FFM_LAUNCH((k_scatter_v<float, true>), gx, 256, 0, s, acc, p->permX, nx, nrhs, (float *)dv); break;
-        case FFM_C128: FFM_LAUNCH((k_scatter_v<double, true>), gx, 256, 0, s, acc, p->permX, nx, nrhs, (double *)dv); break;
+        case FFM_F32: FFM_LAUNCH((k_scatter_v<float, false>), gx, 256, 0, s, acc, accf, p->permX, nx, nrhs, (float *)dv); break;
+        case FFM_F64: FFM_LAUNCH((k_scatter_v<double, false>), gx, 256, 0, s, acc, accf, p->permX, nx, nrhs, (double *)dv); break;
+        case FFM_C64: FFM_LAUNCH((k_scatter_v<float, true>), gx, 256, 0, s, acc, accf, p->permX, nx, nrhs, (float *)dv); break;
+        case FFM_C128: FFM_LAUNCH((k_scatter_v<double, true>), gx, 256, 0, s, acc, accf, p->permX, nx, nrhs, (double *)dv); break;
     }
     if (host_v) {
         FFM_CUDA(cudaMemcpyAsync(v, dv, vb, cudaMemcpyDeviceToHost, s));
@@ -283,6 +309,10 @@ ffm_status ffm_plan(const void *X, ffm_dtype xdt, int64_t nx, const void *Y, ffm
         tmp.stream = p->stream;
         build_plan(p, X, xdt, Y, ydt, w, wdt, tmp);
         tmp.release();
+        if (opts && opts->autotune_cache) {
+            ffm::apply_cached_picks(p, opts->autotune_cache, p->stream);
+            FFM_CUDA(cudaStreamSynchronize(p->stream));
+        }
         p->info.nx = nx;
         p->info.ny = ny;
         *out = p;
@@ -303,6 +333,78 @@ ffm_status ffm_apply(ffm_plan_t *plan, const void *u, ffm_dtype udt, int nrhs, v
     });
 }
 
+ffm_status ffm_autotune(ffm_plan_t *plan, int nrhs, const char *cache_path, void *stream) {
+    return guarded([&] {
+        if (!plan) fail(FFM_EINVAL, "NULL plan");
+        if (nrhs < 1 || nrhs > 65535) fail(FFM_EINVAL, "nrhs must lie in [1, 65535]");
+        ffm::autotune(plan, nrhs, cache_path, (cudaStream_t)stream);
+    });
+}
+
+struct ffm_graph_s {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int64_t kernels = 0;
+    ~ffm_graph_s() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+    }
+};
+
+ffm_status ffm_graph_create(ffm_plan_t *plan, const void *u, ffm_dtype udt, int nrhs, void *v, ffm_graph_t **out) {
+    return guarded([&] {
+        if (!out) fail(FFM_EINVAL, "NULL out");
+        *out = nullptr;
+        if (!plan || !u || !v) fail(FFM_EINVAL, "NULL argument");
+        if (nrhs < 1 || nrhs > 65535) fail(FFM_EINVAL, "nrhs must lie in [1, 65535]");
+        if (!is_device_ptr(u) || !is_device_ptr(v)) fail(FFM_EINVAL, "a captured apply needs device buffers u and v");
+        std::unique_ptr<ffm_graph_s> g(new ffm_graph_s);
+        cudaStream_t cs;
+        FFM_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        int64_t count = 0;
+        g_capture_count = &count;
+        cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed);
+        if (e != cudaSuccess) {
+            g_capture_count = nullptr;
+            cudaStreamDestroy(cs);
+            check_cuda(e, "cudaStreamBeginCapture");
+        }
+        try {
+            apply_impl(plan, u, udt, nrhs, v, cs);
+        } catch (...) {
+            cudaGraph_t partial = nullptr;
+            cudaStreamEndCapture(cs, &partial);
+            if (partial) cudaGraphDestroy(partial);
+            cudaGetLastError();
+            g_capture_count = nullptr;
+            cudaStreamDestroy(cs);
+            throw;
+        }
+        g_capture_count = nullptr;
+        e = cudaStreamEndCapture(cs, &g->graph);
+        cudaStreamDestroy(cs);
+        check_cuda(e, "cudaStreamEndCapture");
+        FFM_CUDA(cudaGraphInstantiate(&g->exec, g->graph, 0));
+        g->kernels = count;
+        *out = g.release();
+    });
+}
+
+ffm_status ffm_graph_launch(ffm_graph_t *graph, void *stream) {
+    return guarded([&] {
+        if (!graph) fail(FFM_EINVAL, "NULL graph");
+        FFM_CUDA(cudaGraphLaunch(graph->exec, (cudaStream_t)stream));
+        g_launches.fetch_add((uint64_t)graph->kernels, std::memory_order_relaxed);
+    });
+}
+
+int64_t ffm_graph_kernels(const ffm_graph_t *graph) { return graph ? graph->kernels : 0; }
+
+void ffm_graph_destroy(ffm_graph_t *graph) {
+    delete graph;
+    cudaGetLastError();
+}
+
 void ffm_destroy(ffm_plan_t *plan) {
     if (!plan) return;
     cudaStreamSynchronize(plan->stream);
@@ -319,6 +421,19 @@ ffm_status ffm_plan_bytes(const ffm_plan_t *plan, size_t *bytes) {
 ffm_status ffm_plan_info(const ffm_plan_t *plan, ffm_info *info) {
     if (!plan || !info) return FFM_EINVAL;
     *info = plan->info;
+    info->autotuned = plan->autotuned;
+    info->p2p_tchunk = plan->p2p_tchunk;
+    info->p2p_smax = (int)plan->p2p_smax;
+    for (int l = 0; l <= ffm::LMAX; ++l) {
+        const ffm::FarLevel &F = plan->far[l];
+        bool act = l <= plan->l_stop && F.n_adm > 0;
+        info->tune_tc[l] = act && F.mode == 1 ? (F.tune_tc != 0 && F.tc_tiles > 0 && plan->kind == FFM_LAPLACE &&
+                                                 (F.r1 * F.r1 * F.r1 + 15) / 16 * 16 <= 256)
+                                              : 0;
+        info->tune_pw[l][0] = act && F.mode == 2 ? F.pw_qpt : 0;
+        info->tune_pw[l][1] = act && F.mode == 2 ? F.pw_ppt : 0;
+        info->tune_pw[l][2] = act && F.mode == 2 ? F.pw_mc : 0;
+    }
     int err = 0;
     if (cudaMemcpy(&err, plan->dev_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) {
         cudaGetLastError();

@@ -16,8 +16,8 @@ namespace ffm {
 constexpr int LMAX = 21;         // finest level of the Morton keys (3 x 21 bits)
 constexpr int R1MAX = 8;         // largest Chebyshev node count per axis
 constexpr int LAG_GEMM_BN = 32;  // pairs (GEMM columns) per tile of the Lagrange transfer
-constexpr int P2P_TCHUNK = 128;  // targets per near-field work item
-constexpr int P2P_SMAX = 4096;   // source points per near-field work item (a larger single leaf stays whole)
+constexpr int P2P_T = 128;        // threads per near-field block (the largest target chunk)
+constexpr int LAG_CHUNK = 512;    // points per block of the Lagrange point-wise kernels
 constexpr double PI = 3.14159265358979323846;
 
 // ---------------------------------------------------------------- errors
@@ -35,6 +35,9 @@ void check_cuda(cudaError_t e, const char *what);
 
 extern std::atomic<uint64_t> g_launches;
 extern bool g_profile;
+// Non-null while this thread records an apply into a CUDA graph: launches are counted
+// there (they run later, once per graph launch) and not profiled.
+extern thread_local int64_t *g_capture_count;
 void profile_begin(const char *name, cudaStream_t s);
 void profile_end(cudaStream_t s);
 
@@ -43,10 +46,14 @@ template <class... KArgs, class... Args>
 inline void launch_kernel(const char *name, void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem,
                           cudaStream_t s, Args &&...args) {
     if (grid.x == 0 || grid.y == 0 || grid.z == 0) return;
-    if (g_profile) profile_begin(name, s);
+    bool prof = g_profile && !g_capture_count;
+    if (prof) profile_begin(name, s);
     k<<<grid, block, smem, s>>>(static_cast<KArgs>(args)...);
-    if (g_profile) profile_end(s);
-    g_launches.fetch_add(1, std::memory_order_relaxed);
+    if (prof) profile_end(s);
+    if (g_capture_count)
+        ++*g_capture_count;
+    else
+        g_launches.fetch_add(1, std::memory_order_relaxed);
     check_cuda(cudaGetLastError(), name);
 }
 
@@ -69,6 +76,7 @@ struct Alloc {
         return static_cast<T *>(raw(sizeof(T) * (count > 0 ? count : 1)));
     }
     void release();
+    void drop(void *p);  // free one allocation of this scope now (stream-ordered)
     ~Alloc() { release(); }
 };
 
@@ -121,12 +129,21 @@ struct FarLevel {
     int64_t n_tiles = 0;            // GEMM column tiles over all translations
     uint32_t *tile_t = nullptr;     // per tile: translation
     uint32_t *tile_p0 = nullptr;    // per tile: first pair (index into bt_*)
+    int64_t n_src_chunks = 0, n_tgt_chunks = 0;
+    uint2 *src_chunks = nullptr;    // (source box, first point): LAG_CHUNK-point pieces of the boxes
+    uint2 *tgt_chunks = nullptr;    // likewise for the target boxes
     int64_t tc_tiles = 0;           // 128-pair tiles for the tensor-core transfer
     uint32_t *tc_tile_t = nullptr;
     uint32_t *tc_tile_p0 = nullptr;
     // plane waves: arithmetic (FFM_PREC_F32 / _F32C with FP32 tables, FFM_PREC_F64 with
     // FP64 tables), chosen from the cancellation of the quadrature sum (tables.cu)
     int prec = 0;
+    // kernel variants picked by ffm_autotune (defaults otherwise): Lagrange transfer on
+    // tensor cores (-1: when the shape allows, 0: CUDA cores, 1: tensor cores); plane-wave
+    // direction pairs per thread (forward), points per thread (backward), right-hand sides
+    // per thread (several-RHS kernels)
+    int tune_tc = -1;
+    int pw_qpt = 4, pw_ppt = 4, pw_mc = 8;
     double cancel = 0;              // sum_q |D(q)| / |sum_q D(q)| for the closest translation
     float4 *ks = nullptr;           // nQ: k * s_q (x, y, z, 0)
     float2 *D = nullptr;            // n_trans * nQ
@@ -160,6 +177,9 @@ struct ffm_plan_s {
     int64_t n_near = 0;
     uint32_t *near_off = nullptr;   // nbx(l_stop)+1 CSR over all target leaves
     uint32_t *near_src = nullptr;   // n_near source leaf per pair
+    int autotuned = 0;
+    int p2p_tchunk = 128;           // work-item shape (autotuned): targets per item
+    uint32_t p2p_smax = 4096;       //   and source points per item (a larger single leaf stays whole)
     int64_t n_items = 0;            // near-field work items (target chunk x bounded source range)
     int4 *items = nullptr;          // (target leaf, first target in the leaf, first pair, end pair)
     int *dev_err = nullptr;         // device-side error flags (bounded waits that gave up)
@@ -170,6 +190,11 @@ namespace ffm {
 // tree.cu
 void build_plan(ffm_plan_s *p, const void *X, ffm_dtype xdt, const void *Y, ffm_dtype ydt, const void *w,
                 ffm_dtype wdt, Alloc &tmp);
+// tree.cu: near-field work items with targets in chunks of tchunk and at most smax source
+// points per item, allocated from out_mem; returns their number.
+int64_t build_p2p_items(ffm_plan_s *p, int tchunk, uint32_t smax, Alloc &out_mem, int4 **items, Alloc &tmp,
+                        cudaStream_t s);
+
 // tables.cu
 // Host staging buffers that must outlive the asynchronous copies reading them.
 struct HostKeep {
@@ -197,8 +222,17 @@ void build_tables(ffm_plan_s *p, int l, TableJob &tj);   // once level l's trans
 void build_octants(ffm_plan_s *p, int l, TableJob &tj);  // once the stop level is known
 int r1_rule(int kind, double eps);
 // farfield.cu / nearfield.cu
-void far_lagrange(const ffm_plan_s *p, int l, const void *q, int nrhs, double2 *acc, Alloc &tmp, cudaStream_t s);
+// Lagrange levels add their contributions in FP32 into accf (float2 per target and RHS);
+// the apply adds accf into the FP64 accumulators once, at the end.
+void far_lagrange(const ffm_plan_s *p, int l, const void *q, int nrhs, float2 *accf, Alloc &tmp, cudaStream_t s);
 void far_planewave(const ffm_plan_s *p, int l, const float2 *q, int nrhs, double2 *acc, Alloc &tmp,
                    cudaStream_t s);
 void near_field(const ffm_plan_s *p, const void *q, int nrhs, double2 *acc, cudaStream_t s);
+// autotune.cu: pick kernel variants by timing them on the plan (ffm_autotune)
+void autotune(ffm_plan_s *p, int nrhs, const char *cache_path, cudaStream_t s);
+// take the picks a cache file holds for this plan's sizes (no timing); at plan creation
+void apply_cached_picks(ffm_plan_s *p, const char *cache_path, cudaStream_t s);
+// The same with explicit work items (the autotuner times candidate item shapes).
+void near_field_items(const ffm_plan_s *p, const int4 *items, int64_t n_items, int tchunk, const void *q, int nrhs,
+                      double2 *acc, cudaStream_t s);
 }  // namespace ffm

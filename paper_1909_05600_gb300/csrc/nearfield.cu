@@ -2,8 +2,8 @@
 // leaf pairs left by the descent, v_i += sum_{j in near leaves} G(x_i - y_j) (w u)_j,
 // with pairs at distance 0 skipped.
 //
-// Work is split into items of at most P2P_TCHUNK targets of one leaf times a range of its
-// near pairs holding at most P2P_SMAX source points, so that clustered inputs with very
+// Work is split into items of at most tchunk targets of one leaf times a range of its
+// near pairs holding at most smax source points (both autotuned), so that clustered inputs with very
 // uneven leaves still spread over the whole GPU; items add into the FP64 accumulators with
 // atomics.  Coordinates are leaf-relative unevaluated FP32 pairs (hi + lo).  Source points
 // are staged in shared memory relative to the target leaf centre: the offset between the
@@ -16,7 +16,6 @@
 
 namespace ffm {
 
-constexpr int P2P_T = 128;
 constexpr int P2P_SB = 256;
 
 struct NearArgs {
@@ -26,8 +25,9 @@ struct NearArgs {
     const float4 *epsXlo, *epsYlo;        // lo parts
     const uint32_t *off, *src;            // CSR over target leaves
     const int4 *items;                    // (target leaf, first target, first pair, end pair)
-    double dls;                           // leaf edge
-    double oyx[3];                        // oY - oX
+    int tchunk;                           // targets per item (<= P2P_T)
+    float dls_h, dls_l;                   // leaf edge as an unevaluated FP32 pair
+    float oyx_h[3], oyx_l[3];             // oY - oX, likewise
     float k;
 };
 
@@ -45,30 +45,49 @@ struct Off3 {
     float h[3], l[3];
 };
 
+// Offset of source leaf b's centre from target leaf a's, oY - oX + d_ls (g_b - g_a), as
+// hi + lo in FP32 only (this part has a small fraction of the FP32 rate in FP64): the
+// product by the small integer offset is split exactly (TwoProd by FMA), then added to
+// oY - oX with a TwoSum.  Relative accuracy about 2^-44, as for the coordinates.
 __device__ __forceinline__ Off3 leaf_offset3(const NearArgs &N, int4 ga, int4 gb) {
-    double o[3] = {N.oyx[0] + N.dls * (double)(gb.x - ga.x), N.oyx[1] + N.dls * (double)(gb.y - ga.y),
-                   N.oyx[2] + N.dls * (double)(gb.z - ga.z)};
+    float g[3] = {(float)(gb.x - ga.x), (float)(gb.y - ga.y), (float)(gb.z - ga.z)};
     Off3 r;
+#pragma unroll
     for (int d = 0; d < 3; ++d) {
-        r.h[d] = (float)o[d];
-        r.l[d] = (float)(o[d] - (double)r.h[d]);
+        float ph = __fmul_rn(N.dls_h, g[d]);
+        float pl = fmaf(N.dls_h, g[d], -ph) + N.dls_l * g[d];
+        float a = N.oyx_h[d];
+        float sum = __fadd_rn(a, ph);
+        float bb = __fsub_rn(sum, a);
+        float err = __fadd_rn(__fsub_rn(a, __fsub_rn(sum, bb)), __fsub_rn(ph, bb));
+        r.h[d] = sum;
+        r.l[d] = err + (N.oyx_l[d] + pl);
     }
     return r;
 }
 
-// Accumulate the staged sources [grp, fill) step G into (sr, si) for target x = xh + xl.
+// 1/sqrt(x) by the hardware approximation (relative error about 2^-23), subnormal inputs
+// flushed to zero; a single special-function instruction.
+__device__ __forceinline__ float rsqrt_hw(float x) {
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// Accumulate the staged sources [j0, j1) into (sr, si) for target x = xh + xl.
 // Staged source j: sy[j] = (hi.x, hi.y, hi.z, lo.x), syl[j] = (lo.y, lo.z).
 template <bool HELM>
-__device__ __forceinline__ void interact(const float4 *sy, const float2 *syl, const float2 *sq, int fill, int grp,
-                                         int G, float4 xh, float4 xl, float k, float &sr, float &si) {
-    for (int j = grp; j < fill; j += G) {
+__device__ __forceinline__ void interact(const float4 *sy, const float2 *syl, const float2 *sq, int j0, int j1,
+                                         float4 xh, float4 xl, float k, float &sr, float &si) {
+#pragma unroll 4
+    for (int j = j0; j < j1; ++j) {
         float4 y = sy[j];
         float2 yl = syl[j];
         float dx = (xh.x - y.x) + (xl.x - y.w);
         float dy = (xh.y - y.y) + (xl.y - yl.x);
         float dz = (xh.z - y.z) + (xl.z - yl.y);
         float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-        float inv = r2 > 0.f ? rsqrtf(r2) : 0.f;
+        float inv = r2 > 0.f ? rsqrt_hw(r2) : 0.f;  // coincident points contribute nothing
         float2 w = sq[j];
         if constexpr (HELM) {
             // phase k r reduced to [-pi, pi] (Cody-Waite, two-term 2 pi) before sincos
@@ -99,7 +118,7 @@ __global__ void __launch_bounds__(P2P_T) k_p2p(NearArgs N, const void *__restric
     int a = it.x, m = blockIdx.y;
     uint32_t e0 = (uint32_t)it.z, e1 = (uint32_t)it.w;
     uint32_t p0 = N.xl_start[a] + (uint32_t)it.y;
-    int np = min(P2P_TCHUNK, (int)(N.xl_start[a + 1] - p0));
+    int np = min(N.tchunk, (int)(N.xl_start[a + 1] - p0));
     int G = P2P_T / np;
     int grp = threadIdx.x / np, pi = threadIdx.x % np;
     bool valid = grp < G;
@@ -135,14 +154,14 @@ __global__ void __launch_bounds__(P2P_T) k_p2p(NearArgs N, const void *__restric
             c0 += take;
             if (fill == P2P_SB) {
                 __syncthreads();
-                if (valid) interact<HELM>(sy, syl, sq, fill, grp, G, x, xl, N.k, sr, si);
+                if (valid) interact<HELM>(sy, syl, sq, grp * fill / G, (grp + 1) * fill / G, x, xl, N.k, sr, si);
                 __syncthreads();
                 fill = 0;
             }
         }
     }
     __syncthreads();
-    if (valid) interact<HELM>(sy, syl, sq, fill, grp, G, x, xl, N.k, sr, si);
+    if (valid) interact<HELM>(sy, syl, sq, grp * fill / G, (grp + 1) * fill / G, x, xl, N.k, sr, si);
     red[threadIdx.x] = make_float2(sr, si);
     __syncthreads();
     if (valid && grp == 0) {
@@ -171,7 +190,7 @@ __global__ void __launch_bounds__(P2P_T) k_p2p_mr(NearArgs N, const void *__rest
     int a = it.x, m0 = blockIdx.y * MC;
     uint32_t e0 = (uint32_t)it.z, e1 = (uint32_t)it.w;
     uint32_t p0 = N.xl_start[a] + (uint32_t)it.y;
-    int np = min(P2P_TCHUNK, (int)(N.xl_start[a + 1] - p0));
+    int np = min(N.tchunk, (int)(N.xl_start[a + 1] - p0));
     int4 ga = N.xl_g[a];
     const float *qr = reinterpret_cast<const float *>(qv);
     const float2 *qc = reinterpret_cast<const float2 *>(qv);
@@ -216,7 +235,7 @@ __global__ void __launch_bounds__(P2P_T) k_p2p_mr(NearArgs N, const void *__rest
                         float dy = (x.y - y.y) + (xl.y - yl2.x);
                         float dz = (x.z - y.z) + (xl.z - yl2.y);
                         float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                        float inv = r2 > 0.f ? rsqrtf(r2) : 0.f;
+                        float inv = r2 > 0.f ? rsqrt_hw(r2) : 0.f;
                         float gr = inv, gi = 0.f;
                         if constexpr (HELM) {
                             float ph = N.k * (r2 * inv);
@@ -231,8 +250,12 @@ __global__ void __launch_bounds__(P2P_T) k_p2p_mr(NearArgs N, const void *__rest
 #pragma unroll
                         for (int m = 0; m < MC; ++m) {
                             float2 w = sq[j][m];
-                            o[m].x = fmaf(gr, w.x, fmaf(-gi, w.y, o[m].x));
-                            o[m].y = fmaf(gr, w.y, fmaf(gi, w.x, o[m].y));
+                            if constexpr (HELM) {
+                                o[m].x = fmaf(gr, w.x, fmaf(-gi, w.y, o[m].x));
+                                o[m].y = fmaf(gr, w.y, fmaf(gi, w.x, o[m].y));
+                            } else {
+                                o[m].x = fmaf(gr, w.x, o[m].x);
+                            }
                         }
                     }
                 }
@@ -252,7 +275,12 @@ __global__ void __launch_bounds__(P2P_T) k_p2p_mr(NearArgs N, const void *__rest
 }
 
 void near_field(const ffm_plan_s *p, const void *q, int nrhs, double2 *acc, cudaStream_t s) {
-    if (p->n_near == 0 || p->n_items == 0) return;
+    near_field_items(p, p->items, p->n_items, p->p2p_tchunk, q, nrhs, acc, s);
+}
+
+void near_field_items(const ffm_plan_s *p, const int4 *items, int64_t n_items, int tchunk, const void *q, int nrhs,
+                      double2 *acc, cudaStream_t s) {
+    if (p->n_near == 0 || n_items == 0) return;
     int ls = p->l_stop;
     NearArgs N;
     N.xl_start = p->bx[ls].start;
@@ -265,20 +293,27 @@ void near_field(const ffm_plan_s *p, const void *q, int nrhs, double2 *acc, cuda
     N.epsYlo = p->epsYlo;
     N.off = p->near_off;
     N.src = p->near_src;
-    N.items = p->items;
-    N.dls = std::ldexp(p->d0, -ls);
-    for (int d = 0; d < 3; ++d) N.oyx[d] = p->oY[d] - p->oX[d];
+    N.items = items;
+    N.tchunk = tchunk;
+    double dls = std::ldexp(p->d0, -ls);
+    N.dls_h = (float)dls;
+    N.dls_l = (float)(dls - (double)N.dls_h);
+    for (int d = 0; d < 3; ++d) {
+        double o = p->oY[d] - p->oX[d];
+        N.oyx_h[d] = (float)o;
+        N.oyx_l[d] = (float)(o - (double)N.oyx_h[d]);
+    }
     N.k = (float)p->k;
     if (nrhs > 1) {
         constexpr int MC = 8;
-        dim3 gm((unsigned)p->n_items, cdiv(nrhs, MC));
+        dim3 gm((unsigned)n_items, cdiv(nrhs, MC));
         if (p->kind == FFM_HELMHOLTZ)
             FFM_LAUNCH((k_p2p_mr<true, MC>), gm, P2P_T, 0, s, N, q, p->ny, nrhs, p->nx, acc);
         else
             FFM_LAUNCH((k_p2p_mr<false, MC>), gm, P2P_T, 0, s, N, q, p->ny, nrhs, p->nx, acc);
         return;
     }
-    dim3 g((unsigned)p->n_items, nrhs);
+    dim3 g((unsigned)n_items, nrhs);
     if (p->kind == FFM_HELMHOLTZ)
         FFM_LAUNCH(k_p2p<true>, g, P2P_T, 0, s, N, q, p->ny, nrhs, p->nx, acc);
     else

@@ -593,17 +593,24 @@ __global__ void k_csr_offsets(const uint32_t *__restrict__ key, int64_t n, int64
     off[b] = (uint32_t)lo;
 }
 
-// Near-field work items of one target leaf: its targets in chunks of P2P_TCHUNK times its
-// near pairs split into consecutive ranges of at most P2P_SMAX source points.
+static uint32_t read_u32(const uint32_t *d, cudaStream_t s) {
+    uint32_t h;
+    FFM_CUDA(cudaMemcpyAsync(&h, d, sizeof h, cudaMemcpyDeviceToHost, s));
+    FFM_CUDA(cudaStreamSynchronize(s));
+    return h;
+}
+
+// Near-field work items of one target leaf: its targets in chunks of tchunk times its
+// near pairs split into consecutive ranges of at most smax source points.
 __device__ __forceinline__ int p2p_ranges(const uint32_t *off, const uint32_t *src, const uint32_t *ystart, int64_t a,
-                                          int4 *out, int base, int tc, int pstart) {
+                                          int4 *out, int base, int tc, int tchunk, uint32_t smax) {
     int nr = 0;
     uint32_t e0 = off[a], acc = 0;
     for (uint32_t e = off[a]; e < off[a + 1]; ++e) {
         uint32_t nb = ystart[src[e] + 1] - ystart[src[e]];
-        if (acc > 0 && acc + nb > P2P_SMAX) {
+        if (acc > 0 && acc + nb > smax) {
             if (out)
-                for (int c = 0; c < tc; ++c) out[base + nr * tc + c] = make_int4((int)a, pstart + c * P2P_TCHUNK, (int)e0, (int)e);
+                for (int c = 0; c < tc; ++c) out[base + nr * tc + c] = make_int4((int)a, c * tchunk, (int)e0, (int)e);
             ++nr;
             e0 = e;
             acc = 0;
@@ -613,7 +620,7 @@ __device__ __forceinline__ int p2p_ranges(const uint32_t *off, const uint32_t *s
     if (off[a + 1] > off[a]) {
         if (out)
             for (int c = 0; c < tc; ++c)
-                out[base + nr * tc + c] = make_int4((int)a, pstart + c * P2P_TCHUNK, (int)e0, (int)off[a + 1]);
+                out[base + nr * tc + c] = make_int4((int)a, c * tchunk, (int)e0, (int)off[a + 1]);
         ++nr;
     }
     return nr;
@@ -621,16 +628,36 @@ __device__ __forceinline__ int p2p_ranges(const uint32_t *off, const uint32_t *s
 
 __global__ void k_p2p_items(const uint32_t *__restrict__ off, const uint32_t *__restrict__ src,
                             const uint32_t *__restrict__ xstart, const uint32_t *__restrict__ ystart, int64_t nleaf,
-                            const uint32_t *__restrict__ pos, uint32_t *__restrict__ cnt, int4 *__restrict__ out) {
+                            int tchunk, uint32_t smax, const uint32_t *__restrict__ pos, uint32_t *__restrict__ cnt,
+                            int4 *__restrict__ out) {
     int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (a >= nleaf) return;
     int np = (int)(xstart[a + 1] - xstart[a]);
-    int tc = (np + P2P_TCHUNK - 1) / P2P_TCHUNK;
+    int tc = (np + tchunk - 1) / tchunk;
     if (!out) {
-        cnt[a] = (uint32_t)(p2p_ranges(off, src, ystart, a, nullptr, 0, tc, 0) * tc);
+        cnt[a] = (uint32_t)(p2p_ranges(off, src, ystart, a, nullptr, 0, tc, tchunk, smax) * tc);
     } else {
-        p2p_ranges(off, src, ystart, a, out, (int)pos[a], tc, 0);
+        p2p_ranges(off, src, ystart, a, out, (int)pos[a], tc, tchunk, smax);
     }
+}
+
+// Work items for the near field with targets in chunks of tchunk (<= P2P_T) and at most
+// smax source points per item (a larger single leaf stays whole); returns the count.
+int64_t build_p2p_items(ffm_plan_s *p, int tchunk, uint32_t smax, Alloc &out_mem, int4 **items, Alloc &tmp,
+                        cudaStream_t s) {
+    int ls = p->l_stop;
+    int64_t nleafX = p->bx[ls].nb;
+    uint32_t *icnt = tmp.get<uint32_t>(nleafX + 1), *ipos = tmp.get<uint32_t>(nleafX + 1);
+    FFM_CUDA(cudaMemsetAsync(icnt, 0, sizeof(uint32_t) * (nleafX + 1), s));
+    FFM_LAUNCH(k_p2p_items, cdiv(nleafX, 128), 128, 0, s, p->near_off, p->near_src, p->bx[ls].start, p->by[ls].start,
+               nleafX, tchunk, smax, (const uint32_t *)nullptr, icnt, (int4 *)nullptr);
+    uint32_t *itot = tmp.get<uint32_t>(1);
+    scan_u32(icnt, ipos, nleafX + 1, itot, tmp, s);
+    int64_t n = read_u32(itot, s);
+    *items = out_mem.get<int4>(n);
+    FFM_LAUNCH(k_p2p_items, cdiv(nleafX, 128), 128, 0, s, p->near_off, p->near_src, p->bx[ls].start, p->by[ls].start,
+               nleafX, tchunk, smax, ipos, icnt, *items);
+    return n;
 }
 
 // Target box of every pair of a CSR list (pairs of listed target x: [off[x], off[x+1])).
@@ -723,12 +750,6 @@ static void launch_leaf_eps(const void *P, const uint32_t *perm, const uint64_t 
                lo);
 }
 
-static uint32_t read_u32(const uint32_t *d, cudaStream_t s) {
-    uint32_t h;
-    FFM_CUDA(cudaMemcpyAsync(&h, d, sizeof h, cudaMemcpyDeviceToHost, s));
-    FFM_CUDA(cudaStreamSynchronize(s));
-    return h;
-}
 
 // Box tables of one set for levels 0..ldeep (boxes at level l = runs of key >> 3(21-l)).
 static void build_boxes(ffm_plan_s *p, BoxLevel *bl, const uint64_t *key, int64_t n, const uint8_t *f,
@@ -804,6 +825,34 @@ static int pw_rank(double k, double dl, double eps) {
 }
 
 // Record the admissible pairs of level l: CSR by target box, source list, translations.
+// Chunks of at most ch points of the listed boxes: (box, first point), so that the
+// point-wise kernels of a level spread large boxes over many blocks.
+__global__ void k_chunk_count(const uint32_t *__restrict__ list, int64_t n, const uint32_t *__restrict__ start,
+                              uint32_t ch, uint32_t *__restrict__ cnt) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint32_t b = list[i];
+    cnt[i] = (start[b + 1] - start[b] + ch - 1) / ch;
+}
+__global__ void k_chunk_emit(const uint32_t *__restrict__ list, int64_t n, const uint32_t *__restrict__ start,
+                             uint32_t ch, const uint32_t *__restrict__ pos, uint2 *__restrict__ out) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint32_t b = list[i], k = pos[i];
+    for (uint32_t q = start[b]; q < start[b + 1]; q += ch) out[k++] = make_uint2(b, q);
+}
+
+static uint2 *build_chunks(ffm_plan_s *p, const uint32_t *list, int64_t n, const uint32_t *start, int64_t *count,
+                           Alloc &tmp, cudaStream_t s) {
+    uint32_t *cnt = tmp.get<uint32_t>(n), *pos = tmp.get<uint32_t>(n), *tot = tmp.get<uint32_t>(1);
+    FFM_LAUNCH(k_chunk_count, cdiv(n, 256), 256, 0, s, list, n, start, (uint32_t)LAG_CHUNK, cnt);
+    scan_u32(cnt, pos, n, tot, tmp, s);
+    *count = read_u32(tot, s);
+    uint2 *out = p->mem.get<uint2>(*count);
+    FFM_LAUNCH(k_chunk_emit, cdiv(n, 256), 256, 0, s, list, n, start, (uint32_t)LAG_CHUNK, pos, out);
+    return out;
+}
+
 static void finish_far_level(ffm_plan_s *p, int l, uint32_t *aa, uint32_t *ab, int64_t na, Alloc &tmp,
                              cudaStream_t s) {
     FarLevel &F = p->far[l];
@@ -896,6 +945,8 @@ static void finish_far_level(ffm_plan_s *p, int l, uint32_t *aa, uint32_t *ab, i
         FFM_CUDA(cudaMemcpyAsync(F.tc_tile_t, ct.data(), sizeof(uint32_t) * ct.size(), cudaMemcpyHostToDevice, s));
         FFM_CUDA(cudaMemcpyAsync(F.tc_tile_p0, cp.data(), sizeof(uint32_t) * cp.size(), cudaMemcpyHostToDevice, s));
         FFM_CUDA(cudaStreamSynchronize(s));
+        F.src_chunks = build_chunks(p, F.src, F.n_src, p->by[l].start, &F.n_src_chunks, tmp, s);
+        F.tgt_chunks = build_chunks(p, F.tgt, F.n_tgt, p->bx[l].start, &F.n_tgt_chunks, tmp, s);
     }
     p->info.mode[l] = F.mode;
     if (F.mode == 1) {
@@ -1083,16 +1134,7 @@ void build_plan(ffm_plan_s *p, const void *X, ffm_dtype xdt, const void *Y, ffm_
         p->near_src = c.b;
         FFM_LAUNCH(k_csr_offsets, cdiv(nleafX + 1, 256), 256, 0, s, c.a, nnear, nleafX, p->near_off);
         // work items: target chunks x bounded source ranges
-        uint32_t *icnt = tmp.get<uint32_t>(nleafX + 1), *ipos = tmp.get<uint32_t>(nleafX + 1);
-        FFM_CUDA(cudaMemsetAsync(icnt, 0, sizeof(uint32_t) * (nleafX + 1), s));
-        FFM_LAUNCH(k_p2p_items, cdiv(nleafX, 128), 128, 0, s, p->near_off, c.b, p->bx[ls].start, p->by[ls].start,
-                   nleafX, (const uint32_t *)nullptr, icnt, (int4 *)nullptr);
-        uint32_t *itot = tmp.get<uint32_t>(1);
-        scan_u32(icnt, ipos, nleafX + 1, itot, tmp, s);
-        p->n_items = read_u32(itot, s);
-        p->items = p->mem.get<int4>(p->n_items);
-        FFM_LAUNCH(k_p2p_items, cdiv(nleafX, 128), 128, 0, s, p->near_off, c.b, p->bx[ls].start, p->by[ls].start,
-                   nleafX, ipos, icnt, p->items);
+        p->n_items = build_p2p_items(p, p->p2p_tchunk, p->p2p_smax, p->mem, &p->items, tmp, s);
         unsigned long long *pp = tmp.get<unsigned long long>(1);
         FFM_CUDA(cudaMemsetAsync(pp, 0, sizeof(unsigned long long), s));
         FFM_LAUNCH(k_sum_pair_sizes, cdiv(nnear, 256), 256, 0, s, c.a, c.b, nnear, p->bx[ls].start, p->by[ls].start,

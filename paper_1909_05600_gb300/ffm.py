@@ -30,7 +30,8 @@ STATUS = {0: "FFM_OK", 1: "FFM_EINVAL", 2: "FFM_ENOMEM", 3: "FFM_ECUDA", 4: "FFM
 # Every symbol include/ffm.h declares.
 ABI_SYMBOLS = ("ffm_plan", "ffm_apply", "ffm_destroy", "ffm_plan_bytes", "ffm_plan_info", "ffm_plan_export",
                "ffm_launch_count", "ffm_profile_enable", "ffm_profile_reset", "ffm_profile_read", "ffm_status_str",
-               "ffm_last_error", "ffm_morton_order_noalloc")
+               "ffm_last_error", "ffm_morton_order_noalloc", "ffm_graph_create", "ffm_graph_launch",
+               "ffm_graph_kernels", "ffm_graph_destroy", "ffm_autotune")
 
 
 class FFMError(RuntimeError):
@@ -41,7 +42,8 @@ class FFMError(RuntimeError):
 
 class Opts(C.Structure):
     _fields_ = [("n_leaf", C.c_int), ("l_cap", C.c_int), ("kappa_switch", C.c_double), ("r1_override", C.c_int),
-                ("precision", C.c_int), ("weights", C.c_void_p), ("weights_dtype", C.c_int)]
+                ("precision", C.c_int), ("weights", C.c_void_p), ("weights_dtype", C.c_int),
+                ("autotune_cache", C.c_char_p)]
 
 
 class Info(C.Structure):
@@ -51,14 +53,17 @@ class Info(C.Structure):
                 ("mode", C.c_int * 22), ("r1", C.c_int * 22), ("L", C.c_int * 22), ("nQ", C.c_int * 22),
                 ("nx", C.c_int64), ("ny", C.c_int64), ("src_points", C.c_int64 * 22),
                 ("tgt_points", C.c_int64 * 22), ("p2p_pairs", C.c_int64), ("pw_prec", C.c_int * 22),
-                ("cancel", C.c_double * 22), ("device_errors", C.c_int)]
+                ("cancel", C.c_double * 22), ("device_errors", C.c_int), ("autotuned", C.c_int),
+                ("p2p_tchunk", C.c_int), ("p2p_smax", C.c_int), ("tune_tc", C.c_int * 22),
+                ("tune_pw", (C.c_int * 3) * 22)]
 
     def as_dict(self):
         d = {"l_stop": self.l_stop, "root_admissible": self.root_admissible, "d0": self.d0, "oX": list(self.oX),
              "oY": list(self.oY), "nx": self.nx, "ny": self.ny, "p2p_pairs": self.p2p_pairs,
-             "device_errors": self.device_errors}
+             "device_errors": self.device_errors, "autotuned": self.autotuned, "p2p_tchunk": self.p2p_tchunk,
+             "p2p_smax": self.p2p_smax, "tune_pw": [list(r) for r in self.tune_pw]}
         for f in ("nboxX", "nboxY", "n_adm", "n_near", "n_trans", "mode", "r1", "L", "nQ", "src_points",
-                  "tgt_points", "pw_prec", "cancel"):
+                  "tgt_points", "pw_prec", "cancel", "tune_tc"):
             d[f] = list(getattr(self, f))
         return d
 
@@ -99,6 +104,16 @@ def lib():
         L.ffm_last_error.restype = C.c_char_p
         L.ffm_morton_order_noalloc.argtypes = [vp, C.c_int, i64, vp, vp]
         L.ffm_morton_order_noalloc.restype = C.c_int
+        L.ffm_graph_create.argtypes = [vp, vp, C.c_int, C.c_int, vp, C.POINTER(vp)]
+        L.ffm_graph_create.restype = C.c_int
+        L.ffm_graph_launch.argtypes = [vp, vp]
+        L.ffm_graph_launch.restype = C.c_int
+        L.ffm_graph_kernels.argtypes = [vp]
+        L.ffm_graph_kernels.restype = i64
+        L.ffm_graph_destroy.argtypes = [vp]
+        L.ffm_graph_destroy.restype = None
+        L.ffm_autotune.argtypes = [vp, C.c_int, C.c_char_p, vp]
+        L.ffm_autotune.restype = C.c_int
         _lib = L
     return _lib
 
@@ -168,6 +183,43 @@ def _stream_of(*arrays, stream=None):
 NOALLOC_MAX_POINTS = 262144
 
 
+class Graph:
+    """ffm_graph_create / ffm_graph_launch / ffm_graph_destroy.  Keeps the plan and the
+    two buffers alive while it exists."""
+
+    def __init__(self, plan, u, out):
+        self._h = None
+        one = u.ndim == 1
+        nrhs = 1 if one else int(u.shape[0])
+        self._keep = (plan, u, out)
+        h = C.c_void_p()
+        _check(lib().ffm_graph_create(plan._h, _ptr(u), _dtype_code(u), nrhs, _ptr(out), C.byref(h)))
+        self._h = h
+        self.kernels = int(lib().ffm_graph_kernels(h))
+
+    def launch(self, stream=None):
+        s = _stream_of(self._keep[1], self._keep[2], stream=stream)
+        _check(lib().ffm_graph_launch(self._h, s))
+
+    def close(self):
+        if self._h:
+            lib().ffm_graph_destroy(self._h)
+            self._h = None
+        self._keep = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
 def morton_order_noalloc(X, perm_out, stream=None):
     """ffm_morton_order_noalloc: Morton ordering of X (device) into perm_out (device uint32),
     without any device allocation inside the library."""
@@ -184,10 +236,11 @@ class Plan:
     """
 
     def __init__(self, X, Y, kernel, k=0.0, eps=1e-3, weights=None, stream=None, n_leaf=0, l_cap=0,
-                 kappa_switch=0.0, r1_override=0, precision=PREC_AUTO):
+                 kappa_switch=0.0, r1_override=0, precision=PREC_AUTO, autotune_cache=None):
         self._h = None
         self._keep = (X, Y, weights)
-        o = Opts(n_leaf, l_cap, float(kappa_switch), r1_override, int(precision), None, F64)
+        o = Opts(n_leaf, l_cap, float(kappa_switch), r1_override, int(precision), None, F64,
+                 autotune_cache.encode() if autotune_cache else None)
         if weights is not None:
             o.weights = _ptr(weights)
             o.weights_dtype = _dtype_code(weights)
@@ -231,6 +284,18 @@ class Plan:
         s = _stream_of(u, out, stream=stream)
         _check(lib().ffm_apply(self._h, _ptr(u), _dtype_code(u), nrhs, _ptr(out), s))
         return out
+
+    def autotune(self, nrhs=1, cache_path=None, stream=None):
+        """Time kernel variants on this plan and keep the fastest (ffm_autotune)."""
+        s = _stream_of(stream=stream) if stream is not None else (
+            torch.cuda.current_stream().cuda_stream if torch is not None and torch.cuda.is_available() else 0)
+        _check(lib().ffm_autotune(self._h, int(nrhs), cache_path.encode() if cache_path else None, s))
+        return self.info()
+
+    def graph(self, u, out):
+        """Capture apply(u, out) into a CUDA graph (device tensors only); Graph.launch()
+        recomputes `out` from the current contents of `u`."""
+        return Graph(self, u, out)
 
     def info(self):
         inf = Info()
