@@ -16,7 +16,7 @@
 
 namespace ffm {
 
-constexpr int P2P_SB = 256;
+constexpr int P2P_SB = 512;
 
 struct NearArgs {
     const uint32_t *xl_start, *yl_start;  // leaf starts (X, Y)
@@ -74,106 +74,125 @@ __device__ __forceinline__ float rsqrt_hw(float x) {
     return r;
 }
 
-// Accumulate the staged sources [j0, j1) into (sr, si) for target x = xh + xl.
-// Staged source j: sy[j] = (hi.x, hi.y, hi.z, lo.x), syl[j] = (lo.y, lo.z).
-template <bool HELM>
-__device__ __forceinline__ void interact(const float4 *sy, const float2 *syl, const float2 *sq, int j0, int j1,
-                                         float4 xh, float4 xl, float k, float &sr, float &si) {
-#pragma unroll 4
+// Accumulate the staged sources [j0, j1) into (sr, si) for the PT targets x = xh + xl of
+// this thread.  Staged source j: sA[j] = (hi.x, hi.y, hi.z, w.re), sB[j] = (lo.x, lo.y,
+// lo.z, w.im): two 16-byte loads serve PT pairs.
+template <bool HELM, int PT>
+__device__ __forceinline__ void interact(const float4 *sA, const float4 *sB, int j0, int j1, const float4 *xh,
+                                         const float4 *xl, float k, float *sr, float *si) {
+#pragma unroll 2
     for (int j = j0; j < j1; ++j) {
-        float4 y = sy[j];
-        float2 yl = syl[j];
-        float dx = (xh.x - y.x) + (xl.x - y.w);
-        float dy = (xh.y - y.y) + (xl.y - yl.x);
-        float dz = (xh.z - y.z) + (xl.z - yl.y);
-        float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-        float inv = r2 > 0.f ? rsqrt_hw(r2) : 0.f;  // coincident points contribute nothing
-        float2 w = sq[j];
-        if constexpr (HELM) {
-            // phase k r reduced to [-pi, pi] (Cody-Waite, two-term 2 pi) before sincos
-            float ph = k * (r2 * inv);
-            float n = rintf(ph * 0.15915494309189535f);
-            ph = fmaf(-n, 6.28318548202514648f, ph);
-            ph = fmaf(-n, -1.7484555314695172e-07f, ph);
-            float sn, cs;
-            __sincosf(ph, &sn, &cs);
-            cs *= inv;
-            sn *= inv;
-            sr = fmaf(cs, w.x, fmaf(-sn, w.y, sr));
-            si = fmaf(cs, w.y, fmaf(sn, w.x, si));
-        } else {
-            sr = fmaf(w.x, inv, sr);
+        float4 y = sA[j];
+        float4 yl = sB[j];
+#pragma unroll
+        for (int t = 0; t < PT; ++t) {
+            float dx = (xh[t].x - y.x) + (xl[t].x - yl.x);
+            float dy = (xh[t].y - y.y) + (xl[t].y - yl.y);
+            float dz = (xh[t].z - y.z) + (xl[t].z - yl.z);
+            float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            float inv = r2 > 0.f ? rsqrt_hw(r2) : 0.f;  // coincident points contribute nothing
+            if constexpr (HELM) {
+                // phase k r reduced to [-pi, pi] (Cody-Waite, two-term 2 pi) before sincos
+                float ph = k * (r2 * inv);
+                float n = rintf(ph * 0.15915494309189535f);
+                ph = fmaf(-n, 6.28318548202514648f, ph);
+                ph = fmaf(-n, -1.7484555314695172e-07f, ph);
+                float sn, cs;
+                __sincosf(ph, &sn, &cs);
+                cs *= inv;
+                sn *= inv;
+                sr[t] = fmaf(cs, y.w, fmaf(-sn, yl.w, sr[t]));
+                si[t] = fmaf(cs, yl.w, fmaf(sn, y.w, si[t]));
+            } else {
+                sr[t] = fmaf(y.w, inv, sr[t]);
+            }
         }
     }
 }
 
+// One work item: up to tchunk targets of a leaf (PT per thread) against a range of its near
+// source leaves, staged P2P_SB points at a time.  When the targets need fewer than P2P_T
+// threads, G groups of threads split each staged batch and are reduced in shared memory.
 template <bool HELM>
 __global__ void __launch_bounds__(P2P_T) k_p2p(NearArgs N, const void *__restrict__ qv, int64_t ny, int nrhs,
                                                int64_t nx, double2 *__restrict__ acc) {
-    __shared__ float4 sy[P2P_SB];
-    __shared__ float2 syl[P2P_SB];
-    __shared__ float2 sq[P2P_SB];
-    __shared__ float2 red[P2P_T];
+    constexpr int PT = 2;
+    __shared__ float4 sA[P2P_SB];
+    __shared__ float4 sB[P2P_SB];
+    __shared__ float2 red[P2P_T * PT];
     int4 it = N.items[blockIdx.x];
     int a = it.x, m = blockIdx.y;
     uint32_t e0 = (uint32_t)it.z, e1 = (uint32_t)it.w;
     uint32_t p0 = N.xl_start[a] + (uint32_t)it.y;
     int np = min(N.tchunk, (int)(N.xl_start[a + 1] - p0));
-    int G = P2P_T / np;
-    int grp = threadIdx.x / np, pi = threadIdx.x % np;
-    bool valid = grp < G;
+    int pr = min((np + PT - 1) / PT, P2P_T);  // threads per group
+    int G = P2P_T / pr;
+    int grp = threadIdx.x / pr, pi = threadIdx.x % pr;
+    bool active = grp < G;
     int4 ga = N.xl_g[a];
     const float *qr = reinterpret_cast<const float *>(qv) + (int64_t)m * ny;
     const float2 *qc = reinterpret_cast<const float2 *>(qv) + (int64_t)m * ny;
-    float4 x = valid ? N.epsX[p0 + pi] : make_float4(0.f, 0.f, 0.f, 0.f);
-    float4 xl = valid ? N.epsXlo[p0 + pi] : make_float4(0.f, 0.f, 0.f, 0.f);
-    float sr = 0.f, si = 0.f;
+    float4 xh[PT], xl[PT];
+    float sr[PT], si[PT];
+#pragma unroll
+    for (int t = 0; t < PT; ++t) {
+        int i = pi + t * pr;
+        bool ok = active && i < np;
+        xh[t] = ok ? N.epsX[p0 + i] : make_float4(0.f, 0.f, 0.f, 0.f);
+        xl[t] = ok ? N.epsXlo[p0 + i] : make_float4(0.f, 0.f, 0.f, 0.f);
+        sr[t] = si[t] = 0.f;
+    }
     int fill = 0;
     for (uint32_t e = e0; e < e1; ++e) {
         uint32_t b = N.src[e];
         uint32_t s0 = N.yl_start[b];
         int cnt = (int)(N.yl_start[b + 1] - s0);
-        Off3 oc = leaf_offset3(N, ga, N.yl_g[b]);
         for (int c0 = 0; c0 < cnt;) {
             int take = min(cnt - c0, P2P_SB - fill);
+            // the leaf-centre offset is formed only by the threads that stage points (most
+            // near leaves hold fewer points than the block has threads)
             for (int j = threadIdx.x; j < take; j += P2P_T) {
+                Off3 oc = leaf_offset3(N, ga, N.yl_g[b]);
                 float4 y = N.epsY[s0 + c0 + j];
                 float4 yl = N.epsYlo[s0 + c0 + j];
                 float hx, lx, hy, ly, hz, lz;
                 stage_coord(y.x, yl.x, oc.h[0], oc.l[0], hx, lx);
                 stage_coord(y.y, yl.y, oc.h[1], oc.l[1], hy, ly);
                 stage_coord(y.z, yl.z, oc.h[2], oc.l[2], hz, lz);
-                sy[fill + j] = make_float4(hx, hy, hz, lx);
-                syl[fill + j] = make_float2(ly, lz);
-                if constexpr (HELM)
-                    sq[fill + j] = qc[s0 + c0 + j];
-                else
-                    sq[fill + j] = make_float2(qr[s0 + c0 + j], 0.f);
+                float2 w = HELM ? qc[s0 + c0 + j] : make_float2(qr[s0 + c0 + j], 0.f);
+                sA[fill + j] = make_float4(hx, hy, hz, w.x);
+                sB[fill + j] = make_float4(lx, ly, lz, w.y);
             }
             fill += take;
             c0 += take;
             if (fill == P2P_SB) {
                 __syncthreads();
-                if (valid) interact<HELM>(sy, syl, sq, grp * fill / G, (grp + 1) * fill / G, x, xl, N.k, sr, si);
+                if (active) interact<HELM, PT>(sA, sB, grp * fill / G, (grp + 1) * fill / G, xh, xl, N.k, sr, si);
                 __syncthreads();
                 fill = 0;
             }
         }
     }
     __syncthreads();
-    if (valid) interact<HELM>(sy, syl, sq, grp * fill / G, (grp + 1) * fill / G, x, xl, N.k, sr, si);
-    red[threadIdx.x] = make_float2(sr, si);
+    if (active) interact<HELM, PT>(sA, sB, grp * fill / G, (grp + 1) * fill / G, xh, xl, N.k, sr, si);
+#pragma unroll
+    for (int t = 0; t < PT; ++t) red[threadIdx.x * PT + t] = make_float2(sr[t], si[t]);
     __syncthreads();
-    if (valid && grp == 0) {
-        float tr = 0.f, ti = 0.f;
-        for (int g = 0; g < G; ++g) {
-            tr += red[g * np + pi].x;
-            ti += red[g * np + pi].y;
-        }
+    if (active && grp == 0) {
         const double c = 0.079577471545947667884;  // 1 / (4 pi)
-        double2 *dst = &acc[(int64_t)m * nx + p0 + pi];
-        atomicAdd(&dst->x, (double)tr * c);
-        atomicAdd(&dst->y, (double)ti * c);
+#pragma unroll
+        for (int t = 0; t < PT; ++t) {
+            int i = pi + t * pr;
+            if (i >= np) continue;
+            float tr = 0.f, ti = 0.f;
+            for (int g = 0; g < G; ++g) {
+                tr += red[(g * pr + pi) * PT + t].x;
+                ti += red[(g * pr + pi) * PT + t].y;
+            }
+            double2 *dst = &acc[(int64_t)m * nx + p0 + i];
+            atomicAdd(&dst->x, (double)tr * c);
+            if (HELM) atomicAdd(&dst->y, (double)ti * c);
+        }
     }
 }
 
