@@ -65,12 +65,16 @@ typedef enum {
  * (closest translation), which amplifies rounding errors by up to C; it is large at low
  * k d_l and small eps.  FFM_PREC_AUTO picks FP32 for C <= 250, compensated FP32 (own
  * accurate sincos, TwoSum accumulation of the direction and translation sums) for
- * C <= 4e3, FP64 above, which keeps the rounding error below ~6e-6 relative. */
+ * C <= 4e3, double-float above, which keeps the rounding error below ~6e-6 relative.
+ * FFM_PREC_F64 is the same arithmetic in FP64 (this part's FP64 rate is a small fraction
+ * of its FP32 rate). */
 typedef enum {
     FFM_PREC_AUTO = 0,
     FFM_PREC_F32 = 1,   /* FP32, hardware sincos approximation */
     FFM_PREC_F32C = 2,  /* FP32 with accurate sincos and compensated sums */
-    FFM_PREC_F64 = 3    /* FP64 */
+    FFM_PREC_F64 = 3,   /* FP64 */
+    FFM_PREC_F32X2 = 4  /* double-float: unevaluated pairs of FP32 numbers (about 2^-44
+                           relative) on the FP32 pipe, with their own sincos */
 } ffm_precision;
 
 /* Plan options.  Zero-initialise and set what you need; a NULL opts pointer means all

@@ -13,7 +13,10 @@
 // so that no large phase is ever rounded to FP32.  This only re-associates the sums of
 // Sec. 2.2.3 (e^{a+b} = e^a e^b); the F matrices are still applied exactly, without
 // NUFFT.
+#include <type_traits>
+
 #include "ffm_internal.cuh"
+#include "dfloat.cuh"
 
 namespace ffm {
 
@@ -641,6 +644,17 @@ struct PwT<double> {
     typedef double2 C;
     typedef D4 K;
 };
+// double-float levels: tables and sums as unevaluated FP32 pairs (dfloat.cuh)
+template <>
+struct PwT<dd> {
+    typedef dd2 C;
+    typedef dd4 K;
+};
+
+__device__ __forceinline__ dd2 cmul(dd2 a, dd2 b) { return dd2{a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x}; }
+__device__ __forceinline__ dd2 cmulc(dd2 a, dd2 b) { return dd2{a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y}; }
+__device__ __forceinline__ dd2 czero(dd) { return dd2{dd(0.f), dd(0.f)}; }
+__device__ __forceinline__ dd2 cone(dd) { return dd2{dd(1.f), dd(0.f)}; }
 
 __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
     return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
@@ -689,7 +703,7 @@ __device__ __forceinline__ void sincos_acc(float x, float &s, float &c) {
 }
 
 template <int PH>
-__device__ __forceinline__ void phase_sincos(float ph, float &s, float &c) {
+__device__ __forceinline__ void phase_sincos(float ph, float &s, float &c, const float4 *) {
     if constexpr (PH == PH_ACC) {
         sincos_acc(ph, s, c);
     } else {
@@ -702,8 +716,12 @@ __device__ __forceinline__ void phase_sincos(float ph, float &s, float &c) {
     }
 }
 template <int PH>
-__device__ __forceinline__ void phase_sincos(double ph, double &s, double &c) {
+__device__ __forceinline__ void phase_sincos(double ph, double &s, double &c, const float4 *) {
     sincos(ph, &s, &c);
+}
+template <int PH>
+__device__ __forceinline__ void phase_sincos(dd ph, dd &s, dd &c, const float4 *tab) {
+    dd_sincos(ph, s, c, tab);
 }
 
 // hi + t with the rounding error carried into lo (Knuth's TwoSum; no ordering assumption)
@@ -714,6 +732,7 @@ __device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float t) {
     hi = sum;
 }
 __device__ __forceinline__ void two_sum_acc(double &hi, double &, double t) { hi += t; }
+__device__ __forceinline__ void two_sum_acc(dd &hi, dd &, dd t) { hi = hi + t; }
 
 // Leaf-relative coordinates of a point in the level's scalar type (hi part only in FP32,
 // hi + lo in FP64).
@@ -723,6 +742,13 @@ template <>
 struct Coord<float> {
     static __device__ __forceinline__ float3 get(const float4 &hi, const float4 *, uint32_t) {
         return make_float3(hi.x, hi.y, hi.z);
+    }
+};
+template <>
+struct Coord<dd> {
+    static __device__ __forceinline__ dd3 get(const float4 &hi, const float4 *lo, uint32_t i) {
+        float4 l = lo[i];
+        return dd3{dd(hi.x, l.x), dd(hi.y, l.y), dd(hi.z, l.z)};
     }
 };
 template <>
@@ -740,6 +766,7 @@ struct PwArgs {
     const typename PwT<R>::K *ks;
     const typename PwT<R>::C *E;  // [depth][oct][q]
     int nQ;
+    const float4 *sctab;          // double-float sin/cos table (double-float levels)
 };
 
 // Octant path of a leaf: oct[d] = octant of its ancestor at depth l+1+d within its parent.
@@ -817,7 +844,7 @@ __global__ void __launch_bounds__(128) k_pw_forward(PwArgs<R> P, const uint32_t 
                 for (int t = 0; t < QPT; ++t) {
                     R ph = fma(kx[t], e.x, fma(ky[t], e.y, kz[t] * e.z));
                     R sn, cs;
-                    phase_sincos<PH>(ph, sn, cs);
+                    phase_sincos<PH>(ph, sn, cs, P.sctab);
                     Pc[t].x = fma(cs, (R)w.x, Pc[t].x);
                     Pc[t].y = fma(cs, (R)w.y, Pc[t].y);
                     Qs[t].x = fma(sn, (R)w.x, Qs[t].x);
@@ -984,7 +1011,7 @@ __global__ void __launch_bounds__(128) k_pw_backward(PwArgs<R> P, const uint32_t
                     for (int u = 0; u < PPT; ++u) {
                         R ph = fma(k4.x, e[u].x, fma(k4.y, e[u].y, k4.z * e[u].z));
                         R sn, cs;
-                        phase_sincos<PH>(ph, sn, cs);
+                        phase_sincos<PH>(ph, sn, cs, P.sctab);
                         if constexpr (COMP) {
                             two_sum_acc(sr[u], lr[u], fma(cs, A.x, sn * B.x));
                             two_sum_acc(si[u], li[u], fma(cs, A.y, sn * B.y));
@@ -1075,7 +1102,7 @@ __global__ void __launch_bounds__(128) k_pw_forward_mr(PwArgs<R> P, const uint32
                 auto e3 = Coord<R>::get(se[j], sl, (uint32_t)j);
                 R ph = fma(kx, e3.x, fma(ky, e3.y, kz * e3.z));
                 R sn, cs;
-                phase_sincos<PH>(ph, sn, cs);
+                phase_sincos<PH>(ph, sn, cs, P.sctab);
                 // e = f e^{-i ph}
                 R er = fma(f.x, cs, f.y * sn), ei = fma(f.y, cs, -f.x * sn);
 #pragma unroll
@@ -1165,7 +1192,7 @@ __global__ void __launch_bounds__(128) k_pw_backward_mr(PwArgs<R> P, const uint3
                     K4 k4 = sk[j];
                     R ph = fma(k4.x, e3.x, fma(k4.y, e3.y, k4.z * e3.z));
                     R sn, cs;
-                    phase_sincos<PH>(ph, sn, cs);
+                    phase_sincos<PH>(ph, sn, cs, P.sctab);
 #pragma unroll
                     for (int m = 0; m < MC; ++m) {
                         C2 A = sA[j][m], B = sB[j][m];
@@ -1206,7 +1233,7 @@ static void planewave_level(const ffm_plan_s *p, int l, const float2 *q, int nrh
                             const typename PwT<R>::C *E) {
     typedef typename PwT<R>::C C2;
     constexpr bool COMP = PH == PH_ACC;
-    const char *tag = sizeof(R) == 8 ? "f64" : COMP ? "f32c" : "f32";
+    const char *tag = std::is_same<R, double>::value ? "f64" : std::is_same<R, dd>::value ? "f32x2" : COMP ? "f32c" : "f32";
     auto name = [&](const char *k) {
         static thread_local char buf[64];
         snprintf(buf, sizeof buf, "%s<%s>", k, tag);
@@ -1214,8 +1241,8 @@ static void planewave_level(const ffm_plan_s *p, int l, const float2 *q, int nrh
     };
     const FarLevel &F = p->far[l];
     int ls = p->l_stop;
-    PwArgs<R> PY{level_args(p, p->by[l], p->by[ls], p->epsY, l), p->epsYlo, ks, E, F.nQ};
-    PwArgs<R> PX{level_args(p, p->bx[l], p->bx[ls], p->epsX, l), p->epsXlo, ks, E, F.nQ};
+    PwArgs<R> PY{level_args(p, p->by[l], p->by[ls], p->epsY, l), p->epsYlo, ks, E, F.nQ, p->sctab};
+    PwArgs<R> PX{level_args(p, p->bx[l], p->bx[ls], p->epsX, l), p->epsXlo, ks, E, F.nQ, p->sctab};
     C2 *ut = tmp.get<C2>((size_t)p->by[l].nb * nrhs * F.nQ);
     C2 *vt = tmp.get<C2>((size_t)p->bx[l].nb * nrhs * F.nQ);
     // kernel variants (autotuned; FP64 levels keep the defaults)
@@ -1288,6 +1315,8 @@ void far_planewave(const ffm_plan_s *p, int l, const float2 *q, int nrhs, double
     bool reduce = p->k * std::sqrt(3.0) * std::ldexp(p->d0, -p->l_stop) * 0.5 > 2.0 * PI;
     if (F.prec == FFM_PREC_F64)
         planewave_level<double, PH_MUFU>(p, l, q, nrhs, acc, tmp, s, F.ksd, F.Dd, F.Ed);
+    else if (F.prec == FFM_PREC_F32X2)
+        planewave_level<dd, PH_MUFU>(p, l, q, nrhs, acc, tmp, s, F.ksx, F.Dx, F.Ex);
     else if (F.prec == FFM_PREC_F32C)
         planewave_level<float, PH_ACC>(p, l, q, nrhs, acc, tmp, s, F.ks, F.D, F.E);
     else if (reduce)

@@ -291,7 +291,7 @@ ffm_status ffm_plan(const void *X, ffm_dtype xdt, int64_t nx, const void *Y, ffm
         if (opts) {
             if (opts->n_leaf < 0 || opts->l_cap < 0 || opts->l_cap > LMAX || opts->kappa_switch < 0 ||
                 opts->r1_override < 0 || opts->r1_override > R1MAX || opts->r1_override == 1 ||
-                opts->precision < FFM_PREC_AUTO || opts->precision > FFM_PREC_F64)
+                opts->precision < FFM_PREC_AUTO || opts->precision > FFM_PREC_F32X2)
                 fail(FFM_EINVAL, "bad option value");
             if (opts->n_leaf > 0) p->n_leaf = opts->n_leaf;
             if (opts->l_cap > 0) p->l_cap = opts->l_cap;

@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "../../include/ffm.h"
+#include "dfloat.cuh"
 
 namespace ffm {
 
@@ -151,6 +152,9 @@ struct FarLevel {
     D4 *ksd = nullptr;
     double2 *Dd = nullptr;
     double2 *Ed = nullptr;
+    dd4 *ksx = nullptr;             // double-float levels
+    dd2 *Dx = nullptr;
+    dd2 *Ex = nullptr;
 };
 
 }  // namespace ffm
@@ -163,6 +167,7 @@ struct ffm_plan_s {
     double kappa = 2.0;
     int r1_override = 0;
     int precision = 0;  // ffm_precision for the plane-wave levels, 0 = by cancellation
+    float4 *sctab = nullptr;  // sin/cos(j/64) in double-float for the double-float levels
     double d0 = 1, oX[3] = {0, 0, 0}, oY[3] = {0, 0, 0}, sigma[3] = {0, 0, 0};
     int l_stop = 0, root_adm = 0;
     cudaStream_t stream = nullptr;

@@ -9,6 +9,7 @@
 #include <cmath>
 #include <map>
 #include <tuple>
+#include <type_traits>
 #include <vector>
 
 #include "ffm_internal.cuh"
@@ -107,14 +108,28 @@ __device__ __forceinline__ dflt df_split(double x) {
 // fraction of FP32), giving ~2^-44 relative accuracy before the final rounding.
 // coef: per translation L+1 complex coefficients split as (re.hi, re.lo, im.hi, im.lo);
 // beta: L entries p/(p+1) split as (hi, lo).
+// a double as an unevaluated FP32 pair
+__device__ __forceinline__ dd split_dd(double v) {
+    float h = (float)v;
+    return dd(h, (float)(v - (double)h));
+}
+
+// complex value (re, im) stored as the table's element type
+template <class OUT>
+__device__ __forceinline__ OUT make_out(double re, double im) {
+    if constexpr (std::is_same<OUT, float2>::value)
+        return make_float2((float)re, (float)im);
+    else if constexpr (std::is_same<OUT, double2>::value)
+        return make_double2(re, im);
+    else
+        return dd2{split_dd(re), split_dd(im)};
+}
+
 template <class OUT>
 __device__ __forceinline__ void put_d(OUT *D, size_t o, double f, dflt r, dflt i) {
     // D = i f (sum_re + i sum_im)
     double tr = (double)r.hi + (double)r.lo, ti = (double)i.hi + (double)i.lo;
-    if constexpr (sizeof(OUT) == sizeof(float2))
-        D[o] = make_float2((float)(-f * ti), (float)(f * tr));
-    else
-        D[o] = make_double2(-f * ti, f * tr);
+    D[o] = make_out<OUT>(-f * ti, f * tr);
 }
 
 // One Legendre recurrence serves four table entries.  With x = s_h . rhat_t, the sum splits
@@ -201,10 +216,7 @@ __global__ void k_pw_octants(const D4 *__restrict__ sw, int nQ, double k, double
     double sn, cs;
     sincos(ph, &sn, &cs);
     size_t o = ((size_t)d * 8 + oct) * nQ + q;
-    if constexpr (sizeof(OUT) == sizeof(float2))
-        E[o] = make_float2((float)cs, (float)sn);
-    else
-        E[o] = make_double2(cs, sn);
+    E[o] = make_out<OUT>(cs, sn);
 }
 
 // Gauss-Legendre nodes (ascending) and weights of order n by Newton's method on P_n.
@@ -358,9 +370,9 @@ void build_tables(ffm_plan_s *p, int l, TableJob &tj) {
     if (p->precision != FFM_PREC_AUTO)
         F.prec = p->precision;
     else
-        F.prec = F.cancel <= 250.0 ? FFM_PREC_F32 : F.cancel <= 4e3 ? FFM_PREC_F32C : FFM_PREC_F64;
+        F.prec = F.cancel <= 250.0 ? FFM_PREC_F32 : F.cancel <= 4e3 ? FFM_PREC_F32C : FFM_PREC_F32X2;
     p->info.pw_prec[l] = F.prec;
-    bool dbl = F.prec == FFM_PREC_F64;
+    bool dbl = F.prec == FFM_PREC_F64, dfl = F.prec == FFM_PREC_F32X2;
     p->info.cancel[l] = F.cancel;
     std::vector<float4> coef((size_t)nt * (L + 1));
     for (size_t i = 0; i < coef.size(); ++i) {
@@ -397,6 +409,21 @@ void build_tables(ffm_plan_s *p, int l, TableJob &tj) {
     if (dbl) {
         F.ksd = p->mem.get<D4>(nQ);
         F.Dd = p->mem.get<double2>((size_t)nt * nQ);
+    } else if (dfl) {
+        F.ksx = p->mem.get<dd4>(nQ);
+        F.Dx = p->mem.get<dd2>((size_t)nt * nQ);
+        if (!p->sctab) {
+            // sin and cos of j/64 for the double-float sincos
+            std::vector<float4> tab(2 * DD_SC_J + 1);
+            for (int j = -DD_SC_J; j <= DD_SC_J; ++j) {
+                double a = j / 64.0, sa = std::sin(a), ca = std::cos(a);
+                float sh = (float)sa, ch = (float)ca;
+                tab[j + DD_SC_J] = make_float4(sh, (float)(sa - (double)sh), ch, (float)(ca - (double)ch));
+            }
+            p->sctab = p->mem.get<float4>(tab.size());
+            size_t nb = sizeof(float4) * tab.size();
+            FFM_CUDA(cudaMemcpyAsync(p->sctab, tj.keep.hold(std::move(tab)), nb, cudaMemcpyHostToDevice, s));
+        }
     } else {
         F.ks = p->mem.get<float4>(nQ);
         F.D = p->mem.get<float2>((size_t)nt * nQ);
@@ -420,6 +447,16 @@ void build_tables(ffm_plan_s *p, int l, TableJob &tj) {
         for (int q = 0; q < nQ; ++q) ks[q] = D4{p->k * sw[q].x, p->k * sw[q].y, p->k * sw[q].z, 0.0};
         FFM_CUDA(cudaMemcpyAsync(F.ksd, keep.hold(std::move(ks)), sizeof(D4) * nQ, cudaMemcpyHostToDevice, s));
         FFM_LAUNCH(k_pw_table<double2>, g1, 256, sm1, s, d_sw, nH, d_coef, d_beta, L, d_rhat, d_pairs, p->k, F.Dd);
+    } else if (dfl) {
+        auto sp = [](double v) {
+            float h = (float)v;
+            return dd(h, (float)(v - (double)h));
+        };
+        std::vector<dd4> ks(nQ);
+        for (int q = 0; q < nQ; ++q)
+            ks[q] = dd4{sp(p->k * sw[q].x), sp(p->k * sw[q].y), sp(p->k * sw[q].z), dd(0.f)};
+        FFM_CUDA(cudaMemcpyAsync(F.ksx, keep.hold(std::move(ks)), sizeof(dd4) * nQ, cudaMemcpyHostToDevice, s));
+        FFM_LAUNCH(k_pw_table<dd2>, g1, 256, sm1, s, d_sw, nH, d_coef, d_beta, L, d_rhat, d_pairs, p->k, F.Dx);
     } else {
         std::vector<float4> ks(nQ);
         for (int q = 0; q < nQ; ++q)
@@ -436,14 +473,16 @@ void build_octants(ffm_plan_s *p, int l, TableJob &tj) {
     int nQ = F.nQ;
     dim3 g2(cdiv(nQ, 128), ndepth, 8);
     double half = std::ldexp(p->d0, -(l + 1));
-    if (F.prec == FFM_PREC_F64)
+    if (F.prec == FFM_PREC_F64) {
         F.Ed = p->mem.get<double2>((size_t)ndepth * 8 * nQ);
-    else
-        F.E = p->mem.get<float2>((size_t)ndepth * 8 * nQ);
-    if (F.prec == FFM_PREC_F64)
         FFM_LAUNCH(k_pw_octants<double2>, g2, 128, 0, tj.side, tj.d_sw[l], nQ, p->k, half, ndepth, F.Ed);
-    else
+    } else if (F.prec == FFM_PREC_F32X2) {
+        F.Ex = p->mem.get<dd2>((size_t)ndepth * 8 * nQ);
+        FFM_LAUNCH(k_pw_octants<dd2>, g2, 128, 0, tj.side, tj.d_sw[l], nQ, p->k, half, ndepth, F.Ex);
+    } else {
+        F.E = p->mem.get<float2>((size_t)ndepth * 8 * nQ);
         FFM_LAUNCH(k_pw_octants<float2>, g2, 128, 0, tj.side, tj.d_sw[l], nQ, p->k, half, ndepth, F.E);
+    }
 }
 
 }  // namespace ffm

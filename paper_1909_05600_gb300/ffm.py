@@ -23,7 +23,7 @@ LIB_PATH = os.path.join(HERE, "libffm_gb300.so")
 LAPLACE, HELMHOLTZ = 0, 1
 F32, F64, C64, C128 = 0, 1, 2, 3
 # plane-wave level arithmetic (ffm_precision)
-PREC_AUTO, PREC_F32, PREC_F32C, PREC_F64 = 0, 1, 2, 3
+PREC_AUTO, PREC_F32, PREC_F32C, PREC_F64, PREC_F32X2 = 0, 1, 2, 3, 4
 EXPORT_PERM_X, EXPORT_PERM_Y, EXPORT_ADM, EXPORT_NEAR = 0, 1, 2, 3
 STATUS = {0: "FFM_OK", 1: "FFM_EINVAL", 2: "FFM_ENOMEM", 3: "FFM_ECUDA", 4: "FFM_ETIMEOUT", 5: "FFM_EUNSUPPORTED"}
 

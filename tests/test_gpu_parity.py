@@ -139,9 +139,9 @@ def test_mixed_levels_coincident_sets_eps_1e4():
 
 def test_precision_modes_error_tracks_cancellation():
     """Forced plane-wave arithmetic on an ill-conditioned level (cube surface, k d = 3,
-    eps = 1e-4, cancellation ratio C ~ 3e4): FP64 matches the oracle FFM to 1e-6; FP32
-    and compensated FP32 move the result by at most ~2.3e-9 C and ~1.3e-9 C; the automatic
-    choice stays within the 1e-5 parity bar."""
+    eps = 1e-4, cancellation ratio C ~ 3e4): FP64 and double-float match the oracle FFM to
+    1e-6; FP32 and compensated FP32 move the result by at most ~2.3e-9 C and ~1.3e-9 C;
+    the automatic choice (double-float here) stays within the 1e-5 parity bar."""
     n = 20000
     X = W.cube_surface(n, 31)
     k = 12.0
@@ -149,7 +149,7 @@ def test_precision_modes_error_tracks_cancellation():
     prob = W.Problem("mixed", X, X.copy(), u, np.full(n, 6.0 / n), W.HELMHOLTZ, k, 1e-4)
     ref = O.ffm(X, X, as_c128(u), O.HELMHOLTZ, k, 1e-4, w=prob.w)[:, 0]
     err = {}
-    for mode in (ffm.PREC_AUTO, ffm.PREC_F32, ffm.PREC_F32C, ffm.PREC_F64):
+    for mode in (ffm.PREC_AUTO, ffm.PREC_F32, ffm.PREC_F32C, ffm.PREC_F64, ffm.PREC_F32X2):
         with gpu_plan(prob, precision=mode) as gp:
             info = gp.info()
             v = gpu_apply(gp, prob.u)
@@ -159,8 +159,9 @@ def test_precision_modes_error_tracks_cancellation():
             assert all(info["pw_prec"][l] == mode for l in pw)
         cmax = max(info["cancel"][l] for l in pw)
         err[mode] = O.rel_l2(v, ref)
-    assert cmax > 4e3  # auto picks FP64 for this level
+    assert cmax > 4e3  # auto picks double-float for this level
     assert err[ffm.PREC_F64] < 1e-6
+    assert err[ffm.PREC_F32X2] < 1e-6
     assert err[ffm.PREC_F32C] < 1.5e-9 * cmax
     assert err[ffm.PREC_F32] < 3e-9 * cmax
     assert err[ffm.PREC_AUTO] < TOL_FFM
@@ -262,7 +263,7 @@ def test_invalid_arguments_raise():
     with ffm.Plan(X, X, ffm.HELMHOLTZ, 3.0, 1e-3) as p:
         with pytest.raises(ffm.FFMError):
             p.apply(_t(np.ones(100)))  # Helmholtz needs complex densities
-    for prec in (-1, 4):
+    for prec in (-1, 5):
         with pytest.raises(ffm.FFMError) as e:
             ffm.Plan(X, X, ffm.HELMHOLTZ, 3.0, 1e-3, precision=prec)
         assert e.value.status == 1
