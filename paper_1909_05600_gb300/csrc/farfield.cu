@@ -1069,8 +1069,9 @@ __global__ void __launch_bounds__(128) k_pw_forward_mr(PwArgs<R> P, const uint32
     constexpr int CH = 128;
     __shared__ float4 se[CH];
     __shared__ float4 sl[sizeof(R) == 8 ? CH : 1];
-    __shared__ float2 sq[CH][MC];
+    __shared__ __align__(16) float2 sq[CH][MC];
     __shared__ int soct[PW_MAXD];
+    static_assert(MC % 2 == 0, "right-hand sides are read in pairs");
     int b = src[blockIdx.x], m0 = blockIdx.z * MC;
     int nH = P.nQ / 2;
     int h = blockIdx.y * blockDim.x + threadIdx.x;
@@ -1105,13 +1106,20 @@ __global__ void __launch_bounds__(128) k_pw_forward_mr(PwArgs<R> P, const uint32
                 phase_sincos<PH>(ph, sn, cs, P.sctab);
                 // e = f e^{-i ph}
                 R er = fma(f.x, cs, f.y * sn), ei = fma(f.y, cs, -f.x * sn);
+                // densities of two right-hand sides per 16-byte read
+                const float4 *sq4 = reinterpret_cast<const float4 *>(&sq[j][0]);
 #pragma unroll
-                for (int m = 0; m < MC; ++m) {
-                    float2 w = sq[j][m];
-                    Pc[m].x = fma(er, (R)w.x, Pc[m].x);
-                    Pc[m].y = fma(er, (R)w.y, Pc[m].y);
-                    Qs[m].x = fma(ei, (R)w.x, Qs[m].x);
-                    Qs[m].y = fma(ei, (R)w.y, Qs[m].y);
+                for (int m2 = 0; m2 < MC / 2; ++m2) {
+                    float4 w2 = sq4[m2];
+                    int m = 2 * m2;
+                    Pc[m].x = fma(er, (R)w2.x, Pc[m].x);
+                    Pc[m].y = fma(er, (R)w2.y, Pc[m].y);
+                    Qs[m].x = fma(ei, (R)w2.x, Qs[m].x);
+                    Qs[m].y = fma(ei, (R)w2.y, Qs[m].y);
+                    Pc[m + 1].x = fma(er, (R)w2.z, Pc[m + 1].x);
+                    Pc[m + 1].y = fma(er, (R)w2.w, Pc[m + 1].y);
+                    Qs[m + 1].x = fma(ei, (R)w2.z, Qs[m + 1].x);
+                    Qs[m + 1].y = fma(ei, (R)w2.w, Qs[m + 1].y);
                 }
             }
         }
@@ -1145,8 +1153,11 @@ __global__ void __launch_bounds__(128) k_pw_backward_mr(PwArgs<R> P, const uint3
     constexpr bool COMP = PH == PH_ACC && sizeof(R) == 4;
     constexpr int QC = 64;
     __shared__ K4 sk[QC];
-    __shared__ C2 sA[QC][MC];
-    __shared__ C2 sB[QC][MC];
+    // (A, B) of a direction pair and right-hand side side by side: one 16-byte read (FP32)
+    struct __align__(16) AB {
+        C2 A, B;
+    };
+    __shared__ AB sw[QC][MC];
     __shared__ int soct[PW_MAXD];
     int leaf = blockIdx.x, m0 = blockIdx.z * MC;
     uint32_t lf = leaf_fine[leaf];
@@ -1178,11 +1189,11 @@ __global__ void __launch_bounds__(128) k_pw_backward_mr(PwArgs<R> P, const uint3
                 int j = e % qc, m = e / qc;
                 if (m0 + m < nrhs) {
                     const C2 *va = vt + ((size_t)a * nrhs + m0 + m) * P.nQ;
-                    backward_weights(va[qb + j], va[qb + j + nH], leaf_factor<false>(P, soct, qb + j), sA[j][m],
-                                     sB[j][m]);
+                    backward_weights(va[qb + j], va[qb + j + nH], leaf_factor<false>(P, soct, qb + j), sw[j][m].A,
+                                     sw[j][m].B);
                 } else {
-                    sA[j][m] = czero(R(0));
-                    sB[j][m] = czero(R(0));
+                    sw[j][m].A = czero(R(0));
+                    sw[j][m].B = czero(R(0));
                 }
                 if (m == 0) sk[j] = P.ks[qb + j];
             }
@@ -1195,7 +1206,8 @@ __global__ void __launch_bounds__(128) k_pw_backward_mr(PwArgs<R> P, const uint3
                     phase_sincos<PH>(ph, sn, cs, P.sctab);
 #pragma unroll
                     for (int m = 0; m < MC; ++m) {
-                        C2 A = sA[j][m], B = sB[j][m];
+                        AB w = sw[j][m];
+                        C2 A = w.A, B = w.B;
                         if constexpr (COMP) {
                             two_sum_acc(o[m].x, ol[m].x, fma(cs, A.x, sn * B.x));
                             two_sum_acc(o[m].y, ol[m].y, fma(cs, A.y, sn * B.y));
