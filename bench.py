@@ -380,7 +380,11 @@ def main():
     with ffm.Plan(X, Y, prob.kind, prob.k, prob.eps, weights=w, autotune_cache=tune_cache) as p0:
         info = p0.info()
 
-    def timed():
+    def timed(profiled):
+        """K steps between a barrier and synchronisations.  The unprofiled pass gives the
+        throughput; the profiled pass (the library brackets every kernel with two events)
+        gives each kernel's device time for the roofline.  Event records cost host time
+        per launch, which shows up as gaps between the many small kernels of a plan."""
         ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
         clocks = Clocks(local)
         ffm.profile_reset()
@@ -392,7 +396,7 @@ def main():
         vlast = None
         for i in range(args.steps):
             flush.zero_()  # L2 flush between steps, outside the step's events
-            ffm.profile_enable(True)
+            ffm.profile_enable(profiled)
             vlast, _ = step(ev[i])
             ffm.profile_enable(False)
         torch.cuda.synchronize()
@@ -402,14 +406,15 @@ def main():
         launches = ffm.launch_count() - l0
         t_plan = sum(e[0].elapsed_time(e[1]) for e in ev)
         t_apply = sum(e[1].elapsed_time(e[2]) for e in ev)
-        return vlast, t_plan, t_apply, clk, launches, ffm.profile_read()
+        return vlast, t_plan, t_apply, clk, launches, (ffm.profile_read() if profiled else None)
 
-    vlast, t_plan, t_apply, clk, launches, prof = timed()
+    vlast, t_plan, t_apply, clk, launches, _ = timed(False)
+    _, tp_plan, tp_apply, _, _, prof = timed(True)
     rep = repeat_applies(ffm, torch, prob, X, Y, w, u, flush, stream, max(3, args.steps), tune_cache)
     note = None
     if rejected(clk):
         note = "first timed run rejected (clock reasons %s); re-measured" % clk.get("reasons")
-        vlast, t_plan, t_apply, clk, launches, prof = timed()
+        vlast, t_plan, t_apply, clk, launches, _ = timed(False)
     t_step = t_plan + t_apply  # ms over all steps (device time between the step's events)
     if dist:
         import torch.distributed as tdist
@@ -475,6 +480,7 @@ def main():
             "t_plan_ms": t_plan / args.steps, "t_apply_ms": t_apply / args.steps,
             "apply_only_per_s": args.steps * world / (t_apply * 1e-3),
             "repeat_apply": rep, "autotune": tune,
+            "profiled_pass_ms_per_step": (tp_plan + tp_apply) / args.steps,
             "err_vs_fp64_direct": err, "err_targets": args.cpu_targets if err is not None else None,
             "roofline": rl, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": launches,
             "kernels": kernels,

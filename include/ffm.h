@@ -95,6 +95,10 @@ typedef struct {
     const char *autotune_cache; /* NULL, or a file written by ffm_autotune: the plan takes the
                                    picks stored for its sizes (single right-hand side picks;
                                    several-RHS picks from 64, else 8 RHS), timing nothing */
+    int lagrange_transfer;      /* Laplace Lagrange levels' transfer: 0 default (tcgen05 per
+                                   translation, or ffm_autotune's pick), 1 CUDA-core GEMM per
+                                   translation, 2 tcgen05 per translation, 3 tcgen05
+                                   target-stationary (r <= 64) */
 } ffm_opts;
 
 /* Build a plan for targets X (nx points) and sources Y (ny points) (Sec. 2.2.1-2.2.4):
@@ -159,7 +163,9 @@ typedef struct {
     /* kernel variants in use (ffm_autotune's picks, else the defaults) */
     int autotuned;             /* 1 after ffm_autotune */
     int p2p_tchunk, p2p_smax;  /* near-field work items: targets, source points per item */
-    int tune_tc[22];           /* Lagrange levels: transfer on tensor cores (1) or CUDA cores (0) */
+    int tune_tc[22];           /* Lagrange levels' transfer: 0 CUDA-core GEMM per translation,
+                                  1 tcgen05 GEMM per translation (atomic scatter), 2 tcgen05
+                                  target-stationary (one write per target box) */
     int tune_pw[22][3];        /* plane-wave levels: direction pairs per thread (forward), points
                                   per thread (backward), right-hand sides per thread (several) */
 } ffm_info;
@@ -177,8 +183,9 @@ ffm_status ffm_plan_export(const ffm_plan_t *plan, int what, int level, void *ho
 
 /* Pick kernel variants for this plan by timing them on its own data, for products with
  * `nrhs` right-hand sides: the near-field work-item shape (targets and source points per
- * item, which balance clustered leaves), the Lagrange transfer GEMM (tcgen05 tiles of 128
- * box pairs, or CUDA-core tiles of 32), and per plane-wave level the direction pairs and
+ * item, which balance clustered leaves), the Lagrange transfer (tcgen05 target-stationary
+ * tiles of 128 target boxes, tcgen05 tiles of 128 box pairs of one translation, or
+ * CUDA-core tiles of 32 pairs), and per plane-wave level the direction pairs and
  * points per thread of the transforms (or right-hand sides per thread).  Costs a few
  * applies of GPU time; results change only by rounding.
  *   cache_path : NULL, or a text file of earlier picks keyed by device, kernel, level

@@ -123,7 +123,7 @@ std::string pw_key(const ffm_plan_s *p, int l, const std::string &dev, int rhsb)
 bool parse_near(const std::string &v, int &tch, unsigned &smax) {
     return sscanf(v.c_str(), "%d %u", &tch, &smax) == 2 && tch >= 1 && tch <= P2P_T && smax >= 1;
 }
-bool parse_lag(const std::string &v, int &pick) { return sscanf(v.c_str(), "%d", &pick) == 1 && (pick == 0 || pick == 1); }
+bool parse_lag(const std::string &v, int &pick) { return sscanf(v.c_str(), "%d", &pick) == 1 && pick >= 0 && pick <= 2; }
 bool parse_pw(const std::string &v, int &a, int &b, int &c) {
     return sscanf(v.c_str(), "%d %d %d", &a, &b, &c) == 3 && (a == 2 || a == 4) && (b == 2 || b == 4) &&
            (c == 4 || c == 8);
@@ -155,7 +155,10 @@ void apply_cached_picks(ffm_plan_s *p, const char *cache_path, cudaStream_t s) {
         if (F.n_adm == 0) continue;
         int a, b, c;
         if (F.mode == 1) {
-            if (cache.get(lag_key(p, l, dev, 1), v) && parse_lag(v, a)) F.tune_tc = a;
+            if (cache.get(lag_key(p, l, dev, 1), v) && parse_lag(v, a)) {
+                if (a == 2) prepare_target_stationary(p, l, s);
+                if (a != 2 || F.ts_ok) F.tune_tc = a;
+            }
         } else if (F.prec != FFM_PREC_F64) {
             if (cache.get(pw_key(p, l, dev, 1), v) && parse_pw(v, a, b, c)) {
                 F.pw_qpt = a;
@@ -228,12 +231,20 @@ void autotune(ffm_plan_s *p, int nrhs, const char *cache_path, cudaStream_t s) {
             if (!tc_ok) continue;
             std::string key = lag_key(p, l, dev, rhs_bucket(nrhs));
             int pick = -1;
-            if (!cache.get(key, v) || !parse_lag(v, pick)) {
-                F.tune_tc = 0;
-                float t_cuda = T.measure(run_level);
-                F.tune_tc = 1;
-                float t_tc = T.measure(run_level);
-                pick = t_tc <= t_cuda ? 1 : 0;
+            bool cached = cache.get(key, v) && parse_lag(v, pick);
+            if (!cached || pick == 2) prepare_target_stationary(p, l, s);
+            if (!cached || (pick == 2 && !F.ts_ok)) {
+                // 0: CUDA-core GEMM per translation, 1: tcgen05 per translation,
+                // 2: tcgen05 target-stationary
+                float best = std::numeric_limits<float>::infinity();
+                for (int c = 0; c <= (F.ts_ok ? 2 : 1); ++c) {
+                    F.tune_tc = c;
+                    float ms = T.measure(run_level);
+                    if (ms < best) {
+                        best = ms;
+                        pick = c;
+                    }
+                }
                 cache.put(key, std::to_string(pick));
             }
             F.tune_tc = pick;

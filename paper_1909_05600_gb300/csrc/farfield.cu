@@ -484,6 +484,221 @@ __global__ void __launch_bounds__(256) k_lag_gemm_tc(const uint32_t *__restrict_
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tcols));
 }
 
+// ---- target-stationary tensor-core transfer (r <= 64)
+//
+// A CTA owns TS_M = 128 consecutive target boxes of the level (TMEM lane = box).  For every
+// translation t present among their admissible pairs (partners are sorted by translation
+// within each target, so a per-row cursor finds the row's source box for t) it gathers the
+// source rows u~_b (zero rows for boxes without a partner at t), multiplies them by T_t
+// (N = 64 target nodes, K = 64 source nodes, zero padded beyond r) and accumulates into the
+// same TMEM tile: D(a, i) = sum_t sum_j u~_{b(a,t)}(j) T_t(i, j).  Each target's v~ is then
+// written once, with no atomics.  Operands as in k_lag_gemm_tc (TF32 hi/lo, three MMAs per
+// K step); T_t arrives pre-split in the core-matrix order by cp.async.  Two operand stages:
+// the gather of translation g+1 overlaps the MMAs of g, each stage released by its own
+// mbarrier.  Waits are bounded and raise the device error flag.
+constexpr int TS_M = 128;
+constexpr int TS_A = TS_M * 64;  // floats per A hi or lo block
+constexpr int TS_B = 64 * 64;    // floats per B hi or lo block
+constexpr int TS_STAGE = 2 * TS_A + 2 * TS_B;
+constexpr int TS_MAXT = 4096;    // translation codes lie in a 16^3 range
+constexpr int TS_DRAIN = 8;      // translations per TMEM accumulation before it is drained
+
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+
+// bounded wait on an mbarrier phase; false if it gave up
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t done = 0;
+    for (int it = 0; it < (1 << 24) && !done; ++it)
+        asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+                     : "=r"(done)
+                     : "r"(smem_addr(bar)), "r"(parity));
+    return done != 0;
+}
+
+__global__ void __launch_bounds__(2 * TS_M) k_lag_gemm_ts(const uint32_t *__restrict__ tgt, int64_t n_tgt,
+                                                         const uint32_t *__restrict__ adm_off,
+                                                         const uint32_t *__restrict__ adm_src,
+                                                         const uint32_t *__restrict__ adm_t, int n_trans,
+                                                         const float *__restrict__ Tsp, int r, int nrhs,
+                                                         const float *__restrict__ ut, float *__restrict__ vt,
+                                                         int *__restrict__ err) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    float *stage0 = reinterpret_cast<float *>(smem);
+    __shared__ uint32_t s_bits[TS_MAXT / 32];
+    __shared__ uint32_t s_tmem;
+    __shared__ __align__(8) uint64_t s_mbar[2];
+    constexpr int NT = 2 * TS_M;
+    // two threads per target row: half 0 takes source nodes / columns 0..31, half 1 32..63
+    int tid = threadIdx.x, warp = tid >> 5;
+    int row = tid & (TS_M - 1), half = tid >> 7;
+    int quarter = warp & 3;  // TMEM lanes 32 quarter .. 32 quarter + 31 (= rows of this warp)
+    int m = blockIdx.y;
+    int64_t x = (int64_t)blockIdx.x * TS_M + row;
+    bool has = x < n_tgt;
+    uint32_t cur = has ? adm_off[x] : 0u, end = has ? adm_off[x + 1] : 0u;
+    int nw = (n_trans + 31) / 32;
+    for (int w = tid; w < nw; w += NT) s_bits[w] = 0u;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&s_tmem)),
+                     "r"(64));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&s_mbar[0])));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&s_mbar[1])));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    uint32_t tmem = s_tmem;
+    if (half == 0)
+        for (uint32_t e = cur; e < end; ++e) {
+            uint32_t t = adm_t[e];
+            atomicOr(&s_bits[t >> 5], 1u << (t & 31));
+        }
+    __syncthreads();
+    const bool r4 = (r & 3) == 0;
+    const uint32_t lbo = 128, sbo = 16 * 128;  // K tile of 64: 16 core matrices along K
+    const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(64 >> 3) << 17) | ((uint32_t)(TS_M >> 4) << 24);
+    uint32_t next_t = cur < end ? adm_t[cur] : 0xffffffffu;
+    uint32_t parity[2] = {0u, 0u};
+    bool ok = true;
+    int g = 0, g0 = 0;  // groups issued; first group of the current TMEM accumulation
+    float sum[32];      // FP32 sums of the drained TMEM partial results (half a row)
+#pragma unroll
+    for (int c = 0; c < 32; ++c) sum[c] = 0.f;
+    // wait for the MMAs in flight and add the TMEM tile into the register sums; the
+    // tensor-core accumulation then restarts, so no FP32 accumulator in TMEM takes more
+    // than TS_DRAIN translations x 24 MMA steps
+    auto drain = [&]() {
+        if (g >= g0 + 2) {
+            int st = (g - 2) & 1;
+            ok &= mbar_wait(&s_mbar[st], parity[st]);
+            parity[st] ^= 1u;
+        }
+        if (g >= g0 + 1) {
+            int st = (g - 1) & 1;
+            ok &= mbar_wait(&s_mbar[st], parity[st]);
+            parity[st] ^= 1u;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+        for (int c0 = 0; c0 < 32; c0 += 8) {
+            uint32_t v[8];
+            uint32_t addr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(half * 32 + c0);
+            asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                         : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+                           "=r"(v[7])
+                         : "r"(addr));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+            for (int q = 0; q < 8; ++q) sum[c0 + q] += __uint_as_float(v[q]);
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        g0 = g;
+    };
+    for (int w = 0; w < nw; ++w) {
+        uint32_t bits = s_bits[w];
+        while (bits) {
+            uint32_t t = (uint32_t)(w * 32 + __ffs(bits) - 1);
+            bits &= bits - 1;
+            if (g - g0 == TS_DRAIN) drain();
+            int st = g & 1;
+            float *S = stage0 + st * TS_STAGE;
+            // the stage was last read by the MMAs of translation g - 2
+            if (g >= g0 + 2) {
+                ok &= mbar_wait(&s_mbar[st], parity[st]);
+                parity[st] ^= 1u;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            }
+            // B: T_t hi and lo, already in the shared-memory image order
+            const float *Tb = Tsp + (size_t)t * 2 * TS_B;
+            float *B = S + 2 * TS_A;
+            for (int c = tid; c < 2 * TS_B / 4; c += NT) cp_async16(B + 4 * c, Tb + 4 * c);
+            asm volatile("cp.async.commit_group;" ::: "memory");
+            // A: this row's source box for translation t, or a zero row (both threads of
+            // the row follow the same cursor)
+            bool pres = next_t == t;
+            uint32_t src = 0u;
+            if (pres) {
+                src = adm_src[cur];
+                ++cur;
+                next_t = cur < end ? adm_t[cur] : 0xffffffffu;
+            }
+            const float *rowp = ut + ((size_t)src * nrhs + m) * r;
+            float4 v[8];
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {  // all loads first
+                int j = half * 32 + 4 * c;
+                v[c] = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (pres && j < r) {
+                    if (r4) {
+                        v[c] = *reinterpret_cast<const float4 *>(rowp + j);
+                    } else {
+                        v[c].x = rowp[j];
+                        v[c].y = j + 1 < r ? rowp[j + 1] : 0.f;
+                        v[c].z = j + 2 < r ? rowp[j + 2] : 0.f;
+                        v[c].w = j + 3 < r ? rowp[j + 3] : 0.f;
+                    }
+                }
+            }
+            float *Ah = S, *Al = S + TS_A;
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                float4 h, l;
+                tf32_split(v[c].x, h.x, l.x);
+                tf32_split(v[c].y, h.y, l.y);
+                tf32_split(v[c].z, h.z, l.z);
+                tf32_split(v[c].w, h.w, l.w);
+                uint32_t o = kmajor_index(row, half * 32 + 4 * c, 64);
+                *reinterpret_cast<float4 *>(Ah + o) = h;
+                *reinterpret_cast<float4 *>(Al + o) = l;
+            }
+            asm volatile("cp.async.wait_all;" ::: "memory");
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncthreads();
+            if (tid == 0) {
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                for (int ks = 0; ks < 8; ++ks) {
+                    uint64_t ah = umma_desc(smem_addr(Ah) + ks * 256, lbo, sbo);
+                    uint64_t al = umma_desc(smem_addr(Al) + ks * 256, lbo, sbo);
+                    uint64_t bh = umma_desc(smem_addr(B) + ks * 256, lbo, sbo);
+                    uint64_t bl = umma_desc(smem_addr(B + TS_B) + ks * 256, lbo, sbo);
+                    uint32_t acc0 = (g > g0 || ks > 0) ? 1u : 0u;
+                    asm volatile(
+                        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                        "l"(ah), "l"(bh), "r"(idesc), "r"(acc0));
+                    asm volatile("tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, 1;\n" ::"r"(tmem), "l"(ah),
+                                 "l"(bl), "r"(idesc));
+                    asm volatile("tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, 1;\n" ::"r"(tmem), "l"(al),
+                                 "l"(bh), "r"(idesc));
+                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                 smem_addr(&s_mbar[st]))
+                             : "memory");
+            }
+            ++g;
+        }
+    }
+    // the last partial accumulation, then one write per target box
+    if (g > g0) drain();
+    if (!ok && tid == 0) atomicOr(err, 1);
+    if (has && ok) {
+        float *dst = vt + ((size_t)tgt[x] * nrhs + m) * r + half * 32;
+#pragma unroll
+        for (int c = 0; c < 32; ++c)
+            if (half * 32 + c < r) dst[c] = sum[c];
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(64));
+}
+
 // Target step of a Lagrange level (L_X^T v~ of eq. 8): v_i += sum_abc L_a(x_i) L_b(y_i) L_c(z_i) v~_a(abc),
 // one block per chunk of at most LAG_CHUNK points of a target box, added in FP32 into accf.
 template <bool CPLX, int R1>
@@ -600,7 +815,17 @@ void far_lagrange(const ffm_plan_s *p, int l, const void *q, int nrhs, float2 *a
     } else {
         lagrange_points_r1<false>(p, F, AY, cb, true, q, nrhs, ut, s);
         int npad = (r + 15) / 16 * 16;
-        if (npad <= 256 && F.tc_tiles > 0 && F.tune_tc != 0) {
+        if (F.ts_ok && F.Tsp && F.tune_tc == 2) {
+            size_t smem = (size_t)2 * TS_STAGE * sizeof(float);
+            static bool attr_ts = false;
+            if (!attr_ts) {
+                FFM_CUDA(cudaFuncSetAttribute(k_lag_gemm_ts, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+                attr_ts = true;
+            }
+            dim3 gts(cdiv(F.n_tgt, TS_M), nrhs);
+            FFM_LAUNCH(k_lag_gemm_ts, gts, 2 * TS_M, smem, s, F.tgt, F.n_tgt, F.adm_off, F.adm_src, F.adm_t, F.n_trans,
+                       F.Tsp, r, nrhs, (const float *)ut, (float *)vt, p->dev_err);
+        } else if (npad <= 256 && F.tc_tiles > 0 && F.tune_tc != 0) {
             // tensor cores: 128-pair tiles, K tiles of KT source nodes
             constexpr int KT = 64;
             int tcols = 32;

@@ -291,13 +291,15 @@ ffm_status ffm_plan(const void *X, ffm_dtype xdt, int64_t nx, const void *Y, ffm
         if (opts) {
             if (opts->n_leaf < 0 || opts->l_cap < 0 || opts->l_cap > LMAX || opts->kappa_switch < 0 ||
                 opts->r1_override < 0 || opts->r1_override > R1MAX || opts->r1_override == 1 ||
-                opts->precision < FFM_PREC_AUTO || opts->precision > FFM_PREC_F32X2)
+                opts->precision < FFM_PREC_AUTO || opts->precision > FFM_PREC_F32X2 ||
+                opts->lagrange_transfer < 0 || opts->lagrange_transfer > 3)
                 fail(FFM_EINVAL, "bad option value");
             if (opts->n_leaf > 0) p->n_leaf = opts->n_leaf;
             if (opts->l_cap > 0) p->l_cap = opts->l_cap;
             if (opts->kappa_switch > 0) p->kappa = opts->kappa_switch;
             p->r1_override = opts->r1_override;
             p->precision = opts->precision;
+            p->lag_transfer = opts->lagrange_transfer;
             w = opts->weights;
             wdt = opts->weights_dtype;
             if (w && wdt != FFM_F32 && wdt != FFM_F64) fail(FFM_EINVAL, "weights dtype must be FFM_F32 or FFM_F64");
@@ -427,9 +429,10 @@ ffm_status ffm_plan_info(const ffm_plan_t *plan, ffm_info *info) {
     for (int l = 0; l <= ffm::LMAX; ++l) {
         const ffm::FarLevel &F = plan->far[l];
         bool act = l <= plan->l_stop && F.n_adm > 0;
-        info->tune_tc[l] = act && F.mode == 1 ? (F.tune_tc != 0 && F.tc_tiles > 0 && plan->kind == FFM_LAPLACE &&
-                                                 (F.r1 * F.r1 * F.r1 + 15) / 16 * 16 <= 256)
-                                              : 0;
+        bool tc = F.tune_tc != 0 && F.tc_tiles > 0 && plan->kind == FFM_LAPLACE &&
+                  (F.r1 * F.r1 * F.r1 + 15) / 16 * 16 <= 256;
+        bool ts = F.ts_ok && F.Tsp && F.tune_tc == 2;
+        info->tune_tc[l] = act && F.mode == 1 ? (ts ? 2 : tc ? 1 : 0) : 0;
         info->tune_pw[l][0] = act && F.mode == 2 ? F.pw_qpt : 0;
         info->tune_pw[l][1] = act && F.mode == 2 ? F.pw_ppt : 0;
         info->tune_pw[l][2] = act && F.mode == 2 ? F.pw_mc : 0;

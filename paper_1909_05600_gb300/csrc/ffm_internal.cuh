@@ -83,6 +83,13 @@ struct Alloc {
 
 inline unsigned cdiv(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b); }
 
+// K-major, no-swizzle operand layout of the tcgen05 kernels: 8-row x 16-byte core
+// matrices, core matrix (row / 8, k / 4) at byte ((row / 8) * KT / 4 + k / 4) * 128, row
+// within it at 16 * (row % 8), element k % 4 at 4 * (k % 4).  Returns a float index.
+__host__ __device__ inline uint32_t kmajor_index(int row, int k, int KT) {
+    return (uint32_t)((((row >> 3) * (KT >> 2) + (k >> 2)) << 5) + ((row & 7) << 2) + (k & 3));
+}
+
 struct alignas(32) D4 {
     double x, y, z, w;
 };
@@ -133,6 +140,10 @@ struct FarLevel {
     int64_t n_src_chunks = 0, n_tgt_chunks = 0;
     uint2 *src_chunks = nullptr;    // (source box, first point): LAG_CHUNK-point pieces of the boxes
     uint2 *tgt_chunks = nullptr;    // likewise for the target boxes
+    bool ts_ok = false;             // target-stationary transfer possible (Laplace, r <= 64,
+                                    // partners sorted by translation within each target)
+    float *Tsp = nullptr;           // target-stationary transfer (r <= 64): T_t split into TF32
+                                    // hi and lo, 64 x 64 each, in the K-major core-matrix layout
     int64_t tc_tiles = 0;           // 128-pair tiles for the tensor-core transfer
     uint32_t *tc_tile_t = nullptr;
     uint32_t *tc_tile_p0 = nullptr;
@@ -168,6 +179,7 @@ struct ffm_plan_s {
     int r1_override = 0;
     int precision = 0;  // ffm_precision for the plane-wave levels, 0 = by cancellation
     float4 *sctab = nullptr;  // sin/cos(j/64) in double-float for the double-float levels
+    int lag_transfer = 0;     // ffm_opts.lagrange_transfer
     double d0 = 1, oX[3] = {0, 0, 0}, oY[3] = {0, 0, 0}, sigma[3] = {0, 0, 0};
     int l_stop = 0, root_adm = 0;
     cudaStream_t stream = nullptr;
@@ -195,6 +207,11 @@ namespace ffm {
 // tree.cu
 void build_plan(ffm_plan_s *p, const void *X, ffm_dtype xdt, const void *Y, ffm_dtype ydt, const void *w,
                 ffm_dtype wdt, Alloc &tmp);
+// tree.cu: partners sorted by translation and T pre-split for the target-stationary
+// transfer of Lagrange level l (on demand); tables.cu: the T split
+void prepare_target_stationary(ffm_plan_s *p, int l, cudaStream_t s);
+void launch_table_split(ffm_plan_s *p, int l, cudaStream_t s);
+
 // tree.cu: near-field work items with targets in chunks of tchunk and at most smax source
 // points per item, allocated from out_mem; returns their number.
 int64_t build_p2p_items(ffm_plan_s *p, int tchunk, uint32_t smax, Alloc &out_mem, int4 **items, Alloc &tmp,

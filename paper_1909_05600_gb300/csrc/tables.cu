@@ -72,6 +72,29 @@ __global__ void k_lag_table(const int4 *__restrict__ m, int ntrans, LagGeo geo, 
     }
 }
 
+// T_t split for the target-stationary tensor-core transfer: per translation a 64 x 64 hi
+// block then a 64 x 64 lo block (rows i, K = j; zero beyond r), each in the K-major
+// core-matrix order the MMA reads from shared memory.  hi keeps the TF32 bits (low 13
+// mantissa bits cleared), lo = T - hi exactly.
+__global__ void k_lag_table_split(const float *__restrict__ T, int r, float *__restrict__ out) {
+    int t = blockIdx.x;
+    for (int e = threadIdx.x; e < 64 * 64; e += blockDim.x) {
+        int i = e / 64, j = e % 64;
+        float v = (i < r && j < r) ? T[(size_t)t * r * r + (size_t)i * r + j] : 0.f;
+        float hi = __uint_as_float(__float_as_uint(v) & 0xffffe000u);
+        uint32_t o = kmajor_index(i, j, 64);
+        out[(size_t)t * 8192 + o] = hi;
+        out[(size_t)t * 8192 + 4096 + o] = v - hi;
+    }
+}
+
+void launch_table_split(ffm_plan_s *p, int l, cudaStream_t s) {
+    FarLevel &F = p->far[l];
+    int r = F.r1 * F.r1 * F.r1;
+    F.Tsp = p->mem.get<float>((size_t)F.n_trans * 8192);
+    FFM_LAUNCH(k_lag_table_split, F.n_trans, 256, 0, s, F.T, r, F.Tsp);
+}
+
 // ---- double-float arithmetic (unevaluated sums hi + lo of two floats, FMA-based)
 
 struct dflt {

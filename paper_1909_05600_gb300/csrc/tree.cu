@@ -97,9 +97,49 @@ __global__ void k_scan_down(const uint32_t *in, uint32_t *out, int64_t n, const 
     }
 }
 
+// The whole scan in one block, tile after tile with a running carry: one launch instead
+// of three for the many small scans of a plan.
+constexpr int64_t SCAN_SMALL = 16 * SCAN_TILE;
+__global__ void __launch_bounds__(SCAN_T) k_scan_small(const uint32_t *in, uint32_t *out, int64_t n,
+                                                       uint32_t *d_total) {
+    __shared__ uint32_t tile[SCAN_TILE];
+    __shared__ uint32_t sw[32];
+    __shared__ uint32_t tot;
+    uint32_t carry = 0;
+    for (int64_t base = 0; base < n; base += SCAN_TILE) {
+        for (int i = threadIdx.x; i < SCAN_TILE; i += SCAN_T) {
+            int64_t g = base + i;
+            tile[i] = g < n ? in[g] : 0;
+        }
+        __syncthreads();
+        uint32_t loc[SCAN_IPT];
+        uint32_t sum = 0;
+#pragma unroll
+        for (int j = 0; j < SCAN_IPT; ++j) {
+            loc[j] = sum;
+            sum += tile[threadIdx.x * SCAN_IPT + j];
+        }
+        uint32_t e = block_excl_scan(sum, sw, &tot) + carry;
+#pragma unroll
+        for (int j = 0; j < SCAN_IPT; ++j) tile[threadIdx.x * SCAN_IPT + j] = loc[j] + e;
+        __syncthreads();
+        for (int i = threadIdx.x; i < SCAN_TILE; i += SCAN_T) {
+            int64_t g = base + i;
+            if (g < n) out[g] = tile[i];
+        }
+        carry += tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && d_total) *d_total = carry;
+}
+
 void scan_u32(const uint32_t *in, uint32_t *out, int64_t n, uint32_t *d_total, Alloc &al, cudaStream_t s) {
     if (n <= 0) {
         if (d_total) FFM_CUDA(cudaMemsetAsync(d_total, 0, sizeof(uint32_t), s));
+        return;
+    }
+    if (n <= SCAN_SMALL) {
+        FFM_LAUNCH(k_scan_small, 1, SCAN_T, 0, s, in, out, n, d_total);
         return;
     }
     int64_t nb = cdiv(n, SCAN_TILE);
@@ -853,6 +893,68 @@ static uint2 *build_chunks(ffm_plan_s *p, const uint32_t *list, int64_t n, const
     return out;
 }
 
+// Admissible partners of each target box sorted by translation index (one warp per target,
+// bitonic sort of (translation, source) keys in shared memory; translations are distinct
+// within a target).  Targets with more than 512 partners are left as they are and flagged.
+__global__ void __launch_bounds__(128) k_sort_partners(const uint32_t *__restrict__ off, int64_t n_tgt,
+                                                       uint32_t *__restrict__ src, uint32_t *__restrict__ tr,
+                                                       int *__restrict__ too_long) {
+    __shared__ unsigned long long sk[4][512];
+    int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int64_t x = (int64_t)blockIdx.x * 4 + w;
+    if (x >= n_tgt) return;  // warp-level work only: no block barrier below
+    uint32_t e0 = off[x];
+    int n = (int)(off[x + 1] - e0);
+    if (n > 512) {
+        if (lane == 0) atomicOr(too_long, 1);
+        return;
+    }
+    int P = 32;
+    while (P < n) P <<= 1;
+    unsigned long long *k = sk[w];
+    for (int i = lane; i < P; i += 32)
+        k[i] = i < n ? ((unsigned long long)tr[e0 + i] << 32) | src[e0 + i] : ~0ull;
+    __syncwarp();
+    for (int size = 2; size <= P; size <<= 1)
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int i = lane; i < P; i += 32) {
+                int j = i ^ stride;
+                if (j > i) {
+                    bool up = (i & size) == 0;
+                    unsigned long long a = k[i], b = k[j];
+                    if ((a > b) == up) {
+                        k[i] = b;
+                        k[j] = a;
+                    }
+                }
+            }
+            __syncwarp();
+        }
+    for (int i = lane; i < n; i += 32) {
+        tr[e0 + i] = (uint32_t)(k[i] >> 32);
+        src[e0 + i] = (uint32_t)k[i];
+    }
+}
+
+// Data of the target-stationary transfer for Lagrange level l, made on demand (it is used
+// when forced or picked by the autotuner): partners sorted by translation within each
+// target (the sort keeps every other consumer of the CSR lists valid) and T_t pre-split.
+// Sets ts_ok if every target has at most 512 partners.
+void prepare_target_stationary(ffm_plan_s *p, int l, cudaStream_t s) {
+    FarLevel &F = p->far[l];
+    if (F.mode != 1 || F.n_adm == 0 || F.Tsp || p->kind != FFM_LAPLACE || F.r1 > 4) return;
+    Alloc tmp;
+    tmp.stream = s;
+    int *flag = tmp.get<int>(1);
+    FFM_CUDA(cudaMemsetAsync(flag, 0, sizeof(int), s));
+    FFM_LAUNCH(k_sort_partners, cdiv(F.n_tgt, 4), 128, 0, s, F.adm_off, F.n_tgt, F.adm_src, F.adm_t, flag);
+    launch_table_split(p, l, s);
+    int hflag = 1;
+    FFM_CUDA(cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+    FFM_CUDA(cudaStreamSynchronize(s));
+    F.ts_ok = hflag == 0;
+}
+
 static void finish_far_level(ffm_plan_s *p, int l, uint32_t *aa, uint32_t *ab, int64_t na, Alloc &tmp,
                              cudaStream_t s) {
     FarLevel &F = p->far[l];
@@ -906,6 +1008,8 @@ static void finish_far_level(ffm_plan_s *p, int l, uint32_t *aa, uint32_t *ab, i
     p->info.src_points[l] = read_u64(sums, s);
     p->info.tgt_points[l] = read_u64(sums + 1, s);
     if (F.mode == 1) {
+        F.r1 = p->r1_override > 0 ? p->r1_override : r1_rule(p->kind, p->eps);
+        if (p->lag_transfer > 0) F.tune_tc = p->lag_transfer - 1;  // forced variant
         // pairs grouped by translation for the transfer GEMMs, and the column tiles
         uint32_t *tk = tmp.get<uint32_t>(na), *pidx = tmp.get<uint32_t>(na);
         FFM_CUDA(cudaMemcpyAsync(tk, F.adm_t, sizeof(uint32_t) * na, cudaMemcpyDeviceToDevice, s));
@@ -1175,6 +1279,8 @@ void build_plan(ffm_plan_s *p, const void *X, ffm_dtype xdt, const void *Y, ffm_
     }
     for (int l = 0; l <= ls; ++l)
         if (p->far[l].n_adm > 0) build_octants(p, l, tj);
+    if (p->lag_transfer == 3)
+        for (int l = 0; l <= ls; ++l) prepare_target_stationary(p, l, s);
     FFM_CUDA(cudaStreamSynchronize(s));
 }
 

@@ -24,6 +24,8 @@ LAPLACE, HELMHOLTZ = 0, 1
 F32, F64, C64, C128 = 0, 1, 2, 3
 # plane-wave level arithmetic (ffm_precision)
 PREC_AUTO, PREC_F32, PREC_F32C, PREC_F64, PREC_F32X2 = 0, 1, 2, 3, 4
+# Lagrange transfer variants (ffm_opts.lagrange_transfer)
+LAG_DEFAULT, LAG_CUDA_CORES, LAG_TC_TRANSLATION, LAG_TC_TARGET = 0, 1, 2, 3
 EXPORT_PERM_X, EXPORT_PERM_Y, EXPORT_ADM, EXPORT_NEAR = 0, 1, 2, 3
 STATUS = {0: "FFM_OK", 1: "FFM_EINVAL", 2: "FFM_ENOMEM", 3: "FFM_ECUDA", 4: "FFM_ETIMEOUT", 5: "FFM_EUNSUPPORTED"}
 
@@ -43,7 +45,7 @@ class FFMError(RuntimeError):
 class Opts(C.Structure):
     _fields_ = [("n_leaf", C.c_int), ("l_cap", C.c_int), ("kappa_switch", C.c_double), ("r1_override", C.c_int),
                 ("precision", C.c_int), ("weights", C.c_void_p), ("weights_dtype", C.c_int),
-                ("autotune_cache", C.c_char_p)]
+                ("autotune_cache", C.c_char_p), ("lagrange_transfer", C.c_int)]
 
 
 class Info(C.Structure):
@@ -236,11 +238,12 @@ class Plan:
     """
 
     def __init__(self, X, Y, kernel, k=0.0, eps=1e-3, weights=None, stream=None, n_leaf=0, l_cap=0,
-                 kappa_switch=0.0, r1_override=0, precision=PREC_AUTO, autotune_cache=None):
+                 kappa_switch=0.0, r1_override=0, precision=PREC_AUTO, autotune_cache=None,
+                 lagrange_transfer=0):
         self._h = None
         self._keep = (X, Y, weights)
         o = Opts(n_leaf, l_cap, float(kappa_switch), r1_override, int(precision), None, F64,
-                 autotune_cache.encode() if autotune_cache else None)
+                 autotune_cache.encode() if autotune_cache else None, int(lagrange_transfer))
         if weights is not None:
             o.weights = _ptr(weights)
             o.weights_dtype = _dtype_code(weights)

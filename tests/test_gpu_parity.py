@@ -3,6 +3,8 @@
 Integer/index work (sorted permutations, box counts, pair lists, translation counts) must
 match the oracle bit for bit; floating-point results must match the plain CPU FFM to
 rel-L2 <= 1e-5 at the same eps and plan constants, and the FP64 direct sum to <= eps."""
+import functools
+
 import numpy as np
 import pytest
 
@@ -135,6 +137,26 @@ def test_mixed_levels_coincident_sets_eps_1e4():
     assert 1 in info["mode"] and 2 in info["mode"]
     ref = O.ffm(X, X, as_c128(u), O.HELMHOLTZ, k, 1e-4, w=prob.w)[:, 0]
     assert O.rel_l2(v, ref) < TOL_FFM
+
+
+@pytest.mark.parametrize("variant", [ffm.LAG_CUDA_CORES, ffm.LAG_TC_TRANSLATION, ffm.LAG_TC_TARGET])
+def test_lagrange_transfer_variants_match_the_oracle(variant):
+    """The three Lagrange transfer kernels (CUDA-core GEMM per translation, tcgen05 per
+    translation with atomic scatter, tcgen05 target-stationary accumulating every
+    translation of 128 target boxes) against the oracle FFM, on uneven clustered boxes."""
+    prob, ref = _clustered_reference()
+    with gpu_plan(prob, lagrange_transfer=variant) as gp:
+        info = gp.info()
+        v = gpu_apply(gp, prob.u)
+    lag = [l for l in range(info["l_stop"] + 1) if info["mode"][l] == 1 and info["n_adm"][l] > 0]
+    assert lag and all(info["tune_tc"][l] == variant - 1 for l in lag)
+    assert O.rel_l2(v, ref) < TOL_FFM
+
+
+@functools.lru_cache(maxsize=1)
+def _clustered_reference():
+    prob = W.laplace_clustered(40000, seed=4)
+    return prob, O.ffm(prob.X, prob.Y, prob.u, O.LAPLACE, 0.0, prob.eps, w=prob.w)[:, 0]
 
 
 def test_precision_modes_error_tracks_cancellation():
