@@ -201,33 +201,74 @@ def run_reference(args, rank):
     print(json.dumps(line), flush=True)
 
 
-def roofline(prof, info, steps, clk, pk, pk_kind):
-    """Dominant kernel of the timed region against its pipe.  Plane-wave transforms and
-    the Helmholtz near field are bound by the special-function (MUFU) pipe.  Algorithmic
-    MUFU work: a point-direction pair of a transform costs one MUFU op (one sin and one
-    cos serve a direction and its antipode, eq. 17's quadrature being symmetric); a
-    Helmholtz near pair costs three (rsqrt, sin, cos); a Laplace near pair one (rsqrt)."""
+def measured_traffic(kernel, workload):
+    """DRAM bytes per launch of `kernel` on `workload` from a committed ncu summary
+    (profiles/traffic_*.txt), or None when there is none or the kernel's source file has
+    changed since the counters were taken."""
+    import glob
+    import hashlib
+    for path in glob.glob(os.path.join(ROOT, "profiles", "traffic_*.txt")):
+        for line in open(path):
+            f = line.split()
+            if len(f) != 5 or line.startswith("#") or f[0] != kernel or f[1] != workload:
+                continue
+            src = os.path.join(ROOT, "paper_1909_05600_gb300", f[3])
+            try:
+                h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+            except OSError:
+                return None
+            return float(f[2]) if h == f[4] else None
+    return None
+
+
+def roofline(prof, info, steps, clk, pk, pk_kind, workload):
+    """Dominant kernel of the timed region against the pipe that bounds it.
+    - Plane-wave transforms and the Helmholtz near field: the special-function (MUFU)
+      pipe.  A point-direction pair of a transform costs one MUFU op (one sin and one cos
+      serve a direction and its antipode, eq. 17's quadrature being symmetric); a Helmholtz
+      near pair costs three (rsqrt, sin, cos).
+    - Laplace near field: instruction issue, at one rsqrt and about nine FP32 operations
+      per pair (10 issue slots).
+    - Lagrange transfer: tensor cores, 2 r^2 FLOP per admissible pair (the single-precision
+      GEMM; the TF32 hi/lo split triples the MMA work but not the algorithmic work), against
+      the measured BF16 peak times the nominal TF32/BF16 ratio (1.1 / 2.25)."""
     name, (nl, ms) = max(prof.items(), key=lambda kv: kv[1][1])
     mhz = pk.get("sm_max_mhz", 2070.0)
-    mufu_peak = SM_COUNT * MUFU_PER_SM_CLK * mhz * 1e6 / 1e12  # Tops/s
+    clk_hz = mhz * 1e6
     helm = any(m == 2 for m in info["mode"])
-    units = None
-    if "k_pw_forward" in name:
-        units = 1.0 * sum(info["src_points"][l] * info["nQ"][l] for l in range(22) if info["mode"][l] == 2)
-    elif "k_pw_backward" in name:
-        units = 1.0 * sum(info["tgt_points"][l] * info["nQ"][l] for l in range(22) if info["mode"][l] == 2)
+    out = {"kernel": name, "launches_per_step": nl / steps, "ms_per_step": ms / steps,
+           "traffic": measured_traffic(name, workload)}
+    per_s = lambda units: units * steps / (ms * 1e-3)
+    basis = "%d SMs x %%s x %.0f MHz (max SM clock, %s peaks file)" % (SM_COUNT, mhz, pk_kind)
+    if "k_pw_forward" in name or "k_pw_backward" in name:
+        key = "src_points" if "forward" in name else "tgt_points"
+        units = 1.0 * sum(info[key][l] * info["nQ"][l] for l in range(22) if info["mode"][l] == 2)
+        peak = SM_COUNT * MUFU_PER_SM_CLK * clk_hz
+        out.update({"bound": "alu", "pipe": "MUFU", "unit": "Tops/s", "units_per_step": units,
+                    "peak_basis": basis % ("%d MUFU results/clk" % MUFU_PER_SM_CLK)})
+    elif "k_p2p" in name and helm:
+        units = 3.0 * info["p2p_pairs"]
+        peak = SM_COUNT * MUFU_PER_SM_CLK * clk_hz
+        out.update({"bound": "alu", "pipe": "MUFU", "unit": "Tops/s", "units_per_step": units,
+                    "peak_basis": basis % ("%d MUFU results/clk" % MUFU_PER_SM_CLK)})
     elif "k_p2p" in name:
-        units = (3.0 if helm else 1.0) * info["p2p_pairs"]
-    out = {"kernel": name, "launches_per_step": nl / steps, "ms_per_step": ms / steps}
-    if units is None:
-        out.update({"bound": "alu", "achieved": None, "peak": None, "unit": None, "frac": None, "traffic": None})
+        units = 1.0 * info["p2p_pairs"]
+        peak = SM_COUNT * 128 * clk_hz / 10.0
+        out.update({"bound": "alu", "pipe": "FP32 issue (10 slots per pair)", "unit": "Tpairs/s",
+                    "units_per_step": units, "peak_basis": basis % "128 lanes/clk / 10"})
+    elif "k_lag_gemm" in name:
+        variant = 2 if "_ts" in name else 1 if "_tc" in name else 0
+        units = sum(2.0 * (info["r1"][l] ** 3) ** 2 * info["n_adm"][l] for l in range(22)
+                    if info["mode"][l] == 1 and info["tune_tc"][l] == variant)
+        peak = pk.get("bf16_tflops", 1900.0) * 1e12 * (1.1 / 2.25)
+        out.update({"bound": "tensor", "pipe": "TF32", "unit": "TFLOP/s", "units_per_step": units,
+                    "peak_basis": "measured BF16 %.1f TFLOP/s x 1.1/2.25 (%s peaks file)"
+                                  % (pk.get("bf16_tflops", 1900.0), pk_kind)})
+    else:
+        out.update({"bound": "alu", "achieved": None, "peak": None, "unit": None, "frac": None})
         return out
-    achieved = units * steps / (ms * 1e-3) / 1e12
-    out.update({"bound": "alu", "pipe": "MUFU", "achieved": achieved, "peak": mufu_peak, "unit": "Tops/s",
-                "frac": achieved / mufu_peak, "traffic": None,
-                "peak_basis": "%d SMs x %d MUFU results/clk x %.0f MHz (max SM clock, %s peaks file)"
-                              % (SM_COUNT, MUFU_PER_SM_CLK, mhz, pk_kind),
-                "units_per_step": units})
+    achieved = per_s(units) / 1e12
+    out.update({"achieved": achieved, "peak": peak / 1e12, "frac": achieved / (peak / 1e12)})
     return out
 
 
@@ -464,7 +505,7 @@ def main():
                          % (prob.Y.shape[0], len(t), nrhs, dt, prob.X.shape[0])}
 
     if rank == 0:
-        rl = roofline(prof, info, args.steps, clk, pk, pk_kind)
+        rl = roofline(prof, info, args.steps, clk, pk, pk_kind, args.workload)
         kernels = {k: {"launches_per_step": v[0] / args.steps, "ms_per_step": v[1] / args.steps}
                    for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}
         line = {
