@@ -1,8 +1,10 @@
 """Recompute the Lagrange rank table (plan constant): for each r1 the relative error of
 the tensor Chebyshev-Lagrange approximation of the kernel block between the closest
-admissible box pair (centre offset 2 d along one axis), for the Laplace kernel and for
-the Helmholtz kernel at k d = 2 (the oscillation switch).  The plan picks the smallest
-r1 whose tabulated error is <= eps.  Calls only the oracle.
+admissible box pair (centre offset 2 d along one axis), for the Laplace kernel, for
+the Helmholtz kernel at k d = 2 (the oscillation switch) and for the Laplace double
+layer (normal derivative of the interpolant in the source variable, fixed unit
+normals).  The plan picks the smallest r1 whose tabulated error is <= eps.  Calls only
+the oracle.
 
 Usage: python -m oracle.calibrate_r1
 """
@@ -13,7 +15,8 @@ from . import oracle as O
 
 def calibrate():
     rows = {}
-    for name, kind, k in (("laplace", O.LAPLACE, 0.0), ("helmholtz_kd2", O.HELMHOLTZ, 2.0)):
+    for name, kind, k in (("laplace", O.LAPLACE, 0.0), ("helmholtz_kd2", O.HELMHOLTZ, 2.0),
+                          ("laplace_double_layer", O.LAPLACE_DL, 0.0)):
         rows[name] = [O.lagrange_block_err(kind, k, r1, 1.0) for r1 in range(2, 11)]
     return rows
 

@@ -43,7 +43,7 @@
 #define ORC_LMAX 21
 #define ORC_PI 3.14159265358979323846
 
-enum { ORC_LAPLACE = 0, ORC_HELMHOLTZ = 1, ORC_POLY = 2 };
+enum { ORC_LAPLACE = 0, ORC_HELMHOLTZ = 1, ORC_POLY = 2, ORC_LAPLACE_DL = 3 };
 enum { ORC_OK = 0, ORC_EINVAL = 1, ORC_ENOMEM = 2 };
 enum { ORC_MODE_NONE = 0, ORC_MODE_LAGRANGE = 1, ORC_MODE_PLANEWAVE = 2 };
 
@@ -59,7 +59,8 @@ static double poly_kernel(double dx, double dy, double dz)
 
 /* G(x - y) for the Laplace kernel 1/(4 pi r) (eq. 19), the Helmholtz kernel
  * e^{ikr}/(4 pi r) (eq. 9), or the polynomial test kernel. r = 0 gives 0 for the
- * singular kernels. */
+ * singular kernels.  The double-layer kind is built on the Laplace G: its transfer
+ * operators are those of G, its source step differentiates the interpolant. */
 static void orc_kernel(int kind, double k, double dx, double dy, double dz, double *gr, double *gi)
 {
     if (kind == ORC_POLY) {
@@ -74,7 +75,7 @@ static void orc_kernel(int kind, double k, double dx, double dy, double dz, doub
         return;
     }
     double a = 1.0 / (4.0 * ORC_PI * r);
-    if (kind == ORC_LAPLACE) {
+    if (kind == ORC_LAPLACE || kind == ORC_LAPLACE_DL) {
         *gr = a;
         *gi = 0.0;
     } else {
@@ -136,6 +137,36 @@ int orc_direct(const double *X, int64_t nx, const double *Y, int64_t ny, const d
             }
             vre[s + nt * m] = ar;
             vim[s + nt * m] = ai;
+        }
+    }
+    return ORC_OK;
+}
+
+/* Double-layer direct sum: v_i = sum_j w_j u_j dG/dn_y(x_i - y_j) with the Laplace G,
+ * dG/dn_y = n_j . (x_i - y_j) / (4 pi |x_i - y_j|^3); pairs at distance 0 contribute 0.
+ * nrm: ny*3 row-major source normals (any length: the kernel is linear in n).  Real
+ * densities u (ny*nrhs column-major); v: nsel*nrhs (all nx targets if tsel is NULL). */
+int orc_direct_dl(const double *X, int64_t nx, const double *Y, int64_t ny, const double *nrm, const double *w,
+                  const double *u, int nrhs, const int64_t *tsel, int64_t nsel, double *v)
+{
+    if (nx < 0 || ny < 0 || nrhs < 1 || !nrm) return ORC_EINVAL;
+    int64_t nt = tsel ? nsel : nx;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t s = 0; s < nt; ++s) {
+        int64_t i = tsel ? tsel[s] : s;
+        const double *x = X + 3 * i;
+        for (int m = 0; m < nrhs; ++m) {
+            double acc = 0.0;
+            for (int64_t j = 0; j < ny; ++j) {
+                double d0 = x[0] - Y[3 * j], d1 = x[1] - Y[3 * j + 1], d2 = x[2] - Y[3 * j + 2];
+                double r2 = d0 * d0 + d1 * d1 + d2 * d2;
+                if (r2 == 0.0) continue;
+                double r = sqrt(r2);
+                double nd = nrm[3 * j] * d0 + nrm[3 * j + 1] * d1 + nrm[3 * j + 2] * d2;
+                double wj = w ? w[j] : 1.0;
+                acc += wj * u[j + ny * m] * nd / (4.0 * ORC_PI * r2 * r);
+            }
+            v[s + nt * m] = acc;
         }
     }
     return ORC_OK;
@@ -301,10 +332,16 @@ int orc_admissible(const double sigma[3], int l, const int64_t m[3])
  * values come from orc_lagrange_block_err (see oracle/calibrate_r1.py), rounded up. */
 static const double ORC_R1_ERR_LAPLACE[11] = {1, 1, 3.2e-2, 4.8e-3, 7.6e-4, 1.1e-4, 1.6e-5, 2.0e-6, 2.4e-7, 8.1e-8, 1.1e-8};
 static const double ORC_R1_ERR_HELM[11] = {1, 1, 2.4e-1, 3.4e-2, 3.6e-3, 3.6e-4, 4.0e-5, 3.9e-6, 3.9e-7, 1.3e-7, 1.4e-8};
+static const double ORC_R1_ERR_LAPLACE_DL[11] = {1, 1, 3.5e-1, 5.3e-2, 9.3e-3, 1.6e-3, 3.4e-4, 7.2e-5, 1.1e-5, 1.4e-6, 4.3e-7};
+
+static const double *r1_table(int kind)
+{
+    return kind == ORC_HELMHOLTZ ? ORC_R1_ERR_HELM : kind == ORC_LAPLACE_DL ? ORC_R1_ERR_LAPLACE_DL : ORC_R1_ERR_LAPLACE;
+}
 
 int orc_r1_rule(int kind, double eps)
 {
-    const double *tab = (kind == ORC_HELMHOLTZ) ? ORC_R1_ERR_HELM : ORC_R1_ERR_LAPLACE;
+    const double *tab = r1_table(kind);
     for (int r1 = 2; r1 <= 10; ++r1)
         if (tab[r1] <= eps) return r1;
     return 10;
@@ -312,8 +349,7 @@ int orc_r1_rule(int kind, double eps)
 
 void orc_r1_table(int kind, double *out11)
 {
-    const double *tab = (kind == ORC_HELMHOLTZ) ? ORC_R1_ERR_HELM : ORC_R1_ERR_LAPLACE;
-    memcpy(out11, tab, sizeof(double) * 11);
+    memcpy(out11, r1_table(kind), sizeof(double) * 11);
 }
 
 /* First-kind Chebyshev nodes t_a = cos((2a+1) pi / (2 r1)). */
@@ -346,6 +382,53 @@ static void lagrange_3d(int r1, const double *t, const double *x, const double *
             for (int e = 0; e < r1; ++e) L[(a * r1 + b) * r1 + e] = lx[a] * ly[b] * lz[e];
 }
 
+/* Derivatives of the 1-D Lagrange polynomials at xi:
+ * l'_a(xi) = sum_{c != a} 1/(t_a - t_c) prod_{b != a, c} (xi - t_b)/(t_a - t_b). */
+static void lagrange_1d_deriv(int r1, const double *t, double xi, double *dl)
+{
+    for (int a = 0; a < r1; ++a) {
+        double s = 0.0;
+        for (int c = 0; c < r1; ++c) {
+            if (c == a) continue;
+            double v = 1.0 / (t[a] - t[c]);
+            for (int b = 0; b < r1; ++b)
+                if (b != a && b != c) v *= (xi - t[b]) / (t[a] - t[b]);
+            s += v;
+        }
+        dl[a] = s;
+    }
+}
+
+/* The 1-D basis and its derivative at xi on the r1 Chebyshev nodes (for tests). */
+void orc_lagrange_1d(int r1, double xi, double *l, double *dl)
+{
+    double t[16];
+    cheb_nodes(r1, t);
+    lagrange_1d(r1, t, xi, l);
+    lagrange_1d_deriv(r1, t, xi, dl);
+}
+
+/* Gradient of the tensor basis at x (box centre c, edge d): G[3 q + axis], q over
+ * (a*r1 + b)*r1 + c as in lagrange_3d; d/dx = (2/d) d/dxi. */
+static void lagrange_3d_grad(int r1, const double *t, const double *x, const double *c, double d, double *G)
+{
+    double l[3][16], dl[3][16];
+    for (int ax = 0; ax < 3; ++ax) {
+        double xi = (x[ax] - c[ax]) / (0.5 * d);
+        lagrange_1d(r1, t, xi, l[ax]);
+        lagrange_1d_deriv(r1, t, xi, dl[ax]);
+    }
+    double sc = 2.0 / d;
+    for (int a = 0; a < r1; ++a)
+        for (int b = 0; b < r1; ++b)
+            for (int e = 0; e < r1; ++e) {
+                int q = (a * r1 + b) * r1 + e;
+                G[3 * q] = sc * dl[0][a] * l[1][b] * l[2][e];
+                G[3 * q + 1] = sc * l[0][a] * dl[1][b] * l[2][e];
+                G[3 * q + 2] = sc * l[0][a] * l[1][b] * dl[2][e];
+            }
+}
+
 /* Relative Frobenius error of the Lagrange approximation L_X^T T L_Y of the kernel
  * block between two boxes of edge d whose centres differ by (2d, 0, 0) (the closest
  * admissible pair), sampled on a 6x6x6 grid of points in each box. */
@@ -369,9 +452,22 @@ double orc_lagrange_block_err(int kind, double k, int r1, double d)
                     py[3 * q + dd] = cy[dd] + o[dd] * 0.93;
                 }
             }
+    /* double layer: source j carries a fixed unit normal; its basis row is n_j . grad L */
+    double *nj = (double *)malloc(sizeof(double) * 3 * np), *Gy = (double *)malloc(sizeof(double) * 3 * r);
+    for (int j = 0; j < np; ++j) {
+        double v[3] = {sin(1.3 * j + 0.2), cos(2.1 * j), sin(0.7 * j + 1.0)};
+        double nn = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+        for (int dd = 0; dd < 3; ++dd) nj[3 * j + dd] = v[dd] / nn;
+    }
     for (int i = 0; i < np; ++i) {
         lagrange_3d(r1, t, px + 3 * i, cx, d, LX + (size_t)i * r);
-        lagrange_3d(r1, t, py + 3 * i, cy, d, LY + (size_t)i * r);
+        if (kind == ORC_LAPLACE_DL) {
+            lagrange_3d_grad(r1, t, py + 3 * i, cy, d, Gy);
+            for (int a = 0; a < r; ++a)
+                LY[(size_t)i * r + a] = nj[3 * i] * Gy[3 * a] + nj[3 * i + 1] * Gy[3 * a + 1] + nj[3 * i + 2] * Gy[3 * a + 2];
+        } else {
+            lagrange_3d(r1, t, py + 3 * i, cy, d, LY + (size_t)i * r);
+        }
     }
     for (int a = 0; a < r; ++a) {
         int ax = a / (r1 * r1), ay = (a / r1) % r1, az = a % r1;
@@ -402,7 +498,14 @@ double orc_lagrange_block_err(int kind, double k, int r1, double d)
                 si += LX[(size_t)i * r + a] * Mi[(size_t)a * np + j];
             }
             double gr, gi;
-            orc_kernel(kind, k, px[3 * i] - py[3 * j], px[3 * i + 1] - py[3 * j + 1], px[3 * i + 2] - py[3 * j + 2], &gr, &gi);
+            double dx = px[3 * i] - py[3 * j], dy = px[3 * i + 1] - py[3 * j + 1], dz = px[3 * i + 2] - py[3 * j + 2];
+            if (kind == ORC_LAPLACE_DL) {
+                double r2 = dx * dx + dy * dy + dz * dz;
+                gr = (nj[3 * j] * dx + nj[3 * j + 1] * dy + nj[3 * j + 2] * dz) / (4.0 * ORC_PI * r2 * sqrt(r2));
+                gi = 0.0;
+            } else {
+                orc_kernel(kind, k, dx, dy, dz, &gr, &gi);
+            }
             num += (sr - gr) * (sr - gr) + (si - gi) * (si - gi);
             den += gr * gr + gi * gi;
         }
@@ -414,6 +517,8 @@ double orc_lagrange_block_err(int kind, double k, int r1, double d)
     free(Ti);
     free(Mr);
     free(Mi);
+    free(nj);
+    free(Gy);
     return sqrt(num / den);
 }
 
@@ -857,8 +962,13 @@ static void box_centre(const double o[3], const int64_t g[3], double dl, double 
 /* Far field of level l (Lagrange, Sec. 2.2.2): u~_b = L_Y(b) (w u)_b for every source
  * box, v~_a = sum_b T_ab u~_b with T_ab computed from its definition for each pair,
  * v_a += L_X(a)^T v~_a. acc: sorted-order accumulators (nx*nrhs). */
-static void far_lagrange(const orc_plan *p, int l, const double *qr, const double *qi, int nrhs, double *accr,
-                         double *acci)
+/* Far field of a Lagrange level (Sec. 2.2.2, eq. 8): source step L_Y (w u) per source
+ * box, transfer T per admissible pair (kernel at the control nodes, evaluated for each
+ * pair), target step L_X^T per target box.  With qv (double layer, 3-vector densities
+ * w u n per source, qv[3 (j + ny m) + axis]) the source step applies the normal
+ * derivative of the interpolant, sum_j (w u n)_j . grad L(y_j). */
+static void far_lagrange(const orc_plan *p, int l, const double *qr, const double *qi, const double *qv, int nrhs,
+                         double *accr, double *acci)
 {
     int r1 = p->st.r1[l], r = r1 * r1 * r1;
     double t[16];
@@ -871,9 +981,19 @@ static void far_lagrange(const orc_plan *p, int l, const double *qr, const doubl
 #pragma omp parallel for schedule(dynamic, 1)
     for (int64_t b = 0; b < nbY; ++b) {
         const obox *B = &p->by[l][b];
-        double c[3], Lb[1000];
+        double c[3], Lb[1000], Gb[3000];
         box_centre(p->ty.o, B->g, dl, c);
         for (int64_t j = B->s; j < B->e; ++j) {
+            if (qv) {
+                lagrange_3d_grad(r1, t, p->ty.p + 3 * j, c, dl, Gb);
+                for (int m = 0; m < nrhs; ++m) {
+                    const double *q3 = qv + 3 * (j + ny * m);
+                    for (int a = 0; a < r; ++a)
+                        utr[((size_t)b * nrhs + m) * r + a] +=
+                            Gb[3 * a] * q3[0] + Gb[3 * a + 1] * q3[1] + Gb[3 * a + 2] * q3[2];
+                }
+                continue;
+            }
             lagrange_3d(r1, t, p->ty.p + 3 * j, c, dl, Lb);
             for (int m = 0; m < nrhs; ++m)
                 for (int a = 0; a < r; ++a) {
@@ -1055,7 +1175,10 @@ static void far_planewave(const orc_plan *p, int l, const double *qr, const doub
 
 /* Near field at the stop level (Sec. 2.2.4): the dense product over the remaining
  * non-admissible leaf pairs. */
-static void near_field(const orc_plan *p, const double *qr, const double *qi, int nrhs, double *accr, double *acci)
+/* Near field at the stop level (Sec. 2.2.4): the direct sum over the near leaf pairs.
+ * With qv (double layer): sum_j (w u n)_j . (x - y_j) / (4 pi |x - y_j|^3). */
+static void near_field(const orc_plan *p, const double *qr, const double *qi, const double *qv, int nrhs,
+                       double *accr, double *acci)
 {
     int l = p->st.l_stop;
     int64_t nbX = p->nbx[l], nn = p->n_nearp, nx = p->tx.n, ny = p->ty.n;
@@ -1079,6 +1202,14 @@ static void near_field(const orc_plan *p, const double *qr, const double *qi, in
                     const obox *B = &p->by[l][pr[e].b];
                     for (int64_t j = B->s; j < B->e; ++j) {
                         const double *y = p->ty.p + 3 * j;
+                        if (qv) {
+                            double d0 = x[0] - y[0], d1 = x[1] - y[1], d2 = x[2] - y[2];
+                            double r2 = d0 * d0 + d1 * d1 + d2 * d2;
+                            if (r2 == 0.0) continue;
+                            const double *q3 = qv + 3 * (j + ny * m);
+                            sr += (q3[0] * d0 + q3[1] * d1 + q3[2] * d2) / (4.0 * ORC_PI * r2 * sqrt(r2));
+                            continue;
+                        }
                         double gr, gi;
                         orc_kernel(p->kind, p->k, x[0] - y[0], x[1] - y[1], x[2] - y[2], &gr, &gi);
                         double ur = qr[j + ny * m], ui = qi[j + ny * m];
@@ -1123,11 +1254,11 @@ int orc_apply(const orc_plan *p, const double *w, const double *ure, const doubl
     for (int l = 0; l <= ORC_LMAX; ++l) {
         if (p->st.n_adm[l] == 0) continue;
         if (p->st.mode[l] == ORC_MODE_LAGRANGE)
-            far_lagrange(p, l, qr, qi, nrhs, accr, acci);
+            far_lagrange(p, l, qr, qi, NULL, nrhs, accr, acci);
         else
             far_planewave(p, l, qr, qi, nrhs, accr, acci);
     }
-    if (p->n_nearp > 0) near_field(p, qr, qi, nrhs, accr, acci);
+    if (p->n_nearp > 0) near_field(p, qr, qi, NULL, nrhs, accr, acci);
     for (int m = 0; m < nrhs; ++m)
         for (int64_t i = 0; i < nx; ++i) {
             int64_t o = p->tx.perm[i];
@@ -1136,6 +1267,43 @@ int orc_apply(const orc_plan *p, const double *w, const double *ure, const doubl
         }
     free(qr);
     free(qi);
+    free(accr);
+    free(acci);
+    return ORC_OK;
+}
+
+/* Double-layer product by the FFM for a plan built with kind ORC_LAPLACE_DL: the
+ * densities w u n (nrm: ny*3 row-major normals in the caller's order) go through the
+ * derivative source step of every Lagrange level and the double-layer near field; real
+ * u and v, column-major per RHS, caller's order. */
+int orc_apply_dl(const orc_plan *p, const double *nrm, const double *w, const double *u, int nrhs, double *v)
+{
+    if (!p || !nrm || nrhs < 1 || p->kind != ORC_LAPLACE_DL) return ORC_EINVAL;
+    int64_t nx = p->tx.n, ny = p->ty.n;
+    double *qv = (double *)malloc(sizeof(double) * 3 * ny * nrhs);
+    double *zero = (double *)calloc((size_t)ny * nrhs, sizeof(double));
+    double *accr = (double *)calloc((size_t)nx * nrhs, sizeof(double));
+    double *acci = (double *)calloc((size_t)nx * nrhs, sizeof(double));
+    if (!qv || !zero || !accr || !acci) {
+        free(qv);
+        free(zero);
+        free(accr);
+        free(acci);
+        return ORC_ENOMEM;
+    }
+    for (int m = 0; m < nrhs; ++m)
+        for (int64_t j = 0; j < ny; ++j) {
+            int64_t o = p->ty.perm[j];
+            double s = (w ? w[o] : 1.0) * u[o + ny * m];
+            for (int ax = 0; ax < 3; ++ax) qv[3 * (j + ny * m) + ax] = s * nrm[3 * o + ax];
+        }
+    for (int l = 0; l <= ORC_LMAX; ++l)
+        if (p->st.n_adm[l] > 0) far_lagrange(p, l, zero, zero, qv, nrhs, accr, acci);
+    if (p->n_nearp > 0) near_field(p, zero, zero, qv, nrhs, accr, acci);
+    for (int m = 0; m < nrhs; ++m)
+        for (int64_t i = 0; i < nx; ++i) v[p->tx.perm[i] + nx * m] = accr[i + nx * m];
+    free(qv);
+    free(zero);
     free(accr);
     free(acci);
     return ORC_OK;

@@ -12,7 +12,7 @@ import numpy as np
 
 from . import build as _build
 
-LAPLACE, HELMHOLTZ, POLY = 0, 1, 2
+LAPLACE, HELMHOLTZ, POLY, LAPLACE_DL = 0, 1, 2, 3
 MODE_NONE, MODE_LAGRANGE, MODE_PLANEWAVE = 0, 1, 2
 LMAX = 21
 
@@ -80,6 +80,11 @@ def lib():
         L.orc_gegenbauer.argtypes = [C.c_double, _dp, C.c_int, _dp, _dp, _dp]
         L.orc_pw_pair.argtypes = [C.c_double, C.c_int, _dp, _dp, _dp, _dp, _dp, _dp]
         L.orc_kernel_eval.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double, C.c_double, _dp, _dp]
+        L.orc_direct_dl.argtypes = [_dp, C.c_int64, _dp, C.c_int64, _dp, _dp, _dp, C.c_int, _i64p, C.c_int64, _dp]
+        L.orc_direct_dl.restype = C.c_int
+        L.orc_apply_dl.argtypes = [C.c_void_p, _dp, _dp, _dp, C.c_int, _dp]
+        L.orc_apply_dl.restype = C.c_int
+        L.orc_lagrange_1d.argtypes = [C.c_int, C.c_double, _dp, _dp]
         L.orc_nthreads.restype = C.c_int
         L.orc_set_threads.argtypes = [C.c_int]
         _lib = L
@@ -184,6 +189,17 @@ class Plan:
         lib().orc_plan_perm(self._h, 0 if which == "X" else 1, out.ctypes.data_as(_i64p))
         return out
 
+    def apply_dl(self, u, nrm, w=None):
+        """Double-layer product (plan built with kind LAPLACE_DL): real u, source normals nrm."""
+        re, _, nrhs = _split_u(u)
+        nrm = _c64(nrm).reshape(-1, 3)
+        w = None if w is None else _c64(w)
+        v = np.zeros((self.nx, nrhs), order="F")
+        rc = lib().orc_apply_dl(self._h, _d(nrm), _d(w), _d(re), nrhs, _d(v))
+        if rc:
+            raise ValueError("orc_apply_dl failed: %d" % rc)
+        return v
+
     def apply(self, u, w=None):
         re, im, nrhs = _split_u(u)
         w = None if w is None else _c64(w)
@@ -193,6 +209,43 @@ class Plan:
         if rc:
             raise ValueError("orc_apply failed: %d" % rc)
         return vr + 1j * vi
+
+
+def direct_dl(X, Y, nrm, u, w=None, targets=None):
+    """O1 for the double layer: v_i = sum_j w_j u_j n_j.(x_i - y_j) / (4 pi |x_i - y_j|^3),
+    real, shape (n, nrhs)."""
+    X = _c64(X).reshape(-1, 3)
+    Y = _c64(Y).reshape(-1, 3)
+    nrm = _c64(nrm).reshape(-1, 3)
+    re, _, nrhs = _split_u(u)
+    w = None if w is None else _c64(w)
+    if targets is None:
+        tsel, nt = None, X.shape[0]
+    else:
+        tsel = np.ascontiguousarray(targets, dtype=np.int64)
+        nt = tsel.shape[0]
+    v = np.zeros((nt, nrhs), order="F")
+    rc = lib().orc_direct_dl(_d(X), X.shape[0], _d(Y), Y.shape[0], _d(nrm), _d(w), _d(re), nrhs,
+                             tsel.ctypes.data_as(_i64p) if tsel is not None else None, nt, _d(v))
+    if rc:
+        raise ValueError("orc_direct_dl failed: %d" % rc)
+    return v
+
+
+def ffm_dl(X, Y, nrm, u, eps=1e-3, w=None, **opts):
+    p = Plan(X, Y, LAPLACE_DL, 0.0, eps, **opts)
+    try:
+        return p.apply_dl(u, nrm, w)
+    finally:
+        p.close()
+
+
+def lagrange_1d(r1, xi):
+    """(values, derivatives) of the r1 1-D Lagrange polynomials on Chebyshev nodes at xi."""
+    l = np.zeros(r1)
+    dl = np.zeros(r1)
+    lib().orc_lagrange_1d(int(r1), float(xi), _d(l), _d(dl))
+    return l, dl
 
 
 def ffm(X, Y, u, kind, k=0.0, eps=1e-3, w=None, **opts):

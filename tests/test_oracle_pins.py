@@ -176,12 +176,77 @@ def test_plane_wave_series_from_p1_misses_eps():
 def test_r1_table_matches_calibration():
     from oracle.calibrate_r1 import calibrate, round_up
     cal = calibrate()
-    for name, kind in (("laplace", O.LAPLACE), ("helmholtz_kd2", O.HELMHOLTZ)):
+    for name, kind in (("laplace", O.LAPLACE), ("helmholtz_kd2", O.HELMHOLTZ),
+                       ("laplace_double_layer", O.LAPLACE_DL)):
         tab = O.r1_table(kind)
         for r1, e in zip(range(2, 11), cal[name]):
             assert tab[r1] == pytest.approx(round_up(e), rel=1e-12)
     assert O.r1_rule(O.LAPLACE, 1e-3) == 4
     assert O.r1_rule(O.LAPLACE, 1e-4) == 6
+    assert O.r1_rule(O.LAPLACE_DL, 1e-3) == 6
+    assert O.r1_rule(O.LAPLACE_DL, 1e-4) == 7
+
+
+# ---- double layer: dG/dn_y with the Laplace G, through the Lagrange path (derivative of the
+# interpolant in the source variable)
+
+def _sphere_grid(L):
+    n = 2 * L * (L + 1)
+    s = np.zeros((n, 3))
+    w = np.zeros(n)
+    O.lib().orc_sphere_quad(L, s.ctypes.data_as(O._dp), w.ctypes.data_as(O._dp))
+    return s, w
+
+
+def test_double_layer_gauss_law():
+    """Gauss: the double-layer potential of the unit density on the unit sphere (outward
+    normals) is -1 inside and 0 outside, to quadrature accuracy away from the sphere."""
+    s, w = _sphere_grid(40)
+    inside = np.array([[0.1, 0.2, -0.3], [0.0, 0.0, 0.0], [-0.4, 0.3, 0.35]])
+    outside = np.array([[1.5, 0.3, 0.2], [0.0, -2.0, 0.5], [3.0, 3.0, -3.0]])
+    v_in = O.direct_dl(inside, s, s, np.ones(len(w)), w=w)[:, 0]
+    v_out = O.direct_dl(outside, s, s, np.ones(len(w)), w=w)[:, 0]
+    assert np.max(np.abs(v_in + 1.0)) < 1e-9
+    assert np.max(np.abs(v_out)) < 1e-9
+
+
+def test_double_layer_is_the_normal_derivative_of_the_laplace_kernel():
+    """Central differences of the Laplace direct sum in the source position along n."""
+    rng = np.random.default_rng(21)
+    for _ in range(5):
+        x = rng.standard_normal((1, 3))
+        y = rng.standard_normal((1, 3))
+        n = rng.standard_normal((1, 3))
+        h = 1e-5
+        g = lambda yy: O.direct(x, yy, np.ones(1), O.LAPLACE)[0, 0].real
+        fd = (g(y + h * n) - g(y - h * n)) / (2 * h)
+        assert O.direct_dl(x, y, n, np.ones(1))[0, 0] == pytest.approx(fd, rel=1e-7)
+
+
+def test_lagrange_basis_derivative_is_exact_on_polynomials():
+    """sum_a p(t_a) l'_a(xi) = p'(xi) for polynomials of degree < r1."""
+    rng = np.random.default_rng(5)
+    P = np.polynomial.polynomial
+    for r1 in range(2, 11):
+        c = rng.standard_normal(r1)
+        t = np.cos((2 * np.arange(r1) + 1) * np.pi / (2 * r1))
+        for xi in (-0.93, -0.2, 0.37, 0.99):
+            l, dl = O.lagrange_1d(r1, xi)
+            assert dl @ P.polyval(t, c) == pytest.approx(P.polyval(xi, P.polyder(c)), abs=1e-9)
+            assert l @ P.polyval(t, c) == pytest.approx(P.polyval(xi, c), abs=1e-12)
+
+
+@pytest.mark.parametrize("eps", [1e-3, 1e-4])
+def test_double_layer_ffm_within_eps(eps):
+    """O2 for the double layer against O1 on a sphere with outward normals."""
+    n = 12000
+    X = W.sphere_surface(n, 1)
+    Y = W.sphere_surface(n, 1001)
+    u = np.random.default_rng(3).standard_normal(n)
+    w = np.full(n, 4 * np.pi / n)
+    v = O.ffm_dl(X, Y, Y, u, eps, w=w)[:, 0]
+    ref = O.direct_dl(X, Y, Y, u, w=w)[:, 0]
+    assert O.rel_l2(v, ref) < eps
 
 
 def test_morton_interleave():
