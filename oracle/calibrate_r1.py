@@ -2,7 +2,7 @@
 the tensor Chebyshev-Lagrange approximation of the kernel block between the closest
 admissible box pair (centre offset 2 d along one axis), for the Laplace kernel, for
 the Helmholtz kernel at k d = 2 (the oscillation switch) and for the Laplace double
-layer (normal derivative of the interpolant in the source variable, fixed unit
+layer (its component kernels dG/dy_d interpolated on their own, weighted by fixed unit
 normals).  The plan picks the smallest r1 whose tabulated error is <= eps.  Calls only
 the oracle.
 

@@ -332,7 +332,7 @@ int orc_admissible(const double sigma[3], int l, const int64_t m[3])
  * values come from orc_lagrange_block_err (see oracle/calibrate_r1.py), rounded up. */
 static const double ORC_R1_ERR_LAPLACE[11] = {1, 1, 3.2e-2, 4.8e-3, 7.6e-4, 1.1e-4, 1.6e-5, 2.0e-6, 2.4e-7, 8.1e-8, 1.1e-8};
 static const double ORC_R1_ERR_HELM[11] = {1, 1, 2.4e-1, 3.4e-2, 3.6e-3, 3.6e-4, 4.0e-5, 3.9e-6, 3.9e-7, 1.3e-7, 1.4e-8};
-static const double ORC_R1_ERR_LAPLACE_DL[11] = {1, 1, 3.5e-1, 5.3e-2, 9.3e-3, 1.6e-3, 3.4e-4, 7.2e-5, 1.1e-5, 1.4e-6, 4.3e-7};
+static const double ORC_R1_ERR_LAPLACE_DL[11] = {1, 1, 1.2e-1, 2.4e-2, 5.1e-3, 1.1e-3, 1.8e-4, 2.6e-5, 3.9e-6, 1.5e-6, 2.0e-7};
 
 static const double *r1_table(int kind)
 {
@@ -382,53 +382,6 @@ static void lagrange_3d(int r1, const double *t, const double *x, const double *
             for (int e = 0; e < r1; ++e) L[(a * r1 + b) * r1 + e] = lx[a] * ly[b] * lz[e];
 }
 
-/* Derivatives of the 1-D Lagrange polynomials at xi:
- * l'_a(xi) = sum_{c != a} 1/(t_a - t_c) prod_{b != a, c} (xi - t_b)/(t_a - t_b). */
-static void lagrange_1d_deriv(int r1, const double *t, double xi, double *dl)
-{
-    for (int a = 0; a < r1; ++a) {
-        double s = 0.0;
-        for (int c = 0; c < r1; ++c) {
-            if (c == a) continue;
-            double v = 1.0 / (t[a] - t[c]);
-            for (int b = 0; b < r1; ++b)
-                if (b != a && b != c) v *= (xi - t[b]) / (t[a] - t[b]);
-            s += v;
-        }
-        dl[a] = s;
-    }
-}
-
-/* The 1-D basis and its derivative at xi on the r1 Chebyshev nodes (for tests). */
-void orc_lagrange_1d(int r1, double xi, double *l, double *dl)
-{
-    double t[16];
-    cheb_nodes(r1, t);
-    lagrange_1d(r1, t, xi, l);
-    lagrange_1d_deriv(r1, t, xi, dl);
-}
-
-/* Gradient of the tensor basis at x (box centre c, edge d): G[3 q + axis], q over
- * (a*r1 + b)*r1 + c as in lagrange_3d; d/dx = (2/d) d/dxi. */
-static void lagrange_3d_grad(int r1, const double *t, const double *x, const double *c, double d, double *G)
-{
-    double l[3][16], dl[3][16];
-    for (int ax = 0; ax < 3; ++ax) {
-        double xi = (x[ax] - c[ax]) / (0.5 * d);
-        lagrange_1d(r1, t, xi, l[ax]);
-        lagrange_1d_deriv(r1, t, xi, dl[ax]);
-    }
-    double sc = 2.0 / d;
-    for (int a = 0; a < r1; ++a)
-        for (int b = 0; b < r1; ++b)
-            for (int e = 0; e < r1; ++e) {
-                int q = (a * r1 + b) * r1 + e;
-                G[3 * q] = sc * dl[0][a] * l[1][b] * l[2][e];
-                G[3 * q + 1] = sc * l[0][a] * dl[1][b] * l[2][e];
-                G[3 * q + 2] = sc * l[0][a] * l[1][b] * dl[2][e];
-            }
-}
-
 /* Relative Frobenius error of the Lagrange approximation L_X^T T L_Y of the kernel
  * block between two boxes of edge d whose centres differ by (2d, 0, 0) (the closest
  * admissible pair), sampled on a 6x6x6 grid of points in each box. */
@@ -438,10 +391,15 @@ double orc_lagrange_block_err(int kind, double k, int r1, double d)
     double t[16];
     cheb_nodes(r1, t);
     double cx[3] = {2.0 * d, 0.0, 0.0}, cy[3] = {0.0, 0.0, 0.0};
+    /* the double layer n . grad_y G is three interpolated component kernels dG/dy_e,
+     * weighted by the source's normal (a fixed unit vector per sample point) */
+    int nc = kind == ORC_LAPLACE_DL ? 3 : 1;
     double *px = (double *)malloc(sizeof(double) * 3 * np), *py = (double *)malloc(sizeof(double) * 3 * np);
+    double *nj = (double *)malloc(sizeof(double) * 3 * np);
     double *LX = (double *)malloc(sizeof(double) * np * r), *LY = (double *)malloc(sizeof(double) * np * r);
     double *Tr = (double *)malloc(sizeof(double) * r * r), *Ti = (double *)malloc(sizeof(double) * r * r);
     double *Mr = (double *)malloc(sizeof(double) * np * r), *Mi = (double *)malloc(sizeof(double) * np * r);
+    double *Ar = (double *)calloc((size_t)np * np, sizeof(double)), *Ai = (double *)calloc((size_t)np * np, sizeof(double));
     int q = 0;
     for (int a = 0; a < ng; ++a)
         for (int b = 0; b < ng; ++b)
@@ -452,73 +410,82 @@ double orc_lagrange_block_err(int kind, double k, int r1, double d)
                     py[3 * q + dd] = cy[dd] + o[dd] * 0.93;
                 }
             }
-    /* double layer: source j carries a fixed unit normal; its basis row is n_j . grad L */
-    double *nj = (double *)malloc(sizeof(double) * 3 * np), *Gy = (double *)malloc(sizeof(double) * 3 * r);
-    for (int j = 0; j < np; ++j) {
-        double v[3] = {sin(1.3 * j + 0.2), cos(2.1 * j), sin(0.7 * j + 1.0)};
+    for (int jj = 0; jj < np; ++jj) {
+        double v[3] = {sin(1.3 * jj + 0.2), cos(2.1 * jj), sin(0.7 * jj + 1.0)};
         double nn = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
-        for (int dd = 0; dd < 3; ++dd) nj[3 * j + dd] = v[dd] / nn;
+        for (int dd = 0; dd < 3; ++dd) nj[3 * jj + dd] = v[dd] / nn;
     }
     for (int i = 0; i < np; ++i) {
         lagrange_3d(r1, t, px + 3 * i, cx, d, LX + (size_t)i * r);
-        if (kind == ORC_LAPLACE_DL) {
-            lagrange_3d_grad(r1, t, py + 3 * i, cy, d, Gy);
-            for (int a = 0; a < r; ++a)
-                LY[(size_t)i * r + a] = nj[3 * i] * Gy[3 * a] + nj[3 * i + 1] * Gy[3 * a + 1] + nj[3 * i + 2] * Gy[3 * a + 2];
-        } else {
-            lagrange_3d(r1, t, py + 3 * i, cy, d, LY + (size_t)i * r);
-        }
+        lagrange_3d(r1, t, py + 3 * i, cy, d, LY + (size_t)i * r);
     }
-    for (int a = 0; a < r; ++a) {
-        int ax = a / (r1 * r1), ay = (a / r1) % r1, az = a % r1;
-        double xc[3] = {cx[0] + t[ax] * 0.5 * d, cx[1] + t[ay] * 0.5 * d, cx[2] + t[az] * 0.5 * d};
-        for (int b = 0; b < r; ++b) {
-            int bx = b / (r1 * r1), by = (b / r1) % r1, bz = b % r1;
-            double yc[3] = {cy[0] + t[bx] * 0.5 * d, cy[1] + t[by] * 0.5 * d, cy[2] + t[bz] * 0.5 * d};
-            orc_kernel(kind, k, xc[0] - yc[0], xc[1] - yc[1], xc[2] - yc[2], &Tr[a * r + b], &Ti[a * r + b]);
-        }
-    }
-    /* M = T L_Y^T  (r x np), then approx(i,j) = sum_a LX[i,a] M[a,j] */
-    for (int a = 0; a < r; ++a)
-        for (int j = 0; j < np; ++j) {
-            double sr = 0, si = 0;
+    for (int comp = 0; comp < nc; ++comp) {
+        for (int a = 0; a < r; ++a) {
+            int ax = a / (r1 * r1), ay = (a / r1) % r1, az = a % r1;
+            double xc[3] = {cx[0] + t[ax] * 0.5 * d, cx[1] + t[ay] * 0.5 * d, cx[2] + t[az] * 0.5 * d};
             for (int b = 0; b < r; ++b) {
-                sr += Tr[a * r + b] * LY[(size_t)j * r + b];
-                si += Ti[a * r + b] * LY[(size_t)j * r + b];
+                int bx = b / (r1 * r1), by = (b / r1) % r1, bz = b % r1;
+                double yc[3] = {cy[0] + t[bx] * 0.5 * d, cy[1] + t[by] * 0.5 * d, cy[2] + t[bz] * 0.5 * d};
+                double dd[3] = {xc[0] - yc[0], xc[1] - yc[1], xc[2] - yc[2]};
+                if (kind == ORC_LAPLACE_DL) {
+                    double r2 = dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2];
+                    Tr[a * r + b] = dd[comp] / (4.0 * ORC_PI * r2 * sqrt(r2));
+                    Ti[a * r + b] = 0.0;
+                } else {
+                    orc_kernel(kind, k, dd[0], dd[1], dd[2], &Tr[a * r + b], &Ti[a * r + b]);
+                }
             }
-            Mr[(size_t)a * np + j] = sr;
-            Mi[(size_t)a * np + j] = si;
         }
+        /* M = T L_Y^T  (r x np), then approx(i,j) += w_j sum_a LX[i,a] M[a,j] */
+        for (int a = 0; a < r; ++a)
+            for (int jj = 0; jj < np; ++jj) {
+                double sr = 0, si = 0;
+                for (int b = 0; b < r; ++b) {
+                    sr += Tr[a * r + b] * LY[(size_t)jj * r + b];
+                    si += Ti[a * r + b] * LY[(size_t)jj * r + b];
+                }
+                Mr[(size_t)a * np + jj] = sr;
+                Mi[(size_t)a * np + jj] = si;
+            }
+        for (int i = 0; i < np; ++i)
+            for (int jj = 0; jj < np; ++jj) {
+                double sr = 0, si = 0;
+                for (int a = 0; a < r; ++a) {
+                    sr += LX[(size_t)i * r + a] * Mr[(size_t)a * np + jj];
+                    si += LX[(size_t)i * r + a] * Mi[(size_t)a * np + jj];
+                }
+                double wgt = kind == ORC_LAPLACE_DL ? nj[3 * jj + comp] : 1.0;
+                Ar[(size_t)i * np + jj] += wgt * sr;
+                Ai[(size_t)i * np + jj] += wgt * si;
+            }
+    }
     double num = 0, den = 0;
     for (int i = 0; i < np; ++i)
-        for (int j = 0; j < np; ++j) {
-            double sr = 0, si = 0;
-            for (int a = 0; a < r; ++a) {
-                sr += LX[(size_t)i * r + a] * Mr[(size_t)a * np + j];
-                si += LX[(size_t)i * r + a] * Mi[(size_t)a * np + j];
-            }
+        for (int jj = 0; jj < np; ++jj) {
             double gr, gi;
-            double dx = px[3 * i] - py[3 * j], dy = px[3 * i + 1] - py[3 * j + 1], dz = px[3 * i + 2] - py[3 * j + 2];
+            double dx = px[3 * i] - py[3 * jj], dy = px[3 * i + 1] - py[3 * jj + 1], dz = px[3 * i + 2] - py[3 * jj + 2];
             if (kind == ORC_LAPLACE_DL) {
                 double r2 = dx * dx + dy * dy + dz * dz;
-                gr = (nj[3 * j] * dx + nj[3 * j + 1] * dy + nj[3 * j + 2] * dz) / (4.0 * ORC_PI * r2 * sqrt(r2));
+                gr = (nj[3 * jj] * dx + nj[3 * jj + 1] * dy + nj[3 * jj + 2] * dz) / (4.0 * ORC_PI * r2 * sqrt(r2));
                 gi = 0.0;
             } else {
                 orc_kernel(kind, k, dx, dy, dz, &gr, &gi);
             }
+            double sr = Ar[(size_t)i * np + jj], si = Ai[(size_t)i * np + jj];
             num += (sr - gr) * (sr - gr) + (si - gi) * (si - gi);
             den += gr * gr + gi * gi;
         }
     free(px);
     free(py);
+    free(nj);
     free(LX);
     free(LY);
     free(Tr);
     free(Ti);
     free(Mr);
     free(Mi);
-    free(nj);
-    free(Gy);
+    free(Ar);
+    free(Ai);
     return sqrt(num / den);
 }
 
@@ -965,8 +932,10 @@ static void box_centre(const double o[3], const int64_t g[3], double dl, double 
 /* Far field of a Lagrange level (Sec. 2.2.2, eq. 8): source step L_Y (w u) per source
  * box, transfer T per admissible pair (kernel at the control nodes, evaluated for each
  * pair), target step L_X^T per target box.  With qv (double layer, 3-vector densities
- * w u n per source, qv[3 (j + ny m) + axis]) the source step applies the normal
- * derivative of the interpolant, sum_j (w u n)_j . grad L(y_j). */
+ * w u n per source, qv[3 (j + ny m) + axis]) the kernel n_y . grad_y G is the sum over
+ * the axes d of n_d dG/dy_d(x - y): each component kernel is interpolated on its own
+ * (source step L_Y (w u n_d), transfer with dG/dy_d at the control nodes) and the three
+ * results are added before the target step. */
 static void far_lagrange(const orc_plan *p, int l, const double *qr, const double *qi, const double *qv, int nrhs,
                          double *accr, double *acci)
 {
@@ -976,25 +945,23 @@ static void far_lagrange(const orc_plan *p, int l, const double *qr, const doubl
     double dl = ldexp(p->d0, -l);
     int64_t nbY = p->nby[l], nbX = p->nbx[l];
     int64_t ny = p->ty.n, nx = p->tx.n;
-    double *utr = (double *)calloc((size_t)nbY * nrhs * r, sizeof(double));
-    double *uti = (double *)calloc((size_t)nbY * nrhs * r, sizeof(double));
+    int nc = qv ? 3 : 1; /* kernel components */
+    double *utr = (double *)calloc((size_t)nbY * nrhs * nc * r, sizeof(double));
+    double *uti = (double *)calloc((size_t)nbY * nrhs * nc * r, sizeof(double));
 #pragma omp parallel for schedule(dynamic, 1)
     for (int64_t b = 0; b < nbY; ++b) {
         const obox *B = &p->by[l][b];
-        double c[3], Lb[1000], Gb[3000];
+        double c[3], Lb[1000];
         box_centre(p->ty.o, B->g, dl, c);
         for (int64_t j = B->s; j < B->e; ++j) {
+            lagrange_3d(r1, t, p->ty.p + 3 * j, c, dl, Lb);
             if (qv) {
-                lagrange_3d_grad(r1, t, p->ty.p + 3 * j, c, dl, Gb);
-                for (int m = 0; m < nrhs; ++m) {
-                    const double *q3 = qv + 3 * (j + ny * m);
-                    for (int a = 0; a < r; ++a)
-                        utr[((size_t)b * nrhs + m) * r + a] +=
-                            Gb[3 * a] * q3[0] + Gb[3 * a + 1] * q3[1] + Gb[3 * a + 2] * q3[2];
-                }
+                for (int m = 0; m < nrhs; ++m)
+                    for (int d = 0; d < 3; ++d)
+                        for (int a = 0; a < r; ++a)
+                            utr[(((size_t)b * nrhs + m) * 3 + d) * r + a] += Lb[a] * qv[3 * (j + ny * m) + d];
                 continue;
             }
-            lagrange_3d(r1, t, p->ty.p + 3 * j, c, dl, Lb);
             for (int m = 0; m < nrhs; ++m)
                 for (int a = 0; a < r; ++a) {
                     utr[((size_t)b * nrhs + m) * r + a] += Lb[a] * qr[j + ny * m];
@@ -1022,7 +989,8 @@ static void far_lagrange(const orc_plan *p, int l, const double *qr, const doubl
         double *vtr = (double *)calloc((size_t)nrhs * r, sizeof(double));
         double *vti = (double *)calloc((size_t)nrhs * r, sizeof(double));
         double *Tr = (double *)malloc(sizeof(double) * r * r), *Ti = (double *)malloc(sizeof(double) * r * r);
-        for (int64_t e = first[a]; e < first[a + 1]; ++e) {
+        for (int64_t e = first[a]; e < first[a + 1]; ++e)
+          for (int d = 0; d < nc; ++d) {
             int64_t b = adm[e].b;
             double cb[3];
             box_centre(p->ty.o, p->by[l][b].g, dl, cb);
@@ -1032,11 +1000,19 @@ static void far_lagrange(const orc_plan *p, int l, const double *qr, const doubl
                 for (int j = 0; j < r; ++j) {
                     int jx = j / (r1 * r1), jy = (j / r1) % r1, jz = j % r1;
                     double yc[3] = {cb[0] + t[jx] * 0.5 * dl, cb[1] + t[jy] * 0.5 * dl, cb[2] + t[jz] * 0.5 * dl};
-                    orc_kernel(p->kind, p->k, xc[0] - yc[0], xc[1] - yc[1], xc[2] - yc[2], &Tr[i * r + j], &Ti[i * r + j]);
+                    double dd[3] = {xc[0] - yc[0], xc[1] - yc[1], xc[2] - yc[2]};
+                    if (qv) {
+                        /* dG/dy_d = (x - y)_d / (4 pi |x - y|^3) */
+                        double r2 = dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2];
+                        Tr[i * r + j] = dd[d] / (4.0 * ORC_PI * r2 * sqrt(r2));
+                        Ti[i * r + j] = 0.0;
+                    } else {
+                        orc_kernel(p->kind, p->k, dd[0], dd[1], dd[2], &Tr[i * r + j], &Ti[i * r + j]);
+                    }
                 }
             }
             for (int m = 0; m < nrhs; ++m) {
-                const double *ur = utr + ((size_t)b * nrhs + m) * r, *ui = uti + ((size_t)b * nrhs + m) * r;
+                const double *ur = utr + (((size_t)b * nrhs + m) * nc + d) * r, *ui = uti + (((size_t)b * nrhs + m) * nc + d) * r;
                 for (int i = 0; i < r; ++i) {
                     double sr = 0, si = 0;
                     for (int j = 0; j < r; ++j) {
@@ -1274,8 +1250,8 @@ int orc_apply(const orc_plan *p, const double *w, const double *ure, const doubl
 
 /* Double-layer product by the FFM for a plan built with kind ORC_LAPLACE_DL: the
  * densities w u n (nrm: ny*3 row-major normals in the caller's order) go through the
- * derivative source step of every Lagrange level and the double-layer near field; real
- * u and v, column-major per RHS, caller's order. */
+ * three component kernels dG/dy_d of every Lagrange level and the double-layer near
+ * field; real u and v, column-major per RHS, caller's order. */
 int orc_apply_dl(const orc_plan *p, const double *nrm, const double *w, const double *u, int nrhs, double *v)
 {
     if (!p || !nrm || nrhs < 1 || p->kind != ORC_LAPLACE_DL) return ORC_EINVAL;

@@ -84,7 +84,6 @@ def lib():
         L.orc_direct_dl.restype = C.c_int
         L.orc_apply_dl.argtypes = [C.c_void_p, _dp, _dp, _dp, C.c_int, _dp]
         L.orc_apply_dl.restype = C.c_int
-        L.orc_lagrange_1d.argtypes = [C.c_int, C.c_double, _dp, _dp]
         L.orc_nthreads.restype = C.c_int
         L.orc_set_threads.argtypes = [C.c_int]
         _lib = L
@@ -238,14 +237,6 @@ def ffm_dl(X, Y, nrm, u, eps=1e-3, w=None, **opts):
         return p.apply_dl(u, nrm, w)
     finally:
         p.close()
-
-
-def lagrange_1d(r1, xi):
-    """(values, derivatives) of the r1 1-D Lagrange polynomials on Chebyshev nodes at xi."""
-    l = np.zeros(r1)
-    dl = np.zeros(r1)
-    lib().orc_lagrange_1d(int(r1), float(xi), _d(l), _d(dl))
-    return l, dl
 
 
 def ffm(X, Y, u, kind, k=0.0, eps=1e-3, w=None, **opts):
