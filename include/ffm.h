@@ -51,7 +51,11 @@ typedef enum {
     FFM_EUNSUPPORTED = 5 /* valid request outside what this build implements */
 } ffm_status;
 
-typedef enum { FFM_LAPLACE = 0, FFM_HELMHOLTZ = 1 } ffm_kernel;
+/* FFM_LAPLACE_DL is the double layer of the Laplace kernel, dG/dn_y(x - y) =
+ * n_y . (x - y) / (4 pi |x - y|^3) with G = 1/(4 pi |x - y|) and n_y the source normals
+ * (ffm_opts.normals, required); it runs through the kernel-independent Lagrange path
+ * with the normal derivative of the interpolant in the source step (Sec. 2.2.2). */
+typedef enum { FFM_LAPLACE = 0, FFM_HELMHOLTZ = 1, FFM_LAPLACE_DL = 2 } ffm_kernel;
 
 typedef enum {
     FFM_F32 = 0,  /* float */
@@ -99,6 +103,9 @@ typedef struct {
                                    translation, or ffm_autotune's pick), 1 CUDA-core GEMM per
                                    translation, 2 tcgen05 per translation, 3 tcgen05
                                    target-stationary (r <= 64) */
+    const void *normals;        /* FFM_LAPLACE_DL: N_Y x 3 row-major source normals (any
+                                   length; the kernel is linear in n), host or device; copied */
+    ffm_dtype normals_dtype;    /* FFM_F32 or FFM_F64 */
 } ffm_opts;
 
 /* Build a plan for targets X (nx points) and sources Y (ny points) (Sec. 2.2.1-2.2.4):

@@ -196,6 +196,72 @@ __global__ void __launch_bounds__(LAG_T) k_lag_anterp(LevelArgs A, const uint2 *
     }
 }
 
+// Source step of a double-layer Lagrange level.  The kernel n_y . grad_y G is the sum over
+// the axes d of n_d dG/dy_d(x - y); each component kernel is interpolated on its own, so
+// the source step gives three coefficient blocks u~_b[d r + abc] = sum_j q_{j,d} L_abc(y_j)
+// with q_j = w_j u_j n_j, and the transfer multiplies them by the stacked operator
+// [T^1 T^2 T^3] (K = 3 r).  Chunked like k_lag_anterp.
+template <int R1>
+__global__ void __launch_bounds__(LAG_T) k_lag_anterp_dl(LevelArgs A, const uint2 *__restrict__ chunks, Cheb cb,
+                                                         const float4 *__restrict__ q, int64_t ny, int nrhs,
+                                                         float *__restrict__ ut) {
+    constexpr int r = R1 * R1 * R1;
+    __shared__ float sl[LAG_T][3 * R1 + 4];  // x, y, z basis values, then q
+    uint2 ck = chunks[blockIdx.x];
+    int b = (int)ck.x, m = blockIdx.y;
+    uint32_t s0 = ck.y, bend = A.box_start[b + 1];
+    uint32_t s1 = min(bend, s0 + (uint32_t)LAG_CHUNK);
+    bool sole = s0 == A.box_start[b] && s1 == bend;
+    int4 gb = A.box_g[b];
+    float acc[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+    for (uint32_t base = s0; base < s1; base += LAG_T) {
+        uint32_t j = base + threadIdx.x;
+        if (j < s1) {
+            float4 e = A.eps[j];
+            int4 gl = A.leaf_g[__float_as_uint(e.w)];
+            float3 o = leaf_offset(gl, gb, A.shift, A.dls);
+            lag1d(cb, (o.x + e.x) * A.inv_half_dl, &sl[threadIdx.x][0]);
+            lag1d(cb, (o.y + e.y) * A.inv_half_dl, &sl[threadIdx.x][R1]);
+            lag1d(cb, (o.z + e.z) * A.inv_half_dl, &sl[threadIdx.x][2 * R1]);
+            float4 qj = q[2 * ((int64_t)m * ny + j)];  // hi part (the far field is smooth)
+            sl[threadIdx.x][3 * R1] = qj.x;
+            sl[threadIdx.x][3 * R1 + 1] = qj.y;
+            sl[threadIdx.x][3 * R1 + 2] = qj.z;
+        }
+        __syncthreads();
+        int cnt = (int)min((uint32_t)LAG_T, s1 - base);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            int a = threadIdx.x + h * LAG_T;
+            if (a < r) {
+                int ia = a / (R1 * R1), ib = (a / R1) % R1, ic = a % R1;
+                for (int jj = 0; jj < cnt; ++jj) {
+                    const float *v = sl[jj];
+                    float L = v[ia] * v[R1 + ib] * v[2 * R1 + ic];
+                    acc[h][0] = fmaf(L, v[3 * R1], acc[h][0]);
+                    acc[h][1] = fmaf(L, v[3 * R1 + 1], acc[h][1]);
+                    acc[h][2] = fmaf(L, v[3 * R1 + 2], acc[h][2]);
+                }
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        int a = threadIdx.x + h * LAG_T;
+        if (a < r) {
+            size_t o = ((size_t)b * nrhs + m) * 3 * r + a;
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                if (sole)
+                    ut[o + (size_t)d * r] = acc[h][d];
+                else
+                    atomicAdd(&ut[o + (size_t)d * r], acc[h][d]);
+            }
+        }
+    }
+}
+
 // Transfer as one GEMM per translation (Sec. 2.2.2, T depends only on the box offset):
 // C(i, p) = sum_j T_t(i, j) u~_{src(p)}(j) for the pairs p of a column tile of translation t,
 // then v~_{tgt(p)}(i) += C(i, p).  A tile is BM control nodes x BN pairs; K runs over the r
@@ -208,8 +274,9 @@ __global__ void __launch_bounds__(LG_T) k_lag_gemm(const uint32_t *__restrict__ 
                                                    const uint32_t *__restrict__ bt_off,
                                                    const uint32_t *__restrict__ bt_src,
                                                    const uint32_t *__restrict__ bt_tgt, const float *__restrict__ T,
-                                                   int r, int nrhs, const typename QT<CPLX>::T *__restrict__ ut,
+                                                   int r, int rk, int nrhs, const typename QT<CPLX>::T *__restrict__ ut,
                                                    typename QT<CPLX>::T *__restrict__ vt) {
+    // rk: K extent (rk = r, or 3 r for the double layer's stacked component kernels)
     typedef typename QT<CPLX>::T Q;
     constexpr int BN = LAG_GEMM_BN;
     __shared__ Q As[LG_BK][LG_BM];
@@ -230,17 +297,17 @@ __global__ void __launch_bounds__(LG_T) k_lag_gemm(const uint32_t *__restrict__ 
     for (int a = 0; a < 4; ++a)
 #pragma unroll
         for (int b = 0; b < 2; ++b) cr[a][b] = ci[a][b] = 0.f;
-    const Q *Tt = reinterpret_cast<const Q *>(T) + (size_t)t * r * r;
+    const Q *Tt = reinterpret_cast<const Q *>(T) + (size_t)t * r * rk;
     __syncthreads();
-    for (int j0 = 0; j0 < r; j0 += LG_BK) {
+    for (int j0 = 0; j0 < rk; j0 += LG_BK) {
         for (int e = tid; e < LG_BK * LG_BM; e += LG_T) {
             int jj = e / LG_BM, ii = e % LG_BM;
             int j = j0 + jj, i = i0 + ii;
             Q v;
             if constexpr (CPLX)
-                v = (j < r && i < r) ? Tt[(size_t)i * r + j] : make_float2(0.f, 0.f);
+                v = (j < rk && i < r) ? Tt[(size_t)i * rk + j] : make_float2(0.f, 0.f);
             else
-                v = (j < r && i < r) ? Tt[(size_t)i * r + j] : 0.f;
+                v = (j < rk && i < r) ? Tt[(size_t)i * rk + j] : 0.f;
             As[jj][ii] = v;
         }
         for (int e = tid; e < LG_BK * BN; e += LG_T) {
@@ -248,9 +315,9 @@ __global__ void __launch_bounds__(LG_T) k_lag_gemm(const uint32_t *__restrict__ 
             int j = j0 + jj;
             Q v;
             if constexpr (CPLX)
-                v = (j < r && pp < np) ? ut[((size_t)s_src[pp] * nrhs + m) * r + j] : make_float2(0.f, 0.f);
+                v = (j < rk && pp < np) ? ut[((size_t)s_src[pp] * nrhs + m) * rk + j] : make_float2(0.f, 0.f);
             else
-                v = (j < r && pp < np) ? ut[((size_t)s_src[pp] * nrhs + m) * r + j] : 0.f;
+                v = (j < rk && pp < np) ? ut[((size_t)s_src[pp] * nrhs + m) * rk + j] : 0.f;
             Bs[jj][pp] = v;
         }
         __syncthreads();
@@ -329,9 +396,10 @@ __global__ void __launch_bounds__(256) k_lag_gemm_tc(const uint32_t *__restrict_
                                                      const uint32_t *__restrict__ bt_off,
                                                      const uint32_t *__restrict__ bt_src,
                                                      const uint32_t *__restrict__ bt_tgt, const float *__restrict__ T,
-                                                     int r, int npad, int tcols, int nrhs,
+                                                     int r, int rk, int npad, int tcols, int nrhs,
                                                      const float *__restrict__ ut, float *__restrict__ vt,
                                                      int *__restrict__ err) {
+    // rk: K extent (rk = r, or 3 r for the double layer's stacked component kernels)
     extern __shared__ __align__(1024) unsigned char smem[];
     float *sAh = reinterpret_cast<float *>(smem);
     float *sAl = sAh + TC_M * KT;
@@ -361,29 +429,29 @@ __global__ void __launch_bounds__(256) k_lag_gemm_tc(const uint32_t *__restrict_
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     uint32_t tmem = s_tmem;
-    const float *Tt = T + (size_t)t * r * r;
-    const bool r4 = (r & 3) == 0;  // rows of u~ and T start on 16-byte boundaries
+    const float *Tt = T + (size_t)t * r * rk;
+    const bool r4 = (rk & 3) == 0;  // rows of u~ and T start on 16-byte boundaries
     const uint32_t lbo = 128, sbo = (KT / 4) * 128;
     const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(npad >> 3) << 17) | ((uint32_t)(TC_M >> 4) << 24);
     bool ok = true;
     int phase = 0;
-    for (int k0 = 0; k0 < r; k0 += KT) {
+    for (int k0 = 0; k0 < rk; k0 += KT) {
         // A: row p = pair, K = source node j (gathered u~ column of the pair's source box).
         // Each thread moves 4 consecutive K elements = one 16-byte row of a core matrix.
         constexpr int C4 = KT / 4;
         for (int e = tid; e < TC_M * C4; e += blockDim.x) {
             int p = e / C4, c = e % C4;
             int j = k0 + 4 * c;
-            const float *src = ut + ((size_t)s_src[p] * nrhs + m) * r + j;
+            const float *src = ut + ((size_t)s_src[p] * nrhs + m) * rk + j;
             float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
             if (p < np) {
-                if (r4 && j + 4 <= r) {
+                if (r4 && j + 4 <= rk) {
                     x = *reinterpret_cast<const float4 *>(src);
                 } else {
-                    x.x = j < r ? src[0] : 0.f;
-                    x.y = j + 1 < r ? src[1] : 0.f;
-                    x.z = j + 2 < r ? src[2] : 0.f;
-                    x.w = j + 3 < r ? src[3] : 0.f;
+                    x.x = j < rk ? src[0] : 0.f;
+                    x.y = j + 1 < rk ? src[1] : 0.f;
+                    x.z = j + 2 < rk ? src[2] : 0.f;
+                    x.w = j + 3 < rk ? src[3] : 0.f;
                 }
             }
             float4 h, l;
@@ -399,16 +467,16 @@ __global__ void __launch_bounds__(256) k_lag_gemm_tc(const uint32_t *__restrict_
         for (int e = tid; e < npad * C4; e += blockDim.x) {
             int i = e / C4, c = e % C4;
             int j = k0 + 4 * c;
-            const float *src = Tt + (size_t)i * r + j;
+            const float *src = Tt + (size_t)i * rk + j;
             float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
             if (i < r) {
-                if (r4 && j + 4 <= r) {
+                if (r4 && j + 4 <= rk) {
                     x = *reinterpret_cast<const float4 *>(src);
                 } else {
-                    x.x = j < r ? src[0] : 0.f;
-                    x.y = j + 1 < r ? src[1] : 0.f;
-                    x.z = j + 2 < r ? src[2] : 0.f;
-                    x.w = j + 3 < r ? src[3] : 0.f;
+                    x.x = j < rk ? src[0] : 0.f;
+                    x.y = j + 1 < rk ? src[1] : 0.f;
+                    x.z = j + 2 < rk ? src[2] : 0.f;
+                    x.w = j + 3 < rk ? src[3] : 0.f;
                 }
             }
             float4 h, l;
@@ -777,6 +845,27 @@ static void lagrange_points(const ffm_plan_s *p, const FarLevel &F, const LevelA
     }
 }
 
+template <int R1>
+static void lagrange_anterp_dl(const ffm_plan_s *p, const FarLevel &F, const LevelArgs &A, const Cheb &cb,
+                               const void *q, int nrhs, void *ut, cudaStream_t s) {
+    dim3 g((unsigned)F.n_src_chunks, nrhs);
+    FFM_LAUNCH((k_lag_anterp_dl<R1>), g, LAG_T, 0, s, A, F.src_chunks, cb, (const float4 *)q, p->ny, nrhs, (float *)ut);
+}
+
+static void lagrange_anterp_dl_r1(const ffm_plan_s *p, const FarLevel &F, const LevelArgs &A, const Cheb &cb,
+                                  const void *q, int nrhs, void *ut, cudaStream_t s) {
+    switch (F.r1) {
+        case 2: lagrange_anterp_dl<2>(p, F, A, cb, q, nrhs, ut, s); break;
+        case 3: lagrange_anterp_dl<3>(p, F, A, cb, q, nrhs, ut, s); break;
+        case 4: lagrange_anterp_dl<4>(p, F, A, cb, q, nrhs, ut, s); break;
+        case 5: lagrange_anterp_dl<5>(p, F, A, cb, q, nrhs, ut, s); break;
+        case 6: lagrange_anterp_dl<6>(p, F, A, cb, q, nrhs, ut, s); break;
+        case 7: lagrange_anterp_dl<7>(p, F, A, cb, q, nrhs, ut, s); break;
+        case 8: lagrange_anterp_dl<8>(p, F, A, cb, q, nrhs, ut, s); break;
+        default: fail(FFM_EUNSUPPORTED, "Chebyshev nodes per axis outside 2..8");
+    }
+}
+
 template <bool CPLX>
 static void lagrange_points_r1(const ffm_plan_s *p, const FarLevel &F, const LevelArgs &A, const Cheb &cb,
                                bool anterp, const void *in, int nrhs, void *out, cudaStream_t s) {
@@ -800,8 +889,9 @@ void far_lagrange(const ffm_plan_s *p, int l, const void *q, int nrhs, float2 *a
     LevelArgs AY = level_args(p, p->by[l], p->by[ls], p->epsY, l);
     LevelArgs AX = level_args(p, p->bx[l], p->bx[ls], p->epsX, l);
     bool cplx = p->kind == FFM_HELMHOLTZ;
+    int rk = p->kind == FFM_LAPLACE_DL ? 3 * r : r;  // K extent of the transfer
     size_t esz = cplx ? sizeof(float2) : sizeof(float);
-    size_t ub = esz * r * nrhs * (size_t)p->by[l].nb, vb = esz * r * nrhs * (size_t)p->bx[l].nb;
+    size_t ub = esz * rk * nrhs * (size_t)p->by[l].nb, vb = esz * r * nrhs * (size_t)p->bx[l].nb;
     void *ut = tmp.raw(ub);
     void *vt = tmp.raw(vb);
     dim3 gg((unsigned)F.n_tiles, cdiv(r, LG_BM), nrhs);
@@ -809,11 +899,14 @@ void far_lagrange(const ffm_plan_s *p, int l, const void *q, int nrhs, float2 *a
     FFM_CUDA(cudaMemsetAsync(vt, 0, vb, s));
     if (cplx) {
         lagrange_points_r1<true>(p, F, AY, cb, true, q, nrhs, ut, s);
-        FFM_LAUNCH(k_lag_gemm<true>, gg, LG_T, 0, s, F.tile_t, F.tile_p0, F.bt_off, F.bt_src, F.bt_tgt, F.T, r,
+        FFM_LAUNCH(k_lag_gemm<true>, gg, LG_T, 0, s, F.tile_t, F.tile_p0, F.bt_off, F.bt_src, F.bt_tgt, F.T, r, rk,
                    nrhs, (const float2 *)ut, (float2 *)vt);
         lagrange_points_r1<true>(p, F, AX, cb, false, vt, nrhs, accf, s);
     } else {
-        lagrange_points_r1<false>(p, F, AY, cb, true, q, nrhs, ut, s);
+        if (p->kind == FFM_LAPLACE_DL)
+            lagrange_anterp_dl_r1(p, F, AY, cb, q, nrhs, ut, s);
+        else
+            lagrange_points_r1<false>(p, F, AY, cb, true, q, nrhs, ut, s);
         int npad = (r + 15) / 16 * 16;
         if (F.ts_ok && F.Tsp && F.tune_tc == 2) {
             size_t smem = (size_t)2 * TS_STAGE * sizeof(float);
@@ -839,10 +932,10 @@ void far_lagrange(const ffm_plan_s *p, int l, const void *q, int nrhs, float2 *a
             }
             dim3 gtc((unsigned)F.tc_tiles, nrhs);
             FFM_LAUNCH(k_lag_gemm_tc<KT>, gtc, 256, smem, s, F.tc_tile_t, F.tc_tile_p0, F.bt_off, F.bt_src, F.bt_tgt,
-                       F.T, r, npad, tcols, nrhs, (const float *)ut, (float *)vt, p->dev_err);
+                       F.T, r, rk, npad, tcols, nrhs, (const float *)ut, (float *)vt, p->dev_err);
         } else {
             FFM_LAUNCH(k_lag_gemm<false>, gg, LG_T, 0, s, F.tile_t, F.tile_p0, F.bt_off, F.bt_src, F.bt_tgt, F.T, r,
-                       nrhs, (const float *)ut, (float *)vt);
+                       rk, nrhs, (const float *)ut, (float *)vt);
         }
         lagrange_points_r1<false>(p, F, AX, cb, false, vt, nrhs, accf, s);
     }

@@ -149,6 +149,24 @@ __global__ void k_gather_q(const UT *__restrict__ u, const uint32_t *__restrict_
 
 // v = near field and plane-wave levels (FP64 accumulators) + Lagrange levels (FP32), summed
 // in FP64 per target, back in the caller's order.
+// Double layer: q_j = w_j u_{perm_j} n_j, a 3-vector per source and right-hand side, formed
+// in FP64 and stored as an unevaluated FP32 pair: q[2 (m ny + j)] = hi, [+1] = lo.
+template <class UT>
+__global__ void k_gather_q_dl(const UT *__restrict__ u, const uint32_t *__restrict__ perm,
+                              const double *__restrict__ w, const float4 *__restrict__ nh,
+                              const float4 *__restrict__ nl, int64_t ny, float4 *__restrict__ q) {
+    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int m = blockIdx.y;
+    if (j >= ny) return;
+    double s = (double)u[(int64_t)perm[j] + (int64_t)m * ny] * (w ? w[j] : 1.0);
+    float4 a = nh[j], b = nl[j];
+    double qx = s * ((double)a.x + (double)b.x), qy = s * ((double)a.y + (double)b.y), qz = s * ((double)a.z + (double)b.z);
+    float hx = (float)qx, hy = (float)qy, hz = (float)qz;
+    int64_t o = 2 * ((int64_t)m * ny + j);
+    q[o] = make_float4(hx, hy, hz, 0.f);
+    q[o + 1] = make_float4((float)(qx - (double)hx), (float)(qy - (double)hy), (float)(qz - (double)hz), 0.f);
+}
+
 template <class VT, bool CPLX>
 __global__ void k_scatter_v(const double2 *__restrict__ acc, const float2 *__restrict__ accf,
                             const uint32_t *__restrict__ perm, int64_t nx, int nrhs, VT *__restrict__ v) {
@@ -194,13 +212,21 @@ static void apply_impl(ffm_plan_s *p, const void *u, ffm_dtype udt, int nrhs, vo
     }
     bool host_v = !is_device_ptr(v);
     void *dv = host_v ? tmp.raw(vb) : v;
-    void *q = tmp.raw((helm ? 8 : 4) * (size_t)ny * nrhs);
+    bool dl = p->kind == FFM_LAPLACE_DL;
+    void *q = tmp.raw((dl ? 32 : helm ? 8 : 4) * (size_t)ny * nrhs);
     double2 *acc = tmp.get<double2>((size_t)nx * nrhs);
     FFM_CUDA(cudaMemsetAsync(acc, 0, sizeof(double2) * (size_t)nx * nrhs, s));
     float2 *accf = tmp.get<float2>((size_t)nx * nrhs);
     FFM_CUDA(cudaMemsetAsync(accf, 0, sizeof(float2) * (size_t)nx * nrhs, s));
     dim3 gy(cdiv(ny, 256), nrhs), gx(cdiv(nx, 256), nrhs);
-    switch (udt) {
+    if (dl) {
+        if (udt == FFM_F64)
+            FFM_LAUNCH(k_gather_q_dl<double>, gy, 256, 0, s, (const double *)du, p->permY, p->wY, p->nY, p->nYlo, ny,
+                       (float4 *)q);
+        else
+            FFM_LAUNCH(k_gather_q_dl<float>, gy, 256, 0, s, (const float *)du, p->permY, p->wY, p->nY, p->nYlo, ny,
+                       (float4 *)q);
+    } else switch (udt) {
         case FFM_F32: FFM_LAUNCH((k_gather_q<float, false>), gy, 256, 0, s, (const float *)du, p->permY, p->wY, ny, nrhs, q); break;
         case FFM_F64: FFM_LAUNCH((k_gather_q<double, false>), gy, 256, 0, s, (const double *)du, p->permY, p->wY, ny, nrhs, q); break;
         case FFM_C64: FFM_LAUNCH((k_gather_q<float, true>), gy, 256, 0, s, (const float *)du, p->permY, p->wY, ny, nrhs, q); break;
@@ -277,7 +303,10 @@ ffm_status ffm_plan(const void *X, ffm_dtype xdt, int64_t nx, const void *Y, ffm
         if ((int64_t)nx + ny >= ((int64_t)1 << 31)) fail(FFM_EUNSUPPORTED, "more than 2^31 points in total");
         if (xdt != FFM_F32 && xdt != FFM_F64) fail(FFM_EINVAL, "X dtype must be FFM_F32 or FFM_F64");
         if (ydt != FFM_F32 && ydt != FFM_F64) fail(FFM_EINVAL, "Y dtype must be FFM_F32 or FFM_F64");
-        if (kernel != FFM_LAPLACE && kernel != FFM_HELMHOLTZ) fail(FFM_EINVAL, "unknown kernel");
+        if (kernel != FFM_LAPLACE && kernel != FFM_HELMHOLTZ && kernel != FFM_LAPLACE_DL)
+            fail(FFM_EINVAL, "unknown kernel");
+        if (kernel == FFM_LAPLACE_DL && (!opts || !opts->normals))
+            fail(FFM_EINVAL, "the double layer needs source normals (opts.normals)");
         if (!(eps > 0.0 && eps < 1.0)) fail(FFM_EINVAL, "eps must lie in (0, 1)");
         if (kernel == FFM_HELMHOLTZ && !(k >= 0.0 && std::isfinite(k))) fail(FFM_EINVAL, "k must be finite and >= 0");
         const void *w = nullptr;
@@ -303,6 +332,12 @@ ffm_status ffm_plan(const void *X, ffm_dtype xdt, int64_t nx, const void *Y, ffm
             w = opts->weights;
             wdt = opts->weights_dtype;
             if (w && wdt != FFM_F32 && wdt != FFM_F64) fail(FFM_EINVAL, "weights dtype must be FFM_F32 or FFM_F64");
+            if (kernel == FFM_LAPLACE_DL) {
+                if (opts->normals_dtype != FFM_F32 && opts->normals_dtype != FFM_F64)
+                    fail(FFM_EINVAL, "normals dtype must be FFM_F32 or FFM_F64");
+                p->normals_in = opts->normals;
+                p->normals_dt = opts->normals_dtype;
+            }
         }
         p->stream = (cudaStream_t)stream;
         p->mem.stream = p->stream;
@@ -429,7 +464,7 @@ ffm_status ffm_plan_info(const ffm_plan_t *plan, ffm_info *info) {
     for (int l = 0; l <= ffm::LMAX; ++l) {
         const ffm::FarLevel &F = plan->far[l];
         bool act = l <= plan->l_stop && F.n_adm > 0;
-        bool tc = F.tune_tc != 0 && F.tc_tiles > 0 && plan->kind == FFM_LAPLACE &&
+        bool tc = F.tune_tc != 0 && F.tc_tiles > 0 && real_kernel(plan->kind) &&
                   (F.r1 * F.r1 * F.r1 + 15) / 16 * 16 <= 256;
         bool ts = F.ts_ok && F.Tsp && F.tune_tc == 2;
         info->tune_tc[l] = act && F.mode == 1 ? (ts ? 2 : tc ? 1 : 0) : 0;

@@ -180,6 +180,10 @@ struct ffm_plan_s {
     int precision = 0;  // ffm_precision for the plane-wave levels, 0 = by cancellation
     float4 *sctab = nullptr;  // sin/cos(j/64) in double-float for the double-float levels
     int lag_transfer = 0;     // ffm_opts.lagrange_transfer
+    const void *normals_in = nullptr;  // double layer: caller's normals (during ffm_plan only)
+    ffm_dtype normals_dt = FFM_F64;
+    float4 *nY = nullptr;     // double layer: source normals in Morton order, hi and lo parts
+    float4 *nYlo = nullptr;
     double d0 = 1, oX[3] = {0, 0, 0}, oY[3] = {0, 0, 0}, sigma[3] = {0, 0, 0};
     int l_stop = 0, root_adm = 0;
     cudaStream_t stream = nullptr;
@@ -247,6 +251,8 @@ int r1_rule(int kind, double eps);
 // Lagrange levels add their contributions in FP32 into accf (float2 per target and RHS);
 // the apply adds accf into the FP64 accumulators once, at the end.
 void far_lagrange(const ffm_plan_s *p, int l, const void *q, int nrhs, float2 *accf, Alloc &tmp, cudaStream_t s);
+// true for the kinds whose transfer operators are the real Laplace G (Laplace, double layer)
+inline bool real_kernel(int kind) { return kind != FFM_HELMHOLTZ; }
 void far_planewave(const ffm_plan_s *p, int l, const float2 *q, int nrhs, double2 *acc, Alloc &tmp,
                    cudaStream_t s);
 void near_field(const ffm_plan_s *p, const void *q, int nrhs, double2 *acc, cudaStream_t s);

@@ -77,9 +77,38 @@ __device__ __forceinline__ float rsqrt_hw(float x) {
 // Accumulate the staged sources [j0, j1) into (sr, si) for the PT targets x = xh + xl of
 // this thread.  Staged source j: sA[j] = (hi.x, hi.y, hi.z, w.re), sB[j] = (lo.x, lo.y,
 // lo.z, w.im): two 16-byte loads serve PT pairs.
-template <bool HELM, int PT>
-__device__ __forceinline__ void interact(const float4 *sA, const float4 *sB, int j0, int j1, const float4 *xh,
-                                         const float4 *xl, float k, float *sr, float *si) {
+constexpr int NF_LAPLACE = 0, NF_HELMHOLTZ = 1, NF_DOUBLE_LAYER = 2;
+
+// a + b with its rounding error (Knuth's TwoSum, no ordering assumption)
+__device__ __forceinline__ void two_sum_f(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// q . (x - y) with x = xh + xl, y = yh + yl (leaf-frame FP32 pairs, .w of yh/yl unused) and
+// q = qh + ql: each component of x - y as a pair (TwoSum), each leading product split
+// exactly by FMA, the three leading terms added with TwoSum, all residuals collected in
+// FP32.  About 2^-44 relative to |q| |x - y| instead of 2^-24.
+__device__ __forceinline__ float dot_pair(float4 xh, float4 xl, float4 yh, float4 yl, float3 qh, float3 ql) {
+    float dh0, de0, dh1, de1, dh2, de2;
+    two_sum_f(xh.x, -yh.x, dh0, de0);
+    two_sum_f(xh.y, -yh.y, dh1, de1);
+    two_sum_f(xh.z, -yh.z, dh2, de2);
+    float dl0 = de0 + (xl.x - yl.x), dl1 = de1 + (xl.y - yl.y), dl2 = de2 + (xl.z - yl.z);
+    float p0 = __fmul_rn(qh.x, dh0), p1 = __fmul_rn(qh.y, dh1), p2 = __fmul_rn(qh.z, dh2);
+    float r = fmaf(qh.x, dh0, -p0) + fmaf(qh.y, dh1, -p1) + fmaf(qh.z, dh2, -p2);
+    r = fmaf(qh.x, dl0, fmaf(qh.y, dl1, fmaf(qh.z, dl2, r)));
+    r = fmaf(ql.x, dh0, fmaf(ql.y, dh1, fmaf(ql.z, dh2, r)));
+    float s1, e1, s2, e2;
+    two_sum_f(p0, p1, s1, e1);
+    two_sum_f(s1, p2, s2, e2);
+    return s2 + ((e1 + e2) + r);
+}
+
+template <int KIND, int PT>
+__device__ __forceinline__ void interact(const float4 *sA, const float4 *sB, const float4 *sC, int j0, int j1,
+                                         const float4 *xh, const float4 *xl, float k, float *sr, float *si) {
 #pragma unroll 2
     for (int j = j0; j < j1; ++j) {
         float4 y = sA[j];
@@ -91,7 +120,13 @@ __device__ __forceinline__ void interact(const float4 *sA, const float4 *sB, int
             float dz = (xh[t].z - y.z) + (xl[t].z - yl.z);
             float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
             float inv = r2 > 0.f ? rsqrt_hw(r2) : 0.f;  // coincident points contribute nothing
-            if constexpr (HELM) {
+            if constexpr (KIND == NF_DOUBLE_LAYER) {
+                // (w u n) . (x - y) / |x - y|^3; for points of one surface the dot product
+                // is second order in |x - y|, so it is formed from x - y and q as FP32 pairs
+                float4 c = sC[j];  // (q_hi.z, q_lo.x, q_lo.y, q_lo.z)
+                float qd = dot_pair(xh[t], xl[t], y, yl, make_float3(y.w, yl.w, c.x), make_float3(c.y, c.z, c.w));
+                sr[t] = fmaf(qd, inv * inv * inv, sr[t]);
+            } else if constexpr (KIND == NF_HELMHOLTZ) {
                 // phase k r reduced to [-pi, pi] (Cody-Waite, two-term 2 pi) before sincos
                 float ph = k * (r2 * inv);
                 float n = rintf(ph * 0.15915494309189535f);
@@ -113,12 +148,14 @@ __device__ __forceinline__ void interact(const float4 *sA, const float4 *sB, int
 // One work item: up to tchunk targets of a leaf (PT per thread) against a range of its near
 // source leaves, staged P2P_SB points at a time.  When the targets need fewer than P2P_T
 // threads, G groups of threads split each staged batch and are reduced in shared memory.
-template <bool HELM>
+template <int KIND>
 __global__ void __launch_bounds__(P2P_T) k_p2p(NearArgs N, const void *__restrict__ qv, int64_t ny, int nrhs,
                                                int64_t nx, double2 *__restrict__ acc) {
     constexpr int PT = 2;
+    constexpr bool HELM = KIND == NF_HELMHOLTZ;
     __shared__ float4 sA[P2P_SB];
     __shared__ float4 sB[P2P_SB];
+    __shared__ float4 sC[KIND == NF_DOUBLE_LAYER ? P2P_SB : 1];  // double layer: (q_hi.z, q_lo)
     __shared__ float2 red[P2P_T * PT];
     int4 it = N.items[blockIdx.x];
     int a = it.x, m = blockIdx.y;
@@ -132,6 +169,7 @@ __global__ void __launch_bounds__(P2P_T) k_p2p(NearArgs N, const void *__restric
     int4 ga = N.xl_g[a];
     const float *qr = reinterpret_cast<const float *>(qv) + (int64_t)m * ny;
     const float2 *qc = reinterpret_cast<const float2 *>(qv) + (int64_t)m * ny;
+    const float4 *q3 = reinterpret_cast<const float4 *>(qv) + 2 * (int64_t)m * ny;
     float4 xh[PT], xl[PT];
     float sr[PT], si[PT];
 #pragma unroll
@@ -159,22 +197,29 @@ __global__ void __launch_bounds__(P2P_T) k_p2p(NearArgs N, const void *__restric
                 stage_coord(y.x, yl.x, oc.h[0], oc.l[0], hx, lx);
                 stage_coord(y.y, yl.y, oc.h[1], oc.l[1], hy, ly);
                 stage_coord(y.z, yl.z, oc.h[2], oc.l[2], hz, lz);
-                float2 w = HELM ? qc[s0 + c0 + j] : make_float2(qr[s0 + c0 + j], 0.f);
-                sA[fill + j] = make_float4(hx, hy, hz, w.x);
-                sB[fill + j] = make_float4(lx, ly, lz, w.y);
+                if constexpr (KIND == NF_DOUBLE_LAYER) {
+                    float4 wh = q3[2 * (s0 + c0 + j)], wl = q3[2 * (s0 + c0 + j) + 1];
+                    sA[fill + j] = make_float4(hx, hy, hz, wh.x);
+                    sB[fill + j] = make_float4(lx, ly, lz, wh.y);
+                    sC[fill + j] = make_float4(wh.z, wl.x, wl.y, wl.z);
+                } else {
+                    float2 w = HELM ? qc[s0 + c0 + j] : make_float2(qr[s0 + c0 + j], 0.f);
+                    sA[fill + j] = make_float4(hx, hy, hz, w.x);
+                    sB[fill + j] = make_float4(lx, ly, lz, w.y);
+                }
             }
             fill += take;
             c0 += take;
             if (fill == P2P_SB) {
                 __syncthreads();
-                if (active) interact<HELM, PT>(sA, sB, grp * fill / G, (grp + 1) * fill / G, xh, xl, N.k, sr, si);
+                if (active) interact<KIND, PT>(sA, sB, sC, grp * fill / G, (grp + 1) * fill / G, xh, xl, N.k, sr, si);
                 __syncthreads();
                 fill = 0;
             }
         }
     }
     __syncthreads();
-    if (active) interact<HELM, PT>(sA, sB, grp * fill / G, (grp + 1) * fill / G, xh, xl, N.k, sr, si);
+    if (active) interact<KIND, PT>(sA, sB, sC, grp * fill / G, (grp + 1) * fill / G, xh, xl, N.k, sr, si);
 #pragma unroll
     for (int t = 0; t < PT; ++t) red[threadIdx.x * PT + t] = make_float2(sr[t], si[t]);
     __syncthreads();
@@ -323,6 +368,11 @@ void near_field_items(const ffm_plan_s *p, const int4 *items, int64_t n_items, i
         N.oyx_l[d] = (float)(o - (double)N.oyx_h[d]);
     }
     N.k = (float)p->k;
+    if (p->kind == FFM_LAPLACE_DL) {
+        dim3 g((unsigned)n_items, nrhs);
+        FFM_LAUNCH(k_p2p<NF_DOUBLE_LAYER>, g, P2P_T, 0, s, N, q, p->ny, nrhs, p->nx, acc);
+        return;
+    }
     if (nrhs > 1) {
         constexpr int MC = 8;
         dim3 gm((unsigned)n_items, cdiv(nrhs, MC));
@@ -334,9 +384,9 @@ void near_field_items(const ffm_plan_s *p, const int4 *items, int64_t n_items, i
     }
     dim3 g((unsigned)n_items, nrhs);
     if (p->kind == FFM_HELMHOLTZ)
-        FFM_LAUNCH(k_p2p<true>, g, P2P_T, 0, s, N, q, p->ny, nrhs, p->nx, acc);
+        FFM_LAUNCH(k_p2p<NF_HELMHOLTZ>, g, P2P_T, 0, s, N, q, p->ny, nrhs, p->nx, acc);
     else
-        FFM_LAUNCH(k_p2p<false>, g, P2P_T, 0, s, N, q, p->ny, nrhs, p->nx, acc);
+        FFM_LAUNCH(k_p2p<NF_LAPLACE>, g, P2P_T, 0, s, N, q, p->ny, nrhs, p->nx, acc);
 }
 
 }  // namespace ffm

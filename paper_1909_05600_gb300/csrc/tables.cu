@@ -21,9 +21,11 @@ namespace ffm {
 // plan constants: the smallest r1 whose error is <= eps is used.
 static const double R1_ERR_LAPLACE[11] = {1, 1, 3.2e-2, 4.8e-3, 7.6e-4, 1.1e-4, 1.6e-5, 2.0e-6, 2.4e-7, 8.1e-8, 1.1e-8};
 static const double R1_ERR_HELM[11] = {1, 1, 2.4e-1, 3.4e-2, 3.6e-3, 3.6e-4, 4.0e-5, 3.9e-6, 3.9e-7, 1.3e-7, 1.4e-8};
+// the double layer: its three component kernels dG/dy_d, weighted by the source normals
+static const double R1_ERR_LAPLACE_DL[11] = {1, 1, 1.2e-1, 2.4e-2, 5.1e-3, 1.1e-3, 1.8e-4, 2.6e-5, 3.9e-6, 1.5e-6, 2.0e-7};
 
 int r1_rule(int kind, double eps) {
-    const double *t = kind == FFM_HELMHOLTZ ? R1_ERR_HELM : R1_ERR_LAPLACE;
+    const double *t = kind == FFM_HELMHOLTZ ? R1_ERR_HELM : kind == FFM_LAPLACE_DL ? R1_ERR_LAPLACE_DL : R1_ERR_LAPLACE;
     for (int r1 = 2; r1 <= 10; ++r1)
         if (t[r1] <= eps) return r1;
     return 10;
@@ -51,6 +53,21 @@ __global__ void k_lag_table(const int4 *__restrict__ m, int ntrans, LagGeo geo, 
           r0z = (float)(geo.oxy[2] + mt.z * geo.dl);
     bool cplx = geo.kind == FFM_HELMHOLTZ;
     const float c4pi = 0.07957747154594767f;  // 1 / (4 pi)
+    if (geo.kind == FFM_LAPLACE_DL) {
+        // the double layer's component kernels dG/dy_d = (x - y)_d / (4 pi |x - y|^3),
+        // stacked along K: T[t][i][d r + j]
+        for (int e = threadIdx.x; e < 3 * r * r; e += blockDim.x) {
+            int i = e / (3 * r), jj = e % (3 * r), d = jj / r, j = jj % r;
+            int ix = i / (r1 * r1), iy = (i / r1) % r1, iz = i % r1;
+            int jx = j / (r1 * r1), jy = (j / r1) % r1, jz = j % r1;
+            float dv[3] = {r0x + (geo.hnode[ix] - geo.hnode[jx]), r0y + (geo.hnode[iy] - geo.hnode[jy]),
+                           r0z + (geo.hnode[iz] - geo.hnode[jz])};
+            float r2 = fmaf(dv[0], dv[0], fmaf(dv[1], dv[1], dv[2] * dv[2]));
+            float rr = sqrtf(r2);
+            T[(size_t)t * 3 * r * r + e] = c4pi * dv[d] / (r2 * rr);
+        }
+        return;
+    }
     for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
         int i = e / r, j = e % r;
         int ix = i / (r1 * r1), iy = (i / r1) % r1, iz = i % r1;
@@ -308,7 +325,7 @@ void build_tables(ffm_plan_s *p, int l, TableJob &tj) {
     if (F.mode == 1) {
         int r = F.r1 * F.r1 * F.r1;
         bool cplx = p->kind == FFM_HELMHOLTZ;
-        F.T = p->mem.get<float>((size_t)F.n_trans * r * r * (cplx ? 2 : 1));
+        F.T = p->mem.get<float>((size_t)F.n_trans * r * r * (cplx ? 2 : p->kind == FFM_LAPLACE_DL ? 3 : 1));
             LagGeo g{};
         for (int d = 0; d < 3; ++d) g.oxy[d] = oxy[d];
         g.dl = dl;

@@ -744,6 +744,20 @@ __global__ void k_sorted_weights(const T *__restrict__ w, const uint32_t *__rest
     if (i < n) out[i] = (double)w[perm[i]];
 }
 
+// Source normals in Morton order as unevaluated FP32 pairs (hi, lo): the double layer's
+// n . (x - y) cancels to second order in |x - y| for points of one surface.
+template <class T>
+__global__ void k_sorted_normals(const T *__restrict__ nrm, const uint32_t *__restrict__ perm, int64_t n,
+                                 float4 *__restrict__ hi, float4 *__restrict__ lo) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const T *v = nrm + 3 * (int64_t)perm[i];
+    double a = (double)v[0], b = (double)v[1], c = (double)v[2];
+    float ah = (float)a, bh = (float)b, ch = (float)c;
+    hi[i] = make_float4(ah, bh, ch, 0.f);
+    lo[i] = make_float4((float)(a - (double)ah), (float)(b - (double)bh), (float)(c - (double)ch), 0.f);
+}
+
 // ================================================================ host side
 
 static int bits_for(int64_t n) {
@@ -1276,6 +1290,18 @@ void build_plan(ffm_plan_s *p, const void *X, ffm_dtype xdt, const void *Y, ffm_
             FFM_LAUNCH(k_sorted_weights<double>, cdiv(ny, 256), 256, 0, s, (const double *)dw, p->permY, ny, p->wY);
         else
             FFM_LAUNCH(k_sorted_weights<float>, cdiv(ny, 256), 256, 0, s, (const float *)dw, p->permY, ny, p->wY);
+    }
+    if (p->kind == FFM_LAPLACE_DL) {
+        size_t esz = p->normals_dt == FFM_F64 ? 8 : 4;
+        const void *dn = to_device(p->normals_in, 3 * esz * (size_t)ny, tmp, s);
+        p->nY = p->mem.get<float4>(ny);
+        p->nYlo = p->mem.get<float4>(ny);
+        if (p->normals_dt == FFM_F64)
+            FFM_LAUNCH(k_sorted_normals<double>, cdiv(ny, 256), 256, 0, s, (const double *)dn, p->permY, ny, p->nY,
+                       p->nYlo);
+        else
+            FFM_LAUNCH(k_sorted_normals<float>, cdiv(ny, 256), 256, 0, s, (const float *)dn, p->permY, ny, p->nY,
+                       p->nYlo);
     }
     for (int l = 0; l <= ls; ++l)
         if (p->far[l].n_adm > 0) build_octants(p, l, tj);

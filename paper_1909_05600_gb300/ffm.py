@@ -20,7 +20,7 @@ except ImportError:  # pragma: no cover - torch is part of the environment
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libffm_gb300.so")
 
-LAPLACE, HELMHOLTZ = 0, 1
+LAPLACE, HELMHOLTZ, LAPLACE_DL = 0, 1, 2
 F32, F64, C64, C128 = 0, 1, 2, 3
 # plane-wave level arithmetic (ffm_precision)
 PREC_AUTO, PREC_F32, PREC_F32C, PREC_F64, PREC_F32X2 = 0, 1, 2, 3, 4
@@ -45,7 +45,8 @@ class FFMError(RuntimeError):
 class Opts(C.Structure):
     _fields_ = [("n_leaf", C.c_int), ("l_cap", C.c_int), ("kappa_switch", C.c_double), ("r1_override", C.c_int),
                 ("precision", C.c_int), ("weights", C.c_void_p), ("weights_dtype", C.c_int),
-                ("autotune_cache", C.c_char_p), ("lagrange_transfer", C.c_int)]
+                ("autotune_cache", C.c_char_p), ("lagrange_transfer", C.c_int), ("normals", C.c_void_p),
+                ("normals_dtype", C.c_int)]
 
 
 class Info(C.Structure):
@@ -239,11 +240,15 @@ class Plan:
 
     def __init__(self, X, Y, kernel, k=0.0, eps=1e-3, weights=None, stream=None, n_leaf=0, l_cap=0,
                  kappa_switch=0.0, r1_override=0, precision=PREC_AUTO, autotune_cache=None,
-                 lagrange_transfer=0):
+                 lagrange_transfer=0, normals=None):
+        """normals: (ny, 3) source normals, required for LAPLACE_DL (double layer)."""
         self._h = None
-        self._keep = (X, Y, weights)
+        self._keep = (X, Y, weights, normals)
         o = Opts(n_leaf, l_cap, float(kappa_switch), r1_override, int(precision), None, F64,
-                 autotune_cache.encode() if autotune_cache else None, int(lagrange_transfer))
+                 autotune_cache.encode() if autotune_cache else None, int(lagrange_transfer), None, F64)
+        if normals is not None:
+            o.normals = _ptr(normals)
+            o.normals_dtype = _dtype_code(normals)
         if weights is not None:
             o.weights = _ptr(weights)
             o.weights_dtype = _dtype_code(weights)
