@@ -41,7 +41,7 @@ def parse():
     ap.add_argument("--impl", default="ffm", choices=["ffm", "reference"])
     ap.add_argument("--workload", default="helmholtz_sphere_1M",
                     choices=["helmholtz_sphere_1M", "laplace_sphere_20k", "helmholtz_cube_200k_64rhs",
-                             "laplace_clustered"])
+                             "laplace_clustered", "laplace_double_layer_sphere_1M"])
     ap.add_argument("--n", type=int, default=0, help="points per set (0: the workload's own size)")
     ap.add_argument("--serving", action="store_true",
                     help="serving stream: Poisson arrivals of mixed requests, p50/p99 latency and throughput")
@@ -65,6 +65,8 @@ def make_problem(name, seed, n=0):
         return W.helmholtz_cube_multirhs(n or 200_000, nrhs=64, seed=seed, eps=1e-4)
     if name == "laplace_clustered":
         return W.laplace_clustered(n or 100_000_000, seed=seed)
+    if name == "laplace_double_layer_sphere_1M":
+        return W.laplace_double_layer_sphere(n or 1_000_000, seed=seed)
     return W.laplace_sphere(n or 20000, seed=seed)
 
 
@@ -135,7 +137,10 @@ def cpu_direct_sample(prob, ntargets, seed=12345):
     t = W.sample_targets(prob.X.shape[0], ntargets, seed)
     u = prob.u.astype(np.complex128) if np.iscomplexobj(prob.u) else prob.u.astype(np.float64)
     t0 = time.perf_counter()
-    ref = O.direct(prob.X, prob.Y, u, prob.kind, prob.k, w=prob.w, targets=t)  # (targets, nrhs)
+    if "normals" in prob.meta:  # the double layer
+        ref = O.direct_dl(prob.X, prob.Y, prob.meta["normals"], u, w=prob.w, targets=t)
+    else:
+        ref = O.direct(prob.X, prob.Y, u, prob.kind, prob.k, w=prob.w, targets=t)  # (targets, nrhs)
     dt = time.perf_counter() - t0
     return t, ref, dt, O.nthreads()
 
@@ -145,12 +150,12 @@ def reference_targets(prob):
     return int(min(prob.X.shape[0], max(64, 1.2e9 // prob.Y.shape[0])))
 
 
-def repeat_applies(ffm, torch, prob, X, Y, w, u, flush, stream, reps, tune_cache=None):
+def repeat_applies(ffm, torch, prob, X, Y, w, u, flush, stream, reps, tune_cache=None, kw=None):
     """Repeated products with one resident plan (an iterative solver's use): eager
     ffm_apply calls against launches of the same apply captured as a CUDA graph.  Device
     time per product with an L2 flush before each one (outside its events)."""
     out = torch.empty_like(u)
-    with ffm.Plan(X, Y, prob.kind, prob.k, prob.eps, weights=w, autotune_cache=tune_cache) as p:
+    with ffm.Plan(X, Y, prob.kind, prob.k, prob.eps, weights=w, autotune_cache=tune_cache, **(kw or {})) as p:
         def run(fn):
             fn()
             torch.cuda.synchronize()
@@ -228,14 +233,17 @@ def roofline(prof, info, steps, clk, pk, pk_kind, workload):
       serve a direction and its antipode, eq. 17's quadrature being symmetric); a Helmholtz
       near pair costs three (rsqrt, sin, cos).
     - Laplace near field: instruction issue, at one rsqrt and about nine FP32 operations
-      per pair (10 issue slots).
-    - Lagrange transfer: tensor cores, 2 r^2 FLOP per admissible pair (the single-precision
-      GEMM; the TF32 hi/lo split triples the MMA work but not the algorithmic work), against
+      per pair (10 issue slots).  Double-layer near field: the same pipe at 64 slots per
+      pair (hi+lo difference, rsqrt, cube, and the compensated dot product n.(x - y)).
+    - Lagrange transfer: tensor cores, 2 r r_K FLOP per admissible pair (r_K = r, or 3 r for
+      the double layer's stacked component kernels; the single-precision GEMM; the TF32 hi/lo split triples the MMA work but not the algorithmic work), against
       the measured BF16 peak times the nominal TF32/BF16 ratio (1.1 / 2.25)."""
     name, (nl, ms) = max(prof.items(), key=lambda kv: kv[1][1])
     mhz = pk.get("sm_max_mhz", 2070.0)
     clk_hz = mhz * 1e6
     helm = any(m == 2 for m in info["mode"])
+    dl = workload.startswith("laplace_double_layer")
+    kfac = 3 if dl else 1
     out = {"kernel": name, "launches_per_step": nl / steps, "ms_per_step": ms / steps,
            "traffic": measured_traffic(name, workload)}
     per_s = lambda units: units * steps / (ms * 1e-3)
@@ -252,13 +260,14 @@ def roofline(prof, info, steps, clk, pk, pk_kind, workload):
         out.update({"bound": "alu", "pipe": "MUFU", "unit": "Tops/s", "units_per_step": units,
                     "peak_basis": basis % ("%d MUFU results/clk" % MUFU_PER_SM_CLK)})
     elif "k_p2p" in name:
+        slots = 64 if dl else 10
         units = 1.0 * info["p2p_pairs"]
-        peak = SM_COUNT * 128 * clk_hz / 10.0
-        out.update({"bound": "alu", "pipe": "FP32 issue (10 slots per pair)", "unit": "Tpairs/s",
-                    "units_per_step": units, "peak_basis": basis % "128 lanes/clk / 10"})
+        peak = SM_COUNT * 128 * clk_hz / slots
+        out.update({"bound": "alu", "pipe": "FP32 issue (%d slots per pair)" % slots, "unit": "Tpairs/s",
+                    "units_per_step": units, "peak_basis": basis % ("128 lanes/clk / %d" % slots)})
     elif "k_lag_gemm" in name:
         variant = 2 if "_ts" in name else 1 if "_tc" in name else 0
-        units = sum(2.0 * (info["r1"][l] ** 3) ** 2 * info["n_adm"][l] for l in range(22)
+        units = sum(2.0 * kfac * (info["r1"][l] ** 3) ** 2 * info["n_adm"][l] for l in range(22)
                     if info["mode"][l] == 1 and info["tune_tc"][l] == variant)
         peak = pk.get("bf16_tflops", 1900.0) * 1e12 * (1.1 / 2.25)
         out.update({"bound": "tensor", "pipe": "TF32", "unit": "TFLOP/s", "units_per_step": units,
@@ -383,6 +392,8 @@ def main():
     u_host = np.ascontiguousarray(prob.u.T) if prob.u.ndim == 2 else prob.u  # (nrhs, n) for several RHS
     nrhs = 1 if prob.u.ndim == 1 else prob.u.shape[1]
     u = torch.as_tensor(u_host, device=dev)
+    # extra plan arguments: the source normals of the double layer
+    kw = {"normals": torch.as_tensor(prob.meta["normals"], device=dev)} if "normals" in prob.meta else {}
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
 
@@ -394,7 +405,7 @@ def main():
         fd, tune_cache = tempfile.mkstemp(prefix="ffm_tune_", suffix=".txt")
         os.close(fd)
         t0 = time.perf_counter()
-        with ffm.Plan(X, Y, prob.kind, prob.k, prob.eps, weights=w) as pt:
+        with ffm.Plan(X, Y, prob.kind, prob.k, prob.eps, weights=w, **kw) as pt:
             ti = pt.autotune(nrhs=nrhs, cache_path=tune_cache)
         tune = {"seconds": time.perf_counter() - t0, "p2p_tchunk": ti["p2p_tchunk"], "p2p_smax": ti["p2p_smax"],
                 "tune_tc": [ti["tune_tc"][l] for l in range(ti["l_stop"] + 1)],
@@ -404,7 +415,7 @@ def main():
     def step(events=None):
         if events:
             events[0].record(stream)
-        p = ffm.Plan(X, Y, prob.kind, prob.k, prob.eps, weights=w, autotune_cache=tune_cache)
+        p = ffm.Plan(X, Y, prob.kind, prob.k, prob.eps, weights=w, autotune_cache=tune_cache, **kw)
         if events:
             events[1].record(stream)
         v = p.apply(u)
@@ -418,7 +429,7 @@ def main():
         flush.zero_()
         v, _ = step()
     torch.cuda.synchronize()
-    with ffm.Plan(X, Y, prob.kind, prob.k, prob.eps, weights=w, autotune_cache=tune_cache) as p0:
+    with ffm.Plan(X, Y, prob.kind, prob.k, prob.eps, weights=w, autotune_cache=tune_cache, **kw) as p0:
         info = p0.info()
 
     def timed(profiled):
@@ -451,7 +462,7 @@ def main():
 
     vlast, t_plan, t_apply, clk, launches, _ = timed(False)
     _, tp_plan, tp_apply, _, _, prof = timed(True)
-    rep = repeat_applies(ffm, torch, prob, X, Y, w, u, flush, stream, max(3, args.steps), tune_cache)
+    rep = repeat_applies(ffm, torch, prob, X, Y, w, u, flush, stream, max(3, args.steps), tune_cache, kw)
     note = None
     if rejected(clk):
         note = "first timed run rejected (clock reasons %s); re-measured" % clk.get("reasons")
@@ -471,6 +482,7 @@ def main():
         Yh = torch.as_tensor(prob.Y).pin_memory()
         wh = torch.as_tensor(prob.w).pin_memory()
         uh = torch.as_tensor(u_host).pin_memory()
+        kwh = {k: torch.as_tensor(prob.meta[k]).pin_memory() for k in kw}
         vh = torch.empty(tuple(uh.shape[:-1]) + (prob.X.shape[0],), dtype=uh.dtype).pin_memory()
         ke = max(2, args.steps // 2)
         ts = []
@@ -478,13 +490,13 @@ def main():
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             with ffm.Plan(Xh, Yh, prob.kind, prob.k, prob.eps, weights=wh, stream=stream,
-                          autotune_cache=tune_cache) as ph:
+                          autotune_cache=tune_cache, **kwh) as ph:
                 ph.apply(uh, out=vh, stream=stream)
             torch.cuda.synchronize()
             if i:
                 ts.append(time.perf_counter() - t0)
         h2d = Xh.numel() * Xh.element_size() + Yh.numel() * Yh.element_size() + wh.numel() * wh.element_size() \
-            + uh.numel() * uh.element_size()
+            + uh.numel() * uh.element_size() + sum(t.numel() * t.element_size() for t in kwh.values())
         e2e = {"value": world * len(ts) / sum(ts), "unit": "applies/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": vh.numel() * vh.element_size(), "steps": len(ts),
                "api": "ffm_plan(host X, Y, w) + ffm_apply(host u -> host v) + ffm_destroy"}
@@ -513,7 +525,8 @@ def main():
             "warmup": args.warmup, "ms_per_step": t_step / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": args.workload, "n_x": int(prob.X.shape[0]), "n_y": int(prob.Y.shape[0]),
-                       "kernel": "helmholtz" if prob.kind == 1 else "laplace", "k": prob.k, "eps": prob.eps,
+                       "kernel": {0: "laplace", 1: "helmholtz", 2: "laplace_double_layer"}[prob.kind],
+                       "k": prob.k, "eps": prob.eps,
                        "u_dtype": str(prob.u.dtype), "step": "ffm_plan + ffm_apply + ffm_destroy",
                        "l2": "flushed between steps (512 MiB write, outside the step events)",
                        "replicas": world, "nrhs": nrhs},
