@@ -36,6 +36,7 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#include "nufft_oracle.h"
 #ifdef _OPENMP
 #include <omp.h>
 #endif
@@ -648,6 +649,7 @@ typedef struct {
     double kappa_switch;
     int r1_override; /* 0: rule */
     int mode_override; /* 0: auto, 1: Lagrange everywhere, 2: plane waves everywhere */
+    int pw_transform;  /* plane-wave steps F: 0 direct sums, 1 type-3 NUFFT (nufft_oracle.c) */
 } orc_opts;
 
 typedef struct {
@@ -733,6 +735,7 @@ void orc_default_opts(orc_opts *o)
     o->kappa_switch = 2.0;
     o->r1_override = 0;
     o->mode_override = 0;
+    o->pw_transform = 0;
 }
 
 static int level_mode(const orc_plan *p, int l)
@@ -1065,9 +1068,38 @@ static void far_planewave(const orc_plan *p, int l, const double *qr, const doub
     const opair *adm = p->adm[l];
     char *used = (char *)calloc((size_t)nbY, 1);
     for (int64_t e = 0; e < na; ++e) used[adm[e].b] = 1;
+    /* NUFFT mode: the same sums as below, through the type-3 NUFFT of one box at a time
+     * (frequencies k s_q, points relative to the box centre) */
+    const int nufft = p->opt.pw_transform == 1;
+    double *ks = (double *)malloc(sizeof(double) * 3 * nq);
+    for (int i = 0; i < 3 * nq; ++i) ks[i] = k * s[i];
+    orc_nu nu;
+    if (nufft) orc_nu_init(&nu, dl, k, p->eps, ks, nq);
 #pragma omp parallel for schedule(dynamic, 1)
     for (int64_t b = 0; b < nbY; ++b) {
         if (!used[b]) continue;
+        if (nufft) {
+            const obox *B = &p->by[l][b];
+            double c[3];
+            box_centre(p->ty.o, B->g, dl, c);
+            int64_t nb = B->e - B->s;
+            double *xr = (double *)malloc(sizeof(double) * 3 * (nb > 0 ? nb : 1));
+            double *cr = (double *)malloc(sizeof(double) * (nb > 0 ? nb : 1));
+            double *ci = (double *)malloc(sizeof(double) * (nb > 0 ? nb : 1));
+            for (int64_t j = 0; j < nb; ++j)
+                for (int d = 0; d < 3; ++d) xr[3 * j + d] = p->ty.p[3 * (B->s + j) + d] - c[d];
+            for (int m = 0; m < nrhs; ++m) {
+                for (int64_t j = 0; j < nb; ++j) {
+                    cr[j] = qr[B->s + j + ny * m];
+                    ci[j] = qi[B->s + j + ny * m];
+                }
+                orc_nu_forward(&nu, xr, nb, cr, ci, utr + ((size_t)b * nrhs + m) * nq, uti + ((size_t)b * nrhs + m) * nq);
+            }
+            free(xr);
+            free(cr);
+            free(ci);
+            continue;
+        }
         const obox *B = &p->by[l][b];
         double c[3];
         box_centre(p->ty.o, B->g, dl, c);
@@ -1121,7 +1153,25 @@ static void far_planewave(const orc_plan *p, int l, const double *qr, const doub
                 }
             }
         }
-        for (int64_t i = A->s; i < A->e; ++i) {
+        if (nufft) {
+            int64_t na_ = A->e - A->s;
+            double *xr = (double *)malloc(sizeof(double) * 3 * (na_ > 0 ? na_ : 1));
+            double *or_ = (double *)malloc(sizeof(double) * (na_ > 0 ? na_ : 1));
+            double *oi = (double *)malloc(sizeof(double) * (na_ > 0 ? na_ : 1));
+            for (int64_t i = 0; i < na_; ++i)
+                for (int d = 0; d < 3; ++d) xr[3 * i + d] = p->tx.p[3 * (A->s + i) + d] - ca[d];
+            for (int m = 0; m < nrhs; ++m) {
+                orc_nu_adjoint(&nu, xr, na_, vtr + (size_t)m * nq, vti + (size_t)m * nq, or_, oi);
+                for (int64_t i = 0; i < na_; ++i) {
+                    accr[A->s + i + nx * m] += or_[i] / (4.0 * ORC_PI);
+                    acci[A->s + i + nx * m] += oi[i] / (4.0 * ORC_PI);
+                }
+            }
+            free(xr);
+            free(or_);
+            free(oi);
+        }
+        for (int64_t i = A->s; i < A->e && !nufft; ++i) {
             const double *x = p->tx.p + 3 * i;
             double d[3] = {x[0] - ca[0], x[1] - ca[1], x[2] - ca[2]};
             for (int m = 0; m < nrhs; ++m) {
@@ -1147,6 +1197,8 @@ static void far_planewave(const orc_plan *p, int l, const double *qr, const doub
     free(uti);
     free(s);
     free(w);
+    free(ks);
+    if (nufft) orc_nu_free(&nu);
 }
 
 /* Near field at the stop level (Sec. 2.2.4): the dense product over the remaining

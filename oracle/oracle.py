@@ -25,7 +25,7 @@ _u64p = C.POINTER(C.c_uint64)
 
 class Opts(C.Structure):
     _fields_ = [("n_leaf", C.c_int), ("l_cap", C.c_int), ("kappa_switch", C.c_double),
-                ("r1_override", C.c_int), ("mode_override", C.c_int)]
+                ("r1_override", C.c_int), ("mode_override", C.c_int), ("pw_transform", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -78,6 +78,18 @@ def lib():
         L.orc_sphere_quad.argtypes = [C.c_int, _dp, _dp]
         L.orc_hankel.argtypes = [C.c_int, C.c_double, _dp, _dp]
         L.orc_gegenbauer.argtypes = [C.c_double, _dp, C.c_int, _dp, _dp, _dp]
+        L.orc_nu_params.argtypes = [C.c_double, C.c_double, C.c_double, C.POINTER(C.c_int), _dp,
+                                    C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]
+        L.orc_nu_init.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_double, _dp, C.c_int]
+        L.orc_nu_init.restype = C.c_int
+        L.orc_nu_free.argtypes = [C.c_void_p]
+        L.orc_nu_forward.argtypes = [C.c_void_p, _dp, C.c_int64, _dp, _dp, _dp, _dp]
+        L.orc_nu_adjoint.argtypes = [C.c_void_p, _dp, C.c_int64, _dp, _dp, _dp, _dp]
+        L.orc_es_kernel.argtypes = [C.c_double, C.c_double]
+        L.orc_es_kernel.restype = C.c_double
+        L.orc_es_hat.argtypes = [C.c_double, C.c_double]
+        L.orc_es_hat.restype = C.c_double
+        L.orc_dft3.argtypes = [C.c_int, _dp, _dp, C.c_int]
         L.orc_pw_pair.argtypes = [C.c_double, C.c_int, _dp, _dp, _dp, _dp, _dp, _dp]
         L.orc_kernel_eval.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double, C.c_double, _dp, _dp]
         L.orc_direct_dl.argtypes = [_dp, C.c_int64, _dp, C.c_int64, _dp, _dp, _dp, C.c_int, _i64p, C.c_int64, _dp]
@@ -329,3 +341,85 @@ def rel_l2(v, ref):
 
 if os.environ.get("FFM_ORACLE_THREADS"):
     set_threads(int(os.environ["FFM_ORACLE_THREADS"]))
+
+
+# ---------------------------------------------------------------- type-3 NUFFT (Sec. 2.2.3)
+
+class _Nu(C.Structure):
+    _fields_ = [("w", C.c_int), ("beta", C.c_double), ("M", C.c_int), ("h", C.c_double), ("n1", C.c_int),
+                ("n2", C.c_int), ("nq", C.c_int), ("s", _dp), ("corr", _dp), ("cinv", _dp)]
+
+
+def nufft_params(d, k, eps):
+    """(w, beta, M, n1, n2) of the NUFFT reading for a box of edge d at wavenumber k."""
+    w, M, n1, n2 = C.c_int(), C.c_int(), C.c_int(), C.c_int()
+    beta = C.c_double()
+    lib().orc_nu_params(float(d), float(k), float(eps), C.byref(w), C.byref(beta), C.byref(M), C.byref(n1),
+                        C.byref(n2))
+    return w.value, beta.value, M.value, n1.value, n2.value
+
+
+class Nufft:
+    """Type-3 NUFFT of one box: forward F_q = sum_j c_j e^{-i s_q.x_j} and its adjoint
+    v_j = sum_q z_q e^{+i s_q.x_j}; x box-centred in [-d/2, d/2]^3, s = k shat."""
+
+    def __init__(self, d, k, eps, s):
+        self.s = _c64(s).reshape(-1, 3)
+        self._nu = _Nu()
+        if lib().orc_nu_init(C.byref(self._nu), float(d), float(k), float(eps), _d(self.s), self.s.shape[0]):
+            raise MemoryError("orc_nu_init")
+
+    def close(self):
+        if getattr(self, "_nu", None) is not None:
+            lib().orc_nu_free(C.byref(self._nu))
+            self._nu = None
+
+    def __del__(self):
+        self.close()
+
+    @property
+    def params(self):
+        return dict(w=self._nu.w, beta=self._nu.beta, M=self._nu.M, h=self._nu.h, n1=self._nu.n1, n2=self._nu.n2)
+
+    def forward(self, x, c):
+        x = _c64(x).reshape(-1, 3)
+        c = np.asarray(c, np.complex128)
+        cr, ci = _c64(c.real), _c64(c.imag)
+        nq = self.s.shape[0]
+        Fr, Fi = np.zeros(nq), np.zeros(nq)
+        lib().orc_nu_forward(C.byref(self._nu), _d(x), x.shape[0], _d(cr), _d(ci), _d(Fr), _d(Fi))
+        return Fr + 1j * Fi
+
+    def adjoint(self, x, z):
+        x = _c64(x).reshape(-1, 3)
+        z = np.asarray(z, np.complex128)
+        zr, zi = _c64(z.real), _c64(z.imag)
+        vr, vi = np.zeros(x.shape[0]), np.zeros(x.shape[0])
+        lib().orc_nu_adjoint(C.byref(self._nu), _d(x), x.shape[0], _d(zr), _d(zi), _d(vr), _d(vi))
+        return vr + 1j * vi
+
+
+def es_kernel(z, beta):
+    return lib().orc_es_kernel(float(z), float(beta))
+
+
+def es_hat(xi, beta):
+    return lib().orc_es_hat(float(xi), float(beta))
+
+
+def dft3(a, sign):
+    """The oracle's 3-D DFT of an n^3 complex array, sum_j a_j e^{sign 2 pi i j.k / n}."""
+    a = np.asarray(a, np.complex128)
+    n = a.shape[0]
+    re, im = _c64(a.real.ravel()), _c64(a.imag.ravel())
+    lib().orc_dft3(n, _d(re), _d(im), int(sign))
+    return (re + 1j * im).reshape(a.shape)
+
+
+def ffm_nufft(X, Y, u, kind, k, eps, w=None, **opts):
+    """O2 with the plane-wave steps computed by the type-3 NUFFT."""
+    with_p = Plan(X, Y, kind, k, eps, pw_transform=1, **opts)
+    try:
+        return with_p.apply(u, w=w)
+    finally:
+        with_p.close()

@@ -444,3 +444,93 @@ def test_ffm_degenerate_inputs():
         O.Plan(one, one, O.LAPLACE, 0.0, 0.0)
     with pytest.raises(ValueError):
         O.Plan(one, one, O.HELMHOLTZ, -1.0, 1e-3)
+
+
+# ------------------------------------------- type-3 NUFFT of the plane-wave steps (Sec. 2.2.3)
+
+def _box_problem(seed, n=1500, nq=600, d=0.5, k=60.0):
+    rng = np.random.default_rng(seed)
+    x = rng.uniform(-d / 2, d / 2, (n, 3))
+    c = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    s = k * _unit_dirs(nq, seed + 7)
+    return d, k, x, c, s
+
+
+@pytest.mark.parametrize("eps", [1e-3, 1e-4])
+def test_nufft_forward_and_adjoint_match_the_exponential_sums(eps):
+    """Against the plain sums F_q = sum_j c_j e^{-i s_q.x_j} and v_j = sum_q z_q e^{+i s_q.x_j}
+    (brute force), within eps / 100: the kernel width makes the NUFFT error that small."""
+    d, k, x, c, s = _box_problem(5)
+    nu = O.Nufft(d, k, eps, s)
+    F = nu.forward(x, c)
+    ex = np.exp(-1j * (s @ x.T)) @ c
+    assert O.rel_l2(F, ex) < eps / 100
+    z = np.random.default_rng(6).standard_normal(len(s)) * (1 + 0.5j)
+    v = nu.adjoint(x, z)
+    exv = np.exp(1j * (x @ s.T)) @ z
+    assert O.rel_l2(v, exv) < eps / 100
+
+
+def test_nufft_single_point_is_a_plane_wave_and_the_adjoint_is_the_transpose():
+    d, k, x, c, s = _box_problem(8, n=1, nq=300)
+    x[0] = [0.249, -0.25, 0.1]  # on the box faces
+    nu = O.Nufft(d, k, 1e-4, s)
+    F = nu.forward(x, np.ones(1))
+    assert np.max(np.abs(F - np.exp(-1j * (s @ x[0])))) < 1e-5  # eps / 10 in the max norm
+    d, k, x, c, s = _box_problem(9, n=700, nq=400)
+    nu = O.Nufft(d, k, 1e-3, s)
+    z = np.random.default_rng(10).standard_normal(len(s)) + 1j
+    lhs = np.vdot(z, nu.forward(x, c))
+    rhs = np.vdot(nu.adjoint(x, z), c)
+    assert abs(lhs - rhs) < 1e-12 * abs(lhs)
+
+
+@pytest.mark.parametrize("n", [7, 12, 30, 35])
+def test_oracle_dft_matches_numpy_fft(n):
+    """The oracle's mixed-radix DFT (prime lengths summed directly) against numpy.fft."""
+    rng = np.random.default_rng(n)
+    a = rng.standard_normal((n, n, n)) + 1j * rng.standard_normal((n, n, n))
+    assert np.max(np.abs(O.dft3(a, -1) - np.fft.fftn(a))) < 1e-10 * n ** 3
+    assert np.max(np.abs(O.dft3(a, +1) - np.fft.ifftn(a) * n ** 3)) < 1e-10 * n ** 3
+
+
+def test_es_kernel_transform_matches_adaptive_quadrature():
+    integrate = pytest.importorskip("scipy.integrate")
+    for w in (6, 8, 10):
+        beta = 2.30 * w
+        assert O.es_kernel(0.0, beta) == 1.0 and O.es_kernel(1.5, beta) == 0.0
+        assert abs(O.es_kernel(1.0, beta) - math.exp(-beta)) < 1e-15
+        for xi in (0.0, 1.3, 0.84 * w):
+            ref = integrate.quad(lambda z: O.es_kernel(z, beta) * math.cos(xi * z), -1, 1, epsabs=1e-14,
+                                 limit=200)[0]
+            assert abs(O.es_hat(xi, beta) - ref) < 1e-9 * abs(ref)
+
+
+def test_nufft_parameter_rule():
+    """Width from eps, the spreading grid fine enough that 2 pi / h - k clears the kernel's
+    band (k h <= 2 pi - 2 beta / w), the FFT grid twice the spreading grid and 7-smooth."""
+    for d, k, eps in [(0.5, 177.2, 1e-3), (0.25, 177.2, 1e-4), (1.0, 3.0, 1e-2), (0.1, 900.0, 1e-6)]:
+        w, beta, M, n1, n2 = O.nufft_params(d, k, eps)
+        assert w == min(12, max(6, math.ceil(-math.log10(eps)) + 4))
+        assert k * d / M <= 2 * math.pi - 2 * beta / w < k * d / (M - 1) if M > 1 else True
+        assert n1 >= M + w + 2 and n1 % 2 == 0
+        assert n2 >= 2 * n1
+        m = n2
+        for p in (2, 3, 5, 7):
+            while m % p == 0:
+                m //= p
+        assert m == 1
+
+
+@pytest.mark.parametrize("eps", [1e-3, 1e-4])
+def test_ffm_with_nufft_within_eps(eps):
+    """O2 with the NUFFT plane-wave steps against O1 (eps) and against O2 with direct
+    sums (within eps / 10: the transform error, ~eps / 200, is amplified by the
+    cancellation of the quadrature sums at the small-kd levels) on the Helmholtz sphere."""
+    prob = W.helmholtz_sphere(8000, seed=2, eps=eps)
+    vn = O.ffm_nufft(prob.X, prob.Y, prob.u, prob.kind, prob.k, eps, w=prob.w)[:, 0]
+    vd = O.ffm(prob.X, prob.Y, prob.u, prob.kind, prob.k, eps, w=prob.w)[:, 0]
+    ref = O.direct(prob.X, prob.Y, prob.u, prob.kind, prob.k, w=prob.w)[:, 0]
+    assert O.rel_l2(vn, ref) < eps
+    assert O.rel_l2(vn, vd) < eps / 10
+    assert O.Plan(prob.X, prob.Y, prob.kind, prob.k, eps).stats()["mode"][2] == O.MODE_PLANEWAVE
