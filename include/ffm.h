@@ -106,6 +106,11 @@ typedef struct {
     const void *normals;        /* FFM_LAPLACE_DL: N_Y x 3 row-major source normals (any
                                    length; the kernel is linear in n), host or device; copied */
     ffm_dtype normals_dtype;    /* FFM_F32 or FFM_F64 */
+    int pw_transform;           /* plane-wave source and target steps F_{Y->s}, F_{s->X} (Sec.
+                                   2.2.3): 0 chosen per level (the type-3 NUFFT on FP32 levels
+                                   with many directions, direct sums elsewhere, or
+                                   ffm_autotune's pick), 1 direct sums everywhere, 2 the NUFFT
+                                   on every FP32 and compensated-FP32 plane-wave level */
 } ffm_opts;
 
 /* Build a plan for targets X (nx points) and sources Y (ny points) (Sec. 2.2.1-2.2.4):
@@ -175,6 +180,9 @@ typedef struct {
                                   target-stationary (one write per target box) */
     int tune_pw[22][3];        /* plane-wave levels: direction pairs per thread (forward), points
                                   per thread (backward), right-hand sides per thread (several) */
+    int nufft[22];             /* plane-wave levels whose F steps run as type-3 NUFFTs (1) */
+    int nufft_w[22];           /* their spreading-kernel width */
+    int nufft_n2[22];          /* their FFT grid edge (n2^3 per box) */
 } ffm_info;
 
 ffm_status ffm_plan_info(const ffm_plan_t *plan, ffm_info *info);

@@ -14,7 +14,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libffm_gb300.so")
-SOURCES = ["tree.cu", "tables.cu", "farfield.cu", "nearfield.cu", "ffm_api.cu", "noalloc.cu", "autotune.cu"]
+SOURCES = ["tree.cu", "tables.cu", "farfield.cu", "nearfield.cu", "ffm_api.cu", "noalloc.cu", "autotune.cu",
+           "nufft.cu"]
 ARCH = os.environ.get("FFM_CUDA_ARCH", "103a")
 
 NVCC_FLAGS = ["-gencode", "arch=compute_%s,code=sm_%s" % (ARCH, ARCH), "-O3", "-lineinfo", "-std=c++17",
@@ -61,7 +62,7 @@ def build(force=False, verbose=False, extra=()):
     if jobs or force or not os.path.exists(LIB):
         tmp = LIB + ".tmp%d" % os.getpid()
         run([nvcc, "-shared", "-gencode", "arch=compute_%s,code=sm_%s" % (ARCH, ARCH), "-o", tmp, *objs,
-             "-lcudart"])
+             "-lcudart", "-lcufft", "-Xlinker", "-rpath,/usr/local/cuda/lib64"])
         os.replace(tmp, LIB)
     return LIB
 

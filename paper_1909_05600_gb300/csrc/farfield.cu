@@ -1585,7 +1585,10 @@ static void planewave_level(const ffm_plan_s *p, int l, const float2 *q, int nrh
     for (int cand : {64, 32})
         if ((double)cdiv(nH, tb * qpt) * tb * qpt > 1.1 * nH) tb = cand;
     bool multi = nrhs > 1;
-    if (multi) {
+    constexpr bool f32 = std::is_same<R, float>::value;
+    if (f32 && F.nufft) {
+        if constexpr (f32) nufft_forward(p, l, q, nrhs, ut, tmp, s);
+    } else if (multi) {
         if (!dbl && mc == 4) {
             dim3 gm((unsigned)F.n_src, cdiv(nH, 128), cdiv(nrhs, 4));
             FFM_LAUNCH_NAMED(name("k_pw_forward_mr"), (k_pw_forward_mr<R, PH, dbl ? 8 : 4>), gm, 128, 0, s, PY, F.src,
@@ -1611,6 +1614,12 @@ static void planewave_level(const ffm_plan_s *p, int l, const float2 *q, int nrh
     else
         FFM_LAUNCH_NAMED(name("k_pw_transfer"), (k_pw_transfer<C2, 8, COMP>), gt, 128, 0, s, F.tgt, F.adm_off,
                          F.adm_src, F.adm_t, D, F.nQ, nrhs, (const C2 *)ut, vt);
+    if constexpr (f32) {
+        if (F.nufft) {
+            nufft_backward(p, l, vt, nrhs, acc, tmp, s);
+            return;
+        }
+    }
     int64_t nbx = p->bx[l].nb;
     int *slot = tmp.get<int>(nbx);
     FFM_LAUNCH(k_slot_init, cdiv(nbx, 256), 256, 0, s, slot, nbx);

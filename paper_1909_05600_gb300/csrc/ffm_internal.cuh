@@ -19,6 +19,8 @@ constexpr int R1MAX = 8;         // largest Chebyshev node count per axis
 constexpr int LAG_GEMM_BN = 32;  // pairs (GEMM columns) per tile of the Lagrange transfer
 constexpr int P2P_T = 128;        // threads per near-field block (the largest target chunk)
 constexpr int LAG_CHUNK = 512;    // points per block of the Lagrange point-wise kernels
+constexpr int NUFFT_MIN_NQ = 8000; // plane-wave levels with at least this many directions run
+                                   // their F steps as NUFFTs (unless forced either way)
 constexpr double PI = 3.14159265358979323846;
 
 // ---------------------------------------------------------------- errors
@@ -116,6 +118,23 @@ struct BoxLevel {
     uint32_t *fine = nullptr;   // nb: index of the first box of the deepest table
 };
 
+// Type-3 NUFFT of a plane-wave level (nufft.cu): grids, direction windows, point blocks
+struct NuLevel {
+    int w = 0, M = 0, n1 = 0, n2 = 0;  // kernel width, cells per box edge, spreading / FFT grid edges
+    double beta = 0, h = 0;             // kernel shape, spreading-grid spacing
+    int dlt = 0, E = 0;                 // bin level below the level, bin subgrid edge
+    float *cinv = nullptr;              // n1: FFT-grid kernel deconvolution
+    int4 *dirU = nullptr;               // nQ: first window node per axis (centred FFT-grid index)
+    float *dirW = nullptr;              // nQ x 3 x w: window kernel values, correction on axis 0
+    int64_t n_tiles = 0;                // FFT-grid tiles reached by some direction
+    uint32_t *tile_id = nullptr, *tile_off = nullptr, *tile_q = nullptr;
+    int64_t n_ych = 0, n_xch = 0;       // point blocks (bin, first, end, slot) of sources / targets
+    int4 *ych = nullptr, *xch = nullptr;
+    int fft_src = 0, fft_tgt = 0;       // cuFFT handles (batched over the level's source / target boxes)
+    size_t work_src = 0, work_tgt = 0;
+    bool has_fft = false;
+};
+
 struct FarLevel {
     int mode = 0;        // 0 none, 1 Lagrange, 2 plane waves
     int r1 = 0, L = 0, nQ = 0;
@@ -166,11 +185,19 @@ struct FarLevel {
     dd4 *ksx = nullptr;             // double-float levels
     dd2 *Dx = nullptr;
     dd2 *Ex = nullptr;
+    int nufft = 0;                  // F steps as type-3 NUFFTs (FP32 plane-wave levels)
+    NuLevel nu;
 };
 
 }  // namespace ffm
 
+struct ffm_plan_s;
+namespace ffm {
+void nufft_release(ffm_plan_s *p);  // nufft.cu: cuFFT handles
+}
+
 struct ffm_plan_s {
+    ~ffm_plan_s() { ffm::nufft_release(this); }
     int64_t nx = 0, ny = 0;
     int kind = 0;
     double k = 0, eps = 0;
@@ -180,6 +207,7 @@ struct ffm_plan_s {
     int precision = 0;  // ffm_precision for the plane-wave levels, 0 = by cancellation
     float4 *sctab = nullptr;  // sin/cos(j/64) in double-float for the double-float levels
     int lag_transfer = 0;     // ffm_opts.lagrange_transfer
+    int pw_transform = 0;     // ffm_opts.pw_transform
     const void *normals_in = nullptr;  // double layer: caller's normals (during ffm_plan only)
     ffm_dtype normals_dt = FFM_F64;
     float4 *nY = nullptr;     // double layer: source normals in Morton order, hi and lo parts
@@ -256,6 +284,13 @@ inline bool real_kernel(int kind) { return kind != FFM_HELMHOLTZ; }
 void far_planewave(const ffm_plan_s *p, int l, const float2 *q, int nrhs, double2 *acc, Alloc &tmp,
                    cudaStream_t s);
 void near_field(const ffm_plan_s *p, const void *q, int nrhs, double2 *acc, cudaStream_t s);
+// nufft.cu: the plane-wave F steps of level l as type-3 NUFFTs (FP32 levels)
+bool nufft_possible(const ffm_plan_s *p, int l);
+void build_nufft(ffm_plan_s *p, int l, Alloc &tmp, cudaStream_t s);
+void nufft_forward(const ffm_plan_s *p, int l, const float2 *q, int nrhs, float2 *ut, Alloc &tmp, cudaStream_t s);
+void nufft_backward(const ffm_plan_s *p, int l, const float2 *vt, int nrhs, double2 *acc, Alloc &tmp,
+                    cudaStream_t s);
+void gauss_legendre_nodes(int n, std::vector<double> &x, std::vector<double> &w);  // tables.cu
 // autotune.cu: pick kernel variants by timing them on the plan (ffm_autotune)
 void autotune(ffm_plan_s *p, int nrhs, const char *cache_path, cudaStream_t s);
 // take the picks a cache file holds for this plan's sizes (no timing); at plan creation

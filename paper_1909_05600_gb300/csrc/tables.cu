@@ -289,6 +289,8 @@ static void gauss_legendre(int n, std::vector<double> &x, std::vector<double> &w
     }
 }
 
+void gauss_legendre_nodes(int n, std::vector<double> &x, std::vector<double> &w) { gauss_legendre(n, x, w); }
+
 // h_p^(1)(z), p = 0..L, upward recurrence from h_0 = -i e^{iz}/z, h_1 = -e^{iz}(z+i)/z^2.
 static void hankel1(int L, double z, std::vector<double> &hr, std::vector<double> &hi) {
     hr.assign(L + 1, 0.0);

@@ -1307,6 +1307,17 @@ void build_plan(ffm_plan_s *p, const void *X, ffm_dtype xdt, const void *Y, ffm_
         if (p->far[l].n_adm > 0) build_octants(p, l, tj);
     if (p->lag_transfer == 3)
         for (int l = 0; l <= ls; ++l) prepare_target_stationary(p, l, s);
+    // plane-wave levels whose F steps run as type-3 NUFFTs: FP32 levels with many directions
+    // (the NUFFT's cost per box barely depends on nQ, the direct sums' grows with it), all
+    // FP32 and compensated-FP32 levels when forced, none when direct sums are forced
+    for (int l = 0; l <= ls; ++l) {
+        const FarLevel &F = p->far[l];
+        if (F.mode != 2 || F.n_adm == 0) continue;
+        bool want = p->pw_transform == 2   ? (F.prec == FFM_PREC_F32 || F.prec == FFM_PREC_F32C)
+                    : p->pw_transform == 1 ? false
+                                           : (F.prec == FFM_PREC_F32 && F.nQ >= NUFFT_MIN_NQ);
+        if (want && nufft_possible(p, l)) build_nufft(p, l, tmp, s);
+    }
     FFM_CUDA(cudaStreamSynchronize(s));
 }
 

@@ -26,6 +26,8 @@ F32, F64, C64, C128 = 0, 1, 2, 3
 PREC_AUTO, PREC_F32, PREC_F32C, PREC_F64, PREC_F32X2 = 0, 1, 2, 3, 4
 # Lagrange transfer variants (ffm_opts.lagrange_transfer)
 LAG_DEFAULT, LAG_CUDA_CORES, LAG_TC_TRANSLATION, LAG_TC_TARGET = 0, 1, 2, 3
+# plane-wave source / target steps (ffm_opts.pw_transform)
+PW_AUTO, PW_DIRECT, PW_NUFFT = 0, 1, 2
 EXPORT_PERM_X, EXPORT_PERM_Y, EXPORT_ADM, EXPORT_NEAR = 0, 1, 2, 3
 STATUS = {0: "FFM_OK", 1: "FFM_EINVAL", 2: "FFM_ENOMEM", 3: "FFM_ECUDA", 4: "FFM_ETIMEOUT", 5: "FFM_EUNSUPPORTED"}
 
@@ -46,7 +48,7 @@ class Opts(C.Structure):
     _fields_ = [("n_leaf", C.c_int), ("l_cap", C.c_int), ("kappa_switch", C.c_double), ("r1_override", C.c_int),
                 ("precision", C.c_int), ("weights", C.c_void_p), ("weights_dtype", C.c_int),
                 ("autotune_cache", C.c_char_p), ("lagrange_transfer", C.c_int), ("normals", C.c_void_p),
-                ("normals_dtype", C.c_int)]
+                ("normals_dtype", C.c_int), ("pw_transform", C.c_int)]
 
 
 class Info(C.Structure):
@@ -58,7 +60,8 @@ class Info(C.Structure):
                 ("tgt_points", C.c_int64 * 22), ("p2p_pairs", C.c_int64), ("pw_prec", C.c_int * 22),
                 ("cancel", C.c_double * 22), ("device_errors", C.c_int), ("autotuned", C.c_int),
                 ("p2p_tchunk", C.c_int), ("p2p_smax", C.c_int), ("tune_tc", C.c_int * 22),
-                ("tune_pw", (C.c_int * 3) * 22)]
+                ("tune_pw", (C.c_int * 3) * 22), ("nufft", C.c_int * 22), ("nufft_w", C.c_int * 22),
+                ("nufft_n2", C.c_int * 22)]
 
     def as_dict(self):
         d = {"l_stop": self.l_stop, "root_admissible": self.root_admissible, "d0": self.d0, "oX": list(self.oX),
@@ -66,7 +69,7 @@ class Info(C.Structure):
              "device_errors": self.device_errors, "autotuned": self.autotuned, "p2p_tchunk": self.p2p_tchunk,
              "p2p_smax": self.p2p_smax, "tune_pw": [list(r) for r in self.tune_pw]}
         for f in ("nboxX", "nboxY", "n_adm", "n_near", "n_trans", "mode", "r1", "L", "nQ", "src_points",
-                  "tgt_points", "pw_prec", "cancel", "tune_tc"):
+                  "tgt_points", "pw_prec", "cancel", "tune_tc", "nufft", "nufft_w", "nufft_n2"):
             d[f] = list(getattr(self, f))
         return d
 
@@ -240,12 +243,14 @@ class Plan:
 
     def __init__(self, X, Y, kernel, k=0.0, eps=1e-3, weights=None, stream=None, n_leaf=0, l_cap=0,
                  kappa_switch=0.0, r1_override=0, precision=PREC_AUTO, autotune_cache=None,
-                 lagrange_transfer=0, normals=None):
-        """normals: (ny, 3) source normals, required for LAPLACE_DL (double layer)."""
+                 lagrange_transfer=0, normals=None, pw_transform=PW_AUTO):
+        """normals: (ny, 3) source normals, required for LAPLACE_DL (double layer).
+        pw_transform: PW_AUTO, PW_DIRECT or PW_NUFFT for the plane-wave levels' F steps."""
         self._h = None
         self._keep = (X, Y, weights, normals)
         o = Opts(n_leaf, l_cap, float(kappa_switch), r1_override, int(precision), None, F64,
-                 autotune_cache.encode() if autotune_cache else None, int(lagrange_transfer), None, F64)
+                 autotune_cache.encode() if autotune_cache else None, int(lagrange_transfer), None, F64,
+                 int(pw_transform))
         if normals is not None:
             o.normals = _ptr(normals)
             o.normals_dtype = _dtype_code(normals)
