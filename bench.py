@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--cpu-targets", type=int, default=4096)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--pw-transform", default="auto", choices=["auto", "direct", "nufft"],
+                    help="plane-wave F steps: chosen per level, direct sums, or the NUFFT where possible")
     ap.add_argument("--no-autotune", action="store_true",
                     help="default kernel variants instead of ffm_autotune's picks")
     return ap.parse_args()
@@ -235,10 +237,14 @@ def roofline(prof, info, steps, clk, pk, pk_kind, workload):
     - Laplace near field: instruction issue, at one rsqrt and about nine FP32 operations
       per pair (10 issue slots).  Double-layer near field: the same pipe at 64 slots per
       pair (hi+lo difference, rsqrt, cube, and the compensated dot product n.(x - y)).
+    - Gegenbauer transfer tables: FP32 issue, 72 instructions per recurrence step (double-float).
+    - NUFFT grid kernels: the FP32 pipe, 4 FLOP per complex x real multiply-add of a W^3
+      kernel window (per direction and box, or per point).
     - Lagrange transfer: tensor cores, 2 r r_K FLOP per admissible pair (r_K = r, or 3 r for
       the double layer's stacked component kernels; the single-precision GEMM; the TF32 hi/lo split triples the MMA work but not the algorithmic work), against
       the measured BF16 peak times the nominal TF32/BF16 ratio (1.1 / 2.25)."""
-    name, (nl, ms) = max(prof.items(), key=lambda kv: kv[1][1])
+    # the dominant kernel of this library (library calls such as cuFFT are listed, not ranked)
+    name, (nl, ms) = max(((k, v) for k, v in prof.items() if "(library)" not in k), key=lambda kv: kv[1][1])
     mhz = pk.get("sm_max_mhz", 2070.0)
     clk_hz = mhz * 1e6
     helm = any(m == 2 for m in info["mode"])
@@ -265,6 +271,32 @@ def roofline(prof, info, steps, clk, pk, pk_kind, workload):
         peak = SM_COUNT * 128 * clk_hz / slots
         out.update({"bound": "alu", "pipe": "FP32 issue (%d slots per pair)" % slots, "unit": "Tpairs/s",
                     "units_per_step": units, "peak_basis": basis % ("128 lanes/clk / %d" % slots)})
+    elif "k_pw_table" in name:
+        # Gegenbauer transfer tables: per recurrence (translation pair, direction pair) and
+        # degree, a Legendre step and the even / odd partial sums in double-float arithmetic,
+        # 4 multiplies (7 FP32 instructions) and 4 adds (11) = 72 FP32 instructions
+        units = 72.0 * sum(info["pw_recurrences"][l] * info["L"][l] for l in range(22) if info["mode"][l] == 2)
+        peak = SM_COUNT * 128 * clk_hz
+        out.update({"bound": "alu", "pipe": "FP32 issue (double-float)", "unit": "Tops/s", "units_per_step": units,
+                    "peak_basis": basis % "128 lanes/clk"})
+    elif "k_nu_" in name:
+        # NUFFT grid kernels: complex x real multiply-adds (4 FLOP) of the W^3 kernel windows,
+        # per direction and box (interpolation at the directions, spread of v~) or per point
+        # (spread of the charges, interpolation at the targets), on the FP32 pipe
+        lv = [l for l in range(22) if info["nufft"][l]]
+        w3 = lambda l: float(info["nufft_w"][l]) ** 3
+        if "k_nu_interp" in name:
+            macs = sum(info["nQ"][l] * info["n_src_boxes"][l] * w3(l) for l in lv)
+        elif "k_nu_bspread" in name:
+            macs = sum(info["nQ"][l] * info["n_tgt_boxes"][l] * w3(l) for l in lv)
+        elif "k_nu_spread" in name:
+            macs = sum(info["src_points"][l] * w3(l) for l in lv)
+        else:
+            macs = sum(info["tgt_points"][l] * w3(l) for l in lv)
+        units = 4.0 * macs
+        peak = SM_COUNT * 128 * 2 * clk_hz
+        out.update({"bound": "alu", "pipe": "FP32 (FMA)", "unit": "TFLOP/s", "units_per_step": units,
+                    "peak_basis": basis % "128 FMA lanes/clk x 2 FLOP"})
     elif "k_lag_gemm" in name:
         variant = 2 if "_ts" in name else 1 if "_tc" in name else 0
         units = sum(2.0 * kfac * (info["r1"][l] ** 3) ** 2 * info["n_adm"][l] for l in range(22)
@@ -394,6 +426,7 @@ def main():
     u = torch.as_tensor(u_host, device=dev)
     # extra plan arguments: the source normals of the double layer
     kw = {"normals": torch.as_tensor(prob.meta["normals"], device=dev)} if "normals" in prob.meta else {}
+    kw["pw_transform"] = {"auto": ffm.PW_AUTO, "direct": ffm.PW_DIRECT, "nufft": ffm.PW_NUFFT}[args.pw_transform]
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
 
@@ -482,7 +515,8 @@ def main():
         Yh = torch.as_tensor(prob.Y).pin_memory()
         wh = torch.as_tensor(prob.w).pin_memory()
         uh = torch.as_tensor(u_host).pin_memory()
-        kwh = {k: torch.as_tensor(prob.meta[k]).pin_memory() for k in kw}
+        kwh = {k: torch.as_tensor(prob.meta[k]).pin_memory() for k in kw if k in prob.meta}
+        kwh["pw_transform"] = kw["pw_transform"]
         vh = torch.empty(tuple(uh.shape[:-1]) + (prob.X.shape[0],), dtype=uh.dtype).pin_memory()
         ke = max(2, args.steps // 2)
         ts = []
@@ -496,7 +530,8 @@ def main():
             if i:
                 ts.append(time.perf_counter() - t0)
         h2d = Xh.numel() * Xh.element_size() + Yh.numel() * Yh.element_size() + wh.numel() * wh.element_size() \
-            + uh.numel() * uh.element_size() + sum(t.numel() * t.element_size() for t in kwh.values())
+            + uh.numel() * uh.element_size() + sum(t.numel() * t.element_size() for t in kwh.values()
+                                                   if hasattr(t, "numel"))
         e2e = {"value": world * len(ts) / sum(ts), "unit": "applies/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": vh.numel() * vh.element_size(), "steps": len(ts),
                "api": "ffm_plan(host X, Y, w) + ffm_apply(host u -> host v) + ffm_destroy"}
@@ -529,7 +564,7 @@ def main():
                        "k": prob.k, "eps": prob.eps,
                        "u_dtype": str(prob.u.dtype), "step": "ffm_plan + ffm_apply + ffm_destroy",
                        "l2": "flushed between steps (512 MiB write, outside the step events)",
-                       "replicas": world, "nrhs": nrhs},
+                       "replicas": world, "nrhs": nrhs, "pw_transform": args.pw_transform},
             "mpoints_per_s": n * value / 1e6, "rhs_per_s": value * nrhs,
             "t_plan_ms": t_plan / args.steps, "t_apply_ms": t_apply / args.steps,
             "apply_only_per_s": args.steps * world / (t_apply * 1e-3),
@@ -540,7 +575,8 @@ def main():
             "kernels": kernels,
             "plan": {"l_stop": info["l_stop"], "mode": info["mode"][:info["l_stop"] + 1],
                      "L": info["L"][:info["l_stop"] + 1], "nQ": info["nQ"][:info["l_stop"] + 1],
-                     "n_adm": info["n_adm"][:info["l_stop"] + 1], "p2p_pairs": info["p2p_pairs"]},
+                     "n_adm": info["n_adm"][:info["l_stop"] + 1], "p2p_pairs": info["p2p_pairs"],
+                     "nufft": info["nufft"][:info["l_stop"] + 1], "nufft_n2": info["nufft_n2"][:info["l_stop"] + 1]},
         }
         if note:
             line["note"] = note

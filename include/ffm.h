@@ -183,6 +183,10 @@ typedef struct {
     int nufft[22];             /* plane-wave levels whose F steps run as type-3 NUFFTs (1) */
     int nufft_w[22];           /* their spreading-kernel width */
     int nufft_n2[22];          /* their FFT grid edge (n2^3 per box) */
+    int64_t n_src_boxes[22];   /* source boxes with admissible pairs (per level) */
+    int64_t n_tgt_boxes[22];   /* target boxes with admissible pairs (per level) */
+    int64_t pw_recurrences[22]; /* plane-wave levels: Legendre recurrences of the transfer table
+                                   (one per translation pair and direction pair, L degrees each) */
 } ffm_info;
 
 ffm_status ffm_plan_info(const ffm_plan_t *plan, ffm_info *info);

@@ -249,7 +249,7 @@ void autotune(ffm_plan_s *p, int nrhs, const char *cache_path, cudaStream_t s) {
             }
             F.tune_tc = pick;
         } else {
-            if (F.prec == FFM_PREC_F64) continue;  // FP64 levels keep the default variants
+            if (F.prec == FFM_PREC_F64 || F.nufft) continue;  // FP64 and NUFFT levels keep their kernels
             std::string key = pw_key(p, l, dev, rhs_bucket(nrhs));
             int a = 0, b = 0, c = 0;
             if (!cache.get(key, v) || !parse_pw(v, a, b, c)) {

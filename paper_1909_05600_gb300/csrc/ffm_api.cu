@@ -473,6 +473,8 @@ ffm_status ffm_plan_info(const ffm_plan_t *plan, ffm_info *info) {
         info->tune_pw[l][0] = act && F.mode == 2 ? F.pw_qpt : 0;
         info->tune_pw[l][1] = act && F.mode == 2 ? F.pw_ppt : 0;
         info->tune_pw[l][2] = act && F.mode == 2 ? F.pw_mc : 0;
+        info->n_src_boxes[l] = F.n_src;
+        info->n_tgt_boxes[l] = F.n_tgt;
     }
     int err = 0;
     if (cudaMemcpy(&err, plan->dev_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) {

@@ -126,8 +126,11 @@ struct NuLevel {
     float *cinv = nullptr;              // n1: FFT-grid kernel deconvolution
     int4 *dirU = nullptr;               // nQ: first window node per axis (centred FFT-grid index)
     float *dirW = nullptr;              // nQ x 3 x w: window kernel values, correction on axis 0
-    int64_t n_tiles = 0;                // FFT-grid tiles reached by some direction
-    uint32_t *tile_id = nullptr, *tile_off = nullptr, *tile_q = nullptr;
+    int64_t n_tiles = 0;                // FFT-grid tiles met by some direction's window: ids,
+    uint32_t *tile_id = nullptr, *tile_off = nullptr, *tile_q = nullptr;  // CSR of directions
+    uint32_t own_max = 0;               // longest of the lists below
+    int64_t n_own = 0;                  // tiles holding some window's first node (each direction
+    uint32_t *own_id = nullptr, *own_off = nullptr, *own_q = nullptr;     // in exactly one)
     int64_t n_ych = 0, n_xch = 0;       // point blocks (bin, first, end, slot) of sources / targets
     int4 *ych = nullptr, *xch = nullptr;
     int fft_src = 0, fft_tgt = 0;       // cuFFT handles (batched over the level's source / target boxes)

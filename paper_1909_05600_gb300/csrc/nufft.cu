@@ -40,6 +40,8 @@ constexpr int NU_TILE = 8;      // FFT-grid tile edge of the backward spread
 constexpr int NU_EMAX = 24;     // largest bin subgrid edge (E^3 float2 in shared memory)
 constexpr int NU_PB = 64;       // points staged per round of the spreading kernel
 constexpr int NU_GL = 32;       // Gauss-Legendre nodes of the kernel's Fourier transform
+constexpr int NU_IB = 8;        // boxes per forward-interpolation block
+constexpr int NU_BB = 64;       // directions staged per batch of the backward spread
 
 std::mutex g_fft_mu;  // a cuFFT handle's stream and work area are set and used under one lock
 
@@ -93,7 +95,9 @@ __device__ __forceinline__ float point_cell(const NuPts &P, const NuGeo &G, int4
            fmaf(ev, G.inv_h, evl * G.inv_h);
 }
 
-// ---- forward: spread one point block into its bin subgrid, add the subgrid to the box grid
+// ---- forward: spread one point block into its bin subgrid, add the subgrid to the box grid.
+// Each thread owns whole (i0, i1) columns of the subgrid and adds the staged points whose
+// window covers its columns: no two threads write one cell, so no shared-memory atomics.
 template <int W>
 __global__ void __launch_bounds__(NU_T) k_nu_spread(NuGeo G, NuPts P, const int4 *__restrict__ ch,
                                                    const float2 *__restrict__ q, int64_t ny, int64_t nslot,
@@ -124,16 +128,21 @@ __global__ void __launch_bounds__(NU_T) k_nu_spread(NuGeo G, NuPts P, const int4
         }
         for (int j = threadIdx.x; j < cnt; j += NU_T) sc[j] = q[(int64_t)m * ny + base + j];
         __syncthreads();
-        for (int it = threadIdx.x; it < cnt * W * W; it += NU_T) {
-            int j = it / (W * W), ab = it % (W * W), a = ab / W, b = ab % W;
-            float wab = sw[j][0][a] * sw[j][1][b];
-            float2 cj = sc[j];
-            float2 *row = sg + ((sf[j][0] + a) * E + (sf[j][1] + b)) * E + sf[j][2];
+        for (int col = threadIdx.x; col < E * E; col += NU_T) {
+            int i0 = col / E, i1 = col - i0 * E;
+            float2 *colp = sg + col * E;
+            for (int j = 0; j < cnt; ++j) {
+                int a = i0 - sf[j][0], b = i1 - sf[j][1];
+                if ((unsigned)a >= (unsigned)W || (unsigned)b >= (unsigned)W) continue;
+                float wab = sw[j][0][a] * sw[j][1][b];
+                float2 cj = sc[j];
+                float2 *row = colp + sf[j][2];
 #pragma unroll
-            for (int cc = 0; cc < W; ++cc) {
-                float wt = wab * sw[j][2][cc];
-                atomicAdd(&row[cc].x, cj.x * wt);
-                atomicAdd(&row[cc].y, cj.y * wt);
+                for (int cc = 0; cc < W; ++cc) {
+                    float wt = wab * sw[j][2][cc];
+                    row[cc].x = fmaf(cj.x, wt, row[cc].x);
+                    row[cc].y = fmaf(cj.y, wt, row[cc].y);
+                }
             }
         }
     }
@@ -150,25 +159,34 @@ __global__ void __launch_bounds__(NU_T) k_nu_spread(NuGeo G, NuPts P, const int4
 }
 
 // ---- forward: deconvolve and zero-pad the n1^3 grids into the n2^3 FFT grids.  FFT index f
-// holds the mode f (f < n2 - c0) or f - n2, i.e. grid node f + c0 or f - n2 + c0.
-__global__ void k_nu_pad(const float2 *__restrict__ grid, const float *__restrict__ cinv, int n1, int c0, int n2,
-                         int64_t nbatch, float2 *__restrict__ fine) {
-    int64_t N2 = (int64_t)n2 * n2 * n2, N1 = (int64_t)n1 * n1 * n1;
-    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= nbatch * N2) return;
-    int64_t b = idx / N2, r = idx % N2;
-    int f0 = (int)(r / ((int64_t)n2 * n2)), f1 = (int)((r / n2) % n2), f2 = (int)(r % n2);
+// holds the mode f (f < n2 - c0) or f - n2, i.e. grid node f + c0 or f - n2 + c0.  One block
+// per (batch, f0); planes without a grid node are written as zeros.
+__global__ void __launch_bounds__(256) k_nu_pad(const float2 *__restrict__ grid, const float *__restrict__ cinv,
+                                                int n1, int c0, int n2, float2 *__restrict__ fine) {
+    int64_t b = blockIdx.x;
+    int f0 = blockIdx.y;
+    int nn = n2 * n2;
+    float2 *out = fine + (b * n2 + f0) * (int64_t)nn;
     int a0 = f0 < n2 - c0 ? f0 + c0 : f0 - n2 + c0;
-    int a1 = f1 < n2 - c0 ? f1 + c0 : f1 - n2 + c0;
-    int a2 = f2 < n2 - c0 ? f2 + c0 : f2 - n2 + c0;
-    float2 v = make_float2(0.f, 0.f);
-    if (a0 < n1 && a1 < n1 && a2 < n1) {
-        v = grid[b * N1 + ((int64_t)a0 * n1 + a1) * n1 + a2];
-        float sc = cinv[a0] * cinv[a1] * cinv[a2];
-        v.x *= sc;
-        v.y *= sc;
+    if (a0 >= n1) {
+        for (int i = threadIdx.x; i < nn; i += blockDim.x) out[i] = make_float2(0.f, 0.f);
+        return;
     }
-    fine[idx] = v;
+    const float2 *in = grid + (b * n1 + a0) * (int64_t)n1 * n1;
+    float s0 = cinv[a0];
+    for (int i = threadIdx.x; i < nn; i += blockDim.x) {
+        int f1 = i / n2, f2 = i - f1 * n2;
+        int a1 = f1 < n2 - c0 ? f1 + c0 : f1 - n2 + c0;
+        int a2 = f2 < n2 - c0 ? f2 + c0 : f2 - n2 + c0;
+        float2 v = make_float2(0.f, 0.f);
+        if (a1 < n1 && a2 < n1) {
+            v = in[a1 * n1 + a2];
+            float sc = s0 * cinv[a1] * cinv[a2];
+            v.x *= sc;
+            v.y *= sc;
+        }
+        out[i] = v;
+    }
 }
 
 // FFT-grid index of centred node u (u - H in (-n2/2, n2/2))
@@ -177,94 +195,151 @@ __device__ __forceinline__ int fft_index(int u, int H, int n2) {
     return f < 0 ? f + n2 : f;
 }
 
-// ---- forward: interpolate every box's transformed grid at the directions
+// ---- forward: interpolate the transformed grids at the directions.  A block stages one
+// FFT-grid tile with its halo (the windows of the directions that start in the tile) for
+// each box of its group in turn; each thread keeps its direction's window in registers
+// across the boxes.
 template <int W>
 __global__ void __launch_bounds__(128) k_nu_interp(NuGeo G, const float2 *__restrict__ fine,
+                                                   const uint32_t *__restrict__ own_id,
+                                                   const uint32_t *__restrict__ own_off,
+                                                   const uint32_t *__restrict__ own_q,
                                                    const int4 *__restrict__ dirU, const float *__restrict__ dirW,
                                                    int nQ, const uint32_t *__restrict__ slot_box, int64_t nslot,
                                                    int nrhs, float2 *__restrict__ ut) {
-    int q = blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= nQ) return;
-    int slot = blockIdx.y, m = blockIdx.z;
-    const int n2 = G.n2;
-    int4 U = dirU[q];
-    const float *wq = dirW + (size_t)q * 3 * W;
-    float w1[W], w2[W];
-    int i2[W];
+    constexpr int X = NU_TILE + W - 1, X3 = X * X * X;
+    extern __shared__ float2 sx[];  // X^3
+    const int n2 = G.n2, nt = (n2 + NU_TILE - 1) / NU_TILE;
+    uint32_t id = own_id[blockIdx.x];
+    int u0 = (int)(id / (nt * nt)) * NU_TILE, v0 = (int)((id / nt) % nt) * NU_TILE, w0 = (int)(id % nt) * NU_TILE;
+    int m = blockIdx.z;
+    uint32_t e0 = own_off[blockIdx.x], e1 = own_off[blockIdx.x + 1];
+    for (uint32_t eb = e0; eb < e1; eb += blockDim.x) {
+        uint32_t e = eb + threadIdx.x;
+        bool on = e < e1;
+        int q = on ? (int)own_q[e] : 0;
+        int4 U = dirU[q];
+        const float *wq = dirW + (size_t)q * 3 * W;
+        float w0v[W], w1v[W], w2v[W];
 #pragma unroll
-    for (int a = 0; a < W; ++a) {
-        w1[a] = wq[W + a];
-        w2[a] = wq[2 * W + a];
-        i2[a] = fft_index(U.z + a, G.H, n2);
-    }
-    const float2 *F = fine + ((int64_t)m * nslot + slot) * (int64_t)n2 * n2 * n2;
-    float ax = 0.f, ay = 0.f;
-    for (int a = 0; a < W; ++a) {
-        int i0 = fft_index(U.x + a, G.H, n2);
-        float bx = 0.f, by = 0.f;
-#pragma unroll
-        for (int b = 0; b < W; ++b) {
-            const float2 *row = F + ((int64_t)i0 * n2 + fft_index(U.y + b, G.H, n2)) * n2;
-            float cx = 0.f, cy = 0.f;
-#pragma unroll
-            for (int c = 0; c < W; ++c) {
-                float2 g = row[i2[c]];
-                cx = fmaf(g.x, w2[c], cx);
-                cy = fmaf(g.y, w2[c], cy);
-            }
-            bx = fmaf(cx, w1[b], bx);
-            by = fmaf(cy, w1[b], by);
+        for (int a = 0; a < W; ++a) {
+            w0v[a] = wq[a];
+            w1v[a] = wq[W + a];
+            w2v[a] = wq[2 * W + a];
         }
-        float w0 = wq[a];
-        ax = fmaf(bx, w0, ax);
-        ay = fmaf(by, w0, ay);
+        int ox = U.x - u0, oy = U.y - v0, oz = U.z - w0;  // in [0, NU_TILE) for an owned direction
+        for (int bi = 0; bi < NU_IB; ++bi) {
+            int64_t slot = (int64_t)blockIdx.y * NU_IB + bi;
+            if (slot >= nslot) break;
+            const float2 *F = fine + ((int64_t)m * nslot + slot) * (int64_t)n2 * n2 * n2;
+            __syncthreads();
+            for (int i = threadIdx.x; i < X3; i += blockDim.x) {
+                int a = i / (X * X), b = (i / X) % X, cc = i % X;
+                int u = u0 + a, v = v0 + b, w = w0 + cc;
+                float2 g = make_float2(0.f, 0.f);
+                if (u < n2 && v < n2 && w < n2)
+                    g = F[((int64_t)fft_index(u, G.H, n2) * n2 + fft_index(v, G.H, n2)) * n2 + fft_index(w, G.H, n2)];
+                sx[i] = g;
+            }
+            __syncthreads();
+            if (!on) continue;
+            float ax = 0.f, ay = 0.f;
+#pragma unroll
+            for (int a = 0; a < W; ++a) {
+                float bx = 0.f, by = 0.f;
+#pragma unroll
+                for (int b = 0; b < W; ++b) {
+                    const float2 *row = sx + ((ox + a) * X + (oy + b)) * X + oz;
+                    float cx = 0.f, cy = 0.f;
+#pragma unroll
+                    for (int c = 0; c < W; ++c) {
+                        float2 g = row[c];
+                        cx = fmaf(g.x, w2v[c], cx);
+                        cy = fmaf(g.y, w2v[c], cy);
+                    }
+                    bx = fmaf(cx, w1v[b], bx);
+                    by = fmaf(cy, w1v[b], by);
+                }
+                ax = fmaf(bx, w0v[a], ax);
+                ay = fmaf(by, w0v[a], ay);
+            }
+            ut[((int64_t)slot_box[slot] * nrhs + m) * nQ + q] = make_float2(ax, ay);
+        }
     }
-    ut[((int64_t)slot_box[slot] * nrhs + m) * nQ + q] = make_float2(ax, ay);
 }
 
-// ---- backward: spread the corrected v~ of one box onto one FFT-grid tile
+// ---- backward: spread the corrected v~ onto one FFT-grid tile.  A warp owns one tile
+// column (NU_TILE cells along z, in registers) for 32 boxes, one box per lane, so the test
+// whether a direction's window covers the column is the same for the whole warp; the
+// tile's directions (those whose window meets the tile) are staged in shared memory in
+// batches, with the 32 boxes' v~ side by side.  Each tile of each box is written once, no
+// atomics.  Block: 16 warps = 16 of the tile's 64 columns.
 template <int W>
-__global__ void __launch_bounds__(NU_T) k_nu_bspread(NuGeo G, const uint32_t *__restrict__ tile_id,
+__global__ void __launch_bounds__(512) k_nu_bspread(NuGeo G, const uint32_t *__restrict__ tile_id,
                                                     const uint32_t *__restrict__ tile_off,
                                                     const uint32_t *__restrict__ tile_q,
                                                     const int4 *__restrict__ dirU, const float *__restrict__ dirW,
                                                     int nQ, const uint32_t *__restrict__ slot_box, int64_t nslot,
                                                     int nrhs, const float2 *__restrict__ vt,
                                                     float2 *__restrict__ fine) {
-    constexpr int T = NU_TILE, T3 = T * T * T;
-    __shared__ float2 st[T3];
+    constexpr int T = NU_TILE;
+    __shared__ int4 sU[NU_BB];
+    __shared__ float sW[NU_BB][3 * W];
+    __shared__ float2 sz[NU_BB][32];
     const int n2 = G.n2, nt = (n2 + T - 1) / T;
-    int slot = blockIdx.y, m = blockIdx.z;
+    int m = blockIdx.z >> 2, cq = blockIdx.z & 3;
     uint32_t id = tile_id[blockIdx.x];
     int u0 = (int)(id / (nt * nt)) * T, v0 = (int)((id / nt) % nt) * T, w0 = (int)(id % nt) * T;
-    for (int i = threadIdx.x; i < T3; i += NU_T) st[i] = make_float2(0.f, 0.f);
-    __syncthreads();
-    const float2 *V = vt + ((int64_t)slot_box[slot] * nrhs + m) * nQ;
     int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (uint32_t e = tile_off[blockIdx.x] + warp; e < tile_off[blockIdx.x + 1]; e += NU_T / 32) {
-        int q = (int)tile_q[e];
-        int4 U = dirU[q];
-        int alo = max(0, u0 - U.x), ahi = min(W, u0 + T - U.x);
-        int blo = max(0, v0 - U.y), bhi = min(W, v0 + T - U.y);
-        int clo = max(0, w0 - U.z), chi = min(W, w0 + T - U.z);
-        int na = ahi - alo, nb = bhi - blo, nc = chi - clo;
-        if (na <= 0 || nb <= 0 || nc <= 0) continue;
-        float2 z = V[q];
-        const float *wq = dirW + (size_t)q * 3 * W;
-        for (int k = lane; k < na * nb * nc; k += 32) {
-            int a = alo + k / (nb * nc), b = blo + (k / nc) % nb, c = clo + k % nc;
-            float wt = wq[a] * wq[W + b] * wq[2 * W + c];
-            float2 *cell = st + ((U.x + a - u0) * T + (U.y + b - v0)) * T + (U.z + c - w0);
-            atomicAdd(&cell->x, z.x * wt);
-            atomicAdd(&cell->y, z.y * wt);
+    int col = cq * 16 + warp;
+    int i0 = col >> 3, i1 = col & 7;
+    int64_t slot = (int64_t)blockIdx.y * 32 + lane;
+    float ax[T], ay[T];
+#pragma unroll
+    for (int cc = 0; cc < T; ++cc) ax[cc] = ay[cc] = 0.f;
+    uint32_t e0 = tile_off[blockIdx.x], e1 = tile_off[blockIdx.x + 1];
+    for (uint32_t eb = e0; eb < e1; eb += NU_BB) {
+        int cnt = (int)min((uint32_t)NU_BB, e1 - eb);
+        __syncthreads();
+        for (int t = threadIdx.x; t < cnt * 3 * W; t += blockDim.x) {
+            int j = t / (3 * W), k = t - j * (3 * W);
+            sW[j][k] = dirW[(size_t)tile_q[eb + j] * 3 * W + k];
+        }
+        for (int t = threadIdx.x; t < cnt; t += blockDim.x) sU[t] = dirU[tile_q[eb + t]];
+        for (int t = threadIdx.x; t < cnt * 32; t += blockDim.x) {
+            int j = t >> 5, b = t & 31;
+            int64_t sl = (int64_t)blockIdx.y * 32 + b;
+            sz[j][b] = sl < nslot ? vt[((int64_t)slot_box[sl] * nrhs + m) * nQ + tile_q[eb + j]] : make_float2(0.f, 0.f);
+        }
+        __syncthreads();
+        for (int j = 0; j < cnt; ++j) {
+            int4 U = sU[j];
+            int a = u0 + i0 - U.x, b = v0 + i1 - U.y;
+            if ((unsigned)a >= (unsigned)W || (unsigned)b >= (unsigned)W) continue;  // uniform in the warp
+            float wab = sW[j][a] * sW[j][W + b];
+            float2 z = sz[j][lane];
+            float zx = z.x * wab, zy = z.y * wab;
+            int kb = w0 - U.z;
+#pragma unroll
+            for (int cc = 0; cc < T; ++cc) {
+                int k = kb + cc;
+                if ((unsigned)k < (unsigned)W) {
+                    float wz = sW[j][2 * W + k];
+                    ax[cc] = fmaf(zx, wz, ax[cc]);
+                    ay[cc] = fmaf(zy, wz, ay[cc]);
+                }
+            }
         }
     }
-    __syncthreads();
-    float2 *F = fine + ((int64_t)m * nslot + slot) * (int64_t)n2 * n2 * n2;
-    for (int i = threadIdx.x; i < T3; i += NU_T) {
-        int u = u0 + i / (T * T), v = v0 + (i / T) % T, w = w0 + i % T;
-        if (u >= n2 || v >= n2 || w >= n2) continue;
-        F[((int64_t)fft_index(u, G.H, n2) * n2 + fft_index(v, G.H, n2)) * n2 + fft_index(w, G.H, n2)] = st[i];
+    if (slot >= nslot) return;
+    int u = u0 + i0, v = v0 + i1;
+    if (u >= n2 || v >= n2) return;
+    float2 *F = fine + ((int64_t)m * nslot + slot) * (int64_t)n2 * n2 * n2 +
+                ((int64_t)fft_index(u, G.H, n2) * n2 + fft_index(v, G.H, n2)) * n2;
+#pragma unroll
+    for (int cc = 0; cc < T; ++cc) {
+        int w = w0 + cc;
+        if (w < n2) F[fft_index(w, G.H, n2)] = make_float2(ax[cc], ay[cc]);
     }
 }
 
@@ -309,6 +384,7 @@ __global__ void __launch_bounds__(NU_T) k_nu_binterp(NuGeo G, NuPts P, const int
             for (int a = 0; a < W; ++a) w[d][a] = es_w(((float)(f[d] + a) - r) * (2.f / W), G.beta);
         }
         float sx = 0.f, sy = 0.f;
+#pragma unroll
         for (int a = 0; a < W; ++a) {
             float bx = 0.f, by = 0.f;
 #pragma unroll
@@ -367,16 +443,20 @@ __global__ void k_nu_dirs(NuGeo G, GlTab gl, float a1, const float4 *__restrict_
     dirU[q] = make_int4(U[0], U[1], U[2], 0);
 }
 
-__global__ void k_nu_tile_count(const int4 *__restrict__ dirU, int nQ, int W, int nt, uint32_t *__restrict__ cnt,
-                                uint32_t *__restrict__ pos, int emit, uint32_t *__restrict__ tile_q) {
+// Per-tile direction lists: with own = 0 every tile a direction's window meets (backward
+// spread), with own = 1 only the tile holding the window's first node (forward
+// interpolation).  Counted first (pos == nullptr), then emitted at the cursors pos.
+__global__ void k_nu_tile_count(const int4 *__restrict__ dirU, int nQ, int W, int nt, int own,
+                                uint32_t *__restrict__ cnt, uint32_t *__restrict__ pos, uint32_t *__restrict__ tile_q) {
     int q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= nQ) return;
     int4 U = dirU[q];
-    for (int a = U.x / NU_TILE; a <= (U.x + W - 1) / NU_TILE; ++a)
-        for (int b = U.y / NU_TILE; b <= (U.y + W - 1) / NU_TILE; ++b)
-            for (int c = U.z / NU_TILE; c <= (U.z + W - 1) / NU_TILE; ++c) {
+    int ext = own ? 0 : W - 1;
+    for (int a = U.x / NU_TILE; a <= (U.x + ext) / NU_TILE; ++a)
+        for (int b = U.y / NU_TILE; b <= (U.y + ext) / NU_TILE; ++b)
+            for (int c = U.z / NU_TILE; c <= (U.z + ext) / NU_TILE; ++c) {
                 uint32_t t = ((uint32_t)a * nt + b) * nt + c;
-                if (emit)
+                if (pos)
                     tile_q[atomicAdd(&pos[t], 1u)] = (uint32_t)q;
                 else
                     atomicAdd(&cnt[t], 1u);
@@ -469,6 +549,45 @@ int4 *build_point_blocks(ffm_plan_s *p, const BoxLevel &bins, const BoxLevel &bo
     return out;
 }
 
+void tile_lists(ffm_plan_s *p, int l, int own, int64_t *n_tiles, uint32_t **ids_out, uint32_t **off_out,
+                uint32_t **q_out, uint32_t *max_len, Alloc &tmp, cudaStream_t s) {
+    FarLevel &F = p->far[l];
+    NuLevel &N = F.nu;
+    int nt = (N.n2 + NU_TILE - 1) / NU_TILE;
+    int64_t ntt = (int64_t)nt * nt * nt;
+    uint32_t *cnt = tmp.get<uint32_t>(ntt);
+    FFM_CUDA(cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * ntt, s));
+    FFM_LAUNCH(k_nu_tile_count, cdiv(F.nQ, 128), 128, 0, s, (const int4 *)N.dirU, F.nQ, N.w, nt, own, cnt,
+               (uint32_t *)nullptr, (uint32_t *)nullptr);
+    std::vector<uint32_t> hc(ntt);
+    FFM_CUDA(cudaMemcpyAsync(hc.data(), cnt, sizeof(uint32_t) * ntt, cudaMemcpyDeviceToHost, s));
+    FFM_CUDA(cudaStreamSynchronize(s));
+    std::vector<uint32_t> pos(ntt), ids, off;
+    uint32_t run = 0;
+    *max_len = 0;
+    for (int64_t t = 0; t < ntt; ++t) {
+        pos[t] = run;
+        *max_len = std::max(*max_len, hc[t]);
+        if (hc[t]) {
+            ids.push_back((uint32_t)t);
+            off.push_back(run);
+        }
+        run += hc[t];
+    }
+    off.push_back(run);
+    *n_tiles = (int64_t)ids.size();
+    *ids_out = p->mem.get<uint32_t>(ids.size());
+    *off_out = p->mem.get<uint32_t>(off.size());
+    *q_out = p->mem.get<uint32_t>(run);
+    uint32_t *dpos = tmp.get<uint32_t>(ntt);
+    FFM_CUDA(cudaMemcpyAsync(*ids_out, ids.data(), sizeof(uint32_t) * ids.size(), cudaMemcpyHostToDevice, s));
+    FFM_CUDA(cudaMemcpyAsync(*off_out, off.data(), sizeof(uint32_t) * off.size(), cudaMemcpyHostToDevice, s));
+    FFM_CUDA(cudaMemcpyAsync(dpos, pos.data(), sizeof(uint32_t) * ntt, cudaMemcpyHostToDevice, s));
+    FFM_LAUNCH(k_nu_tile_count, cdiv(F.nQ, 128), 128, 0, s, (const int4 *)N.dirU, F.nQ, N.w, nt, own, cnt, dpos,
+               *q_out);
+    FFM_CUDA(cudaStreamSynchronize(s));  // the host vectors feed the copies above
+}
+
 cufftHandle make_fft(int n2, int64_t batch, size_t *work) {
     cufftHandle h;
     check_fft(cufftCreate(&h), "cufftCreate");
@@ -487,10 +606,14 @@ void exec_fft(cufftHandle h, size_t work, float2 *data, int64_t per_rhs, int nrh
     std::lock_guard<std::mutex> lk(g_fft_mu);
     check_fft(cufftSetStream(h, s), "cufftSetStream");
     check_fft(cufftSetWorkArea(h, wa), "cufftSetWorkArea");
+    // the library's kernels are timed as one entry by the profile hooks (not counted as ours)
+    bool prof = g_profile && !g_capture_count;
+    if (prof) profile_begin("cufftExecC2C (library)", s);
     for (int m = 0; m < nrhs; ++m) {
         cufftComplex *d = reinterpret_cast<cufftComplex *>(data + (int64_t)m * per_rhs);
         check_fft(cufftExecC2C(h, d, d, dir), "cufftExecC2C");
     }
+    if (prof) profile_end(s);
 }
 
 NuGeo geo_of(const NuLevel &N) {
@@ -541,12 +664,15 @@ void launch_forward(const ffm_plan_s *p, int l, const float2 *q, int nrhs, float
     FFM_CUDA(cudaFuncSetAttribute(k_nu_spread<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     FFM_LAUNCH(k_nu_spread<W>, dim3((unsigned)N.n_ych, nrhs), NU_T, smem, s, G, P, N.ych, q, p->ny, ns, grid);
     float2 *fine = tmp.get<float2>(ns * nrhs * N2);
-    FFM_LAUNCH(k_nu_pad, cdiv(ns * nrhs * N2, 256), 256, 0, s, (const float2 *)grid, N.cinv, N.n1, N.n1 / 2, N.n2,
-               ns * nrhs, fine);
+    FFM_LAUNCH(k_nu_pad, dim3((unsigned)(ns * nrhs), N.n2), 256, 0, s, (const float2 *)grid, N.cinv, N.n1,
+               N.n1 / 2, N.n2, fine);
     tmp.drop(grid);
     exec_fft(N.fft_src, N.work_src, fine, ns * N2, nrhs, CUFFT_FORWARD, tmp, s);
-    FFM_LAUNCH(k_nu_interp<W>, dim3(cdiv(F.nQ, 128), (unsigned)ns, nrhs), 128, 0, s, G, (const float2 *)fine, N.dirU,
-               N.dirW, F.nQ, F.src, ns, nrhs, ut);
+    constexpr int X = NU_TILE + W - 1;
+    size_t xs = sizeof(float2) * X * X * X;
+    FFM_CUDA(cudaFuncSetAttribute(k_nu_interp<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xs));
+    FFM_LAUNCH(k_nu_interp<W>, dim3((unsigned)N.n_own, cdiv(ns, NU_IB), nrhs), 128, xs, s, G, (const float2 *)fine,
+               N.own_id, N.own_off, N.own_q, N.dirU, N.dirW, F.nQ, F.src, ns, nrhs, ut);
     tmp.drop(fine);
 }
 
@@ -561,7 +687,7 @@ void launch_backward(const ffm_plan_s *p, int l, const float2 *vt, int nrhs, dou
     int64_t N2 = (int64_t)N.n2 * N.n2 * N.n2;
     float2 *fine = tmp.get<float2>(nt * nrhs * N2);
     FFM_CUDA(cudaMemsetAsync(fine, 0, sizeof(float2) * nt * nrhs * N2, s));
-    FFM_LAUNCH(k_nu_bspread<W>, dim3((unsigned)N.n_tiles, (unsigned)nt, nrhs), NU_T, 0, s, G, N.tile_id, N.tile_off,
+    FFM_LAUNCH(k_nu_bspread<W>, dim3((unsigned)N.n_tiles, cdiv(nt, 32), 4 * nrhs), 512, 0, s, G, N.tile_id, N.tile_off,
                N.tile_q, N.dirU, N.dirW, F.nQ, F.tgt, nt, nrhs, vt, fine);
     exec_fft(N.fft_tgt, N.work_tgt, fine, nt * N2, nrhs, CUFFT_INVERSE, tmp, s);
     size_t smem = sizeof(float2) * N.E * N.E * N.E;
@@ -638,37 +764,11 @@ void build_nufft(ffm_plan_s *p, int l, Alloc &tmp, cudaStream_t s) {
     N.dirW = p->mem.get<float>((size_t)F.nQ * 3 * N.w);
     float a1 = (float)(0.5 * N.w * N.h);
     NU_DISPATCH(N.w, launch_dirs, p, l, gl, a1, s);
-    // per-tile direction lists of the backward spread
-    int nt = (N.n2 + NU_TILE - 1) / NU_TILE;
-    int64_t ntt = (int64_t)nt * nt * nt;
-    uint32_t *cnt = tmp.get<uint32_t>(ntt);
-    FFM_CUDA(cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * ntt, s));
-    FFM_LAUNCH(k_nu_tile_count, cdiv(F.nQ, 128), 128, 0, s, (const int4 *)N.dirU, F.nQ, N.w, nt, cnt,
-               (uint32_t *)nullptr, 0, (uint32_t *)nullptr);
-    std::vector<uint32_t> hc(ntt);
-    FFM_CUDA(cudaMemcpyAsync(hc.data(), cnt, sizeof(uint32_t) * ntt, cudaMemcpyDeviceToHost, s));
-    FFM_CUDA(cudaStreamSynchronize(s));
-    std::vector<uint32_t> pos(ntt), ids, off;
-    uint32_t run = 0;
-    for (int64_t t = 0; t < ntt; ++t) {
-        pos[t] = run;
-        if (hc[t]) {
-            ids.push_back((uint32_t)t);
-            off.push_back(run);
-        }
-        run += hc[t];
-    }
-    off.push_back(run);
-    N.n_tiles = (int64_t)ids.size();
-    N.tile_id = p->mem.get<uint32_t>(ids.size());
-    N.tile_off = p->mem.get<uint32_t>(off.size());
-    N.tile_q = p->mem.get<uint32_t>(run);
-    uint32_t *dpos = tmp.get<uint32_t>(ntt);
-    FFM_CUDA(cudaMemcpyAsync(N.tile_id, ids.data(), sizeof(uint32_t) * ids.size(), cudaMemcpyHostToDevice, s));
-    FFM_CUDA(cudaMemcpyAsync(N.tile_off, off.data(), sizeof(uint32_t) * off.size(), cudaMemcpyHostToDevice, s));
-    FFM_CUDA(cudaMemcpyAsync(dpos, pos.data(), sizeof(uint32_t) * ntt, cudaMemcpyHostToDevice, s));
-    FFM_LAUNCH(k_nu_tile_count, cdiv(F.nQ, 128), 128, 0, s, (const int4 *)N.dirU, F.nQ, N.w, nt, cnt, dpos, 1,
-               N.tile_q);
+    // per-tile direction lists: every tile a window meets (backward spread), and the tile
+    // holding each window's first node (forward interpolation)
+    uint32_t tmax = 0;
+    tile_lists(p, l, 0, &N.n_tiles, &N.tile_id, &N.tile_off, &N.tile_q, &tmax, tmp, s);
+    tile_lists(p, l, 1, &N.n_own, &N.own_id, &N.own_off, &N.own_q, &N.own_max, tmp, s);
     // point blocks of the source and target bins
     int lb = l + N.dlt;
     N.ych = build_point_blocks(p, p->by[lb], p->by[l], F.src, F.n_src, &N.n_ych, tmp, s);

@@ -447,6 +447,7 @@ void build_tables(ffm_plan_s *p, int l, TableJob &tj) {
     }
     int npairs = (int)pairs.size();
     dim3 g1(cdiv(nH, 256), npairs);
+    p->info.pw_recurrences[l] = (int64_t)npairs * nH;
     size_t sm1 = sizeof(float4) * (L + 1) + sizeof(float2) * L;
     if (dbl) {
         F.ksd = p->mem.get<D4>(nQ);

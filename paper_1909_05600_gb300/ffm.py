@@ -61,7 +61,8 @@ class Info(C.Structure):
                 ("cancel", C.c_double * 22), ("device_errors", C.c_int), ("autotuned", C.c_int),
                 ("p2p_tchunk", C.c_int), ("p2p_smax", C.c_int), ("tune_tc", C.c_int * 22),
                 ("tune_pw", (C.c_int * 3) * 22), ("nufft", C.c_int * 22), ("nufft_w", C.c_int * 22),
-                ("nufft_n2", C.c_int * 22)]
+                ("nufft_n2", C.c_int * 22), ("n_src_boxes", C.c_int64 * 22), ("n_tgt_boxes", C.c_int64 * 22),
+                ("pw_recurrences", C.c_int64 * 22)]
 
     def as_dict(self):
         d = {"l_stop": self.l_stop, "root_admissible": self.root_admissible, "d0": self.d0, "oX": list(self.oX),
@@ -69,7 +70,8 @@ class Info(C.Structure):
              "device_errors": self.device_errors, "autotuned": self.autotuned, "p2p_tchunk": self.p2p_tchunk,
              "p2p_smax": self.p2p_smax, "tune_pw": [list(r) for r in self.tune_pw]}
         for f in ("nboxX", "nboxY", "n_adm", "n_near", "n_trans", "mode", "r1", "L", "nQ", "src_points",
-                  "tgt_points", "pw_prec", "cancel", "tune_tc", "nufft", "nufft_w", "nufft_n2"):
+                  "tgt_points", "pw_prec", "cancel", "tune_tc", "nufft", "nufft_w", "nufft_n2",
+                  "n_src_boxes", "n_tgt_boxes", "pw_recurrences"):
             d[f] = list(getattr(self, f))
         return d
 
