@@ -390,30 +390,54 @@ __device__ __forceinline__ void tf32_split(float x, float &hi, float &lo) {
     lo = x - hi;
 }
 
-template <int KT>
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+
+// Bounded wait for the completion of phase `parity` of an mbarrier; false if it gave up.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t done = 0;
+    for (int it = 0; it < (1 << 24) && !done; ++it)
+        asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+                     : "=r"(done)
+                     : "r"(smem_addr(bar)), "r"(parity));
+    return done != 0;
+}
+
+// The K loop runs over chunks of KT source nodes through an NS-stage shared-memory ring, with
+// the warps specialised: warps 1-7 copy the chunks (cp.async, 16-byte segments; operands are
+// pre-split into TF32 hi and lo parts and padded to rows of rkp floats, T_t to npad rows),
+// and one thread of warp 0 issues the MMAs.  Stage s has two mbarriers: full[s] completes
+// when every copying thread's segments of the chunk have landed (each thread waits for its
+// own copies, fences them for the tensor cores and arrives), empty[s] when the MMAs that
+// read the stage have completed (tcgen05.commit).  No block-wide barrier runs in the loop,
+// so up to NS chunks are queued ahead of the tensor cores.
+template <int KT, int NS>
 __global__ void __launch_bounds__(256) k_lag_gemm_tc(const uint32_t *__restrict__ tile_t,
                                                      const uint32_t *__restrict__ tile_p0,
                                                      const uint32_t *__restrict__ bt_off,
                                                      const uint32_t *__restrict__ bt_src,
-                                                     const uint32_t *__restrict__ bt_tgt, const float *__restrict__ T,
-                                                     int r, int rk, int npad, int tcols, int nrhs,
-                                                     const float *__restrict__ ut, float *__restrict__ vt,
-                                                     int *__restrict__ err) {
-    // rk: K extent (rk = r, or 3 r for the double layer's stacked component kernels)
+                                                     const uint32_t *__restrict__ bt_tgt,
+                                                     const float *__restrict__ Th, const float *__restrict__ Tl,
+                                                     int r, int rkp, int npad, int tcols, int nrhs,
+                                                     const float *__restrict__ uh, const float *__restrict__ ul,
+                                                     float *__restrict__ vt, int *__restrict__ err) {
+    constexpr int C4 = KT / 4;       // 16-byte segments per operand row and chunk
+    constexpr int NP = 224;          // copying threads (warps 1-7)
+    constexpr int LAG = NS - 2;      // chunks a copying thread keeps in flight before arriving
     extern __shared__ __align__(1024) unsigned char smem[];
-    float *sAh = reinterpret_cast<float *>(smem);
-    float *sAl = sAh + TC_M * KT;
-    float *sBh = sAl + TC_M * KT;
-    float *sBl = sBh + npad * KT;
+    const int stage_f = 2 * TC_M * KT + 2 * npad * KT;  // floats per stage
+    float *st0 = reinterpret_cast<float *>(smem);
     __shared__ uint32_t s_tmem;
-    __shared__ __align__(8) uint64_t s_mbar;
+    __shared__ __align__(8) uint64_t s_full[NS], s_empty[NS];
     __shared__ uint32_t s_src[TC_M], s_tgt[TC_M];
     int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     int t = tile_t[blockIdx.x], m = blockIdx.y;
     uint32_t p0 = tile_p0[blockIdx.x];
     int np = (int)min((uint32_t)TC_M, bt_off[t + 1] - p0);
     if (tid < TC_M) {
-        s_src[tid] = tid < np ? bt_src[p0 + tid] : 0u;
+        // rows past the tile's pairs repeat its first pair; their TMEM lanes are not read
+        s_src[tid] = bt_src[p0 + (tid < np ? tid : 0)];
         s_tgt[tid] = tid < np ? bt_tgt[p0 + tid] : 0u;
     }
     if (warp == 0) {
@@ -422,81 +446,73 @@ __global__ void __launch_bounds__(256) k_lag_gemm_tc(const uint32_t *__restrict_
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&s_mbar)));
+        for (int i = 0; i < NS; ++i) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(&s_full[i])), "r"(NP));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&s_empty[i])));
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     uint32_t tmem = s_tmem;
-    const float *Tt = T + (size_t)t * r * rk;
-    const bool r4 = (rk & 3) == 0;  // rows of u~ and T start on 16-byte boundaries
+    const size_t toff = (size_t)t * npad * rkp;
     const uint32_t lbo = 128, sbo = (KT / 4) * 128;
     const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(npad >> 3) << 17) | ((uint32_t)(TC_M >> 4) << 24);
+    const int nk = rkp / KT;
+    const int nseg = (TC_M + npad) * C4;  // segments per operand part (hi or lo) and chunk
     bool ok = true;
-    int phase = 0;
-    for (int k0 = 0; k0 < rk; k0 += KT) {
-        // A: row p = pair, K = source node j (gathered u~ column of the pair's source box).
-        // Each thread moves 4 consecutive K elements = one 16-byte row of a core matrix.
-        constexpr int C4 = KT / 4;
-        for (int e = tid; e < TC_M * C4; e += blockDim.x) {
-            int p = e / C4, c = e % C4;
-            int j = k0 + 4 * c;
-            const float *src = ut + ((size_t)s_src[p] * nrhs + m) * rk + j;
-            float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (p < np) {
-                if (r4 && j + 4 <= rk) {
-                    x = *reinterpret_cast<const float4 *>(src);
+    if (warp >= 1) {
+        // ---- copying warps
+        const int pt = tid - 32;
+        auto arrive_full = [&](int kc) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(&s_full[kc % NS])) : "memory");
+        };
+        for (int kn = 0; kn < nk; ++kn) {
+            const int b = kn % NS;
+            if (kn >= NS) ok = mbar_wait(&s_empty[b], (uint32_t)((kn / NS - 1) & 1)) && ok;  // MMAs of kn - NS done
+            float *sAh = st0 + (size_t)b * stage_f, *sAl = sAh + TC_M * KT, *sBh = sAl + TC_M * KT,
+                  *sBl = sBh + npad * KT;
+            const int k0 = kn * KT;
+            for (int e = pt; e < nseg; e += NP) {
+                int row = e / C4, c = e - row * C4;
+                if (row < TC_M) {
+                    size_t g = ((size_t)s_src[row] * nrhs + m) * rkp + k0 + 4 * c;
+                    uint32_t o = kmajor_off(row, 4 * c, KT) >> 2;
+                    cp_async16(sAh + o, uh + g);
+                    cp_async16(sAl + o, ul + g);
                 } else {
-                    x.x = j < rk ? src[0] : 0.f;
-                    x.y = j + 1 < rk ? src[1] : 0.f;
-                    x.z = j + 2 < rk ? src[2] : 0.f;
-                    x.w = j + 3 < rk ? src[3] : 0.f;
+                    int i = row - TC_M;
+                    size_t g = toff + (size_t)i * rkp + k0 + 4 * c;
+                    uint32_t o = kmajor_off(i, 4 * c, KT) >> 2;
+                    cp_async16(sBh + o, Th + g);
+                    cp_async16(sBl + o, Tl + g);
                 }
             }
-            float4 h, l;
-            tf32_split(x.x, h.x, l.x);
-            tf32_split(x.y, h.y, l.y);
-            tf32_split(x.z, h.z, l.z);
-            tf32_split(x.w, h.w, l.w);
-            uint32_t o = kmajor_off(p, 4 * c, KT) >> 2;
-            *reinterpret_cast<float4 *>(sAh + o) = h;
-            *reinterpret_cast<float4 *>(sAl + o) = l;
-        }
-        // B: row n = target node i, K = source node j (rows of T_t)
-        for (int e = tid; e < npad * C4; e += blockDim.x) {
-            int i = e / C4, c = e % C4;
-            int j = k0 + 4 * c;
-            const float *src = Tt + (size_t)i * rk + j;
-            float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (i < r) {
-                if (r4 && j + 4 <= rk) {
-                    x = *reinterpret_cast<const float4 *>(src);
-                } else {
-                    x.x = j < rk ? src[0] : 0.f;
-                    x.y = j + 1 < rk ? src[1] : 0.f;
-                    x.z = j + 2 < rk ? src[2] : 0.f;
-                    x.w = j + 3 < rk ? src[3] : 0.f;
-                }
+            asm volatile("cp.async.commit_group;" ::: "memory");
+            if (kn >= LAG) {
+                asm volatile("cp.async.wait_group %0;" ::"n"(LAG) : "memory");  // chunk kn - LAG landed
+                arrive_full(kn - LAG);
             }
-            float4 h, l;
-            tf32_split(x.x, h.x, l.x);
-            tf32_split(x.y, h.y, l.y);
-            tf32_split(x.z, h.z, l.z);
-            tf32_split(x.w, h.w, l.w);
-            uint32_t o = kmajor_off(i, 4 * c, KT) >> 2;
-            *reinterpret_cast<float4 *>(sBh + o) = h;
-            *reinterpret_cast<float4 *>(sBl + o) = l;
         }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
-        if (tid == 0) {
+        asm volatile("cp.async.wait_all;" ::: "memory");
+        for (int kc = max(0, nk - LAG); kc < nk; ++kc) arrive_full(kc);
+    } else if (lane == 0) {
+        // ---- MMA thread
+        for (int kc = 0; kc < nk; ++kc) {
+            const int b = kc % NS;
+            ok = mbar_wait(&s_full[b], (uint32_t)((kc / NS) & 1)) && ok;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            float *sAh = st0 + (size_t)b * stage_f, *sAl = sAh + TC_M * KT, *sBh = sAl + TC_M * KT,
+                  *sBl = sBh + npad * KT;
+#pragma unroll
             for (int ks = 0; ks < KT / 8; ++ks) {
                 uint64_t ah = umma_desc(smem_addr(sAh) + ks * 256, lbo, sbo);
                 uint64_t al = umma_desc(smem_addr(sAl) + ks * 256, lbo, sbo);
                 uint64_t bh = umma_desc(smem_addr(sBh) + ks * 256, lbo, sbo);
                 uint64_t bl = umma_desc(smem_addr(sBl) + ks * 256, lbo, sbo);
-                uint32_t acc0 = (k0 > 0 || ks > 0) ? 1u : 0u;
+                uint32_t acc0 = (kc > 0 || ks > 0) ? 1u : 0u;
                 asm volatile(
                     "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
                     "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
@@ -507,21 +523,21 @@ __global__ void __launch_bounds__(256) k_lag_gemm_tc(const uint32_t *__restrict_
                              "r"(idesc));
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                             smem_addr(&s_mbar))
+                             smem_addr(&s_empty[b]))
                          : "memory");
         }
-        // bounded wait for this K tile's MMAs before the buffers are refilled or D is read
-        uint32_t done = 0;
-        for (int it = 0; it < (1 << 24) && !done; ++it)
-            asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
-                         : "=r"(done)
-                         : "r"(smem_addr(&s_mbar)), "r"(phase));
-        if (!done) ok = false;
-        phase ^= 1;
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        __syncthreads();
+        // the last chunk's MMAs complete after all earlier ones
+        ok = mbar_wait(&s_empty[(nk - 1) % NS], (uint32_t)(((nk - 1) / NS) & 1)) && ok;
     }
-    if (!ok && tid == 0) atomicOr(err, 1);
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (!ok) atomicOr(err, 1);
+    __shared__ int s_bad;
+    if (tid == 0) s_bad = 0;
+    __syncthreads();
+    if (!ok) s_bad = 1;
+    __syncthreads();
+    ok = s_bad == 0;
     // epilogue: warps 0-3 hold TMEM lanes 32w..32w+31 = pairs; columns = target nodes i.
     // Warps 4-7 (the second warpgroup) take the odd column chunks of the same lanes.
     int quarter = warp & 3;
@@ -552,6 +568,23 @@ __global__ void __launch_bounds__(256) k_lag_gemm_tc(const uint32_t *__restrict_
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tcols));
 }
 
+// TF32 hi / lo parts of nmat row-major matrices (rows x cols), written with rows_pad rows
+// of cols_pad floats each (padding zero).
+__global__ void k_split_pad(const float *__restrict__ src, int64_t nmat, int rows, int cols, int rows_pad,
+                            int cols_pad, float *__restrict__ hi, float *__restrict__ lo) {
+    int64_t n = nmat * rows_pad * (int64_t)cols_pad;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        int64_t mat = i / ((int64_t)rows_pad * cols_pad);
+        int rem = (int)(i - mat * rows_pad * (int64_t)cols_pad);
+        int row = rem / cols_pad, col = rem - row * cols_pad;
+        float x = row < rows && col < cols ? src[(mat * rows + row) * (int64_t)cols + col] : 0.f;
+        float h, l;
+        tf32_split(x, h, l);
+        hi[i] = h;
+        lo[i] = l;
+    }
+}
+
 // ---- target-stationary tensor-core transfer (r <= 64)
 //
 // A CTA owns TS_M = 128 consecutive target boxes of the level (TMEM lane = box).  For every
@@ -570,20 +603,6 @@ constexpr int TS_B = 64 * 64;    // floats per B hi or lo block
 constexpr int TS_STAGE = 2 * TS_A + 2 * TS_B;
 constexpr int TS_MAXT = 4096;    // translation codes lie in a 16^3 range
 constexpr int TS_DRAIN = 8;      // translations per TMEM accumulation before it is drained
-
-__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
-}
-
-// bounded wait on an mbarrier phase; false if it gave up
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
-    uint32_t done = 0;
-    for (int it = 0; it < (1 << 24) && !done; ++it)
-        asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
-                     : "=r"(done)
-                     : "r"(smem_addr(bar)), "r"(parity));
-    return done != 0;
-}
 
 __global__ void __launch_bounds__(2 * TS_M) k_lag_gemm_ts(const uint32_t *__restrict__ tgt, int64_t n_tgt,
                                                          const uint32_t *__restrict__ adm_off,
@@ -881,6 +900,13 @@ static void lagrange_points_r1(const ffm_plan_s *p, const FarLevel &F, const Lev
     }
 }
 
+void split_pad(const float *src, int64_t nmat, int rows, int cols, int rows_pad, int cols_pad, float *hi, float *lo,
+               cudaStream_t s) {
+    int64_t n = nmat * rows_pad * (int64_t)cols_pad;
+    unsigned g = (unsigned)std::min<int64_t>((n + 255) / 256, 152 * 16);
+    FFM_LAUNCH(k_split_pad, g, 256, 0, s, src, nmat, rows, cols, rows_pad, cols_pad, hi, lo);
+}
+
 void far_lagrange(const ffm_plan_s *p, int l, const void *q, int nrhs, float2 *accf, Alloc &tmp, cudaStream_t s) {
     const FarLevel &F = p->far[l];
     int ls = p->l_stop;
@@ -918,21 +944,30 @@ void far_lagrange(const ffm_plan_s *p, int l, const void *q, int nrhs, float2 *a
             dim3 gts(cdiv(F.n_tgt, TS_M), nrhs);
             FFM_LAUNCH(k_lag_gemm_ts, gts, 2 * TS_M, smem, s, F.tgt, F.n_tgt, F.adm_off, F.adm_src, F.adm_t, F.n_trans,
                        F.Tsp, r, nrhs, (const float *)ut, (float *)vt, p->dev_err);
-        } else if (npad <= 256 && F.tc_tiles > 0 && F.tune_tc != 0) {
-            // tensor cores: 128-pair tiles, K tiles of KT source nodes
-            constexpr int KT = 64;
+        } else if (npad <= 256 && F.tc_tiles > 0 && F.tune_tc != 0 && F.Tsh) {
+            // tensor cores: 128-pair tiles, K chunks of KT source nodes through NS stages, operands
+            // pre-split into TF32 hi and lo parts with rows padded to rkp floats
+            constexpr int KT = 16, NS = 4;
+            int rkp = F.rkp;
+            int64_t nrow = (int64_t)p->by[l].nb * nrhs;
+            float *uh = tmp.get<float>((size_t)nrow * rkp), *ul = tmp.get<float>((size_t)nrow * rkp);
+            split_pad((const float *)ut, 1, (int)nrow, rk, (int)nrow, rkp, uh, ul, s);
             int tcols = 32;
             while (tcols < npad) tcols <<= 1;
-            size_t smem = (size_t)(2 * TC_M * KT + 2 * npad * KT) * sizeof(float);
+            size_t smem = NS * (size_t)(2 * TC_M * KT + 2 * npad * KT) * sizeof(float);
             static bool attr = false;
             if (!attr) {
-                FFM_CUDA(cudaFuncSetAttribute(k_lag_gemm_tc<KT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              (int)(2 * TC_M * KT + 2 * 256 * KT) * (int)sizeof(float)));
+                FFM_CUDA(cudaFuncSetAttribute(k_lag_gemm_tc<KT, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              NS * (int)(2 * TC_M * KT + 2 * 256 * KT) * (int)sizeof(float)));
                 attr = true;
             }
+            size_t tsz = (size_t)F.n_trans * npad * rkp;
             dim3 gtc((unsigned)F.tc_tiles, nrhs);
-            FFM_LAUNCH(k_lag_gemm_tc<KT>, gtc, 256, smem, s, F.tc_tile_t, F.tc_tile_p0, F.bt_off, F.bt_src, F.bt_tgt,
-                       F.T, r, rk, npad, tcols, nrhs, (const float *)ut, (float *)vt, p->dev_err);
+            FFM_LAUNCH((k_lag_gemm_tc<KT, NS>), gtc, 256, smem, s, F.tc_tile_t, F.tc_tile_p0, F.bt_off, F.bt_src,
+                       F.bt_tgt, (const float *)F.Tsh, (const float *)(F.Tsh + tsz), r, rkp, npad, tcols, nrhs,
+                       (const float *)uh, (const float *)ul, (float *)vt, p->dev_err);
+            tmp.drop(ul);
+            tmp.drop(uh);
         } else {
             FFM_LAUNCH(k_lag_gemm<false>, gg, LG_T, 0, s, F.tile_t, F.tile_p0, F.bt_off, F.bt_src, F.bt_tgt, F.T, r,
                        rk, nrhs, (const float *)ut, (float *)vt);

@@ -336,6 +336,15 @@ void build_tables(ffm_plan_s *p, int l, TableJob &tj) {
         g.kind = p->kind;
         for (int a = 0; a < F.r1; ++a) g.hnode[a] = (float)(0.5 * dl * std::cos((2.0 * a + 1.0) * PI / (2.0 * F.r1)));
         FFM_LAUNCH(k_lag_table, F.n_trans, 256, 0, s, F.trans_m, F.n_trans, g, F.T);
+        int rk = p->kind == FFM_LAPLACE_DL ? 3 * r : r, npad = (r + 15) / 16 * 16;
+        if (!cplx && npad <= 256) {
+            // the tensor-core transfer's operand: T_t in TF32 hi and lo parts, npad rows of rkp
+            // (a multiple of its 16-node K chunks) floats, padding zero
+            F.rkp = (rk + 15) / 16 * 16;
+            size_t tsz = (size_t)F.n_trans * npad * F.rkp;
+            F.Tsh = p->mem.get<float>(2 * tsz);
+            split_pad(F.T, F.n_trans, r, rk, npad, F.rkp, F.Tsh, F.Tsh + tsz, s);
+        }
         return;
     }
     // plane waves: quadrature of eq. 17, (L+1) Gauss-Legendre nodes in cos(theta) times 2L
