@@ -44,7 +44,7 @@
 #define ORC_LMAX 21
 #define ORC_PI 3.14159265358979323846
 
-enum { ORC_LAPLACE = 0, ORC_HELMHOLTZ = 1, ORC_POLY = 2, ORC_LAPLACE_DL = 3 };
+enum { ORC_LAPLACE = 0, ORC_HELMHOLTZ = 1, ORC_POLY = 2, ORC_LAPLACE_DL = 3, ORC_LAPLACE_GRAD = 4 };
 enum { ORC_OK = 0, ORC_EINVAL = 1, ORC_ENOMEM = 2 };
 enum { ORC_MODE_NONE = 0, ORC_MODE_LAGRANGE = 1, ORC_MODE_PLANEWAVE = 2 };
 
@@ -76,7 +76,7 @@ static void orc_kernel(int kind, double k, double dx, double dy, double dz, doub
         return;
     }
     double a = 1.0 / (4.0 * ORC_PI * r);
-    if (kind == ORC_LAPLACE || kind == ORC_LAPLACE_DL) {
+    if (kind == ORC_LAPLACE || kind == ORC_LAPLACE_DL || kind == ORC_LAPLACE_GRAD) {
         *gr = a;
         *gi = 0.0;
     } else {
@@ -168,6 +168,33 @@ int orc_direct_dl(const double *X, int64_t nx, const double *Y, int64_t ny, cons
                 acc += wj * u[j + ny * m] * nd / (4.0 * ORC_PI * r2 * r);
             }
             v[s + nt * m] = acc;
+        }
+    }
+    return ORC_OK;
+}
+
+/* O1 for the gradient of the single layer in the target variable (the MFIE kernel of
+ * Sec. 4.2): v_i = sum_j w_j u_j grad_x G(x_i - y_j), grad_x G = -(x - y) / (4 pi |x - y|^3);
+ * component d of right-hand side m in column 3 m + d of v (nt x 3 nrhs, column-major). */
+int orc_direct_grad(const double *X, int64_t nx, const double *Y, int64_t ny, const double *w, const double *u,
+                    int nrhs, const int64_t *tsel, int64_t nsel, double *v)
+{
+    if (nx < 0 || ny < 0 || nrhs < 1) return ORC_EINVAL;
+    int64_t nt = tsel ? nsel : nx;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t s = 0; s < nt; ++s) {
+        int64_t i = tsel ? tsel[s] : s;
+        const double *x = X + 3 * i;
+        for (int m = 0; m < nrhs; ++m) {
+            double acc[3] = {0.0, 0.0, 0.0};
+            for (int64_t j = 0; j < ny; ++j) {
+                double d[3] = {x[0] - Y[3 * j], x[1] - Y[3 * j + 1], x[2] - Y[3 * j + 2]};
+                double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+                if (r2 == 0.0) continue;
+                double f = (w ? w[j] : 1.0) * u[j + ny * m] / (4.0 * ORC_PI * r2 * sqrt(r2));
+                for (int c = 0; c < 3; ++c) acc[c] -= f * d[c];
+            }
+            for (int c = 0; c < 3; ++c) v[s + nt * (3 * m + c)] = acc[c];
         }
     }
     return ORC_OK;
@@ -337,7 +364,11 @@ static const double ORC_R1_ERR_LAPLACE_DL[11] = {1, 1, 1.2e-1, 2.4e-2, 5.1e-3, 1
 
 static const double *r1_table(int kind)
 {
-    return kind == ORC_HELMHOLTZ ? ORC_R1_ERR_HELM : kind == ORC_LAPLACE_DL ? ORC_R1_ERR_LAPLACE_DL : ORC_R1_ERR_LAPLACE;
+    /* the gradient's component kernels dG/dx_d = -(x - y)_d / (4 pi |x - y|^3) are the double
+     * layer's up to sign: same interpolation error, same table */
+    return kind == ORC_HELMHOLTZ ? ORC_R1_ERR_HELM
+           : (kind == ORC_LAPLACE_DL || kind == ORC_LAPLACE_GRAD) ? ORC_R1_ERR_LAPLACE_DL
+                                                                  : ORC_R1_ERR_LAPLACE;
 }
 
 int orc_r1_rule(int kind, double eps)
@@ -1334,5 +1365,157 @@ int orc_apply_dl(const orc_plan *p, const double *nrm, const double *w, const do
     free(zero);
     free(accr);
     free(acci);
+    return ORC_OK;
+}
+
+/* Gradient (kind ORC_LAPLACE_GRAD), one Lagrange level: the source step is the plain
+ * Laplace one, u~_b = L_Y(b) w u; the three component kernels dG/dx_d are interpolated
+ * separately (Sec. 2.2.2 per component), v~^d_a = sum_b T^d_{ab} u~_b with
+ * T^d_{ab}[i][j] = -(x_i - y_j)_d / (4 pi |x_i - y_j|^3) at the Chebyshev nodes, and the
+ * target step interpolates each component. */
+static void far_lagrange_grad(const orc_plan *p, int l, const double *q, int nrhs, double *acc)
+{
+    int r1 = p->st.r1[l], r = r1 * r1 * r1;
+    double t[16];
+    cheb_nodes(r1, t);
+    double dl = ldexp(p->d0, -l);
+    int64_t nbY = p->nby[l], nbX = p->nbx[l];
+    int64_t ny = p->ty.n, nx = p->tx.n;
+    double *ut = (double *)calloc((size_t)nbY * nrhs * r, sizeof(double));
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t b = 0; b < nbY; ++b) {
+        const obox *B = &p->by[l][b];
+        double c[3], Lb[1000];
+        box_centre(p->ty.o, B->g, dl, c);
+        for (int64_t j = B->s; j < B->e; ++j) {
+            lagrange_3d(r1, t, p->ty.p + 3 * j, c, dl, Lb);
+            for (int m = 0; m < nrhs; ++m)
+                for (int a = 0; a < r; ++a) ut[((size_t)b * nrhs + m) * r + a] += Lb[a] * q[j + ny * m];
+        }
+    }
+    int64_t na = p->st.n_adm[l];
+    const opair *adm = p->adm[l];
+    int64_t *first = (int64_t *)malloc(sizeof(int64_t) * (nbX + 1));
+    {
+        int64_t i = 0;
+        for (int64_t a = 0; a <= nbX; ++a) {
+            while (i < na && adm[i].a < a) ++i;
+            first[a] = i;
+        }
+    }
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t a = 0; a < nbX; ++a) {
+        if (first[a] == first[a + 1]) continue;
+        const obox *A = &p->bx[l][a];
+        double ca[3];
+        box_centre(p->tx.o, A->g, dl, ca);
+        double *vt = (double *)calloc((size_t)nrhs * 3 * r, sizeof(double));
+        double *T = (double *)malloc(sizeof(double) * 3 * r * r);
+        for (int64_t e = first[a]; e < first[a + 1]; ++e) {
+            int64_t b = adm[e].b;
+            double cb[3];
+            box_centre(p->ty.o, p->by[l][b].g, dl, cb);
+            for (int i = 0; i < r; ++i) {
+                int ix = i / (r1 * r1), iy = (i / r1) % r1, iz = i % r1;
+                double xc[3] = {ca[0] + t[ix] * 0.5 * dl, ca[1] + t[iy] * 0.5 * dl, ca[2] + t[iz] * 0.5 * dl};
+                for (int j = 0; j < r; ++j) {
+                    int jx = j / (r1 * r1), jy = (j / r1) % r1, jz = j % r1;
+                    double yc[3] = {cb[0] + t[jx] * 0.5 * dl, cb[1] + t[jy] * 0.5 * dl, cb[2] + t[jz] * 0.5 * dl};
+                    double dd[3] = {xc[0] - yc[0], xc[1] - yc[1], xc[2] - yc[2]};
+                    double r2 = dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2];
+                    for (int d = 0; d < 3; ++d) T[((size_t)d * r + i) * r + j] = -dd[d] / (4.0 * ORC_PI * r2 * sqrt(r2));
+                }
+            }
+            for (int m = 0; m < nrhs; ++m) {
+                const double *u = ut + ((size_t)b * nrhs + m) * r;
+                for (int d = 0; d < 3; ++d)
+                    for (int i = 0; i < r; ++i) {
+                        double sum = 0;
+                        for (int j = 0; j < r; ++j) sum += T[((size_t)d * r + i) * r + j] * u[j];
+                        vt[((size_t)m * 3 + d) * r + i] += sum;
+                    }
+            }
+        }
+        double La[1000];
+        for (int64_t i = A->s; i < A->e; ++i) {
+            lagrange_3d(r1, t, p->tx.p + 3 * i, ca, dl, La);
+            for (int m = 0; m < nrhs; ++m)
+                for (int d = 0; d < 3; ++d) {
+                    double sum = 0;
+                    for (int c = 0; c < r; ++c) sum += La[c] * vt[((size_t)m * 3 + d) * r + c];
+                    acc[i + nx * (3 * m + d)] += sum;
+                }
+        }
+        free(vt);
+        free(T);
+    }
+    free(first);
+    free(ut);
+}
+
+/* Gradient near field at the stop level: the direct sum over the near leaf pairs. */
+static void near_field_grad(const orc_plan *p, const double *q, int nrhs, double *acc)
+{
+    int l = p->st.l_stop;
+    int64_t nbX = p->nbx[l], nn = p->n_nearp, nx = p->tx.n, ny = p->ty.n;
+    const opair *pr = p->nearp;
+    int64_t *first = (int64_t *)malloc(sizeof(int64_t) * (nbX + 1));
+    {
+        int64_t i = 0;
+        for (int64_t a = 0; a <= nbX; ++a) {
+            while (i < nn && pr[i].a < a) ++i;
+            first[a] = i;
+        }
+    }
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t a = 0; a < nbX; ++a) {
+        const obox *A = &p->bx[l][a];
+        for (int64_t i = A->s; i < A->e; ++i) {
+            const double *x = p->tx.p + 3 * i;
+            for (int m = 0; m < nrhs; ++m) {
+                double g[3] = {0, 0, 0};
+                for (int64_t e = first[a]; e < first[a + 1]; ++e) {
+                    const obox *B = &p->by[l][pr[e].b];
+                    for (int64_t j = B->s; j < B->e; ++j) {
+                        const double *y = p->ty.p + 3 * j;
+                        double d[3] = {x[0] - y[0], x[1] - y[1], x[2] - y[2]};
+                        double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+                        if (r2 == 0.0) continue;
+                        double f = q[j + ny * m] / (4.0 * ORC_PI * r2 * sqrt(r2));
+                        for (int c = 0; c < 3; ++c) g[c] -= f * d[c];
+                    }
+                }
+                for (int c = 0; c < 3; ++c) acc[i + nx * (3 * m + c)] += g[c];
+            }
+        }
+    }
+    free(first);
+}
+
+/* Gradient product by the FFM for a plan built with kind ORC_LAPLACE_GRAD (Lagrange levels
+ * only): v (nx x 3 nrhs, column 3 m + d) = sum_j w_j u_j grad_x G(x_i - y_j). */
+int orc_apply_grad(const orc_plan *p, const double *w, const double *u, int nrhs, double *v)
+{
+    if (!p || nrhs < 1 || p->kind != ORC_LAPLACE_GRAD) return ORC_EINVAL;
+    int64_t nx = p->tx.n, ny = p->ty.n;
+    double *q = (double *)malloc(sizeof(double) * ny * nrhs);
+    double *acc = (double *)calloc((size_t)nx * 3 * nrhs, sizeof(double));
+    if (!q || !acc) {
+        free(q);
+        free(acc);
+        return ORC_ENOMEM;
+    }
+    for (int m = 0; m < nrhs; ++m)
+        for (int64_t j = 0; j < ny; ++j) {
+            int64_t o = p->ty.perm[j];
+            q[j + ny * m] = (w ? w[o] : 1.0) * u[o + ny * m];
+        }
+    for (int l = 0; l <= ORC_LMAX; ++l)
+        if (p->st.n_adm[l] > 0) far_lagrange_grad(p, l, q, nrhs, acc);
+    if (p->n_nearp > 0) near_field_grad(p, q, nrhs, acc);
+    for (int c = 0; c < 3 * nrhs; ++c)
+        for (int64_t i = 0; i < nx; ++i) v[p->tx.perm[i] + nx * c] = acc[i + nx * c];
+    free(q);
+    free(acc);
     return ORC_OK;
 }

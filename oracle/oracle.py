@@ -12,7 +12,7 @@ import numpy as np
 
 from . import build as _build
 
-LAPLACE, HELMHOLTZ, POLY, LAPLACE_DL = 0, 1, 2, 3
+LAPLACE, HELMHOLTZ, POLY, LAPLACE_DL, LAPLACE_GRAD = 0, 1, 2, 3, 4
 MODE_NONE, MODE_LAGRANGE, MODE_PLANEWAVE = 0, 1, 2
 LMAX = 21
 
@@ -96,6 +96,10 @@ def lib():
         L.orc_direct_dl.restype = C.c_int
         L.orc_apply_dl.argtypes = [C.c_void_p, _dp, _dp, _dp, C.c_int, _dp]
         L.orc_apply_dl.restype = C.c_int
+        L.orc_direct_grad.argtypes = [_dp, C.c_int64, _dp, C.c_int64, _dp, _dp, C.c_int, _i64p, C.c_int64, _dp]
+        L.orc_direct_grad.restype = C.c_int
+        L.orc_apply_grad.argtypes = [C.c_void_p, _dp, _dp, C.c_int, _dp]
+        L.orc_apply_grad.restype = C.c_int
         L.orc_nthreads.restype = C.c_int
         L.orc_set_threads.argtypes = [C.c_int]
         _lib = L
@@ -210,6 +214,16 @@ class Plan:
         if rc:
             raise ValueError("orc_apply_dl failed: %d" % rc)
         return v
+
+    def apply_grad(self, u, w=None):
+        """Gradient product (plan built with kind LAPLACE_GRAD): real u; returns (nx, nrhs, 3)."""
+        re, _, nrhs = _split_u(u)
+        w = None if w is None else _c64(w)
+        v = np.zeros((self.nx, 3 * nrhs), order="F")
+        rc = lib().orc_apply_grad(self._h, _d(w), _d(re), nrhs, _d(v))
+        if rc:
+            raise ValueError("orc_apply_grad failed: %d" % rc)
+        return v.reshape(self.nx, nrhs, 3)
 
     def apply(self, u, w=None):
         re, im, nrhs = _split_u(u)
@@ -423,3 +437,32 @@ def ffm_nufft(X, Y, u, kind, k, eps, w=None, **opts):
         return with_p.apply(u, w=w)
     finally:
         with_p.close()
+
+
+def direct_grad(X, Y, u, w=None, targets=None):
+    """O1 for the gradient of the single layer in the target variable:
+    v_i = sum_j w_j u_j grad_x G(x_i - y_j), shape (n, nrhs, 3)."""
+    X = _c64(X).reshape(-1, 3)
+    Y = _c64(Y).reshape(-1, 3)
+    re, _, nrhs = _split_u(u)
+    w = None if w is None else _c64(w)
+    if targets is None:
+        tsel, nt = None, X.shape[0]
+    else:
+        tsel = np.ascontiguousarray(targets, dtype=np.int64)
+        nt = tsel.shape[0]
+    v = np.zeros((nt, 3 * nrhs), order="F")
+    rc = lib().orc_direct_grad(_d(X), X.shape[0], _d(Y), Y.shape[0], _d(w), _d(re), nrhs,
+                               tsel.ctypes.data_as(_i64p) if tsel is not None else None, nt, _d(v))
+    if rc:
+        raise ValueError("orc_direct_grad failed: %d" % rc)
+    return v.reshape(nt, nrhs, 3)
+
+
+def ffm_grad(X, Y, u, eps=1e-3, w=None, **opts):
+    """O2 for the gradient: Lagrange levels with the three component kernels dG/dx_d."""
+    p = Plan(X, Y, LAPLACE_GRAD, 0.0, eps, **opts)
+    try:
+        return p.apply_grad(u, w=w)
+    finally:
+        p.close()

@@ -534,3 +534,48 @@ def test_ffm_with_nufft_within_eps(eps):
     assert O.rel_l2(vn, ref) < eps
     assert O.rel_l2(vn, vd) < eps / 10
     assert O.Plan(prob.X, prob.Y, prob.kind, prob.k, eps).stats()["mode"][2] == O.MODE_PLANEWAVE
+
+
+# ------------------------------------------------- gradient of the single layer (Sec. 4.2)
+
+def test_gradient_of_the_charged_sphere_potential():
+    """The potential of the uniformly charged unit sphere is 1 inside and 1/|x| outside, so
+    its gradient is 0 inside and -x/|x|^3 outside (to quadrature accuracy)."""
+    s, w = _sphere_grid(40)
+    inside = np.array([[0.1, 0.2, -0.3], [0.0, 0.0, 0.0], [-0.4, 0.3, 0.35]])
+    outside = np.array([[1.5, 0.3, 0.2], [0.0, -2.0, 0.5], [3.0, 3.0, -3.0]])
+    g_in = O.direct_grad(inside, s, np.ones(len(w)), w=w)[:, 0, :]
+    g_out = O.direct_grad(outside, s, np.ones(len(w)), w=w)[:, 0, :]
+    assert np.max(np.abs(g_in)) < 1e-9
+    exact = -outside / np.linalg.norm(outside, axis=1)[:, None] ** 3
+    assert np.max(np.abs(g_out - exact)) < 1e-9
+
+
+def test_gradient_is_the_derivative_of_the_laplace_potential():
+    """Central differences of the Laplace direct sum in the target position."""
+    rng = np.random.default_rng(31)
+    Y = rng.standard_normal((50, 3))
+    u = rng.standard_normal(50)
+    x = np.array([[0.3, -2.5, 1.7]])
+    h = 1e-5
+    g = O.direct_grad(x, Y, u)[0, 0, :]
+    for d in range(3):
+        e = np.zeros((1, 3))
+        e[0, d] = h
+        fd = (O.direct(x + e, Y, u, O.LAPLACE)[0, 0].real - O.direct(x - e, Y, u, O.LAPLACE)[0, 0].real) / (2 * h)
+        assert abs(fd - g[d]) < 1e-7 * max(1.0, abs(g[d]))
+
+
+@pytest.mark.parametrize("eps,rad", [(1e-3, 0.6), (1e-4, 1.25)])
+def test_gradient_ffm_within_eps(eps, rad):
+    """O2 for the gradient against O1, targets on a sphere of radius rad inside / outside
+    the source sphere (the far field carries most of the result there)."""
+    n = 15000
+    Y = W.sphere_surface(n, 1001)
+    X = W.sphere_surface(n, 1) * rad
+    u = np.random.default_rng(3).standard_normal(n)
+    w = np.full(n, 4 * np.pi / n)
+    v = O.ffm_grad(X, Y, u, eps, w=w)[:, 0, :]
+    ref = O.direct_grad(X, Y, u, w=w)[:, 0, :]
+    assert O.rel_l2(v, ref) < eps
+    assert O.r1_rule(O.LAPLACE_GRAD, eps) == O.r1_rule(O.LAPLACE_DL, eps)
