@@ -41,7 +41,7 @@ def parse():
     ap.add_argument("--impl", default="ffm", choices=["ffm", "reference"])
     ap.add_argument("--workload", default="helmholtz_sphere_1M",
                     choices=["helmholtz_sphere_1M", "laplace_sphere_20k", "helmholtz_cube_200k_64rhs",
-                             "laplace_clustered", "laplace_double_layer_sphere_1M"])
+                             "laplace_clustered", "laplace_double_layer_sphere_1M", "laplace_gradient_sphere_1M"])
     ap.add_argument("--n", type=int, default=0, help="points per set (0: the workload's own size)")
     ap.add_argument("--serving", action="store_true",
                     help="serving stream: Poisson arrivals of mixed requests, p50/p99 latency and throughput")
@@ -69,6 +69,8 @@ def make_problem(name, seed, n=0):
         return W.laplace_clustered(n or 100_000_000, seed=seed)
     if name == "laplace_double_layer_sphere_1M":
         return W.laplace_double_layer_sphere(n or 1_000_000, seed=seed)
+    if name == "laplace_gradient_sphere_1M":
+        return W.laplace_gradient_sphere(n or 1_000_000, seed=seed)
     return W.laplace_sphere(n or 20000, seed=seed)
 
 
@@ -141,6 +143,8 @@ def cpu_direct_sample(prob, ntargets, seed=12345):
     t0 = time.perf_counter()
     if "normals" in prob.meta:  # the double layer
         ref = O.direct_dl(prob.X, prob.Y, prob.meta["normals"], u, w=prob.w, targets=t)
+    elif prob.kind == W.LAPLACE_GRAD:  # (targets, nrhs, 3) -> (targets, 3 nrhs)
+        ref = O.direct_grad(prob.X, prob.Y, u, w=prob.w, targets=t).reshape(len(t), -1)
     else:
         ref = O.direct(prob.X, prob.Y, u, prob.kind, prob.k, w=prob.w, targets=t)  # (targets, nrhs)
     dt = time.perf_counter() - t0
@@ -156,8 +160,9 @@ def repeat_applies(ffm, torch, prob, X, Y, w, u, flush, stream, reps, tune_cache
     """Repeated products with one resident plan (an iterative solver's use): eager
     ffm_apply calls against launches of the same apply captured as a CUDA graph.  Device
     time per product with an L2 flush before each one (outside its events)."""
-    out = torch.empty_like(u)
     with ffm.Plan(X, Y, prob.kind, prob.k, prob.eps, weights=w, autotune_cache=tune_cache, **(kw or {})) as p:
+        out = p.apply(u)  # the output buffer (its shape depends on the kernel)
+
         def run(fn):
             fn()
             torch.cuda.synchronize()
@@ -237,6 +242,7 @@ def roofline(prof, info, steps, clk, pk, pk_kind, workload):
     - Laplace near field: instruction issue, at one rsqrt and about nine FP32 operations
       per pair (10 issue slots).  Double-layer near field: the same pipe at 64 slots per
       pair (hi+lo difference, rsqrt, cube, and the compensated dot product n.(x - y)).
+      Gradient near field: 20 slots (hi+lo difference, rsqrt, cube, three multiply-adds).
     - Gegenbauer transfer tables: FP32 issue, 72 instructions per recurrence step (double-float).
     - NUFFT grid kernels: the FP32 pipe, 4 FLOP per complex x real multiply-add of a W^3
       kernel window (per direction and box, or per point).
@@ -249,7 +255,8 @@ def roofline(prof, info, steps, clk, pk, pk_kind, workload):
     clk_hz = mhz * 1e6
     helm = any(m == 2 for m in info["mode"])
     dl = workload.startswith("laplace_double_layer")
-    kfac = 3 if dl else 1
+    grad = workload.startswith("laplace_gradient")
+    kfac = 3 if dl or grad else 1
     out = {"kernel": name, "launches_per_step": nl / steps, "ms_per_step": ms / steps,
            "traffic": measured_traffic(name, workload)}
     per_s = lambda units: units * steps / (ms * 1e-3)
@@ -266,7 +273,7 @@ def roofline(prof, info, steps, clk, pk, pk_kind, workload):
         out.update({"bound": "alu", "pipe": "MUFU", "unit": "Tops/s", "units_per_step": units,
                     "peak_basis": basis % ("%d MUFU results/clk" % MUFU_PER_SM_CLK)})
     elif "k_p2p" in name:
-        slots = 64 if dl else 10
+        slots = 64 if dl else 20 if grad else 10
         units = 1.0 * info["p2p_pairs"]
         peak = SM_COUNT * 128 * clk_hz / slots
         out.update({"bound": "alu", "pipe": "FP32 issue (%d slots per pair)" % slots, "unit": "Tpairs/s",
@@ -411,7 +418,7 @@ def main():
         return
 
     import torch
-    from paper_1909_05600_gb300 import build, ffm
+    from paper_1909_05600_gb300 import build, ffm, workloads as W
 
     build.build()
     torch.cuda.set_device(local)
@@ -517,7 +524,8 @@ def main():
         uh = torch.as_tensor(u_host).pin_memory()
         kwh = {k: torch.as_tensor(prob.meta[k]).pin_memory() for k in kw if k in prob.meta}
         kwh["pw_transform"] = kw["pw_transform"]
-        vh = torch.empty(tuple(uh.shape[:-1]) + (prob.X.shape[0],), dtype=uh.dtype).pin_memory()
+        vshape = tuple(uh.shape[:-1]) + ((3,) if prob.kind == W.LAPLACE_GRAD else ()) + (prob.X.shape[0],)
+        vh = torch.empty(vshape, dtype=uh.dtype).pin_memory()
         ke = max(2, args.steps // 2)
         ts = []
         for i in range(ke + 1):
@@ -540,10 +548,13 @@ def main():
     err = None
     if rank == 0 and not args.no_cpu_baseline:
         vg = vlast.cpu().numpy()
-        if vg.ndim == 2:
-            vg = vg[0]
         t, ref, dt, cores = cpu_direct_sample(prob, args.cpu_targets)
-        ref = ref[:, 0]
+        if prob.kind == W.LAPLACE_GRAD:
+            vg = (vg if vg.ndim == 2 else vg[0]).T  # (nx, 3) of the first right-hand side
+            ref = ref[:, :3]
+        else:
+            vg = vg if vg.ndim == 1 else vg[0]
+            ref = ref[:, 0]
         err = float(np.linalg.norm(vg[t] - ref) / np.linalg.norm(ref))
         cpu = {"value": 1.0 / (dt * prob.X.shape[0] / len(t)), "unit": "applies/s", "cores": cores,
                "kind": "oracle",
@@ -560,7 +571,8 @@ def main():
             "warmup": args.warmup, "ms_per_step": t_step / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": args.workload, "n_x": int(prob.X.shape[0]), "n_y": int(prob.Y.shape[0]),
-                       "kernel": {0: "laplace", 1: "helmholtz", 2: "laplace_double_layer"}[prob.kind],
+                       "kernel": {0: "laplace", 1: "helmholtz", 2: "laplace_double_layer",
+                                  3: "laplace_gradient"}[prob.kind],
                        "k": prob.k, "eps": prob.eps,
                        "u_dtype": str(prob.u.dtype), "step": "ffm_plan + ffm_apply + ffm_destroy",
                        "l2": "flushed between steps (512 MiB write, outside the step events)",

@@ -53,9 +53,12 @@ typedef enum {
 
 /* FFM_LAPLACE_DL is the double layer of the Laplace kernel, dG/dn_y(x - y) =
  * n_y . (x - y) / (4 pi |x - y|^3) with G = 1/(4 pi |x - y|) and n_y the source normals
- * (ffm_opts.normals, required); it runs through the kernel-independent Lagrange path
- * with the normal derivative of the interpolant in the source step (Sec. 2.2.2). */
-typedef enum { FFM_LAPLACE = 0, FFM_HELMHOLTZ = 1, FFM_LAPLACE_DL = 2 } ffm_kernel;
+ * (ffm_opts.normals, required).  FFM_LAPLACE_GRAD is the gradient of the single layer in
+ * the target variable, grad_x G(x - y) = -(x - y) / (4 pi |x - y|^3) (the MFIE kernel of
+ * Sec. 4.2): three outputs per target and right-hand side.  Both run through the
+ * kernel-independent Lagrange path (Sec. 2.2.2) with their three component kernels
+ * (x - y)_d / (4 pi |x - y|^3) interpolated separately. */
+typedef enum { FFM_LAPLACE = 0, FFM_HELMHOLTZ = 1, FFM_LAPLACE_DL = 2, FFM_LAPLACE_GRAD = 3 } ffm_kernel;
 
 typedef enum {
     FFM_F32 = 0,  /* float */
@@ -133,9 +136,11 @@ ffm_status ffm_plan(const void *X, ffm_dtype xdt, int64_t nx, const void *Y, ffm
 
 /* v = G W u through the plan (Sec. 2.2, Fig. of the descent): far field of every level
  * with admissible pairs, near field at the stop level, FP64 accumulation per target.
- *   u   : N_Y x nrhs column-major; Laplace: FFM_F32 or FFM_F64; Helmholtz: FFM_C64 or
- *         FFM_C128.
+ *   u   : N_Y x nrhs column-major; Laplace kinds: FFM_F32 or FFM_F64; Helmholtz: FFM_C64
+ *         or FFM_C128.
  *   v   : N_X x nrhs column-major, same dtype as u; overwritten (not accumulated).
+ *         FFM_LAPLACE_GRAD: N_X x 3 nrhs, component d of right-hand side m in column
+ *         3 m + d.
  *   nrhs: number of right-hand sides, >= 1.
  * Works on `stream`; returns once the work is enqueued (device u, v) or after the
  * result has been copied back (host v).  The plan is read-only here, so concurrent

@@ -177,14 +177,17 @@ void autotune(ffm_plan_s *p, int nrhs, const char *cache_path, cudaStream_t s) {
     const bool helm = p->kind == FFM_HELMHOLTZ;
     Alloc tmp;
     tmp.stream = s;
-    // densities and accumulators of the timing runs (values do not change the timing)
-    size_t qb = (helm ? 8 : 4) * (size_t)p->ny * nrhs;
+    // densities and accumulators of the timing runs (values do not change the timing), sized as
+    // in an apply: the double layer's densities are hi / lo float4 pairs, the gradient has three
+    // outputs per target and density
+    size_t qb = (p->kind == FFM_LAPLACE_DL ? 32 : helm ? 8 : 4) * (size_t)p->ny * nrhs;
     void *q = tmp.raw(qb);
     FFM_CUDA(cudaMemsetAsync(q, 0, qb, s));
-    double2 *acc = tmp.get<double2>((size_t)p->nx * nrhs);
-    FFM_CUDA(cudaMemsetAsync(acc, 0, sizeof(double2) * (size_t)p->nx * nrhs, s));
-    float2 *accf = tmp.get<float2>((size_t)p->nx * nrhs);
-    FFM_CUDA(cudaMemsetAsync(accf, 0, sizeof(float2) * (size_t)p->nx * nrhs, s));
+    size_t nout = (size_t)nrhs * (p->kind == FFM_LAPLACE_GRAD ? 3 : 1);
+    double2 *acc = tmp.get<double2>((size_t)p->nx * nout);
+    FFM_CUDA(cudaMemsetAsync(acc, 0, sizeof(double2) * (size_t)p->nx * nout, s));
+    float2 *accf = tmp.get<float2>((size_t)p->nx * nout);
+    FFM_CUDA(cudaMemsetAsync(accf, 0, sizeof(float2) * (size_t)p->nx * nout, s));
     Timer T(s);
 
     // ---- near field: work-item shape

@@ -917,7 +917,8 @@ void far_lagrange(const ffm_plan_s *p, int l, const void *q, int nrhs, float2 *a
     bool cplx = p->kind == FFM_HELMHOLTZ;
     int rk = p->kind == FFM_LAPLACE_DL ? 3 * r : r;  // K extent of the transfer
     size_t esz = cplx ? sizeof(float2) : sizeof(float);
-    size_t ub = esz * rk * nrhs * (size_t)p->by[l].nb, vb = esz * r * nrhs * (size_t)p->bx[l].nb;
+    size_t ub = esz * rk * nrhs * (size_t)p->by[l].nb,
+           vb = esz * r * nrhs * (size_t)p->bx[l].nb * (p->kind == FFM_LAPLACE_GRAD ? 3 : 1);
     void *ut = tmp.raw(ub);
     void *vt = tmp.raw(vb);
     dim3 gg((unsigned)F.n_tiles, cdiv(r, LG_BM), nrhs);
@@ -934,6 +935,23 @@ void far_lagrange(const ffm_plan_s *p, int l, const void *q, int nrhs, float2 *a
         else
             lagrange_points_r1<false>(p, F, AY, cb, true, q, nrhs, ut, s);
         int npad = (r + 15) / 16 * 16;
+        // the gradient has three operator blocks (component-major) and three outputs per
+        // target; v~ and the FP32 accumulators are component-major too
+        const int ncomp = p->kind == FFM_LAPLACE_GRAD ? 3 : 1;
+        const size_t tblk = (size_t)F.n_trans * r * rk;
+        const size_t vblk = (size_t)r * nrhs * p->bx[l].nb;
+        float *uh = nullptr, *ul = nullptr;
+        const bool use_tc = !(F.ts_ok && F.Tsp && F.tune_tc == 2) && npad <= 256 && F.tc_tiles > 0 &&
+                            F.tune_tc != 0 && F.Tsh;
+        if (use_tc) {
+            int64_t nrow = (int64_t)p->by[l].nb * nrhs;
+            uh = tmp.get<float>((size_t)nrow * F.rkp);
+            ul = tmp.get<float>((size_t)nrow * F.rkp);
+            split_pad((const float *)ut, 1, (int)nrow, rk, (int)nrow, F.rkp, uh, ul, s);
+        }
+        for (int d = 0; d < ncomp; ++d) {
+            const float *Td = F.T + d * tblk;
+            float *vtd = (float *)vt + d * vblk;
         if (F.ts_ok && F.Tsp && F.tune_tc == 2) {
             size_t smem = (size_t)2 * TS_STAGE * sizeof(float);
             static bool attr_ts = false;
@@ -943,15 +961,12 @@ void far_lagrange(const ffm_plan_s *p, int l, const void *q, int nrhs, float2 *a
             }
             dim3 gts(cdiv(F.n_tgt, TS_M), nrhs);
             FFM_LAUNCH(k_lag_gemm_ts, gts, 2 * TS_M, smem, s, F.tgt, F.n_tgt, F.adm_off, F.adm_src, F.adm_t, F.n_trans,
-                       F.Tsp, r, nrhs, (const float *)ut, (float *)vt, p->dev_err);
-        } else if (npad <= 256 && F.tc_tiles > 0 && F.tune_tc != 0 && F.Tsh) {
+                       F.Tsp, r, nrhs, (const float *)ut, vtd, p->dev_err);
+        } else if (use_tc) {
             // tensor cores: 128-pair tiles, K chunks of KT source nodes through NS stages, operands
             // pre-split into TF32 hi and lo parts with rows padded to rkp floats
             constexpr int KT = 16, NS = 4;
             int rkp = F.rkp;
-            int64_t nrow = (int64_t)p->by[l].nb * nrhs;
-            float *uh = tmp.get<float>((size_t)nrow * rkp), *ul = tmp.get<float>((size_t)nrow * rkp);
-            split_pad((const float *)ut, 1, (int)nrow, rk, (int)nrow, rkp, uh, ul, s);
             int tcols = 32;
             while (tcols < npad) tcols <<= 1;
             size_t smem = NS * (size_t)(2 * TC_M * KT + 2 * npad * KT) * sizeof(float);
@@ -961,18 +976,21 @@ void far_lagrange(const ffm_plan_s *p, int l, const void *q, int nrhs, float2 *a
                                               NS * (int)(2 * TC_M * KT + 2 * 256 * KT) * (int)sizeof(float)));
                 attr = true;
             }
-            size_t tsz = (size_t)F.n_trans * npad * rkp;
+            size_t tsz = (size_t)ncomp * F.n_trans * npad * rkp, dsz = (size_t)F.n_trans * npad * rkp;
             dim3 gtc((unsigned)F.tc_tiles, nrhs);
             FFM_LAUNCH((k_lag_gemm_tc<KT, NS>), gtc, 256, smem, s, F.tc_tile_t, F.tc_tile_p0, F.bt_off, F.bt_src,
-                       F.bt_tgt, (const float *)F.Tsh, (const float *)(F.Tsh + tsz), r, rkp, npad, tcols, nrhs,
-                       (const float *)uh, (const float *)ul, (float *)vt, p->dev_err);
+                       F.bt_tgt, (const float *)(F.Tsh + d * dsz), (const float *)(F.Tsh + tsz + d * dsz), r, rkp,
+                       npad, tcols, nrhs, (const float *)uh, (const float *)ul, vtd, p->dev_err);
+        } else {
+            FFM_LAUNCH(k_lag_gemm<false>, gg, LG_T, 0, s, F.tile_t, F.tile_p0, F.bt_off, F.bt_src, F.bt_tgt, Td, r,
+                       rk, nrhs, (const float *)ut, vtd);
+        }
+            lagrange_points_r1<false>(p, F, AX, cb, false, vtd, nrhs, accf + (size_t)d * nrhs * p->nx, s);
+        }
+        if (uh) {
             tmp.drop(ul);
             tmp.drop(uh);
-        } else {
-            FFM_LAUNCH(k_lag_gemm<false>, gg, LG_T, 0, s, F.tile_t, F.tile_p0, F.bt_off, F.bt_src, F.bt_tgt, F.T, r,
-                       rk, nrhs, (const float *)ut, (float *)vt);
         }
-        lagrange_points_r1<false>(p, F, AX, cb, false, vt, nrhs, accf, s);
     }
 }
 

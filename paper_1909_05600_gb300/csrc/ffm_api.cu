@@ -167,17 +167,19 @@ __global__ void k_gather_q_dl(const UT *__restrict__ u, const uint32_t *__restri
     q[o + 1] = make_float4((float)(qx - (double)hx), (float)(qy - (double)hy), (float)(qz - (double)hz), 0.f);
 }
 
+// accumulator slot sl = d nrhs + m (d < ncomp) -> output column ncomp m + d
 template <class VT, bool CPLX>
 __global__ void k_scatter_v(const double2 *__restrict__ acc, const float2 *__restrict__ accf,
-                            const uint32_t *__restrict__ perm, int64_t nx, int nrhs, VT *__restrict__ v) {
+                            const uint32_t *__restrict__ perm, int64_t nx, int nrhs, int ncomp, VT *__restrict__ v) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    int m = blockIdx.y;
+    int sl = blockIdx.y;
     if (i >= nx) return;
-    double2 a = acc[(int64_t)m * nx + i];
-    float2 f = accf[(int64_t)m * nx + i];
+    double2 a = acc[(int64_t)sl * nx + i];
+    float2 f = accf[(int64_t)sl * nx + i];
     a.x += (double)f.x;
     a.y += (double)f.y;
-    int64_t o = (int64_t)perm[i] + (int64_t)m * nx;
+    int col = ncomp == 1 ? sl : ncomp * (sl % nrhs) + sl / nrhs;
+    int64_t o = (int64_t)perm[i] + (int64_t)col * nx;
     if constexpr (CPLX) {
         v[2 * o] = (VT)a.x;
         v[2 * o + 1] = (VT)a.y;
@@ -203,7 +205,10 @@ static void apply_impl(ffm_plan_s *p, const void *u, ffm_dtype udt, int nrhs, vo
     Alloc tmp;
     tmp.stream = s;
     int64_t nx = p->nx, ny = p->ny;
-    size_t ub = dtype_size(udt) * (size_t)ny * nrhs, vb = dtype_size(udt) * (size_t)nx * nrhs;
+    const int ncomp = p->kind == FFM_LAPLACE_GRAD ? 3 : 1;  // outputs per target and density
+    const int nout = ncomp * nrhs;
+    if (nout > 65535) fail(FFM_EINVAL, "the gradient takes at most 21845 right-hand sides");
+    size_t ub = dtype_size(udt) * (size_t)ny * nrhs, vb = dtype_size(udt) * (size_t)nx * nout;
     const void *du = u;
     if (!is_device_ptr(u)) {
         void *d = tmp.raw(ub);
@@ -214,11 +219,11 @@ static void apply_impl(ffm_plan_s *p, const void *u, ffm_dtype udt, int nrhs, vo
     void *dv = host_v ? tmp.raw(vb) : v;
     bool dl = p->kind == FFM_LAPLACE_DL;
     void *q = tmp.raw((dl ? 32 : helm ? 8 : 4) * (size_t)ny * nrhs);
-    double2 *acc = tmp.get<double2>((size_t)nx * nrhs);
-    FFM_CUDA(cudaMemsetAsync(acc, 0, sizeof(double2) * (size_t)nx * nrhs, s));
-    float2 *accf = tmp.get<float2>((size_t)nx * nrhs);
-    FFM_CUDA(cudaMemsetAsync(accf, 0, sizeof(float2) * (size_t)nx * nrhs, s));
-    dim3 gy(cdiv(ny, 256), nrhs), gx(cdiv(nx, 256), nrhs);
+    double2 *acc = tmp.get<double2>((size_t)nx * nout);
+    FFM_CUDA(cudaMemsetAsync(acc, 0, sizeof(double2) * (size_t)nx * nout, s));
+    float2 *accf = tmp.get<float2>((size_t)nx * nout);
+    FFM_CUDA(cudaMemsetAsync(accf, 0, sizeof(float2) * (size_t)nx * nout, s));
+    dim3 gy(cdiv(ny, 256), nrhs), gx(cdiv(nx, 256), nout);
     if (dl) {
         if (udt == FFM_F64)
             FFM_LAUNCH(k_gather_q_dl<double>, gy, 256, 0, s, (const double *)du, p->permY, p->wY, p->nY, p->nYlo, ny,
@@ -242,10 +247,10 @@ static void apply_impl(ffm_plan_s *p, const void *u, ffm_dtype udt, int nrhs, vo
     }
     near_field(p, q, nrhs, acc, s);
     switch (udt) {
-        case FFM_F32: FFM_LAUNCH((k_scatter_v<float, false>), gx, 256, 0, s, acc, accf, p->permX, nx, nrhs, (float *)dv); break;
-        case FFM_F64: FFM_LAUNCH((k_scatter_v<double, false>), gx, 256, 0, s, acc, accf, p->permX, nx, nrhs, (double *)dv); break;
-        case FFM_C64: FFM_LAUNCH((k_scatter_v<float, true>), gx, 256, 0, s, acc, accf, p->permX, nx, nrhs, (float *)dv); break;
-        case FFM_C128: FFM_LAUNCH((k_scatter_v<double, true>), gx, 256, 0, s, acc, accf, p->permX, nx, nrhs, (double *)dv); break;
+        case FFM_F32: FFM_LAUNCH((k_scatter_v<float, false>), gx, 256, 0, s, acc, accf, p->permX, nx, nrhs, ncomp, (float *)dv); break;
+        case FFM_F64: FFM_LAUNCH((k_scatter_v<double, false>), gx, 256, 0, s, acc, accf, p->permX, nx, nrhs, ncomp, (double *)dv); break;
+        case FFM_C64: FFM_LAUNCH((k_scatter_v<float, true>), gx, 256, 0, s, acc, accf, p->permX, nx, nrhs, ncomp, (float *)dv); break;
+        case FFM_C128: FFM_LAUNCH((k_scatter_v<double, true>), gx, 256, 0, s, acc, accf, p->permX, nx, nrhs, ncomp, (double *)dv); break;
     }
     if (host_v) {
         FFM_CUDA(cudaMemcpyAsync(v, dv, vb, cudaMemcpyDeviceToHost, s));
@@ -303,7 +308,7 @@ ffm_status ffm_plan(const void *X, ffm_dtype xdt, int64_t nx, const void *Y, ffm
         if ((int64_t)nx + ny >= ((int64_t)1 << 31)) fail(FFM_EUNSUPPORTED, "more than 2^31 points in total");
         if (xdt != FFM_F32 && xdt != FFM_F64) fail(FFM_EINVAL, "X dtype must be FFM_F32 or FFM_F64");
         if (ydt != FFM_F32 && ydt != FFM_F64) fail(FFM_EINVAL, "Y dtype must be FFM_F32 or FFM_F64");
-        if (kernel != FFM_LAPLACE && kernel != FFM_HELMHOLTZ && kernel != FFM_LAPLACE_DL)
+        if (kernel != FFM_LAPLACE && kernel != FFM_HELMHOLTZ && kernel != FFM_LAPLACE_DL && kernel != FFM_LAPLACE_GRAD)
             fail(FFM_EINVAL, "unknown kernel");
         if (kernel == FFM_LAPLACE_DL && (!opts || !opts->normals))
             fail(FFM_EINVAL, "the double layer needs source normals (opts.normals)");

@@ -77,7 +77,7 @@ __device__ __forceinline__ float rsqrt_hw(float x) {
 // Accumulate the staged sources [j0, j1) into (sr, si) for the PT targets x = xh + xl of
 // this thread.  Staged source j: sA[j] = (hi.x, hi.y, hi.z, w.re), sB[j] = (lo.x, lo.y,
 // lo.z, w.im): two 16-byte loads serve PT pairs.
-constexpr int NF_LAPLACE = 0, NF_HELMHOLTZ = 1, NF_DOUBLE_LAYER = 2;
+constexpr int NF_LAPLACE = 0, NF_HELMHOLTZ = 1, NF_DOUBLE_LAYER = 2, NF_GRADIENT = 3;
 
 // a + b with its rounding error (Knuth's TwoSum, no ordering assumption)
 __device__ __forceinline__ void two_sum_f(float a, float b, float &s, float &e) {
@@ -108,7 +108,8 @@ __device__ __forceinline__ float dot_pair(float4 xh, float4 xl, float4 yh, float
 
 template <int KIND, int PT>
 __device__ __forceinline__ void interact(const float4 *sA, const float4 *sB, const float4 *sC, int j0, int j1,
-                                         const float4 *xh, const float4 *xl, float k, float *sr, float *si) {
+                                         const float4 *xh, const float4 *xl, float k, float *sr, float *si,
+                                         float *sz) {
 #pragma unroll 2
     for (int j = j0; j < j1; ++j) {
         float4 y = sA[j];
@@ -126,6 +127,12 @@ __device__ __forceinline__ void interact(const float4 *sA, const float4 *sB, con
                 float4 c = sC[j];  // (q_hi.z, q_lo.x, q_lo.y, q_lo.z)
                 float qd = dot_pair(xh[t], xl[t], y, yl, make_float3(y.w, yl.w, c.x), make_float3(c.y, c.z, c.w));
                 sr[t] = fmaf(qd, inv * inv * inv, sr[t]);
+            } else if constexpr (KIND == NF_GRADIENT) {
+                // grad_x of w u / |x - y|: -(x - y) w u / |x - y|^3
+                float f = y.w * (inv * inv * inv);
+                sr[t] = fmaf(-f, dx, sr[t]);
+                si[t] = fmaf(-f, dy, si[t]);
+                sz[t] = fmaf(-f, dz, sz[t]);
             } else if constexpr (KIND == NF_HELMHOLTZ) {
                 // phase k r reduced to [-pi, pi] (Cody-Waite, two-term 2 pi) before sincos
                 float ph = k * (r2 * inv);
@@ -156,7 +163,7 @@ __global__ void __launch_bounds__(P2P_T) k_p2p(NearArgs N, const void *__restric
     __shared__ float4 sA[P2P_SB];
     __shared__ float4 sB[P2P_SB];
     __shared__ float4 sC[KIND == NF_DOUBLE_LAYER ? P2P_SB : 1];  // double layer: (q_hi.z, q_lo)
-    __shared__ float2 red[P2P_T * PT];
+    __shared__ float4 red[P2P_T * PT];
     int4 it = N.items[blockIdx.x];
     int a = it.x, m = blockIdx.y;
     uint32_t e0 = (uint32_t)it.z, e1 = (uint32_t)it.w;
@@ -171,14 +178,14 @@ __global__ void __launch_bounds__(P2P_T) k_p2p(NearArgs N, const void *__restric
     const float2 *qc = reinterpret_cast<const float2 *>(qv) + (int64_t)m * ny;
     const float4 *q3 = reinterpret_cast<const float4 *>(qv) + 2 * (int64_t)m * ny;
     float4 xh[PT], xl[PT];
-    float sr[PT], si[PT];
+    float sr[PT], si[PT], sz[PT];
 #pragma unroll
     for (int t = 0; t < PT; ++t) {
         int i = pi + t * pr;
         bool ok = active && i < np;
         xh[t] = ok ? N.epsX[p0 + i] : make_float4(0.f, 0.f, 0.f, 0.f);
         xl[t] = ok ? N.epsXlo[p0 + i] : make_float4(0.f, 0.f, 0.f, 0.f);
-        sr[t] = si[t] = 0.f;
+        sr[t] = si[t] = sz[t] = 0.f;
     }
     int fill = 0;
     for (uint32_t e = e0; e < e1; ++e) {
@@ -212,16 +219,17 @@ __global__ void __launch_bounds__(P2P_T) k_p2p(NearArgs N, const void *__restric
             c0 += take;
             if (fill == P2P_SB) {
                 __syncthreads();
-                if (active) interact<KIND, PT>(sA, sB, sC, grp * fill / G, (grp + 1) * fill / G, xh, xl, N.k, sr, si);
+                if (active)
+                    interact<KIND, PT>(sA, sB, sC, grp * fill / G, (grp + 1) * fill / G, xh, xl, N.k, sr, si, sz);
                 __syncthreads();
                 fill = 0;
             }
         }
     }
     __syncthreads();
-    if (active) interact<KIND, PT>(sA, sB, sC, grp * fill / G, (grp + 1) * fill / G, xh, xl, N.k, sr, si);
+    if (active) interact<KIND, PT>(sA, sB, sC, grp * fill / G, (grp + 1) * fill / G, xh, xl, N.k, sr, si, sz);
 #pragma unroll
-    for (int t = 0; t < PT; ++t) red[threadIdx.x * PT + t] = make_float2(sr[t], si[t]);
+    for (int t = 0; t < PT; ++t) red[threadIdx.x * PT + t] = make_float4(sr[t], si[t], sz[t], 0.f);
     __syncthreads();
     if (active && grp == 0) {
         const double c = 0.079577471545947667884;  // 1 / (4 pi)
@@ -229,10 +237,18 @@ __global__ void __launch_bounds__(P2P_T) k_p2p(NearArgs N, const void *__restric
         for (int t = 0; t < PT; ++t) {
             int i = pi + t * pr;
             if (i >= np) continue;
-            float tr = 0.f, ti = 0.f;
+            float tr = 0.f, ti = 0.f, tz = 0.f;
             for (int g = 0; g < G; ++g) {
                 tr += red[(g * pr + pi) * PT + t].x;
                 ti += red[(g * pr + pi) * PT + t].y;
+                tz += red[(g * pr + pi) * PT + t].z;
+            }
+            if constexpr (KIND == NF_GRADIENT) {
+                // component d of right-hand side m in accumulator slot d nrhs + m
+                atomicAdd(&acc[(int64_t)m * nx + p0 + i].x, (double)tr * c);
+                atomicAdd(&acc[((int64_t)nrhs + m) * nx + p0 + i].x, (double)ti * c);
+                atomicAdd(&acc[(2 * (int64_t)nrhs + m) * nx + p0 + i].x, (double)tz * c);
+                continue;
             }
             double2 *dst = &acc[(int64_t)m * nx + p0 + i];
             atomicAdd(&dst->x, (double)tr * c);
@@ -371,6 +387,11 @@ void near_field_items(const ffm_plan_s *p, const int4 *items, int64_t n_items, i
     if (p->kind == FFM_LAPLACE_DL) {
         dim3 g((unsigned)n_items, nrhs);
         FFM_LAUNCH(k_p2p<NF_DOUBLE_LAYER>, g, P2P_T, 0, s, N, q, p->ny, nrhs, p->nx, acc);
+        return;
+    }
+    if (p->kind == FFM_LAPLACE_GRAD) {
+        dim3 g((unsigned)n_items, nrhs);
+        FFM_LAUNCH(k_p2p<NF_GRADIENT>, g, P2P_T, 0, s, N, q, p->ny, nrhs, p->nx, acc);
         return;
     }
     if (nrhs > 1) {

@@ -25,7 +25,10 @@ static const double R1_ERR_HELM[11] = {1, 1, 2.4e-1, 3.4e-2, 3.6e-3, 3.6e-4, 4.0
 static const double R1_ERR_LAPLACE_DL[11] = {1, 1, 1.2e-1, 2.4e-2, 5.1e-3, 1.1e-3, 1.8e-4, 2.6e-5, 3.9e-6, 1.5e-6, 2.0e-7};
 
 int r1_rule(int kind, double eps) {
-    const double *t = kind == FFM_HELMHOLTZ ? R1_ERR_HELM : kind == FFM_LAPLACE_DL ? R1_ERR_LAPLACE_DL : R1_ERR_LAPLACE;
+    // the gradient's component kernels are the double layer's up to sign: same table
+    const double *t = kind == FFM_HELMHOLTZ                                  ? R1_ERR_HELM
+                      : (kind == FFM_LAPLACE_DL || kind == FFM_LAPLACE_GRAD) ? R1_ERR_LAPLACE_DL
+                                                                             : R1_ERR_LAPLACE;
     for (int r1 = 2; r1 <= 10; ++r1)
         if (t[r1] <= eps) return r1;
     return 10;
@@ -53,6 +56,21 @@ __global__ void k_lag_table(const int4 *__restrict__ m, int ntrans, LagGeo geo, 
           r0z = (float)(geo.oxy[2] + mt.z * geo.dl);
     bool cplx = geo.kind == FFM_HELMHOLTZ;
     const float c4pi = 0.07957747154594767f;  // 1 / (4 pi)
+    if (geo.kind == FFM_LAPLACE_GRAD) {
+        // the gradient's component kernels dG/dx_d = -(x - y)_d / (4 pi |x - y|^3), one
+        // r x r block per component: T[(d * ntrans + t)][i][j]
+        for (int e = threadIdx.x; e < 3 * r * r; e += blockDim.x) {
+            int d = e / (r * r), ij = e - d * r * r, i = ij / r, j = ij - i * r;
+            int ix = i / (r1 * r1), iy = (i / r1) % r1, iz = i % r1;
+            int jx = j / (r1 * r1), jy = (j / r1) % r1, jz = j % r1;
+            float dv[3] = {r0x + (geo.hnode[ix] - geo.hnode[jx]), r0y + (geo.hnode[iy] - geo.hnode[jy]),
+                           r0z + (geo.hnode[iz] - geo.hnode[jz])};
+            float r2 = fmaf(dv[0], dv[0], fmaf(dv[1], dv[1], dv[2] * dv[2]));
+            float rr = sqrtf(r2);
+            T[((size_t)d * ntrans + t) * r * r + ij] = -c4pi * dv[d] / (r2 * rr);
+        }
+        return;
+    }
     if (geo.kind == FFM_LAPLACE_DL) {
         // the double layer's component kernels dG/dy_d = (x - y)_d / (4 pi |x - y|^3),
         // stacked along K: T[t][i][d r + j]
@@ -327,7 +345,8 @@ void build_tables(ffm_plan_s *p, int l, TableJob &tj) {
     if (F.mode == 1) {
         int r = F.r1 * F.r1 * F.r1;
         bool cplx = p->kind == FFM_HELMHOLTZ;
-        F.T = p->mem.get<float>((size_t)F.n_trans * r * r * (cplx ? 2 : p->kind == FFM_LAPLACE_DL ? 3 : 1));
+        bool three = p->kind == FFM_LAPLACE_DL || p->kind == FFM_LAPLACE_GRAD;
+        F.T = p->mem.get<float>((size_t)F.n_trans * r * r * (cplx ? 2 : three ? 3 : 1));
             LagGeo g{};
         for (int d = 0; d < 3; ++d) g.oxy[d] = oxy[d];
         g.dl = dl;
@@ -339,11 +358,13 @@ void build_tables(ffm_plan_s *p, int l, TableJob &tj) {
         int rk = p->kind == FFM_LAPLACE_DL ? 3 * r : r, npad = (r + 15) / 16 * 16;
         if (!cplx && npad <= 256) {
             // the tensor-core transfer's operand: T_t in TF32 hi and lo parts, npad rows of rkp
-            // (a multiple of its 16-node K chunks) floats, padding zero
+            // (a multiple of its 16-node K chunks) floats, padding zero; the gradient's three
+            // component blocks one after another
+            int nblk = p->kind == FFM_LAPLACE_GRAD ? 3 : 1;
             F.rkp = (rk + 15) / 16 * 16;
-            size_t tsz = (size_t)F.n_trans * npad * F.rkp;
+            size_t tsz = (size_t)nblk * F.n_trans * npad * F.rkp;
             F.Tsh = p->mem.get<float>(2 * tsz);
-            split_pad(F.T, F.n_trans, r, rk, npad, F.rkp, F.Tsh, F.Tsh + tsz, s);
+            split_pad(F.T, (int64_t)nblk * F.n_trans, r, rk, npad, F.rkp, F.Tsh, F.Tsh + tsz, s);
         }
         return;
     }

@@ -20,7 +20,7 @@ except ImportError:  # pragma: no cover - torch is part of the environment
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libffm_gb300.so")
 
-LAPLACE, HELMHOLTZ, LAPLACE_DL = 0, 1, 2
+LAPLACE, HELMHOLTZ, LAPLACE_DL, LAPLACE_GRAD = 0, 1, 2, 3
 F32, F64, C64, C128 = 0, 1, 2, 3
 # plane-wave level arithmetic (ffm_precision)
 PREC_AUTO, PREC_F32, PREC_F32C, PREC_F64, PREC_F32X2 = 0, 1, 2, 3, 4
@@ -287,10 +287,13 @@ class Plan:
 
     def apply(self, u, out=None, stream=None):
         """v = G W u.  u: (ny,) or (nrhs, ny); returns (nx,) or (nrhs, nx) of u's dtype,
-        on u's device (torch) or as a numpy array (numpy input)."""
+        on u's device (torch) or as a numpy array (numpy input).  LAPLACE_GRAD returns
+        (3, nx) or (nrhs, 3, nx): the three components of the gradient."""
         one = u.ndim == 1
         nrhs = 1 if one else int(u.shape[0])
         shape = (self.nx,) if one else (nrhs, self.nx)
+        if self.kernel == LAPLACE_GRAD:
+            shape = (3, self.nx) if one else (nrhs, 3, self.nx)
         if out is None:
             if torch is not None and isinstance(u, torch.Tensor):
                 out = torch.empty(shape, dtype=u.dtype, device=u.device)

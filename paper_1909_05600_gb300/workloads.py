@@ -17,7 +17,7 @@ import math
 
 import numpy as np
 
-LAPLACE, HELMHOLTZ, LAPLACE_DL = 0, 1, 2
+LAPLACE, HELMHOLTZ, LAPLACE_DL, LAPLACE_GRAD = 0, 1, 2, 3
 
 
 def sphere_surface(n, seed):
@@ -101,6 +101,16 @@ def laplace_double_layer_sphere(n=20000, seed=1, eps=1e-3):
     u = np.random.default_rng(seed + 2000).standard_normal(n)
     w = np.full(n, 4.0 * math.pi / n)
     return Problem("laplace_dl_sphere_%d" % n, X, Y, u, w, LAPLACE_DL, 0.0, eps, meta={"normals": Y.copy()})
+
+
+def laplace_gradient_sphere(n=20000, seed=1, eps=1e-3):
+    """Gradient of the Laplace single layer (the MFIE kernel) on the unit sphere: X and Y
+    independent uniform draws, w = 4 pi / n, u ~ N(0, 1); three outputs per target."""
+    X = sphere_surface(n, seed)
+    Y = sphere_surface(n, seed + 1000)
+    u = np.random.default_rng(seed + 2000).standard_normal(n)
+    w = np.full(n, 4.0 * math.pi / n)
+    return Problem("laplace_grad_sphere_%d" % n, X, Y, u, w, LAPLACE_GRAD, 0.0, eps)
 
 
 def helmholtz_sphere(n=1_000_000, seed=1, eps=1e-3, ppw=10.0):
