@@ -404,49 +404,66 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
     return done != 0;
 }
 
-// The K loop runs over chunks of KT source nodes through an NS-stage shared-memory ring, with
-// the warps specialised: warps 1-7 copy the chunks (cp.async, 16-byte segments; operands are
-// pre-split into TF32 hi and lo parts and padded to rows of rkp floats, T_t to npad rows),
-// and one thread of warp 0 issues the MMAs.  Stage s has two mbarriers: full[s] completes
-// when every copying thread's segments of the chunk have landed (each thread waits for its
-// own copies, fences them for the tensor cores and arrives), empty[s] when the MMAs that
-// read the stage have completed (tcgen05.commit).  No block-wide barrier runs in the loop,
-// so up to NS chunks are queued ahead of the tensor cores.
-template <int KT, int NS>
+__device__ __forceinline__ void store_split(float *hi, float *lo, uint32_t o, float4 x) {
+    float4 h, l;
+    tf32_split(x.x, h.x, l.x);
+    tf32_split(x.y, h.y, l.y);
+    tf32_split(x.z, h.z, l.z);
+    tf32_split(x.w, h.w, l.w);
+    *reinterpret_cast<float4 *>(hi + o) = h;
+    *reinterpret_cast<float4 *>(lo + o) = l;
+}
+
+// Tiles of up to 256 pairs of one translation: two 128-pair halves, each with its own TMEM
+// accumulator, share every chunk of T_t.  The K loop runs over chunks of KT source nodes.
+// Warps 1-7 copy each chunk's rows (u~ of the pairs' source boxes, and T_t) as raw FP32
+// into an NR-deep ring with cp.async, each thread always the same 16-byte segments; once its
+// own segments have landed a thread splits them into TF32 hi and lo parts and stores them
+// into the NO-deep ring of MMA operands (K-major core matrices), then arrives on that
+// stage's "full" mbarrier.  One thread of warp 0 waits on "full", issues the MMAs
+// (hi*hi + hi*lo + lo*hi for each half) and commits them to the stage's "empty" mbarrier,
+// which the copying threads wait on before they overwrite the stage.  Operands are padded
+// (rows of rkp floats, T_t with npad rows), so every copy is a whole, aligned segment.
+constexpr int TC_P = 256;  // pairs per tensor-core tile
+
+template <int KT, int NR, int NO>
 __global__ void __launch_bounds__(256) k_lag_gemm_tc(const uint32_t *__restrict__ tile_t,
                                                      const uint32_t *__restrict__ tile_p0,
                                                      const uint32_t *__restrict__ bt_off,
                                                      const uint32_t *__restrict__ bt_src,
-                                                     const uint32_t *__restrict__ bt_tgt,
-                                                     const float *__restrict__ Th, const float *__restrict__ Tl,
+                                                     const uint32_t *__restrict__ bt_tgt, const float *__restrict__ Tp,
                                                      int r, int rkp, int npad, int tcols, int nrhs,
-                                                     const float *__restrict__ uh, const float *__restrict__ ul,
-                                                     float *__restrict__ vt, int *__restrict__ err) {
-    constexpr int C4 = KT / 4;       // 16-byte segments per operand row and chunk
-    constexpr int NP = 224;          // copying threads (warps 1-7)
-    constexpr int LAG = NS - 2;      // chunks a copying thread keeps in flight before arriving
+                                                     const float *__restrict__ up, float *__restrict__ vt,
+                                                     int *__restrict__ err) {
+    constexpr int C4 = KT / 4;  // 16-byte segments per row and chunk
+    constexpr int NP = 224;     // copying threads (warps 1-7)
     extern __shared__ __align__(1024) unsigned char smem[];
-    const int stage_f = 2 * TC_M * KT + 2 * npad * KT;  // floats per stage
-    float *st0 = reinterpret_cast<float *>(smem);
+    const int op_f = 2 * TC_P * KT + 2 * npad * KT;  // floats per operand stage: A hi, A lo, B hi, B lo
+    const int raw_f = (TC_P + npad) * KT;            // floats per raw stage: A rows, then B rows
+    float *op0 = reinterpret_cast<float *>(smem);
+    float *raw0 = op0 + (size_t)NO * op_f;
     __shared__ uint32_t s_tmem;
-    __shared__ __align__(8) uint64_t s_full[NS], s_empty[NS];
-    __shared__ uint32_t s_src[TC_M], s_tgt[TC_M];
+    __shared__ __align__(8) uint64_t s_full[NO], s_empty[NO];
+    __shared__ uint32_t s_src[TC_P], s_tgt[TC_P];
+    __shared__ int s_bad;
     int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     int t = tile_t[blockIdx.x], m = blockIdx.y;
     uint32_t p0 = tile_p0[blockIdx.x];
-    int np = (int)min((uint32_t)TC_M, bt_off[t + 1] - p0);
-    if (tid < TC_M) {
+    int np = (int)min((uint32_t)TC_P, bt_off[t + 1] - p0);
+    const int nh = np > 128 ? 2 : 1;  // halves with pairs
+    {
         // rows past the tile's pairs repeat its first pair; their TMEM lanes are not read
         s_src[tid] = bt_src[p0 + (tid < np ? tid : 0)];
         s_tgt[tid] = tid < np ? bt_tgt[p0 + tid] : 0u;
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&s_tmem)),
-                     "r"(tcols));
+                     "r"(2 * tcols));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
-        for (int i = 0; i < NS; ++i) {
+        s_bad = 0;
+        for (int i = 0; i < NO; ++i) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(&s_full[i])), "r"(NP));
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&s_empty[i])));
         }
@@ -456,132 +473,141 @@ __global__ void __launch_bounds__(256) k_lag_gemm_tc(const uint32_t *__restrict_
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     uint32_t tmem = s_tmem;
-    const size_t toff = (size_t)t * npad * rkp;
+    const float *Tt = Tp + (size_t)t * npad * rkp;
     const uint32_t lbo = 128, sbo = (KT / 4) * 128;
-    const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(npad >> 3) << 17) | ((uint32_t)(TC_M >> 4) << 24);
+    const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(npad >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
     const int nk = rkp / KT;
-    const int nseg = (TC_M + npad) * C4;  // segments per operand part (hi or lo) and chunk
+    const int nseg = (TC_P + npad) * C4;
     bool ok = true;
     if (warp >= 1) {
-        // ---- copying warps
+        // ---- copying warps: segments e = pt, pt + NP, ... of every chunk
         const int pt = tid - 32;
-        auto arrive_full = [&](int kc) {
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(&s_full[kc % NS])) : "memory");
-        };
-        for (int kn = 0; kn < nk; ++kn) {
-            const int b = kn % NS;
-            if (kn >= NS) ok = mbar_wait(&s_empty[b], (uint32_t)((kn / NS - 1) & 1)) && ok;  // MMAs of kn - NS done
-            float *sAh = st0 + (size_t)b * stage_f, *sAl = sAh + TC_M * KT, *sBh = sAl + TC_M * KT,
-                  *sBl = sBh + npad * KT;
-            const int k0 = kn * KT;
+        auto copy_chunk = [&](int kc) {
+            float *raw = raw0 + (size_t)(kc % NR) * raw_f;
+            const int k0 = kc * KT;
             for (int e = pt; e < nseg; e += NP) {
                 int row = e / C4, c = e - row * C4;
-                if (row < TC_M) {
-                    size_t g = ((size_t)s_src[row] * nrhs + m) * rkp + k0 + 4 * c;
-                    uint32_t o = kmajor_off(row, 4 * c, KT) >> 2;
-                    cp_async16(sAh + o, uh + g);
-                    cp_async16(sAl + o, ul + g);
-                } else {
-                    int i = row - TC_M;
-                    size_t g = toff + (size_t)i * rkp + k0 + 4 * c;
-                    uint32_t o = kmajor_off(i, 4 * c, KT) >> 2;
-                    cp_async16(sBh + o, Th + g);
-                    cp_async16(sBl + o, Tl + g);
-                }
+                const float *g = row < TC_P ? up + ((size_t)s_src[row] * nrhs + m) * rkp + k0 + 4 * c
+                                            : Tt + (size_t)(row - TC_P) * rkp + k0 + 4 * c;
+                cp_async16(raw + row * KT + 4 * c, g);
             }
+        };
+        for (int kc = 0; kc < NR - 1; ++kc) {
+            if (kc < nk) copy_chunk(kc);
             asm volatile("cp.async.commit_group;" ::: "memory");
-            if (kn >= LAG) {
-                asm volatile("cp.async.wait_group %0;" ::"n"(LAG) : "memory");  // chunk kn - LAG landed
-                arrive_full(kn - LAG);
-            }
         }
-        asm volatile("cp.async.wait_all;" ::: "memory");
-        for (int kc = max(0, nk - LAG); kc < nk; ++kc) arrive_full(kc);
+        for (int kn = 0; kn < nk; ++kn) {
+            if (kn + NR - 1 < nk) copy_chunk(kn + NR - 1);
+            asm volatile("cp.async.commit_group;" ::: "memory");
+            asm volatile("cp.async.wait_group %0;" ::"n"(NR - 1) : "memory");  // chunk kn's segments landed
+            const int b = kn % NO;
+            if (kn >= NO) ok = mbar_wait(&s_empty[b], (uint32_t)((kn / NO - 1) & 1)) && ok;  // MMAs of kn - NO done
+            const float *raw = raw0 + (size_t)(kn % NR) * raw_f;
+            float *sAh = op0 + (size_t)b * op_f, *sAl = sAh + TC_P * KT, *sBh = sAl + TC_P * KT,
+                  *sBl = sBh + npad * KT;
+            for (int e = pt; e < nseg; e += NP) {
+                int row = e / C4, c = e - row * C4;
+                float4 x = *reinterpret_cast<const float4 *>(raw + row * KT + 4 * c);
+                if (row < TC_P)
+                    store_split(sAh, sAl, kmajor_off(row, 4 * c, KT) >> 2, x);
+                else
+                    store_split(sBh, sBl, kmajor_off(row - TC_P, 4 * c, KT) >> 2, x);
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(&s_full[b])) : "memory");
+        }
     } else if (lane == 0) {
         // ---- MMA thread
         for (int kc = 0; kc < nk; ++kc) {
-            const int b = kc % NS;
-            ok = mbar_wait(&s_full[b], (uint32_t)((kc / NS) & 1)) && ok;
+            const int b = kc % NO;
+            ok = mbar_wait(&s_full[b], (uint32_t)((kc / NO) & 1)) && ok;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            float *sAh = st0 + (size_t)b * stage_f, *sAl = sAh + TC_M * KT, *sBh = sAl + TC_M * KT,
+            float *sAh = op0 + (size_t)b * op_f, *sAl = sAh + TC_P * KT, *sBh = sAl + TC_P * KT,
                   *sBl = sBh + npad * KT;
+            for (int h = 0; h < nh; ++h) {
+                uint32_t d = tmem + (uint32_t)(h * tcols);
+                uint32_t ao = smem_addr(sAh + h * 128 * KT), alo = smem_addr(sAl + h * 128 * KT);
 #pragma unroll
-            for (int ks = 0; ks < KT / 8; ++ks) {
-                uint64_t ah = umma_desc(smem_addr(sAh) + ks * 256, lbo, sbo);
-                uint64_t al = umma_desc(smem_addr(sAl) + ks * 256, lbo, sbo);
-                uint64_t bh = umma_desc(smem_addr(sBh) + ks * 256, lbo, sbo);
-                uint64_t bl = umma_desc(smem_addr(sBl) + ks * 256, lbo, sbo);
-                uint32_t acc0 = (kc > 0 || ks > 0) ? 1u : 0u;
-                asm volatile(
-                    "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-                    "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-                    "l"(ah), "l"(bh), "r"(idesc), "r"(acc0));
-                asm volatile("tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, 1;\n" ::"r"(tmem), "l"(ah), "l"(bl),
-                             "r"(idesc));
-                asm volatile("tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, 1;\n" ::"r"(tmem), "l"(al), "l"(bh),
-                             "r"(idesc));
+                for (int ks = 0; ks < KT / 8; ++ks) {
+                    uint64_t ah = umma_desc(ao + ks * 256, lbo, sbo);
+                    uint64_t al = umma_desc(alo + ks * 256, lbo, sbo);
+                    uint64_t bh = umma_desc(smem_addr(sBh) + ks * 256, lbo, sbo);
+                    uint64_t bl = umma_desc(smem_addr(sBl) + ks * 256, lbo, sbo);
+                    uint32_t acc0 = (kc > 0 || ks > 0) ? 1u : 0u;
+                    asm volatile(
+                        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+                        "l"(ah), "l"(bh), "r"(idesc), "r"(acc0));
+                    asm volatile("tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, 1;\n" ::"r"(d), "l"(ah),
+                                 "l"(bl), "r"(idesc));
+                    asm volatile("tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, 1;\n" ::"r"(d), "l"(al),
+                                 "l"(bh), "r"(idesc));
+                }
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                              smem_addr(&s_empty[b]))
                          : "memory");
         }
         // the last chunk's MMAs complete after all earlier ones
-        ok = mbar_wait(&s_empty[(nk - 1) % NS], (uint32_t)(((nk - 1) / NS) & 1)) && ok;
+        ok = mbar_wait(&s_empty[(nk - 1) % NO], (uint32_t)(((nk - 1) / NO) & 1)) && ok;
     }
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (!ok) atomicOr(err, 1);
-    __shared__ int s_bad;
-    if (tid == 0) s_bad = 0;
-    __syncthreads();
+    if (warp >= 1) asm volatile("cp.async.wait_all;" ::: "memory");
     if (!ok) s_bad = 1;
     __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     ok = s_bad == 0;
-    // epilogue: warps 0-3 hold TMEM lanes 32w..32w+31 = pairs; columns = target nodes i.
-    // Warps 4-7 (the second warpgroup) take the odd column chunks of the same lanes.
-    int quarter = warp & 3;
-    int p = quarter * 32 + lane;
-    float *dst = vt + ((size_t)s_tgt[p] * nrhs + m) * r;
-    for (int c0 = (warp >> 2) * 8; c0 < npad; c0 += 16) {
-        uint32_t v[8];
-        uint32_t addr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c0;
-        asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                     : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
-                     : "r"(addr));
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        if (ok && p < np) {
-            if ((r & 3) == 0 && c0 + 8 <= r) {
-                atomicAdd(reinterpret_cast<float4 *>(dst + c0),
-                          make_float4(__uint_as_float(v[0]), __uint_as_float(v[1]), __uint_as_float(v[2]), __uint_as_float(v[3])));
-                atomicAdd(reinterpret_cast<float4 *>(dst + c0 + 4),
-                          make_float4(__uint_as_float(v[4]), __uint_as_float(v[5]), __uint_as_float(v[6]), __uint_as_float(v[7])));
-            } else {
+    if (!ok && tid == 0) atomicOr(err, 1);
+    // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 of half w / 4; columns = target nodes
+    const int h = warp >> 2, quarter = warp & 3;
+    const int p = h * 128 + quarter * 32 + lane;
+    if (h < nh) {
+        float *dst = vt + ((size_t)s_tgt[p] * nrhs + m) * r;
+        for (int c0 = 0; c0 < npad; c0 += 8) {
+            uint32_t v[8];
+            uint32_t addr = tmem + (uint32_t)(h * tcols) + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c0;
+            asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                         : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+                         : "r"(addr));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            if (ok && p < np) {
+                if ((r & 3) == 0 && c0 + 8 <= r) {
+                    atomicAdd(reinterpret_cast<float4 *>(dst + c0),
+                              make_float4(__uint_as_float(v[0]), __uint_as_float(v[1]), __uint_as_float(v[2]),
+                                          __uint_as_float(v[3])));
+                    atomicAdd(reinterpret_cast<float4 *>(dst + c0 + 4),
+                              make_float4(__uint_as_float(v[4]), __uint_as_float(v[5]), __uint_as_float(v[6]),
+                                          __uint_as_float(v[7])));
+                } else {
 #pragma unroll
-                for (int q = 0; q < 8; ++q)
-                    if (c0 + q < r) atomicAdd(dst + c0 + q, __uint_as_float(v[q]));
+                    for (int q = 0; q < 8; ++q)
+                        if (c0 + q < r) atomicAdd(dst + c0 + q, __uint_as_float(v[q]));
+                }
             }
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tcols));
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * tcols));
 }
 
-// TF32 hi / lo parts of nmat row-major matrices (rows x cols), written with rows_pad rows
-// of cols_pad floats each (padding zero).
+// nmat row-major matrices (rows x cols) copied with rows_pad rows of cols_pad floats each
+// (padding zero); with lo != nullptr the TF32 hi part goes to out and the lo part to lo.
 __global__ void k_split_pad(const float *__restrict__ src, int64_t nmat, int rows, int cols, int rows_pad,
-                            int cols_pad, float *__restrict__ hi, float *__restrict__ lo) {
+                            int cols_pad, float *__restrict__ out, float *__restrict__ lo) {
     int64_t n = nmat * rows_pad * (int64_t)cols_pad;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         int64_t mat = i / ((int64_t)rows_pad * cols_pad);
         int rem = (int)(i - mat * rows_pad * (int64_t)cols_pad);
         int row = rem / cols_pad, col = rem - row * cols_pad;
         float x = row < rows && col < cols ? src[(mat * rows + row) * (int64_t)cols + col] : 0.f;
-        float h, l;
-        tf32_split(x, h, l);
-        hi[i] = h;
-        lo[i] = l;
+        if (lo) {
+            float h, l;
+            tf32_split(x, h, l);
+            out[i] = h;
+            lo[i] = l;
+        } else {
+            out[i] = x;
+        }
     }
 }
 
@@ -901,7 +927,7 @@ static void lagrange_points_r1(const ffm_plan_s *p, const FarLevel &F, const Lev
 }
 
 void split_pad(const float *src, int64_t nmat, int rows, int cols, int rows_pad, int cols_pad, float *hi, float *lo,
-               cudaStream_t s) {
+               cudaStream_t s) {  // lo == nullptr: padded copy into hi
     int64_t n = nmat * rows_pad * (int64_t)cols_pad;
     unsigned g = (unsigned)std::min<int64_t>((n + 255) / 256, 152 * 16);
     FFM_LAUNCH(k_split_pad, g, 256, 0, s, src, nmat, rows, cols, rows_pad, cols_pad, hi, lo);
@@ -940,14 +966,14 @@ void far_lagrange(const ffm_plan_s *p, int l, const void *q, int nrhs, float2 *a
         const int ncomp = p->kind == FFM_LAPLACE_GRAD ? 3 : 1;
         const size_t tblk = (size_t)F.n_trans * r * rk;
         const size_t vblk = (size_t)r * nrhs * p->bx[l].nb;
-        float *uh = nullptr, *ul = nullptr;
-        const bool use_tc = !(F.ts_ok && F.Tsp && F.tune_tc == 2) && npad <= 256 && F.tc_tiles > 0 &&
+        float *upad = nullptr;
+        const bool use_tc = !(F.ts_ok && F.Tsp && F.tune_tc == 2) && npad <= 224 && F.tc_tiles > 0 &&
                             F.tune_tc != 0 && F.Tsh;
         if (use_tc) {
+            // u~ with rows padded to rkp floats (whole, aligned 16-byte segments for cp.async)
             int64_t nrow = (int64_t)p->by[l].nb * nrhs;
-            uh = tmp.get<float>((size_t)nrow * F.rkp);
-            ul = tmp.get<float>((size_t)nrow * F.rkp);
-            split_pad((const float *)ut, 1, (int)nrow, rk, (int)nrow, F.rkp, uh, ul, s);
+            upad = tmp.get<float>((size_t)nrow * F.rkp);
+            split_pad((const float *)ut, 1, (int)nrow, rk, (int)nrow, F.rkp, upad, nullptr, s);
         }
         for (int d = 0; d < ncomp; ++d) {
             const float *Td = F.T + d * tblk;
@@ -963,34 +989,33 @@ void far_lagrange(const ffm_plan_s *p, int l, const void *q, int nrhs, float2 *a
             FFM_LAUNCH(k_lag_gemm_ts, gts, 2 * TS_M, smem, s, F.tgt, F.n_tgt, F.adm_off, F.adm_src, F.adm_t, F.n_trans,
                        F.Tsp, r, nrhs, (const float *)ut, vtd, p->dev_err);
         } else if (use_tc) {
-            // tensor cores: 128-pair tiles, K chunks of KT source nodes through NS stages, operands
-            // pre-split into TF32 hi and lo parts with rows padded to rkp floats
-            constexpr int KT = 16, NS = 4;
+            // tensor cores: 256-pair tiles, K chunks of KT source nodes, NR raw and NO operand stages
+            constexpr int KT = 16, NR = 3, NO = 2;
             int rkp = F.rkp;
             int tcols = 32;
             while (tcols < npad) tcols <<= 1;
-            size_t smem = NS * (size_t)(2 * TC_M * KT + 2 * npad * KT) * sizeof(float);
+            auto smem_of = [](int np_) {
+                return (size_t)NO * (2 * TC_P * KT + 2 * np_ * KT) * sizeof(float) +
+                       (size_t)NR * (TC_P + np_) * KT * sizeof(float);
+            };
             static bool attr = false;
             if (!attr) {
-                FFM_CUDA(cudaFuncSetAttribute(k_lag_gemm_tc<KT, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              NS * (int)(2 * TC_M * KT + 2 * 256 * KT) * (int)sizeof(float)));
+                FFM_CUDA(cudaFuncSetAttribute(k_lag_gemm_tc<KT, NR, NO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)smem_of(224)));
                 attr = true;
             }
-            size_t tsz = (size_t)ncomp * F.n_trans * npad * rkp, dsz = (size_t)F.n_trans * npad * rkp;
+            size_t dsz = (size_t)F.n_trans * npad * rkp;
             dim3 gtc((unsigned)F.tc_tiles, nrhs);
-            FFM_LAUNCH((k_lag_gemm_tc<KT, NS>), gtc, 256, smem, s, F.tc_tile_t, F.tc_tile_p0, F.bt_off, F.bt_src,
-                       F.bt_tgt, (const float *)(F.Tsh + d * dsz), (const float *)(F.Tsh + tsz + d * dsz), r, rkp,
-                       npad, tcols, nrhs, (const float *)uh, (const float *)ul, vtd, p->dev_err);
+            FFM_LAUNCH((k_lag_gemm_tc<KT, NR, NO>), gtc, 256, smem_of(npad), s, F.tc_tile_t, F.tc_tile_p0, F.bt_off,
+                       F.bt_src, F.bt_tgt, (const float *)(F.Tsh + d * dsz), r, rkp, npad, tcols, nrhs,
+                       (const float *)upad, vtd, p->dev_err);
         } else {
             FFM_LAUNCH(k_lag_gemm<false>, gg, LG_T, 0, s, F.tile_t, F.tile_p0, F.bt_off, F.bt_src, F.bt_tgt, Td, r,
                        rk, nrhs, (const float *)ut, vtd);
         }
             lagrange_points_r1<false>(p, F, AX, cb, false, vtd, nrhs, accf + (size_t)d * nrhs * p->nx, s);
         }
-        if (uh) {
-            tmp.drop(ul);
-            tmp.drop(uh);
-        }
+        if (upad) tmp.drop(upad);
     }
 }
 

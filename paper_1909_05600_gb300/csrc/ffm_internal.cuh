@@ -166,9 +166,9 @@ struct FarLevel {
                                     // partners sorted by translation within each target)
     float *Tsp = nullptr;           // target-stationary transfer (r <= 64): T_t split into TF32
                                     // hi and lo, 64 x 64 each, in the K-major core-matrix layout
-    float *Tsh = nullptr;           // tensor-core transfer: T_t split into TF32 hi (first n_trans *
-    int rkp = 0;                    // npad * rkp floats) and lo parts, npad rows of rkp floats
-    int64_t tc_tiles = 0;           // 128-pair tiles for the tensor-core transfer
+    float *Tsh = nullptr;           // tensor-core transfer: T_t padded to npad rows of rkp floats
+    int rkp = 0;                    // (per component block for the gradient)
+    int64_t tc_tiles = 0;           // 256-pair tiles for the tensor-core transfer
     uint32_t *tc_tile_t = nullptr;
     uint32_t *tc_tile_p0 = nullptr;
     // plane waves: arithmetic (FFM_PREC_F32 / _F32C with FP32 tables, FFM_PREC_F64 with
@@ -284,7 +284,8 @@ int r1_rule(int kind, double eps);
 // Lagrange levels add their contributions in FP32 into accf (float2 per target and RHS);
 // the apply adds accf into the FP64 accumulators once, at the end.
 void far_lagrange(const ffm_plan_s *p, int l, const void *q, int nrhs, float2 *accf, Alloc &tmp, cudaStream_t s);
-// TF32 hi / lo parts of nmat row-major matrices, written with padded rows and columns (zeros)
+// nmat row-major matrices written with padded rows and columns (zeros): as TF32 hi / lo parts,
+// or (lo == nullptr) as a plain copy into hi
 void split_pad(const float *src, int64_t nmat, int rows, int cols, int rows_pad, int cols_pad, float *hi, float *lo,
                cudaStream_t s);
 // true for the kinds whose transfer operators are the real Laplace G (Laplace, double layer)

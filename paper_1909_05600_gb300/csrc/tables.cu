@@ -356,15 +356,15 @@ void build_tables(ffm_plan_s *p, int l, TableJob &tj) {
         for (int a = 0; a < F.r1; ++a) g.hnode[a] = (float)(0.5 * dl * std::cos((2.0 * a + 1.0) * PI / (2.0 * F.r1)));
         FFM_LAUNCH(k_lag_table, F.n_trans, 256, 0, s, F.trans_m, F.n_trans, g, F.T);
         int rk = p->kind == FFM_LAPLACE_DL ? 3 * r : r, npad = (r + 15) / 16 * 16;
-        if (!cplx && npad <= 256) {
-            // the tensor-core transfer's operand: T_t in TF32 hi and lo parts, npad rows of rkp
-            // (a multiple of its 16-node K chunks) floats, padding zero; the gradient's three
-            // component blocks one after another
+        if (!cplx && npad <= 224) {
+            // the tensor-core transfer's operand: T_t with npad rows of rkp (a multiple of its
+            // 16-node K chunks) floats, padding zero; the gradient's three component blocks one
+            // after another
             int nblk = p->kind == FFM_LAPLACE_GRAD ? 3 : 1;
             F.rkp = (rk + 15) / 16 * 16;
             size_t tsz = (size_t)nblk * F.n_trans * npad * F.rkp;
-            F.Tsh = p->mem.get<float>(2 * tsz);
-            split_pad(F.T, (int64_t)nblk * F.n_trans, r, rk, npad, F.rkp, F.Tsh, F.Tsh + tsz, s);
+            F.Tsh = p->mem.get<float>(tsz);
+            split_pad(F.T, (int64_t)nblk * F.n_trans, r, rk, npad, F.rkp, F.Tsh, nullptr, s);
         }
         return;
     }

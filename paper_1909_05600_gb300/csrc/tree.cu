@@ -1047,7 +1047,7 @@ static void finish_far_level(ffm_plan_s *p, int l, uint32_t *aa, uint32_t *ab, i
                 tt.push_back((uint32_t)t);
                 tp.push_back(q0);
             }
-            for (uint32_t q0 = hoff[t]; q0 < hoff[t + 1]; q0 += 128) {
+            for (uint32_t q0 = hoff[t]; q0 < hoff[t + 1]; q0 += 256) {  // tensor-core tiles
                 ct.push_back((uint32_t)t);
                 cp.push_back(q0);
             }
