@@ -25,6 +25,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <map>
 #include <mutex>
 #include <vector>
 
@@ -588,7 +589,23 @@ void tile_lists(ffm_plan_s *p, int l, int own, int64_t *n_tiles, uint32_t **ids_
     FFM_CUDA(cudaStreamSynchronize(s));  // the host vectors feed the copies above
 }
 
-cufftHandle make_fft(int n2, int64_t batch, size_t *work) {
+// cuFFT plans depend only on (n2, batch) and the device; they are made once per process and
+// shared by every FFM plan (use is serialised by g_fft_mu, each call sets its own stream and
+// work area).  They live until the process exits.
+struct FftKey {
+    int dev, n2;
+    int64_t batch;
+    bool operator<(const FftKey &o) const {
+        return dev != o.dev ? dev < o.dev : n2 != o.n2 ? n2 < o.n2 : batch < o.batch;
+    }
+};
+struct FftPlan {
+    cufftHandle h;
+    size_t work;
+};
+std::map<FftKey, FftPlan> g_fft_cache;
+
+cufftHandle make_fft_uncached(int n2, int64_t batch, size_t *work) {
     cufftHandle h;
     check_fft(cufftCreate(&h), "cufftCreate");
     check_fft(cufftSetAutoAllocation(h, 0), "cufftSetAutoAllocation");
@@ -597,6 +614,21 @@ cufftHandle make_fft(int n2, int64_t batch, size_t *work) {
     check_fft(cufftMakePlanMany64(h, 3, n, nullptr, 1, dist, nullptr, 1, dist, CUFFT_C2C, (long long)batch, work),
               "cufftMakePlanMany64");
     return h;
+}
+
+cufftHandle make_fft(int n2, int64_t batch, size_t *work) {
+    int dev = 0;
+    FFM_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(g_fft_mu);
+    FftKey key{dev, n2, batch};
+    auto it = g_fft_cache.find(key);
+    if (it == g_fft_cache.end()) {
+        FftPlan fp;
+        fp.h = make_fft_uncached(n2, batch, &fp.work);
+        it = g_fft_cache.emplace(key, fp).first;
+    }
+    *work = it->second.work;
+    return it->second.h;
 }
 
 // one transform per right-hand side, each over all boxes of the level, in place
@@ -796,9 +828,7 @@ void nufft_backward(const ffm_plan_s *p, int l, const float2 *vt, int nrhs, doub
 void nufft_release(ffm_plan_s *p) {
     for (int l = 0; l <= LMAX; ++l) {
         NuLevel &N = p->far[l].nu;
-        if (N.has_fft) {
-            cufftDestroy(N.fft_src);
-            cufftDestroy(N.fft_tgt);
+        if (N.has_fft) {  // the cuFFT plans belong to the process-wide cache
             N.has_fft = false;
         }
     }
