@@ -579,3 +579,88 @@ def test_gradient_ffm_within_eps(eps, rad):
     ref = O.direct_grad(X, Y, u, w=w)[:, 0, :]
     assert O.rel_l2(v, ref) < eps
     assert O.r1_rule(O.LAPLACE_GRAD, eps) == O.r1_rule(O.LAPLACE_DL, eps)
+
+
+# ------------------------------------------ boundary-element wrapper (Sec. 4.2, S = L*^T G L)
+
+def _polar_integrals(P, x, n=400):
+    """V0 = int_T dA / |y - x| and Vv = int_T (y - x) / |y - x| dA by quadrature over the polar
+    angle about x: along direction theta the triangle ends at rho(theta), so V0 = int rho dtheta
+    and Vv = int rho dir(theta) dtheta."""
+    nrm = np.cross(P[1] - P[0], P[2] - P[0])
+    nrm /= np.linalg.norm(nrm)
+    e1 = (P[0] - x) / np.linalg.norm(P[0] - x)
+    e2 = np.cross(nrm, e1)
+    ang = [np.arctan2(np.dot(p - x, e2), np.dot(p - x, e1)) for p in P]
+    V0, Vv = 0.0, np.zeros(3)
+    t, w = np.polynomial.legendre.leggauss(n)
+    for i in range(3):
+        a, b = P[i], P[(i + 1) % 3]
+        th0, th1 = ang[i], ang[(i + 1) % 3]
+        dth = (th1 - th0 + np.pi) % (2 * np.pi) - np.pi
+        for tk, wk in zip(t, w):
+            th = th0 + 0.5 * (tk + 1) * dth
+            d = np.cos(th) * e1 + np.sin(th) * e2
+            # the ray x + r d meets the edge line a + s (b - a)
+            M = np.stack([d, a - b], 1)
+            r = np.linalg.lstsq(M, a - x, rcond=None)[0][0]
+            V0 += 0.5 * wk * abs(dth) * r
+            Vv += 0.5 * wk * abs(dth) * r * d
+    return V0, Vv
+
+
+def test_bem_plane_integrals_match_polar_quadrature():
+    """Closed-form in-plane potential of a constant and of a linear density on a flat
+    triangle against quadrature over the polar angle (a separate route)."""
+    from oracle import bem as B
+    rng = np.random.default_rng(41)
+    for _ in range(4):
+        P = rng.standard_normal((3, 3))
+        lam = rng.dirichlet([2, 2, 2])
+        x = lam @ P
+        V0, Vv = B.plane_integrals(P, x)
+        R0, Rv = _polar_integrals(P, x)
+        assert abs(V0 - R0) < 1e-9 * abs(R0)
+        assert np.max(np.abs(Vv - Rv)) < 1e-9 * np.linalg.norm(Rv)
+
+
+def test_bem_self_element_is_symmetric_and_converged():
+    from oracle import bem as B
+    P = np.random.default_rng(43).standard_normal((2, 3, 3))
+    A = B.self_element(P, 32)
+    A2 = B.self_element(P, 48)
+    assert np.max(np.abs(A - np.swapaxes(A, 1, 2))) < 1e-7 * np.max(np.abs(A))
+    assert np.max(np.abs(A - A2)) < 2e-6 * np.max(np.abs(A))
+
+
+def test_bem_quadrature_integrates_piecewise_linear_functions():
+    from oracle import bem as B
+    V, F = W.icosphere(2)
+    X, w, L = B.quadrature(V, F)
+    u = np.random.default_rng(2).standard_normal(len(V))
+    P = V[F]
+    area = 0.5 * np.linalg.norm(np.cross(P[:, 1] - P[:, 0], P[:, 2] - P[:, 0]), axis=1)
+    exact = np.sum(area * u[F].mean(axis=1))  # integral of a linear function = area x vertex mean
+    assert abs(np.dot(w, L @ u) - exact) < 1e-12 * np.sum(area * np.abs(u[F]).mean(axis=1))
+    assert np.allclose(L.sum(axis=1), 1.0)
+
+
+def test_bem_single_layer_of_the_sphere_has_unit_density():
+    """The unit sphere's single layer maps the constant 1 to 1 (charged-sphere potential), so
+    S sigma = (L*)^T 1 has sigma = 1 up to the discretisation error, which shrinks with h."""
+    from oracle import bem as B
+    errs = []
+    for lev in (2, 3):
+        V, F = W.icosphere(lev)
+        X, w, L = B.quadrature(V, F)
+        sig = np.linalg.solve(B.dense_matrix(V, F), L.T @ w)
+        errs.append((abs(sig.mean() - 1), np.max(np.abs(sig - 1))))
+    assert errs[1][0] < errs[0][0] and errs[1][0] < 5e-3 and errs[1][1] < 4e-2
+
+
+def test_bem_ffm_product_matches_the_dense_matrix():
+    from oracle import bem as B
+    V, F = W.icosphere(2)
+    u = np.random.default_rng(4).standard_normal(len(V))
+    S = B.dense_matrix(V, F)
+    assert O.rel_l2(B.apply_ffm(V, F, u, 1e-4), S @ u) < 1e-4
