@@ -271,6 +271,40 @@ int ffm_profile_read(char *names, uint64_t *launches, double *ms, int cap);
  * Errors: FFM_EINVAL (NULL or host pointers, bad dtype, n out of range), FFM_ECUDA. */
 ffm_status ffm_morton_order_noalloc(const void *X, ffm_dtype xdt, int64_t n, uint32_t *perm_out, void *stream);
 
+/* ---- Boundary-element wrapper (Sec. 4.2): the Galerkin matrix of a boundary integral operator
+ * written as S = (Lambda*)^T (G W) Lambda + C, where Lambda carries the basis functions to the
+ * quadrature nodes, G W is one FFM product between the nodes, (Lambda*)^T brings the weighted
+ * node values back to the test functions, and C is the sparse matrix that replaces the
+ * singular integrals the node quadrature misses.  This version: the Laplace single layer
+ * G = 1/(4 pi |x - y|) with P1 (nodal, piecewise-linear) functions on a flat-triangle mesh,
+ * 3 quadrature nodes per triangle (barycentric (2/3, 1/6, 1/6) and permutations, weights
+ * area / 3), and C holding each triangle's exact self-interaction (closed-form in-plane
+ * potential of a linear density, collapsed 32 x 32 Gauss outer rule) minus its node
+ * quadrature.  Interactions between distinct triangles use the node quadrature. */
+typedef struct ffm_bem_s ffm_bem_t;
+
+/* Build the operator for a mesh.
+ *   vertices : nv x 3 row-major FP64, host or device; copied.
+ *   triangles: nt x 3 int32 vertex indices (0-based), host or device; copied.
+ *   kernel   : FFM_LAPLACE (others return FFM_EUNSUPPORTED); k ignored.
+ *   eps      : accuracy of the FFM products; opts as for ffm_plan (its weights are replaced
+ *              by the quadrature weights).
+ * Errors: FFM_EINVAL (NULL, empty mesh, index out of range), FFM_ENOMEM, FFM_ECUDA. */
+ffm_status ffm_bem_create(const double *vertices, int64_t nv, const int *triangles, int64_t nt, ffm_kernel kernel,
+                          double k, double eps, const ffm_opts *opts, void *stream, ffm_bem_t **out);
+/* v = S u for nv vertex values (FP64, host or device; v overwritten). */
+ffm_status ffm_bem_apply(ffm_bem_t *bem, const double *u, double *v, void *stream);
+/* Solve S x = rhs by restarted GMRES (restart vectors, at most maxit products, stop at
+ * ||rhs - S x|| <= tol ||rhs|| by the GMRES residual estimate); x (FP64, host or device)
+ * receives the solution, *iters the products used, *relres the final relative residual.
+ * x starts from 0. */
+ffm_status ffm_bem_solve(ffm_bem_t *bem, const double *rhs, double *x, double tol, int restart, int maxit,
+                         int *iters, double *relres, void *stream);
+/* FFM products of the last solve (Arnoldi steps plus restarts). */
+ffm_status ffm_bem_products(const ffm_bem_t *bem, int64_t *products);
+/* NULL-safe; synchronises the operator's stream first. */
+void ffm_bem_destroy(ffm_bem_t *bem);
+
 /* Human-readable status name, and the message of the last failure in this thread. */
 const char *ffm_status_str(ffm_status s);
 const char *ffm_last_error(void);

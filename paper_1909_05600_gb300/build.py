@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libffm_gb300.so")
 SOURCES = ["tree.cu", "tables.cu", "farfield.cu", "nearfield.cu", "ffm_api.cu", "noalloc.cu", "autotune.cu",
-           "nufft.cu"]
+           "nufft.cu", "bem.cu"]
 ARCH = os.environ.get("FFM_CUDA_ARCH", "103a")
 
 NVCC_FLAGS = ["-gencode", "arch=compute_%s,code=sm_%s" % (ARCH, ARCH), "-O3", "-lineinfo", "-std=c++17",

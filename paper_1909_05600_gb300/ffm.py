@@ -35,7 +35,8 @@ STATUS = {0: "FFM_OK", 1: "FFM_EINVAL", 2: "FFM_ENOMEM", 3: "FFM_ECUDA", 4: "FFM
 ABI_SYMBOLS = ("ffm_plan", "ffm_apply", "ffm_destroy", "ffm_plan_bytes", "ffm_plan_info", "ffm_plan_export",
                "ffm_launch_count", "ffm_profile_enable", "ffm_profile_reset", "ffm_profile_read", "ffm_status_str",
                "ffm_last_error", "ffm_morton_order_noalloc", "ffm_graph_create", "ffm_graph_launch",
-               "ffm_graph_kernels", "ffm_graph_destroy", "ffm_autotune")
+               "ffm_graph_kernels", "ffm_graph_destroy", "ffm_autotune", "ffm_bem_create", "ffm_bem_apply",
+               "ffm_bem_solve", "ffm_bem_products", "ffm_bem_destroy")
 
 
 class FFMError(RuntimeError):
@@ -122,6 +123,18 @@ def lib():
         L.ffm_graph_destroy.restype = None
         L.ffm_autotune.argtypes = [vp, C.c_int, C.c_char_p, vp]
         L.ffm_autotune.restype = C.c_int
+        L.ffm_bem_create.argtypes = [vp, i64, vp, i64, C.c_int, C.c_double, C.c_double, C.POINTER(Opts), vp,
+                                     C.POINTER(vp)]
+        L.ffm_bem_create.restype = C.c_int
+        L.ffm_bem_apply.argtypes = [vp, vp, vp, vp]
+        L.ffm_bem_apply.restype = C.c_int
+        L.ffm_bem_solve.argtypes = [vp, vp, vp, C.c_double, C.c_int, C.c_int, C.POINTER(C.c_int),
+                                    C.POINTER(C.c_double), vp]
+        L.ffm_bem_solve.restype = C.c_int
+        L.ffm_bem_products.argtypes = [vp, C.POINTER(C.c_int64)]
+        L.ffm_bem_products.restype = C.c_int
+        L.ffm_bem_destroy.argtypes = [vp]
+        L.ffm_bem_destroy.restype = None
         _lib = L
     return _lib
 
@@ -342,3 +355,57 @@ class Plan:
         if n.value:
             _check(lib().ffm_plan_export(self._h, what, level, out.ctypes.data, C.byref(n)))
         return out
+
+
+class Bem:
+    """Boundary-element operator S = (Lambda*)^T (G W) Lambda + C of the Laplace single layer on
+    P1 functions over a triangle mesh (ffm_bem_create / ffm_bem_apply / ffm_bem_solve /
+    ffm_bem_destroy).  vertices (nv, 3) float64, triangles (nt, 3) int32; vectors are float64
+    (nv,) arrays or tensors."""
+
+    def __init__(self, vertices, triangles, eps=1e-3, stream=None):
+        self._h = None
+        self.nv = int(vertices.shape[0])
+        self.stream = _stream_of(vertices, triangles, stream=stream)
+        h = C.c_void_p()
+        _check(lib().ffm_bem_create(_ptr(vertices), self.nv, _ptr(triangles), int(triangles.shape[0]), LAPLACE, 0.0,
+                                    float(eps), None, self.stream, C.byref(h)))
+        self._h = h
+
+    def apply(self, u, out=None):
+        if out is None:
+            out = torch.empty_like(u) if torch is not None and isinstance(u, torch.Tensor) else np.empty_like(u)
+        _check(lib().ffm_bem_apply(self._h, _ptr(u), _ptr(out), self.stream))
+        return out
+
+    def solve(self, rhs, tol=1e-8, restart=30, maxit=300, out=None):
+        """GMRES for S x = rhs: returns (x, iterations, relative residual)."""
+        if out is None:
+            out = torch.empty_like(rhs) if torch is not None and isinstance(rhs, torch.Tensor) else np.empty_like(rhs)
+        it = C.c_int()
+        rr = C.c_double()
+        _check(lib().ffm_bem_solve(self._h, _ptr(rhs), _ptr(out), float(tol), int(restart), int(maxit), C.byref(it),
+                                   C.byref(rr), self.stream))
+        return out, it.value, rr.value
+
+    def products(self):
+        n = C.c_int64()
+        _check(lib().ffm_bem_products(self._h, C.byref(n)))
+        return n.value
+
+    def close(self):
+        if self._h:
+            lib().ffm_bem_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
