@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--serving", action="store_true",
                     help="serving stream: Poisson arrivals of mixed requests, p50/p99 latency and throughput")
     ap.add_argument("--requests", type=int, default=500)
+    ap.add_argument("--bem", type=int, default=0, metavar="LEVEL",
+                    help="boundary-element solve on an icosphere of this refinement level (GMRES over FFM products)")
     ap.add_argument("--workers", type=int, default=4)
     ap.add_argument("--cpu-targets", type=int, default=4096)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -393,6 +395,59 @@ def run_serving(args):
     print(json.dumps(line), flush=True)
 
 
+def run_bem(args):
+    """Boundary-element solve: the Laplace single layer's Galerkin system on the unit sphere
+    (P1, icosphere of level args.bem) with the Galerkin right-hand side of the constant 1, whose
+    solution is the unit density.  A step is ffm_bem_create + ffm_bem_solve + ffm_bem_destroy,
+    timed with CUDA events; the density's deviation from 1 is the accuracy."""
+    import torch
+    from paper_1909_05600_gb300 import build, ffm, workloads as W
+    build.build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    V, F = W.icosphere(args.bem)
+    P = V[F]
+    area = 0.5 * np.linalg.norm(np.cross(P[:, 1] - P[:, 0], P[:, 2] - P[:, 0]), axis=1)
+    rhs = np.zeros(len(V))
+    np.add.at(rhs, F.ravel(), np.repeat(area / 3.0, 3))  # integral of each hat function
+    tV, tF, trhs = (torch.as_tensor(a, device=dev) for a in (V, F, rhs))
+    stream = torch.cuda.current_stream(dev)
+    eps, tol = 1e-4, 1e-5
+
+    def step():
+        with ffm.Bem(tV, tF, eps=eps) as bem:
+            x, it, rr = bem.solve(trhs, tol=tol, restart=100, maxit=1000)
+            return x, it, rr, bem.products()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = Clocks(0)
+    clocks.start()
+    l0 = ffm.launch_count()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        x, it, rr, prods = step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    launches = ffm.launch_count() - l0
+    t = ev0.elapsed_time(ev1) * 1e-3
+    xs = x.cpu().numpy()
+    line = {"metric": "BEM GMRES solves/s", "value": args.steps / t, "unit": "solves/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+            "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "bem_laplace_single_layer_icosphere_%d" % args.bem, "vertices": len(V),
+                       "triangles": len(F), "quadrature_nodes": 3 * len(F), "eps": eps, "gmres_tol": tol,
+                       "step": "ffm_bem_create + ffm_bem_solve + ffm_bem_destroy"},
+            "gmres_iterations": it, "ffm_products_per_solve": prods, "relres": rr,
+            "ffm_products_per_s": prods * args.steps / t,
+            "density_error": {"mean_minus_1": float(xs.mean() - 1), "max_abs_minus_1": float(np.max(np.abs(xs - 1)))},
+            "clocks": clk, "gpu_launches": launches}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -403,6 +458,13 @@ def main():
         import torch.distributed as dist
         os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
         dist.init_process_group("gloo", rank=rank, world_size=world)
+    if args.bem and args.impl == "ffm":
+        if rank == 0:
+            run_bem(args)
+        if dist:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
     if args.serving and args.impl == "ffm":
         if rank == 0:
             run_serving(args)
