@@ -208,8 +208,13 @@ __global__ void __launch_bounds__(128) k_nu_interp(NuGeo G, const float2 *__rest
                                                    const int4 *__restrict__ dirU, const float *__restrict__ dirW,
                                                    int nQ, const uint32_t *__restrict__ slot_box, int64_t nslot,
                                                    int nrhs, float2 *__restrict__ ut) {
+    // the staged tile holds real and imaginary parts in separate planes with odd row and
+    // plane strides: the directions of a warp start their windows at offsets (ox, oy) that
+    // differ by small integers, and odd strides spread those reads over the banks
     constexpr int X = NU_TILE + W - 1, X3 = X * X * X;
-    extern __shared__ float2 sx[];  // X^3
+    constexpr int XP = X | 1, PS = (X * XP) | 1;
+    extern __shared__ float sxs[];  // 2 planes of X * PS floats
+    float *sre = sxs, *sim = sxs + X * PS;
     const int n2 = G.n2, nt = (n2 + NU_TILE - 1) / NU_TILE;
     uint32_t id = own_id[blockIdx.x];
     int u0 = (int)(id / (nt * nt)) * NU_TILE, v0 = (int)((id / nt) % nt) * NU_TILE, w0 = (int)(id % nt) * NU_TILE;
@@ -240,7 +245,8 @@ __global__ void __launch_bounds__(128) k_nu_interp(NuGeo G, const float2 *__rest
                 float2 g = make_float2(0.f, 0.f);
                 if (u < n2 && v < n2 && w < n2)
                     g = F[((int64_t)fft_index(u, G.H, n2) * n2 + fft_index(v, G.H, n2)) * n2 + fft_index(w, G.H, n2)];
-                sx[i] = g;
+                sre[a * PS + b * XP + cc] = g.x;
+                sim[a * PS + b * XP + cc] = g.y;
             }
             __syncthreads();
             if (!on) continue;
@@ -250,13 +256,12 @@ __global__ void __launch_bounds__(128) k_nu_interp(NuGeo G, const float2 *__rest
                 float bx = 0.f, by = 0.f;
 #pragma unroll
                 for (int b = 0; b < W; ++b) {
-                    const float2 *row = sx + ((ox + a) * X + (oy + b)) * X + oz;
+                    const int r0 = (ox + a) * PS + (oy + b) * XP + oz;
                     float cx = 0.f, cy = 0.f;
 #pragma unroll
                     for (int c = 0; c < W; ++c) {
-                        float2 g = row[c];
-                        cx = fmaf(g.x, w2v[c], cx);
-                        cy = fmaf(g.y, w2v[c], cy);
+                        cx = fmaf(sre[r0 + c], w2v[c], cx);
+                        cy = fmaf(sim[r0 + c], w2v[c], cy);
                     }
                     bx = fmaf(cx, w1v[b], bx);
                     by = fmaf(cy, w1v[b], by);
@@ -701,7 +706,7 @@ void launch_forward(const ffm_plan_s *p, int l, const float2 *q, int nrhs, float
     tmp.drop(grid);
     exec_fft(N.fft_src, N.work_src, fine, ns * N2, nrhs, CUFFT_FORWARD, tmp, s);
     constexpr int X = NU_TILE + W - 1;
-    size_t xs = sizeof(float2) * X * X * X;
+    size_t xs = 2 * sizeof(float) * X * ((X * (X | 1)) | 1);
     FFM_CUDA(cudaFuncSetAttribute(k_nu_interp<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xs));
     FFM_LAUNCH(k_nu_interp<W>, dim3((unsigned)N.n_own, cdiv(ns, NU_IB), nrhs), 128, xs, s, G, (const float2 *)fine,
                N.own_id, N.own_off, N.own_q, N.dirU, N.dirW, F.nQ, F.src, ns, nrhs, ut);
