@@ -245,7 +245,8 @@ def roofline(prof, info, steps, clk, pk, pk_kind, workload):
       per pair (10 issue slots).  Double-layer near field: the same pipe at 64 slots per
       pair (hi+lo difference, rsqrt, cube, and the compensated dot product n.(x - y)).
       Gradient near field: 20 slots (hi+lo difference, rsqrt, cube, three multiply-adds).
-    - Gegenbauer transfer tables: FP32 issue, 72 instructions per recurrence step (double-float).
+    - Gegenbauer transfer tables: FP32 issue, 72 instructions per recurrence step (double-float),
+      19 on FP32 levels.
     - NUFFT grid kernels: the FP32 pipe, 4 FLOP per complex x real multiply-add of a W^3
       kernel window (per direction and box, or per point).
     - Lagrange transfer: tensor cores, 2 r r_K FLOP per admissible pair (r_K = r, or 3 r for
@@ -282,11 +283,15 @@ def roofline(prof, info, steps, clk, pk, pk_kind, workload):
                     "units_per_step": units, "peak_basis": basis % ("128 lanes/clk / %d" % slots)})
     elif "k_pw_table" in name:
         # Gegenbauer transfer tables: per recurrence (translation pair, direction pair) and
-        # degree, a Legendre step and the even / odd partial sums in double-float arithmetic,
-        # 4 multiplies (7 FP32 instructions) and 4 adds (11) = 72 FP32 instructions
-        units = 72.0 * sum(info["pw_recurrences"][l] * info["L"][l] for l in range(22) if info["mode"][l] == 2)
+        # degree, a Legendre step and the even / odd partial sums: in double-float arithmetic
+        # 4 multiplies (7 FP32 instructions) and 4 adds (11) = 72 FP32 instructions; on FP32
+        # levels (k_pw_table_f32) a 3-instruction step and two compensated products (8) = 19
+        f32 = "f32" in name
+        units = (19.0 if f32 else 72.0) * sum(info["pw_recurrences"][l] * info["L"][l] for l in range(22)
+                                              if info["mode"][l] == 2
+                                              and (info["pw_prec"][l] == 1 and info["cancel"][l] <= 250.0) == f32)
         peak = SM_COUNT * 128 * clk_hz
-        out.update({"bound": "alu", "pipe": "FP32 issue (double-float)", "unit": "Tops/s", "units_per_step": units,
+        out.update({"bound": "alu", "pipe": "FP32 issue" + ("" if f32 else " (double-float)"), "unit": "Tops/s", "units_per_step": units,
                     "peak_basis": basis % "128 lanes/clk"})
     elif "k_nu_" in name:
         # NUFFT grid kernels: complex x real multiply-adds (4 FLOP) of the W^3 kernel windows,

@@ -190,6 +190,82 @@ __device__ __forceinline__ void put_d(OUT *D, size_t o, double f, dflt r, dflt i
     D[o] = make_out<OUT>(-f * ti, f * tr);
 }
 
+// FP32 levels (the quadrature sum's cancellation ratio is at most 250): the same recurrence and
+// partial sums in FP32, each partial sum compensated (its rounding error carried in a second
+// FP32 term, TwoSum).  The forward Legendre recurrence is stable, its error grows about
+// linearly with the degree.
+__device__ __forceinline__ void comp_add(float &sum, float &cmp, float term) {
+    float t = sum + term;
+    float bb = t - sum;
+    cmp += (sum - (t - bb)) + (term - bb);
+    sum = t;
+}
+
+__global__ void __launch_bounds__(256) k_pw_table_f32(const D4 *__restrict__ sw, int nH, const float4 *__restrict__ coef,
+                                                      const float2 *__restrict__ beta, int L,
+                                                      const D4 *__restrict__ rhat, const int2 *__restrict__ pairs,
+                                                      double k, float2 *__restrict__ D) {
+    extern __shared__ float4 sm[];
+    float4 *sc = sm;                                      // L+1 coefficients
+    float2 *sb = reinterpret_cast<float2 *>(sm + L + 1);  // L betas
+    int2 tp = pairs[blockIdx.y];
+    int t = tp.x;
+    for (int i = threadIdx.x; i <= L; i += blockDim.x) sc[i] = coef[(size_t)t * (L + 1) + i];
+    for (int i = threadIdx.x; i < L; i += blockDim.x) sb[i] = beta[i];
+    __syncthreads();
+    int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nH) return;
+    D4 sv = sw[q];
+    D4 rh = rhat[t];
+    float x = (float)(sv.x * rh.x + sv.y * rh.y + sv.z * rh.z);
+    float p0 = 1.f, p1 = x;
+    float4 c0 = sc[0];
+    float er = c0.x + c0.y, ei = c0.z + c0.w, erc = 0.f, eic = 0.f;
+    float orr = 0.f, oi = 0.f, orc = 0.f, oic = 0.f;
+    if (L >= 1) {
+        float4 c1 = sc[1];
+        orr = (c1.x + c1.y) * x;
+        oi = (c1.z + c1.w) * x;
+    }
+    // P_{p+1} = x P_p + (p/(p+1)) (x P_p - P_{p-1}); degree p+1 is even for odd p
+    auto step = [&](int pp) {
+        float xp = x * p1;
+        float p2 = fmaf(sb[pp].x, xp - p0, xp);
+        p0 = p1;
+        p1 = p2;
+        return p2;
+    };
+    int pp = 1;
+    for (; pp + 1 < L; pp += 2) {
+        float pe = step(pp);
+        float4 c = sc[pp + 1];
+        comp_add(er, erc, (c.x + c.y) * pe);
+        comp_add(ei, eic, (c.z + c.w) * pe);
+        float po = step(pp + 1);
+        float4 d = sc[pp + 2];
+        comp_add(orr, orc, (d.x + d.y) * po);
+        comp_add(oi, oic, (d.z + d.w) * po);
+    }
+    if (pp < L) {
+        float pe = step(pp);
+        float4 c = sc[pp + 1];
+        comp_add(er, erc, (c.x + c.y) * pe);
+        comp_add(ei, eic, (c.z + c.w) * pe);
+    }
+    double f = k * sv.w / (4.0 * PI);
+    double Er = (double)er + erc, Ei = (double)ei + eic, Or = (double)orr + orc, Oi = (double)oi + oic;
+    size_t nQ = 2 * (size_t)nH;
+    // D = i f (sum_re + i sum_im), sum = E + O for direction h and E - O for its antipode
+    float2 dp = make_float2((float)(-f * (Ei + Oi)), (float)(f * (Er + Or)));
+    float2 dm = make_float2((float)(-f * (Ei - Oi)), (float)(f * (Er - Or)));
+    D[(size_t)t * nQ + q] = dp;
+    D[(size_t)t * nQ + q + nH] = dm;
+    if (tp.y >= 0) {
+        D[(size_t)tp.y * nQ + q] = dm;
+        D[(size_t)tp.y * nQ + q + nH] = dp;
+    }
+}
+
 // One Legendre recurrence serves four table entries.  With x = s_h . rhat_t, the sum splits
 // into even-degree and odd-degree parts E(x) + O(x); direction h + nQ/2 is -s_h, where the
 // sum is E - O.  A translation -m with the same length (the two root boxes share their
@@ -535,7 +611,12 @@ void build_tables(ffm_plan_s *p, int l, TableJob &tj) {
         for (int q = 0; q < nQ; ++q)
             ks[q] = make_float4((float)(p->k * sw[q].x), (float)(p->k * sw[q].y), (float)(p->k * sw[q].z), 0.f);
         FFM_CUDA(cudaMemcpyAsync(F.ks, keep.hold(std::move(ks)), sizeof(float4) * nQ, cudaMemcpyHostToDevice, s));
-        FFM_LAUNCH(k_pw_table<float2>, g1, 256, sm1, s, d_sw, nH, d_coef, d_beta, L, d_rhat, d_pairs, p->k, F.D);
+        // the FP32 table only where the sum is well conditioned (a forced FP32 level with a large
+        // cancellation ratio keeps the double-float table, so only the sum itself is FP32)
+        if (F.prec == FFM_PREC_F32 && F.cancel <= 250.0)
+            FFM_LAUNCH(k_pw_table_f32, g1, 256, sm1, s, d_sw, nH, d_coef, d_beta, L, d_rhat, d_pairs, p->k, F.D);
+        else
+            FFM_LAUNCH(k_pw_table<float2>, g1, 256, sm1, s, d_sw, nH, d_coef, d_beta, L, d_rhat, d_pairs, p->k, F.D);
     }
 }
 
