@@ -29,6 +29,10 @@
  *   - Pairs at distance 0 contribute nothing for the singular kernels.
  *   - Plane waves at level l iff the kernel is Helmholtz and k d_l >= kappa_switch (2.0);
  *     otherwise Lagrange with r1 from the calibrated error table below.
+ *   - ACA of T (eq. 11, optional, Laplace single layer): full pivoting on the explicit
+ *     r x r matrix, near-ties of pivot magnitudes (within a factor 1 - 1e-9) to the first
+ *     entry in row-major order, stop once |T - A B^T|_F <= aca_eps |T|_F or at min(r, 64)
+ *     terms (orc_aca).
  *
  * Build: gcc -O2 -fopenmp -ffp-contract=off -fPIC -shared (see oracle/build.py).
  */
@@ -681,6 +685,7 @@ typedef struct {
     int r1_override; /* 0: rule */
     int mode_override; /* 0: auto, 1: Lagrange everywhere, 2: plane waves everywhere */
     int pw_transform;  /* plane-wave steps F: 0 direct sums, 1 type-3 NUFFT (nufft_oracle.c) */
+    double aca_eps;    /* > 0: Laplace Lagrange transfers as ACA factors A B^T (eq. 11) */
 } orc_opts;
 
 typedef struct {
@@ -695,6 +700,7 @@ typedef struct {
     int r1[ORC_LMAX + 1];
     int L[ORC_LMAX + 1];
     int nQ[ORC_LMAX + 1];
+    int aca_rank[ORC_LMAX + 1]; /* with aca_eps: largest ACA rank over the level's translations */
 } orc_stats;
 
 typedef struct {
@@ -767,6 +773,7 @@ void orc_default_opts(orc_opts *o)
     o->r1_override = 0;
     o->mode_override = 0;
     o->pw_transform = 0;
+    o->aca_eps = 0.0;
 }
 
 static int level_mode(const orc_plan *p, int l)
@@ -791,6 +798,8 @@ void orc_plan_destroy(orc_plan *p)
     free(p->nearp);
     free(p);
 }
+
+static int level_aca_rank(const orc_plan *p, int l);
 
 /* Build both trees and the per-level pair lists (Sec. 2.2.1, 2.2.2, 2.2.4). */
 orc_plan *orc_plan_create(const double *X, int64_t nx, const double *Y, int64_t ny, int kind, double k,
@@ -910,6 +919,7 @@ annotate:
         double dl = ldexp(d0, -l);
         if (p->st.mode[l] == ORC_MODE_LAGRANGE) {
             p->st.r1[l] = p->opt.r1_override > 0 ? p->opt.r1_override : orc_r1_rule(kind, eps);
+            if (p->opt.aca_eps > 0.0 && kind == ORC_LAPLACE) p->st.aca_rank[l] = level_aca_rank(p, l);
         } else {
             p->st.L[l] = orc_pw_rank(k, dl, eps);
             p->st.nQ[l] = 2 * p->st.L[l] * (p->st.L[l] + 1);
@@ -960,6 +970,113 @@ static void box_centre(const double o[3], const int64_t g[3], double dl, double 
     for (int d = 0; d < 3; ++d) c[d] = o[d] + ((double)g[d] + 0.5) * dl;
 }
 
+/* ------------------------------------------------ adaptive cross approximation */
+
+#define ORC_ACA_KMAX 64
+
+/* Adaptive cross approximation of a small explicit matrix (Sec. 2.2.2, eq. 11, after
+ * Bebendorf), with full pivoting: M (nr x nc, row-major) ~ S_k = sum_{l<k} a_l b_l^T,
+ * a_l = A + l nr, b_l = B + l nc.  Step k takes the residual R = M - S_k, its entry of
+ * largest magnitude (i, j) (near-ties within a factor 1 - 1e-9 go to the first in
+ * row-major order), a = R(:, j), b = R(i, :) / R(i, j), and subtracts a b^T from R.  It
+ * stops once |R|_F <= tol |M|_F, at a zero residual, or after kmax terms.  Returns k. */
+int orc_aca(const double *M, int nr, int nc, double tol, int kmax, double *A, double *B)
+{
+    size_t n = (size_t)nr * nc;
+    double *R = (double *)malloc(sizeof(double) * n);
+    memcpy(R, M, sizeof(double) * n);
+    double m2 = 0.0;
+    for (size_t e = 0; e < n; ++e) m2 += M[e] * M[e];
+    int k = 0;
+    while (k < kmax) {
+        double mx = 0.0;
+        for (size_t e = 0; e < n; ++e)
+            if (fabs(R[e]) > mx) mx = fabs(R[e]);
+        if (mx == 0.0) break;
+        double thr = (1.0 - 1e-9) * mx;
+        size_t piv = 0;
+        while (fabs(R[piv]) < thr) ++piv;
+        int i = (int)(piv / nc), j = (int)(piv % nc);
+        double delta = R[piv];
+        double *a = A + (size_t)k * nr, *b = B + (size_t)k * nc;
+        for (int ii = 0; ii < nr; ++ii) a[ii] = R[(size_t)ii * nc + j];
+        for (int jj = 0; jj < nc; ++jj) b[jj] = R[(size_t)i * nc + jj] / delta;
+        double r2 = 0.0;
+        for (int ii = 0; ii < nr; ++ii)
+            for (int jj = 0; jj < nc; ++jj) {
+                double v = R[(size_t)ii * nc + jj] - a[ii] * b[jj];
+                R[(size_t)ii * nc + jj] = v;
+                r2 += v * v;
+            }
+        ++k;
+        if (r2 <= tol * tol * m2) break;
+    }
+    free(R);
+    return k;
+}
+
+static double dot(const double *a, const double *b, int n)
+{
+    double s = 0.0;
+    for (int i = 0; i < n; ++i) s += a[i] * b[i];
+    return s;
+}
+
+/* T of the Laplace single layer between the control nodes of boxes with centres ca
+ * (targets, rows i) and cb (sources, columns j), Sec. 2.2.2. */
+static void laplace_T(int r1, const double *t, double dl, const double ca[3], const double cb[3], double *T)
+{
+    int r = r1 * r1 * r1;
+    for (int i = 0; i < r; ++i) {
+        int ix = i / (r1 * r1), iy = (i / r1) % r1, iz = i % r1;
+        for (int j = 0; j < r; ++j) {
+            int jx = j / (r1 * r1), jy = (j / r1) % r1, jz = j % r1;
+            double dx = (ca[0] + t[ix] * 0.5 * dl) - (cb[0] + t[jx] * 0.5 * dl);
+            double dy = (ca[1] + t[iy] * 0.5 * dl) - (cb[1] + t[jy] * 0.5 * dl);
+            double dz = (ca[2] + t[iz] * 0.5 * dl) - (cb[2] + t[jz] * 0.5 * dl);
+            double gi;
+            orc_kernel(ORC_LAPLACE, 0.0, dx, dy, dz, &T[(size_t)i * r + j], &gi);
+        }
+    }
+}
+
+/* Largest ACA rank over the distinct translations of a Laplace Lagrange level (the first
+ * pair of each translation, in sorted pair order). */
+static int level_aca_rank(const orc_plan *p, int l)
+{
+    int64_t na = p->st.n_adm[l];
+    int r1 = p->st.r1[l], r = r1 * r1 * r1, kmax = r < ORC_ACA_KMAX ? r : ORC_ACA_KMAX;
+    double t[16], dl = ldexp(p->d0, -l);
+    cheb_nodes(r1, t);
+    keyidx *ki = (keyidx *)malloc(sizeof(keyidx) * (size_t)na);
+    for (int64_t e = 0; e < na; ++e) {
+        uint64_t c = 0;
+        for (int d = 0; d < 3; ++d)
+            c = (c << 21) | (uint64_t)((p->bx[l][p->adm[l][e].a].g[d] - p->by[l][p->adm[l][e].b].g[d]) + (1 << 20));
+        ki[e].key = c;
+        ki[e].idx = e;
+    }
+    qsort(ki, (size_t)na, sizeof(keyidx), cmp_keyidx);
+    int best = 0;
+    double *T = (double *)malloc(sizeof(double) * r * r), *A = (double *)malloc(sizeof(double) * r * kmax),
+           *B = (double *)malloc(sizeof(double) * r * kmax);
+    for (int64_t e = 0; e < na; ++e) {
+        if (e > 0 && ki[e].key == ki[e - 1].key) continue;
+        const opair *pr = &p->adm[l][ki[e].idx];
+        double ca[3], cb[3];
+        box_centre(p->tx.o, p->bx[l][pr->a].g, dl, ca);
+        box_centre(p->ty.o, p->by[l][pr->b].g, dl, cb);
+        laplace_T(r1, t, dl, ca, cb, T);
+        int k = orc_aca(T, r, r, p->opt.aca_eps, kmax, A, B);
+        if (k > best) best = k;
+    }
+    free(T);
+    free(A);
+    free(B);
+    free(ki);
+    return best;
+}
+
 /* Far field of level l (Lagrange, Sec. 2.2.2): u~_b = L_Y(b) (w u)_b for every source
  * box, v~_a = sum_b T_ab u~_b with T_ab computed from its definition for each pair,
  * v_a += L_X(a)^T v~_a. acc: sorted-order accumulators (nx*nrhs). */
@@ -969,7 +1086,8 @@ static void box_centre(const double o[3], const int64_t g[3], double dl, double 
  * w u n per source, qv[3 (j + ny m) + axis]) the kernel n_y . grad_y G is the sum over
  * the axes d of n_d dG/dy_d(x - y): each component kernel is interpolated on its own
  * (source step L_Y (w u n_d), transfer with dG/dy_d at the control nodes) and the three
- * results are added before the target step. */
+ * results are added before the target step.  With aca_eps (Laplace single layer) each
+ * pair's T is replaced by its ACA factors: v~_a += A (B^T u~_b) (eq. 11). */
 static void far_lagrange(const orc_plan *p, int l, const double *qr, const double *qi, const double *qv, int nrhs,
                          double *accr, double *acci)
 {
@@ -1023,6 +1141,10 @@ static void far_lagrange(const orc_plan *p, int l, const double *qr, const doubl
         double *vtr = (double *)calloc((size_t)nrhs * r, sizeof(double));
         double *vti = (double *)calloc((size_t)nrhs * r, sizeof(double));
         double *Tr = (double *)malloc(sizeof(double) * r * r), *Ti = (double *)malloc(sizeof(double) * r * r);
+        const int aca = p->opt.aca_eps > 0.0 && p->kind == ORC_LAPLACE && !qv;
+        const int kmax = r < ORC_ACA_KMAX ? r : ORC_ACA_KMAX;
+        double *Aa = aca ? (double *)malloc(sizeof(double) * r * kmax) : NULL;
+        double *Ba = aca ? (double *)malloc(sizeof(double) * r * kmax) : NULL;
         for (int64_t e = first[a]; e < first[a + 1]; ++e)
           for (int d = 0; d < nc; ++d) {
             int64_t b = adm[e].b;
@@ -1044,6 +1166,17 @@ static void far_lagrange(const orc_plan *p, int l, const double *qr, const doubl
                         orc_kernel(p->kind, p->k, dd[0], dd[1], dd[2], &Tr[i * r + j], &Ti[i * r + j]);
                     }
                 }
+            }
+            if (aca) {
+                int kk = orc_aca(Tr, r, r, p->opt.aca_eps, kmax, Aa, Ba);
+                for (int m = 0; m < nrhs; ++m) {
+                    const double *ur = utr + ((size_t)b * nrhs + m) * r;
+                    for (int q = 0; q < kk; ++q) {
+                        double s = dot(Ba + (size_t)q * r, ur, r); /* B^T u~ */
+                        for (int i = 0; i < r; ++i) vtr[m * r + i] += Aa[(size_t)q * r + i] * s;
+                    }
+                }
+                continue;
             }
             for (int m = 0; m < nrhs; ++m) {
                 const double *ur = utr + (((size_t)b * nrhs + m) * nc + d) * r, *ui = uti + (((size_t)b * nrhs + m) * nc + d) * r;
@@ -1075,6 +1208,8 @@ static void far_lagrange(const orc_plan *p, int l, const double *qr, const doubl
         free(vti);
         free(Tr);
         free(Ti);
+        free(Aa);
+        free(Ba);
     }
     free(first);
     free(utr);

@@ -25,7 +25,8 @@ _u64p = C.POINTER(C.c_uint64)
 
 class Opts(C.Structure):
     _fields_ = [("n_leaf", C.c_int), ("l_cap", C.c_int), ("kappa_switch", C.c_double),
-                ("r1_override", C.c_int), ("mode_override", C.c_int), ("pw_transform", C.c_int)]
+                ("r1_override", C.c_int), ("mode_override", C.c_int), ("pw_transform", C.c_int),
+                ("aca_eps", C.c_double)]
 
 
 class Stats(C.Structure):
@@ -34,12 +35,13 @@ class Stats(C.Structure):
                 ("nboxX", C.c_int64 * (LMAX + 1)), ("nboxY", C.c_int64 * (LMAX + 1)),
                 ("n_adm", C.c_int64 * (LMAX + 1)), ("n_near", C.c_int64 * (LMAX + 1)),
                 ("n_trans", C.c_int64 * (LMAX + 1)), ("mode", C.c_int * (LMAX + 1)),
-                ("r1", C.c_int * (LMAX + 1)), ("L", C.c_int * (LMAX + 1)), ("nQ", C.c_int * (LMAX + 1))]
+                ("r1", C.c_int * (LMAX + 1)), ("L", C.c_int * (LMAX + 1)), ("nQ", C.c_int * (LMAX + 1)),
+                ("aca_rank", C.c_int * (LMAX + 1))]
 
     def as_dict(self):
         out = {"l_stop": self.l_stop, "root_admissible": self.root_admissible, "d0": self.d0,
                "oX": list(self.oX), "oY": list(self.oY)}
-        for name in ("nboxX", "nboxY", "n_adm", "n_near", "n_trans", "mode", "r1", "L", "nQ"):
+        for name in ("nboxX", "nboxY", "n_adm", "n_near", "n_trans", "mode", "r1", "L", "nQ", "aca_rank"):
             out[name] = list(getattr(self, name))
         return out
 
@@ -67,6 +69,8 @@ def lib():
         L.orc_admissible.restype = C.c_int
         L.orc_morton.argtypes = [C.c_uint64] * 3
         L.orc_morton.restype = C.c_uint64
+        L.orc_aca.argtypes = [_dp, C.c_int, C.c_int, C.c_double, C.c_int, _dp, _dp]
+        L.orc_aca.restype = C.c_int
         L.orc_r1_rule.argtypes = [C.c_int, C.c_double]
         L.orc_r1_rule.restype = C.c_int
         L.orc_r1_table.argtypes = [C.c_int, _dp]
@@ -285,6 +289,18 @@ def morton(gx, gy, gz):
 
 def r1_rule(kind, eps):
     return int(lib().orc_r1_rule(kind, float(eps)))
+
+
+def aca(M, tol, kmax=None):
+    """ACA with partial pivoting of a real matrix M (eq. 11): (A, B) with M ~ A @ B.T,
+    A: nr x k, B: nc x k."""
+    M = np.ascontiguousarray(M, dtype=np.float64)
+    nr, nc = M.shape
+    kmax = min(nr, nc) if kmax is None else int(kmax)
+    A = np.zeros((kmax, nr))
+    B = np.zeros((kmax, nc))
+    k = int(lib().orc_aca(_d(M), nr, nc, float(tol), kmax, _d(A), _d(B)))
+    return A[:k].T.copy(), B[:k].T.copy()
 
 
 def r1_table(kind):

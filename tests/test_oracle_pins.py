@@ -664,3 +664,88 @@ def test_bem_ffm_product_matches_the_dense_matrix():
     u = np.random.default_rng(4).standard_normal(len(V))
     S = B.dense_matrix(V, F)
     assert O.rel_l2(B.apply_ffm(V, F, u, 1e-4), S @ u) < 1e-4
+
+
+# ------------------------------------------------- ACA of the transfer (eq. 11)
+
+def _cheb_grid(r1):
+    t = np.cos((2 * np.arange(r1) + 1) * np.pi / (2 * r1)) * 0.5
+    return np.stack(np.meshgrid(t, t, t, indexing="ij"), -1).reshape(-1, 3)
+
+
+def _laplace_T(r1, offset):
+    """The Laplace transfer between the control nodes of two unit boxes whose centres are
+    `offset` apart (Sec. 2.2.2), written out from the kernel."""
+    g = _cheb_grid(r1)
+    d = (g[:, None, :] + np.asarray(offset, float)) - g[None, :, :]
+    return 1.0 / (4 * np.pi * np.linalg.norm(d, axis=-1))
+
+
+def test_aca_recovers_a_low_rank_matrix_exactly():
+    rng = np.random.default_rng(0)
+    M = rng.standard_normal((50, 3)) @ rng.standard_normal((3, 40))
+    A, B = O.aca(M, 1e-12)
+    assert A.shape == (50, 3) and B.shape == (40, 3)
+    assert np.abs(A @ B.T - M).max() < 1e-13 * np.abs(M).max()
+
+
+def test_aca_is_gaussian_elimination_with_full_pivoting():
+    """After k steps the residual vanishes on k rows and k columns (the pivots), its
+    first pivot is the largest entry, and n steps reproduce a full-rank n x n matrix."""
+    rng = np.random.default_rng(1)
+    M = rng.standard_normal((9, 9))
+    A, B = O.aca(M, 0.0)
+    assert A.shape[1] == 9 and np.abs(A @ B.T - M).max() < 1e-12
+    i, j = np.unravel_index(np.argmax(np.abs(M)), M.shape)
+    assert np.allclose(A[:, 0], M[:, j]) and np.allclose(B[:, 0], M[i, :] / M[i, j])
+    for k in (2, 5):
+        A, B = O.aca(M, 0.0, kmax=k)
+        R = M - A @ B.T
+        assert np.sum(np.abs(R).max(axis=1) < 1e-12) == k
+        assert np.sum(np.abs(R).max(axis=0) < 1e-12) == k
+
+
+@pytest.mark.parametrize("r1", [4, 5])
+@pytest.mark.parametrize("offset", [(2, 0, 0), (2, 2, 2), (3, 1, 0)])
+def test_aca_of_the_laplace_transfer_meets_its_tolerance_near_the_optimal_rank(r1, offset):
+    """Frobenius error <= tol (the stopping rule is exact), and the rank is at least the
+    Eckart-Young minimum for that error (from the singular values) and within a small
+    factor of it."""
+    T = _laplace_T(r1, offset)
+    s = np.linalg.svd(T, compute_uv=False)
+    tail = np.sqrt(np.cumsum((s ** 2)[::-1]))[::-1]  # tail[k] = error of the best rank-k
+    prev = 0
+    for tol in (1e-3, 1e-4, 1e-5, 1e-7):
+        A, B = O.aca(T, tol)
+        k = A.shape[1]
+        assert np.linalg.norm(T - A @ B.T) <= tol * np.linalg.norm(T) * (1 + 1e-9)
+        kmin = int(np.sum(tail > tol * np.linalg.norm(T)))
+        assert kmin <= k <= 1.5 * kmin + 6
+        assert k >= prev
+        prev = k
+
+
+def test_ffm_with_aca_within_eps_and_within_aca_eps_of_the_dense_transfer():
+    prob = W.laplace_sphere(20000)
+    ref = O.direct(prob.X, prob.Y, prob.u, O.LAPLACE, w=prob.w)
+    dense = O.ffm(prob.X, prob.Y, prob.u, O.LAPLACE, 0.0, prob.eps, w=prob.w)
+    ranks = []
+    for ae in (1e-4, 1e-5):
+        p = O.Plan(prob.X, prob.Y, O.LAPLACE, 0.0, prob.eps, aca_eps=ae)
+        st = p.stats()
+        v = p.apply(prob.u, prob.w)
+        p.close()
+        lag = [l for l in range(st["l_stop"] + 1) if st["n_adm"][l] > 0]
+        r = st["r1"][lag[0]] ** 3
+        assert all(0 < st["aca_rank"][l] < r for l in lag)
+        ranks.append(max(st["aca_rank"]))
+        assert O.rel_l2(v, ref) < prob.eps
+        assert O.rel_l2(v, dense) < ae
+    assert ranks[1] > ranks[0]
+
+
+def test_ffm_with_a_vanishing_aca_tolerance_is_the_dense_ffm():
+    prob = W.laplace_sphere(6000)
+    dense = O.ffm(prob.X, prob.Y, prob.u, O.LAPLACE, 0.0, prob.eps, w=prob.w)
+    v = O.ffm(prob.X, prob.Y, prob.u, O.LAPLACE, 0.0, prob.eps, w=prob.w, aca_eps=1e-15)
+    assert O.rel_l2(v, dense) < 1e-12
