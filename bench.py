@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--pw-transform", default="auto", choices=["auto", "direct", "nufft"],
                     help="plane-wave F steps: chosen per level, direct sums, or the NUFFT where possible")
+    ap.add_argument("--aca", type=float, default=0.0, metavar="EPS_T",
+                    help="Laplace workloads: transfer matrices as ACA factors to this tolerance (eq. 11)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="default kernel variants instead of ffm_autotune's picks")
     return ap.parse_args()
@@ -313,12 +315,29 @@ def roofline(prof, info, steps, clk, pk, pk_kind, workload):
                     "peak_basis": basis % "128 FMA lanes/clk x 2 FLOP"})
     elif "k_lag_gemm" in name:
         variant = 2 if "_ts" in name else 1 if "_tc" in name else 0
-        units = sum(2.0 * kfac * (info["r1"][l] ** 3) ** 2 * info["n_adm"][l] for l in range(22)
-                    if info["mode"][l] == 1 and info["tune_tc"][l] == variant)
+
+        def lag_units(l):
+            # (flops, transfer variant) of a Lagrange level: a dense r x r (x kfac) GEMM per
+            # pair, or with ACA factors two r x rank GEMMs per pair (rank: the level's largest)
+            r, rk = info["r1"][l] ** 3, info["aca_rank"][l]
+            if rk > 0:
+                tc = (r + 15) // 16 * 16 <= 224 and (rk + 15) // 16 * 16 <= 224
+                return 4.0 * r * info["aca_pair_terms"][l], 1 if tc else 0
+            return 2.0 * kfac * r * r * info["n_adm"][l], info["tune_tc"][l]
+
+        units = sum(u for l in range(22) if info["mode"][l] == 1 for u, v in [lag_units(l)] if v == variant)
         peak = pk.get("bf16_tflops", 1900.0) * 1e12 * (1.1 / 2.25)
         out.update({"bound": "tensor", "pipe": "TF32", "unit": "TFLOP/s", "units_per_step": units,
                     "peak_basis": "measured BF16 %.1f TFLOP/s x 1.1/2.25 (%s peaks file)"
                                   % (pk.get("bf16_tflops", 1900.0), pk_kind)})
+    elif name == "k_lag_aca":
+        # ACA of the transfer matrices: per term, the rank-one update of the r x r residual
+        # with its squared norm (3 FP64 operations per entry), plus filling the matrix
+        units = sum(3.0 * (info["r1"][l] ** 3) ** 2 * (info["aca_terms"][l] + info["n_trans"][l])
+                    for l in range(22) if info["aca_rank"][l] > 0)
+        peak = 1.25e12
+        out.update({"bound": "alu", "pipe": "FP64", "unit": "TFLOP/s", "units_per_step": units,
+                    "peak_basis": "nominal FP64 1.25 TFLOP/s (no measured FP64 peak)"})
     else:
         out.update({"bound": "alu", "achieved": None, "peak": None, "unit": None, "frac": None})
         return out
@@ -501,6 +520,8 @@ def main():
     # extra plan arguments: the source normals of the double layer
     kw = {"normals": torch.as_tensor(prob.meta["normals"], device=dev)} if "normals" in prob.meta else {}
     kw["pw_transform"] = {"auto": ffm.PW_AUTO, "direct": ffm.PW_DIRECT, "nufft": ffm.PW_NUFFT}[args.pw_transform]
+    if args.aca > 0:
+        kw["aca_eps"] = args.aca
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
 
@@ -591,6 +612,8 @@ def main():
         uh = torch.as_tensor(u_host).pin_memory()
         kwh = {k: torch.as_tensor(prob.meta[k]).pin_memory() for k in kw if k in prob.meta}
         kwh["pw_transform"] = kw["pw_transform"]
+        if "aca_eps" in kw:
+            kwh["aca_eps"] = kw["aca_eps"]
         vshape = tuple(uh.shape[:-1]) + ((3,) if prob.kind == W.LAPLACE_GRAD else ()) + (prob.X.shape[0],)
         vh = torch.empty(vshape, dtype=uh.dtype).pin_memory()
         ke = max(2, args.steps // 2)
@@ -643,7 +666,8 @@ def main():
                        "k": prob.k, "eps": prob.eps,
                        "u_dtype": str(prob.u.dtype), "step": "ffm_plan + ffm_apply + ffm_destroy",
                        "l2": "flushed between steps (512 MiB write, outside the step events)",
-                       "replicas": world, "nrhs": nrhs, "pw_transform": args.pw_transform},
+                       "replicas": world, "nrhs": nrhs, "pw_transform": args.pw_transform,
+                       **({"aca_eps": args.aca} if args.aca > 0 else {})},
             "mpoints_per_s": n * value / 1e6, "rhs_per_s": value * nrhs,
             "t_plan_ms": t_plan / args.steps, "t_apply_ms": t_apply / args.steps,
             "apply_only_per_s": args.steps * world / (t_apply * 1e-3),
@@ -655,7 +679,8 @@ def main():
             "plan": {"l_stop": info["l_stop"], "mode": info["mode"][:info["l_stop"] + 1],
                      "L": info["L"][:info["l_stop"] + 1], "nQ": info["nQ"][:info["l_stop"] + 1],
                      "n_adm": info["n_adm"][:info["l_stop"] + 1], "p2p_pairs": info["p2p_pairs"],
-                     "nufft": info["nufft"][:info["l_stop"] + 1], "nufft_n2": info["nufft_n2"][:info["l_stop"] + 1]},
+                     "nufft": info["nufft"][:info["l_stop"] + 1], "nufft_n2": info["nufft_n2"][:info["l_stop"] + 1],
+                     **({"aca_rank": info["aca_rank"][:info["l_stop"] + 1]} if args.aca > 0 else {})},
         }
         if note:
             line["note"] = note

@@ -114,6 +114,12 @@ typedef struct {
                                    with many directions, direct sums elsewhere, or
                                    ffm_autotune's pick), 1 direct sums everywhere, 2 the NUFFT
                                    on every FP32 and compensated-FP32 plane-wave level */
+    double aca_eps;             /* FFM_LAPLACE: 0 -> dense transfer matrices T; > 0 -> each T_t
+                                   replaced by its adaptive cross approximation A_t B_t^T (Sec.
+                                   2.2.2, eq. 11; full pivoting, FP64, at plan time) with
+                                   |T_t - A_t B_t^T|_F <= aca_eps |T_t|_F or rank 64, and the
+                                   transfer applied as A_t (B_t^T u~) (two GEMMs per translation);
+                                   must be < 1; FFM_EUNSUPPORTED for the other kernels */
 } ffm_opts;
 
 /* Build a plan for targets X (nx points) and sources Y (ny points) (Sec. 2.2.1-2.2.4):
@@ -192,6 +198,10 @@ typedef struct {
     int64_t n_tgt_boxes[22];   /* target boxes with admissible pairs (per level) */
     int64_t pw_recurrences[22]; /* plane-wave levels: Legendre recurrences of the transfer table
                                    (one per translation pair and direction pair, L degrees each) */
+    int aca_rank[22];          /* Lagrange levels with aca_eps: largest ACA rank over the level's
+                                  translations (0 otherwise) */
+    int64_t aca_terms[22];     /* sum of the ACA ranks over the level's translations */
+    int64_t aca_pair_terms[22]; /* sum over the admissible pairs of their translation's rank */
 } ffm_info;
 
 ffm_status ffm_plan_info(const ffm_plan_t *plan, ffm_info *info);

@@ -961,6 +961,51 @@ void far_lagrange(const ffm_plan_s *p, int l, const void *q, int nrhs, float2 *a
         else
             lagrange_points_r1<false>(p, F, AY, cb, true, q, nrhs, ut, s);
         int npad = (r + 15) / 16 * 16;
+        if (F.aca) {
+            // ACA factors (eq. 11): w_p = B_t^T u~_src(p) for every pair p of translation t
+            // (rows of w indexed by pair), then v~_tgt(p) += A_t w_p
+            const int rp = F.aca_rp;
+            float *w = tmp.get<float>((size_t)F.n_adm * nrhs * rp);
+            FFM_CUDA(cudaMemsetAsync(w, 0, sizeof(float) * (size_t)F.n_adm * nrhs * rp, s));
+            if (F.aca_tc) {
+                constexpr int KT = 16, NR = 3, NO = 2;
+                auto smem_of = [](int np_) {
+                    return (size_t)NO * (2 * TC_P * KT + 2 * np_ * KT) * sizeof(float) +
+                           (size_t)NR * (TC_P + np_) * KT * sizeof(float);
+                };
+                auto tcols_of = [](int np_) {
+                    int c = 32;
+                    while (c < np_) c <<= 1;
+                    return c;
+                };
+                static bool attr_aca = false;
+                if (!attr_aca) {
+                    FFM_CUDA(cudaFuncSetAttribute(k_lag_gemm_tc<KT, NR, NO>,
+                                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_of(224)));
+                    attr_aca = true;
+                }
+                int64_t nrow = (int64_t)p->by[l].nb * nrhs;
+                float *upad = tmp.get<float>((size_t)nrow * F.rkp);
+                split_pad((const float *)ut, 1, (int)nrow, r, (int)nrow, F.rkp, upad, nullptr, s);
+                dim3 gtc((unsigned)F.tc_tiles, nrhs);
+                FFM_LAUNCH((k_lag_gemm_tc<KT, NR, NO>), gtc, 256, smem_of(rp), s, F.tc_tile_t, F.tc_tile_p0,
+                           F.bt_off, F.bt_src, F.pair_id, (const float *)F.Bca, rp, F.rkp, rp, tcols_of(rp), nrhs,
+                           (const float *)upad, w, p->dev_err);
+                FFM_LAUNCH((k_lag_gemm_tc<KT, NR, NO>), gtc, 256, smem_of(npad), s, F.tc_tile_t, F.tc_tile_p0,
+                           F.bt_off, F.pair_id, F.bt_tgt, (const float *)F.Aca, r, rp, npad, tcols_of(npad), nrhs,
+                           (const float *)w, (float *)vt, p->dev_err);
+                tmp.drop(upad);
+            } else {
+                dim3 g1((unsigned)F.n_tiles, cdiv(rp, LG_BM), nrhs);
+                FFM_LAUNCH(k_lag_gemm<false>, g1, LG_T, 0, s, F.tile_t, F.tile_p0, F.bt_off, F.bt_src, F.pair_id,
+                           F.Bca, rp, r, nrhs, (const float *)ut, w);
+                FFM_LAUNCH(k_lag_gemm<false>, gg, LG_T, 0, s, F.tile_t, F.tile_p0, F.bt_off, F.pair_id, F.bt_tgt,
+                           F.Aca, r, rp, nrhs, (const float *)w, (float *)vt);
+            }
+            tmp.drop(w);
+            lagrange_points_r1<false>(p, F, AX, cb, false, vt, nrhs, accf, s);
+            return;
+        }
         // the gradient has three operator blocks (component-major) and three outputs per
         // target; v~ and the FP32 accumulators are component-major too
         const int ncomp = p->kind == FFM_LAPLACE_GRAD ? 3 : 1;

@@ -327,8 +327,10 @@ ffm_status ffm_plan(const void *X, ffm_dtype xdt, int64_t nx, const void *Y, ffm
                 opts->r1_override < 0 || opts->r1_override > R1MAX || opts->r1_override == 1 ||
                 opts->precision < FFM_PREC_AUTO || opts->precision > FFM_PREC_F32X2 ||
                 opts->lagrange_transfer < 0 || opts->lagrange_transfer > 3 || opts->pw_transform < 0 ||
-                opts->pw_transform > 2)
+                opts->pw_transform > 2 || !(opts->aca_eps >= 0.0 && opts->aca_eps < 1.0))
                 fail(FFM_EINVAL, "bad option value");
+            if (opts->aca_eps > 0.0 && kernel != FFM_LAPLACE)
+                fail(FFM_EUNSUPPORTED, "the ACA transfer is built for the Laplace single layer");
             if (opts->n_leaf > 0) p->n_leaf = opts->n_leaf;
             if (opts->l_cap > 0) p->l_cap = opts->l_cap;
             if (opts->kappa_switch > 0) p->kappa = opts->kappa_switch;
@@ -336,6 +338,7 @@ ffm_status ffm_plan(const void *X, ffm_dtype xdt, int64_t nx, const void *Y, ffm
             p->precision = opts->precision;
             p->lag_transfer = opts->lagrange_transfer;
             p->pw_transform = opts->pw_transform;
+            p->aca_eps = opts->aca_eps;
             w = opts->weights;
             wdt = opts->weights_dtype;
             if (w && wdt != FFM_F32 && wdt != FFM_F64) fail(FFM_EINVAL, "weights dtype must be FFM_F32 or FFM_F64");

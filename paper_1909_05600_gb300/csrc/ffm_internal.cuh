@@ -168,6 +168,15 @@ struct FarLevel {
                                     // hi and lo, 64 x 64 each, in the K-major core-matrix layout
     float *Tsh = nullptr;           // tensor-core transfer: T_t padded to npad rows of rkp floats
     int rkp = 0;                    // (per component block for the gradient)
+    // ACA of T (eq. 11, Laplace single layer with ffm_opts.aca_eps): T_t ~ A_t B_t^T with
+    // rank_t <= aca_rank (the level's largest); the transfer runs as w_p = B_t^T u~_src(p)
+    // per pair, then v~_tgt(p) += A_t w_p.  B^T as [t][aca_rp][K] and A as [t][rows][aca_rp]
+    // (tensor cores: K = rkp, rows = npad, aca_rp = aca_rank rounded up to 16; CUDA cores:
+    // K = rows = r, aca_rp = aca_rank), zero past each rank.
+    bool aca = false, aca_tc = false;
+    int aca_rank = 0, aca_rp = 0;
+    float *Aca = nullptr, *Bca = nullptr;
+    uint32_t *pair_id = nullptr;    // n_adm: p -> p (pair-indexed rows of w)
     int64_t tc_tiles = 0;           // 256-pair tiles for the tensor-core transfer
     uint32_t *tc_tile_t = nullptr;
     uint32_t *tc_tile_p0 = nullptr;
@@ -213,6 +222,7 @@ struct ffm_plan_s {
     float4 *sctab = nullptr;  // sin/cos(j/64) in double-float for the double-float levels
     int lag_transfer = 0;     // ffm_opts.lagrange_transfer
     int pw_transform = 0;     // ffm_opts.pw_transform
+    double aca_eps = 0;       // ffm_opts.aca_eps
     const void *normals_in = nullptr;  // double layer: caller's normals (during ffm_plan only)
     ffm_dtype normals_dt = FFM_F64;
     float4 *nY = nullptr;     // double layer: source normals in Morton order, hi and lo parts

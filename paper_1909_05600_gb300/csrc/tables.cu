@@ -411,6 +411,190 @@ TableJob::~TableJob() {
     tmp.release();
 }
 
+// ---- ACA of the transfer matrices (Sec. 2.2.2, eq. 11), after Bebendorf, with full
+// pivoting on the explicit r x r matrix (it is small, and full pivoting bounds the
+// Frobenius error exactly): step k takes the residual R = T - S_k, its entry of largest
+// magnitude (i, j) (near-ties within a factor 1 - 1e-9 go to the first in row-major
+// order), a = R(:, j), b = R(i, :) / R(i, j), and subtracts a b^T; it stops once
+// |R|_F <= tol |T|_F, at a zero residual, or after kmax terms.  One block per translation,
+// FP64 throughout (entries from the FP64 translation and node offsets); the products are
+// rounded before the subtraction (no contraction) so that the pivots follow the plain
+// FP64 arithmetic of the definition.
+constexpr int ACA_T = 512, ACA_KMAX = 64;
+
+struct AcaGeo {
+    double oxy[3];
+    double dl;
+    int r1;
+    double hnode[R1MAX];  // (d_l / 2) cos((2a+1) pi / (2 r1))
+};
+
+// block-wide sum and maximum in one pass (ACA_T threads)
+__device__ __forceinline__ void aca_block_sum_max(double &sum, double &mx, double2 *red) {
+    for (int o = 16; o > 0; o >>= 1) {
+        sum += __shfl_xor_sync(0xffffffffu, sum, o);
+        mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    }
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = make_double2(sum, mx);
+    __syncthreads();
+    sum = 0.0;
+    mx = 0.0;
+    for (int w = 0; w < ACA_T / 32; ++w) {
+        sum += red[w].x;
+        mx = fmax(mx, red[w].y);
+    }
+}
+
+__device__ __forceinline__ unsigned aca_block_min(unsigned v, unsigned *red) {
+    for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    unsigned s = 0xffffffffu;
+    for (int w = 0; w < ACA_T / 32; ++w) s = min(s, red[w]);
+    return s;
+}
+
+// The residual lives in shared memory when it fits (r <= 125: up to 125 KB), else in the
+// global scratch R.
+__global__ void __launch_bounds__(ACA_T) k_lag_aca(const int4 *__restrict__ m, AcaGeo g, double tol, int kmax,
+                                                   int in_smem, double *__restrict__ R, double *__restrict__ Ad,
+                                                   double *__restrict__ Bd, int *__restrict__ rank) {
+    extern __shared__ double sR[];
+    __shared__ double sa[R1MAX * R1MAX * R1MAX], sb[R1MAX * R1MAX * R1MAX];
+    __shared__ double2 red[ACA_T / 32];
+    __shared__ unsigned redi[ACA_T / 32];
+    const int t = blockIdx.x, r1 = g.r1, r = r1 * r1 * r1, n = r * r;
+    double *Rt = in_smem ? sR : R + (size_t)t * n;
+    const int4 mt = m[t];
+    const double r0x = g.oxy[0] + mt.x * g.dl, r0y = g.oxy[1] + mt.y * g.dl, r0z = g.oxy[2] + mt.z * g.dl;
+    double m2 = 0.0, mx = 0.0;
+    for (int e = threadIdx.x; e < n; e += ACA_T) {
+        int i = e / r, j = e - i * r;
+        int ix = i / (r1 * r1), iy = (i / r1) % r1, iz = i % r1;
+        int jx = j / (r1 * r1), jy = (j / r1) % r1, jz = j % r1;
+        double dx = r0x + (g.hnode[ix] - g.hnode[jx]), dy = r0y + (g.hnode[iy] - g.hnode[jy]),
+               dz = r0z + (g.hnode[iz] - g.hnode[jz]);
+        double v = 1.0 / (4.0 * 3.14159265358979323846 * sqrt(dx * dx + dy * dy + dz * dz));
+        Rt[e] = v;
+        m2 += v * v;
+        mx = fmax(mx, fabs(v));
+    }
+    aca_block_sum_max(m2, mx, red);
+    int k = 0;
+    while (k < kmax && mx > 0.0) {
+        const double thr = (1.0 - 1e-9) * mx;
+        unsigned first = 0xffffffffu;
+        for (int e = threadIdx.x; e < n; e += ACA_T)
+            if (fabs(Rt[e]) >= thr) {
+                first = (unsigned)e;
+                break;
+            }
+        const unsigned piv = aca_block_min(first, redi);
+        const int i = (int)(piv / (unsigned)r), j = (int)(piv % (unsigned)r);
+        const double delta = Rt[piv];
+        double *a = Ad + ((size_t)t * kmax + k) * r, *b = Bd + ((size_t)t * kmax + k) * r;
+        for (int q = threadIdx.x; q < r; q += ACA_T) {
+            double av = Rt[(size_t)q * r + j], bv = Rt[(size_t)i * r + q] / delta;
+            sa[q] = av;
+            sb[q] = bv;
+            a[q] = av;
+            b[q] = bv;
+        }
+        __syncthreads();
+        double r2 = 0.0;
+        mx = 0.0;
+        for (int e = threadIdx.x; e < n; e += ACA_T) {
+            int ii = e / r, jj = e - ii * r;
+            double v = __dsub_rn(Rt[e], __dmul_rn(sa[ii], sb[jj]));
+            Rt[e] = v;
+            r2 += v * v;
+            mx = fmax(mx, fabs(v));
+        }
+        aca_block_sum_max(r2, mx, red);
+        ++k;
+        if (r2 <= tol * tol * m2) break;
+    }
+    if (threadIdx.x == 0) rank[t] = k;
+}
+
+// FP32 operands of the two transfer stages: B^T as [t][rb][cb] (row q = b_q), A as
+// [t][ra][ca] (column q = a_q), zero past the rank and past r.
+__global__ void k_aca_pack(const double *__restrict__ Ad, const double *__restrict__ Bd, const int *__restrict__ rank,
+                           int kmax, int r, int rb, int cb, int ra, int ca, float *__restrict__ Bt,
+                           float *__restrict__ At) {
+    const int t = blockIdx.x, kt = rank[t];
+    for (int e = threadIdx.x; e < rb * cb; e += blockDim.x) {
+        int q = e / cb, j = e - q * cb;
+        Bt[(size_t)t * rb * cb + e] = (q < kt && j < r) ? (float)Bd[((size_t)t * kmax + q) * r + j] : 0.f;
+    }
+    for (int e = threadIdx.x; e < ra * ca; e += blockDim.x) {
+        int i = e / ca, q = e - i * ca;
+        At[(size_t)t * ra * ca + e] = (q < kt && i < r) ? (float)Ad[((size_t)t * kmax + q) * r + i] : 0.f;
+    }
+}
+
+__global__ void k_aca_pair_id(uint32_t *id, int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) id[i] = (uint32_t)i;
+}
+
+static void build_aca(ffm_plan_s *p, int l, const double oxy[3], double dl, TableJob &tj) {
+    FarLevel &F = p->far[l];
+    cudaStream_t s = tj.side;
+    Alloc &tmp = tj.tmp;
+    const int r = F.r1 * F.r1 * F.r1, kmax = std::min(r, ACA_KMAX), nt = F.n_trans;
+    AcaGeo g{};
+    for (int d = 0; d < 3; ++d) g.oxy[d] = oxy[d];
+    g.dl = dl;
+    g.r1 = F.r1;
+    for (int a = 0; a < F.r1; ++a) g.hnode[a] = 0.5 * dl * std::cos((2.0 * a + 1.0) * PI / (2.0 * F.r1));
+    const size_t rbytes = sizeof(double) * (size_t)r * r;
+    const int in_smem = rbytes <= 125 * 1024;
+    double *R = in_smem ? nullptr : tmp.get<double>((size_t)nt * r * r);
+    double *Ad = tmp.get<double>((size_t)nt * kmax * r), *Bd = tmp.get<double>((size_t)nt * kmax * r);
+    int *rank = tmp.get<int>(nt);
+    static bool attr = false;
+    if (!attr) {
+        FFM_CUDA(cudaFuncSetAttribute(k_lag_aca, cudaFuncAttributeMaxDynamicSharedMemorySize, 125 * 1024));
+        attr = true;
+    }
+    FFM_LAUNCH(k_lag_aca, nt, ACA_T, in_smem ? rbytes : 0, s, F.trans_m, g, p->aca_eps, kmax, in_smem, R, Ad, Bd,
+               rank);
+    std::vector<int> hr(nt);
+    FFM_CUDA(cudaMemcpyAsync(hr.data(), rank, sizeof(int) * nt, cudaMemcpyDeviceToHost, s));
+    FFM_CUDA(cudaStreamSynchronize(s));
+    if (R) tmp.drop(R);
+    int kt = 1;
+    for (int v : hr) kt = std::max(kt, v);
+    // ACA terms over the translations, and over the pairs (each pair applies its translation's)
+    std::vector<uint32_t> hoff(nt + 1);
+    FFM_CUDA(cudaMemcpyAsync(hoff.data(), F.bt_off, sizeof(uint32_t) * (nt + 1), cudaMemcpyDeviceToHost, s));
+    FFM_CUDA(cudaStreamSynchronize(s));
+    int64_t terms = 0, pair_terms = 0;
+    for (int t = 0; t < nt; ++t) {
+        terms += hr[t];
+        pair_terms += (int64_t)hr[t] * (hoff[t + 1] - hoff[t]);
+    }
+    p->info.aca_terms[l] = terms;
+    p->info.aca_pair_terms[l] = pair_terms;
+    F.aca = true;
+    F.aca_rank = kt;
+    p->info.aca_rank[l] = kt;
+    const int npad = (r + 15) / 16 * 16, rp16 = (kt + 15) / 16 * 16;
+    // tensor cores when both stages fit the tcgen05 transfer (operand rows <= 224), unless
+    // the CUDA-core transfer is forced
+    F.aca_tc = npad <= 224 && rp16 <= 224 && F.tc_tiles > 0 && F.rkp > 0 && p->lag_transfer != 1;
+    F.aca_rp = F.aca_tc ? rp16 : kt;
+    const int rb = F.aca_rp, cb = F.aca_tc ? F.rkp : r, ra = F.aca_tc ? npad : r, ca = F.aca_rp;
+    F.Bca = p->mem.get<float>((size_t)nt * rb * cb);
+    F.Aca = p->mem.get<float>((size_t)nt * ra * ca);
+    FFM_LAUNCH(k_aca_pack, nt, 256, 0, s, Ad, Bd, rank, kmax, r, rb, cb, ra, ca, F.Bca, F.Aca);
+    F.pair_id = p->mem.get<uint32_t>((size_t)F.n_adm);
+    FFM_LAUNCH(k_aca_pair_id, cdiv(F.n_adm, 256), 256, 0, s, F.pair_id, F.n_adm);
+}
+
 void build_tables(ffm_plan_s *p, int l, TableJob &tj) {
     FarLevel &F = p->far[l];
     cudaStream_t s = tj.side;
@@ -442,6 +626,7 @@ void build_tables(ffm_plan_s *p, int l, TableJob &tj) {
             F.Tsh = p->mem.get<float>(tsz);
             split_pad(F.T, (int64_t)nblk * F.n_trans, r, rk, npad, F.rkp, F.Tsh, nullptr, s);
         }
+        if (p->aca_eps > 0.0 && p->kind == FFM_LAPLACE) build_aca(p, l, oxy, dl, tj);
         return;
     }
     // plane waves: quadrature of eq. 17, (L+1) Gauss-Legendre nodes in cos(theta) times 2L

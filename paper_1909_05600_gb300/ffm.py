@@ -49,7 +49,7 @@ class Opts(C.Structure):
     _fields_ = [("n_leaf", C.c_int), ("l_cap", C.c_int), ("kappa_switch", C.c_double), ("r1_override", C.c_int),
                 ("precision", C.c_int), ("weights", C.c_void_p), ("weights_dtype", C.c_int),
                 ("autotune_cache", C.c_char_p), ("lagrange_transfer", C.c_int), ("normals", C.c_void_p),
-                ("normals_dtype", C.c_int), ("pw_transform", C.c_int)]
+                ("normals_dtype", C.c_int), ("pw_transform", C.c_int), ("aca_eps", C.c_double)]
 
 
 class Info(C.Structure):
@@ -63,7 +63,8 @@ class Info(C.Structure):
                 ("p2p_tchunk", C.c_int), ("p2p_smax", C.c_int), ("tune_tc", C.c_int * 22),
                 ("tune_pw", (C.c_int * 3) * 22), ("nufft", C.c_int * 22), ("nufft_w", C.c_int * 22),
                 ("nufft_n2", C.c_int * 22), ("n_src_boxes", C.c_int64 * 22), ("n_tgt_boxes", C.c_int64 * 22),
-                ("pw_recurrences", C.c_int64 * 22)]
+                ("pw_recurrences", C.c_int64 * 22), ("aca_rank", C.c_int * 22), ("aca_terms", C.c_int64 * 22),
+                ("aca_pair_terms", C.c_int64 * 22)]
 
     def as_dict(self):
         d = {"l_stop": self.l_stop, "root_admissible": self.root_admissible, "d0": self.d0, "oX": list(self.oX),
@@ -72,7 +73,7 @@ class Info(C.Structure):
              "p2p_smax": self.p2p_smax, "tune_pw": [list(r) for r in self.tune_pw]}
         for f in ("nboxX", "nboxY", "n_adm", "n_near", "n_trans", "mode", "r1", "L", "nQ", "src_points",
                   "tgt_points", "pw_prec", "cancel", "tune_tc", "nufft", "nufft_w", "nufft_n2",
-                  "n_src_boxes", "n_tgt_boxes", "pw_recurrences"):
+                  "n_src_boxes", "n_tgt_boxes", "pw_recurrences", "aca_rank", "aca_terms", "aca_pair_terms"):
             d[f] = list(getattr(self, f))
         return d
 
@@ -258,14 +259,16 @@ class Plan:
 
     def __init__(self, X, Y, kernel, k=0.0, eps=1e-3, weights=None, stream=None, n_leaf=0, l_cap=0,
                  kappa_switch=0.0, r1_override=0, precision=PREC_AUTO, autotune_cache=None,
-                 lagrange_transfer=0, normals=None, pw_transform=PW_AUTO):
+                 lagrange_transfer=0, normals=None, pw_transform=PW_AUTO, aca_eps=0.0):
         """normals: (ny, 3) source normals, required for LAPLACE_DL (double layer).
-        pw_transform: PW_AUTO, PW_DIRECT or PW_NUFFT for the plane-wave levels' F steps."""
+        pw_transform: PW_AUTO, PW_DIRECT or PW_NUFFT for the plane-wave levels' F steps.
+        aca_eps: LAPLACE only; > 0 replaces each transfer matrix by its adaptive cross
+        approximation to that Frobenius tolerance (eq. 11)."""
         self._h = None
         self._keep = (X, Y, weights, normals)
         o = Opts(n_leaf, l_cap, float(kappa_switch), r1_override, int(precision), None, F64,
                  autotune_cache.encode() if autotune_cache else None, int(lagrange_transfer), None, F64,
-                 int(pw_transform))
+                 int(pw_transform), float(aca_eps))
         if normals is not None:
             o.normals = _ptr(normals)
             o.normals_dtype = _dtype_code(normals)

@@ -51,3 +51,28 @@ def test_null_arguments_are_rejected_on_the_host(lib):
     lib.ffm_destroy(None)
     info = ffm.Info()
     assert lib.ffm_plan_info(None, C.byref(info)) == 1
+
+
+def test_python_structs_match_the_header_layout(tmp_path):
+    """ffm_opts and ffm_info as the C compiler lays them out (size and the offset of every
+    field) equal the ctypes mirrors of the binding."""
+    import ctypes
+    import subprocess
+
+    from paper_1909_05600_gb300 import ffm
+
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "ffm.h"', 'int main(void) {']
+    for cname, py in (("ffm_opts", ffm.Opts), ("ffm_info", ffm.Info)):
+        lines.append('printf("%s %%zu\\n", sizeof(%s));' % (cname, cname))
+        for f, _ in py._fields_:
+            lines.append('printf("%s.%s %%zu\\n", offsetof(%s, %s));' % (cname, f, cname, f))
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    got = dict(l.split() for l in subprocess.check_output([str(exe)]).decode().split("\n") if l)
+    for cname, py in (("ffm_opts", ffm.Opts), ("ffm_info", ffm.Info)):
+        assert int(got[cname]) == ctypes.sizeof(py), cname
+        for f, _ in py._fields_:
+            assert int(got["%s.%s" % (cname, f)]) == getattr(py, f).offset, (cname, f)
