@@ -54,6 +54,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--pw-transform", default="auto", choices=["auto", "direct", "nufft"],
                     help="plane-wave F steps: chosen per level, direct sums, or the NUFFT where possible")
+    ap.add_argument("--eps", type=float, default=0.0, help="accuracy eps (0: the workload's own)")
     ap.add_argument("--aca", type=float, default=0.0, metavar="EPS_T",
                     help="Laplace workloads: transfer matrices as ACA factors to this tolerance (eq. 11)")
     ap.add_argument("--no-autotune", action="store_true",
@@ -195,6 +196,8 @@ def run_reference(args, rank):
     if rank != 0:
         return
     prob = make_problem(args.workload, 1, args.n)
+    if args.eps > 0:
+        prob.eps = args.eps
     n = prob.X.shape[0]
     ns = reference_targets(prob)
     for _ in range(args.warmup):
@@ -510,6 +513,8 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     prob = make_problem(args.workload, 1 + rank, args.n)
+    if args.eps > 0:
+        prob.eps = args.eps
     n = max(prob.X.shape[0], prob.Y.shape[0])
     X = torch.as_tensor(prob.X, device=dev)
     Y = torch.as_tensor(prob.Y, device=dev)

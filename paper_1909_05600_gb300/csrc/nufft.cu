@@ -275,11 +275,13 @@ __global__ void __launch_bounds__(128) k_nu_interp(NuGeo G, const float2 *__rest
 }
 
 // ---- backward: spread the corrected v~ onto one FFT-grid tile.  A warp owns one tile
-// column (NU_TILE cells along z, in registers) for 32 boxes, one box per lane, so the test
-// whether a direction's window covers the column is the same for the whole warp; the
-// tile's directions (those whose window meets the tile) are staged in shared memory in
-// batches, with the 32 boxes' v~ side by side.  Each tile of each box is written once, no
-// atomics.  Block: 16 warps = 16 of the tile's 64 columns.
+// column (NU_TILE cells along z, in registers) for 32 boxes, one box per lane; the tile's
+// directions (those whose window meets the tile) are staged in shared memory in batches,
+// with the 32 boxes' v~ side by side and each direction's z weights shifted onto the
+// tile's cells (zero outside the window).  Per batch a warp finds the directions whose
+// window covers its column with one ballot per 32 directions and visits only those.  Each
+// tile of each box is written once, no atomics.  Block: 16 warps = 16 of the tile's 64
+// columns.
 template <int W>
 __global__ void __launch_bounds__(512) k_nu_bspread(NuGeo G, const uint32_t *__restrict__ tile_id,
                                                     const uint32_t *__restrict__ tile_off,
@@ -289,8 +291,10 @@ __global__ void __launch_bounds__(512) k_nu_bspread(NuGeo G, const uint32_t *__r
                                                     int nrhs, const float2 *__restrict__ vt,
                                                     float2 *__restrict__ fine) {
     constexpr int T = NU_TILE;
+    static_assert(NU_BB == 64 && T == 8, "two ballots per batch, two float4 of z weights");
     __shared__ int4 sU[NU_BB];
-    __shared__ float sW[NU_BB][3 * W];
+    __shared__ float sW[NU_BB][2 * W];
+    __shared__ __align__(16) float sWz[NU_BB][T];
     __shared__ float2 sz[NU_BB][32];
     const int n2 = G.n2, nt = (n2 + T - 1) / T;
     int m = blockIdx.z >> 2, cq = blockIdx.z & 3;
@@ -303,13 +307,22 @@ __global__ void __launch_bounds__(512) k_nu_bspread(NuGeo G, const uint32_t *__r
     float ax[T], ay[T];
 #pragma unroll
     for (int cc = 0; cc < T; ++cc) ax[cc] = ay[cc] = 0.f;
+    for (int t = threadIdx.x; t < NU_BB * T; t += blockDim.x) sWz[t / T][t % T] = 0.f;
     uint32_t e0 = tile_off[blockIdx.x], e1 = tile_off[blockIdx.x + 1];
     for (uint32_t eb = e0; eb < e1; eb += NU_BB) {
         int cnt = (int)min((uint32_t)NU_BB, e1 - eb);
         __syncthreads();
         for (int t = threadIdx.x; t < cnt * 3 * W; t += blockDim.x) {
             int j = t / (3 * W), k = t - j * (3 * W);
-            sW[j][k] = dirW[(size_t)tile_q[eb + j] * 3 * W + k];
+            float wv = dirW[(size_t)tile_q[eb + j] * 3 * W + k];
+            if (k < 2 * W)
+                sW[j][k] = wv;
+            else {
+                // z weight of window node k - 2W: cell w0 + cc of the tile with
+                // cc = U.z + (k - 2W) - w0
+                int cc = dirU[tile_q[eb + j]].z + (k - 2 * W) - w0;
+                if ((unsigned)cc < (unsigned)T) sWz[j][cc] = wv;
+            }
         }
         for (int t = threadIdx.x; t < cnt; t += blockDim.x) sU[t] = dirU[tile_q[eb + t]];
         for (int t = threadIdx.x; t < cnt * 32; t += blockDim.x) {
@@ -318,24 +331,45 @@ __global__ void __launch_bounds__(512) k_nu_bspread(NuGeo G, const uint32_t *__r
             sz[j][b] = sl < nslot ? vt[((int64_t)slot_box[sl] * nrhs + m) * nQ + tile_q[eb + j]] : make_float2(0.f, 0.f);
         }
         __syncthreads();
-        for (int j = 0; j < cnt; ++j) {
+        // which directions of the batch cover this warp's column (u0 + i0, v0 + i1): bit j of
+        // the 64-bit mask
+        uint64_t mk = 0;
+        {
+            int4 U0 = lane < cnt ? sU[lane] : make_int4(-(1 << 20), 0, 0, 0);
+            int4 U1 = lane + 32 < cnt ? sU[lane + 32] : make_int4(-(1 << 20), 0, 0, 0);
+            bool c0 = (unsigned)(u0 + i0 - U0.x) < (unsigned)W && (unsigned)(v0 + i1 - U0.y) < (unsigned)W;
+            bool c1 = (unsigned)(u0 + i0 - U1.x) < (unsigned)W && (unsigned)(v0 + i1 - U1.y) < (unsigned)W;
+            mk = (uint64_t)__ballot_sync(0xffffffffu, c0) | ((uint64_t)__ballot_sync(0xffffffffu, c1) << 32);
+        }
+        while (mk) {
+            int j = __ffsll((long long)mk) - 1;
+            mk &= mk - 1;
             int4 U = sU[j];
-            int a = u0 + i0 - U.x, b = v0 + i1 - U.y;
-            if ((unsigned)a >= (unsigned)W || (unsigned)b >= (unsigned)W) continue;  // uniform in the warp
-            float wab = sW[j][a] * sW[j][W + b];
+            float wab = sW[j][u0 + i0 - U.x] * sW[j][W + (v0 + i1 - U.y)];
             float2 z = sz[j][lane];
             float zx = z.x * wab, zy = z.y * wab;
-            int kb = w0 - U.z;
-#pragma unroll
-            for (int cc = 0; cc < T; ++cc) {
-                int k = kb + cc;
-                if ((unsigned)k < (unsigned)W) {
-                    float wz = sW[j][2 * W + k];
-                    ax[cc] = fmaf(zx, wz, ax[cc]);
-                    ay[cc] = fmaf(zy, wz, ay[cc]);
-                }
-            }
+            float4 wa = *reinterpret_cast<const float4 *>(&sWz[j][0]);
+            float4 wb = *reinterpret_cast<const float4 *>(&sWz[j][4]);
+            ax[0] = fmaf(zx, wa.x, ax[0]);
+            ay[0] = fmaf(zy, wa.x, ay[0]);
+            ax[1] = fmaf(zx, wa.y, ax[1]);
+            ay[1] = fmaf(zy, wa.y, ay[1]);
+            ax[2] = fmaf(zx, wa.z, ax[2]);
+            ay[2] = fmaf(zy, wa.z, ay[2]);
+            ax[3] = fmaf(zx, wa.w, ax[3]);
+            ay[3] = fmaf(zy, wa.w, ay[3]);
+            ax[4] = fmaf(zx, wb.x, ax[4]);
+            ay[4] = fmaf(zy, wb.x, ay[4]);
+            ax[5] = fmaf(zx, wb.y, ax[5]);
+            ay[5] = fmaf(zy, wb.y, ay[5]);
+            ax[6] = fmaf(zx, wb.z, ax[6]);
+            ay[6] = fmaf(zy, wb.z, ay[6]);
+            ax[7] = fmaf(zx, wb.w, ax[7]);
+            ay[7] = fmaf(zy, wb.w, ay[7]);
         }
+        __syncthreads();
+        // the next batch's z weights start from zero
+        for (int t = threadIdx.x; t < NU_BB * T; t += blockDim.x) sWz[t / T][t % T] = 0.f;
     }
     if (slot >= nslot) return;
     int u = u0 + i0, v = v0 + i1;

@@ -429,20 +429,30 @@ struct AcaGeo {
     double hnode[R1MAX];  // (d_l / 2) cos((2a+1) pi / (2 r1))
 };
 
+// Magnitudes are compared as the bit patterns of non-negative doubles (their order is the
+// unsigned integer order), which keeps the maxima and the pivot search off the FP64 pipe.
+__device__ __forceinline__ unsigned long long mag_bits(double v) {
+    return (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffull;
+}
+
 // block-wide sum and maximum in one pass (ACA_T threads)
-__device__ __forceinline__ void aca_block_sum_max(double &sum, double &mx, double2 *red) {
+__device__ __forceinline__ void aca_block_sum_max(double &sum, unsigned long long &mx, double *reds,
+                                                  unsigned long long *redm) {
     for (int o = 16; o > 0; o >>= 1) {
         sum += __shfl_xor_sync(0xffffffffu, sum, o);
-        mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     }
     __syncthreads();
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = make_double2(sum, mx);
+    if ((threadIdx.x & 31) == 0) {
+        reds[threadIdx.x >> 5] = sum;
+        redm[threadIdx.x >> 5] = mx;
+    }
     __syncthreads();
     sum = 0.0;
-    mx = 0.0;
+    mx = 0ull;
     for (int w = 0; w < ACA_T / 32; ++w) {
-        sum += red[w].x;
-        mx = fmax(mx, red[w].y);
+        sum += reds[w];
+        mx = max(mx, redm[w]);
     }
 }
 
@@ -463,13 +473,15 @@ __global__ void __launch_bounds__(ACA_T) k_lag_aca(const int4 *__restrict__ m, A
                                                    double *__restrict__ Bd, int *__restrict__ rank) {
     extern __shared__ double sR[];
     __shared__ double sa[R1MAX * R1MAX * R1MAX], sb[R1MAX * R1MAX * R1MAX];
-    __shared__ double2 red[ACA_T / 32];
+    __shared__ double reds[ACA_T / 32];
+    __shared__ unsigned long long redm[ACA_T / 32];
     __shared__ unsigned redi[ACA_T / 32];
     const int t = blockIdx.x, r1 = g.r1, r = r1 * r1 * r1, n = r * r;
     double *Rt = in_smem ? sR : R + (size_t)t * n;
     const int4 mt = m[t];
     const double r0x = g.oxy[0] + mt.x * g.dl, r0y = g.oxy[1] + mt.y * g.dl, r0z = g.oxy[2] + mt.z * g.dl;
-    double m2 = 0.0, mx = 0.0;
+    double m2 = 0.0;
+    unsigned long long mx = 0ull;
     for (int e = threadIdx.x; e < n; e += ACA_T) {
         int i = e / r, j = e - i * r;
         int ix = i / (r1 * r1), iy = (i / r1) % r1, iz = i % r1;
@@ -479,15 +491,15 @@ __global__ void __launch_bounds__(ACA_T) k_lag_aca(const int4 *__restrict__ m, A
         double v = 1.0 / (4.0 * 3.14159265358979323846 * sqrt(dx * dx + dy * dy + dz * dz));
         Rt[e] = v;
         m2 += v * v;
-        mx = fmax(mx, fabs(v));
+        mx = max(mx, mag_bits(v));
     }
-    aca_block_sum_max(m2, mx, red);
+    aca_block_sum_max(m2, mx, reds, redm);
     int k = 0;
-    while (k < kmax && mx > 0.0) {
-        const double thr = (1.0 - 1e-9) * mx;
+    while (k < kmax && mx != 0ull) {
+        const unsigned long long thr = mag_bits((1.0 - 1e-9) * __longlong_as_double((long long)mx));
         unsigned first = 0xffffffffu;
         for (int e = threadIdx.x; e < n; e += ACA_T)
-            if (fabs(Rt[e]) >= thr) {
+            if (mag_bits(Rt[e]) >= thr) {
                 first = (unsigned)e;
                 break;
             }
@@ -504,15 +516,15 @@ __global__ void __launch_bounds__(ACA_T) k_lag_aca(const int4 *__restrict__ m, A
         }
         __syncthreads();
         double r2 = 0.0;
-        mx = 0.0;
+        mx = 0ull;
         for (int e = threadIdx.x; e < n; e += ACA_T) {
             int ii = e / r, jj = e - ii * r;
             double v = __dsub_rn(Rt[e], __dmul_rn(sa[ii], sb[jj]));
             Rt[e] = v;
-            r2 += v * v;
-            mx = fmax(mx, fabs(v));
+            r2 = fma(v, v, r2);
+            mx = max(mx, mag_bits(v));
         }
-        aca_block_sum_max(r2, mx, red);
+        aca_block_sum_max(r2, mx, reds, redm);
         ++k;
         if (r2 <= tol * tol * m2) break;
     }
