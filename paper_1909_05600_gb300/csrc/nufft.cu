@@ -23,7 +23,6 @@
 //     from the apply's stream-ordered temporaries).
 #include <cufft.h>
 
-#include <algorithm>
 #include <cmath>
 #include <map>
 #include <mutex>
@@ -198,21 +197,24 @@ __device__ __forceinline__ int fft_index(int u, int H, int n2) {
 
 // ---- forward: interpolate the transformed grids at the directions.  A block stages one
 // FFT-grid tile with its halo (the windows of the directions that start in the tile) for
-// each box of its group in turn; each thread keeps its direction's window in registers
-// across the boxes.
+// each box of its group in turn, once per box, and its threads then interpolate all the
+// tile's directions from it.
+constexpr int NU_IT = 128;  // threads of the interpolation block
+
 template <int W>
-__global__ void __launch_bounds__(128) k_nu_interp(NuGeo G, const float2 *__restrict__ fine,
-                                                   const uint32_t *__restrict__ own_id,
-                                                   const uint32_t *__restrict__ own_off,
-                                                   const uint32_t *__restrict__ own_q,
-                                                   const int4 *__restrict__ dirU, const float *__restrict__ dirW,
-                                                   int nQ, const uint32_t *__restrict__ slot_box, int64_t nslot,
-                                                   int nrhs, float2 *__restrict__ ut) {
+__global__ void __launch_bounds__(NU_IT) k_nu_interp(NuGeo G, const float2 *__restrict__ fine,
+                                                     const uint32_t *__restrict__ own_id,
+                                                     const uint32_t *__restrict__ own_off,
+                                                     const uint32_t *__restrict__ own_q,
+                                                     const int4 *__restrict__ dirU, const float *__restrict__ dirW,
+                                                     int nQ, const uint32_t *__restrict__ slot_box, int64_t nslot,
+                                                     int nrhs, float2 *__restrict__ ut) {
     // the staged tile holds real and imaginary parts in separate planes with odd row and
     // plane strides: the directions of a warp start their windows at offsets (ox, oy) that
     // differ by small integers, and odd strides spread those reads over the banks
     constexpr int X = NU_TILE + W - 1, X3 = X * X * X;
     constexpr int XP = X | 1, PS = (X * XP) | 1;
+    constexpr int NS = (X3 + NU_IT - 1) / NU_IT;  // staged nodes per thread
     extern __shared__ float sxs[];  // 2 planes of X * PS floats
     float *sre = sxs, *sim = sxs + X * PS;
     const int n2 = G.n2, nt = (n2 + NU_TILE - 1) / NU_TILE;
@@ -220,36 +222,39 @@ __global__ void __launch_bounds__(128) k_nu_interp(NuGeo G, const float2 *__rest
     int u0 = (int)(id / (nt * nt)) * NU_TILE, v0 = (int)((id / nt) % nt) * NU_TILE, w0 = (int)(id % nt) * NU_TILE;
     int m = blockIdx.z;
     uint32_t e0 = own_off[blockIdx.x], e1 = own_off[blockIdx.x + 1];
-    for (uint32_t eb = e0; eb < e1; eb += blockDim.x) {
-        uint32_t e = eb + threadIdx.x;
-        bool on = e < e1;
-        int q = on ? (int)own_q[e] : 0;
-        int4 U = dirU[q];
-        const float *wq = dirW + (size_t)q * 3 * W;
-        float w0v[W], w1v[W], w2v[W];
-#pragma unroll
-        for (int a = 0; a < W; ++a) {
-            w0v[a] = wq[a];
-            w1v[a] = wq[W + a];
-            w2v[a] = wq[2 * W + a];
-        }
-        int ox = U.x - u0, oy = U.y - v0, oz = U.z - w0;  // in [0, NU_TILE) for an owned direction
-        for (int bi = 0; bi < NU_IB; ++bi) {
-            int64_t slot = (int64_t)blockIdx.y * NU_IB + bi;
-            if (slot >= nslot) break;
-            const float2 *F = fine + ((int64_t)m * nslot + slot) * (int64_t)n2 * n2 * n2;
-            __syncthreads();
-            for (int i = threadIdx.x; i < X3; i += blockDim.x) {
+    for (int bi = 0; bi < NU_IB; ++bi) {
+        int64_t slot = (int64_t)blockIdx.y * NU_IB + bi;
+        if (slot >= nslot) break;
+        const float2 *F = fine + ((int64_t)m * nslot + slot) * (int64_t)n2 * n2 * n2;
+        __syncthreads();
+        // compile-time trip count: the loads of several nodes are in flight together
+#pragma unroll 4
+        for (int sI = 0; sI < NS; ++sI) {
+            int i = sI * NU_IT + (int)threadIdx.x;
+            if (i < X3) {
                 int a = i / (X * X), b = (i / X) % X, cc = i % X;
                 int u = u0 + a, v = v0 + b, w = w0 + cc;
                 float2 g = make_float2(0.f, 0.f);
                 if (u < n2 && v < n2 && w < n2)
-                    g = F[((int64_t)fft_index(u, G.H, n2) * n2 + fft_index(v, G.H, n2)) * n2 + fft_index(w, G.H, n2)];
+                    g = F[((int64_t)fft_index(u, G.H, n2) * n2 + fft_index(v, G.H, n2)) * n2 +
+                          fft_index(w, G.H, n2)];
                 sre[a * PS + b * XP + cc] = g.x;
                 sim[a * PS + b * XP + cc] = g.y;
             }
-            __syncthreads();
-            if (!on) continue;
+        }
+        __syncthreads();
+        for (uint32_t e = e0 + threadIdx.x; e < e1; e += NU_IT) {
+            const int q = (int)own_q[e];
+            const int4 U = dirU[q];
+            const float *wq = dirW + (size_t)q * 3 * W;
+            float w0v[W], w1v[W], w2v[W];
+#pragma unroll
+            for (int a = 0; a < W; ++a) {
+                w0v[a] = wq[a];
+                w1v[a] = wq[W + a];
+                w2v[a] = wq[2 * W + a];
+            }
+            const int ox = U.x - u0, oy = U.y - v0, oz = U.z - w0;  // in [0, NU_TILE) for an owned direction
             float ax = 0.f, ay = 0.f;
 #pragma unroll
             for (int a = 0; a < W; ++a) {
@@ -742,7 +747,7 @@ void launch_forward(const ffm_plan_s *p, int l, const float2 *q, int nrhs, float
     constexpr int X = NU_TILE + W - 1;
     size_t xs = 2 * sizeof(float) * X * ((X * (X | 1)) | 1);
     FFM_CUDA(cudaFuncSetAttribute(k_nu_interp<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xs));
-    FFM_LAUNCH(k_nu_interp<W>, dim3((unsigned)N.n_own, cdiv(ns, NU_IB), nrhs), 128, xs, s, G, (const float2 *)fine,
+    FFM_LAUNCH(k_nu_interp<W>, dim3((unsigned)N.n_own, cdiv(ns, NU_IB), nrhs), NU_IT, xs, s, G, (const float2 *)fine,
                N.own_id, N.own_off, N.own_q, N.dirU, N.dirW, F.nQ, F.src, ns, nrhs, ut);
     tmp.drop(fine);
 }
