@@ -40,7 +40,7 @@ constexpr int NU_TILE = 8;      // FFT-grid tile edge of the backward spread
 constexpr int NU_EMAX = 24;     // largest bin subgrid edge (E^3 float2 in shared memory)
 constexpr int NU_PB = 64;       // points staged per round of the spreading kernel
 constexpr int NU_GL = 32;       // Gauss-Legendre nodes of the kernel's Fourier transform
-constexpr int NU_IB = 8;        // boxes per forward-interpolation block
+constexpr int NU_IB = 4;        // boxes per forward-interpolation block
 constexpr int NU_BB = 64;       // directions staged per batch of the backward spread
 
 std::mutex g_fft_mu;  // a cuFFT handle's stream and work area are set and used under one lock

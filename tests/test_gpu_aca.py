@@ -28,7 +28,8 @@ def _apply(p, u):
     return v.cpu().numpy()
 
 
-@pytest.mark.parametrize("n,eps,aca_eps", [(20000, 1e-3, 1e-4), (8000, 1e-4, 1e-5)])
+# r = 64 and r = 125 keep the residual in shared memory (125 KB at r = 125), r = 216 in global memory
+@pytest.mark.parametrize("n,eps,aca_eps", [(20000, 1e-3, 1e-4), (12000, 5e-4, 5e-5), (8000, 1e-4, 1e-5)])
 def test_aca_ranks_and_products_match_the_oracle(n, eps, aca_eps):
     assert torch.cuda.is_available()
     prob = W.laplace_sphere(n)
