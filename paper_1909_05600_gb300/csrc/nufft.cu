@@ -35,12 +35,12 @@ namespace ffm {
 namespace {
 
 constexpr int NU_T = 256;       // threads of the point and tile kernels
-constexpr int NU_CHUNK = 1024;  // points per spreading / interpolation block
+constexpr int NU_CHUNK = 512;   // points per spreading / interpolation block
 constexpr int NU_TILE = 8;      // FFT-grid tile edge of the backward spread
 constexpr int NU_EMAX = 24;     // largest bin subgrid edge (E^3 float2 in shared memory)
 constexpr int NU_PB = 64;       // points staged per round of the spreading kernel
 constexpr int NU_GL = 32;       // Gauss-Legendre nodes of the kernel's Fourier transform
-constexpr int NU_IB = 4;        // boxes per forward-interpolation block
+constexpr int NU_IB = 2;        // boxes per forward-interpolation block
 constexpr int NU_BB = 64;       // directions staged per batch of the backward spread
 
 std::mutex g_fft_mu;  // a cuFFT handle's stream and work area are set and used under one lock
