@@ -35,12 +35,13 @@ namespace ffm {
 namespace {
 
 constexpr int NU_T = 256;       // threads of the point and tile kernels
-constexpr int NU_CHUNK = 512;   // points per spreading / interpolation block
+constexpr int NU_CHUNK_S = 256;  // points per spreading block (source side)
+constexpr int NU_CHUNK_T = 1024; // points per interpolation block (target side)
 constexpr int NU_TILE = 8;      // FFT-grid tile edge of the backward spread
 constexpr int NU_EMAX = 24;     // largest bin subgrid edge (E^3 float2 in shared memory)
 constexpr int NU_PB = 64;       // points staged per round of the spreading kernel
 constexpr int NU_GL = 32;       // Gauss-Legendre nodes of the kernel's Fourier transform
-constexpr int NU_IB = 2;        // boxes per forward-interpolation block
+constexpr int NU_IB = 1;        // boxes per forward-interpolation block
 constexpr int NU_BB = 64;       // directions staged per batch of the backward spread
 
 std::mutex g_fft_mu;  // a cuFFT handle's stream and work area are set and used under one lock
@@ -516,7 +517,7 @@ __global__ void k_nu_slot_of(const uint32_t *__restrict__ list, int64_t n, int *
 }
 
 __global__ void k_nu_bins(const uint32_t *__restrict__ bin_start, int64_t nbin, const uint32_t *__restrict__ box_start,
-                          int64_t nbox, const int *__restrict__ slot_of, uint32_t *__restrict__ cnt,
+                          int64_t nbox, const int *__restrict__ slot_of, uint32_t chunk, uint32_t *__restrict__ cnt,
                           const uint32_t *__restrict__ pos, int4 *__restrict__ out) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nbin) return;
@@ -531,13 +532,13 @@ __global__ void k_nu_bins(const uint32_t *__restrict__ bin_start, int64_t nbin, 
             hi = mid;
     }
     int slot = slot_of[lo];
-    uint32_t n = slot < 0 ? 0u : (s1 - s0 + NU_CHUNK - 1) / NU_CHUNK;
+    uint32_t n = slot < 0 ? 0u : (s1 - s0 + chunk - 1) / chunk;
     if (!out) {
         cnt[i] = n;
         return;
     }
     uint32_t k = pos[i];
-    for (uint32_t a = s0; n > 0 && a < s1; a += NU_CHUNK) out[k++] = make_int4((int)i, (int)a, (int)min(s1, a + NU_CHUNK), slot);
+    for (uint32_t a = s0; n > 0 && a < s1; a += chunk) out[k++] = make_int4((int)i, (int)a, (int)min(s1, a + chunk), slot);
 }
 
 struct Params {
@@ -576,21 +577,21 @@ double es_hat_host(double xi, double beta, const std::vector<double> &t, const s
 }
 
 int4 *build_point_blocks(ffm_plan_s *p, const BoxLevel &bins, const BoxLevel &boxes, const uint32_t *list,
-                         int64_t nlist, int64_t *count, Alloc &tmp, cudaStream_t s) {
+                         int64_t nlist, uint32_t chunk, int64_t *count, Alloc &tmp, cudaStream_t s) {
     int *slot_of = tmp.get<int>(boxes.nb);
     FFM_CUDA(cudaMemsetAsync(slot_of, 0xff, sizeof(int) * boxes.nb, s));
     FFM_LAUNCH(k_nu_slot_of, cdiv(nlist, 256), 256, 0, s, list, nlist, slot_of);
     uint32_t *cnt = tmp.get<uint32_t>(bins.nb), *pos = tmp.get<uint32_t>(bins.nb), *tot = tmp.get<uint32_t>(1);
-    FFM_LAUNCH(k_nu_bins, cdiv(bins.nb, 256), 256, 0, s, bins.start, bins.nb, boxes.start, boxes.nb, slot_of, cnt,
-               (const uint32_t *)nullptr, (int4 *)nullptr);
+    FFM_LAUNCH(k_nu_bins, cdiv(bins.nb, 256), 256, 0, s, bins.start, bins.nb, boxes.start, boxes.nb, slot_of, chunk,
+               cnt, (const uint32_t *)nullptr, (int4 *)nullptr);
     scan_u32(cnt, pos, bins.nb, tot, tmp, s);
     uint32_t n = 0;
     FFM_CUDA(cudaMemcpyAsync(&n, tot, sizeof n, cudaMemcpyDeviceToHost, s));
     FFM_CUDA(cudaStreamSynchronize(s));
     *count = n;
     int4 *out = p->mem.get<int4>(n);
-    FFM_LAUNCH(k_nu_bins, cdiv(bins.nb, 256), 256, 0, s, bins.start, bins.nb, boxes.start, boxes.nb, slot_of, cnt, pos,
-               out);
+    FFM_LAUNCH(k_nu_bins, cdiv(bins.nb, 256), 256, 0, s, bins.start, bins.nb, boxes.start, boxes.nb, slot_of, chunk,
+               cnt, pos, out);
     return out;
 }
 
@@ -847,8 +848,8 @@ void build_nufft(ffm_plan_s *p, int l, Alloc &tmp, cudaStream_t s) {
     tile_lists(p, l, 1, &N.n_own, &N.own_id, &N.own_off, &N.own_q, &N.own_max, tmp, s);
     // point blocks of the source and target bins
     int lb = l + N.dlt;
-    N.ych = build_point_blocks(p, p->by[lb], p->by[l], F.src, F.n_src, &N.n_ych, tmp, s);
-    N.xch = build_point_blocks(p, p->bx[lb], p->bx[l], F.tgt, F.n_tgt, &N.n_xch, tmp, s);
+    N.ych = build_point_blocks(p, p->by[lb], p->by[l], F.src, F.n_src, NU_CHUNK_S, &N.n_ych, tmp, s);
+    N.xch = build_point_blocks(p, p->bx[lb], p->bx[l], F.tgt, F.n_tgt, NU_CHUNK_T, &N.n_xch, tmp, s);
     // one cuFFT plan per side, batched over the level's boxes
     N.fft_src = make_fft(N.n2, F.n_src, &N.work_src);
     N.fft_tgt = make_fft(N.n2, F.n_tgt, &N.work_tgt);
