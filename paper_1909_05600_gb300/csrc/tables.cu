@@ -650,11 +650,17 @@ void build_tables(ffm_plan_s *p, int l, TableJob &tj) {
     gauss_legendre(L + 1, mu, wg);
     std::vector<D4> sw(nQ);
     {
+        // the azimuths' cosines and sines depend on j only: 2L library calls, not 2 nQ
+        std::vector<double> cph(np), sph(np);
+        for (int j = 0; j < np; ++j) {
+            double ph = j * PI / L;
+            cph[j] = std::cos(ph);
+            sph[j] = std::sin(ph);
+        }
         int h = 0;
         auto put = [&](int i, int j) {
             double st = std::sqrt(1.0 - mu[i] * mu[i]);
-            double ph = j * PI / L;
-            sw[h] = D4{st * std::cos(ph), st * std::sin(ph), mu[i], wg[i] * PI / L};
+            sw[h] = D4{st * cph[j], st * sph[j], mu[i], wg[i] * PI / L};
             sw[h + nH] = D4{-sw[h].x, -sw[h].y, -sw[h].z, sw[h].w};
             ++h;
         };
