@@ -324,8 +324,7 @@ def roofline(prof, info, steps, clk, pk, pk_kind, workload):
             # pair, or with ACA factors two r x rank GEMMs per pair (rank: the level's largest)
             r, rk = info["r1"][l] ** 3, info["aca_rank"][l]
             if rk > 0:
-                tc = (r + 15) // 16 * 16 <= 224 and (rk + 15) // 16 * 16 <= 224
-                return 4.0 * r * info["aca_pair_terms"][l], 1 if tc else 0
+                return 4.0 * r * info["aca_pair_terms"][l], info["tune_tc"][l]
             return 2.0 * kfac * r * r * info["n_adm"][l], info["tune_tc"][l]
 
         units = sum(u for l in range(22) if info["mode"][l] == 1 for u, v in [lag_units(l)] if v == variant)

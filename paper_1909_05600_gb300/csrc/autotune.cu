@@ -230,7 +230,7 @@ void autotune(ffm_plan_s *p, int nrhs, const char *cache_path, cudaStream_t s) {
         std::string v;
         if (F.mode == 1) {
             int r = F.r1 * F.r1 * F.r1;
-            bool tc_ok = !helm && (r + 15) / 16 * 16 <= 224 && F.tc_tiles > 0 && !F.aca;
+            bool tc_ok = !helm && F.tc_tiles > 0 && !F.aca;
             if (!tc_ok) continue;
             std::string key = lag_key(p, l, dev, rhs_bucket(nrhs));
             int pick = -1;

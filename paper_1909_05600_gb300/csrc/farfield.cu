@@ -432,7 +432,8 @@ __global__ void __launch_bounds__(256) k_lag_gemm_tc(const uint32_t *__restrict_
                                                      const uint32_t *__restrict__ bt_off,
                                                      const uint32_t *__restrict__ bt_src,
                                                      const uint32_t *__restrict__ bt_tgt, const float *__restrict__ Tp,
-                                                     int r, int rkp, int npad, int tcols, int nrhs,
+                                                     int64_t tstride, int ostride, int nout, int rkp, int npad,
+                                                     int tcols, int nrhs,
                                                      const float *__restrict__ up, float *__restrict__ vt,
                                                      int *__restrict__ err) {
     constexpr int C4 = KT / 4;  // 16-byte segments per row and chunk
@@ -473,7 +474,7 @@ __global__ void __launch_bounds__(256) k_lag_gemm_tc(const uint32_t *__restrict_
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     uint32_t tmem = s_tmem;
-    const float *Tt = Tp + (size_t)t * npad * rkp;
+    const float *Tt = Tp + (size_t)t * tstride;
     const uint32_t lbo = 128, sbo = (KT / 4) * 128;
     const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(npad >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
     const int nk = rkp / KT;
@@ -561,7 +562,7 @@ __global__ void __launch_bounds__(256) k_lag_gemm_tc(const uint32_t *__restrict_
     const int h = warp >> 2, quarter = warp & 3;
     const int p = h * 128 + quarter * 32 + lane;
     if (h < nh) {
-        float *dst = vt + ((size_t)s_tgt[p] * nrhs + m) * r;
+        float *dst = vt + ((size_t)s_tgt[p] * nrhs + m) * ostride;
         for (int c0 = 0; c0 < npad; c0 += 8) {
             uint32_t v[8];
             uint32_t addr = tmem + (uint32_t)(h * tcols) + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c0;
@@ -570,7 +571,7 @@ __global__ void __launch_bounds__(256) k_lag_gemm_tc(const uint32_t *__restrict_
                          : "r"(addr));
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
             if (ok && p < np) {
-                if ((r & 3) == 0 && c0 + 8 <= r) {
+                if ((ostride & 3) == 0 && c0 + 8 <= nout) {
                     atomicAdd(reinterpret_cast<float4 *>(dst + c0),
                               make_float4(__uint_as_float(v[0]), __uint_as_float(v[1]), __uint_as_float(v[2]),
                                           __uint_as_float(v[3])));
@@ -580,7 +581,7 @@ __global__ void __launch_bounds__(256) k_lag_gemm_tc(const uint32_t *__restrict_
                 } else {
 #pragma unroll
                     for (int q = 0; q < 8; ++q)
-                        if (c0 + q < r) atomicAdd(dst + c0 + q, __uint_as_float(v[q]));
+                        if (c0 + q < nout) atomicAdd(dst + c0 + q, __uint_as_float(v[q]));
                 }
             }
         }
@@ -933,6 +934,35 @@ void split_pad(const float *src, int64_t nmat, int rows, int cols, int rows_pad,
     FFM_LAUNCH(k_split_pad, g, 256, 0, s, src, nmat, rows, cols, rows_pad, cols_pad, hi, lo);
 }
 
+// The tcgen05 transfer over row blocks of the operator: every launch takes rows [row0, row0 +
+// nb) of each T_t (nb <= 224, a multiple of 16, the blocks as even as possible) with the
+// whole K, and adds output columns row0 .. of v~.  T_t starts every tstride floats with rows
+// of rkp floats (zero past `rows`); v~ rows are ostride floats apart.
+static void tc_transfer(const FarLevel &F, const uint32_t *src, const uint32_t *tgt, const float *Tp, int64_t tstride,
+                        int rows, int rkp, int ostride, int nrhs, const float *up, float *vt, int *err,
+                        cudaStream_t s) {
+    constexpr int KT = 16, NR = 3, NO = 2;
+    auto smem_of = [](int np_) {
+        return (size_t)NO * (2 * TC_P * KT + 2 * np_ * KT) * sizeof(float) + (size_t)NR * (TC_P + np_) * KT * sizeof(float);
+    };
+    static bool attr = false;
+    if (!attr) {
+        FFM_CUDA(cudaFuncSetAttribute(k_lag_gemm_tc<KT, NR, NO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem_of(224)));
+        attr = true;
+    }
+    const int npad = (rows + 15) / 16 * 16, parts = cdiv(npad, 224);
+    const int nb = (cdiv(npad, parts) + 15) / 16 * 16;
+    for (int row0 = 0; row0 < npad; row0 += nb) {
+        const int nbk = std::min(nb, npad - row0), nout = std::min(nbk, rows - row0);
+        int tcols = 32;
+        while (tcols < nbk) tcols <<= 1;
+        FFM_LAUNCH((k_lag_gemm_tc<KT, NR, NO>), dim3((unsigned)F.tc_tiles, nrhs), 256, smem_of(nbk), s, F.tc_tile_t,
+                   F.tc_tile_p0, F.bt_off, src, tgt, Tp + (size_t)row0 * rkp, tstride, ostride, nout, rkp, nbk, tcols,
+                   nrhs, up, vt + row0, err);
+    }
+}
+
 void far_lagrange(const ffm_plan_s *p, int l, const void *q, int nrhs, float2 *accf, Alloc &tmp, cudaStream_t s) {
     const FarLevel &F = p->far[l];
     int ls = p->l_stop;
@@ -968,32 +998,13 @@ void far_lagrange(const ffm_plan_s *p, int l, const void *q, int nrhs, float2 *a
             float *w = tmp.get<float>((size_t)F.n_adm * nrhs * rp);
             FFM_CUDA(cudaMemsetAsync(w, 0, sizeof(float) * (size_t)F.n_adm * nrhs * rp, s));
             if (F.aca_tc) {
-                constexpr int KT = 16, NR = 3, NO = 2;
-                auto smem_of = [](int np_) {
-                    return (size_t)NO * (2 * TC_P * KT + 2 * np_ * KT) * sizeof(float) +
-                           (size_t)NR * (TC_P + np_) * KT * sizeof(float);
-                };
-                auto tcols_of = [](int np_) {
-                    int c = 32;
-                    while (c < np_) c <<= 1;
-                    return c;
-                };
-                static bool attr_aca = false;
-                if (!attr_aca) {
-                    FFM_CUDA(cudaFuncSetAttribute(k_lag_gemm_tc<KT, NR, NO>,
-                                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_of(224)));
-                    attr_aca = true;
-                }
                 int64_t nrow = (int64_t)p->by[l].nb * nrhs;
                 float *upad = tmp.get<float>((size_t)nrow * F.rkp);
                 split_pad((const float *)ut, 1, (int)nrow, r, (int)nrow, F.rkp, upad, nullptr, s);
-                dim3 gtc((unsigned)F.tc_tiles, nrhs);
-                FFM_LAUNCH((k_lag_gemm_tc<KT, NR, NO>), gtc, 256, smem_of(rp), s, F.tc_tile_t, F.tc_tile_p0,
-                           F.bt_off, F.bt_src, F.pair_id, (const float *)F.Bca, rp, F.rkp, rp, tcols_of(rp), nrhs,
-                           (const float *)upad, w, p->dev_err);
-                FFM_LAUNCH((k_lag_gemm_tc<KT, NR, NO>), gtc, 256, smem_of(npad), s, F.tc_tile_t, F.tc_tile_p0,
-                           F.bt_off, F.pair_id, F.bt_tgt, (const float *)F.Aca, r, rp, npad, tcols_of(npad), nrhs,
-                           (const float *)w, (float *)vt, p->dev_err);
+                tc_transfer(F, F.bt_src, F.pair_id, F.Bca, (int64_t)rp * F.rkp, rp, F.rkp, rp, nrhs, upad, w,
+                            p->dev_err, s);
+                tc_transfer(F, F.pair_id, F.bt_tgt, F.Aca, (int64_t)npad * rp, r, rp, r, nrhs, w, (float *)vt,
+                            p->dev_err, s);
                 tmp.drop(upad);
             } else {
                 dim3 g1((unsigned)F.n_tiles, cdiv(rp, LG_BM), nrhs);
@@ -1012,8 +1023,7 @@ void far_lagrange(const ffm_plan_s *p, int l, const void *q, int nrhs, float2 *a
         const size_t tblk = (size_t)F.n_trans * r * rk;
         const size_t vblk = (size_t)r * nrhs * p->bx[l].nb;
         float *upad = nullptr;
-        const bool use_tc = !(F.ts_ok && F.Tsp && F.tune_tc == 2) && npad <= 224 && F.tc_tiles > 0 &&
-                            F.tune_tc != 0 && F.Tsh;
+        const bool use_tc = !(F.ts_ok && F.Tsp && F.tune_tc == 2) && F.tc_tiles > 0 && F.tune_tc != 0 && F.Tsh;
         if (use_tc) {
             // u~ with rows padded to rkp floats (whole, aligned 16-byte segments for cp.async)
             int64_t nrow = (int64_t)p->by[l].nb * nrhs;
@@ -1034,26 +1044,11 @@ void far_lagrange(const ffm_plan_s *p, int l, const void *q, int nrhs, float2 *a
             FFM_LAUNCH(k_lag_gemm_ts, gts, 2 * TS_M, smem, s, F.tgt, F.n_tgt, F.adm_off, F.adm_src, F.adm_t, F.n_trans,
                        F.Tsp, r, nrhs, (const float *)ut, vtd, p->dev_err);
         } else if (use_tc) {
-            // tensor cores: 256-pair tiles, K chunks of KT source nodes, NR raw and NO operand stages
-            constexpr int KT = 16, NR = 3, NO = 2;
-            int rkp = F.rkp;
-            int tcols = 32;
-            while (tcols < npad) tcols <<= 1;
-            auto smem_of = [](int np_) {
-                return (size_t)NO * (2 * TC_P * KT + 2 * np_ * KT) * sizeof(float) +
-                       (size_t)NR * (TC_P + np_) * KT * sizeof(float);
-            };
-            static bool attr = false;
-            if (!attr) {
-                FFM_CUDA(cudaFuncSetAttribute(k_lag_gemm_tc<KT, NR, NO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              (int)smem_of(224)));
-                attr = true;
-            }
-            size_t dsz = (size_t)F.n_trans * npad * rkp;
-            dim3 gtc((unsigned)F.tc_tiles, nrhs);
-            FFM_LAUNCH((k_lag_gemm_tc<KT, NR, NO>), gtc, 256, smem_of(npad), s, F.tc_tile_t, F.tc_tile_p0, F.bt_off,
-                       F.bt_src, F.bt_tgt, (const float *)(F.Tsh + d * dsz), r, rkp, npad, tcols, nrhs,
-                       (const float *)upad, vtd, p->dev_err);
+            // tensor cores: 256-pair tiles, K chunks of 16 source nodes, row blocks of <= 224
+            const int rkp = F.rkp;
+            const size_t dsz = (size_t)F.n_trans * npad * rkp;
+            tc_transfer(F, F.bt_src, F.bt_tgt, F.Tsh + d * dsz, (int64_t)npad * rkp, r, rkp, r, nrhs, upad, vtd,
+                        p->dev_err, s);
         } else {
             FFM_LAUNCH(k_lag_gemm<false>, gg, LG_T, 0, s, F.tile_t, F.tile_p0, F.bt_off, F.bt_src, F.bt_tgt, Td, r,
                        rk, nrhs, (const float *)ut, vtd);

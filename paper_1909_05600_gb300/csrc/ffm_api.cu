@@ -474,8 +474,9 @@ ffm_status ffm_plan_info(const ffm_plan_t *plan, ffm_info *info) {
     for (int l = 0; l <= ffm::LMAX; ++l) {
         const ffm::FarLevel &F = plan->far[l];
         bool act = l <= plan->l_stop && F.n_adm > 0;
-        bool tc = F.tune_tc != 0 && F.tc_tiles > 0 && real_kernel(plan->kind) &&
-                  (F.r1 * F.r1 * F.r1 + 15) / 16 * 16 <= 256;
+        // the variant far_lagrange runs: ACA levels by their own choice, dense levels on tcgen05
+        // (row blocks of <= 224) wherever the padded real operator exists
+        bool tc = F.aca ? F.aca_tc : (F.tune_tc != 0 && F.tc_tiles > 0 && F.Tsh != nullptr);
         bool ts = F.ts_ok && F.Tsp && F.tune_tc == 2;
         info->tune_tc[l] = act && F.mode == 1 ? (ts ? 2 : tc ? 1 : 0) : 0;
         info->tune_pw[l][0] = act && F.mode == 2 ? F.pw_qpt : 0;

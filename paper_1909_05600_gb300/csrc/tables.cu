@@ -595,9 +595,9 @@ static void build_aca(ffm_plan_s *p, int l, const double oxy[3], double dl, Tabl
     F.aca_rank = kt;
     p->info.aca_rank[l] = kt;
     const int npad = (r + 15) / 16 * 16, rp16 = (kt + 15) / 16 * 16;
-    // tensor cores when both stages fit the tcgen05 transfer (operand rows <= 224), unless
-    // the CUDA-core transfer is forced
-    F.aca_tc = npad <= 224 && rp16 <= 224 && F.tc_tiles > 0 && F.rkp > 0 && p->lag_transfer != 1;
+    // tensor cores (the tcgen05 transfer in row blocks of at most 224), unless the CUDA-core
+    // transfer is forced
+    F.aca_tc = rp16 <= 224 && F.tc_tiles > 0 && F.rkp > 0 && p->lag_transfer != 1;
     F.aca_rp = F.aca_tc ? rp16 : kt;
     const int rb = F.aca_rp, cb = F.aca_tc ? F.rkp : r, ra = F.aca_tc ? npad : r, ca = F.aca_rp;
     F.Bca = p->mem.get<float>((size_t)nt * rb * cb);
@@ -628,7 +628,7 @@ void build_tables(ffm_plan_s *p, int l, TableJob &tj) {
         for (int a = 0; a < F.r1; ++a) g.hnode[a] = (float)(0.5 * dl * std::cos((2.0 * a + 1.0) * PI / (2.0 * F.r1)));
         FFM_LAUNCH(k_lag_table, F.n_trans, 256, 0, s, F.trans_m, F.n_trans, g, F.T);
         int rk = p->kind == FFM_LAPLACE_DL ? 3 * r : r, npad = (r + 15) / 16 * 16;
-        if (!cplx && npad <= 224) {
+        if (!cplx) {
             // the tensor-core transfer's operand: T_t with npad rows of rkp (a multiple of its
             // 16-node K chunks) floats, padding zero; the gradient's three component blocks one
             // after another
