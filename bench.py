@@ -474,6 +474,24 @@ def run_bem(args):
     print(json.dumps(line), flush=True)
 
 
+def max_over_ranks(vals, dist):
+    """Element-wise maximum of per-rank timings (ms) over all ranks (the slowest replica sets
+    the job's time); the values themselves with one rank."""
+    if not dist:
+        return list(vals)
+    import torch
+    import torch.distributed as tdist
+    tt = torch.tensor(list(vals), dtype=torch.float64)
+    tdist.all_reduce(tt, op=tdist.ReduceOp.MAX)
+    return tt.tolist()
+
+
+def whole_job_rate(steps, world, t_ms):
+    """Products per second of the whole job: every rank runs `steps` products (weak scaling,
+    one independent replica per GPU) in at most t_ms."""
+    return steps * world / (t_ms * 1e-3)
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -599,13 +617,8 @@ def main():
     if rejected(clk):
         note = "first timed run rejected (clock reasons %s); re-measured" % clk.get("reasons")
         vlast, t_plan, t_apply, clk, launches, _ = timed(False)
-    t_step = t_plan + t_apply  # ms over all steps (device time between the step's events)
-    if dist:
-        import torch.distributed as tdist
-        tt = torch.tensor([t_step, t_plan, t_apply], dtype=torch.float64)
-        tdist.all_reduce(tt, op=tdist.ReduceOp.MAX)
-        t_step, t_plan, t_apply = tt.tolist()
-    value = args.steps * world / (t_step * 1e-3)
+    t_step, t_plan, t_apply = max_over_ranks([t_plan + t_apply, t_plan, t_apply], dist)
+    value = whole_job_rate(args.steps, world, t_step)
     pk, pk_kind = peaks()
 
     e2e = None
