@@ -48,7 +48,7 @@ typedef enum {
     FFM_ENOMEM = 2,      /* device allocation failed; nothing is leaked, no plan is returned */
     FFM_ECUDA = 3,       /* a CUDA runtime call or kernel launch failed */
     FFM_ETIMEOUT = 4,    /* a bounded device-side wait gave up */
-    FFM_EUNSUPPORTED = 5 /* valid request outside what this build implements */
+    FFM_EUNSUPPORTED = 5 /* valid request outside what this library implements */
 } ffm_status;
 
 /* FFM_LAPLACE_DL is the double layer of the Laplace kernel, dG/dn_y(x - y) =
