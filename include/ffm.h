@@ -218,7 +218,7 @@ ffm_status ffm_plan_export(const ffm_plan_t *plan, int what, int level, void *ho
 /* Pick kernel variants for this plan by timing them on its own data, for products with
  * `nrhs` right-hand sides: the near-field work-item shape (targets and source points per
  * item, which balance clustered leaves), the Lagrange transfer (tcgen05 target-stationary
- * tiles of 128 target boxes, tcgen05 tiles of 128 box pairs of one translation, or
+ * tiles of 128 target boxes, tcgen05 tiles of 256 box pairs of one translation, or
  * CUDA-core tiles of 32 pairs), and per plane-wave level the direction pairs and
  * points per thread of the transforms (or right-hand sides per thread).  Costs a few
  * applies of GPU time; results change only by rounding.

@@ -363,9 +363,10 @@ __global__ void __launch_bounds__(LG_T) k_lag_gemm(const uint32_t *__restrict__ 
 
 // ---- tensor-core transfer (5th-generation tensor cores, tcgen05, TF32 with hi/lo split)
 //
-// D(p, i) = sum_j u~_{src(p)}(j) T_t(i, j) for a tile of 128 pairs p of translation t:
-// A = gathered u~ columns (M = 128 pairs, K = r, K-major), B = T_t (N = r padded to a
-// multiple of 16, K-major), accumulator in TMEM (lane = pair, column = i).  Each operand is
+// D(p, i) = sum_j u~_{src(p)}(j) T_t(i, j) for 128 pairs p of translation t (one MMA
+// half-tile): A = gathered u~ columns (M = 128 pairs, K = r, K-major), B = rows of T_t (N
+// = a row block of at most 224, a multiple of 16, K-major), accumulator in TMEM (lane = pair,
+// column = i).  Each operand is
 // split into hi + lo TF32 parts (hi: low 13 mantissa bits cleared, lo = x - hi exactly), and
 // D += A_hi B_hi + A_hi B_lo + A_lo B_hi in FP32, about 2^-21 relative per product.
 // Operands use the no-swizzle K-major layout of 8-row x 16-byte core matrices: core matrix
