@@ -39,17 +39,24 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ffm", choices=["ffm", "reference"])
-    ap.add_argument("--workload", default="helmholtz_sphere_1M",
+    ap.add_argument("--workload", default="laplace_clustered",
                     choices=["helmholtz_sphere_1M", "laplace_sphere_20k", "helmholtz_cube_200k_64rhs",
                              "laplace_clustered", "laplace_double_layer_sphere_1M", "laplace_gradient_sphere_1M"])
     ap.add_argument("--n", type=int, default=0, help="points per set (0: the workload's own size)")
     ap.add_argument("--serving", action="store_true",
                     help="serving stream: Poisson arrivals of mixed requests, p50/p99 latency and throughput")
     ap.add_argument("--requests", type=int, default=500)
+    ap.add_argument("--scenes", type=int, default=0,
+                    help="serving: requests share this many scenes (point sets, kernel, k, eps); 0: all distinct")
+    ap.add_argument("--err-requests", type=int, default=12, help="serving: requests whose error is measured")
+    ap.add_argument("--err-targets", type=int, default=256, help="serving: sampled targets per measured request")
     ap.add_argument("--bem", type=int, default=0, metavar="LEVEL",
                     help="boundary-element solve on an icosphere of this refinement level (GMRES over FFM products)")
     ap.add_argument("--workers", type=int, default=4)
-    ap.add_argument("--cpu-targets", type=int, default=4096)
+    ap.add_argument("--cpu-targets", type=int, default=0,
+                    help="targets of the FP64 direct-sum check (0: as many as fill --cpu-seconds, 256..4096)")
+    ap.add_argument("--cpu-seconds", type=float, default=45.0,
+                    help="time budget of the all-core direct-sum leg when --cpu-targets is 0")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--pw-transform", default="auto", choices=["auto", "direct", "nufft"],
@@ -77,6 +84,17 @@ def make_problem(name, seed, n=0):
     if name == "laplace_gradient_sphere_1M":
         return W.laplace_gradient_sphere(n or 1_000_000, seed=seed)
     return W.laplace_sphere(n or 20000, seed=seed)
+
+
+def workload_name(args, prob):
+    """The workload as named in the JSON line: its name, with the point count when it is not
+    the workload's own (1e8 written as 1e8)."""
+    n = int(prob.X.shape[0])
+    lg = math.log10(n) if n > 0 else 0.0
+    label = "1e%d" % round(lg) if abs(lg - round(lg)) < 1e-12 else str(n)
+    if args.workload == "laplace_clustered":
+        return "laplace_clustered_%s" % label
+    return args.workload if args.n == 0 else "%s_n%s" % (args.workload, label)
 
 
 def peaks():
@@ -157,8 +175,75 @@ def cpu_direct_sample(prob, ntargets, seed=12345):
 
 
 def reference_targets(prob):
-    """Targets per timed oracle step: about 1.2e9 target-source pairs, at most all targets."""
-    return int(min(prob.X.shape[0], max(64, 1.2e9 // prob.Y.shape[0])))
+    """Targets per timed oracle step: about 1.2e9 target-source pairs, at least 16, at most
+    all targets."""
+    return int(min(prob.X.shape[0], max(16, 1.2e9 // prob.Y.shape[0])))
+
+
+def as_f64(prob):
+    """The problem's coordinates and weights as FP64 arrays, converted once (the oracle
+    computes in FP64; float32 inputs are promoted exactly)."""
+    prob.X = np.ascontiguousarray(prob.X, dtype=np.float64)
+    prob.Y = np.ascontiguousarray(prob.Y, dtype=np.float64)
+    prob.w = np.ascontiguousarray(prob.w, dtype=np.float64)
+    return prob
+
+
+def cpu_legs(prob, args, vg):
+    """The oracle beside the GPU result vg (first right-hand side; (nx,) or (nx, 3) for the
+    gradient), on this host's cores:
+      - O1 (FP64 direct sum) on a seeded subset of targets with all cores: the rel-L2 error of
+        the GPU result there, and the baseline rate scaled to the full product; with
+        --cpu-targets 0 the subset is as large as fills --cpu-seconds (256..4096 targets,
+        sized from a 16-target probe);
+      - O1 with one core on a smaller subset (about a quarter of that time), scaled;
+      - O2 (the plain CPU FFM, plan + apply) on the 20,000-point Laplace sphere (the smallest
+        workload), with all cores and with one core."""
+    from oracle import oracle as O
+    from paper_1909_05600_gb300 import workloads as W
+    nx = prob.X.shape[0]
+    cores = O.nthreads()
+    ntg = args.cpu_targets
+    if ntg <= 0:
+        _, _, dtp, _ = cpu_direct_sample(prob, 16, seed=777)
+        ntg = int(min(4096, max(256, 16 * args.cpu_seconds / max(dtp, 1e-6))))
+    ntg = min(ntg, nx)
+    t, ref, dt, _ = cpu_direct_sample(prob, ntg)
+    if prob.kind == W.LAPLACE_GRAD:
+        vg = vg.T  # (nx, 3)
+        ref = ref[:, :3]
+    else:
+        ref = ref[:, 0]
+    err = float(np.linalg.norm(vg[t] - ref) / np.linalg.norm(ref))
+    nrhs = 1 if prob.u.ndim == 1 else prob.u.shape[1]
+    cpu = {"value": 1.0 / (dt * nx / len(t)), "unit": "applies/s", "cores": cores, "kind": "oracle",
+           "sample": "O1, FP64 direct sum over all %d sources for %d seeded targets and all %d right-hand sides "
+                     "(%.1f s), scaled to %d targets" % (prob.Y.shape[0], len(t), nrhs, dt, nx)}
+    # one core, a smaller seeded subset
+    n1 = max(4, int(len(t) * 0.25 / cores))
+    O.set_threads(1)
+    try:
+        _, _, dt1, _ = cpu_direct_sample(prob, n1, seed=4242)
+    finally:
+        O.set_threads(cores)
+    cpu["one_core"] = {"value": 1.0 / (dt1 * nx / n1), "unit": "applies/s", "cores": 1,
+                       "sample": "O1 for %d seeded targets (%.1f s), scaled to %d targets" % (n1, dt1, nx)}
+    # O2 on the smallest workload (plan + apply; FP64 per-pair operators)
+    small = as_f64(W.laplace_sphere(20000, seed=1))
+    o2 = {}
+    for nthr in (cores, 1):
+        O.set_threads(nthr)
+        try:
+            t0 = time.perf_counter()
+            O.ffm(small.X, small.Y, small.u, O.LAPLACE, 0.0, small.eps, w=small.w)
+            o2["cores_%d" % nthr] = {"value": 1.0 / (time.perf_counter() - t0), "unit": "applies/s",
+                                     "cores": nthr}
+        finally:
+            O.set_threads(cores)
+    cpu["o2_cpu_ffm"] = dict(o2, workload="laplace_sphere_20k", eps=small.eps,
+                             note="the plain CPU FFM (plan + apply) of the oracle; the headline workload is "
+                                  "far beyond its reach")
+    return err, len(t), cpu
 
 
 def repeat_applies(ffm, torch, prob, X, Y, w, u, flush, stream, reps, tune_cache=None, kw=None):
@@ -195,7 +280,7 @@ def run_reference(args, rank):
     sum over all sources for a bounded sample of targets, scaled to the full product."""
     if rank != 0:
         return
-    prob = make_problem(args.workload, 1, args.n)
+    prob = as_f64(make_problem(args.workload, 1, args.n))
     if args.eps > 0:
         prob.eps = args.eps
     n = prob.X.shape[0]
@@ -212,7 +297,7 @@ def run_reference(args, rank):
     line = {"impl": "reference", "metric": "FFM applies/s", "value": value, "unit": "applies/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": args.workload, "n": n, "k": prob.k, "eps": prob.eps},
+            "config": {"workload": workload_name(args, prob), "n": n, "k": prob.k, "eps": prob.eps},
             "cpu_baseline": {"value": value, "unit": "applies/s", "cores": cores, "kind": "oracle",
                              "sample": "FP64 direct sum over all %d sources for %d seeded targets per step, "
                                        "scaled to %d targets" % (n, ns, n)},
@@ -350,43 +435,72 @@ def roofline(prof, info, steps, clk, pk, pk_kind, workload):
 
 def run_serving(args):
     """Serving stream: requests with N log-uniform in [1e4, 2e6], Laplace or Helmholtz,
-    three geometries, eps in {1e-3, 1e-4}.  Three passes over the same requests (inputs
-    resident in HBM): the plain path (one stream, ffm_plan + ffm_apply + ffm_destroy in turn),
-    the server with every request queued at once (throughput), and the server fed by Poisson
-    arrivals at 0.8 x the plain path's capacity (latency p50 / p99)."""
+    three geometries, eps in {1e-3, 1e-4}; with --scenes S > 0 the requests share S scenes
+    (point sets, kernel, k, eps) and differ in their densities, so plans are reused and
+    same-scene requests merge into multi-RHS applies.  Inputs resident in HBM.  Passes over
+    the same requests:
+      - plain FP32: one stream, ffm_plan + ffm_apply + ffm_destroy in turn, with FP32 forced
+        on every plane-wave level, direct plane-wave sums and the CUDA-core transfer;
+      - single stream: the same loop with the default (mixed-precision, tensor-core, NUFFT)
+        kernels; its throughput is the capacity the arrival rates refer to;
+      - served, saturated: every request queued at once (continuous batching, plan cache,
+        multi-RHS merging, one stream per worker);
+      - served at Poisson arrival rates 0.5, 0.8 and 1.0 x capacity: p50 / p99 latency.
+    Device overlap = summed per-batch device time (CUDA events on each worker stream) over
+    the wall time of the pass.  Accuracy: rel-L2 vs the FP64 direct sum on sampled targets
+    of the first requests, for the plain FP32 and the served results."""
     import torch
+    from oracle import oracle as O
     from paper_1909_05600_gb300 import build, ffm, workloads as W
     from paper_1909_05600_gb300.serving import Request, Server, latency_stats
     build.build()
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
-    descs = W.serving_stream(args.requests)
+    descs = W.serving_stream(args.requests, scenes=args.scenes)
     t0 = time.perf_counter()
-    reqs = []
+    reqs, scene_pts, probs = [], {}, {}
     for d in descs:
-        pr = W.serving_problem(d)
+        if d["scene"] not in scene_pts:
+            pts = W.serving_points(d)
+            t = lambda a: torch.as_tensor(np.ascontiguousarray(a), device=dev)
+            scene_pts[d["scene"]] = (pts, t(pts[0]), t(pts[1]))
+        pts, tX, tY = scene_pts[d["scene"]]
+        pr = W.serving_problem(d, points=pts)
+        if len(probs) < args.err_requests:
+            probs[d["id"]] = pr
         t = lambda a: torch.as_tensor(np.ascontiguousarray(a), device=dev)
-        reqs.append(dict(rid=d["id"], key=(d["seed"], pr.kind, pr.k, pr.eps), nx=pr.X.shape[0], ny=pr.Y.shape[0],
-                         kind=pr.kind, k=pr.k, eps=pr.eps, X=t(pr.X), Y=t(pr.Y), w=t(pr.w), u=t(pr.u)))
+        reqs.append(dict(rid=d["id"], key=(d["scene"], pr.kind, pr.k, pr.eps), nx=pr.X.shape[0], ny=pr.Y.shape[0],
+                         kind=pr.kind, k=pr.k, eps=pr.eps, X=tX, Y=tY, w=t(pr.w), u=t(pr.u)))
     t_gen = time.perf_counter() - t0
     n_pts = sum(r["nx"] for r in reqs)
-    # plain path: one stream, requests in arrival order
     stream = torch.cuda.current_stream(dev)
     l0 = ffm.launch_count()
-    torch.cuda.synchronize()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    lat_plain = []
-    for r in reqs:
-        tq = time.perf_counter()
-        with ffm.Plan(r["X"], r["Y"], r["kind"], r["k"], r["eps"], weights=r["w"]) as p:
-            p.apply(r["u"])
+    plain_kw = dict(precision=ffm.PREC_F32, pw_transform=ffm.PW_DIRECT, lagrange_transfer=ffm.LAG_CUDA_CORES)
+
+    def one_stream(kw):
+        """Requests in arrival order on one stream; device-timed throughput, per-request
+        latency (plan + apply + destroy, synchronised), and the results of the first ones."""
         torch.cuda.synchronize()
-        lat_plain.append(1e3 * (time.perf_counter() - tq))
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    t_plain = ev0.elapsed_time(ev1) * 1e-3
-    cap = len(reqs) / t_plain
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        lat, res = [], {}
+        for r in reqs:
+            tq = time.perf_counter()
+            with ffm.Plan(r["X"], r["Y"], r["kind"], r["k"], r["eps"], weights=r["w"], **kw) as p:
+                v = p.apply(r["u"])
+            torch.cuda.synchronize()
+            lat.append(1e3 * (time.perf_counter() - tq))
+            if r["rid"] in probs:
+                res[r["rid"]] = v.cpu().numpy()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        t = ev0.elapsed_time(ev1) * 1e-3
+        return {"throughput_rps": len(reqs) / t, "p50_ms": float(np.percentile(lat, 50)),
+                "p99_ms": float(np.percentile(lat, 99))}, res
+
+    st_plain, res_plain = one_stream(plain_kw)
+    st_single, _ = one_stream({})
+    cap = st_single["throughput_rps"]
 
     def serve(rate):
         rng = np.random.default_rng(7)
@@ -403,21 +517,48 @@ def run_serving(args):
             srv.drain(len(objs), timeout=1800)
         finally:
             srv.close()
-        return latency_stats(objs), objs
+        st = latency_stats(objs)
+        st.update({"device_overlap": srv.device_ms * 1e-3 / st["wall_s"] if st.get("wall_s") else None,
+                   "batches": srv.batches, "plan_cache_hits": srv.cache.hits, "plan_cache_misses": srv.cache.misses})
+        if rate is not None:
+            st["rate_rps"] = rate
+        return st, objs
 
-    st_sat, _ = serve(None)
-    st_08, objs = serve(0.8 * cap)
+    st_sat, objs_sat = serve(None)
+    at = {}
+    for f in (0.5, 0.8, 1.0):
+        at["%.1f" % f], _ = serve(f * cap)
     launches = ffm.launch_count() - l0
+
+    def err(res_of):
+        e = []
+        for rid, pr in probs.items():
+            t = W.sample_targets(pr.X.shape[0], args.err_targets, seed=rid)
+            u = pr.u.astype(np.complex128) if np.iscomplexobj(pr.u) else pr.u.astype(np.float64)
+            ref = O.direct(pr.X, pr.Y, u, pr.kind, pr.k, w=pr.w, targets=t)[:, 0]
+            v = res_of(rid)
+            e.append({"rid": rid, "n": int(pr.X.shape[0]), "kernel": int(pr.kind), "eps": pr.eps,
+                      "err": float(np.linalg.norm(v[t] - ref) / np.linalg.norm(ref))})
+        return e
+
+    by_id = {o.rid: o for o in objs_sat}
+    err_plain = err(lambda rid: res_plain[rid])
+    err_served = err(lambda rid: by_id[rid].result.cpu().numpy())
     line = {"metric": "serving requests/s", "value": st_sat["throughput_rps"], "unit": "requests/s", "n_gpus": 1,
             "higher_is_better": True, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "serving_stream", "requests": len(reqs), "n_points_total": n_pts,
-                       "workers": args.workers, "generation_s": t_gen},
-            "plain": {"throughput_rps": cap, "p50_ms": float(np.percentile(lat_plain, 50)),
-                      "p99_ms": float(np.percentile(lat_plain, 99)),
-                      "path": "one stream, ffm_plan + ffm_apply + ffm_destroy per request"},
-            "served_saturated": st_sat, "served_at_0.8_capacity": dict(st_08, rate_rps=0.8 * cap),
-            "speedup_vs_plain": st_sat["throughput_rps"] / cap, "gpu_launches": launches,
-            "failed": [o.error for o in objs if o.error][:3]}
+            "config": {"workload": "serving_stream", "requests": len(reqs), "scenes": args.scenes,
+                       "n_points_total": n_pts, "workers": args.workers, "generation_s": t_gen},
+            "plain_fp32": dict(st_plain, path="one stream, plan + apply + destroy per request; FP32 forced on "
+                                              "plane-wave levels, direct plane-wave sums, CUDA-core transfer"),
+            "single_stream": dict(st_single, path="one stream, plan + apply + destroy per request, default kernels"),
+            "served_saturated": st_sat, "served_at_capacity_fraction": at,
+            "speedup_vs_plain_fp32": st_sat["throughput_rps"] / st_plain["throughput_rps"],
+            "speedup_vs_single_stream": st_sat["throughput_rps"] / cap,
+            "err_vs_fp64_direct": {"targets_per_request": args.err_targets, "plain_fp32": err_plain,
+                                   "served": err_served,
+                                   "max_err_over_eps": {"plain_fp32": max(x["err"] / x["eps"] for x in err_plain),
+                                                        "served": max(x["err"] / x["eps"] for x in err_served)}},
+            "gpu_launches": launches, "failed": [o.error for o in objs_sat if o.error][:3]}
     print(json.dumps(line), flush=True)
 
 
@@ -582,12 +723,12 @@ def main():
     with ffm.Plan(X, Y, prob.kind, prob.k, prob.eps, weights=w, autotune_cache=tune_cache, **kw) as p0:
         info = p0.info()
 
-    def timed(profiled):
-        """K steps between a barrier and synchronisations.  The unprofiled pass gives the
-        throughput; the profiled pass (the library brackets every kernel with two events)
-        gives each kernel's device time for the roofline.  Event records cost host time
-        per launch, which shows up as gaps between the many small kernels of a plan."""
-        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    def timed(profiled, nsteps):
+        """nsteps steps between a barrier and synchronisations.  The unprofiled pass (K steps)
+        gives the throughput; the profiled pass (the library brackets every kernel with two
+        events) gives each kernel's device time for the roofline.  Event records cost host
+        time per launch, which shows up as gaps between the many small kernels of a plan."""
+        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(nsteps)]
         clocks = Clocks(local)
         ffm.profile_reset()
         l0 = ffm.launch_count()
@@ -596,7 +737,7 @@ def main():
         torch.cuda.synchronize()
         clocks.start()
         vlast = None
-        for i in range(args.steps):
+        for i in range(nsteps):
             flush.zero_()  # L2 flush between steps, outside the step's events
             ffm.profile_enable(profiled)
             vlast, _ = step(ev[i])
@@ -610,13 +751,19 @@ def main():
         t_apply = sum(e[1].elapsed_time(e[2]) for e in ev)
         return vlast, t_plan, t_apply, clk, launches, (ffm.profile_read() if profiled else None)
 
-    vlast, t_plan, t_apply, clk, launches, _ = timed(False)
-    _, tp_plan, tp_apply, _, _, prof = timed(True)
-    rep = repeat_applies(ffm, torch, prob, X, Y, w, u, flush, stream, max(3, args.steps), tune_cache, kw)
+    vlast, t_plan, t_apply, clk, launches, _ = timed(False, args.steps)
+    # the profiled pass and the repeated applies take at most about 10 s each on large
+    # workloads (at least one step, at most K)
+    step_s = (t_plan + t_apply) * 1e-3 / args.steps
+    apply_s = t_apply * 1e-3 / args.steps
+    k_prof = max(1, min(args.steps, math.ceil(10.0 / max(step_s, 1e-9))))
+    _, tp_plan, tp_apply, _, _, prof = timed(True, k_prof)
+    reps = max(3, min(args.steps, math.ceil(5.0 / max(apply_s, 1e-9))))
+    rep = repeat_applies(ffm, torch, prob, X, Y, w, u, flush, stream, reps, tune_cache, kw)
     note = None
     if rejected(clk):
         note = "first timed run rejected (clock reasons %s); re-measured" % clk.get("reasons")
-        vlast, t_plan, t_apply, clk, launches, _ = timed(False)
+        vlast, t_plan, t_apply, clk, launches, _ = timed(False, args.steps)
     t_step, t_plan, t_apply = max_over_ranks([t_plan + t_apply, t_plan, t_apply], dist)
     value = whole_job_rate(args.steps, world, t_step)
     pk, pk_kind = peaks()
@@ -633,7 +780,7 @@ def main():
             kwh["aca_eps"] = kw["aca_eps"]
         vshape = tuple(uh.shape[:-1]) + ((3,) if prob.kind == W.LAPLACE_GRAD else ()) + (prob.X.shape[0],)
         vh = torch.empty(vshape, dtype=uh.dtype).pin_memory()
-        ke = max(2, args.steps // 2)
+        ke = max(2, min(args.steps // 2, math.ceil(15.0 / max(step_s, 1e-9))))
         ts = []
         for i in range(ke + 1):
             torch.cuda.synchronize()
@@ -653,31 +800,25 @@ def main():
 
     cpu = None
     err = None
+    err_targets = None
     if rank == 0 and not args.no_cpu_baseline:
         vg = vlast.cpu().numpy()
-        t, ref, dt, cores = cpu_direct_sample(prob, args.cpu_targets)
         if prob.kind == W.LAPLACE_GRAD:
-            vg = (vg if vg.ndim == 2 else vg[0]).T  # (nx, 3) of the first right-hand side
-            ref = ref[:, :3]
+            vg = vg if vg.ndim == 2 else vg[0]  # (3, nx) of the first right-hand side
         else:
             vg = vg if vg.ndim == 1 else vg[0]
-            ref = ref[:, 0]
-        err = float(np.linalg.norm(vg[t] - ref) / np.linalg.norm(ref))
-        cpu = {"value": 1.0 / (dt * prob.X.shape[0] / len(t)), "unit": "applies/s", "cores": cores,
-               "kind": "oracle",
-               "sample": "FP64 direct sum over all %d sources for %d seeded targets and all %d right-hand sides "
-                         "(%.1f s), scaled to %d targets"
-                         % (prob.Y.shape[0], len(t), nrhs, dt, prob.X.shape[0])}
+        err, err_targets, cpu = cpu_legs(as_f64(prob), args, vg)
 
     if rank == 0:
-        rl = roofline(prof, info, args.steps, clk, pk, pk_kind, args.workload)
-        kernels = {k: {"launches_per_step": v[0] / args.steps, "ms_per_step": v[1] / args.steps}
+        rl = roofline(prof, info, k_prof, clk, pk, pk_kind, args.workload)
+        kernels = {k: {"launches_per_step": v[0] / k_prof, "ms_per_step": v[1] / k_prof}
                    for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}
         line = {
             "metric": "FFM applies/s", "value": value, "unit": "applies/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_step / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": args.workload, "n_x": int(prob.X.shape[0]), "n_y": int(prob.Y.shape[0]),
+            "config": {"workload": workload_name(args, prob), "n_x": int(prob.X.shape[0]),
+                       "n_y": int(prob.Y.shape[0]),
                        "kernel": {0: "laplace", 1: "helmholtz", 2: "laplace_double_layer",
                                   3: "laplace_gradient"}[prob.kind],
                        "k": prob.k, "eps": prob.eps,
@@ -689,8 +830,8 @@ def main():
             "t_plan_ms": t_plan / args.steps, "t_apply_ms": t_apply / args.steps,
             "apply_only_per_s": args.steps * world / (t_apply * 1e-3),
             "repeat_apply": rep, "autotune": tune,
-            "profiled_pass_ms_per_step": (tp_plan + tp_apply) / args.steps,
-            "err_vs_fp64_direct": err, "err_targets": args.cpu_targets if err is not None else None,
+            "profiled_pass_ms_per_step": (tp_plan + tp_apply) / k_prof, "profiled_pass_steps": k_prof,
+            "err_vs_fp64_direct": err, "err_targets": err_targets,
             "roofline": rl, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": launches,
             "kernels": kernels,
             "plan": {"l_stop": info["l_stop"], "mode": info["mode"][:info["l_stop"] + 1],

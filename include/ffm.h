@@ -120,6 +120,15 @@ typedef struct {
                                    |T_t - A_t B_t^T|_F <= aca_eps |T_t|_F or rank 64, and the
                                    transfer applied as A_t (B_t^T u~) (two GEMMs per translation);
                                    must be < 1; FFM_EUNSUPPORTED for the other kernels */
+    int wait_tries;             /* attempts of each bounded device-side wait (the mbarrier waits
+                                   of the tensor-core transfer kernels) before it gives up and
+                                   the plan reports FFM_ETIMEOUT: 0 -> 2^24; > 0 -> that many;
+                                   -1 -> none, every such wait gives up at once (a host-side way
+                                   to exercise the failure path; results are then discarded).
+                                   A kernel that gave up still waits for the tensor-core work
+                                   it had committed before it frees TMEM, so a timed-out plan
+                                   leaves the device usable; its results are unspecified and the
+                                   plan should be destroyed */
 } ffm_opts;
 
 /* Build a plan for targets X (nx points) and sources Y (ny points) (Sec. 2.2.1-2.2.4):
@@ -270,15 +279,19 @@ int ffm_profile_read(char *names, uint64_t *launches, double *ms, int cap);
  *   n        : 1 <= n <= 262144; larger n returns FFM_EINVAL (the scratch is fixed).
  *   perm_out : n uint32 DEVICE entries; receives sorted position -> original index, the
  *              same order ffm_plan gives X when called with Y = X (bounding cube, FP64
- *              quantisation, 63-bit Morton key, ties by original index).
- *   stream   : cudaStream_t; the call only enqueues work.
+ *              quantisation, 63-bit Morton key, ties by original index).  If any
+ *              coordinate is NaN or infinite (which ffm_plan refuses with FFM_EINVAL),
+ *              every entry is set to 0xFFFFFFFF instead: the call does not synchronise,
+ *              so that error is reported in the output, once the stream has run.
+ *   stream   : cudaStream_t of the current device; the call only enqueues work.
  * Scratch: one file-scope device array of about 6.3 MB (keys, indices, histograms, cube),
  * reserved on every GPU that loads the library until the process exits; no cudaMalloc,
  * cudaFree or allocating library call is made.  The first call on each device resolves
  * the array's device address (cudaGetSymbolAddress), so make that first call before any
  * stream capture.  All calls share the array: calls whose work overlaps on the GPU (other
  * streams, other threads) race and must be serialised by the caller.
- * Errors: FFM_EINVAL (NULL or host pointers, bad dtype, n out of range), FFM_ECUDA. */
+ * Errors: FFM_EINVAL (NULL or host pointers, memory of another device, bad dtype, n out
+ * of range), FFM_ECUDA. */
 ffm_status ffm_morton_order_noalloc(const void *X, ffm_dtype xdt, int64_t n, uint32_t *perm_out, void *stream);
 
 /* ---- Boundary-element wrapper (Sec. 4.2): the Galerkin matrix of a boundary integral operator

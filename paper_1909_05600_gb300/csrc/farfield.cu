@@ -395,14 +395,30 @@ __device__ __forceinline__ void cp_async16(void *dst, const void *src) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
 }
 
-// Bounded wait for the completion of phase `parity` of an mbarrier; false if it gave up.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+// Bounded wait for the completion of phase `parity` of an mbarrier: at most `tries`
+// try_wait attempts (none for tries <= 0); false if it gave up.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int tries) {
     uint32_t done = 0;
-    for (int it = 0; it < (1 << 24) && !done; ++it)
+    for (int it = 0; it < tries && !done; ++it)
         asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
                      : "=r"(done)
                      : "r"(smem_addr(bar)), "r"(parity));
     return done != 0;
+}
+
+// After a wait has given up, a kernel still waits for the tensor-core operations it has
+// already committed before it releases TMEM and exits (they read its shared memory and
+// write its TMEM columns); that wait is bounded too, by this larger count.
+constexpr int DRAIN_TRIES = 1 << 28;
+
+// Wait for committed tensor-core work (its commit arrives on `bar`): at most `tries`
+// attempts; after a give-up, recorded in ok, the wait goes on up to DRAIN_TRIES, because
+// the MMAs still read the stage and write TMEM.
+__device__ __forceinline__ void mma_wait(uint64_t *bar, uint32_t parity, int tries, bool &ok) {
+    if (!mbar_wait(bar, parity, tries)) {
+        ok = false;
+        mbar_wait(bar, parity, DRAIN_TRIES);
+    }
 }
 
 __device__ __forceinline__ void store_split(float *hi, float *lo, uint32_t o, float4 x) {
@@ -436,7 +452,7 @@ __global__ void __launch_bounds__(256) k_lag_gemm_tc(const uint32_t *__restrict_
                                                      int64_t tstride, int ostride, int nout, int rkp, int npad,
                                                      int tcols, int nrhs,
                                                      const float *__restrict__ up, float *__restrict__ vt,
-                                                     int *__restrict__ err) {
+                                                     int *__restrict__ err, int tries) {
     constexpr int C4 = KT / 4;  // 16-byte segments per row and chunk
     constexpr int NP = 224;     // copying threads (warps 1-7)
     extern __shared__ __align__(1024) unsigned char smem[];
@@ -503,7 +519,12 @@ __global__ void __launch_bounds__(256) k_lag_gemm_tc(const uint32_t *__restrict_
             asm volatile("cp.async.commit_group;" ::: "memory");
             asm volatile("cp.async.wait_group %0;" ::"n"(NR - 1) : "memory");  // chunk kn's segments landed
             const int b = kn % NO;
-            if (kn >= NO) ok = mbar_wait(&s_empty[b], (uint32_t)((kn / NO - 1) & 1)) && ok;  // MMAs of kn - NO done
+            // MMAs of kn - NO done; a thread that gives up stops copying (its copies in
+            // flight are awaited below)
+            if (kn >= NO && !mbar_wait(&s_empty[b], (uint32_t)((kn / NO - 1) & 1), tries)) {
+                ok = false;
+                break;
+            }
             const float *raw = raw0 + (size_t)(kn % NR) * raw_f;
             float *sAh = op0 + (size_t)b * op_f, *sAl = sAh + TC_P * KT, *sBh = sAl + TC_P * KT,
                   *sBl = sBh + npad * KT;
@@ -520,9 +541,13 @@ __global__ void __launch_bounds__(256) k_lag_gemm_tc(const uint32_t *__restrict_
         }
     } else if (lane == 0) {
         // ---- MMA thread
+        int issued = 0;  // chunks whose MMAs were committed
         for (int kc = 0; kc < nk; ++kc) {
             const int b = kc % NO;
-            ok = mbar_wait(&s_full[b], (uint32_t)((kc / NO) & 1)) && ok;
+            if (!mbar_wait(&s_full[b], (uint32_t)((kc / NO) & 1), tries)) {
+                ok = false;  // operands not ready: issue nothing more
+                break;
+            }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             float *sAh = op0 + (size_t)b * op_f, *sAl = sAh + TC_P * KT, *sBh = sAl + TC_P * KT,
                   *sBl = sBh + npad * KT;
@@ -549,9 +574,19 @@ __global__ void __launch_bounds__(256) k_lag_gemm_tc(const uint32_t *__restrict_
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                              smem_addr(&s_empty[b]))
                          : "memory");
+            issued = kc + 1;
         }
-        // the last chunk's MMAs complete after all earlier ones
-        ok = mbar_wait(&s_empty[(nk - 1) % NO], (uint32_t)(((nk - 1) / NO) & 1)) && ok;
+        // the last committed chunk's MMAs complete after all earlier ones; after a give-up
+        // this wait (bounded by DRAIN_TRIES) keeps TMEM and the operand ring owned until
+        // every committed MMA has finished
+        if (issued > 0) {
+            uint64_t *last = &s_empty[(issued - 1) % NO];
+            const uint32_t par = (uint32_t)(((issued - 1) / NO) & 1);
+            if (!ok || !mbar_wait(last, par, tries)) {
+                ok = false;
+                mbar_wait(last, par, DRAIN_TRIES);
+            }
+        }
     }
     if (warp >= 1) asm volatile("cp.async.wait_all;" ::: "memory");
     if (!ok) s_bad = 1;
@@ -559,10 +594,11 @@ __global__ void __launch_bounds__(256) k_lag_gemm_tc(const uint32_t *__restrict_
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     ok = s_bad == 0;
     if (!ok && tid == 0) atomicOr(err, 1);
-    // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 of half w / 4; columns = target nodes
+    // epilogue (skipped after a give-up: the accumulators are incomplete): warp w reads TMEM
+    // lanes 32 (w % 4) .. + 31 of half w / 4; columns = target nodes
     const int h = warp >> 2, quarter = warp & 3;
     const int p = h * 128 + quarter * 32 + lane;
-    if (h < nh) {
+    if (ok && h < nh) {
         float *dst = vt + ((size_t)s_tgt[p] * nrhs + m) * ostride;
         for (int c0 = 0; c0 < npad; c0 += 8) {
             uint32_t v[8];
@@ -571,7 +607,7 @@ __global__ void __launch_bounds__(256) k_lag_gemm_tc(const uint32_t *__restrict_
                          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
                          : "r"(addr));
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            if (ok && p < np) {
+            if (p < np) {
                 if ((ostride & 3) == 0 && c0 + 8 <= nout) {
                     atomicAdd(reinterpret_cast<float4 *>(dst + c0),
                               make_float4(__uint_as_float(v[0]), __uint_as_float(v[1]), __uint_as_float(v[2]),
@@ -638,7 +674,7 @@ __global__ void __launch_bounds__(2 * TS_M) k_lag_gemm_ts(const uint32_t *__rest
                                                          const uint32_t *__restrict__ adm_t, int n_trans,
                                                          const float *__restrict__ Tsp, int r, int nrhs,
                                                          const float *__restrict__ ut, float *__restrict__ vt,
-                                                         int *__restrict__ err) {
+                                                         int *__restrict__ err, int tries) {
     extern __shared__ __align__(1024) unsigned char smem[];
     float *stage0 = reinterpret_cast<float *>(smem);
     __shared__ uint32_t s_bits[TS_MAXT / 32];
@@ -691,12 +727,12 @@ __global__ void __launch_bounds__(2 * TS_M) k_lag_gemm_ts(const uint32_t *__rest
     auto drain = [&]() {
         if (g >= g0 + 2) {
             int st = (g - 2) & 1;
-            ok &= mbar_wait(&s_mbar[st], parity[st]);
+            mma_wait(&s_mbar[st], parity[st], tries, ok);
             parity[st] ^= 1u;
         }
         if (g >= g0 + 1) {
             int st = (g - 1) & 1;
-            ok &= mbar_wait(&s_mbar[st], parity[st]);
+            mma_wait(&s_mbar[st], parity[st], tries, ok);
             parity[st] ^= 1u;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -726,7 +762,7 @@ __global__ void __launch_bounds__(2 * TS_M) k_lag_gemm_ts(const uint32_t *__rest
             float *S = stage0 + st * TS_STAGE;
             // the stage was last read by the MMAs of translation g - 2
             if (g >= g0 + 2) {
-                ok &= mbar_wait(&s_mbar[st], parity[st]);
+                mma_wait(&s_mbar[st], parity[st], tries, ok);
                 parity[st] ^= 1u;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             }
@@ -941,17 +977,14 @@ void split_pad(const float *src, int64_t nmat, int rows, int cols, int rows_pad,
 // of rkp floats (zero past `rows`); v~ rows are ostride floats apart.
 static void tc_transfer(const FarLevel &F, const uint32_t *src, const uint32_t *tgt, const float *Tp, int64_t tstride,
                         int rows, int rkp, int ostride, int nrhs, const float *up, float *vt, int *err,
-                        cudaStream_t s) {
+                        int tries, cudaStream_t s) {
     constexpr int KT = 16, NR = 3, NO = 2;
     auto smem_of = [](int np_) {
         return (size_t)NO * (2 * TC_P * KT + 2 * np_ * KT) * sizeof(float) + (size_t)NR * (TC_P + np_) * KT * sizeof(float);
     };
-    static bool attr = false;
-    if (!attr) {
-        FFM_CUDA(cudaFuncSetAttribute(k_lag_gemm_tc<KT, NR, NO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)smem_of(224)));
-        attr = true;
-    }
+    // per device and cheap: set before every launch (plans may live on several devices)
+    FFM_CUDA(cudaFuncSetAttribute(k_lag_gemm_tc<KT, NR, NO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem_of(224)));
     const int npad = (rows + 15) / 16 * 16, parts = cdiv(npad, 224);
     const int nb = (cdiv(npad, parts) + 15) / 16 * 16;
     for (int row0 = 0; row0 < npad; row0 += nb) {
@@ -960,7 +993,7 @@ static void tc_transfer(const FarLevel &F, const uint32_t *src, const uint32_t *
         while (tcols < nbk) tcols <<= 1;
         FFM_LAUNCH((k_lag_gemm_tc<KT, NR, NO>), dim3((unsigned)F.tc_tiles, nrhs), 256, smem_of(nbk), s, F.tc_tile_t,
                    F.tc_tile_p0, F.bt_off, src, tgt, Tp + (size_t)row0 * rkp, tstride, ostride, nout, rkp, nbk, tcols,
-                   nrhs, up, vt + row0, err);
+                   nrhs, up, vt + row0, err, tries);
     }
 }
 
@@ -1003,9 +1036,9 @@ void far_lagrange(const ffm_plan_s *p, int l, const void *q, int nrhs, float2 *a
                 float *upad = tmp.get<float>((size_t)nrow * F.rkp);
                 split_pad((const float *)ut, 1, (int)nrow, r, (int)nrow, F.rkp, upad, nullptr, s);
                 tc_transfer(F, F.bt_src, F.pair_id, F.Bca, (int64_t)rp * F.rkp, rp, F.rkp, rp, nrhs, upad, w,
-                            p->dev_err, s);
+                            p->dev_err, p->wait_tries, s);
                 tc_transfer(F, F.pair_id, F.bt_tgt, F.Aca, (int64_t)npad * rp, r, rp, r, nrhs, w, (float *)vt,
-                            p->dev_err, s);
+                            p->dev_err, p->wait_tries, s);
                 tmp.drop(upad);
             } else {
                 dim3 g1((unsigned)F.n_tiles, cdiv(rp, LG_BM), nrhs);
@@ -1036,20 +1069,16 @@ void far_lagrange(const ffm_plan_s *p, int l, const void *q, int nrhs, float2 *a
             float *vtd = (float *)vt + d * vblk;
         if (F.ts_ok && F.Tsp && F.tune_tc == 2) {
             size_t smem = (size_t)2 * TS_STAGE * sizeof(float);
-            static bool attr_ts = false;
-            if (!attr_ts) {
-                FFM_CUDA(cudaFuncSetAttribute(k_lag_gemm_ts, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-                attr_ts = true;
-            }
+            FFM_CUDA(cudaFuncSetAttribute(k_lag_gemm_ts, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
             dim3 gts(cdiv(F.n_tgt, TS_M), nrhs);
             FFM_LAUNCH(k_lag_gemm_ts, gts, 2 * TS_M, smem, s, F.tgt, F.n_tgt, F.adm_off, F.adm_src, F.adm_t, F.n_trans,
-                       F.Tsp, r, nrhs, (const float *)ut, vtd, p->dev_err);
+                       F.Tsp, r, nrhs, (const float *)ut, vtd, p->dev_err, p->wait_tries);
         } else if (use_tc) {
             // tensor cores: 256-pair tiles, K chunks of 16 source nodes, row blocks of <= 224
             const int rkp = F.rkp;
             const size_t dsz = (size_t)F.n_trans * npad * rkp;
             tc_transfer(F, F.bt_src, F.bt_tgt, F.Tsh + d * dsz, (int64_t)npad * rkp, r, rkp, r, nrhs, upad, vtd,
-                        p->dev_err, s);
+                        p->dev_err, p->wait_tries, s);
         } else {
             FFM_LAUNCH(k_lag_gemm<false>, gg, LG_T, 0, s, F.tile_t, F.tile_p0, F.bt_off, F.bt_src, F.bt_tgt, Td, r,
                        rk, nrhs, (const float *)ut, vtd);

@@ -1,6 +1,7 @@
 // C ABI of libffm_gb300.so (include/ffm.h): argument checks, host/device staging, the
 // apply sequence (gather w u in Morton order, far field per level, near field, FP64
 // per-target accumulation, scatter to the caller's order) and plan introspection.
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -105,18 +106,23 @@ void Alloc::release() {
     bytes = 0;
 }
 
+// The default pool of each device keeps freed memory (stream-ordered frees of one product
+// are reused by the next); set once per device.
 static void keep_pool_memory() {
-    static bool done = false;
-    if (done) return;
+    static std::atomic<bool> done[64];
     int dev = 0;
-    cudaGetDevice(&dev);
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+        cudaGetLastError();
+        return;
+    }
+    if (done[dev].load()) return;
     cudaMemPool_t pool;
     if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
         uint64_t thr = UINT64_MAX;
         cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
     }
     cudaGetLastError();
-    done = true;
+    done[dev].store(true);
 }
 
 static bool is_device_ptr(const void *p) {
@@ -327,7 +333,7 @@ ffm_status ffm_plan(const void *X, ffm_dtype xdt, int64_t nx, const void *Y, ffm
                 opts->r1_override < 0 || opts->r1_override > R1MAX || opts->r1_override == 1 ||
                 opts->precision < FFM_PREC_AUTO || opts->precision > FFM_PREC_F32X2 ||
                 opts->lagrange_transfer < 0 || opts->lagrange_transfer > 3 || opts->pw_transform < 0 ||
-                opts->pw_transform > 2 || !(opts->aca_eps >= 0.0 && opts->aca_eps < 1.0))
+                opts->pw_transform > 2 || !(opts->aca_eps >= 0.0 && opts->aca_eps < 1.0) || opts->wait_tries < -1)
                 fail(FFM_EINVAL, "bad option value");
             if (opts->aca_eps > 0.0 && kernel != FFM_LAPLACE)
                 fail(FFM_EUNSUPPORTED, "the ACA transfer is built for the Laplace single layer");
@@ -339,6 +345,7 @@ ffm_status ffm_plan(const void *X, ffm_dtype xdt, int64_t nx, const void *Y, ffm
             p->lag_transfer = opts->lagrange_transfer;
             p->pw_transform = opts->pw_transform;
             p->aca_eps = opts->aca_eps;
+            if (opts->wait_tries != 0) p->wait_tries = opts->wait_tries < 0 ? 0 : opts->wait_tries;
             w = opts->weights;
             wdt = opts->weights_dtype;
             if (w && wdt != FFM_F32 && wdt != FFM_F64) fail(FFM_EINVAL, "weights dtype must be FFM_F32 or FFM_F64");

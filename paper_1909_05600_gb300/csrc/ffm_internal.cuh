@@ -247,6 +247,7 @@ struct ffm_plan_s {
     int64_t n_items = 0;            // near-field work items (target chunk x bounded source range)
     int4 *items = nullptr;          // (target leaf, first target in the leaf, first pair, end pair)
     int *dev_err = nullptr;         // device-side error flags (bounded waits that gave up)
+    int wait_tries = 1 << 24;       // try_wait attempts per bounded device-side wait (ffm_opts.wait_tries)
     ffm_info info{};
 };
 

@@ -26,13 +26,15 @@ constexpr int TILE = T * ITEMS;
 constexpr int MAX_BLOCKS = (int)((MAX_POINTS + TILE - 1) / TILE);
 
 // Scratch layout (bytes): two key buffers, two index buffers, digit histograms,
-// the cube extent (min/max as ordered integers), the cube (origin, edge).
+// the cube extent (min/max as ordered integers), the cube (origin, edge), and a flag
+// raised when a coordinate is not finite.
 struct Scratch {
     unsigned long long keys[2][MAX_POINTS];
     uint32_t vals[2][MAX_POINTS];
     uint32_t hist[256 * MAX_BLOCKS];
     unsigned long long ext[6];
     double cube[4];
+    unsigned int nonfinite;
 };
 
 static __device__ __align__(256) unsigned char g_scratch[sizeof(Scratch)];
@@ -51,17 +53,22 @@ __global__ void k_ext_init(Scratch *S) {
         S->ext[threadIdx.x] = ~0ull;
         S->ext[3 + threadIdx.x] = 0ull;
     }
+    if (threadIdx.x == 0) S->nonfinite = 0u;
 }
 
 template <class P>
 __global__ void k_ext(const P *__restrict__ X, int64_t n, Scratch *S) {
     double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    bool bad = false;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         for (int d = 0; d < 3; ++d) {
             double x = (double)X[3 * i + d];
+            bad |= !isfinite(x);
             lo[d] = fmin(lo[d], x);
             hi[d] = fmax(hi[d], x);
         }
+    // a NaN or an infinity has no place in the cube: the call's output is poisoned instead
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(&S->nonfinite, 1u);
     for (int d = 0; d < 3; ++d)
         for (int off = 16; off; off >>= 1) {
             lo[d] = fmin(lo[d], __shfl_xor_sync(0xffffffffu, lo[d], off));
@@ -202,9 +209,12 @@ __global__ void __launch_bounds__(T) k_scatter(const unsigned long long *__restr
     }
 }
 
-__global__ void k_copy_perm(const uint32_t *__restrict__ v, int64_t n, uint32_t *__restrict__ out) {
+// The sorted indices to the caller's array; every entry 0xFFFFFFFF when a coordinate was
+// not finite (the call only enqueues work, so the error travels with the output).
+__global__ void k_copy_perm(const uint32_t *__restrict__ v, int64_t n, const Scratch *S,
+                            uint32_t *__restrict__ out) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) out[i] = v[i];
+    if (i < n) out[i] = S->nonfinite ? 0xFFFFFFFFu : v[i];
 }
 
 // Device address of the scratch array, resolved once per device.
@@ -247,7 +257,7 @@ static void run(const void *X, int64_t n, uint32_t *perm, cudaStream_t s) {
         FFM_LAUNCH(k_scatter, nblk, T, 0, s, kb[cur], vb[cur], n, shift, hist, nblk, kb[1 - cur], vb[1 - cur]);
         cur = 1 - cur;
     }
-    FFM_LAUNCH(k_copy_perm, cdiv(n, 256), 256, 0, s, vb[cur], n, perm);
+    FFM_LAUNCH(k_copy_perm, cdiv(n, 256), 256, 0, s, vb[cur], n, S, perm);
 }
 
 }  // namespace noalloc
@@ -261,6 +271,8 @@ extern "C" ffm_status ffm_morton_order_noalloc(const void *X, ffm_dtype xdt, int
         if (n < 1 || n > noalloc::MAX_POINTS)
             fail(FFM_EINVAL, "n must lie in [1, 262144] (size of the static scratch array)");
         if (xdt != FFM_F32 && xdt != FFM_F64) fail(FFM_EINVAL, "X dtype must be FFM_F32 or FFM_F64");
+        int dev = 0;
+        check_cuda(cudaGetDevice(&dev), "cudaGetDevice");
         for (const void *p : {X, (const void *)perm_out}) {
             cudaPointerAttributes a;
             if (cudaPointerGetAttributes(&a, p) != cudaSuccess ||
@@ -268,6 +280,8 @@ extern "C" ffm_status ffm_morton_order_noalloc(const void *X, ffm_dtype xdt, int
                 cudaGetLastError();
                 fail(FFM_EINVAL, "X and perm_out must be device memory");
             }
+            if (a.type == cudaMemoryTypeDevice && a.device != dev)
+                fail(FFM_EINVAL, "X and perm_out must be memory of the current device");
         }
         cudaStream_t s = (cudaStream_t)stream;
         if (xdt == FFM_F64)

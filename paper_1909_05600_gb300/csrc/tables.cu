@@ -567,11 +567,7 @@ static void build_aca(ffm_plan_s *p, int l, const double oxy[3], double dl, Tabl
     double *R = in_smem ? nullptr : tmp.get<double>((size_t)nt * r * r);
     double *Ad = tmp.get<double>((size_t)nt * kmax * r), *Bd = tmp.get<double>((size_t)nt * kmax * r);
     int *rank = tmp.get<int>(nt);
-    static bool attr = false;
-    if (!attr) {
-        FFM_CUDA(cudaFuncSetAttribute(k_lag_aca, cudaFuncAttributeMaxDynamicSharedMemorySize, 125 * 1024));
-        attr = true;
-    }
+    FFM_CUDA(cudaFuncSetAttribute(k_lag_aca, cudaFuncAttributeMaxDynamicSharedMemorySize, 125 * 1024));
     FFM_LAUNCH(k_lag_aca, nt, ACA_T, in_smem ? rbytes : 0, s, F.trans_m, g, p->aca_eps, kmax, in_smem, R, Ad, Bd,
                rank);
     std::vector<int> hr(nt);

@@ -49,7 +49,8 @@ class Opts(C.Structure):
     _fields_ = [("n_leaf", C.c_int), ("l_cap", C.c_int), ("kappa_switch", C.c_double), ("r1_override", C.c_int),
                 ("precision", C.c_int), ("weights", C.c_void_p), ("weights_dtype", C.c_int),
                 ("autotune_cache", C.c_char_p), ("lagrange_transfer", C.c_int), ("normals", C.c_void_p),
-                ("normals_dtype", C.c_int), ("pw_transform", C.c_int), ("aca_eps", C.c_double)]
+                ("normals_dtype", C.c_int), ("pw_transform", C.c_int), ("aca_eps", C.c_double),
+                ("wait_tries", C.c_int)]
 
 
 class Info(C.Structure):
@@ -243,8 +244,20 @@ class Graph:
 
 
 def morton_order_noalloc(X, perm_out, stream=None):
-    """ffm_morton_order_noalloc: Morton ordering of X (device) into perm_out (device uint32),
-    without any device allocation inside the library."""
+    """ffm_morton_order_noalloc: Morton ordering of X (n x 3, device) into perm_out (n int32 or
+    uint32 entries, device), without any device allocation inside the library.  Every entry
+    of perm_out is 0xFFFFFFFF once the stream has run if a coordinate was not finite."""
+    if torch is None or not isinstance(X, torch.Tensor) or not isinstance(perm_out, torch.Tensor):
+        raise TypeError("X and perm_out must be CUDA tensors")
+    n = int(X.shape[0])
+    if X.dim() != 2 or X.shape[1] != 3:
+        raise ValueError("X must have shape (n, 3)")
+    ok_dt = (torch.int32,) + ((torch.uint32,) if hasattr(torch, "uint32") else ())
+    if perm_out.dtype not in ok_dt or perm_out.numel() < n:
+        raise ValueError("perm_out must hold at least n 32-bit integers")
+    cur = torch.cuda.current_device()
+    if not (X.is_cuda and perm_out.is_cuda and X.device.index == cur and perm_out.device.index == cur):
+        raise ValueError("X and perm_out must be on the current CUDA device")
     _check(lib().ffm_morton_order_noalloc(_ptr(X), _dtype_code(X), int(X.shape[0]), _ptr(perm_out),
                                           _stream_of(X, stream=stream)))
     return perm_out
@@ -259,16 +272,18 @@ class Plan:
 
     def __init__(self, X, Y, kernel, k=0.0, eps=1e-3, weights=None, stream=None, n_leaf=0, l_cap=0,
                  kappa_switch=0.0, r1_override=0, precision=PREC_AUTO, autotune_cache=None,
-                 lagrange_transfer=0, normals=None, pw_transform=PW_AUTO, aca_eps=0.0):
+                 lagrange_transfer=0, normals=None, pw_transform=PW_AUTO, aca_eps=0.0, wait_tries=0):
         """normals: (ny, 3) source normals, required for LAPLACE_DL (double layer).
         pw_transform: PW_AUTO, PW_DIRECT or PW_NUFFT for the plane-wave levels' F steps.
         aca_eps: LAPLACE only; > 0 replaces each transfer matrix by its adaptive cross
-        approximation to that Frobenius tolerance (eq. 11)."""
+        approximation to that Frobenius tolerance (eq. 11).
+        wait_tries: attempts per bounded device-side wait (0: the default; -1: none, so the
+        failure path runs and info() raises FFM_ETIMEOUT)."""
         self._h = None
         self._keep = (X, Y, weights, normals)
         o = Opts(n_leaf, l_cap, float(kappa_switch), r1_override, int(precision), None, F64,
                  autotune_cache.encode() if autotune_cache else None, int(lagrange_transfer), None, F64,
-                 int(pw_transform), float(aca_eps))
+                 int(pw_transform), float(aca_eps), int(wait_tries))
         if normals is not None:
             o.normals = _ptr(normals)
             o.normals_dtype = _dtype_code(normals)

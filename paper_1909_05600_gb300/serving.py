@@ -39,24 +39,36 @@ class Request:
     batch: int = 1
 
 
-def footprint_bytes(nx, ny, kind, nrhs=1):
-    """Conservative device-memory estimate of one plan plus one apply.  The plan holds
-    ~120 B per point (keys, permutation, hi/lo coordinates, box tables, pair lists); an apply
-    holds w u, the FP64 accumulators and the per-level plane-wave arrays (~96 B per point
-    per right-hand side for Helmholtz)."""
+def apply_bytes(nx, ny, kind, nrhs=1):
+    """Device-memory estimate of the temporaries of one apply: w u in Morton order, the FP64
+    accumulators and the per-level coefficient arrays (~96 B per point per right-hand side
+    for Helmholtz, ~24 B for Laplace), plus a fixed allowance."""
     n = nx + ny
-    per_rhs = (96 if kind == 1 else 24) * n
-    return 160 * n + (64 << 20) + per_rhs * nrhs
+    return (16 << 20) + (96 if kind == 1 else 24) * n * nrhs
+
+
+def footprint_bytes(nx, ny, kind, nrhs=1):
+    """Conservative device-memory estimate of one plan plus one apply, for a plan that does
+    not exist yet.  The plan holds ~160 B per point (keys, permutation, hi/lo coordinates,
+    box tables, pair lists, operators); once it is built, ffm_plan_bytes gives the real
+    figure (Server corrects its reservation with it)."""
+    return 160 * (nx + ny) + (48 << 20) + apply_bytes(nx, ny, kind, nrhs)
 
 
 class Scheduler:
     """FIFO admission by memory footprint and free workers, with batching of queued
-    requests that share a plan key (up to max_batch right-hand sides)."""
+    requests that share a plan key (up to max_batch right-hand sides).
 
-    def __init__(self, budget_bytes, workers, max_batch=16):
+    footprint(req, nrhs) gives the bytes a batch of nrhs requests like req needs; by default
+    the plan-plus-apply estimate.  A server that keeps plans resident passes one that counts
+    only the apply for a resident plan, and corrects reservations with adjust() once a new
+    plan's real size is known."""
+
+    def __init__(self, budget_bytes, workers, max_batch=16, footprint=None):
         self.budget = budget_bytes
         self.workers = workers
         self.max_batch = max_batch
+        self.footprint = footprint or (lambda req, nrhs: footprint_bytes(req.nx, req.ny, req.kind, nrhs))
         self.queue = collections.deque()
         self.in_use = 0
         self.busy = 0
@@ -86,7 +98,14 @@ class Scheduler:
                     break
                 if r.key == head.key:
                     batch.append(r)
-            need = footprint_bytes(head.nx, head.ny, head.kind, len(batch))
+            # the largest prefix of the batch that fits (at least the head, which submit()
+            # checked against the whole budget): a merged batch too large for the free
+            # memory must not hold back a head that fits alone
+            while True:
+                need = self.footprint(head, len(batch))
+                if self.in_use + need <= self.budget or len(batch) == 1:
+                    break
+                batch.pop()
             if self.in_use + need > self.budget:
                 return None, 0
             for r in batch:
@@ -94,6 +113,13 @@ class Scheduler:
             self.in_use += need
             self.busy += 1
             return batch, need
+
+    def adjust(self, old, new):
+        """Replace a running batch's reservation of `old` bytes by `new` (the real size of
+        its plan is known once built); returns new."""
+        with self.lock:
+            self.in_use += new - old
+            return new
 
     def release(self, need):
         with self.lock:
@@ -114,6 +140,11 @@ class PlanCache:
         self.lock = threading.Lock()
         self.hits = 0
         self.misses = 0
+
+    def resident(self, key):
+        """True if a plan for key is cached (its bytes are already on the device)."""
+        with self.lock:
+            return key in self.plans
 
     def acquire(self, key, build):
         with self.lock:
@@ -187,8 +218,10 @@ class Server:
         torch.cuda.set_device(self.device)
         free, _ = torch.cuda.mem_get_info(self.device)
         self.budget = budget_bytes if budget_bytes is not None else int(0.5 * free)
-        self.sched = Scheduler(self.budget, workers, max_batch)
         self.cache = PlanCache(plan_cache_bytes if plan_cache_bytes is not None else int(0.25 * free))
+        self.sched = Scheduler(self.budget, workers, max_batch, footprint=self._footprint)
+        self.device_ms = 0.0  # summed device time of the batches (CUDA events on each worker stream)
+        self.batches = 0
         self.streams = [torch.cuda.Stream(self.device) for _ in range(workers)]
         self.done = []
         self.done_lock = threading.Lock()
@@ -207,23 +240,44 @@ class Server:
         with self.wake:
             self.wake.notify_all()
 
-    def _run_batch(self, batch, stream):
+    def _footprint(self, req, nrhs):
+        # a resident plan costs only its apply; a new one the estimate until it is built
+        if self.cache.resident(req.key):
+            return apply_bytes(req.nx, req.ny, req.kind, nrhs)
+        return footprint_bytes(req.nx, req.ny, req.kind, nrhs)
+
+    def _run_batch(self, batch, stream, res):
+        """Plan (or cached plan) and one apply of the batch on the worker's stream.  res[0] is
+        the batch's reservation; it is corrected to the plan's ffm_plan_bytes (plus the apply)
+        if the plan was built here."""
         torch, ffm = self.torch, self.ffm
         head = batch[0]
+        built = []
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         with torch.cuda.stream(stream):
             def build():
+                built.append(1)
                 return ffm.Plan(head.X, head.Y, head.kind, head.k, head.eps, weights=head.w, stream=stream)
+            ev0.record(stream)
             plan = self.cache.acquire(head.key, build)
             try:
+                if built:
+                    res[0] = self.sched.adjust(res[0], plan.bytes() + apply_bytes(head.nx, head.ny, head.kind,
+                                                                                  len(batch)))
                 if len(batch) == 1:
                     U = head.u
                 else:
                     U = torch.stack([r.u for r in batch], 0)
                 V = plan.apply(U, stream=stream)
+                ev1.record(stream)
                 stream.synchronize()
             finally:
                 self.cache.release(plan)
         t = time.perf_counter()
+        ms = ev0.elapsed_time(ev1)
+        with self.done_lock:
+            self.device_ms += ms
+            self.batches += 1
         for i, r in enumerate(batch):
             r.result = V if len(batch) == 1 else V[i]
             r.t_done = t
@@ -244,14 +298,15 @@ class Server:
             t0 = time.perf_counter()
             for r in batch:
                 r.t_admit = t0
+            res = [need]
             try:
-                self._run_batch(batch, stream)
+                self._run_batch(batch, stream, res)
             except Exception as e:  # report, keep serving
                 for r in batch:
                     r.error = str(e)
                     r.t_done = time.perf_counter()
             finally:
-                self.sched.release(need)
+                self.sched.release(res[0])
                 with self.done_lock:
                     self.done.extend(batch)
                 with self.wake:

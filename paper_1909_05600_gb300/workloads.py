@@ -138,39 +138,52 @@ def helmholtz_cube_multirhs(n=200_000, nrhs=64, seed=1, eps=1e-4, ppw=10.0):
 
 def laplace_clustered(n=100_000_000, seed=1, eps=1e-3):
     """Laplace on a mixture of 8 Gaussians (sigma 0.05, shared centres), X and Y
-    independent, u ~ U(-1, 1) float32, w = 1/n."""
-    X = gaussian_mixture(n, seed)
-    Y = gaussian_mixture(n, seed + 1000)
+    independent float32 point sets, u ~ U(-1, 1) float32, w = 1/n (float32)."""
+    X = gaussian_mixture(n, seed).astype(np.float32)
+    Y = gaussian_mixture(n, seed + 1000).astype(np.float32)
     u = np.random.default_rng(seed + 2000).uniform(-1.0, 1.0, n).astype(np.float32)
-    w = np.full(n, 1.0 / n)
+    w = np.full(n, 1.0 / n, dtype=np.float32)
     return Problem("laplace_clustered_%d" % n, X, Y, u, w, LAPLACE, 0.0, eps)
 
 
-def serving_stream(nreq=500, seed=7, nmin=10_000, nmax=2_000_000, rate_hz=10.0):
+def serving_stream(nreq=500, seed=7, nmin=10_000, nmax=2_000_000, rate_hz=10.0, scenes=0):
     """Request descriptors for the serving stream: Poisson arrivals, N log-uniform in
-    [nmin, nmax], kernel 50/50, geometry uniform over three shapes, eps in {1e-3, 1e-4}."""
+    [nmin, nmax], kernel 50/50, geometry uniform over three shapes, eps in {1e-3, 1e-4}.
+
+    scenes = 0: every request has its own point sets.  scenes = S > 0: S scenes (point sets,
+    kernel, k, eps) are drawn from the same distributions, and each request picks one of
+    them uniformly with a density of its own, as when clients apply one operator to many
+    right-hand sides; requests of one scene share a plan."""
     rng = np.random.default_rng(seed)
     t = np.cumsum(rng.exponential(1.0 / rate_hz, nreq))
-    ns = np.exp(rng.uniform(math.log(nmin), math.log(nmax), nreq)).astype(np.int64)
-    kinds = rng.integers(0, 2, nreq)
-    geos = rng.integers(0, 3, nreq)
-    epss = np.where(rng.integers(0, 2, nreq) == 0, 1e-3, 1e-4)
+    nd = scenes if scenes > 0 else nreq
+    ns = np.exp(rng.uniform(math.log(nmin), math.log(nmax), nd)).astype(np.int64)
+    kinds = rng.integers(0, 2, nd)
+    geos = rng.integers(0, 3, nd)
+    epss = np.where(rng.integers(0, 2, nd) == 0, 1e-3, 1e-4)
+    pick = rng.integers(0, nd, nreq) if scenes > 0 else np.arange(nreq)
     names = list(GEOMETRIES)
     out = []
     for i in range(nreq):
-        g = names[geos[i]]
-        out.append({"id": i, "t_arrival": float(t[i]), "n": int(ns[i]), "kind": int(kinds[i]), "geometry": g,
-                    "eps": float(epss[i]), "seed": int(seed * 100000 + i)})
+        c = int(pick[i])
+        out.append({"id": i, "t_arrival": float(t[i]), "n": int(ns[c]), "kind": int(kinds[c]),
+                    "geometry": names[geos[c]], "eps": float(epss[c]), "seed": int(seed * 100000 + c),
+                    "scene": c, "useed": int(seed * 100000 + 50000 + i) if scenes > 0 else None})
     return out
 
 
-def serving_problem(req):
-    """Materialise one serving request: X = Y drawn independently per set."""
+def serving_points(req):
+    """The point sets of a request's scene: X and Y drawn independently."""
+    g = req["geometry"]
+    return GEOMETRIES[g](req["n"], req["seed"]), GEOMETRIES[g](req["n"], req["seed"] + 1000)
+
+
+def serving_problem(req, points=None):
+    """Materialise one serving request (points: its scene's (X, Y) if already drawn)."""
     g = req["geometry"]
     n = req["n"]
-    X = GEOMETRIES[g](n, req["seed"])
-    Y = GEOMETRIES[g](n, req["seed"] + 1000)
-    rng = np.random.default_rng(req["seed"] + 2000)
+    X, Y = points if points is not None else serving_points(req)
+    rng = np.random.default_rng(req["useed"] if req.get("useed") is not None else req["seed"] + 2000)
     w = np.full(n, AREA[g] / n)
     if req["kind"] == LAPLACE:
         u = rng.standard_normal(n).astype(np.float32)

@@ -305,6 +305,21 @@ def test_full_size_helmholtz_sphere_1M_sampled_targets():
     assert O.rel_l2(v[t], ref) < prob.eps
 
 
+def test_clustered_laplace_10M_sampled_targets():
+    """The clustered Laplace workload (8 Gaussians, sigma 0.05, float32 points and densities)
+    at 10,000,000 + 10,000,000 points, in the default launch configuration: uneven leaves of
+    up to tens of thousands of near sources per target, checked on 512 seeded targets
+    against the FP64 direct sum."""
+    prob = W.laplace_clustered(10_000_000)
+    with gpu_plan(prob) as gp:
+        info = gp.info()
+        v = gpu_apply(gp, prob.u)
+    assert info["device_errors"] == 0 and info["p2p_pairs"] > 1e11
+    t = W.sample_targets(prob.X.shape[0], 512)
+    ref = O.direct(prob.X, prob.Y, prob.u.astype(np.float64), O.LAPLACE, 0.0, w=prob.w, targets=t)[:, 0].real
+    assert O.rel_l2(v[t], ref) < prob.eps
+
+
 def test_laplace_volume_eps_1e4_transfer_gemm():
     """Volume points with X = Y at eps = 1e-4: r1 = 6 (216 control nodes), transfers by the
     per-translation GEMM with 189 admissible partners per interior box."""

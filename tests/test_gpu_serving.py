@@ -48,6 +48,7 @@ def test_same_result_alone_and_in_a_mix():
         assert O.rel_l2(v, v0) < 1e-6, (r.rid, O.rel_l2(v, v0))
     st = latency_stats(reqs)
     assert st["completed"] == 4 and st["p99_ms"] >= st["p50_ms"] > 0
+    assert srv.batches >= 1 and srv.device_ms > 0
 
 
 def test_oversize_request_is_rejected_others_complete():

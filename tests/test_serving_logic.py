@@ -68,3 +68,41 @@ def test_plan_cache_lru_and_deferred_close():
     c.release(p4)
     c.clear()
     assert p1.closed and p4.closed
+
+
+def test_merged_batch_too_large_still_admits_the_head():
+    """A budget that fits one right-hand side but not the merged batch: the head (and as
+    many same-key requests as fit) must be admitted, not held back forever."""
+    one = footprint_bytes(1_000_000, 1_000_000, 1, 1)
+    two = footprint_bytes(1_000_000, 1_000_000, 1, 2)
+    s = Scheduler(budget_bytes=(one + two) // 2, workers=4, max_batch=16)
+    for i in range(6):
+        assert s.submit(req(i, "same", 1_000_000, 1))
+    b, n = s.next_batch()
+    assert b is not None and [r.rid for r in b] == [0] and n == one
+    s.release(n)
+    s2 = Scheduler(budget_bytes=footprint_bytes(1_000_000, 1_000_000, 1, 3), workers=4, max_batch=16)
+    for i in range(6):
+        s2.submit(req(i, "same", 1_000_000, 1))
+    b, n = s2.next_batch()
+    assert [r.rid for r in b] == [0, 1, 2]           # the largest prefix that fits
+
+
+def test_resident_plans_cost_only_their_apply_and_reservations_follow_real_plan_bytes():
+    from paper_1909_05600_gb300.serving import apply_bytes
+    resident = {"hot"}
+    fp = lambda r, nrhs: (apply_bytes(r.nx, r.ny, r.kind, nrhs) if r.key in resident
+                          else footprint_bytes(r.nx, r.ny, r.kind, nrhs))
+    budget = footprint_bytes(500_000, 500_000, 0, 1) + apply_bytes(500_000, 500_000, 0, 1)
+    s = Scheduler(budget_bytes=budget, workers=4, footprint=fp)
+    s.submit(req(0, "cold", 500_000))
+    s.submit(req(1, "hot", 500_000))
+    b0, n0 = s.next_batch()
+    b1, n1 = s.next_batch()                           # fits beside the cold plan: apply only
+    assert [r.rid for r in b0] == [0] and [r.rid for r in b1] == [1]
+    assert n1 == apply_bytes(500_000, 500_000, 0, 1)
+    real = s.adjust(n0, 12345)                        # the cold plan's real size once built
+    assert s.in_use == real + n1
+    s.release(real)
+    s.release(n1)
+    assert s.in_use == 0 and s.busy == 0

@@ -51,3 +51,45 @@ def test_noalloc_refuses_sizes_beyond_its_scratch():
     ffm.morton_order_noalloc(one, o1)
     torch.cuda.synchronize()
     assert int(o1.item()) == 0
+
+
+def test_noalloc_warm_call_allocates_nothing():
+    """Once the first call on the device has resolved the scratch address, a call must leave
+    the device's free memory exactly as it found it (no cudaMalloc, no allocating library
+    call, no lazily created buffer)."""
+    X = torch.as_tensor(W.gaussian_mixture(100000, 9), device="cuda")
+    out = torch.empty(X.shape[0], dtype=torch.int32, device="cuda")
+    ffm.morton_order_noalloc(X, out)  # warm: address resolution and module loading
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    stats0 = torch.cuda.memory_stats()
+    for _ in range(3):
+        ffm.morton_order_noalloc(X, out)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    stats1 = torch.cuda.memory_stats()
+    assert free1 == free0
+    assert stats1.get("allocation.all.allocated", 0) == stats0.get("allocation.all.allocated", 0)
+
+
+def test_noalloc_non_finite_coordinates_poison_the_output():
+    """A NaN or an infinite coordinate (refused by ffm_plan) sets every entry to 0xFFFFFFFF;
+    the next call on finite input, which reuses the shared scratch, is unaffected."""
+    Xn = W.sphere_surface(5000, 11)
+    good = torch.as_tensor(Xn, device="cuda")
+    for bad_value in (float("nan"), float("inf")):
+        Xb = Xn.copy()
+        Xb[1234, 1] = bad_value
+        bad = torch.as_tensor(Xb, device="cuda")
+        assert np.all(_noalloc_order(bad) == 0xFFFFFFFF)
+        assert np.array_equal(_noalloc_order(good), _plan_order(good))
+
+
+def test_noalloc_wrapper_checks_its_arguments():
+    X = torch.zeros((10, 3), dtype=torch.float64, device="cuda")
+    with pytest.raises(ValueError):
+        ffm.morton_order_noalloc(X, torch.empty(10, dtype=torch.int64, device="cuda"))
+    with pytest.raises(ValueError):
+        ffm.morton_order_noalloc(X, torch.empty(9, dtype=torch.int32, device="cuda"))
+    with pytest.raises(ValueError):
+        ffm.morton_order_noalloc(X[:, :2].contiguous(), torch.empty(10, dtype=torch.int32, device="cuda"))
