@@ -141,6 +141,15 @@ void set_items(ffm_plan_s *p, int tch, unsigned smax, Alloc &tmp, cudaStream_t s
 
 }  // namespace
 
+int cached_lag_pick(const ffm_plan_s *p, int l) {
+    if (p->tune_cache.empty()) return -1;
+    Cache cache(p->tune_cache.c_str());
+    std::string v;
+    int a = -1;
+    if (cache.get(lag_key(p, l, device_tag(), 1), v) && parse_lag(v, a)) return a;
+    return -1;
+}
+
 void apply_cached_picks(ffm_plan_s *p, const char *cache_path, cudaStream_t s) {
     Cache cache(cache_path);
     const std::string dev = device_tag();
@@ -230,6 +239,7 @@ void autotune(ffm_plan_s *p, int nrhs, const char *cache_path, cudaStream_t s) {
         std::string v;
         if (F.mode == 1) {
             int r = F.r1 * F.r1 * F.r1;
+            if (!helm && !F.aca) build_translation_groups(p, l, s);  // the per-translation candidates
             bool tc_ok = !helm && F.tc_tiles > 0 && !F.aca;
             if (!tc_ok) continue;
             std::string key = lag_key(p, l, dev, rhs_bucket(nrhs));

@@ -345,6 +345,7 @@ ffm_status ffm_plan(const void *X, ffm_dtype xdt, int64_t nx, const void *Y, ffm
             p->lag_transfer = opts->lagrange_transfer;
             p->pw_transform = opts->pw_transform;
             p->aca_eps = opts->aca_eps;
+            if (opts->autotune_cache) p->tune_cache = opts->autotune_cache;
             if (opts->wait_tries != 0) p->wait_tries = opts->wait_tries < 0 ? 0 : opts->wait_tries;
             w = opts->weights;
             wdt = opts->weights_dtype;

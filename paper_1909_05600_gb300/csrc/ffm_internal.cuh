@@ -248,6 +248,7 @@ struct ffm_plan_s {
     int4 *items = nullptr;          // (target leaf, first target in the leaf, first pair, end pair)
     int *dev_err = nullptr;         // device-side error flags (bounded waits that gave up)
     int wait_tries = 1 << 24;       // try_wait attempts per bounded device-side wait (ffm_opts.wait_tries)
+    std::string tune_cache;         // ffm_opts.autotune_cache (empty: none)
     ffm_info info{};
 };
 
@@ -258,6 +259,12 @@ void build_plan(ffm_plan_s *p, const void *X, ffm_dtype xdt, const void *Y, ffm_
 // tree.cu: partners sorted by translation and T pre-split for the target-stationary
 // transfer of Lagrange level l (on demand); tables.cu: the T split
 void prepare_target_stationary(ffm_plan_s *p, int l, cudaStream_t s);
+// tree.cu: pairs of Lagrange level l grouped by translation and the per-translation tiles
+// (on demand; no-op if present)
+void build_translation_groups(ffm_plan_s *p, int l, cudaStream_t s);
+// autotune.cu: the transfer variant stored for Lagrange level l in the plan's autotune
+// cache (0 CUDA cores, 1 tcgen05 per translation, 2 target-stationary), or -1
+int cached_lag_pick(const ffm_plan_s *p, int l);
 void launch_table_split(ffm_plan_s *p, int l, cudaStream_t s);
 
 // tree.cu: near-field work items with targets in chunks of tchunk and at most smax source

@@ -257,6 +257,265 @@ __global__ void __launch_bounds__(P2P_T) k_p2p(NearArgs N, const void *__restric
     }
 }
 
+// ---- Laplace single layer, one right-hand side: packed FP32 pairs
+//
+// Sources are staged per batch as FP32 structure-of-arrays in the target leaf's frame (hi
+// and lo parts of x, y, z, and w u).  A thread holds PT targets, each coordinate part
+// duplicated into both halves of a 64-bit register, and takes its sources four at a time
+// (one 16-byte shared load per array), so every arithmetic instruction is a packed f32x2
+// operation on two pairs: per coordinate the hi difference, the lo difference and their sum
+// ((x_hi - y_hi) + (x_lo - y_lo), exact in its hi part for nearby points), a multiply and two
+// fused multiply-adds for |x - y|^2, two hardware rsqrt, and one packed multiply-add into the
+// target's accumulator pair: 6.5 issue slots of FP32 arithmetic (13 FP32 operations) and one
+// special-function result per pair, against about 17 issue slots in the generic kernel.
+//
+// Coincident points: rsqrt of 0 is +inf, which makes the target's accumulator non-finite.
+// Each thread checks its accumulators after every batch and recomputes that batch for the
+// affected target with the pair test (pairs with |x - y|^2 below the smallest normal FP32
+// number contribute nothing, as in the generic kernel), starting again from the value it
+// had before the batch.
+__device__ __forceinline__ uint64_t f2_pack(float a, float b) {
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void f2_unpack(uint64_t v, float &a, float &b) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ uint64_t f2_add(uint64_t a, uint64_t b) {
+    uint64_t r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ uint64_t f2_sub(uint64_t a, uint64_t b) {
+    uint64_t r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ uint64_t f2_mul(uint64_t a, uint64_t b) {
+    uint64_t r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ uint64_t f2_fma(uint64_t a, uint64_t b, uint64_t c) {
+    uint64_t r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+
+constexpr int LAP_SB = 512;         // staged sources per batch (a multiple of 4)
+constexpr float LAP_FAR = 1.0e15f;  // coordinate of the padding sources (weight 0)
+
+// a target: hi and lo parts of each coordinate, duplicated in both halves
+struct Tgt2 {
+    uint64_t h[3], l[3];
+};
+// staged sources, structure of arrays: hi x, y, z, lo x, y, z, w u
+struct LapStage {
+    float4 a[7][LAP_SB / 4];
+};
+
+// Two pairs (sources a, b of one quad half) for one target: acc += w / |x - y| in both halves.
+template <bool GUARD>
+__device__ __forceinline__ uint64_t lap_two(const Tgt2 &x, const uint64_t *yh, const uint64_t *yl, uint64_t w,
+                                            uint64_t acc) {
+    uint64_t d[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) d[c] = f2_add(f2_sub(x.h[c], yh[c]), f2_sub(x.l[c], yl[c]));
+    uint64_t r2 = f2_fma(d[2], d[2], f2_fma(d[1], d[1], f2_mul(d[0], d[0])));
+    float ra, rb;
+    f2_unpack(r2, ra, rb);
+    float ia = rsqrt_hw(ra), ib = rsqrt_hw(rb);
+    if constexpr (GUARD) {
+        ia = ra >= 1.17549435e-38f ? ia : 0.f;
+        ib = rb >= 1.17549435e-38f ? ib : 0.f;
+    }
+    return f2_fma(w, f2_pack(ia, ib), acc);
+}
+
+template <bool GUARD, int PT>
+__device__ __forceinline__ void lap_quads(const LapStage &S, int q0, int q1, int qstep, const Tgt2 *X,
+                                          uint64_t *acc) {
+#pragma unroll 1
+    for (int q = q0; q < q1; q += qstep) {
+        float4 v[7];
+#pragma unroll
+        for (int c = 0; c < 7; ++c) v[c] = S.a[c][q];
+        uint64_t ha[3], hb[3], la[3], lb[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            ha[c] = f2_pack(v[c].x, v[c].y);
+            hb[c] = f2_pack(v[c].z, v[c].w);
+            la[c] = f2_pack(v[3 + c].x, v[3 + c].y);
+            lb[c] = f2_pack(v[3 + c].z, v[3 + c].w);
+        }
+        uint64_t wa = f2_pack(v[6].x, v[6].y), wb = f2_pack(v[6].z, v[6].w);
+#pragma unroll
+        for (int t = 0; t < PT; ++t) {
+            acc[t] = lap_two<GUARD>(X[t], ha, la, wa, acc[t]);
+            acc[t] = lap_two<GUARD>(X[t], hb, lb, wb, acc[t]);
+        }
+    }
+}
+
+template <int PT>
+__global__ void __launch_bounds__(P2P_T) k_p2p_lap(NearArgs N, const float *__restrict__ qv, int64_t nx,
+                                                   double2 *__restrict__ acc) {
+    __shared__ LapStage S;
+    __shared__ float red[P2P_T * PT];
+    int4 it = N.items[blockIdx.x];
+    int a = it.x;
+    uint32_t e0 = (uint32_t)it.z, e1 = (uint32_t)it.w;
+    uint32_t p0 = N.xl_start[a] + (uint32_t)it.y;
+    int np = min(N.tchunk, (int)(N.xl_start[a + 1] - p0));
+    int pr = min((np + PT - 1) / PT, P2P_T);  // threads per group
+    int G = P2P_T / pr;
+    int grp = threadIdx.x / pr, pi = threadIdx.x % pr;
+    bool active = grp < G;
+    int4 ga = N.xl_g[a];
+    Tgt2 X[PT];
+    uint64_t A[PT];
+#pragma unroll
+    for (int t = 0; t < PT; ++t) {
+        int i = pi + t * pr;
+        bool ok = active && i < np;
+        float4 xh = ok ? N.epsX[p0 + i] : make_float4(0.f, 0.f, 0.f, 0.f);
+        float4 xl = ok ? N.epsXlo[p0 + i] : make_float4(0.f, 0.f, 0.f, 0.f);
+        X[t].h[0] = f2_pack(xh.x, xh.x);
+        X[t].h[1] = f2_pack(xh.y, xh.y);
+        X[t].h[2] = f2_pack(xh.z, xh.z);
+        X[t].l[0] = f2_pack(xl.x, xl.x);
+        X[t].l[1] = f2_pack(xl.y, xl.y);
+        X[t].l[2] = f2_pack(xl.z, xl.z);
+        A[t] = 0ull;  // +0.0f in both halves
+    }
+    float *f[7];
+#pragma unroll
+    for (int c = 0; c < 7; ++c) f[c] = reinterpret_cast<float *>(S.a[c]);
+    auto run_batch = [&](int fill) {
+        // pad to whole quads with far, weightless sources
+        for (int j = fill + threadIdx.x; j < ((fill + 3) & ~3); j += P2P_T) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                f[c][j] = LAP_FAR;
+                f[3 + c][j] = 0.f;
+            }
+            f[6][j] = 0.f;
+        }
+        __syncthreads();
+        if (active) {
+            const int nq = (fill + 3) >> 2;
+            uint64_t save[PT];
+#pragma unroll
+            for (int t = 0; t < PT; ++t) save[t] = A[t];
+            lap_quads<false, PT>(S, grp, nq, G, X, A);
+#pragma unroll
+            for (int t = 0; t < PT; ++t) {
+                float u0, u1;
+                f2_unpack(A[t], u0, u1);
+                if (!isfinite(u0 + u1)) {  // a coincident pair: this batch again with the pair test
+                    uint64_t one[1] = {save[t]};
+                    lap_quads<true, 1>(S, grp, nq, G, &X[t], one);
+                    A[t] = one[0];
+                }
+            }
+        }
+        __syncthreads();
+    };
+    // Source leaves are taken P2P_T at a time: their start, size and centre offset are read
+    // and formed in parallel into a shared table (one thread per leaf), then every thread
+    // stages whichever sources of the batch fall to it, finding its leaf by a binary search
+    // of the table's prefix sums.  Near leaves of a few points each (fine levels of clustered
+    // inputs) are thus staged with all loads in flight at once, not one leaf after another.
+    __shared__ uint32_t lb_s0[P2P_T], lb_pre[P2P_T + 1];
+    __shared__ float lb_off[6][P2P_T];
+    int fill = 0;
+    for (uint32_t eg = e0; eg < e1; eg += P2P_T) {
+        const int ne = (int)min((uint32_t)P2P_T, e1 - eg);
+        uint32_t cnt = 0;
+        if ((int)threadIdx.x < ne) {
+            uint32_t b = N.src[eg + threadIdx.x];
+            uint32_t s0 = N.yl_start[b];
+            cnt = N.yl_start[b + 1] - s0;
+            Off3 oc = leaf_offset3(N, ga, N.yl_g[b]);
+            lb_s0[threadIdx.x] = s0;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                lb_off[c][threadIdx.x] = oc.h[c];
+                lb_off[3 + c][threadIdx.x] = oc.l[c];
+            }
+        }
+        // inclusive prefix of the leaf sizes (warp scans, then the warp totals)
+        {
+            __shared__ uint32_t wsum[P2P_T / 32];
+            const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+            uint32_t inc = cnt;
+            for (int o = 1; o < 32; o <<= 1) {
+                uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
+                if (lane >= o) inc += t;
+            }
+            if (lane == 31) wsum[warp] = inc;
+            __syncthreads();
+            for (int w = 0; w < warp; ++w) inc += wsum[w];
+            lb_pre[threadIdx.x + 1] = inc;
+            if (threadIdx.x == 0) lb_pre[0] = 0;
+            __syncthreads();
+        }
+        const int total = (int)lb_pre[ne];
+        for (int base = 0; base < total;) {
+            const int take = min(total - base, LAP_SB - fill);
+            for (int j = threadIdx.x; j < take; j += P2P_T) {
+                const int flat = base + j;
+                int lo = 0, hi = ne;  // leaf: last index with lb_pre[leaf] <= flat
+                while (hi - lo > 1) {
+                    int mid = (lo + hi) >> 1;
+                    if ((int)lb_pre[mid] <= flat) lo = mid; else hi = mid;
+                }
+                const uint32_t i = lb_s0[lo] + (uint32_t)(flat - (int)lb_pre[lo]);
+                float4 y = N.epsY[i];
+                float4 yl = N.epsYlo[i];
+                float hx, lx, hy, ly, hz, lz;
+                stage_coord(y.x, yl.x, lb_off[0][lo], lb_off[3][lo], hx, lx);
+                stage_coord(y.y, yl.y, lb_off[1][lo], lb_off[4][lo], hy, ly);
+                stage_coord(y.z, yl.z, lb_off[2][lo], lb_off[5][lo], hz, lz);
+                f[0][fill + j] = hx;
+                f[1][fill + j] = hy;
+                f[2][fill + j] = hz;
+                f[3][fill + j] = lx;
+                f[4][fill + j] = ly;
+                f[5][fill + j] = lz;
+                f[6][fill + j] = qv[i];
+            }
+            fill += take;
+            base += take;
+            if (fill == LAP_SB) {
+                run_batch(fill);
+                fill = 0;
+            }
+        }
+        __syncthreads();  // the table is rewritten for the next leaves
+    }
+    if (fill > 0) run_batch(fill);
+#pragma unroll
+    for (int t = 0; t < PT; ++t) {
+        float u0, u1;
+        f2_unpack(A[t], u0, u1);
+        red[threadIdx.x * PT + t] = u0 + u1;
+    }
+    __syncthreads();
+    if (active && grp == 0) {
+        const double c = 0.079577471545947667884;  // 1 / (4 pi)
+#pragma unroll
+        for (int t = 0; t < PT; ++t) {
+            int i = pi + t * pr;
+            if (i >= np) continue;
+            float tr = 0.f;
+            for (int g = 0; g < G; ++g) tr += red[(g * pr + pi) * PT + t];
+            atomicAdd(&acc[p0 + i].x, (double)tr * c);
+        }
+    }
+}
+
 // Several right-hand sides: each kernel value G(x_i - y_j) is computed once and applied
 // to MC densities.  One thread per target point of the leaf.
 template <bool HELM, int MC>
@@ -407,7 +666,7 @@ void near_field_items(const ffm_plan_s *p, const int4 *items, int64_t n_items, i
     if (p->kind == FFM_HELMHOLTZ)
         FFM_LAUNCH(k_p2p<NF_HELMHOLTZ>, g, P2P_T, 0, s, N, q, p->ny, nrhs, p->nx, acc);
     else
-        FFM_LAUNCH(k_p2p<NF_LAPLACE>, g, P2P_T, 0, s, N, q, p->ny, nrhs, p->nx, acc);
+        FFM_LAUNCH(k_p2p_lap<4>, (unsigned)n_items, P2P_T, 0, s, N, (const float *)q, p->nx, acc);
 }
 
 }  // namespace ffm

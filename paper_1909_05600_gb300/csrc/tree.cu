@@ -187,53 +187,110 @@ __global__ void k_rs_hist(const K *__restrict__ kin, int64_t n, int shift, uint3
     hist[(int64_t)threadIdx.x * nblk + blockIdx.x] = c[threadIdx.x];
 }
 
-// Stable scatter: within a tile, elements keep their order per digit (ranks from
-// warp match masks, then a prefix over the 8 warps of the block per digit).
+__device__ __forceinline__ unsigned long long ld_keep(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.volatile.global.u64 %0, [%1];" : "=l"(v) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ uint32_t ld_keep(const uint32_t *p) {
+    uint32_t v;
+    asm volatile("ld.volatile.global.u32 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
+}
+
+// Stable scatter staged in shared memory.  A block owns a tile of RS_TILE elements: their
+// ranks within the tile's digit runs (in element order) come from warp match masks and a
+// prefix over the 8 warps per digit, round by round, and each element is placed at its run's
+// position in a shared-memory copy of the tile, which ends up sorted by digit.  The block
+// then writes that copy in order: consecutive threads write consecutive slots of one digit's
+// run in the output (its start from the scanned digit-major histogram), so the stores are
+// coalesced instead of one scattered store per element.  The tile's own digit counts are
+// differences of consecutive entries of the scanned histogram.
 template <class K>
 __global__ void __launch_bounds__(RS_T) k_rs_scatter(const K *__restrict__ kin, const uint32_t *__restrict__ vin,
                                                      int64_t n, int shift, const uint32_t *__restrict__ off,
                                                      int nblk, K *__restrict__ kout, uint32_t *__restrict__ vout) {
-    __shared__ uint32_t base[256];
+    extern __shared__ __align__(16) unsigned char rs_smem[];
+    K *skey = reinterpret_cast<K *>(rs_smem);
+    uint32_t *sval = reinterpret_cast<uint32_t *>(skey + RS_TILE);
+    __shared__ uint32_t base[256], start[256], run[256];
     __shared__ uint32_t wcnt[RS_T / 32][257];
-    __shared__ uint32_t tot[256];
+    __shared__ uint32_t wtot[RS_T / 32];
     int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    base[tid] = off[(int64_t)tid * nblk + blockIdx.x];
+    const int64_t t0 = (int64_t)blockIdx.x * RS_TILE;
+    const int tile_n = (int)min((int64_t)RS_TILE, n - t0);
+    {
+        const int64_t flat = (int64_t)tid * nblk + blockIdx.x;
+        const uint32_t b = off[flat];
+        const uint32_t c = flat + 1 < 256LL * nblk ? off[flat + 1] - b : (uint32_t)(n - b);
+        base[tid] = b;
+        // exclusive prefix of the tile's digit counts (digit = thread)
+        uint32_t inc = c;
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += t;
+        }
+        if (lane == 31) wtot[warp] = inc;
+        __syncthreads();
+        uint32_t before = 0;
+        for (int w = 0; w < warp; ++w) before += wtot[w];
+        start[tid] = before + inc - c;
+        run[tid] = 0;
 #pragma unroll
-    for (int w = 0; w < RS_T / 32; ++w) wcnt[w][tid] = 0;
+        for (int w = 0; w < RS_T / 32; ++w) wcnt[w][tid] = 0;
+    }
+    // every load of the tile in flight at once (registers), before the ranking rounds; the
+    // loads are volatile so that they are issued here and not repeated at their uses
+    K keys[RS_ITEMS];
+    uint32_t vals[RS_ITEMS];
+#pragma unroll
+    for (int r = 0; r < RS_ITEMS; ++r) {
+        int64_t i = t0 + r * RS_T + tid;
+        keys[r] = (K)0;
+        vals[r] = 0u;
+        if (i < n) {
+            keys[r] = ld_keep(kin + i);
+            vals[r] = ld_keep(vin + i);
+        }
+    }
     __syncthreads();
-    int64_t t0 = (int64_t)blockIdx.x * RS_TILE;
+#pragma unroll
     for (int r = 0; r < RS_ITEMS; ++r) {
         int64_t i = t0 + r * RS_T + tid;
         bool valid = i < n;
-        K key = valid ? kin[i] : (K)0;
-        uint32_t val = valid ? vin[i] : 0u;
+        K key = keys[r];
+        uint32_t val = vals[r];
         uint32_t d = valid ? ((uint32_t)(key >> shift) & 255u) : 256u;
         uint32_t peers = __match_any_sync(0xffffffffu, d);
         uint32_t lt = peers & ((1u << lane) - 1u);
         uint32_t rank = __popc(lt);
         if (valid && lt == 0) wcnt[warp][d] = __popc(peers);
         __syncthreads();
-        {
-            uint32_t run = 0;
+        uint32_t round_tot = 0;  // digit tid's elements in this round
 #pragma unroll
-            for (int w = 0; w < RS_T / 32; ++w) {
-                uint32_t c = wcnt[w][tid];
-                wcnt[w][tid] = run;
-                run += c;
-            }
-            tot[tid] = run;
+        for (int w = 0; w < RS_T / 32; ++w) {
+            uint32_t c = wcnt[w][tid];
+            wcnt[w][tid] = round_tot;
+            round_tot += c;
         }
         __syncthreads();
         if (valid) {
-            uint32_t pos = base[d] + wcnt[warp][d] + rank;
-            kout[pos] = key;
-            vout[pos] = val;
+            uint32_t pos = start[d] + run[d] + wcnt[warp][d] + rank;
+            skey[pos] = key;
+            sval[pos] = val;
         }
         __syncthreads();
-        base[tid] += tot[tid];
+        run[tid] += round_tot;
 #pragma unroll
         for (int w = 0; w < RS_T / 32; ++w) wcnt[w][tid] = 0;
         __syncthreads();
+    }
+    for (int i = tid; i < tile_n; i += RS_T) {
+        K key = skey[i];
+        uint32_t d = (uint32_t)(key >> shift) & 255u;
+        uint32_t gp = base[d] + (uint32_t)i - start[d];
+        kout[gp] = key;
+        vout[gp] = sval[i];
     }
 }
 
@@ -254,11 +311,13 @@ static void radix_sort(K *keys, uint32_t *vals, int64_t n, int nbits, Alloc &al,
     uint32_t *v2 = al.get<uint32_t>(n);
     K *ka = keys, *kb = k2;
     uint32_t *va = vals, *vb = v2;
+    const size_t scatter_smem = (size_t)RS_TILE * (sizeof(K) + sizeof(uint32_t));
+    FFM_CUDA(cudaFuncSetAttribute(k_rs_scatter<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)scatter_smem));
     for (int shift = 0; shift < nbits; shift += 8) {
         if (((vary >> shift) & 255ull) == 0) continue;
         FFM_LAUNCH(k_rs_hist<K>, nblk, RS_T, 0, s, ka, n, shift, hist, nblk);
         scan_u32(hist, hist, (int64_t)256 * nblk, nullptr, al, s);
-        FFM_LAUNCH(k_rs_scatter<K>, nblk, RS_T, 0, s, ka, va, n, shift, hist, nblk, kb, vb);
+        FFM_LAUNCH(k_rs_scatter<K>, nblk, RS_T, scatter_smem, s, ka, va, n, shift, hist, nblk, kb, vb);
         std::swap(ka, kb);
         std::swap(va, vb);
     }
@@ -967,6 +1026,65 @@ void prepare_target_stationary(ffm_plan_s *p, int l, cudaStream_t s) {
     FFM_CUDA(cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, s));
     FFM_CUDA(cudaStreamSynchronize(s));
     F.ts_ok = hflag == 0;
+    // a level the target-stationary kernel cannot take runs the per-translation transfer
+    if (!F.ts_ok) build_translation_groups(p, l, s);
+}
+
+// Column tiles of the per-translation transfer: tile i of translation t covers pairs
+// off[t] + i bn .. (count per translation, then one block per translation emits its tiles).
+__global__ void k_tile_count(const uint32_t *__restrict__ off, int n_trans, uint32_t bn, uint32_t *__restrict__ cnt) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n_trans) cnt[t] = (off[t + 1] - off[t] + bn - 1) / bn;
+}
+__global__ void k_tile_emit(const uint32_t *__restrict__ off, uint32_t bn, const uint32_t *__restrict__ pos,
+                            uint32_t *__restrict__ tt, uint32_t *__restrict__ tp) {
+    int t = blockIdx.x;
+    uint32_t p0 = off[t], n = (off[t + 1] - p0 + bn - 1) / bn, o = pos[t];
+    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
+        tt[o + i] = (uint32_t)t;
+        tp[o + i] = p0 + i * bn;
+    }
+}
+
+static int64_t build_tiles(ffm_plan_s *p, const FarLevel &F, uint32_t bn, uint32_t **tt, uint32_t **tp, Alloc &tmp,
+                           cudaStream_t s) {
+    uint32_t *cnt = tmp.get<uint32_t>(F.n_trans), *pos = tmp.get<uint32_t>(F.n_trans), *tot = tmp.get<uint32_t>(1);
+    FFM_LAUNCH(k_tile_count, cdiv(F.n_trans, 256), 256, 0, s, F.bt_off, F.n_trans, bn, cnt);
+    scan_u32(cnt, pos, F.n_trans, tot, tmp, s);
+    int64_t n = read_u32(tot, s);
+    *tt = p->mem.get<uint32_t>(n);
+    *tp = p->mem.get<uint32_t>(n);
+    if (n > 0) FFM_LAUNCH(k_tile_emit, F.n_trans, 128, 0, s, F.bt_off, bn, pos, *tt, *tp);
+    return n;
+}
+
+// Pairs of Lagrange level l grouped by translation (CSR bt_off over translations, with each
+// pair's source and target box) and the column tiles of the per-translation transfer
+// kernels (32 pairs for the CUDA-core GEMM, 256 for tcgen05).  Made while the plan is built,
+// or later by the autotuner or when the target-stationary transfer cannot take the level;
+// a level that runs the target-stationary transfer does without them.
+void build_translation_groups(ffm_plan_s *p, int l, cudaStream_t s) {
+    FarLevel &F = p->far[l];
+    if (F.mode != 1 || F.n_adm == 0 || F.bt_off) return;
+    const int64_t na = F.n_adm;
+    Alloc tmp;
+    tmp.stream = s;
+    uint32_t *tk = tmp.get<uint32_t>(na), *pidx = tmp.get<uint32_t>(na);
+    FFM_CUDA(cudaMemcpyAsync(tk, F.adm_t, sizeof(uint32_t) * na, cudaMemcpyDeviceToDevice, s));
+    FFM_LAUNCH(k_iota, cdiv(na, 256), 256, 0, s, pidx, na);
+    radix_sort_u32(tk, pidx, na, bits_for(F.n_trans), tmp, s);
+    // target of every pair in CSR order
+    uint32_t *ptgt = tmp.get<uint32_t>(na);
+    FFM_LAUNCH(k_expand_csr_targets, cdiv(F.n_tgt, 128), 128, 0, s, F.tgt, F.adm_off, F.n_tgt, ptgt);
+    F.bt_src = p->mem.get<uint32_t>(na);
+    F.bt_tgt = p->mem.get<uint32_t>(na);
+    FFM_LAUNCH(k_gather_u32, cdiv(na, 256), 256, 0, s, F.adm_src, pidx, na, F.bt_src);
+    FFM_LAUNCH(k_gather_u32, cdiv(na, 256), 256, 0, s, ptgt, pidx, na, F.bt_tgt);
+    F.bt_off = p->mem.get<uint32_t>(F.n_trans + 1);
+    FFM_LAUNCH(k_csr_offsets, cdiv(F.n_trans + 1, 256), 256, 0, s, tk, na, F.n_trans, F.bt_off);
+    F.n_tiles = build_tiles(p, F, LAG_GEMM_BN, &F.tile_t, &F.tile_p0, tmp, s);
+    F.tc_tiles = build_tiles(p, F, 256, &F.tc_tile_t, &F.tc_tile_p0, tmp, s);
+    tmp.release();
 }
 
 static void finish_far_level(ffm_plan_s *p, int l, uint32_t *aa, uint32_t *ab, int64_t na, Alloc &tmp,
@@ -1024,45 +1142,13 @@ static void finish_far_level(ffm_plan_s *p, int l, uint32_t *aa, uint32_t *ab, i
     if (F.mode == 1) {
         F.r1 = p->r1_override > 0 ? p->r1_override : r1_rule(p->kind, p->eps);
         if (p->lag_transfer > 0) F.tune_tc = p->lag_transfer - 1;  // forced variant
-        // pairs grouped by translation for the transfer GEMMs, and the column tiles
-        uint32_t *tk = tmp.get<uint32_t>(na), *pidx = tmp.get<uint32_t>(na);
-        FFM_CUDA(cudaMemcpyAsync(tk, F.adm_t, sizeof(uint32_t) * na, cudaMemcpyDeviceToDevice, s));
-        FFM_LAUNCH(k_iota, cdiv(na, 256), 256, 0, s, pidx, na);
-        radix_sort_u32(tk, pidx, na, bits_for(F.n_trans), tmp, s);
-        // target of every pair in CSR order
-        uint32_t *ptgt = tmp.get<uint32_t>(na);
-        FFM_LAUNCH(k_expand_csr_targets, cdiv(F.n_tgt, 128), 128, 0, s, F.tgt, F.adm_off, F.n_tgt, ptgt);
-        F.bt_src = p->mem.get<uint32_t>(na);
-        F.bt_tgt = p->mem.get<uint32_t>(na);
-        FFM_LAUNCH(k_gather_u32, cdiv(na, 256), 256, 0, s, F.adm_src, pidx, na, F.bt_src);
-        FFM_LAUNCH(k_gather_u32, cdiv(na, 256), 256, 0, s, ptgt, pidx, na, F.bt_tgt);
-        F.bt_off = p->mem.get<uint32_t>(F.n_trans + 1);
-        FFM_LAUNCH(k_csr_offsets, cdiv(F.n_trans + 1, 256), 256, 0, s, tk, na, F.n_trans, F.bt_off);
-        std::vector<uint32_t> hoff(F.n_trans + 1);
-        FFM_CUDA(cudaMemcpyAsync(hoff.data(), F.bt_off, sizeof(uint32_t) * (F.n_trans + 1), cudaMemcpyDeviceToHost, s));
-        FFM_CUDA(cudaStreamSynchronize(s));
-        std::vector<uint32_t> tt, tp, ct, cp;
-        for (int t = 0; t < F.n_trans; ++t) {
-            for (uint32_t q0 = hoff[t]; q0 < hoff[t + 1]; q0 += LAG_GEMM_BN) {
-                tt.push_back((uint32_t)t);
-                tp.push_back(q0);
-            }
-            for (uint32_t q0 = hoff[t]; q0 < hoff[t + 1]; q0 += 256) {  // tensor-core tiles
-                ct.push_back((uint32_t)t);
-                cp.push_back(q0);
-            }
-        }
-        F.n_tiles = (int64_t)tt.size();
-        F.tile_t = p->mem.get<uint32_t>(tt.size());
-        F.tile_p0 = p->mem.get<uint32_t>(tp.size());
-        F.tc_tiles = (int64_t)ct.size();
-        F.tc_tile_t = p->mem.get<uint32_t>(ct.size());
-        F.tc_tile_p0 = p->mem.get<uint32_t>(cp.size());
-        FFM_CUDA(cudaMemcpyAsync(F.tile_t, tt.data(), sizeof(uint32_t) * tt.size(), cudaMemcpyHostToDevice, s));
-        FFM_CUDA(cudaMemcpyAsync(F.tile_p0, tp.data(), sizeof(uint32_t) * tp.size(), cudaMemcpyHostToDevice, s));
-        FFM_CUDA(cudaMemcpyAsync(F.tc_tile_t, ct.data(), sizeof(uint32_t) * ct.size(), cudaMemcpyHostToDevice, s));
-        FFM_CUDA(cudaMemcpyAsync(F.tc_tile_p0, cp.data(), sizeof(uint32_t) * cp.size(), cudaMemcpyHostToDevice, s));
-        FFM_CUDA(cudaStreamSynchronize(s));
+        // pairs grouped by translation for the per-translation transfer kernels, unless the
+        // level is to run the target-stationary transfer, which reads the per-target lists
+        // (forced, or the pick stored in the plan's autotune cache); ACA levels need them
+        const int pick = p->lag_transfer == 0 ? cached_lag_pick(p, l) : -1;
+        const bool ts_first = (p->lag_transfer == 3 || pick == 2) && p->kind == FFM_LAPLACE && F.r1 <= 4 &&
+                              !(p->aca_eps > 0.0);
+        if (!ts_first) build_translation_groups(p, l, s);
         F.src_chunks = build_chunks(p, F.src, F.n_src, p->by[l].start, &F.n_src_chunks, tmp, s);
         F.tgt_chunks = build_chunks(p, F.tgt, F.n_tgt, p->bx[l].start, &F.n_tgt_chunks, tmp, s);
     }
