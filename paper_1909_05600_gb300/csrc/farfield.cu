@@ -651,203 +651,266 @@ __global__ void k_split_pad(const float *__restrict__ src, int64_t nmat, int row
 
 // ---- target-stationary tensor-core transfer (r <= 64)
 //
-// A CTA owns TS_M = 128 consecutive target boxes of the level (TMEM lane = box).  For every
-// translation t present among their admissible pairs (partners are sorted by translation
-// within each target, so a per-row cursor finds the row's source box for t) it gathers the
-// source rows u~_b (zero rows for boxes without a partner at t), multiplies them by T_t
-// (N = 64 target nodes, K = 64 source nodes, zero padded beyond r) and accumulates into the
-// same TMEM tile: D(a, i) = sum_t sum_j u~_{b(a,t)}(j) T_t(i, j).  Each target's v~ is then
-// written once, with no atomics.  Operands as in k_lag_gemm_tc (TF32 hi/lo, three MMAs per
-// K step); T_t arrives pre-split in the core-matrix order by cp.async.  Two operand stages:
-// the gather of translation g+1 overlaps the MMAs of g, each stage released by its own
-// mbarrier.  Waits are bounded and raise the device error flag.
+// A CTA owns TS_M = 128 consecutive target boxes of the level (TMEM lane = box) and runs
+// over every translation t present among their admissible pairs, in increasing order
+// (partners are sorted by translation within each target, so a per-row cursor finds the
+// row's source box for t, or none).  For each t it multiplies the source rows u~_b (zero
+// rows for boxes without a partner at t) by T_t (N = 64 target nodes, K = 64 source nodes,
+// zero padded beyond r) and accumulates D(a, i) = sum_t sum_j u~_{b(a,t)}(j) T_t(i, j) in
+// TMEM; each target's v~ is written once, with no atomics.  TF32 hi/lo split with three
+// MMAs per K step (hi hi + hi lo + lo hi), FP32 accumulation.
+//
+// Pipeline.  A step is one translation and one half of K (32 source nodes).  Warps 1-8
+// produce: the two threads of a target row copy the hi and the lo part of its source row's
+// half (8 x 16 B each, zero-filled where the row has no partner) with cp.async straight into
+// the K-major core-matrix layout, and together they copy T_t's pre-split image of that half
+// (16 KB), into a ring of TS_NST stages; each thread's copies arrive on the stage's "full"
+// mbarrier once they have landed (cp.async.mbarrier.arrive).  One thread of warp 0 waits on
+// "full", issues the step's 12 MMAs and commits them to the stage's "empty" mbarrier, which
+// the producers wait on before they reuse the stage.  u~ arrives pre-split into hi and lo
+// rows of 64 floats, so producers do no arithmetic and never wait for their own loads.
+//
+// Accumulation.  One long tcgen05 accumulation loses accuracy, so the tile alternates
+// between two TMEM accumulators (64 columns each) every TS_DRAIN translations; the producers
+// add each finished accumulator into FP32 registers (tcgen05.ld) while the tensor cores fill
+// the other one, and the MMA thread waits for that drain before it reuses the accumulator.
+// Every wait is bounded; a give-up raises the device error flag, the CTA then waits for its
+// copies and committed MMAs, skips its results and frees TMEM.
 constexpr int TS_M = 128;
-constexpr int TS_A = TS_M * 64;  // floats per A hi or lo block
-constexpr int TS_B = 64 * 64;    // floats per B hi or lo block
-constexpr int TS_STAGE = 2 * TS_A + 2 * TS_B;
-constexpr int TS_MAXT = 4096;    // translation codes lie in a 16^3 range
-constexpr int TS_DRAIN = 8;      // translations per TMEM accumulation before it is drained
+constexpr int TS_KH = 32;                       // source nodes per step (half of K = 64)
+constexpr int TS_AH = TS_M * TS_KH;             // floats per A hi or lo block of a step
+constexpr int TS_BH = 64 * TS_KH;               // floats per B hi or lo block of a step
+constexpr int TS_STEP = 2 * TS_AH + 2 * TS_BH;  // floats per stage (48 KB)
+constexpr int TS_NST = 4;                       // stages
+constexpr int TS_MAXT = 4096;                   // translation codes lie in a 16^3 range
+constexpr int TS_DRAIN = 8;                     // translations per TMEM accumulator fill
+constexpr int TS_NP = 2 * TS_M;                 // producer threads (warps 1-8)
 
-__global__ void __launch_bounds__(2 * TS_M) k_lag_gemm_ts(const uint32_t *__restrict__ tgt, int64_t n_tgt,
-                                                         const uint32_t *__restrict__ adm_off,
-                                                         const uint32_t *__restrict__ adm_src,
-                                                         const uint32_t *__restrict__ adm_t, int n_trans,
-                                                         const float *__restrict__ Tsp, int r, int nrhs,
-                                                         const float *__restrict__ ut, float *__restrict__ vt,
-                                                         int *__restrict__ err, int tries) {
+// 16-byte cp.async that copies src_bytes (0 or 16) and zero-fills the rest
+__device__ __forceinline__ void cp_async16_zfill(void *dst, const void *src, uint32_t src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_addr(dst)), "l"(src), "r"(src_bytes)
+                 : "memory");
+}
+
+__global__ void __launch_bounds__(TS_NP + 32) k_lag_gemm_ts(const uint32_t *__restrict__ tgt, int64_t n_tgt,
+                                                           const uint32_t *__restrict__ adm_off,
+                                                           const uint32_t *__restrict__ adm_src,
+                                                           const uint32_t *__restrict__ adm_t, int n_trans,
+                                                           const float *__restrict__ Tsp, int r, int nrhs,
+                                                           const float *__restrict__ uhi,
+                                                           const float *__restrict__ ulo, float *__restrict__ vt,
+                                                           int *__restrict__ err, int tries) {
     extern __shared__ __align__(1024) unsigned char smem[];
     float *stage0 = reinterpret_cast<float *>(smem);
     __shared__ uint32_t s_bits[TS_MAXT / 32];
     __shared__ uint32_t s_tmem;
-    __shared__ __align__(8) uint64_t s_mbar[2];
-    constexpr int NT = 2 * TS_M;
-    // two threads per target row: half 0 takes source nodes / columns 0..31, half 1 32..63
-    int tid = threadIdx.x, warp = tid >> 5;
-    int row = tid & (TS_M - 1), half = tid >> 7;
-    int quarter = warp & 3;  // TMEM lanes 32 quarter .. 32 quarter + 31 (= rows of this warp)
-    int m = blockIdx.y;
-    int64_t x = (int64_t)blockIdx.x * TS_M + row;
-    bool has = x < n_tgt;
-    uint32_t cur = has ? adm_off[x] : 0u, end = has ? adm_off[x + 1] : 0u;
-    int nw = (n_trans + 31) / 32;
-    for (int w = tid; w < nw; w += NT) s_bits[w] = 0u;
+    __shared__ __align__(8) uint64_t s_full[TS_NST], s_empty[TS_NST], s_drained;
+    __shared__ int s_bad;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int m = blockIdx.y;
+    const int64_t x0 = (int64_t)blockIdx.x * TS_M;
+    const int nw = (n_trans + 31) / 32;
+    for (int w = tid; w < nw; w += blockDim.x) s_bits[w] = 0u;
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&s_tmem)),
-                     "r"(64));
+                     "r"(128));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&s_mbar[0])));
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&s_mbar[1])));
+        s_bad = 0;
+        for (int i = 0; i < TS_NST; ++i) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(&s_full[i])), "r"(TS_NP));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&s_empty[i])));
+        }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(&s_drained)), "r"(TS_NP));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    uint32_t tmem = s_tmem;
-    if (half == 0)
+    const uint32_t tmem = s_tmem;
+    // producers: row (TMEM lane) and part (0: hi, 1: lo) they copy
+    const bool prod = warp >= 1;
+    const int p = tid - 32, row = p & (TS_M - 1), part = p >> 7;
+    const int64_t x = x0 + row;
+    const bool has = prod && x < n_tgt;
+    uint32_t cur = has ? adm_off[x] : 0u, end = has ? adm_off[x + 1] : 0u;
+    if (has && part == 0)
         for (uint32_t e = cur; e < end; ++e) {
             uint32_t t = adm_t[e];
             atomicOr(&s_bits[t >> 5], 1u << (t & 31));
         }
     __syncthreads();
-    const bool r4 = (r & 3) == 0;
-    const uint32_t lbo = 128, sbo = 16 * 128;  // K tile of 64: 16 core matrices along K
-    const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(64 >> 3) << 17) | ((uint32_t)(TS_M >> 4) << 24);
-    uint32_t next_t = cur < end ? adm_t[cur] : 0xffffffffu;
-    uint32_t parity[2] = {0u, 0u};
     bool ok = true;
-    int g = 0, g0 = 0;  // groups issued; first group of the current TMEM accumulation
-    float sum[32];      // FP32 sums of the drained TMEM partial results (half a row)
+    int total = 0;  // steps issued or produced
+    if (prod) {
+        // drain rows / columns: warp w reads TMEM lanes 32 (w % 4) .. + 31, columns dcol .. + 31
+        const int dq = warp & 3, dcol = ((warp - 1) >> 2) * 32;
+        float sum[32];
 #pragma unroll
-    for (int c = 0; c < 32; ++c) sum[c] = 0.f;
-    // wait for the MMAs in flight and add the TMEM tile into the register sums; the
-    // tensor-core accumulation then restarts, so no FP32 accumulator in TMEM takes more
-    // than TS_DRAIN translations x 24 MMA steps
-    auto drain = [&]() {
-        if (g >= g0 + 2) {
-            int st = (g - 2) & 1;
-            mma_wait(&s_mbar[st], parity[st], tries, ok);
-            parity[st] ^= 1u;
-        }
-        if (g >= g0 + 1) {
-            int st = (g - 1) & 1;
-            mma_wait(&s_mbar[st], parity[st], tries, ok);
-            parity[st] ^= 1u;
-        }
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        for (int c = 0; c < 32; ++c) sum[c] = 0.f;
+        int drained = 0;  // accumulator fills added into sum
+        auto drain = [&](int k) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t base = tmem + (uint32_t)((k & 1) * 64 + dcol) + ((uint32_t)(dq * 32) << 16);
 #pragma unroll
-        for (int c0 = 0; c0 < 32; c0 += 8) {
-            uint32_t v[8];
-            uint32_t addr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(half * 32 + c0);
-            asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                         : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
-                           "=r"(v[7])
-                         : "r"(addr));
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            for (int c0 = 0; c0 < 32; c0 += 8) {
+                uint32_t v[8];
+                asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                             : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+                               "=r"(v[7])
+                             : "r"(base + (uint32_t)c0));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-            for (int q = 0; q < 8; ++q) sum[c0 + q] += __uint_as_float(v[q]);
-        }
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();
-        g0 = g;
-    };
-    for (int w = 0; w < nw; ++w) {
-        uint32_t bits = s_bits[w];
-        while (bits) {
-            uint32_t t = (uint32_t)(w * 32 + __ffs(bits) - 1);
-            bits &= bits - 1;
-            if (g - g0 == TS_DRAIN) drain();
-            int st = g & 1;
-            float *S = stage0 + st * TS_STAGE;
-            // the stage was last read by the MMAs of translation g - 2
-            if (g >= g0 + 2) {
-                mma_wait(&s_mbar[st], parity[st], tries, ok);
-                parity[st] ^= 1u;
-                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                for (int q = 0; q < 8; ++q) sum[c0 + q] += __uint_as_float(v[q]);
             }
-            // B: T_t hi and lo, already in the shared-memory image order
-            const float *Tb = Tsp + (size_t)t * 2 * TS_B;
-            float *B = S + 2 * TS_A;
-            for (int c = tid; c < 2 * TS_B / 4; c += NT) cp_async16(B + 4 * c, Tb + 4 * c);
-            asm volatile("cp.async.commit_group;" ::: "memory");
-            // A: this row's source box for translation t, or a zero row (both threads of
-            // the row follow the same cursor)
-            bool pres = next_t == t;
-            uint32_t src = 0u;
-            if (pres) {
-                src = adm_src[cur];
-                ++cur;
-                next_t = cur < end ? adm_t[cur] : 0xffffffffu;
-            }
-            const float *rowp = ut + ((size_t)src * nrhs + m) * r;
-            float4 v[8];
-#pragma unroll
-            for (int c = 0; c < 8; ++c) {  // all loads first
-                int j = half * 32 + 4 * c;
-                v[c] = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (pres && j < r) {
-                    if (r4) {
-                        v[c] = *reinterpret_cast<const float4 *>(rowp + j);
-                    } else {
-                        v[c].x = rowp[j];
-                        v[c].y = j + 1 < r ? rowp[j + 1] : 0.f;
-                        v[c].z = j + 2 < r ? rowp[j + 2] : 0.f;
-                        v[c].w = j + 3 < r ? rowp[j + 3] : 0.f;
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(&s_drained)) : "memory");
+        };
+        const float *usrc = part ? ulo : uhi;
+        uint32_t next_t = cur < end ? adm_t[cur] : 0xffffffffu;
+        int s = 0;
+        for (int w = 0; w < nw && ok; ++w) {
+            uint32_t bits = s_bits[w];
+            while (bits && ok) {
+                const uint32_t t = (uint32_t)(w * 32 + __ffs(bits) - 1);
+                bits &= bits - 1;
+                const bool pres = next_t == t;
+                uint32_t src = 0u;
+                if (pres) {
+                    src = adm_src[cur];
+                    ++cur;
+                    next_t = cur < end ? adm_t[cur] : 0xffffffffu;
+                }
+                const float *rowp = usrc + ((size_t)src * nrhs + m) * 64;
+                const float *Tb = Tsp + (size_t)t * 4 * TS_BH;
+                for (int h = 0; h < 2; ++h, ++s) {
+                    const int b = s % TS_NST;
+                    if (s >= TS_NST) {
+                        // the MMAs of step s - TS_NST are done, and with them every earlier
+                        // accumulator fill: add the finished ones into the sums (a give-up
+                        // is made warp-uniform: the drains are warp-wide TMEM loads)
+                        bool w_ok = mbar_wait(&s_empty[b], (uint32_t)((s / TS_NST - 1) & 1), tries);
+                        if (!__all_sync(0xffffffffu, w_ok)) {
+                            ok = false;
+                            break;
+                        }
+                        const int done = (s - TS_NST) / (2 * TS_DRAIN);
+                        while (drained < done) drain(drained++);
                     }
-                }
-            }
-            float *Ah = S, *Al = S + TS_A;
+                    float *st = stage0 + (size_t)b * TS_STEP;
+                    float *A = st + part * TS_AH, *B = st + 2 * TS_AH;
 #pragma unroll
-            for (int c = 0; c < 8; ++c) {
-                float4 h, l;
-                tf32_split(v[c].x, h.x, l.x);
-                tf32_split(v[c].y, h.y, l.y);
-                tf32_split(v[c].z, h.z, l.z);
-                tf32_split(v[c].w, h.w, l.w);
-                uint32_t o = kmajor_index(row, half * 32 + 4 * c, 64);
-                *reinterpret_cast<float4 *>(Ah + o) = h;
-                *reinterpret_cast<float4 *>(Al + o) = l;
-            }
-            asm volatile("cp.async.wait_all;" ::: "memory");
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            __syncthreads();
-            if (tid == 0) {
-                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                for (int ks = 0; ks < 8; ++ks) {
-                    uint64_t ah = umma_desc(smem_addr(Ah) + ks * 256, lbo, sbo);
-                    uint64_t al = umma_desc(smem_addr(Al) + ks * 256, lbo, sbo);
-                    uint64_t bh = umma_desc(smem_addr(B) + ks * 256, lbo, sbo);
-                    uint64_t bl = umma_desc(smem_addr(B + TS_B) + ks * 256, lbo, sbo);
-                    uint32_t acc0 = (g > g0 || ks > 0) ? 1u : 0u;
-                    asm volatile(
-                        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-                        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-                        "l"(ah), "l"(bh), "r"(idesc), "r"(acc0));
-                    asm volatile("tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, 1;\n" ::"r"(tmem), "l"(ah),
-                                 "l"(bl), "r"(idesc));
-                    asm volatile("tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, 1;\n" ::"r"(tmem), "l"(al),
-                                 "l"(bh), "r"(idesc));
+                    for (int c = 0; c < TS_KH / 4; ++c)
+                        cp_async16_zfill(A + kmajor_index(row, 4 * c, TS_KH), pres ? rowp + h * TS_KH + 4 * c : usrc,
+                                         pres ? 16u : 0u);
+                    const float *Bs = Tb + h * 2 * TS_BH;
+#pragma unroll
+                    for (int i = 0; i < 2 * TS_BH / 4 / TS_NP; ++i) {
+                        const int e = p + TS_NP * i;
+                        cp_async16(B + 4 * e, Bs + 4 * e);
+                    }
+                    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_addr(&s_full[b]))
+                                 : "memory");
                 }
-                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                                 smem_addr(&s_mbar[st]))
-                             : "memory");
             }
-            ++g;
         }
-    }
-    // the last partial accumulation, then one write per target box
-    if (g > g0) drain();
-    if (!ok && tid == 0) atomicOr(err, 1);
-    if (has && ok) {
-        float *dst = vt + ((size_t)tgt[x] * nrhs + m) * r + half * 32;
+        total = s;
+        if (ok && total > 0) {
+            // the last step's MMAs complete after all others: then the last fills
+            const int l = total - 1;
+            bool w_ok = mbar_wait(&s_empty[l % TS_NST], (uint32_t)((l / TS_NST) & 1), tries);
+            if (!__all_sync(0xffffffffu, w_ok)) ok = false;
+            const int fills = (total + 2 * TS_DRAIN - 1) / (2 * TS_DRAIN);
+            while (ok && drained < fills) drain(drained++);
+        }
+        asm volatile("cp.async.wait_all;" ::: "memory");
+        if (!ok) s_bad = 1;
+        if (ok) {
+            const int64_t xd = x0 + dq * 32 + lane;
+            if (xd < n_tgt) {
+                float *dst = vt + ((size_t)tgt[xd] * nrhs + m) * r + dcol;
 #pragma unroll
-        for (int c = 0; c < 32; ++c)
-            if (half * 32 + c < r) dst[c] = sum[c];
+                for (int c = 0; c < 32; ++c)
+                    if (dcol + c < r) dst[c] = sum[c];
+            }
+        }
+    } else if (lane == 0) {
+        // ---- MMA thread
+        const uint32_t lbo = 128, sbo = (TS_KH / 4) * 128;
+        const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(64 >> 3) << 17) |
+                               ((uint32_t)(TS_M >> 4) << 24);
+        int s = 0, g = 0, issued = 0;
+        for (int w = 0; w < nw && ok; ++w) {
+            uint32_t bits = s_bits[w];
+            while (bits && ok) {
+                bits &= bits - 1;
+                const int fill = g / TS_DRAIN;
+                // the accumulator of fill - 2 must have been added into the producers' sums
+                if (g % TS_DRAIN == 0 && fill >= 2 && !mbar_wait(&s_drained, (uint32_t)((fill - 2) & 1), tries)) {
+                    ok = false;
+                    break;
+                }
+                const uint32_t d = tmem + (uint32_t)((fill & 1) * 64);
+                for (int h = 0; h < 2; ++h, ++s) {
+                    const int b = s % TS_NST;
+                    if (!mbar_wait(&s_full[b], (uint32_t)((s / TS_NST) & 1), tries)) {
+                        ok = false;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const float *st = stage0 + (size_t)b * TS_STEP;
+                    const uint32_t ah0 = smem_addr(st), al0 = smem_addr(st + TS_AH), bh0 = smem_addr(st + 2 * TS_AH),
+                                   bl0 = smem_addr(st + 2 * TS_AH + TS_BH);
+#pragma unroll
+                    for (int ks = 0; ks < TS_KH / 8; ++ks) {
+                        uint64_t ah = umma_desc(ah0 + ks * 256, lbo, sbo), al = umma_desc(al0 + ks * 256, lbo, sbo);
+                        uint64_t bh = umma_desc(bh0 + ks * 256, lbo, sbo), bl = umma_desc(bl0 + ks * 256, lbo, sbo);
+                        uint32_t acc0 = (g % TS_DRAIN != 0 || h > 0 || ks > 0) ? 1u : 0u;
+                        asm volatile(
+                            "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+                            "l"(ah), "l"(bh), "r"(idesc), "r"(acc0));
+                        asm volatile("tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, 1;\n" ::"r"(d), "l"(ah),
+                                     "l"(bl), "r"(idesc));
+                        asm volatile("tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, 1;\n" ::"r"(d), "l"(al),
+                                     "l"(bh), "r"(idesc));
+                    }
+                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                     smem_addr(&s_empty[b]))
+                                 : "memory");
+                    issued = s + 1;
+                }
+                ++g;
+            }
+        }
+        // after a give-up: keep TMEM and the stages owned until the committed MMAs are done
+        if (!ok) {
+            s_bad = 1;
+            if (issued > 0)
+                mbar_wait(&s_empty[(issued - 1) % TS_NST], (uint32_t)(((issued - 1) / TS_NST) & 1), DRAIN_TRIES);
+        }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(64));
+    if (tid == 0 && s_bad) atomicOr(err, 1);
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(128));
+}
+
+// u~ rows (r floats, r <= 64) split into TF32 hi and lo rows of 64 floats (zero padded),
+// the operand of the target-stationary transfer.
+__global__ void k_split_rows64(const float *__restrict__ u, int64_t nrow, int r, float *__restrict__ hi,
+                               float *__restrict__ lo) {
+    int64_t n = nrow * 64;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        int64_t row = i >> 6;
+        int k = (int)(i & 63);
+        float v = k < r ? u[row * r + k] : 0.f;
+        float h, l;
+        tf32_split(v, h, l);
+        hi[i] = h;
+        lo[i] = l;
+    }
 }
 
 // Target step of a Lagrange level (L_X^T v~ of eq. 8): v_i += sum_abc L_a(x_i) L_b(y_i) L_c(z_i) v~_a(abc),
@@ -913,10 +976,174 @@ static LevelArgs level_args(const ffm_plan_s *p, const BoxLevel &B, const BoxLev
     return A;
 }
 
+// ---- warp-per-chunk forms of the two point-wise Lagrange steps
+//
+// Fine levels of clustered inputs have millions of boxes holding a few points each; a block
+// per chunk then leaves most of its threads idle.  Here a warp takes one chunk (at most
+// LAG_CHUNK points of a box) and a block holds eight of them.  Source step: the lanes form
+// the 1-D Lagrange weights of 32 points at a time into the warp's shared rows, then each
+// lane adds those points into its own control nodes (lane, lane + 32, ...).  Target step:
+// the warp stages the box's r coefficients once and each lane interpolates its own points.
+constexpr int LAG_WC = 8;  // chunks (warps) per block
+
+template <bool CPLX, int R1>
+__global__ void __launch_bounds__(32 * LAG_WC) k_lag_anterp_w(LevelArgs A, const uint2 *__restrict__ chunks,
+                                                             int64_t nchunks, Cheb cb,
+                                                             const typename QT<CPLX>::T *__restrict__ q, int64_t ny,
+                                                             int nrhs, typename QT<CPLX>::T *__restrict__ ut) {
+    typedef typename QT<CPLX>::T Q;
+    constexpr int r = R1 * R1 * R1, NA = (r + 31) / 32, W = 3 * R1;
+    __shared__ float sl[LAG_WC][32][W + 1];
+    __shared__ Q sq[LAG_WC][CPLX ? 32 : 1];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t ci = (int64_t)blockIdx.x * LAG_WC + warp;
+    if (ci >= nchunks) return;  // warp-level work only: no block barrier below
+    const int m = blockIdx.y;
+    const uint2 ck = chunks[ci];
+    const int b = (int)ck.x;
+    const uint32_t s0 = ck.y, bend = A.box_start[b + 1], s1 = min(bend, s0 + (uint32_t)LAG_CHUNK);
+    const bool sole = s0 == A.box_start[b] && s1 == bend;
+    const int4 gb = A.box_g[b];
+    float accr[NA], acci[NA];
+#pragma unroll
+    for (int k = 0; k < NA; ++k) accr[k] = acci[k] = 0.f;
+    float(*row)[W + 1] = sl[warp];
+    for (uint32_t base = s0; base < s1; base += 32) {
+        const uint32_t j = base + lane;
+        if (j < s1) {
+            float4 e = A.eps[j];
+            int4 gl = A.leaf_g[__float_as_uint(e.w)];
+            float3 o = leaf_offset(gl, gb, A.shift, A.dls);
+            float lx[R1MAX], ly[R1MAX], lz[R1MAX];
+            lag1d(cb, (o.x + e.x) * A.inv_half_dl, lx);
+            lag1d(cb, (o.y + e.y) * A.inv_half_dl, ly);
+            lag1d(cb, (o.z + e.z) * A.inv_half_dl, lz);
+            Q w = q[(int64_t)m * ny + j];
+#pragma unroll
+            for (int a = 0; a < R1; ++a) {
+                if constexpr (CPLX)
+                    row[lane][a] = lx[a];
+                else
+                    row[lane][a] = lx[a] * w;
+                row[lane][R1 + a] = ly[a];
+                row[lane][2 * R1 + a] = lz[a];
+            }
+            if constexpr (CPLX) sq[warp][lane] = w;
+        }
+        __syncwarp();
+        const int cnt = (int)min((uint32_t)32, s1 - base);
+#pragma unroll
+        for (int k = 0; k < NA; ++k) {
+            const int a = lane + 32 * k;
+            if (a < r) {
+                const int ia = a / (R1 * R1), ib = (a / R1) % R1, ic = a % R1;
+                for (int jj = 0; jj < cnt; ++jj) {
+                    float L = row[jj][ia] * row[jj][R1 + ib];
+                    if constexpr (CPLX) {
+                        L *= row[jj][2 * R1 + ic];
+                        accr[k] = fmaf(L, sq[warp][jj].x, accr[k]);
+                        acci[k] = fmaf(L, sq[warp][jj].y, acci[k]);
+                    } else {
+                        accr[k] = fmaf(L, row[jj][2 * R1 + ic], accr[k]);
+                    }
+                }
+            }
+        }
+        __syncwarp();
+    }
+#pragma unroll
+    for (int k = 0; k < NA; ++k) {
+        const int a = lane + 32 * k;
+        if (a < r) {
+            size_t o = ((size_t)b * nrhs + m) * r + a;
+            if constexpr (CPLX) {
+                if (sole) {
+                    ut[o] = make_float2(accr[k], acci[k]);
+                } else {
+                    atomicAdd(&ut[o].x, accr[k]);
+                    atomicAdd(&ut[o].y, acci[k]);
+                }
+            } else {
+                if (sole)
+                    ut[o] = accr[k];
+                else
+                    atomicAdd(&ut[o], accr[k]);
+            }
+        }
+    }
+}
+
+template <bool CPLX, int R1>
+__global__ void __launch_bounds__(32 * LAG_WC) k_lag_interp_w(LevelArgs A, const uint2 *__restrict__ chunks,
+                                                             int64_t nchunks, Cheb cb,
+                                                             const typename QT<CPLX>::T *__restrict__ vt, int nrhs,
+                                                             int64_t nx, float2 *__restrict__ accf) {
+    typedef typename QT<CPLX>::T Q;
+    constexpr int r = R1 * R1 * R1;
+    __shared__ Q sv[LAG_WC][r];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t ci = (int64_t)blockIdx.x * LAG_WC + warp;
+    if (ci >= nchunks) return;  // warp-level work only: no block barrier below
+    const int m = blockIdx.y;
+    const uint2 ck = chunks[ci];
+    const int a = (int)ck.x;
+    Q *v = sv[warp];
+    for (int i = lane; i < r; i += 32) v[i] = vt[((size_t)a * nrhs + m) * r + i];
+    __syncwarp();
+    const uint32_t s0 = ck.y, s1 = min(A.box_start[a + 1], s0 + (uint32_t)LAG_CHUNK);
+    const int4 gb = A.box_g[a];
+    for (uint32_t i = s0 + lane; i < s1; i += 32) {
+        float4 e = A.eps[i];
+        int4 gl = A.leaf_g[__float_as_uint(e.w)];
+        float3 o = leaf_offset(gl, gb, A.shift, A.dls);
+        float lx[R1MAX], ly[R1MAX], lz[R1MAX];
+        lag1d(cb, (o.x + e.x) * A.inv_half_dl, lx);
+        lag1d(cb, (o.y + e.y) * A.inv_half_dl, ly);
+        lag1d(cb, (o.z + e.z) * A.inv_half_dl, lz);
+        float sr = 0.f, si = 0.f;
+#pragma unroll
+        for (int ia = 0; ia < R1; ++ia)
+#pragma unroll
+            for (int ib = 0; ib < R1; ++ib) {
+                float lab = lx[ia] * ly[ib];
+                const Q *rw = v + (ia * R1 + ib) * R1;
+                float pr = 0.f, pi = 0.f;
+#pragma unroll
+                for (int ic = 0; ic < R1; ++ic) {
+                    if constexpr (CPLX) {
+                        pr = fmaf(lz[ic], rw[ic].x, pr);
+                        pi = fmaf(lz[ic], rw[ic].y, pi);
+                    } else {
+                        pr = fmaf(lz[ic], rw[ic], pr);
+                    }
+                }
+                sr = fmaf(lab, pr, sr);
+                if constexpr (CPLX) si = fmaf(lab, pi, si);
+            }
+        float2 &dst = accf[(int64_t)m * nx + i];
+        dst.x += sr;
+        if constexpr (CPLX) dst.y += si;
+    }
+}
+
 template <bool CPLX, int R1>
 static void lagrange_points(const ffm_plan_s *p, const FarLevel &F, const LevelArgs &A, const Cheb &cb, bool anterp,
                             const void *in, int nrhs, void *out, cudaStream_t s) {
     typedef typename QT<CPLX>::T Q;
+    // warp per chunk up to r = 64 (the ranks of eps >= 1e-4 for the single layer); the block
+    // forms keep the larger bases, whose per-point sums need more registers per thread
+    if constexpr (R1 <= 4) {
+        if (anterp) {
+            dim3 g(cdiv(F.n_src_chunks, LAG_WC), nrhs);
+            FFM_LAUNCH((k_lag_anterp_w<CPLX, R1>), g, 32 * LAG_WC, 0, s, A, F.src_chunks, F.n_src_chunks, cb,
+                       (const Q *)in, p->ny, nrhs, (Q *)out);
+        } else {
+            dim3 g(cdiv(F.n_tgt_chunks, LAG_WC), nrhs);
+            FFM_LAUNCH((k_lag_interp_w<CPLX, R1>), g, 32 * LAG_WC, 0, s, A, F.tgt_chunks, F.n_tgt_chunks, cb,
+                       (const Q *)in, nrhs, p->nx, (float2 *)out);
+        }
+        return;
+    }
     if (anterp) {
         dim3 g((unsigned)F.n_src_chunks, nrhs);
         FFM_LAUNCH((k_lag_anterp<CPLX, R1>), g, LAG_T, 0, s, A, F.src_chunks, cb, (const Q *)in, p->ny, nrhs,
@@ -1056,7 +1283,7 @@ void far_lagrange(const ffm_plan_s *p, int l, const void *q, int nrhs, float2 *a
         const int ncomp = p->kind == FFM_LAPLACE_GRAD ? 3 : 1;
         const size_t tblk = (size_t)F.n_trans * r * rk;
         const size_t vblk = (size_t)r * nrhs * p->bx[l].nb;
-        float *upad = nullptr;
+        float *upad = nullptr, *uts = nullptr;
         const bool use_tc = !(F.ts_ok && F.Tsp && F.tune_tc == 2) && F.tc_tiles > 0 && F.tune_tc != 0 && F.Tsh;
         if (use_tc) {
             // u~ with rows padded to rkp floats (whole, aligned 16-byte segments for cp.async)
@@ -1068,11 +1295,18 @@ void far_lagrange(const ffm_plan_s *p, int l, const void *q, int nrhs, float2 *a
             const float *Td = F.T + d * tblk;
             float *vtd = (float *)vt + d * vblk;
         if (F.ts_ok && F.Tsp && F.tune_tc == 2) {
-            size_t smem = (size_t)2 * TS_STAGE * sizeof(float);
+            size_t smem = (size_t)TS_NST * TS_STEP * sizeof(float);
             FFM_CUDA(cudaFuncSetAttribute(k_lag_gemm_ts, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            if (!uts) {  // u~ split into hi / lo rows of 64 floats, once for all components
+                int64_t nrow = (int64_t)p->by[l].nb * nrhs;
+                uts = tmp.get<float>((size_t)2 * nrow * 64);
+                unsigned gs = (unsigned)std::min<int64_t>(cdiv(nrow * 64, 256), 152 * 16);
+                FFM_LAUNCH(k_split_rows64, gs, 256, 0, s, (const float *)ut, nrow, r, uts, uts + (size_t)nrow * 64);
+            }
+            const int64_t nrow = (int64_t)p->by[l].nb * nrhs;
             dim3 gts(cdiv(F.n_tgt, TS_M), nrhs);
-            FFM_LAUNCH(k_lag_gemm_ts, gts, 2 * TS_M, smem, s, F.tgt, F.n_tgt, F.adm_off, F.adm_src, F.adm_t, F.n_trans,
-                       F.Tsp, r, nrhs, (const float *)ut, vtd, p->dev_err, p->wait_tries);
+            FFM_LAUNCH(k_lag_gemm_ts, gts, TS_NP + 32, smem, s, F.tgt, F.n_tgt, F.adm_off, F.adm_src, F.adm_t,
+                       F.n_trans, F.Tsp, r, nrhs, uts, uts + (size_t)nrow * 64, vtd, p->dev_err, p->wait_tries);
         } else if (use_tc) {
             // tensor cores: 256-pair tiles, K chunks of 16 source nodes, row blocks of <= 224
             const int rkp = F.rkp;
@@ -1086,6 +1320,7 @@ void far_lagrange(const ffm_plan_s *p, int l, const void *q, int nrhs, float2 *a
             lagrange_points_r1<false>(p, F, AX, cb, false, vtd, nrhs, accf + (size_t)d * nrhs * p->nx, s);
         }
         if (upad) tmp.drop(upad);
+        if (uts) tmp.drop(uts);
     }
 }
 

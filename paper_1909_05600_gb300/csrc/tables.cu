@@ -111,15 +111,19 @@ __global__ void k_lag_table(const int4 *__restrict__ m, int ntrans, LagGeo geo, 
 // block then a 64 x 64 lo block (rows i, K = j; zero beyond r), each in the K-major
 // core-matrix order the MMA reads from shared memory.  hi keeps the TF32 bits (low 13
 // mantissa bits cleared), lo = T - hi exactly.
+// Per translation, the image the target-stationary transfer copies into shared memory for
+// each half of K (source nodes 0..31, 32..63): the TF32 hi block, then the lo block, each 64
+// rows (target nodes) x 32 in the K-major core-matrix layout; zero padded beyond r.
 __global__ void k_lag_table_split(const float *__restrict__ T, int r, float *__restrict__ out) {
     int t = blockIdx.x;
     for (int e = threadIdx.x; e < 64 * 64; e += blockDim.x) {
         int i = e / 64, j = e % 64;
         float v = (i < r && j < r) ? T[(size_t)t * r * r + (size_t)i * r + j] : 0.f;
         float hi = __uint_as_float(__float_as_uint(v) & 0xffffe000u);
-        uint32_t o = kmajor_index(i, j, 64);
-        out[(size_t)t * 8192 + o] = hi;
-        out[(size_t)t * 8192 + 4096 + o] = v - hi;
+        int h = j >> 5;
+        uint32_t o = kmajor_index(i, j & 31, 32);
+        out[(size_t)t * 8192 + h * 4096 + o] = hi;
+        out[(size_t)t * 8192 + h * 4096 + 2048 + o] = v - hi;
     }
 }
 

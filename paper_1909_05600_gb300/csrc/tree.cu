@@ -525,58 +525,114 @@ __global__ void k_lower_bound(const uint32_t *__restrict__ needle, int64_t nb, c
 
 // ================================================================== descent
 
-
-
 // Two-pass expansion without candidate arrays: pass 1 counts the admissible children of
 // each near pair, pass 2 writes admissible and near child pairs at their scanned offsets.
 // Children of (a, b) are visited in the same order in both passes.
-__device__ __forceinline__ bool child_admissible(int4 p, int4 q, const D3 &sig) {
-    return fabs(sig.v[0] + (double)(p.x - q.x)) >= 2.0 || fabs(sig.v[1] + (double)(p.y - q.y)) >= 2.0 ||
-           fabs(sig.v[2] + (double)(p.z - q.z)) >= 2.0;
+
+// Admissibility of a child pair as integer comparisons.  The offset test |sigma + k| >= 2
+// (k = g_X - g_Y per axis, sigma the trees' shift in box units, FP64) depends on k through
+// the rounded sum fl(sigma + k), which is non-decreasing in k: it holds exactly for k >= klo
+// or k <= khi, the two integer thresholds found on the host by evaluating that same FP64
+// sum (adm_thresholds).  The decision is therefore the FP64 one, bit for bit.
+struct AdmK {
+    int lo[3], hi[3];
+};
+
+__device__ __forceinline__ bool child_adm_k(int4 p, int4 q, const AdmK &K) {
+    int kx = p.x - q.x, ky = p.y - q.y, kz = p.z - q.z;
+    return kx >= K.lo[0] || kx <= K.hi[0] || ky >= K.lo[1] || ky <= K.hi[1] || kz >= K.lo[2] || kz <= K.hi[2];
 }
 
-__global__ void k_expand_count(const uint32_t *__restrict__ na, const uint32_t *__restrict__ nbb, int64_t nnear,
-                               const uint32_t *__restrict__ fcx, const uint32_t *__restrict__ fcy,
-                               const int4 *__restrict__ gx, const int4 *__restrict__ gy, D3 sig,
-                               uint32_t *__restrict__ nadm, uint32_t *__restrict__ nnr) {
-    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= nnear) return;
-    uint32_t a = na[e], b = nbb[e];
-    uint32_t c = 0, t = 0;
-    for (uint32_t a2 = fcx[a]; a2 < fcx[a + 1]; ++a2) {
-        int4 p = gx[a2];
-        for (uint32_t b2 = fcy[b]; b2 < fcy[b + 1]; ++b2) {
-            c += child_admissible(p, gy[b2], sig) ? 1u : 0u;
-            ++t;
-        }
+static AdmK adm_thresholds(const D3 &sig) {
+    AdmK K;
+    for (int d = 0; d < 3; ++d) {
+        const volatile double sv = sig.v[d];
+        // smallest k with fl(sigma + k) >= 2, largest k with fl(sigma + k) <= -2
+        int lo = (int)std::floor(2.0 - sv) - 2;
+        while (!(sv + (double)lo >= 2.0)) ++lo;
+        while (sv + (double)(lo - 1) >= 2.0) --lo;
+        int hi = (int)std::ceil(-2.0 - sv) + 2;
+        while (!(sv + (double)hi <= -2.0)) --hi;
+        while (sv + (double)(hi + 1) <= -2.0) ++hi;
+        K.lo[d] = lo;
+        K.hi[d] = hi;
     }
-    nadm[e] = c;
-    nnr[e] = t - c;
+    return K;
 }
 
-__global__ void k_expand_emit(const uint32_t *__restrict__ na, const uint32_t *__restrict__ nbb, int64_t nnear,
-                              const uint32_t *__restrict__ fcx, const uint32_t *__restrict__ fcy,
-                              const int4 *__restrict__ gx, const int4 *__restrict__ gy, D3 sig,
-                              const uint32_t *__restrict__ oadm, const uint32_t *__restrict__ onr,
-                              uint32_t *__restrict__ aa, uint32_t *__restrict__ ab, uint32_t *__restrict__ ea,
-                              uint32_t *__restrict__ eb) {
-    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+// One warp per near pair (a, b) of level l: lane c takes child pair c and c + 32 of the at
+// most 8 x 8 children (a2 = first child of a + c / nb, b2 = first child of b + c % nb);
+// ballots count and place the admissible ones and the near ones, so a warp writes its
+// pairs contiguously.
+constexpr int EXP_W = 8;  // warps (near pairs) per block
+
+__global__ void __launch_bounds__(32 * EXP_W) k_expand_count(const uint32_t *__restrict__ na,
+                                                            const uint32_t *__restrict__ nbb, int64_t nnear,
+                                                            const uint32_t *__restrict__ fcx,
+                                                            const uint32_t *__restrict__ fcy,
+                                                            const int4 *__restrict__ gx, const int4 *__restrict__ gy,
+                                                            AdmK K, uint32_t *__restrict__ nadm,
+                                                            uint32_t *__restrict__ nnr) {
+    const int lane = threadIdx.x & 31;
+    const int64_t e = (int64_t)blockIdx.x * EXP_W + (threadIdx.x >> 5);
     if (e >= nnear) return;
-    uint32_t a = na[e], b = nbb[e];
+    const uint32_t a = na[e], b = nbb[e];
+    const uint32_t a0 = fcx[a], b0 = fcy[b];
+    const int nax = (int)(fcx[a + 1] - a0), nby = (int)(fcy[b + 1] - b0), tot = nax * nby;
+    uint32_t c = 0;
+    for (int c0 = 0; c0 < tot; c0 += 32) {
+        const int ci = c0 + lane;
+        bool adm = false;
+        if (ci < tot) adm = child_adm_k(gx[a0 + ci / nby], gy[b0 + ci % nby], K);
+        c += __popc(__ballot_sync(0xffffffffu, adm));
+    }
+    if (lane == 0) {
+        nadm[e] = c;
+        nnr[e] = (uint32_t)tot - c;
+    }
+}
+
+__global__ void __launch_bounds__(32 * EXP_W) k_expand_emit(const uint32_t *__restrict__ na,
+                                                           const uint32_t *__restrict__ nbb, int64_t nnear,
+                                                           const uint32_t *__restrict__ fcx,
+                                                           const uint32_t *__restrict__ fcy,
+                                                           const int4 *__restrict__ gx, const int4 *__restrict__ gy,
+                                                           AdmK K, const uint32_t *__restrict__ oadm,
+                                                           const uint32_t *__restrict__ onr, uint32_t *__restrict__ aa,
+                                                           uint32_t *__restrict__ ab, uint32_t *__restrict__ ea,
+                                                           uint32_t *__restrict__ eb) {
+    const int lane = threadIdx.x & 31;
+    const int64_t e = (int64_t)blockIdx.x * EXP_W + (threadIdx.x >> 5);
+    if (e >= nnear) return;
+    const uint32_t a = na[e], b = nbb[e];
+    const uint32_t a0 = fcx[a], b0 = fcy[b];
+    const int nax = (int)(fcx[a + 1] - a0), nby = (int)(fcy[b + 1] - b0), tot = nax * nby;
     uint32_t ia = oadm[e], in = onr[e];
-    for (uint32_t a2 = fcx[a]; a2 < fcx[a + 1]; ++a2) {
-        int4 p = gx[a2];
-        for (uint32_t b2 = fcy[b]; b2 < fcy[b + 1]; ++b2) {
-            if (child_admissible(p, gy[b2], sig)) {
-                aa[ia] = a2;
-                ab[ia] = b2;
-                ++ia;
+    const uint32_t below = (1u << lane) - 1u;
+    for (int c0 = 0; c0 < tot; c0 += 32) {
+        const int ci = c0 + lane;
+        const bool valid = ci < tot;
+        uint32_t a2 = 0, b2 = 0;
+        bool adm = false;
+        if (valid) {
+            a2 = a0 + (uint32_t)(ci / nby);
+            b2 = b0 + (uint32_t)(ci % nby);
+            adm = child_adm_k(gx[a2], gy[b2], K);
+        }
+        const uint32_t ma = __ballot_sync(0xffffffffu, valid && adm), mn = __ballot_sync(0xffffffffu, valid && !adm);
+        if (valid) {
+            if (adm) {
+                uint32_t o = ia + __popc(ma & below);
+                aa[o] = a2;
+                ab[o] = b2;
             } else {
-                ea[in] = a2;
-                eb[in] = b2;
-                ++in;
+                uint32_t o = in + __popc(mn & below);
+                ea[o] = a2;
+                eb[o] = b2;
             }
         }
+        ia += __popc(ma);
+        in += __popc(mn);
     }
 }
 
@@ -589,20 +645,28 @@ __global__ void k_gather_u32(const uint32_t *__restrict__ src, const uint32_t *_
 
 // Translation code of a pair: integer offset m = gX - gY relative to c = round(-sigma 2^l),
 // 4 bits per axis (the descent bounds |sigma 2^l + m| < 5).
+// Translation code of every pair; the codes in use are collected in a 4096-bit map per block
+// (shared atomics) and written once per block and code, not once per pair.
 __global__ void k_trans_code(const uint32_t *__restrict__ a, const uint32_t *__restrict__ b, int64_t n,
                              const int4 *__restrict__ gx, const int4 *__restrict__ gy, int4 c,
                              uint32_t *__restrict__ code, uint32_t *__restrict__ used, int *__restrict__ err) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    int4 p = gx[a[i]], q = gy[b[i]];
-    int mx = p.x - q.x - c.x + 8, my = p.y - q.y - c.y + 8, mz = p.z - q.z - c.z + 8;
-    if (mx < 0 || mx > 15 || my < 0 || my > 15 || mz < 0 || mz > 15) {
-        atomicOr(err, 1);
-        mx = my = mz = 0;
+    __shared__ uint32_t bits[128];
+    if (threadIdx.x < 128) bits[threadIdx.x] = 0u;
+    __syncthreads();
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        int4 p = gx[a[i]], q = gy[b[i]];
+        int mx = p.x - q.x - c.x + 8, my = p.y - q.y - c.y + 8, mz = p.z - q.z - c.z + 8;
+        if (mx < 0 || mx > 15 || my < 0 || my > 15 || mz < 0 || mz > 15) {
+            atomicOr(err, 1);
+            mx = my = mz = 0;
+        }
+        uint32_t k = (uint32_t)(mx | (my << 4) | (mz << 8));
+        code[i] = k;
+        atomicOr(&bits[k >> 5], 1u << (k & 31));
     }
-    uint32_t k = (uint32_t)(mx | (my << 4) | (mz << 8));
-    code[i] = k;
-    used[k] = 1u;
+    __syncthreads();
+    for (int k = threadIdx.x; k < 4096; k += blockDim.x)
+        if (bits[k >> 5] & (1u << (k & 31))) used[k] = 1u;
 }
 
 __global__ void k_trans_list(const uint32_t *__restrict__ used, const uint32_t *__restrict__ pos, int4 c,
@@ -966,46 +1030,67 @@ static uint2 *build_chunks(ffm_plan_s *p, const uint32_t *list, int64_t n, const
     return out;
 }
 
-// Admissible partners of each target box sorted by translation index (one warp per target,
-// bitonic sort of (translation, source) keys in shared memory; translations are distinct
-// within a target).  Targets with more than 512 partners are left as they are and flagged.
+// Admissible partners of each target box sorted by translation index, one warp per target.
+// Translations are distinct within a target and below 4096, so the sort is a rank by
+// counting: the warp sets one bit per partner's translation in a 4096-bit map in shared
+// memory, prefix-counts the map's words, and each partner's rank is the number of set bits
+// below its own.  Targets with more than 512 partners are left as they are and flagged.
+constexpr int SP_MAX = 512;
 __global__ void __launch_bounds__(128) k_sort_partners(const uint32_t *__restrict__ off, int64_t n_tgt,
                                                        uint32_t *__restrict__ src, uint32_t *__restrict__ tr,
                                                        int *__restrict__ too_long) {
-    __shared__ unsigned long long sk[4][512];
+    __shared__ uint32_t bm[4][128], pre[4][128];
     int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int64_t x = (int64_t)blockIdx.x * 4 + w;
     if (x >= n_tgt) return;  // warp-level work only: no block barrier below
     uint32_t e0 = off[x];
     int n = (int)(off[x + 1] - e0);
-    if (n > 512) {
+    if (n > SP_MAX) {
         if (lane == 0) atomicOr(too_long, 1);
         return;
     }
-    int P = 32;
-    while (P < n) P <<= 1;
-    unsigned long long *k = sk[w];
-    for (int i = lane; i < P; i += 32)
-        k[i] = i < n ? ((unsigned long long)tr[e0 + i] << 32) | src[e0 + i] : ~0ull;
+    uint32_t *b = bm[w], *pr = pre[w];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) b[lane * 4 + j] = 0u;
     __syncwarp();
-    for (int size = 2; size <= P; size <<= 1)
-        for (int stride = size >> 1; stride > 0; stride >>= 1) {
-            for (int i = lane; i < P; i += 32) {
-                int j = i ^ stride;
-                if (j > i) {
-                    bool up = (i & size) == 0;
-                    unsigned long long a = k[i], b = k[j];
-                    if ((a > b) == up) {
-                        k[i] = b;
-                        k[j] = a;
-                    }
-                }
-            }
-            __syncwarp();
+    uint32_t t[SP_MAX / 32], sv[SP_MAX / 32];
+#pragma unroll
+    for (int k = 0; k < SP_MAX / 32; ++k) {
+        int i = lane + 32 * k;
+        if (i < n) {
+            t[k] = tr[e0 + i];
+            sv[k] = src[e0 + i];
+            atomicOr(&b[t[k] >> 5], 1u << (t[k] & 31));
         }
-    for (int i = lane; i < n; i += 32) {
-        tr[e0 + i] = (uint32_t)(k[i] >> 32);
-        src[e0 + i] = (uint32_t)k[i];
+    }
+    __syncwarp();
+    uint32_t c[4], tot = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        c[j] = __popc(b[lane * 4 + j]);
+        tot += c[j];
+    }
+    uint32_t inc = tot;
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t v = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += v;
+    }
+    uint32_t run = inc - tot;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        pr[lane * 4 + j] = run;
+        run += c[j];
+    }
+    __syncwarp();
+#pragma unroll
+    for (int k = 0; k < SP_MAX / 32; ++k) {
+        int i = lane + 32 * k;
+        if (i < n) {
+            uint32_t q = t[k];
+            uint32_t rank = pr[q >> 5] + __popc(b[q >> 5] & ((1u << (q & 31)) - 1u));
+            tr[e0 + rank] = q;
+            src[e0 + rank] = sv[k];
+        }
     }
 }
 
@@ -1111,7 +1196,8 @@ static void finish_far_level(ffm_plan_s *p, int l, uint32_t *aa, uint32_t *ab, i
     int *err = tmp.get<int>(1);
     FFM_CUDA(cudaMemsetAsync(used, 0, 4096 * sizeof(uint32_t), s));
     FFM_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
-    FFM_LAUNCH(k_trans_code, cdiv(na, 256), 256, 0, s, c.a, c.b, na, p->bx[l].g, p->by[l].g, cc, code, used, err);
+    FFM_LAUNCH(k_trans_code, std::min<unsigned>(cdiv(na, 256), 152u * 8u), 256, 0, s, c.a, c.b, na, p->bx[l].g,
+               p->by[l].g, cc, code, used, err);
     scan_u32(used, upos, 4096, tot, tmp, s);
     F.adm_t = p->mem.get<uint32_t>(na);
     FFM_LAUNCH(k_map, cdiv(na, 256), 256, 0, s, code, upos, na, F.adm_t);
@@ -1304,8 +1390,9 @@ void build_plan(ffm_plan_s *p, const void *X, ffm_dtype xdt, const void *Y, ffm_
             uint32_t *nadm = lvl.get<uint32_t>(nnear), *nnr = lvl.get<uint32_t>(nnear);
             uint32_t *oadm = lvl.get<uint32_t>(nnear), *onr = lvl.get<uint32_t>(nnear);
             uint32_t *tot = lvl.get<uint32_t>(2);
-            FFM_LAUNCH(k_expand_count, cdiv(nnear, 128), 128, 0, s, nearA, nearB, nnear, p->bx[l].first_child,
-                       p->by[l].first_child, p->bx[lc].g, p->by[lc].g, sg, nadm, nnr);
+            const AdmK K = adm_thresholds(sg);
+            FFM_LAUNCH(k_expand_count, cdiv(nnear, EXP_W), 32 * EXP_W, 0, s, nearA, nearB, nnear,
+                       p->bx[l].first_child, p->by[l].first_child, p->bx[lc].g, p->by[lc].g, K, nadm, nnr);
             scan_u32(nadm, oadm, nnear, tot, lvl, s);
             scan_u32(nnr, onr, nnear, tot + 1, lvl, s);
             uint32_t htot[2];
@@ -1314,8 +1401,9 @@ void build_plan(ffm_plan_s *p, const void *X, ffm_dtype xdt, const void *Y, ffm_
             int64_t na = htot[0], nn = htot[1];
             uint32_t *aa = lvl.get<uint32_t>(na), *ab = lvl.get<uint32_t>(na);
             uint32_t *ea = lvl.get<uint32_t>(nn), *eb = lvl.get<uint32_t>(nn);
-            FFM_LAUNCH(k_expand_emit, cdiv(nnear, 128), 128, 0, s, nearA, nearB, nnear, p->bx[l].first_child,
-                       p->by[l].first_child, p->bx[lc].g, p->by[lc].g, sg, oadm, onr, aa, ab, ea, eb);
+            FFM_LAUNCH(k_expand_emit, cdiv(nnear, EXP_W), 32 * EXP_W, 0, s, nearA, nearB, nnear,
+                       p->bx[l].first_child, p->by[l].first_child, p->bx[lc].g, p->by[lc].g, K, oadm, onr, aa, ab,
+                       ea, eb);
             // the previous level's near list is no longer needed
             if (l >= 1) levels[l].release();
             finish_far_level(p, lc, aa, ab, na, lvl, s);
