@@ -64,6 +64,9 @@ def parse():
     ap.add_argument("--eps", type=float, default=0.0, help="accuracy eps (0: the workload's own)")
     ap.add_argument("--aca", type=float, default=0.0, metavar="EPS_T",
                     help="Laplace workloads: transfer matrices as ACA factors to this tolerance (eq. 11)")
+    ap.add_argument("--lagrange-transfer", default="default", choices=["default", "cuda", "tc", "ts"],
+                    help="Laplace Lagrange transfer: the default / autotuned pick, or forced (CUDA cores, tcgen05 "
+                         "per translation, tcgen05 target-stationary)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="default kernel variants instead of ffm_autotune's picks")
     return ap.parse_args()
@@ -305,23 +308,27 @@ def run_reference(args, rank):
     print(json.dumps(line), flush=True)
 
 
-def measured_traffic(kernel, workload):
-    """DRAM bytes per launch of `kernel` on `workload` from a committed ncu summary
-    (profiles/traffic_*.txt), or None when there is none or the kernel's source file has
-    changed since the counters were taken."""
-    import glob
+def measured_traffic(kernel):
+    """DRAM bytes per algorithmic unit of `kernel` (the unit of its roofline family) from the
+    committed ncu summary profiles/traffic.txt, or None when there is none or the kernel's
+    source file has changed since the counters were taken.  Each line:
+    kernel  capture_workload  bytes_per_unit  unit  source_file  source_sha256[:16]."""
     import hashlib
-    for path in glob.glob(os.path.join(ROOT, "profiles", "traffic_*.txt")):
-        for line in open(path):
-            f = line.split()
-            if len(f) != 5 or line.startswith("#") or f[0] != kernel or f[1] != workload:
-                continue
-            src = os.path.join(ROOT, "paper_1909_05600_gb300", f[3])
-            try:
-                h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-            except OSError:
-                return None
-            return float(f[2]) if h == f[4] else None
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    try:
+        lines = open(path).read().splitlines()
+    except OSError:
+        return None
+    for line in lines:
+        f = line.split()
+        if len(f) != 6 or line.startswith("#") or f[0] != kernel:
+            continue
+        src = os.path.join(ROOT, "paper_1909_05600_gb300", "csrc", f[4])
+        try:
+            h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        except OSError:
+            return None
+        return {"bytes_per_unit": float(f[2]), "unit": f[3], "captured_on": f[1]} if h == f[5] else None
     return None
 
 
@@ -350,8 +357,7 @@ def roofline(prof, info, steps, clk, pk, pk_kind, workload):
     dl = workload.startswith("laplace_double_layer")
     grad = workload.startswith("laplace_gradient")
     kfac = 3 if dl or grad else 1
-    out = {"kernel": name, "launches_per_step": nl / steps, "ms_per_step": ms / steps,
-           "traffic": measured_traffic(name, workload)}
+    out = {"kernel": name, "launches_per_step": nl / steps, "ms_per_step": ms / steps, "traffic": None}
     per_s = lambda units: units * steps / (ms * 1e-3)
     basis = "%d SMs x %%s x %.0f MHz (max SM clock, %s peaks file)" % (SM_COUNT, mhz, pk_kind)
     if "k_pw_forward" in name or "k_pw_backward" in name:
@@ -430,6 +436,13 @@ def roofline(prof, info, steps, clk, pk, pk_kind, workload):
         return out
     achieved = per_s(units) / 1e12
     out.update({"achieved": achieved, "peak": peak / 1e12, "frac": achieved / (peak / 1e12)})
+    # DRAM bytes per launch: the per-unit figure of a one-launch ncu capture on a smaller case
+    # of the same workload, times this step's units per launch
+    tr = measured_traffic(name)
+    if tr is not None:
+        out["traffic"] = tr["bytes_per_unit"] * units / max(nl / steps, 1e-9)
+        out["traffic_basis"] = ("dram__bytes_read.sum + dram__bytes_write.sum per %s from one ncu capture on %s, "
+                                "scaled to this step's units per launch" % (tr["unit"], tr["captured_on"]))
     return out
 
 
@@ -685,6 +698,9 @@ def main():
     kw["pw_transform"] = {"auto": ffm.PW_AUTO, "direct": ffm.PW_DIRECT, "nufft": ffm.PW_NUFFT}[args.pw_transform]
     if args.aca > 0:
         kw["aca_eps"] = args.aca
+    if args.lagrange_transfer != "default":
+        kw["lagrange_transfer"] = {"cuda": ffm.LAG_CUDA_CORES, "tc": ffm.LAG_TC_TRANSLATION,
+                                   "ts": ffm.LAG_TC_TARGET}[args.lagrange_transfer]
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
 
@@ -776,8 +792,9 @@ def main():
         uh = torch.as_tensor(u_host).pin_memory()
         kwh = {k: torch.as_tensor(prob.meta[k]).pin_memory() for k in kw if k in prob.meta}
         kwh["pw_transform"] = kw["pw_transform"]
-        if "aca_eps" in kw:
-            kwh["aca_eps"] = kw["aca_eps"]
+        for key in ("aca_eps", "lagrange_transfer"):
+            if key in kw:
+                kwh[key] = kw[key]
         vshape = tuple(uh.shape[:-1]) + ((3,) if prob.kind == W.LAPLACE_GRAD else ()) + (prob.X.shape[0],)
         vh = torch.empty(vshape, dtype=uh.dtype).pin_memory()
         ke = max(2, min(args.steps // 2, math.ceil(15.0 / max(step_s, 1e-9))))
@@ -825,6 +842,7 @@ def main():
                        "u_dtype": str(prob.u.dtype), "step": "ffm_plan + ffm_apply + ffm_destroy",
                        "l2": "flushed between steps (512 MiB write, outside the step events)",
                        "replicas": world, "nrhs": nrhs, "pw_transform": args.pw_transform,
+                       "lagrange_transfer": args.lagrange_transfer,
                        **({"aca_eps": args.aca} if args.aca > 0 else {})},
             "mpoints_per_s": n * value / 1e6, "rhs_per_s": value * nrhs,
             "t_plan_ms": t_plan / args.steps, "t_apply_ms": t_apply / args.steps,
@@ -838,6 +856,8 @@ def main():
                      "L": info["L"][:info["l_stop"] + 1], "nQ": info["nQ"][:info["l_stop"] + 1],
                      "n_adm": info["n_adm"][:info["l_stop"] + 1], "p2p_pairs": info["p2p_pairs"],
                      "nufft": info["nufft"][:info["l_stop"] + 1], "nufft_n2": info["nufft_n2"][:info["l_stop"] + 1],
+                     "pw_prec": info["pw_prec"][:info["l_stop"] + 1], "cancel": info["cancel"][:info["l_stop"] + 1],
+                     "tune_tc": info["tune_tc"][:info["l_stop"] + 1],
                      **({"aca_rank": info["aca_rank"][:info["l_stop"] + 1]} if args.aca > 0 else {})},
         }
         if note:

@@ -397,12 +397,17 @@ __device__ __forceinline__ void cp_async16(void *dst, const void *src) {
 
 // Bounded wait for the completion of phase `parity` of an mbarrier: at most `tries`
 // try_wait attempts (none for tries <= 0); false if it gave up.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int tries) {
+// With `abort` (the launch's device error flag), the wait also gives up once another CTA has
+// raised the flag (checked every 1024 attempts), so one failure does not make every later
+// CTA spend its whole limit.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int tries, const int *abort = nullptr) {
     uint32_t done = 0;
-    for (int it = 0; it < tries && !done; ++it)
+    for (int it = 0; it < tries && !done; ++it) {
         asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
                      : "=r"(done)
                      : "r"(smem_addr(bar)), "r"(parity));
+        if (!done && abort && (it & 1023) == 1023 && *reinterpret_cast<const volatile int *>(abort)) break;
+    }
     return done != 0;
 }
 
@@ -410,16 +415,6 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int tr
 // already committed before it releases TMEM and exits (they read its shared memory and
 // write its TMEM columns); that wait is bounded too, by this larger count.
 constexpr int DRAIN_TRIES = 1 << 28;
-
-// Wait for committed tensor-core work (its commit arrives on `bar`): at most `tries`
-// attempts; after a give-up, recorded in ok, the wait goes on up to DRAIN_TRIES, because
-// the MMAs still read the stage and write TMEM.
-__device__ __forceinline__ void mma_wait(uint64_t *bar, uint32_t parity, int tries, bool &ok) {
-    if (!mbar_wait(bar, parity, tries)) {
-        ok = false;
-        mbar_wait(bar, parity, DRAIN_TRIES);
-    }
-}
 
 __device__ __forceinline__ void store_split(float *hi, float *lo, uint32_t o, float4 x) {
     float4 h, l;
@@ -521,7 +516,7 @@ __global__ void __launch_bounds__(256) k_lag_gemm_tc(const uint32_t *__restrict_
             const int b = kn % NO;
             // MMAs of kn - NO done; a thread that gives up stops copying (its copies in
             // flight are awaited below)
-            if (kn >= NO && !mbar_wait(&s_empty[b], (uint32_t)((kn / NO - 1) & 1), tries)) {
+            if (kn >= NO && !mbar_wait(&s_empty[b], (uint32_t)((kn / NO - 1) & 1), tries, err)) {
                 ok = false;
                 break;
             }
@@ -544,7 +539,7 @@ __global__ void __launch_bounds__(256) k_lag_gemm_tc(const uint32_t *__restrict_
         int issued = 0;  // chunks whose MMAs were committed
         for (int kc = 0; kc < nk; ++kc) {
             const int b = kc % NO;
-            if (!mbar_wait(&s_full[b], (uint32_t)((kc / NO) & 1), tries)) {
+            if (!mbar_wait(&s_full[b], (uint32_t)((kc / NO) & 1), tries, err)) {
                 ok = false;  // operands not ready: issue nothing more
                 break;
             }
@@ -582,7 +577,7 @@ __global__ void __launch_bounds__(256) k_lag_gemm_tc(const uint32_t *__restrict_
         if (issued > 0) {
             uint64_t *last = &s_empty[(issued - 1) % NO];
             const uint32_t par = (uint32_t)(((issued - 1) / NO) & 1);
-            if (!ok || !mbar_wait(last, par, tries)) {
+            if (!ok || !mbar_wait(last, par, tries, err)) {
                 ok = false;
                 mbar_wait(last, par, DRAIN_TRIES);
             }
@@ -660,15 +655,19 @@ __global__ void k_split_pad(const float *__restrict__ src, int64_t nmat, int row
 // TMEM; each target's v~ is written once, with no atomics.  TF32 hi/lo split with three
 // MMAs per K step (hi hi + hi lo + lo hi), FP32 accumulation.
 //
-// Pipeline.  A step is one translation and one half of K (32 source nodes).  Warps 1-8
-// produce: the two threads of a target row copy the hi and the lo part of its source row's
-// half (8 x 16 B each, zero-filled where the row has no partner) with cp.async straight into
-// the K-major core-matrix layout, and together they copy T_t's pre-split image of that half
-// (16 KB), into a ring of TS_NST stages; each thread's copies arrive on the stage's "full"
-// mbarrier once they have landed (cp.async.mbarrier.arrive).  One thread of warp 0 waits on
-// "full", issues the step's 12 MMAs and commits them to the stage's "empty" mbarrier, which
-// the producers wait on before they reuse the stage.  u~ arrives pre-split into hi and lo
-// rows of 64 floats, so producers do no arithmetic and never wait for their own loads.
+// Operands.  The A operand (the gathered source rows) lives in tensor memory: the MMAs read
+// it from TMEM, so shared memory only carries T_t (the B operand), and the operand reads of
+// the tensor cores from shared memory drop to a third.  A step is one translation and one
+// half of K (32 source nodes).  Warps 1-8 produce; the two producers of a target row each
+// own 16 of the step's 32 values.  A producer loads its values of the row's source (zero
+// where the row has no partner) from global memory into registers TS_P steps ahead, splits
+// them into TF32 hi and lo parts and writes them into one of TS_NA TMEM operand stages
+// (tcgen05.st), then arrives on that stage's "A full" mbarrier.  It also copies its share of
+// T_t's pre-split image of the half (16 KB in all) with cp.async into one of TS_NB shared
+// stages, TS_DB steps ahead, and arrives on that stage's "B full" mbarrier once the copies
+// land.  One thread of warp 0 waits on both, issues the step's 12 MMAs and commits them to
+// the B stage's "empty" mbarrier; the producers wait on it (TS_NA steps later) before they
+// reuse the A and B stages.
 //
 // Accumulation.  One long tcgen05 accumulation loses accuracy, so the tile alternates
 // between two TMEM accumulators (64 columns each) every TS_DRAIN translations; the producers
@@ -677,51 +676,53 @@ __global__ void k_split_pad(const float *__restrict__ src, int64_t nmat, int row
 // Every wait is bounded; a give-up raises the device error flag, the CTA then waits for its
 // copies and committed MMAs, skips its results and frees TMEM.
 constexpr int TS_M = 128;
-constexpr int TS_KH = 32;                       // source nodes per step (half of K = 64)
-constexpr int TS_AH = TS_M * TS_KH;             // floats per A hi or lo block of a step
-constexpr int TS_BH = 64 * TS_KH;               // floats per B hi or lo block of a step
-constexpr int TS_STEP = 2 * TS_AH + 2 * TS_BH;  // floats per stage (48 KB)
-constexpr int TS_NST = 4;                       // stages
-constexpr int TS_MAXT = 4096;                   // translation codes lie in a 16^3 range
-constexpr int TS_DRAIN = 8;                     // translations per TMEM accumulator fill
-constexpr int TS_NP = 2 * TS_M;                 // producer threads (warps 1-8)
+constexpr int TS_KH = 32;             // source nodes per step (half of K = 64)
+constexpr int TS_BH = 64 * TS_KH;     // floats per B hi or lo block of a step
+constexpr int TS_BST = 2 * TS_BH;     // floats per B stage (16 KB)
+constexpr int TS_NA = 4;              // A stages (tensor memory); producers run TS_NA steps ahead
+constexpr int TS_DB = 2;              // steps the copies of T_t's image run ahead
+constexpr int TS_NB = TS_NA + TS_DB;  // B stages (shared memory)
+constexpr int TS_P = 4;               // steps the source loads run ahead (registers)
+constexpr int TS_MAXT = 4096;         // translation codes lie in a 16^3 range
+constexpr int TS_DRAIN = 8;           // translations per TMEM accumulator fill
+constexpr int TS_NP = 2 * TS_M;       // producer threads (warps 1-8)
+constexpr int TS_TCOLS = 512;         // TMEM: 2 accumulators x 64 columns, TS_NA A stages x 64 (hi, lo)
+constexpr size_t TS_SMEM = sizeof(float) * (size_t)TS_NB * TS_BST;
 
-// 16-byte cp.async that copies src_bytes (0 or 16) and zero-fills the rest
-__device__ __forceinline__ void cp_async16_zfill(void *dst, const void *src, uint32_t src_bytes) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_addr(dst)), "l"(src), "r"(src_bytes)
-                 : "memory");
-}
-
-__global__ void __launch_bounds__(TS_NP + 32) k_lag_gemm_ts(const uint32_t *__restrict__ tgt, int64_t n_tgt,
-                                                           const uint32_t *__restrict__ adm_off,
-                                                           const uint32_t *__restrict__ adm_src,
-                                                           const uint32_t *__restrict__ adm_t, int n_trans,
-                                                           const float *__restrict__ Tsp, int r, int nrhs,
-                                                           const float *__restrict__ uhi,
-                                                           const float *__restrict__ ulo, float *__restrict__ vt,
-                                                           int *__restrict__ err, int tries) {
+// u holds rows of 64 floats (r <= 64, zero padded): row (b, m) at ((b nrhs + m) 64).
+__global__ void __launch_bounds__(TS_NP + 32, 1) k_lag_gemm_ts(const uint32_t *__restrict__ tgt, int64_t n_tgt,
+                                                              const uint32_t *__restrict__ adm_off,
+                                                              const uint32_t *__restrict__ adm_src,
+                                                              const uint32_t *__restrict__ adm_t, int n_trans,
+                                                              const float *__restrict__ Tsp, int r, int nrhs,
+                                                              const float *__restrict__ u, float *__restrict__ vt,
+                                                              int *__restrict__ err, int tries) {
     extern __shared__ __align__(1024) unsigned char smem[];
-    float *stage0 = reinterpret_cast<float *>(smem);
+    float *bring = reinterpret_cast<float *>(smem);
     __shared__ uint32_t s_bits[TS_MAXT / 32];
+    __shared__ uint16_t s_tl[TS_MAXT];  // the translations present, in increasing order
+    __shared__ uint32_t s_wpre[TS_MAXT / 32 + 1];
     __shared__ uint32_t s_tmem;
-    __shared__ __align__(8) uint64_t s_full[TS_NST], s_empty[TS_NST], s_drained;
+    __shared__ __align__(8) uint64_t s_bfull[TS_NB], s_empty[TS_NB], s_afull[TS_NA], s_drained;
     __shared__ int s_bad;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int m = blockIdx.y;
     const int64_t x0 = (int64_t)blockIdx.x * TS_M;
     const int nw = (n_trans + 31) / 32;
-    for (int w = tid; w < nw; w += blockDim.x) s_bits[w] = 0u;
+    for (int w = tid; w < TS_MAXT / 32; w += blockDim.x) s_bits[w] = 0u;
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&s_tmem)),
-                     "r"(128));
+                     "r"(TS_TCOLS));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
         s_bad = 0;
-        for (int i = 0; i < TS_NST; ++i) {
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(&s_full[i])), "r"(TS_NP));
+        for (int i = 0; i < TS_NB; ++i) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(&s_bfull[i])), "r"(TS_NP));
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&s_empty[i])));
         }
+        for (int i = 0; i < TS_NA; ++i)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(&s_afull[i])), "r"(TS_NP));
         asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(&s_drained)), "r"(TS_NP));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -729,30 +730,45 @@ __global__ void __launch_bounds__(TS_NP + 32) k_lag_gemm_ts(const uint32_t *__re
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = s_tmem;
-    // producers: row (TMEM lane) and part (0: hi, 1: lo) they copy
+    // producers: warp w (1-8) holds TMEM lanes 32 (w % 4) .. + 31, one target row per lane,
+    // and values 16 qh .. 16 qh + 15 of each step's half
     const bool prod = warp >= 1;
-    const int p = tid - 32, row = p & (TS_M - 1), part = p >> 7;
+    const int dq = warp & 3, qh = (warp - 1) >> 2, row = dq * 32 + lane;
     const int64_t x = x0 + row;
     const bool has = prod && x < n_tgt;
     uint32_t cur = has ? adm_off[x] : 0u, end = has ? adm_off[x + 1] : 0u;
-    if (has && part == 0)
+    if (has && qh == 0)
         for (uint32_t e = cur; e < end; ++e) {
             uint32_t t = adm_t[e];
             atomicOr(&s_bits[t >> 5], 1u << (t & 31));
         }
     __syncthreads();
+    // list of the translations present: word counts, their prefix, then the set bits in order
+    if (tid < TS_MAXT / 32) s_wpre[tid + 1] = __popc(s_bits[tid]);
+    if (tid == 0) s_wpre[0] = 0u;
+    __syncthreads();
+    if (tid == 0)
+        for (int w = 1; w <= TS_MAXT / 32; ++w) s_wpre[w] += s_wpre[w - 1];
+    __syncthreads();
+    if (tid < nw) {
+        uint32_t bits = s_bits[tid], o = s_wpre[tid];
+        while (bits) {
+            s_tl[o++] = (uint16_t)(tid * 32 + __ffs(bits) - 1);
+            bits &= bits - 1;
+        }
+    }
+    __syncthreads();
+    const int nsteps = 2 * (int)s_wpre[TS_MAXT / 32];
     bool ok = true;
-    int total = 0;  // steps issued or produced
     if (prod) {
-        // drain rows / columns: warp w reads TMEM lanes 32 (w % 4) .. + 31, columns dcol .. + 31
-        const int dq = warp & 3, dcol = ((warp - 1) >> 2) * 32;
+        const int p = tid - 32;
         float sum[32];
 #pragma unroll
         for (int c = 0; c < 32; ++c) sum[c] = 0.f;
-        int drained = 0;  // accumulator fills added into sum
+        int drained = 0;  // accumulator fills added into sum (columns 32 qh .. + 31)
         auto drain = [&](int k) {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t base = tmem + (uint32_t)((k & 1) * 64 + dcol) + ((uint32_t)(dq * 32) << 16);
+            const uint32_t base = tmem + (uint32_t)((k & 1) * 64 + qh * 32) + ((uint32_t)(dq * 32) << 16);
 #pragma unroll
             for (int c0 = 0; c0 < 32; c0 += 8) {
                 uint32_t v[8];
@@ -767,149 +783,184 @@ __global__ void __launch_bounds__(TS_NP + 32) k_lag_gemm_ts(const uint32_t *__re
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(&s_drained)) : "memory");
         };
-        const float *usrc = part ? ulo : uhi;
-        uint32_t next_t = cur < end ? adm_t[cur] : 0xffffffffu;
-        int s = 0;
-        for (int w = 0; w < nw && ok; ++w) {
-            uint32_t bits = s_bits[w];
-            while (bits && ok) {
-                const uint32_t t = (uint32_t)(w * 32 + __ffs(bits) - 1);
-                bits &= bits - 1;
-                const bool pres = next_t == t;
-                uint32_t src = 0u;
-                if (pres) {
-                    src = adm_src[cur];
-                    ++cur;
-                    next_t = cur < end ? adm_t[cur] : 0xffffffffu;
-                }
-                const float *rowp = usrc + ((size_t)src * nrhs + m) * 64;
-                const float *Tb = Tsp + (size_t)t * 4 * TS_BH;
-                for (int h = 0; h < 2; ++h, ++s) {
-                    const int b = s % TS_NST;
-                    if (s >= TS_NST) {
-                        // the MMAs of step s - TS_NST are done, and with them every earlier
-                        // accumulator fill: add the finished ones into the sums (a give-up
-                        // is made warp-uniform: the drains are warp-wide TMEM loads)
-                        bool w_ok = mbar_wait(&s_empty[b], (uint32_t)((s / TS_NST - 1) & 1), tries);
-                        if (!__all_sync(0xffffffffu, w_ok)) {
-                            ok = false;
-                            break;
-                        }
-                        const int done = (s - TS_NST) / (2 * TS_DRAIN);
-                        while (drained < done) drain(drained++);
-                    }
-                    float *st = stage0 + (size_t)b * TS_STEP;
-                    float *A = st + part * TS_AH, *B = st + 2 * TS_AH;
+        // T_t's image of step sp's half into B stage sp % TS_NB: 1024 segments, 4 per producer;
+        // the arrive fires once this thread's copies (and its earlier ones) have landed
+        auto copy_b = [&](int sp) {
+            if (sp >= nsteps) return;
+            const float *Bs = Tsp + (size_t)s_tl[sp >> 1] * 4 * TS_BH + (sp & 1) * TS_BST;
+            float *B = bring + (size_t)(sp % TS_NB) * TS_BST;
 #pragma unroll
-                    for (int c = 0; c < TS_KH / 4; ++c)
-                        cp_async16_zfill(A + kmajor_index(row, 4 * c, TS_KH), pres ? rowp + h * TS_KH + 4 * c : usrc,
-                                         pres ? 16u : 0u);
-                    const float *Bs = Tb + h * 2 * TS_BH;
-#pragma unroll
-                    for (int i = 0; i < 2 * TS_BH / 4 / TS_NP; ++i) {
-                        const int e = p + TS_NP * i;
-                        cp_async16(B + 4 * e, Bs + 4 * e);
+            for (int i = 0; i < TS_BST / 4 / TS_NP; ++i) {
+                const int e = p + TS_NP * i;
+                cp_async16(B + 4 * e, Bs + 4 * e);
+            }
+            asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_addr(&s_bfull[sp % TS_NB]))
+                         : "memory");
+        };
+        // this row's source values of step sp (zero without a partner), into registers
+        uint32_t next_t = cur < end ? adm_t[cur] : 0xffffffffu, src = 0u;
+        bool pres = false;
+        float4 ring[TS_P][4];
+        auto load_a = [&](int sp, float4 *dst) {
+            bool use = false;
+            if (sp < nsteps) {
+                if ((sp & 1) == 0) {
+                    const uint32_t t = s_tl[sp >> 1];
+                    pres = next_t == t;
+                    if (pres) {
+                        src = adm_src[cur];
+                        ++cur;
+                        next_t = cur < end ? adm_t[cur] : 0xffffffffu;
                     }
-                    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_addr(&s_full[b]))
-                                 : "memory");
                 }
+                use = pres;
+            }
+            const float4 *g = reinterpret_cast<const float4 *>(u + ((size_t)src * nrhs + m) * 64 + (sp & 1) * TS_KH +
+                                                               qh * 16);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) dst[c] = use ? __ldg(g + c) : make_float4(0.f, 0.f, 0.f, 0.f);
+        };
+#pragma unroll
+        for (int k = 0; k < TS_P; ++k) load_a(k, ring[k]);
+        for (int sp = 0; sp < TS_DB; ++sp) copy_b(sp);
+        for (int s0 = 0; s0 < nsteps && ok; s0 += TS_P) {
+#pragma unroll
+            for (int k = 0; k < TS_P; ++k) {
+                const int s = s0 + k;
+                // (no break in this loop: it is unrolled so that the ring slot k is static)
+                if (s >= nsteps || !ok) continue;
+                if (s >= TS_NA) {
+                    // the MMAs of step s - TS_NA are done: its A and B stages are free.  A fill k
+                    // is drained once the first step of fill k + 1 is done: then the fill is
+                    // final, and the MMA thread has passed its wait for the drain of fill k - 1,
+                    // so the drain barrier is never two phases ahead of that wait (a give-up
+                    // is made warp-uniform: the drains are warp-wide TMEM loads)
+                    const int sb = s - TS_NA;
+                    bool w_ok = mbar_wait(&s_empty[sb % TS_NB], (uint32_t)((sb / TS_NB) & 1), tries, err);
+                    if (!__all_sync(0xffffffffu, w_ok)) {
+                        ok = false;
+                        continue;
+                    }
+                    const int done = sb / (2 * TS_DRAIN);
+                    while (drained < done) drain(drained++);
+                }
+                // split into TF32 hi and lo and write A stage s % TS_NA: columns 128 + 64 (s % TS_NA) + 16 qh
+                // (hi) and + 32 (lo), lane = row
+                uint32_t hi[16], lo[16];
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const float v4[4] = {ring[k][c].x, ring[k][c].y, ring[k][c].z, ring[k][c].w};
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        float h, l;
+                        tf32_split(v4[q], h, l);
+                        hi[4 * c + q] = __float_as_uint(h);
+                        lo[4 * c + q] = __float_as_uint(l);
+                    }
+                }
+                const uint32_t ta = tmem + (uint32_t)(128 + (s % TS_NA) * 64 + qh * 16) + ((uint32_t)(dq * 32) << 16);
+                asm volatile(
+                    "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                    "%16};" ::"r"(ta),
+                    "r"(hi[0]), "r"(hi[1]), "r"(hi[2]), "r"(hi[3]), "r"(hi[4]), "r"(hi[5]), "r"(hi[6]), "r"(hi[7]),
+                    "r"(hi[8]), "r"(hi[9]), "r"(hi[10]), "r"(hi[11]), "r"(hi[12]), "r"(hi[13]), "r"(hi[14]),
+                    "r"(hi[15])
+                    : "memory");
+                asm volatile(
+                    "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                    "%16};" ::"r"(ta + 32u),
+                    "r"(lo[0]), "r"(lo[1]), "r"(lo[2]), "r"(lo[3]), "r"(lo[4]), "r"(lo[5]), "r"(lo[6]), "r"(lo[7]),
+                    "r"(lo[8]), "r"(lo[9]), "r"(lo[10]), "r"(lo[11]), "r"(lo[12]), "r"(lo[13]), "r"(lo[14]),
+                    "r"(lo[15])
+                    : "memory");
+                asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(&s_afull[s % TS_NA])) : "memory");
+                copy_b(s + TS_DB);          // its stage held step s - TS_NA's image
+                load_a(s + TS_P, ring[k]);  // this ring slot's next step
             }
         }
-        total = s;
-        if (ok && total > 0) {
+        if (ok && nsteps > 0) {
             // the last step's MMAs complete after all others: then the last fills
-            const int l = total - 1;
-            bool w_ok = mbar_wait(&s_empty[l % TS_NST], (uint32_t)((l / TS_NST) & 1), tries);
+            const int l = nsteps - 1;
+            bool w_ok = mbar_wait(&s_empty[l % TS_NB], (uint32_t)((l / TS_NB) & 1), tries, err);
             if (!__all_sync(0xffffffffu, w_ok)) ok = false;
-            const int fills = (total + 2 * TS_DRAIN - 1) / (2 * TS_DRAIN);
+            const int fills = (nsteps + 2 * TS_DRAIN - 1) / (2 * TS_DRAIN);
             while (ok && drained < fills) drain(drained++);
         }
         asm volatile("cp.async.wait_all;" ::: "memory");
         if (!ok) s_bad = 1;
-        if (ok) {
-            const int64_t xd = x0 + dq * 32 + lane;
-            if (xd < n_tgt) {
-                float *dst = vt + ((size_t)tgt[xd] * nrhs + m) * r + dcol;
+        if (ok && x < n_tgt) {
+            float *dst = vt + ((size_t)tgt[x] * nrhs + m) * r + qh * 32;
 #pragma unroll
-                for (int c = 0; c < 32; ++c)
-                    if (dcol + c < r) dst[c] = sum[c];
-            }
+            for (int c = 0; c < 32; ++c)
+                if (qh * 32 + c < r) dst[c] = sum[c];
         }
     } else if (lane == 0) {
         // ---- MMA thread
         const uint32_t lbo = 128, sbo = (TS_KH / 4) * 128;
         const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(64 >> 3) << 17) |
                                ((uint32_t)(TS_M >> 4) << 24);
-        int s = 0, g = 0, issued = 0;
-        for (int w = 0; w < nw && ok; ++w) {
-            uint32_t bits = s_bits[w];
-            while (bits && ok) {
-                bits &= bits - 1;
-                const int fill = g / TS_DRAIN;
-                // the accumulator of fill - 2 must have been added into the producers' sums
-                if (g % TS_DRAIN == 0 && fill >= 2 && !mbar_wait(&s_drained, (uint32_t)((fill - 2) & 1), tries)) {
-                    ok = false;
-                    break;
-                }
-                const uint32_t d = tmem + (uint32_t)((fill & 1) * 64);
-                for (int h = 0; h < 2; ++h, ++s) {
-                    const int b = s % TS_NST;
-                    if (!mbar_wait(&s_full[b], (uint32_t)((s / TS_NST) & 1), tries)) {
-                        ok = false;
-                        break;
-                    }
-                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                    const float *st = stage0 + (size_t)b * TS_STEP;
-                    const uint32_t ah0 = smem_addr(st), al0 = smem_addr(st + TS_AH), bh0 = smem_addr(st + 2 * TS_AH),
-                                   bl0 = smem_addr(st + 2 * TS_AH + TS_BH);
-#pragma unroll
-                    for (int ks = 0; ks < TS_KH / 8; ++ks) {
-                        uint64_t ah = umma_desc(ah0 + ks * 256, lbo, sbo), al = umma_desc(al0 + ks * 256, lbo, sbo);
-                        uint64_t bh = umma_desc(bh0 + ks * 256, lbo, sbo), bl = umma_desc(bl0 + ks * 256, lbo, sbo);
-                        uint32_t acc0 = (g % TS_DRAIN != 0 || h > 0 || ks > 0) ? 1u : 0u;
-                        asm volatile(
-                            "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-                            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
-                            "l"(ah), "l"(bh), "r"(idesc), "r"(acc0));
-                        asm volatile("tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, 1;\n" ::"r"(d), "l"(ah),
-                                     "l"(bl), "r"(idesc));
-                        asm volatile("tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, 1;\n" ::"r"(d), "l"(al),
-                                     "l"(bh), "r"(idesc));
-                    }
-                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                                     smem_addr(&s_empty[b]))
-                                 : "memory");
-                    issued = s + 1;
-                }
-                ++g;
+        int issued = 0;
+        for (int s = 0; s < nsteps; ++s) {
+            const int g = s >> 1, h = s & 1, fill = g / TS_DRAIN;
+            // the accumulator of fill - 2 must have been added into the producers' sums
+            if (h == 0 && g % TS_DRAIN == 0 && fill >= 2 &&
+                !mbar_wait(&s_drained, (uint32_t)((fill - 2) & 1), tries, err)) {
+                ok = false;
+                break;
             }
+            const int b = s % TS_NB;
+            if (!mbar_wait(&s_bfull[b], (uint32_t)((s / TS_NB) & 1), tries, err) ||
+                !mbar_wait(&s_afull[s % TS_NA], (uint32_t)((s / TS_NA) & 1), tries, err)) {
+                ok = false;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t d = tmem + (uint32_t)((fill & 1) * 64);
+            const uint32_t a0 = tmem + (uint32_t)(128 + (s % TS_NA) * 64);
+            const float *B = bring + (size_t)b * TS_BST;
+            const uint32_t bh0 = smem_addr(B), bl0 = smem_addr(B + TS_BH);
+#pragma unroll
+            for (int ks = 0; ks < TS_KH / 8; ++ks) {
+                const uint32_t ah = a0 + (uint32_t)(ks * 8), al = a0 + 32u + (uint32_t)(ks * 8);
+                const uint64_t bh = umma_desc(bh0 + ks * 256, lbo, sbo), bl = umma_desc(bl0 + ks * 256, lbo, sbo);
+                const uint32_t acc0 = (g % TS_DRAIN != 0 || h > 0 || ks > 0) ? 1u : 0u;
+                asm volatile(
+                    "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                    "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}\n" ::"r"(d),
+                    "r"(ah), "l"(bh), "r"(idesc), "r"(acc0));
+                asm volatile("tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, 1;\n" ::"r"(d), "r"(ah), "l"(bl),
+                             "r"(idesc));
+                asm volatile("tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, 1;\n" ::"r"(d), "r"(al), "l"(bh),
+                             "r"(idesc));
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             smem_addr(&s_empty[b]))
+                         : "memory");
+            issued = s + 1;
         }
         // after a give-up: keep TMEM and the stages owned until the committed MMAs are done
         if (!ok) {
             s_bad = 1;
             if (issued > 0)
-                mbar_wait(&s_empty[(issued - 1) % TS_NST], (uint32_t)(((issued - 1) / TS_NST) & 1), DRAIN_TRIES);
+                mbar_wait(&s_empty[(issued - 1) % TS_NB], (uint32_t)(((issued - 1) / TS_NB) & 1), DRAIN_TRIES);
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (tid == 0 && s_bad) atomicOr(err, 1);
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(128));
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TS_TCOLS));
 }
 
-// u~ rows (r floats, r <= 64) split into TF32 hi and lo rows of 64 floats (zero padded),
-// the operand of the target-stationary transfer.
-__global__ void k_split_rows64(const float *__restrict__ u, int64_t nrow, int r, float *__restrict__ hi,
-                               float *__restrict__ lo) {
+// u~ rows of r < 64 floats copied into rows of 64 (zero padded), the row layout the
+// target-stationary transfer reads.
+__global__ void k_pad_rows64(const float *__restrict__ u, int64_t nrow, int r, float *__restrict__ out) {
     int64_t n = nrow * 64;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         int64_t row = i >> 6;
         int k = (int)(i & 63);
-        float v = k < r ? u[row * r + k] : 0.f;
-        float h, l;
-        tf32_split(v, h, l);
-        hi[i] = h;
-        lo[i] = l;
+        out[i] = k < r ? u[row * r + k] : 0.f;
     }
 }
 
@@ -1295,18 +1346,20 @@ void far_lagrange(const ffm_plan_s *p, int l, const void *q, int nrhs, float2 *a
             const float *Td = F.T + d * tblk;
             float *vtd = (float *)vt + d * vblk;
         if (F.ts_ok && F.Tsp && F.tune_tc == 2) {
-            size_t smem = (size_t)TS_NST * TS_STEP * sizeof(float);
-            FFM_CUDA(cudaFuncSetAttribute(k_lag_gemm_ts, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            if (!uts) {  // u~ split into hi / lo rows of 64 floats, once for all components
-                int64_t nrow = (int64_t)p->by[l].nb * nrhs;
-                uts = tmp.get<float>((size_t)2 * nrow * 64);
-                unsigned gs = (unsigned)std::min<int64_t>(cdiv(nrow * 64, 256), 152 * 16);
-                FFM_LAUNCH(k_split_rows64, gs, 256, 0, s, (const float *)ut, nrow, r, uts, uts + (size_t)nrow * 64);
+            FFM_CUDA(cudaFuncSetAttribute(k_lag_gemm_ts, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TS_SMEM));
+            const float *u64 = (const float *)ut;
+            if (r < 64) {  // rows of 64 floats, once for all components
+                const int64_t nrow = (int64_t)p->by[l].nb * nrhs;
+                if (!uts) {
+                    uts = tmp.get<float>((size_t)nrow * 64);
+                    unsigned gs = (unsigned)std::min<int64_t>(cdiv(nrow * 64, 256), 152 * 16);
+                    FFM_LAUNCH(k_pad_rows64, gs, 256, 0, s, (const float *)ut, nrow, r, uts);
+                }
+                u64 = uts;
             }
-            const int64_t nrow = (int64_t)p->by[l].nb * nrhs;
             dim3 gts(cdiv(F.n_tgt, TS_M), nrhs);
-            FFM_LAUNCH(k_lag_gemm_ts, gts, TS_NP + 32, smem, s, F.tgt, F.n_tgt, F.adm_off, F.adm_src, F.adm_t,
-                       F.n_trans, F.Tsp, r, nrhs, uts, uts + (size_t)nrow * 64, vtd, p->dev_err, p->wait_tries);
+            FFM_LAUNCH(k_lag_gemm_ts, gts, TS_NP + 32, TS_SMEM, s, F.tgt, F.n_tgt, F.adm_off, F.adm_src, F.adm_t,
+                       F.n_trans, F.Tsp, r, nrhs, u64, vtd, p->dev_err, p->wait_tries);
         } else if (use_tc) {
             // tensor cores: 256-pair tiles, K chunks of 16 source nodes, row blocks of <= 224
             const int rkp = F.rkp;

@@ -187,25 +187,27 @@ __global__ void k_rs_hist(const K *__restrict__ kin, int64_t n, int shift, uint3
     hist[(int64_t)threadIdx.x * nblk + blockIdx.x] = c[threadIdx.x];
 }
 
-__device__ __forceinline__ unsigned long long ld_keep(const unsigned long long *p) {
+__device__ __forceinline__ unsigned long long ld_stream(const unsigned long long *p) {
     unsigned long long v;
     asm volatile("ld.volatile.global.u64 %0, [%1];" : "=l"(v) : "l"(p));
     return v;
 }
-__device__ __forceinline__ uint32_t ld_keep(const uint32_t *p) {
+__device__ __forceinline__ uint32_t ld_stream(const uint32_t *p) {
     uint32_t v;
     asm volatile("ld.volatile.global.u32 %0, [%1];" : "=r"(v) : "l"(p));
     return v;
 }
 
-// Stable scatter staged in shared memory.  A block owns a tile of RS_TILE elements: their
-// ranks within the tile's digit runs (in element order) come from warp match masks and a
-// prefix over the 8 warps per digit, round by round, and each element is placed at its run's
-// position in a shared-memory copy of the tile, which ends up sorted by digit.  The block
-// then writes that copy in order: consecutive threads write consecutive slots of one digit's
-// run in the output (its start from the scanned digit-major histogram), so the stores are
-// coalesced instead of one scattered store per element.  The tile's own digit counts are
-// differences of consecutive entries of the scanned histogram.
+// Stable scatter staged in shared memory.  A block owns a tile of RS_TILE elements; warp w
+// takes the tile's elements w RS_ITEMS 32 .. in order, 32 per round.  Each element's rank
+// within its warp's digit run comes from a warp match mask and a warp-private count per
+// digit (no block barrier per round); the warps' counts are then turned into offsets within
+// the tile's digit runs (in element order: warps in turn), and each element is placed in a
+// shared-memory copy of the tile, which ends up sorted by digit.  The block then writes that
+// copy in order: consecutive threads write consecutive slots of one digit's run in the
+// output (its start from the scanned digit-major histogram), so the stores are coalesced.
+// The tile's own digit counts are differences of consecutive entries of the scanned
+// histogram.
 template <class K>
 __global__ void __launch_bounds__(RS_T) k_rs_scatter(const K *__restrict__ kin, const uint32_t *__restrict__ vin,
                                                      int64_t n, int shift, const uint32_t *__restrict__ off,
@@ -213,12 +215,14 @@ __global__ void __launch_bounds__(RS_T) k_rs_scatter(const K *__restrict__ kin, 
     extern __shared__ __align__(16) unsigned char rs_smem[];
     K *skey = reinterpret_cast<K *>(rs_smem);
     uint32_t *sval = reinterpret_cast<uint32_t *>(skey + RS_TILE);
-    __shared__ uint32_t base[256], start[256], run[256];
-    __shared__ uint32_t wcnt[RS_T / 32][257];
+    __shared__ uint32_t base[256], start[256];
+    __shared__ uint32_t wc[RS_T / 32][256];  // per warp and digit: counts, then offsets in the tile
     __shared__ uint32_t wtot[RS_T / 32];
     int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t t0 = (int64_t)blockIdx.x * RS_TILE;
     const int tile_n = (int)min((int64_t)RS_TILE, n - t0);
+#pragma unroll
+    for (int d = 0; d < 256; d += 32) wc[warp][d + lane] = 0u;
     {
         const int64_t flat = (int64_t)tid * nblk + blockIdx.x;
         const uint32_t b = off[flat];
@@ -235,56 +239,55 @@ __global__ void __launch_bounds__(RS_T) k_rs_scatter(const K *__restrict__ kin, 
         uint32_t before = 0;
         for (int w = 0; w < warp; ++w) before += wtot[w];
         start[tid] = before + inc - c;
-        run[tid] = 0;
-#pragma unroll
-        for (int w = 0; w < RS_T / 32; ++w) wcnt[w][tid] = 0;
     }
-    // every load of the tile in flight at once (registers), before the ranking rounds; the
-    // loads are volatile so that they are issued here and not repeated at their uses
+    // warp-local stable ranks, RS_ITEMS rounds of 32 consecutive elements; every load of the
+    // warp is issued first (volatile, so the compiler keeps them here, all in flight)
     K keys[RS_ITEMS];
-    uint32_t vals[RS_ITEMS];
+    uint32_t vals[RS_ITEMS], rk[RS_ITEMS], dg[RS_ITEMS];
+    const int64_t w0 = t0 + (int64_t)warp * RS_ITEMS * 32;
 #pragma unroll
     for (int r = 0; r < RS_ITEMS; ++r) {
-        int64_t i = t0 + r * RS_T + tid;
+        const int64_t i = w0 + r * 32 + lane;
         keys[r] = (K)0;
         vals[r] = 0u;
         if (i < n) {
-            keys[r] = ld_keep(kin + i);
-            vals[r] = ld_keep(vin + i);
+            keys[r] = ld_stream(kin + i);
+            vals[r] = ld_stream(vin + i);
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < RS_ITEMS; ++r) {
+        const int64_t i = w0 + r * 32 + lane;
+        const bool valid = i < n;
+        const uint32_t d = valid ? ((uint32_t)(keys[r] >> shift) & 255u) : 256u;
+        dg[r] = d;
+        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        const uint32_t lt = peers & ((1u << lane) - 1u);
+        rk[r] = valid ? wc[warp][d] + __popc(lt) : 0u;
+        __syncwarp();
+        if (valid && lt == 0) wc[warp][d] += __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    {
+        // digit tid: the warps' runs in turn, after the runs of the smaller digits
+        uint32_t o = start[tid];
+#pragma unroll
+        for (int w = 0; w < RS_T / 32; ++w) {
+            const uint32_t c = wc[w][tid];
+            wc[w][tid] = o;
+            o += c;
         }
     }
     __syncthreads();
 #pragma unroll
-    for (int r = 0; r < RS_ITEMS; ++r) {
-        int64_t i = t0 + r * RS_T + tid;
-        bool valid = i < n;
-        K key = keys[r];
-        uint32_t val = vals[r];
-        uint32_t d = valid ? ((uint32_t)(key >> shift) & 255u) : 256u;
-        uint32_t peers = __match_any_sync(0xffffffffu, d);
-        uint32_t lt = peers & ((1u << lane) - 1u);
-        uint32_t rank = __popc(lt);
-        if (valid && lt == 0) wcnt[warp][d] = __popc(peers);
-        __syncthreads();
-        uint32_t round_tot = 0;  // digit tid's elements in this round
-#pragma unroll
-        for (int w = 0; w < RS_T / 32; ++w) {
-            uint32_t c = wcnt[w][tid];
-            wcnt[w][tid] = round_tot;
-            round_tot += c;
+    for (int r = 0; r < RS_ITEMS; ++r)
+        if (dg[r] < 256u) {
+            const uint32_t pos = wc[warp][dg[r]] + rk[r];
+            skey[pos] = keys[r];
+            sval[pos] = vals[r];
         }
-        __syncthreads();
-        if (valid) {
-            uint32_t pos = start[d] + run[d] + wcnt[warp][d] + rank;
-            skey[pos] = key;
-            sval[pos] = val;
-        }
-        __syncthreads();
-        run[tid] += round_tot;
-#pragma unroll
-        for (int w = 0; w < RS_T / 32; ++w) wcnt[w][tid] = 0;
-        __syncthreads();
-    }
+    __syncthreads();
     for (int i = tid; i < tile_n; i += RS_T) {
         K key = skey[i];
         uint32_t d = (uint32_t)(key >> shift) & 255u;

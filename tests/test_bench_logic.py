@@ -68,10 +68,26 @@ def test_traffic_figures_are_void_once_the_kernel_source_changes(tmp_path, monke
     (src / "k.cu").write_text("kernel v1\n")
     h = hashlib.sha256(b"kernel v1\n").hexdigest()[:16]
     (tmp_path / "profiles").mkdir()
-    (tmp_path / "profiles" / "traffic_w.txt").write_text(
-        "# comment\nk_x<W> wl 123456 csrc/k.cu %s\n" % h)
+    (tmp_path / "profiles" / "traffic.txt").write_text(
+        "# comment\nk_x<W> wl_small 12.5 pair k.cu %s\n" % h)
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
-    assert bench.measured_traffic("k_x<W>", "wl") == 123456.0
-    assert bench.measured_traffic("k_x<W>", "other") is None
+    tr = bench.measured_traffic("k_x<W>")
+    assert tr["bytes_per_unit"] == 12.5 and tr["captured_on"] == "wl_small"
+    assert bench.measured_traffic("k_y") is None
     (src / "k.cu").write_text("kernel v2\n")
-    assert bench.measured_traffic("k_x<W>", "wl") is None
+    assert bench.measured_traffic("k_x<W>") is None
+
+
+def test_roofline_traffic_scales_the_per_unit_figure_to_the_launch(tmp_path, monkeypatch):
+    src = tmp_path / "paper_1909_05600_gb300" / "csrc"
+    src.mkdir(parents=True)
+    (src / "nearfield.cu").write_text("v\n")
+    h = hashlib.sha256(b"v\n").hexdigest()[:16]
+    (tmp_path / "profiles").mkdir()
+    (tmp_path / "profiles" / "traffic.txt").write_text("k_p2p_lap<4> small 0.5 pair nearfield.cu %s\n" % h)
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    info = _info()
+    info["p2p_pairs"] = 1000
+    rl = bench.roofline({"k_p2p_lap<4>": (2, 4.0)}, info, 2, 2070.0, PK, "measured", "laplace_clustered")
+    assert rl["units_per_step"] == 1000.0
+    assert rl["traffic"] == pytest.approx(0.5 * 1000.0 / 1.0)
