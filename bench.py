@@ -3,8 +3,9 @@
 A step is one whole FFM product through the C ABI, ffm_plan + ffm_apply + ffm_destroy
 (bounding cubes, Morton sort, box tables, descent, per-level operators, far field of every
 level, near field, accumulation), on inputs already resident in HBM.  The default workload
-is the Helmholtz kernel on 1,000,000 + 1,000,000 independent uniform points on the unit
-sphere, k at 10 points per wavelength (k = 177.2), complex64 densities, eps = 1e-3.
+is the Laplace kernel on 1e8 + 1e8 independent float32 points drawn from a mixture of 8
+Gaussians (sigma 0.05, centres uniform in the unit cube), u ~ U(-1, 1) float32, w = 1/N,
+eps = 1e-3 (laplace_clustered_1e8).
 
 Prints one JSON line (rank 0).  `value` is FFM products per second over all ranks;
 `e2e` is the same metric through the same API with host buffers (copies included);
@@ -208,6 +209,7 @@ def cpu_legs(prob, args, vg):
     cores = O.nthreads()
     ntg = args.cpu_targets
     if ntg <= 0:
+        cpu_direct_sample(prob, 1, seed=778)  # loads the library and starts its threads
         _, _, dtp, _ = cpu_direct_sample(prob, 16, seed=777)
         ntg = int(min(4096, max(256, 16 * args.cpu_seconds / max(dtp, 1e-6))))
     ntg = min(ntg, nx)

@@ -657,17 +657,17 @@ __global__ void k_split_pad(const float *__restrict__ src, int64_t nmat, int row
 //
 // Operands.  The A operand (the gathered source rows) lives in tensor memory: the MMAs read
 // it from TMEM, so shared memory only carries T_t (the B operand), and the operand reads of
-// the tensor cores from shared memory drop to a third.  A step is one translation and one
-// half of K (32 source nodes).  Warps 1-8 produce; the two producers of a target row each
-// own 16 of the step's 32 values.  A producer loads its values of the row's source (zero
-// where the row has no partner) from global memory into registers TS_P steps ahead, splits
-// them into TF32 hi and lo parts and writes them into one of TS_NA TMEM operand stages
-// (tcgen05.st), then arrives on that stage's "A full" mbarrier.  It also copies its share of
-// T_t's pre-split image of the half (16 KB in all) with cp.async into one of TS_NB shared
-// stages, TS_DB steps ahead, and arrives on that stage's "B full" mbarrier once the copies
-// land.  One thread of warp 0 waits on both, issues the step's 12 MMAs and commits them to
-// the B stage's "empty" mbarrier; the producers wait on it (TS_NA steps later) before they
-// reuse the A and B stages.
+// the tensor cores from shared memory drop to a third.  A step is one translation (K = 64
+// source nodes, 24 MMAs).  Warps 1-8 produce; the two producers of a target row each own 32
+// of the row's 64 values.  A producer loads its values of the row's source (zero where the
+// row has no partner) from global memory into registers TS_P steps ahead, splits them into
+// TF32 hi and lo parts and writes them into one of TS_NA TMEM operand stages (tcgen05.st),
+// then arrives on that stage's "A full" mbarrier.  It also copies its share of T_t's
+// pre-split image (32 KB in all) with cp.async into one of TS_NB shared stages, TS_DB steps
+// ahead, and arrives on that stage's "B full" mbarrier once the copies land.  One thread of
+// warp 0 waits on both, issues the step's 24 MMAs and commits them to the B stage's "empty"
+// mbarrier; the producers wait on it (TS_NA steps later) before they reuse the A and B
+// stages.  Each barrier round trip thus serves 24 MMAs.
 //
 // Accumulation.  One long tcgen05 accumulation loses accuracy, so the tile alternates
 // between two TMEM accumulators (64 columns each) every TS_DRAIN translations; the producers
@@ -676,18 +676,27 @@ __global__ void k_split_pad(const float *__restrict__ src, int64_t nmat, int row
 // Every wait is bounded; a give-up raises the device error flag, the CTA then waits for its
 // copies and committed MMAs, skips its results and frees TMEM.
 constexpr int TS_M = 128;
-constexpr int TS_KH = 32;             // source nodes per step (half of K = 64)
-constexpr int TS_BH = 64 * TS_KH;     // floats per B hi or lo block of a step
-constexpr int TS_BST = 2 * TS_BH;     // floats per B stage (16 KB)
-constexpr int TS_NA = 4;              // A stages (tensor memory); producers run TS_NA steps ahead
+constexpr int TS_K = 64;              // source nodes (K) per step: one translation
+constexpr int TS_BH = 64 * 32;        // floats per B hi or lo block of one half of K
+constexpr int TS_BST = 4 * TS_BH;     // floats per B stage: T_t's whole image (32 KB)
+constexpr int TS_NA = 3;              // A stages (tensor memory); producers run TS_NA steps ahead
 constexpr int TS_DB = 2;              // steps the copies of T_t's image run ahead
 constexpr int TS_NB = TS_NA + TS_DB;  // B stages (shared memory)
-constexpr int TS_P = 4;               // steps the source loads run ahead (registers)
+constexpr int TS_P = 2;               // steps the source loads run ahead (registers)
 constexpr int TS_MAXT = 4096;         // translation codes lie in a 16^3 range
 constexpr int TS_DRAIN = 8;           // translations per TMEM accumulator fill
 constexpr int TS_NP = 2 * TS_M;       // producer threads (warps 1-8)
-constexpr int TS_TCOLS = 512;         // TMEM: 2 accumulators x 64 columns, TS_NA A stages x 64 (hi, lo)
+constexpr int TS_TCOLS = 512;         // TMEM: 2 accumulators x 64 columns, TS_NA A stages x 128 (hi, lo)
 constexpr size_t TS_SMEM = sizeof(float) * (size_t)TS_NB * TS_BST;
+
+// 16 values of one lane into consecutive TMEM columns of the warp's lanes
+__device__ __forceinline__ void tmem_st16(uint32_t ta, const uint32_t (&v)[16]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(ta),
+        "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]),
+        "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15])
+        : "memory");
+}
 
 // u holds rows of 64 floats (r <= 64, zero padded): row (b, m) at ((b nrhs + m) 64).
 __global__ void __launch_bounds__(TS_NP + 32, 1) k_lag_gemm_ts(const uint32_t *__restrict__ tgt, int64_t n_tgt,
@@ -731,7 +740,7 @@ __global__ void __launch_bounds__(TS_NP + 32, 1) k_lag_gemm_ts(const uint32_t *_
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = s_tmem;
     // producers: warp w (1-8) holds TMEM lanes 32 (w % 4) .. + 31, one target row per lane,
-    // and values 16 qh .. 16 qh + 15 of each step's half
+    // and values 32 qh .. 32 qh + 31 of each step
     const bool prod = warp >= 1;
     const int dq = warp & 3, qh = (warp - 1) >> 2, row = dq * 32 + lane;
     const int64_t x = x0 + row;
@@ -758,7 +767,7 @@ __global__ void __launch_bounds__(TS_NP + 32, 1) k_lag_gemm_ts(const uint32_t *_
         }
     }
     __syncthreads();
-    const int nsteps = 2 * (int)s_wpre[TS_MAXT / 32];
+    const int nsteps = (int)s_wpre[TS_MAXT / 32];
     bool ok = true;
     if (prod) {
         const int p = tid - 32;
@@ -783,11 +792,11 @@ __global__ void __launch_bounds__(TS_NP + 32, 1) k_lag_gemm_ts(const uint32_t *_
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(&s_drained)) : "memory");
         };
-        // T_t's image of step sp's half into B stage sp % TS_NB: 1024 segments, 4 per producer;
-        // the arrive fires once this thread's copies (and its earlier ones) have landed
+        // T_t's image of step sp into B stage sp % TS_NB: 2048 segments, 8 per producer; the
+        // arrive fires once this thread's copies (and its earlier ones) have landed
         auto copy_b = [&](int sp) {
             if (sp >= nsteps) return;
-            const float *Bs = Tsp + (size_t)s_tl[sp >> 1] * 4 * TS_BH + (sp & 1) * TS_BST;
+            const float *Bs = Tsp + (size_t)s_tl[sp] * TS_BST;
             float *B = bring + (size_t)(sp % TS_NB) * TS_BST;
 #pragma unroll
             for (int i = 0; i < TS_BST / 4 / TS_NP; ++i) {
@@ -797,28 +806,37 @@ __global__ void __launch_bounds__(TS_NP + 32, 1) k_lag_gemm_ts(const uint32_t *_
             asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_addr(&s_bfull[sp % TS_NB]))
                          : "memory");
         };
-        // this row's source values of step sp (zero without a partner), into registers
-        uint32_t next_t = cur < end ? adm_t[cur] : 0xffffffffu, src = 0u;
-        bool pres = false;
-        float4 ring[TS_P][4];
+        // this row's source values of step sp (zero without a partner), into registers.  The
+        // row's next two partners (translation, source) are held in registers and the one after
+        // is loaded as one is used, so the source row's address never waits on a list load.
+        uint32_t t0 = 0xffffffffu, b0 = 0u, t1 = 0xffffffffu, b1 = 0u;
+        if (cur < end) {
+            t0 = adm_t[cur];
+            b0 = adm_src[cur];
+        }
+        if (cur + 1 < end) {
+            t1 = adm_t[cur + 1];
+            b1 = adm_src[cur + 1];
+        }
+        float4 ring[TS_P][8];
         auto load_a = [&](int sp, float4 *dst) {
             bool use = false;
-            if (sp < nsteps) {
-                if ((sp & 1) == 0) {
-                    const uint32_t t = s_tl[sp >> 1];
-                    pres = next_t == t;
-                    if (pres) {
-                        src = adm_src[cur];
-                        ++cur;
-                        next_t = cur < end ? adm_t[cur] : 0xffffffffu;
-                    }
+            uint32_t src = 0u;
+            if (sp < nsteps && t0 == (uint32_t)s_tl[sp]) {
+                use = true;
+                src = b0;
+                t0 = t1;
+                b0 = b1;
+                ++cur;
+                t1 = 0xffffffffu;
+                if (cur + 1 < end) {
+                    t1 = adm_t[cur + 1];
+                    b1 = adm_src[cur + 1];
                 }
-                use = pres;
             }
-            const float4 *g = reinterpret_cast<const float4 *>(u + ((size_t)src * nrhs + m) * 64 + (sp & 1) * TS_KH +
-                                                               qh * 16);
+            const float4 *g = reinterpret_cast<const float4 *>(u + ((size_t)src * nrhs + m) * 64 + qh * 32);
 #pragma unroll
-            for (int c = 0; c < 4; ++c) dst[c] = use ? __ldg(g + c) : make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int c = 0; c < 8; ++c) dst[c] = use ? __ldg(g + c) : make_float4(0.f, 0.f, 0.f, 0.f);
         };
 #pragma unroll
         for (int k = 0; k < TS_P; ++k) load_a(k, ring[k]);
@@ -841,38 +859,31 @@ __global__ void __launch_bounds__(TS_NP + 32, 1) k_lag_gemm_ts(const uint32_t *_
                         ok = false;
                         continue;
                     }
-                    const int done = sb / (2 * TS_DRAIN);
+                    const int done = sb / TS_DRAIN;
                     while (drained < done) drain(drained++);
                 }
-                // split into TF32 hi and lo and write A stage s % TS_NA: columns 128 + 64 (s % TS_NA) + 16 qh
-                // (hi) and + 32 (lo), lane = row
-                uint32_t hi[16], lo[16];
+                // split into TF32 hi and lo and write A stage s % TS_NA: columns 128 + 128 (s % TS_NA)
+                // + 32 qh (hi) and + 64 (lo), lane = row
+                const uint32_t ta =
+                    tmem + (uint32_t)(128 + (s % TS_NA) * 128 + qh * 32) + ((uint32_t)(dq * 32) << 16);
 #pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    const float v4[4] = {ring[k][c].x, ring[k][c].y, ring[k][c].z, ring[k][c].w};
+                for (int hh = 0; hh < 2; ++hh) {  // 16 values at a time: fewer live registers
+                    uint32_t hv[16], lv[16];
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        float h, l;
-                        tf32_split(v4[q], h, l);
-                        hi[4 * c + q] = __float_as_uint(h);
-                        lo[4 * c + q] = __float_as_uint(l);
+                    for (int c = 0; c < 4; ++c) {
+                        const float4 f4 = ring[k][4 * hh + c];
+                        const float v4[4] = {f4.x, f4.y, f4.z, f4.w};
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            float h, l;
+                            tf32_split(v4[q], h, l);
+                            hv[4 * c + q] = __float_as_uint(h);
+                            lv[4 * c + q] = __float_as_uint(l);
+                        }
                     }
+                    tmem_st16(ta + 16u * hh, hv);
+                    tmem_st16(ta + 64u + 16u * hh, lv);
                 }
-                const uint32_t ta = tmem + (uint32_t)(128 + (s % TS_NA) * 64 + qh * 16) + ((uint32_t)(dq * 32) << 16);
-                asm volatile(
-                    "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-                    "%16};" ::"r"(ta),
-                    "r"(hi[0]), "r"(hi[1]), "r"(hi[2]), "r"(hi[3]), "r"(hi[4]), "r"(hi[5]), "r"(hi[6]), "r"(hi[7]),
-                    "r"(hi[8]), "r"(hi[9]), "r"(hi[10]), "r"(hi[11]), "r"(hi[12]), "r"(hi[13]), "r"(hi[14]),
-                    "r"(hi[15])
-                    : "memory");
-                asm volatile(
-                    "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-                    "%16};" ::"r"(ta + 32u),
-                    "r"(lo[0]), "r"(lo[1]), "r"(lo[2]), "r"(lo[3]), "r"(lo[4]), "r"(lo[5]), "r"(lo[6]), "r"(lo[7]),
-                    "r"(lo[8]), "r"(lo[9]), "r"(lo[10]), "r"(lo[11]), "r"(lo[12]), "r"(lo[13]), "r"(lo[14]),
-                    "r"(lo[15])
-                    : "memory");
                 asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
                 asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
                 asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(&s_afull[s % TS_NA])) : "memory");
@@ -885,7 +896,7 @@ __global__ void __launch_bounds__(TS_NP + 32, 1) k_lag_gemm_ts(const uint32_t *_
             const int l = nsteps - 1;
             bool w_ok = mbar_wait(&s_empty[l % TS_NB], (uint32_t)((l / TS_NB) & 1), tries, err);
             if (!__all_sync(0xffffffffu, w_ok)) ok = false;
-            const int fills = (nsteps + 2 * TS_DRAIN - 1) / (2 * TS_DRAIN);
+            const int fills = (nsteps + TS_DRAIN - 1) / TS_DRAIN;
             while (ok && drained < fills) drain(drained++);
         }
         asm volatile("cp.async.wait_all;" ::: "memory");
@@ -898,15 +909,14 @@ __global__ void __launch_bounds__(TS_NP + 32, 1) k_lag_gemm_ts(const uint32_t *_
         }
     } else if (lane == 0) {
         // ---- MMA thread
-        const uint32_t lbo = 128, sbo = (TS_KH / 4) * 128;
+        const uint32_t lbo = 128, sbo = 8 * 128;  // B image: per half of K, 64 rows x 32 in core matrices
         const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(64 >> 3) << 17) |
                                ((uint32_t)(TS_M >> 4) << 24);
         int issued = 0;
         for (int s = 0; s < nsteps; ++s) {
-            const int g = s >> 1, h = s & 1, fill = g / TS_DRAIN;
+            const int fill = s / TS_DRAIN;
             // the accumulator of fill - 2 must have been added into the producers' sums
-            if (h == 0 && g % TS_DRAIN == 0 && fill >= 2 &&
-                !mbar_wait(&s_drained, (uint32_t)((fill - 2) & 1), tries, err)) {
+            if (s % TS_DRAIN == 0 && fill >= 2 && !mbar_wait(&s_drained, (uint32_t)((fill - 2) & 1), tries, err)) {
                 ok = false;
                 break;
             }
@@ -918,14 +928,16 @@ __global__ void __launch_bounds__(TS_NP + 32, 1) k_lag_gemm_ts(const uint32_t *_
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t d = tmem + (uint32_t)((fill & 1) * 64);
-            const uint32_t a0 = tmem + (uint32_t)(128 + (s % TS_NA) * 64);
-            const float *B = bring + (size_t)b * TS_BST;
-            const uint32_t bh0 = smem_addr(B), bl0 = smem_addr(B + TS_BH);
+            const uint32_t a0 = tmem + (uint32_t)(128 + (s % TS_NA) * 128);
+            const uint32_t bst = smem_addr(bring + (size_t)b * TS_BST);
 #pragma unroll
-            for (int ks = 0; ks < TS_KH / 8; ++ks) {
-                const uint32_t ah = a0 + (uint32_t)(ks * 8), al = a0 + 32u + (uint32_t)(ks * 8);
-                const uint64_t bh = umma_desc(bh0 + ks * 256, lbo, sbo), bl = umma_desc(bl0 + ks * 256, lbo, sbo);
-                const uint32_t acc0 = (g % TS_DRAIN != 0 || h > 0 || ks > 0) ? 1u : 0u;
+            for (int ks = 0; ks < TS_K / 8; ++ks) {
+                // K step ks: A columns 8 ks (hi) and 64 + 8 ks (lo); B in half ks / 4 of the image
+                // (hi block, then lo block), core matrices 2 (ks % 4) and 2 (ks % 4) + 1
+                const uint32_t ah = a0 + (uint32_t)(ks * 8), al = a0 + 64u + (uint32_t)(ks * 8);
+                const uint32_t bh0 = bst + (uint32_t)((ks >> 2) * 2 * TS_BH * 4 + (ks & 3) * 256);
+                const uint64_t bh = umma_desc(bh0, lbo, sbo), bl = umma_desc(bh0 + TS_BH * 4, lbo, sbo);
+                const uint32_t acc0 = (s % TS_DRAIN != 0 || ks > 0) ? 1u : 0u;
                 asm volatile(
                     "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
                     "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}\n" ::"r"(d),

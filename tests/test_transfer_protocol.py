@@ -8,7 +8,7 @@ import random
 
 import pytest
 
-NA, DB, DRAIN = 4, 2, 8  # A stages, B copies ahead, translations per accumulator fill, as in the kernel
+NA, DB, DRAIN = 3, 2, 8  # A stages, B copies ahead, steps (translations) per accumulator fill, as in the kernel
 NB = NA + DB             # B stages
 
 
@@ -57,16 +57,15 @@ def run(nsteps, seed, drain_rule):
             last = nsteps - 1
             while not empty[last % NB].test(last // NB):
                 yield
-            fills = (nsteps + 2 * DRAIN - 1) // (2 * DRAIN)
+            fills = (nsteps + DRAIN - 1) // DRAIN
             while n_drained < fills:
                 drained.arrive()
                 n_drained += 1
 
     def mma():
         for s in range(nsteps):
-            g, h = s >> 1, s & 1
-            fill = g // DRAIN
-            if h == 0 and g % DRAIN == 0 and fill >= 2:
+            fill = s // DRAIN
+            if s % DRAIN == 0 and fill >= 2:
                 while not drained.test(fill - 2):
                     yield
             while not bfull[s % NB].test(s // NB):
@@ -93,7 +92,7 @@ def run(nsteps, seed, drain_rule):
     raise AssertionError("no progress: deadlock")
 
 
-KERNEL_RULE = lambda s: (s - NA) // (2 * DRAIN)  # drain a fill once the next fill's first step is done
+KERNEL_RULE = lambda s: (s - NA) // DRAIN  # drain a fill once the next fill's first step is done
 
 
 @pytest.mark.parametrize("nsteps", [2, 3, 16, 17, 32, 33, 40, 64, 100, 631])
@@ -103,7 +102,7 @@ def test_transfer_protocol_never_deadlocks_or_aliases(nsteps):
 
 
 def test_model_catches_a_drain_two_phases_ahead():
-    early = lambda s: (s - NA + 1) // (2 * DRAIN)  # drains as soon as a fill is complete
+    early = lambda s: (s - NA + 1) // DRAIN  # drains as soon as a fill is complete
     with pytest.raises(AssertionError):
         for seed in range(20):
             run(100, seed, early)
