@@ -334,7 +334,7 @@ def measured_traffic(kernel):
     return None
 
 
-def roofline(prof, info, steps, clk, pk, pk_kind, workload):
+def roofline(prof, info, steps, clk, pk, pk_kind, workload, nrhs=1):
     """Dominant kernel of the timed region against the pipe that bounds it.
     - Plane-wave transforms and the Helmholtz near field: the special-function (MUFU)
       pipe.  A point-direction pair of a transform costs one MUFU op (one sin and one cos
@@ -350,7 +350,14 @@ def roofline(prof, info, steps, clk, pk, pk_kind, workload):
       kernel window (per direction and box, or per point).
     - Lagrange transfer: tensor cores, 2 r r_K FLOP per admissible pair (r_K = r, or 3 r for
       the double layer's stacked component kernels; the single-precision GEMM; the TF32 hi/lo split triples the MMA work but not the algorithmic work), against
-      the measured BF16 peak times the nominal TF32/BF16 ratio (1.1 / 2.25)."""
+      the measured BF16 peak times the nominal TF32/BF16 ratio (1.1 / 2.25).
+    - Plane-wave transforms of several right-hand sides on the tensor cores: 8 FLOP per
+      (point, direction pair, right-hand side) (the real GEMMs P and Q over 2 columns per
+      right-hand side), against the same TF32 peak.
+    - Plane-wave transfer, and the double-float transforms of several right-hand sides: FP32
+      issue, per (admissible pair or point, direction, right-hand side) a complex
+      multiply-add: 4 instructions in FP32, 16 compensated (TwoSum), 72 in double-float
+      arithmetic (4 multiplies of 7 instructions and 4 additions of 11)."""
     # the dominant kernel of this library (library calls such as cuFFT are listed, not ranked)
     name, (nl, ms) = max(((k, v) for k, v in prof.items() if "(library)" not in k), key=lambda kv: kv[1][1])
     mhz = pk.get("sm_max_mhz", 2070.0)
@@ -362,7 +369,29 @@ def roofline(prof, info, steps, clk, pk, pk_kind, workload):
     out = {"kernel": name, "launches_per_step": nl / steps, "ms_per_step": ms / steps, "traffic": None}
     per_s = lambda units: units * steps / (ms * 1e-3)
     basis = "%d SMs x %%s x %.0f MHz (max SM clock, %s peaks file)" % (SM_COUNT, mhz, pk_kind)
-    if "k_pw_forward" in name or "k_pw_backward" in name:
+    tag = name[name.find("<") + 1:name.find(">")] if "<" in name else ""
+    prec_of = {"f32": 1, "f32c": 2, "f64": 3, "f32x2": 4}
+    nufft = info.get("nufft", [0] * 22)
+    levels = [l for l in range(22) if info["mode"][l] == 2 and not nufft[l] and info["pw_prec"][l] == prec_of.get(tag, -1)]
+    if ("k_pw_forward_tc" in name or "k_pw_backward_tc" in name) and tag in prec_of:
+        key = "src_points" if "forward" in name else "tgt_points"
+        units = 8.0 * nrhs * sum(info[key][l] * info["nQ"][l] / 2 for l in levels)
+        peak = pk.get("bf16_tflops", 1900.0) * 1e12 * (1.1 / 2.25)
+        out.update({"bound": "tensor", "pipe": "TF32", "unit": "TFLOP/s", "units_per_step": units,
+                    "peak_basis": "measured BF16 %.1f TFLOP/s x 1.1/2.25 (%s peaks file)"
+                                  % (pk.get("bf16_tflops", 1900.0), pk_kind)})
+    elif ("k_pw_transfer" in name or (nrhs > 1 and tag in ("f32x2", "f32c") and
+                                      ("k_pw_forward_mr" in name or "k_pw_backward_mr" in name))) and tag != "f64":
+        per = {"f32": 4.0, "f32c": 16.0, "f32x2": 72.0}.get(tag, 4.0)
+        if "k_pw_transfer" in name:
+            units = per * nrhs * sum(info["n_adm"][l] * info["nQ"][l] for l in levels)
+        else:
+            key = "src_points" if "forward" in name else "tgt_points"
+            units = per * nrhs * sum(info[key][l] * info["nQ"][l] / 2 for l in levels)
+        peak = SM_COUNT * 128 * clk_hz
+        out.update({"bound": "alu", "pipe": "FP32 issue (%g instructions per complex multiply-add)" % per,
+                    "unit": "Tops/s", "units_per_step": units, "peak_basis": basis % "128 lanes/clk"})
+    elif "k_pw_forward" in name or "k_pw_backward" in name:
         key = "src_points" if "forward" in name else "tgt_points"
         units = 1.0 * sum(info[key][l] * info["nQ"][l] for l in range(22) if info["mode"][l] == 2)
         peak = SM_COUNT * MUFU_PER_SM_CLK * clk_hz
@@ -829,7 +858,7 @@ def main():
         err, err_targets, cpu = cpu_legs(as_f64(prob), args, vg)
 
     if rank == 0:
-        rl = roofline(prof, info, k_prof, clk, pk, pk_kind, args.workload)
+        rl = roofline(prof, info, k_prof, clk, pk, pk_kind, args.workload, nrhs)
         kernels = {k: {"launches_per_step": v[0] / k_prof, "ms_per_step": v[1] / k_prof}
                    for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}
         line = {

@@ -112,8 +112,14 @@ typedef struct {
     int pw_transform;           /* plane-wave source and target steps F_{Y->s}, F_{s->X} (Sec.
                                    2.2.3): 0 chosen per level (the type-3 NUFFT on FP32 levels
                                    with many directions, direct sums elsewhere, or
-                                   ffm_autotune's pick), 1 direct sums everywhere, 2 the NUFFT
-                                   on every FP32 and compensated-FP32 plane-wave level */
+                                   ffm_autotune's pick; with 16 or more right-hand sides the
+                                   direct sums of FP32 and compensated-FP32 levels run as
+                                   TF32 x3 tensor-core products), 1 direct sums on the CUDA
+                                   cores everywhere, 2 the NUFFT on every FP32 and
+                                   compensated-FP32 plane-wave level, 3 as 0 without the NUFFT
+                                   and with the tensor-core products from 2 right-hand sides
+                                   (the forward transform on FP32 and compensated-FP32 levels,
+                                   the backward transform on FP32 levels) */
     double aca_eps;             /* FFM_LAPLACE: 0 -> dense transfer matrices T; > 0 -> each T_t
                                    replaced by its adaptive cross approximation A_t B_t^T (Sec.
                                    2.2.2, eq. 11; full pivoting, FP64, at plan time) with

@@ -698,6 +698,13 @@ __device__ __forceinline__ void tmem_st16(uint32_t ta, const uint32_t (&v)[16]) 
         : "memory");
 }
 
+// 8 values of one lane into consecutive TMEM columns of the warp's lanes
+__device__ __forceinline__ void tmem_st8(uint32_t ta, const uint32_t (&v)[8]) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(ta), "r"(v[0]),
+                 "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
+                 : "memory");
+}
+
 // u holds rows of 64 floats (r <= 64, zero padded): row (b, m) at ((b nrhs + m) 64).
 __global__ void __launch_bounds__(TS_NP + 32, 1) k_lag_gemm_ts(const uint32_t *__restrict__ tgt, int64_t n_tgt,
                                                               const uint32_t *__restrict__ adm_off,
@@ -2005,6 +2012,607 @@ __global__ void k_slot_set(const uint32_t *__restrict__ tgt, int64_t n, int *slo
     if (i < n) slot[tgt[i]] = (int)i;
 }
 
+// ---- several right-hand sides on the tensor cores (FP32 plane-wave levels)
+//
+// The forward transform of a source box b is a product of a generated matrix and the
+// densities: for direction pairs h (antipodes h, h + nQ/2) and right-hand sides m,
+//   P(h, m) = sum_j Re(e_hj) w_jm,   Q(h, m) = sum_j Im(e_hj) w_jm,
+//   e_hj = F_leaf(j)(h) e^{-i k s_h . e_j}   (leaf-centred phase times the leaf's octant factor),
+// and u~(h) = P + iQ, u~(h + nQ/2) = P - iQ per right-hand side (the antipode's phasor is the
+// conjugate).  With the complex densities written as 2 real columns per right-hand side,
+// both are real GEMMs of M = direction pairs, N = 2 x right-hand sides, K = points.
+//
+// k_pw_forward_tc: a CTA takes 128 direction pairs (TMEM lanes), 64 right-hand sides (N =
+// 128) and one chunk of at most PWT_CH points of a box, in steps of 32 points aligned to the
+// density image's 32-point blocks (points outside the chunk get phasor 0).  Warps 1-16
+// produce, four threads per direction pair h (8 points of the step each): a thread forms
+// its 8 phasors (one sincos each, the leaf factor kept while the leaf does not change),
+// splits Re and Im into TF32 hi and lo and writes them into one of two TMEM operand stages
+// (tcgen05.st); one producer also starts a bulk copy of the step's density block (hi and
+// lo, K-major, 32 KB) two steps ahead into one of four shared stages.  One thread of warp 0
+// issues per 8 points hi hi + hi lo + lo hi for P and for Q (6 MMAs, M = 128, N = 128, K =
+// 8, A from TMEM) and commits to the stage's "empty" barrier.  The epilogue reads P and Q
+// from TMEM and adds u~ into the output (atomics: a box may be split over several chunks;
+// the output is zeroed first).  The TF32 x3 products carry about 2^-22 of each term (the
+// dropped lo lo product and the rounding of the lo parts), a few times FP32's rounding.
+constexpr int PWT_M = 128;                 // direction pairs per CTA
+constexpr int PWT_KC = 32;                 // points per step
+constexpr int PWT_MC = 64;                 // right-hand sides per CTA
+constexpr int PWT_N = 2 * PWT_MC;          // GEMM columns (re, im of each right-hand side)
+constexpr int PWT_CH = PW_TC_FCH;          // points per chunk of a box
+constexpr int PWT_NA = 2;                  // A stages (tensor memory)
+constexpr int PWT_DB = 2;                  // steps the density copies run ahead
+constexpr int PWT_QS = 4;                  // producer threads per direction pair
+constexpr int PWT_PP = PWT_KC / PWT_QS;    // points per producer thread and step
+constexpr int PWT_NP = PWT_QS * PWT_M;     // producer threads (warps 1-16)
+constexpr int PWT_NB = PWT_NA + PWT_DB;    // density stages (shared memory)
+constexpr int PWT_BH = PWT_N * PWT_KC;     // floats per density hi or lo block
+constexpr int PWT_BST = 2 * PWT_BH;        // floats per density stage (32 KB)
+constexpr int PWT_TCOLS = 512;             // TMEM: P 128 + Q 128 columns, 2 A stages x 128
+constexpr size_t PWT_SMEM = sizeof(float) * (size_t)PWT_NB * PWT_BST;  // 128 KB: one CTA per SM
+
+// Density image: for every block of 32 consecutive points (Morton order) and every group of
+// 64 right-hand sides, the TF32 hi block then the lo block of the K-major operand (rows n =
+// 2 m + part, part 0 = real, 1 = imaginary; columns = the block's points), zero beyond ny
+// and nrhs.  Shared by every plane-wave level of one apply.
+__global__ void k_pw_density_image(const float2 *__restrict__ q, int64_t ny, int nrhs, int nblk_m,
+                                   float *__restrict__ img) {
+    const int64_t nimg = (int64_t)((ny + PWT_KC - 1) / PWT_KC) * nblk_m * PWT_BH;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nimg; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t blk = i / PWT_BH;  // (point block, right-hand-side group)
+        const int e = (int)(i - blk * PWT_BH);
+        const int n = e / PWT_KC, k = e % PWT_KC;
+        const int64_t c = blk / nblk_m;
+        const int mb = (int)(blk - c * nblk_m);
+        const int64_t j = c * PWT_KC + k;
+        const int mm = mb * PWT_MC + (n >> 1);
+        float v = 0.f;
+        if (j < ny && mm < nrhs) {
+            float2 w = q[(int64_t)mm * ny + j];
+            v = (n & 1) ? w.y : w.x;
+        }
+        float h, l;
+        tf32_split(v, h, l);
+        const uint32_t o = kmajor_index(n, k, PWT_KC);
+        img[blk * 2 * PWT_BH + o] = h;
+        img[blk * 2 * PWT_BH + PWT_BH + o] = l;
+    }
+}
+
+// bulk copy global -> shared, completion counted in bytes on an mbarrier
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+
+// Leaf factor F_leaf(h) = prod_d E[d][oct_d][h] of one direction (octant path from the
+// leaf's integer coordinates), in the order of leaf_factor.
+__device__ __forceinline__ float2 leaf_factor_dir(const PwArgs<float> &P, uint32_t leaf, int h) {
+    const int4 gl = P.A.leaf_g[leaf];
+    float2 f = make_float2(1.f, 0.f);
+    for (int d = 0; d < P.A.shift; ++d) f = cmul(f, P.E[((size_t)d * 8 + leaf_octant(gl, P.A.shift, d)) * P.nQ + h]);
+    return f;
+}
+
+template <int PH>
+__global__ void __launch_bounds__(PWT_NP + 32, 1) k_pw_forward_tc(PwArgs<float> P, const uint2 *__restrict__ chunks,
+                                                         const float *__restrict__ img, int nblk_m, int nrhs,
+                                                         float2 *__restrict__ ut, int *__restrict__ err, int tries) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    float *bring = reinterpret_cast<float *>(smem);
+    __shared__ uint32_t s_tmem;
+    __shared__ __align__(8) uint64_t s_bfull[PWT_NB], s_empty[PWT_NB], s_afull[PWT_NA];
+    __shared__ int s_bad;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    // blocks run the direction tiles of a chunk side by side: they share its density blocks
+    // in L2, and their atomic additions go to distinct directions
+    const int ntile = (P.nQ / 2 + PWT_M - 1) / PWT_M;
+    const int tile = (int)(blockIdx.x % (unsigned)ntile);
+    const uint2 ck = chunks[blockIdx.x / (unsigned)ntile];
+    const int b = (int)ck.x;
+    const uint32_t p0 = ck.y, p1 = min(P.A.box_start[b + 1], p0 + (uint32_t)PWT_CH);
+    const bool sole = p0 == P.A.box_start[b] && p1 == P.A.box_start[b + 1];
+    const int mb = blockIdx.z, nH = P.nQ / 2;
+    const uint32_t c0 = p0 / PWT_KC;
+    const int nsteps = (int)((p1 + PWT_KC - 1) / PWT_KC - c0);
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&s_tmem)),
+                     "r"(PWT_TCOLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        s_bad = 0;
+        for (int i = 0; i < PWT_NB; ++i) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&s_bfull[i])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&s_empty[i])));
+        }
+        for (int i = 0; i < PWT_NA; ++i)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(&s_afull[i])), "r"(PWT_NP));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = s_tmem;
+    bool ok = true;
+    if (warp >= 1) {
+        // producer of direction pair h (TMEM lane row), points PWT_PP qq .. PWT_PP (qq + 1) - 1
+        // of each step
+        const int dq = warp & 3, qq = (warp - 1) >> 2, row = dq * 32 + lane, h = tile * PWT_M + row;
+        const bool on = h < nH;
+        const float4 kv = P.ks[on ? h : 0];
+        int last_b = -1;  // last density copy issued (producer 0)
+        auto copy_b = [&](int sp) {
+            if (tid != 32 || sp >= nsteps) return;
+            uint64_t *bar = &s_bfull[sp % PWT_NB];
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+                         "r"((uint32_t)(PWT_BST * sizeof(float)))
+                         : "memory");
+            bulk_g2s(bring + (size_t)(sp % PWT_NB) * PWT_BST, img + ((size_t)(c0 + sp) * nblk_m + mb) * PWT_BST,
+                     (uint32_t)(PWT_BST * sizeof(float)), bar);
+            last_b = sp;
+        };
+        for (int sp = 0; sp < PWT_DB; ++sp) copy_b(sp);
+        uint32_t cur_leaf = 0xffffffffu;
+        float2 f = make_float2(1.f, 0.f);
+        for (int s = 0; s < nsteps && ok; ++s) {
+            if (s >= PWT_NA) {
+                // the MMAs of step s - PWT_NA are done: its A stage and density stage are free
+                const int sb = s - PWT_NA;
+                bool w_ok = mbar_wait(&s_empty[sb % PWT_NB], (uint32_t)((sb / PWT_NB) & 1), tries, err);
+                if (!__all_sync(0xffffffffu, w_ok)) {
+                    ok = false;
+                    break;
+                }
+            }
+            copy_b(s + PWT_DB);
+            const uint32_t jb = (c0 + (uint32_t)s) * PWT_KC + (uint32_t)(PWT_PP * qq);
+            const uint32_t ta =
+                tmem + (uint32_t)(256 + (s % PWT_NA) * 128 + PWT_PP * qq) + ((uint32_t)(dq * 32) << 16);
+            {
+                // the points' coordinates first (one latency for all), then the phasors
+                float4 ev[PWT_PP];
+#pragma unroll
+                for (int i = 0; i < PWT_PP; ++i)
+                    ev[i] = (jb + i >= p0 && jb + i < p1) ? P.A.eps[jb + i] : make_float4(0.f, 0.f, 0.f, 0.f);
+                uint32_t rh[PWT_PP], rl[PWT_PP], ih[PWT_PP], il[PWT_PP];
+#pragma unroll
+                for (int i = 0; i < PWT_PP; ++i) {
+                    const uint32_t j = jb + i;
+                    float er = 0.f, ei = 0.f;
+                    if (on && j >= p0 && j < p1) {
+                        const float4 e = ev[i];
+                        const uint32_t leaf = __float_as_uint(e.w);
+                        if (leaf != cur_leaf) {
+                            f = leaf_factor_dir(P, leaf, h);
+                            cur_leaf = leaf;
+                        }
+                        const float ph = fmaf(kv.x, e.x, fmaf(kv.y, e.y, kv.z * e.z));
+                        float sn, cs;
+                        phase_sincos<PH>(ph, sn, cs, nullptr);
+                        er = fmaf(f.x, cs, f.y * sn);  // e = f e^{-i ph}
+                        ei = fmaf(f.y, cs, -f.x * sn);
+                    }
+                    float a, c;
+                    tf32_split(er, a, c);
+                    rh[i] = __float_as_uint(a);
+                    rl[i] = __float_as_uint(c);
+                    tf32_split(ei, a, c);
+                    ih[i] = __float_as_uint(a);
+                    il[i] = __float_as_uint(c);
+                }
+                tmem_st8(ta, rh);
+                tmem_st8(ta + 32u, rl);
+                tmem_st8(ta + 64u, ih);
+                tmem_st8(ta + 96u, il);
+            }
+            asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(&s_afull[s % PWT_NA])) : "memory");
+        }
+        if (ok) {
+            // every MMA done (the last commit completes after the others): u~ from P and Q
+            const int l = nsteps - 1;
+            bool w_ok = mbar_wait(&s_empty[l % PWT_NB], (uint32_t)((l / PWT_NB) & 1), tries, err);
+            if (!__all_sync(0xffffffffu, w_ok)) ok = false;
+        }
+        if (ok) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t lanes = (uint32_t)(dq * 32) << 16;
+#pragma unroll 1
+            for (int c8 = qq * PWT_MC / (8 * PWT_QS); c8 < (qq + 1) * PWT_MC / (8 * PWT_QS); ++c8) {
+                uint32_t pv[16], qv[16];
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                    : "=r"(pv[0]), "=r"(pv[1]), "=r"(pv[2]), "=r"(pv[3]), "=r"(pv[4]), "=r"(pv[5]), "=r"(pv[6]),
+                      "=r"(pv[7]), "=r"(pv[8]), "=r"(pv[9]), "=r"(pv[10]), "=r"(pv[11]), "=r"(pv[12]), "=r"(pv[13]),
+                      "=r"(pv[14]), "=r"(pv[15])
+                    : "r"(tmem + lanes + (uint32_t)(16 * c8)));
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                    : "=r"(qv[0]), "=r"(qv[1]), "=r"(qv[2]), "=r"(qv[3]), "=r"(qv[4]), "=r"(qv[5]), "=r"(qv[6]),
+                      "=r"(qv[7]), "=r"(qv[8]), "=r"(qv[9]), "=r"(qv[10]), "=r"(qv[11]), "=r"(qv[12]), "=r"(qv[13]),
+                      "=r"(qv[14]), "=r"(qv[15])
+                    : "r"(tmem + lanes + 128u + (uint32_t)(16 * c8)));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                for (int mm = 0; mm < 8; ++mm) {
+                    const int m = mb * PWT_MC + c8 * 8 + mm;
+                    if (!on || m >= nrhs) continue;
+                    const float pr = __uint_as_float(pv[2 * mm]), pi = __uint_as_float(pv[2 * mm + 1]);
+                    const float qr = __uint_as_float(qv[2 * mm]), qi = __uint_as_float(qv[2 * mm + 1]);
+                    float2 *o = ut + ((size_t)b * nrhs + m) * P.nQ;
+                    if (sole) {
+                        o[h] = make_float2(pr - qi, pi + qr);
+                        o[h + nH] = make_float2(pr + qi, pi - qr);
+                    } else {
+                        atomicAdd(&o[h].x, pr - qi);
+                        atomicAdd(&o[h].y, pi + qr);
+                        atomicAdd(&o[h + nH].x, pr + qi);
+                        atomicAdd(&o[h + nH].y, pi - qr);
+                    }
+                }
+            }
+        } else {
+            s_bad = 1;
+            // density copies in flight complete on their own: wait for the last one issued
+            // into each stage
+            for (int sp = max(0, last_b - PWT_NB + 1); sp <= last_b; ++sp)
+                mbar_wait(&s_bfull[sp % PWT_NB], (uint32_t)((sp / PWT_NB) & 1), DRAIN_TRIES);
+        }
+    } else if (lane == 0) {
+        // ---- MMA thread: per 8 points, P += Re hi B hi + Re hi B lo + Re lo B hi, and Q likewise
+        const uint32_t lbo = 128, sbo = (PWT_KC / 4) * 128;
+        const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(PWT_N >> 3) << 17) |
+                               ((uint32_t)(PWT_M >> 4) << 24);
+        int issued = 0;
+        for (int s = 0; s < nsteps; ++s) {
+            if (!mbar_wait(&s_bfull[s % PWT_NB], (uint32_t)((s / PWT_NB) & 1), tries, err) ||
+                !mbar_wait(&s_afull[s % PWT_NA], (uint32_t)((s / PWT_NA) & 1), tries, err)) {
+                ok = false;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t a0 = tmem + (uint32_t)(256 + (s % PWT_NA) * 128);
+            const uint32_t bst = smem_addr(bring + (size_t)(s % PWT_NB) * PWT_BST);
+#pragma unroll
+            for (int ks = 0; ks < PWT_KC / 8; ++ks) {
+                const uint64_t bh = umma_desc(bst + ks * 256, lbo, sbo);
+                const uint64_t bl = umma_desc(bst + PWT_BH * 4 + ks * 256, lbo, sbo);
+                const uint32_t acc0 = (s > 0 || ks > 0) ? 1u : 0u;
+#pragma unroll
+                for (int pq = 0; pq < 2; ++pq) {  // P from Re (columns 0..63 of the stage), Q from Im (64..127)
+                    const uint32_t d = tmem + (uint32_t)(128 * pq);
+                    const uint32_t ah = a0 + (uint32_t)(64 * pq + ks * 8), al = ah + 32u;
+                    asm volatile(
+                        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                        "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}\n" ::"r"(d),
+                        "r"(ah), "l"(bh), "r"(idesc), "r"(acc0));
+                    asm volatile("tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, 1;\n" ::"r"(d), "r"(ah),
+                                 "l"(bl), "r"(idesc));
+                    asm volatile("tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, 1;\n" ::"r"(d), "r"(al),
+                                 "l"(bh), "r"(idesc));
+                }
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             smem_addr(&s_empty[s % PWT_NB]))
+                         : "memory");
+            issued = s + 1;
+        }
+        if (!ok) {
+            s_bad = 1;
+            if (issued > 0)
+                mbar_wait(&s_empty[(issued - 1) % PWT_NB], (uint32_t)(((issued - 1) / PWT_NB) & 1), DRAIN_TRIES);
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (tid == 0 && s_bad) atomicOr(err, 1);
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(PWT_TCOLS));
+}
+
+// The backward transform of a target box a is the transposed product: for a point x of the
+// box (leaf-relative coordinate e_x) and right-hand side m,
+//   v(x, m) = sum_h g_xh a_hm + conj(g_xh) b_hm,   g_xh = e^{i k s_h . e_x} conj(F_leaf(x)(h)),
+// with a = v~_a(h), b = v~_a(h + nQ/2).  With S = a + b and D = a - b,
+//   Re v = sum_h Re(g) Re(S) - Im(g) Im(D),   Im v = sum_h Re(g) Im(S) + Im(g) Re(D):
+// a real GEMM of M = points, K = 2 x direction pairs (Re g, Im g of each), N = 2 x
+// right-hand sides, whose B operand (S and D of the box) is shared by all its points.
+// k_pw_vt_image writes that operand per target box, per step of 16 direction pairs and per
+// group of 64 right-hand sides, split into TF32 hi and lo blocks in the K-major layout.
+//
+// k_pw_backward_tc: a CTA takes 128 points of one target box (TMEM lanes) and 64 right-hand
+// sides.  Warps 1-16 produce, four threads per point (4 direction pairs of each step each):
+// a thread forms Re g and Im g (its leaf's octant factors from the E table, one sincos),
+// splits them and writes them into one of three TMEM operand stages; one producer copies the
+// box's B block of the step (32 KB, bulk copy) into one of five shared stages two steps
+// ahead.  One thread of warp 0 issues hi hi + hi lo + lo hi per 8 K values (12 MMAs of M =
+// 128, N = 128, K = 8 per step).  The sum over directions alternates between two TMEM
+// accumulators every PWB_DRAIN steps; the producers add each finished one into FP32
+// registers while the other fills (the same protocol as the target-stationary transfer),
+// and add their sums into the point's FP64 accumulator at the end.
+constexpr int PWB_M = PW_TC_BCH;         // points per CTA
+constexpr int PWB_KC = 32;               // K values per step (16 direction pairs)
+constexpr int PWB_N = 128;               // GEMM columns: re, im of 64 right-hand sides
+constexpr int PWB_MC = PWB_N / 2;
+constexpr int PWB_NA = 3;                // A stages (tensor memory)
+constexpr int PWB_DB = 2;                // steps the B copies run ahead
+constexpr int PWB_NB = PWB_NA + PWB_DB;  // B stages (shared memory)
+constexpr int PWB_DRAIN = 8;             // steps per TMEM accumulator fill
+constexpr int PWB_QS = 4;                // producer threads per point
+constexpr int PWB_HP = PWB_KC / 2 / PWB_QS;  // direction pairs per producer thread and step
+constexpr int PWB_SC = PWB_N / PWB_QS;   // accumulator columns per producer thread
+constexpr int PWB_NP = PWB_QS * PWB_M;   // producer threads (warps 1-16)
+static_assert(PWB_HP == 4, "a producer reads its octant factors as two float4");
+constexpr int PWB_BH = PWB_N * PWB_KC;   // floats per B hi or lo block
+constexpr int PWB_BST = 2 * PWB_BH;      // floats per B stage (32 KB)
+constexpr int PWB_TCOLS = 512;           // TMEM: 2 accumulators x 128, 3 A stages x 64
+constexpr size_t PWB_SMEM = sizeof(float) * (size_t)PWB_NB * PWB_BST;  // 160 KB
+
+// B operand of the backward GEMM: block (target t, step st, group mb) at
+// ((t nsteps + st) nblk_m + mb) 2 PWB_BH, hi then lo; row n = 2 m + (0: Re, 1: Im), column
+// k = 2 (h - 16 st) + (0: Re g, 1: Im g); zero past nH and nrhs.
+__global__ void k_pw_vt_image(const float2 *__restrict__ vt, const uint32_t *__restrict__ tgt, int64_t n_tgt,
+                              int nrhs, int nQ, int nsteps, int nblk_m, float *__restrict__ img) {
+    const int nH = nQ / 2;
+    const int64_t nimg = n_tgt * nsteps * nblk_m * (int64_t)PWB_BH;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nimg; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t blk = i / PWB_BH;
+        const int e = (int)(i - blk * PWB_BH);
+        const int n = e / PWB_KC, k = e % PWB_KC;
+        const int64_t tb = blk / nblk_m;
+        const int mb = (int)(blk - tb * nblk_m);
+        const int64_t t = tb / nsteps;
+        const int st = (int)(tb - t * nsteps);
+        const int h = st * (PWB_KC / 2) + (k >> 1), m = mb * PWB_MC + (n >> 1);
+        float v = 0.f;
+        if (h < nH && m < nrhs) {
+            const float2 *va = vt + ((size_t)tgt[t] * nrhs + m) * nQ;
+            const float2 a = va[h], b = va[h + nH];
+            if ((k & 1) == 0)
+                v = (n & 1) ? a.y + b.y : a.x + b.x;  // Re g row: S
+            else
+                v = (n & 1) ? a.x - b.x : b.y - a.y;  // Im g row: (-Im D, Re D)
+        }
+        float hi, lo;
+        tf32_split(v, hi, lo);
+        const uint32_t o = kmajor_index(n, k, PWB_KC);
+        img[blk * 2 * PWB_BH + o] = hi;
+        img[blk * 2 * PWB_BH + PWB_BH + o] = lo;
+    }
+}
+
+template <int PH>
+__global__ void __launch_bounds__(PWB_NP + 32, 1) k_pw_backward_tc(PwArgs<float> P, const uint2 *__restrict__ chunks,
+                                                                  const int *__restrict__ slot,
+                                                                  const float *__restrict__ img, int nblk_m,
+                                                                  int nrhs, int64_t nx, double2 *__restrict__ acc,
+                                                                  int *__restrict__ err, int tries) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    float *bring = reinterpret_cast<float *>(smem);
+    __shared__ uint32_t s_tmem;
+    __shared__ __align__(8) uint64_t s_bfull[PWB_NB], s_empty[PWB_NB], s_afull[PWB_NA], s_drained;
+    __shared__ int s_bad;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint2 ck = chunks[blockIdx.x];
+    const int a = (int)ck.x, mb = blockIdx.y;
+    const uint32_t x0 = ck.y, x1 = min(P.A.box_start[a + 1], x0 + (uint32_t)PWB_M);
+    const int nH = P.nQ / 2;
+    const int nsteps = (nH + PWB_KC / 2 - 1) / (PWB_KC / 2);
+    const float *bimg = img + (size_t)slot[a] * nsteps * nblk_m * PWB_BST;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&s_tmem)),
+                     "r"(PWB_TCOLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        s_bad = 0;
+        for (int i = 0; i < PWB_NB; ++i) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&s_bfull[i])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&s_empty[i])));
+        }
+        for (int i = 0; i < PWB_NA; ++i)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(&s_afull[i])), "r"(PWB_NP));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(&s_drained)), "r"(PWB_NP));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = s_tmem;
+    bool ok = true;
+    if (warp >= 1) {
+        // producer of point x (TMEM lane row), direction pairs PWB_HP qq .. PWB_HP (qq + 1) - 1
+        // of each step, accumulator columns PWB_SC qq .. PWB_SC (qq + 1) - 1
+        const int dq = warp & 3, qq = (warp - 1) >> 2, row = dq * 32 + lane;
+        const uint32_t x = x0 + (uint32_t)row;
+        const bool on = x < x1;
+        const float4 e = P.A.eps[on ? x : x0];
+        uint64_t oct = 0;  // octant path of the point's leaf, 3 bits per level
+        {
+            const int4 gl = P.A.leaf_g[__float_as_uint(e.w)];
+            for (int d = 0; d < P.A.shift; ++d) oct |= (uint64_t)leaf_octant(gl, P.A.shift, d) << (3 * d);
+        }
+        float sum[PWB_SC];
+#pragma unroll
+        for (int c = 0; c < PWB_SC; ++c) sum[c] = 0.f;
+        int drained = 0;
+        auto drain = [&](int k) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t base =
+                tmem + (uint32_t)((k & 1) * 128 + qq * PWB_SC) + ((uint32_t)(dq * 32) << 16);
+#pragma unroll
+            for (int c0 = 0; c0 < PWB_SC; c0 += 16) {
+                uint32_t v[16];
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                      "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+                      "=r"(v[15])
+                    : "r"(base + (uint32_t)c0));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                for (int q = 0; q < 16; ++q) sum[c0 + q] += __uint_as_float(v[q]);
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(&s_drained)) : "memory");
+        };
+        int last_b = -1;
+        auto copy_b = [&](int sp) {
+            if (tid != 32 || sp >= nsteps) return;
+            uint64_t *bar = &s_bfull[sp % PWB_NB];
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+                         "r"((uint32_t)(PWB_BST * sizeof(float)))
+                         : "memory");
+            bulk_g2s(bring + (size_t)(sp % PWB_NB) * PWB_BST, bimg + ((size_t)sp * nblk_m + mb) * PWB_BST,
+                     (uint32_t)(PWB_BST * sizeof(float)), bar);
+            last_b = sp;
+        };
+        for (int sp = 0; sp < PWB_DB; ++sp) copy_b(sp);
+        for (int s = 0; s < nsteps && ok; ++s) {
+            if (s >= PWB_NA) {
+                // the MMAs of step s - PWB_NA are done: its A and B stages are free; fill k is
+                // drained once the first step of fill k + 1 is done (see k_lag_gemm_ts)
+                const int sb = s - PWB_NA;
+                bool w_ok = mbar_wait(&s_empty[sb % PWB_NB], (uint32_t)((sb / PWB_NB) & 1), tries, err);
+                if (!__all_sync(0xffffffffu, w_ok)) {
+                    ok = false;
+                    break;
+                }
+                const int done = sb / PWB_DRAIN;
+                while (drained < done) drain(drained++);
+            }
+            copy_b(s + PWB_DB);
+            // leaf factors of this thread's PWB_HP directions (one row of the octant factors per
+            // level, consecutive directions), then the phasors
+            const int h0 = s * (PWB_KC / 2) + PWB_HP * qq;
+            const bool full = h0 + PWB_HP <= nH;
+            float2 f[PWB_HP];
+#pragma unroll
+            for (int i = 0; i < PWB_HP; ++i) f[i] = make_float2(1.f, 0.f);
+            if (on && full) {
+#pragma unroll 2
+                for (int d = 0; d < P.A.shift; ++d) {
+                    const float4 *er = reinterpret_cast<const float4 *>(
+                        P.E + (uint32_t)(d * 8 + (int)((oct >> (3 * d)) & 7)) * (uint32_t)P.nQ + (uint32_t)h0);
+                    const float4 e01 = __ldg(er), e23 = __ldg(er + 1);
+                    f[0] = cmul(f[0], make_float2(e01.x, e01.y));
+                    f[1] = cmul(f[1], make_float2(e01.z, e01.w));
+                    f[2] = cmul(f[2], make_float2(e23.x, e23.y));
+                    f[3] = cmul(f[3], make_float2(e23.z, e23.w));
+                }
+            } else if (on) {
+                for (int i = 0; i < PWB_HP && h0 + i < nH; ++i)
+                    for (int d = 0; d < P.A.shift; ++d)
+                        f[i] = cmul(f[i], P.E[(uint32_t)(d * 8 + (int)((oct >> (3 * d)) & 7)) * (uint32_t)P.nQ +
+                                             (uint32_t)(h0 + i)]);
+            }
+            uint32_t hv[2 * PWB_HP], lv[2 * PWB_HP];
+#pragma unroll
+            for (int i = 0; i < PWB_HP; ++i) {
+                const int h = h0 + i;
+                float gr = 0.f, gi = 0.f;
+                if (on && h < nH) {
+                    const float4 kv = P.ks[h];
+                    const float ph = fmaf(kv.x, e.x, fmaf(kv.y, e.y, kv.z * e.z));
+                    float sn, cs;
+                    phase_sincos<PH>(ph, sn, cs, nullptr);
+                    gr = fmaf(cs, f[i].x, sn * f[i].y);  // g = e^{i ph} conj(f)
+                    gi = fmaf(sn, f[i].x, -cs * f[i].y);
+                }
+                float hi, lo;
+                tf32_split(gr, hi, lo);
+                hv[2 * i] = __float_as_uint(hi);
+                lv[2 * i] = __float_as_uint(lo);
+                tf32_split(gi, hi, lo);
+                hv[2 * i + 1] = __float_as_uint(hi);
+                lv[2 * i + 1] = __float_as_uint(lo);
+            }
+            const uint32_t ta =
+                tmem + (uint32_t)(256 + (s % PWB_NA) * 64 + 2 * PWB_HP * qq) + ((uint32_t)(dq * 32) << 16);
+            tmem_st8(ta, hv);
+            tmem_st8(ta + 32u, lv);
+            asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(&s_afull[s % PWB_NA])) : "memory");
+        }
+        if (ok) {
+            const int l = nsteps - 1;
+            bool w_ok = mbar_wait(&s_empty[l % PWB_NB], (uint32_t)((l / PWB_NB) & 1), tries, err);
+            if (!__all_sync(0xffffffffu, w_ok)) ok = false;
+            const int fills = (nsteps + PWB_DRAIN - 1) / PWB_DRAIN;
+            while (ok && drained < fills) drain(drained++);
+        }
+        if (!ok) {
+            s_bad = 1;
+            for (int sp = max(0, last_b - PWB_NB + 1); sp <= last_b; ++sp)  // copies still in flight
+                mbar_wait(&s_bfull[sp % PWB_NB], (uint32_t)((sp / PWB_NB) & 1), DRAIN_TRIES);
+        } else if (on) {
+#pragma unroll
+            for (int j = 0; j < PWB_SC / 2; ++j) {
+                const int m = mb * PWB_MC + (PWB_SC / 2) * qq + j;
+                if (m < nrhs) {
+                    double2 &dst = acc[(int64_t)m * nx + x];
+                    dst.x += (double)sum[2 * j];
+                    dst.y += (double)sum[2 * j + 1];
+                }
+            }
+        }
+    } else if (lane == 0) {
+        // ---- MMA thread
+        const uint32_t lbo = 128, sbo = (PWB_KC / 4) * 128;
+        const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(PWB_N >> 3) << 17) |
+                               ((uint32_t)(PWB_M >> 4) << 24);
+        int issued = 0;
+        for (int s = 0; s < nsteps; ++s) {
+            const int fill = s / PWB_DRAIN;
+            if (s % PWB_DRAIN == 0 && fill >= 2 && !mbar_wait(&s_drained, (uint32_t)((fill - 2) & 1), tries, err)) {
+                ok = false;
+                break;
+            }
+            if (!mbar_wait(&s_bfull[s % PWB_NB], (uint32_t)((s / PWB_NB) & 1), tries, err) ||
+                !mbar_wait(&s_afull[s % PWB_NA], (uint32_t)((s / PWB_NA) & 1), tries, err)) {
+                ok = false;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t d = tmem + (uint32_t)((fill & 1) * 128);
+            const uint32_t a0 = tmem + (uint32_t)(256 + (s % PWB_NA) * 64);
+            const uint32_t bst = smem_addr(bring + (size_t)(s % PWB_NB) * PWB_BST);
+#pragma unroll
+            for (int ks = 0; ks < PWB_KC / 8; ++ks) {
+                const uint32_t ah = a0 + (uint32_t)(ks * 8), al = ah + 32u;
+                const uint64_t bh = umma_desc(bst + ks * 256, lbo, sbo);
+                const uint64_t bl = umma_desc(bst + PWB_BH * 4 + ks * 256, lbo, sbo);
+                const uint32_t acc0 = (s % PWB_DRAIN != 0 || ks > 0) ? 1u : 0u;
+                asm volatile(
+                    "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                    "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}\n" ::"r"(d),
+                    "r"(ah), "l"(bh), "r"(idesc), "r"(acc0));
+                asm volatile("tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, 1;\n" ::"r"(d), "r"(ah), "l"(bl),
+                             "r"(idesc));
+                asm volatile("tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, 1;\n" ::"r"(d), "r"(al), "l"(bh),
+                             "r"(idesc));
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             smem_addr(&s_empty[s % PWB_NB]))
+                         : "memory");
+            issued = s + 1;
+        }
+        if (!ok) {
+            s_bad = 1;
+            if (issued > 0)
+                mbar_wait(&s_empty[(issued - 1) % PWB_NB], (uint32_t)(((issued - 1) / PWB_NB) & 1), DRAIN_TRIES);
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (tid == 0 && s_bad) atomicOr(err, 1);
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(PWB_TCOLS));
+}
+
 template <class R, int PH>
 static void planewave_level(const ffm_plan_s *p, int l, const float2 *q, int nrhs, double2 *acc, Alloc &tmp,
                             cudaStream_t s, const typename PwT<R>::K *ks, const typename PwT<R>::C *D,
@@ -2034,8 +2642,29 @@ static void planewave_level(const ffm_plan_s *p, int l, const float2 *q, int nrh
         if ((double)cdiv(nH, tb * qpt) * tb * qpt > 1.1 * nH) tb = cand;
     bool multi = nrhs > 1;
     constexpr bool f32 = std::is_same<R, float>::value;
+    // several right-hand sides on the tensor cores (TF32 x3): the forward transform on FP32
+    // and compensated-FP32 levels, the backward transform on FP32 levels (the compensated
+    // one carries its rounding error through the direction sum, which the tensor cores do not)
+    const bool tc_fwd = f32 && multi && F.pw_chunks != nullptr &&
+                        (p->pw_transform == 3 || (p->pw_transform == 0 && nrhs >= PW_TC_MIN_RHS));
+    const bool tc_bwd = tc_fwd && !COMP;
     if (f32 && F.nufft) {
         if constexpr (f32) nufft_forward(p, l, q, nrhs, ut, tmp, s);
+    } else if (tc_fwd) {
+        if constexpr (f32) {
+            const int nblk_m = (int)cdiv(nrhs, PWT_MC);
+            float *img = tmp.get<float>((size_t)cdiv(p->ny, PWT_KC) * nblk_m * PWT_BST);
+            const int64_t nimg = (int64_t)cdiv(p->ny, PWT_KC) * nblk_m * PWT_BH;
+            FFM_LAUNCH(k_pw_density_image, std::min<int64_t>(cdiv(nimg, 256), 152 * 16), 256, 0, s, q, p->ny, nrhs,
+                       nblk_m, img);
+            FFM_CUDA(cudaMemsetAsync(ut, 0, sizeof(C2) * (size_t)p->by[l].nb * nrhs * F.nQ, s));
+            FFM_CUDA(cudaFuncSetAttribute(k_pw_forward_tc<PH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)PWT_SMEM));
+            dim3 g((unsigned)(F.n_pw_chunks * cdiv(nH, PWT_M)), 1, (unsigned)nblk_m);
+            FFM_LAUNCH_NAMED(name("k_pw_forward_tc"), k_pw_forward_tc<PH>, g, PWT_NP + 32, PWT_SMEM, s, PY,
+                             F.pw_chunks, img, nblk_m, nrhs, ut, p->dev_err, p->wait_tries);
+            tmp.drop(img);
+        }
     } else if (multi) {
         if (!dbl && mc == 4) {
             dim3 gm((unsigned)F.n_src, cdiv(nH, 128), cdiv(nrhs, 4));
@@ -2072,6 +2701,22 @@ static void planewave_level(const ffm_plan_s *p, int l, const float2 *q, int nrh
     int *slot = tmp.get<int>(nbx);
     FFM_LAUNCH(k_slot_init, cdiv(nbx, 256), 256, 0, s, slot, nbx);
     FFM_LAUNCH(k_slot_set, cdiv(F.n_tgt, 256), 256, 0, s, F.tgt, F.n_tgt, slot);
+    if (tc_bwd) {
+        if constexpr (f32) {
+            const int nblk_m = (int)cdiv(nrhs, PWB_MC), nst = (int)cdiv(nH, PWB_KC / 2);
+            float *bimg = tmp.get<float>((size_t)F.n_tgt * nst * nblk_m * PWB_BST);
+            const int64_t nimg = F.n_tgt * nst * nblk_m * (int64_t)PWB_BH;
+            FFM_LAUNCH(k_pw_vt_image, std::min<int64_t>(cdiv(nimg, 256), 152 * 16), 256, 0, s, (const float2 *)vt,
+                       F.tgt, F.n_tgt, nrhs, F.nQ, nst, nblk_m, bimg);
+            FFM_CUDA(cudaFuncSetAttribute(k_pw_backward_tc<PH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)PWB_SMEM));
+            dim3 g((unsigned)F.n_pw_tchunks, (unsigned)nblk_m, 1);
+            FFM_LAUNCH_NAMED(name("k_pw_backward_tc"), k_pw_backward_tc<PH>, g, PWB_NP + 32, PWB_SMEM, s, PX,
+                             F.pw_tchunks, slot, bimg, nblk_m, nrhs, p->nx, acc, p->dev_err, p->wait_tries);
+            tmp.drop(bimg);
+        }
+        return;
+    }
     if (multi) {
         if (!dbl && mc == 4) {
             dim3 gm((unsigned)p->bx[ls].nb, 1, cdiv(nrhs, 4));

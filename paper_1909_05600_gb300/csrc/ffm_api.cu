@@ -333,7 +333,7 @@ ffm_status ffm_plan(const void *X, ffm_dtype xdt, int64_t nx, const void *Y, ffm
                 opts->r1_override < 0 || opts->r1_override > R1MAX || opts->r1_override == 1 ||
                 opts->precision < FFM_PREC_AUTO || opts->precision > FFM_PREC_F32X2 ||
                 opts->lagrange_transfer < 0 || opts->lagrange_transfer > 3 || opts->pw_transform < 0 ||
-                opts->pw_transform > 2 || !(opts->aca_eps >= 0.0 && opts->aca_eps < 1.0) || opts->wait_tries < -1)
+                opts->pw_transform > 3 || !(opts->aca_eps >= 0.0 && opts->aca_eps < 1.0) || opts->wait_tries < -1)
                 fail(FFM_EINVAL, "bad option value");
             if (opts->aca_eps > 0.0 && kernel != FFM_LAPLACE)
                 fail(FFM_EUNSUPPORTED, "the ACA transfer is built for the Laplace single layer");

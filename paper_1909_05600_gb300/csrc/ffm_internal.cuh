@@ -19,6 +19,10 @@ constexpr int R1MAX = 8;         // largest Chebyshev node count per axis
 constexpr int LAG_GEMM_BN = 32;  // pairs (GEMM columns) per tile of the Lagrange transfer
 constexpr int P2P_T = 128;        // threads per near-field block (the largest target chunk)
 constexpr int LAG_CHUNK = 512;    // points per block of the Lagrange point-wise kernels
+constexpr int PW_TC_FCH = 256;    // points per block of the tensor-core plane-wave forward transform
+constexpr int PW_TC_BCH = 128;    // points per block of the tensor-core plane-wave backward transform
+constexpr int PW_TC_MIN_RHS = 16; // right-hand sides from which the plane-wave transforms run on
+                                  // the tensor cores by default
 constexpr int NUFFT_MIN_NQ = 8000; // plane-wave levels with at least this many directions run
                                    // their F steps as NUFFTs (unless forced either way)
 constexpr double PI = 3.14159265358979323846;
@@ -201,6 +205,12 @@ struct FarLevel {
     dd2 *Ex = nullptr;
     int nufft = 0;                  // F steps as type-3 NUFFTs (FP32 plane-wave levels)
     NuLevel nu;
+    // tensor-core F steps for several right-hand sides (FP32 and compensated-FP32 direct
+    // levels): (box, first point) pieces of PW_TC_FCH points of the source boxes and of
+    // PW_TC_BCH points of the target boxes
+    int64_t n_pw_chunks = 0, n_pw_tchunks = 0;
+    uint2 *pw_chunks = nullptr;
+    uint2 *pw_tchunks = nullptr;
 };
 
 }  // namespace ffm

@@ -1023,13 +1023,13 @@ __global__ void k_chunk_emit(const uint32_t *__restrict__ list, int64_t n, const
 }
 
 static uint2 *build_chunks(ffm_plan_s *p, const uint32_t *list, int64_t n, const uint32_t *start, int64_t *count,
-                           Alloc &tmp, cudaStream_t s) {
+                           Alloc &tmp, cudaStream_t s, uint32_t ch = LAG_CHUNK) {
     uint32_t *cnt = tmp.get<uint32_t>(n), *pos = tmp.get<uint32_t>(n), *tot = tmp.get<uint32_t>(1);
-    FFM_LAUNCH(k_chunk_count, cdiv(n, 256), 256, 0, s, list, n, start, (uint32_t)LAG_CHUNK, cnt);
+    FFM_LAUNCH(k_chunk_count, cdiv(n, 256), 256, 0, s, list, n, start, ch, cnt);
     scan_u32(cnt, pos, n, tot, tmp, s);
     *count = read_u32(tot, s);
     uint2 *out = p->mem.get<uint2>(*count);
-    FFM_LAUNCH(k_chunk_emit, cdiv(n, 256), 256, 0, s, list, n, start, (uint32_t)LAG_CHUNK, pos, out);
+    FFM_LAUNCH(k_chunk_emit, cdiv(n, 256), 256, 0, s, list, n, start, ch, pos, out);
     return out;
 }
 
@@ -1495,6 +1495,17 @@ void build_plan(ffm_plan_s *p, const void *X, ffm_dtype xdt, const void *Y, ffm_
                                            : (F.prec == FFM_PREC_F32 && F.nQ >= NUFFT_MIN_NQ);
         if (want && nufft_possible(p, l)) build_nufft(p, l, tmp, s);
     }
+    // the remaining FP32 and compensated-FP32 direct levels: point pieces of their boxes for
+    // the tensor-core transforms of several right-hand sides (not with direct sums forced
+    // onto the CUDA cores, nor for the NUFFT)
+    if (p->pw_transform == 0 || p->pw_transform == 3)
+        for (int l = 0; l <= ls; ++l) {
+            FarLevel &F = p->far[l];
+            if (F.mode != 2 || F.n_adm == 0 || F.nufft || (F.prec != FFM_PREC_F32 && F.prec != FFM_PREC_F32C))
+                continue;
+            F.pw_chunks = build_chunks(p, F.src, F.n_src, p->by[l].start, &F.n_pw_chunks, tmp, s, PW_TC_FCH);
+            F.pw_tchunks = build_chunks(p, F.tgt, F.n_tgt, p->bx[l].start, &F.n_pw_tchunks, tmp, s, PW_TC_BCH);
+        }
     FFM_CUDA(cudaStreamSynchronize(s));
 }
 

@@ -27,7 +27,7 @@ PREC_AUTO, PREC_F32, PREC_F32C, PREC_F64, PREC_F32X2 = 0, 1, 2, 3, 4
 # Lagrange transfer variants (ffm_opts.lagrange_transfer)
 LAG_DEFAULT, LAG_CUDA_CORES, LAG_TC_TRANSLATION, LAG_TC_TARGET = 0, 1, 2, 3
 # plane-wave source / target steps (ffm_opts.pw_transform)
-PW_AUTO, PW_DIRECT, PW_NUFFT = 0, 1, 2
+PW_AUTO, PW_DIRECT, PW_NUFFT, PW_DIRECT_TC = 0, 1, 2, 3
 EXPORT_PERM_X, EXPORT_PERM_Y, EXPORT_ADM, EXPORT_NEAR = 0, 1, 2, 3
 STATUS = {0: "FFM_OK", 1: "FFM_EINVAL", 2: "FFM_ENOMEM", 3: "FFM_ECUDA", 4: "FFM_ETIMEOUT", 5: "FFM_EUNSUPPORTED"}
 
@@ -274,7 +274,8 @@ class Plan:
                  kappa_switch=0.0, r1_override=0, precision=PREC_AUTO, autotune_cache=None,
                  lagrange_transfer=0, normals=None, pw_transform=PW_AUTO, aca_eps=0.0, wait_tries=0):
         """normals: (ny, 3) source normals, required for LAPLACE_DL (double layer).
-        pw_transform: PW_AUTO, PW_DIRECT or PW_NUFFT for the plane-wave levels' F steps.
+        pw_transform: PW_AUTO, PW_DIRECT, PW_NUFFT or PW_DIRECT_TC for the plane-wave levels'
+        F steps (PW_DIRECT_TC: direct sums, on the tensor cores from 2 right-hand sides).
         aca_eps: LAPLACE only; > 0 replaces each transfer matrix by its adaptive cross
         approximation to that Frobenius tolerance (eq. 11).
         wait_tries: attempts per bounded device-side wait (0: the default; -1: none, so the

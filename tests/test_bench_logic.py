@@ -62,6 +62,24 @@ def test_gegenbauer_table_units_follow_each_levels_table_kernel():
     assert dd["units_per_step"] == pytest.approx(72.0 * 40 * 20)
 
 
+def test_tensor_core_transform_units_count_each_levels_points_directions_and_columns():
+    # levels 2, 3 FP32, level 4 compensated, level 5 double-float; 64 right-hand sides
+    info = _info(mode={2: 2, 3: 2, 4: 2, 5: 2}, nQ={2: 6844, 3: 2380, 4: 924, 5: 480},
+                 pw_prec={2: 1, 3: 1, 4: 2, 5: 4}, src_points={2: 200000, 3: 199000, 4: 198000, 5: 190000},
+                 tgt_points={2: 150000, 3: 149000, 4: 148000, 5: 140000}, n_adm={2: 2504, 3: 12960, 5: 184896})
+    fwd = bench.roofline({"k_pw_forward_tc<f32>": (2, 4.0)}, info, 1, 2070.0, PK, "measured", "cube", nrhs=64)
+    assert fwd["bound"] == "tensor"
+    assert fwd["units_per_step"] == pytest.approx(8.0 * 64 * (200000 * 3422 + 199000 * 1190))
+    fwc = bench.roofline({"k_pw_forward_tc<f32c>": (1, 1.0)}, info, 1, 2070.0, PK, "measured", "cube", nrhs=64)
+    assert fwc["units_per_step"] == pytest.approx(8.0 * 64 * 198000 * 462)
+    bwd = bench.roofline({"k_pw_backward_tc<f32>": (2, 4.0)}, info, 1, 2070.0, PK, "measured", "cube", nrhs=64)
+    assert bwd["units_per_step"] == pytest.approx(8.0 * 64 * (150000 * 3422 + 149000 * 1190))
+    tr = bench.roofline({"k_pw_transfer<f32x2>": (1, 17.0)}, info, 1, 2070.0, PK, "measured", "cube", nrhs=64)
+    assert tr["bound"] == "alu" and tr["units_per_step"] == pytest.approx(72.0 * 64 * 184896 * 480)
+    bdd = bench.roofline({"k_pw_backward_mr<f32x2>": (1, 16.0)}, info, 1, 2070.0, PK, "measured", "cube", nrhs=64)
+    assert bdd["units_per_step"] == pytest.approx(72.0 * 64 * 140000 * 240)
+
+
 def test_traffic_figures_are_void_once_the_kernel_source_changes(tmp_path, monkeypatch):
     src = tmp_path / "paper_1909_05600_gb300" / "csrc"
     src.mkdir(parents=True)

@@ -109,5 +109,5 @@ def test_nufft_apply_in_a_graph_matches_eager():
 def test_pw_transform_option_is_checked():
     prob = W.helmholtz_sphere(2000, seed=8)
     with pytest.raises(ffm.FFMError) as e:
-        _plan(prob, pw_transform=3)
+        _plan(prob, pw_transform=4)
     assert e.value.status == 1

@@ -1,6 +1,7 @@
-"""CPU model of the synchronisation of the target-stationary tensor-core transfer
-(k_lag_gemm_ts): producers, the MMA thread, and the asynchronous completions of the copies and
-of the committed MMAs, over random interleavings.  mbarrier waits follow the hardware's parity
+"""CPU model of the synchronisation of the pipelined tcgen05 kernels (the target-stationary
+transfer k_lag_gemm_ts, and the plane-wave transforms k_pw_backward_tc, same constants, and
+k_pw_forward_tc, two A stages and no accumulator drains): producers, the MMA thread, and the
+asynchronous completions of the copies and of the committed MMAs, over random interleavings.  mbarrier waits follow the hardware's parity
 rule: a wait for phase k succeeds iff the barrier's completed-phase count has a parity other
 than k's, so a barrier two phases ahead of a wait looks incomplete.  The model checks that no
 schedule deadlocks and that no wait ever sees its barrier two phases ahead."""
@@ -25,7 +26,8 @@ class Bar:
         return ok
 
 
-def run(nsteps, seed, drain_rule):
+def run(nsteps, seed, drain_rule, NA=NA, DB=DB, DRAIN=DRAIN):
+    NB = NA + DB
     rnd = random.Random(seed)
     bfull = [Bar("bfull%d" % i) for i in range(NB)]
     empty = [Bar("empty%d" % i) for i in range(NB)]
@@ -99,6 +101,14 @@ KERNEL_RULE = lambda s: (s - NA) // DRAIN  # drain a fill once the next fill's f
 def test_transfer_protocol_never_deadlocks_or_aliases(nsteps):
     for seed in range(10):
         run(nsteps, seed, KERNEL_RULE)
+
+
+@pytest.mark.parametrize("nsteps", [1, 2, 3, 5, 8, 9, 31, 214])
+def test_forward_transform_protocol_never_deadlocks_or_aliases(nsteps):
+    # k_pw_forward_tc: two TMEM operand stages, density copies two steps ahead, one
+    # accumulator that is never drained mid-way
+    for seed in range(10):
+        run(nsteps, seed, lambda s: 0, NA=2, DB=2, DRAIN=1 << 30)
 
 
 def test_model_catches_a_drain_two_phases_ahead():
