@@ -60,8 +60,9 @@ def parse():
                     help="time budget of the all-core direct-sum leg when --cpu-targets is 0")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--pw-transform", default="auto", choices=["auto", "direct", "nufft"],
-                    help="plane-wave F steps: chosen per level, direct sums, or the NUFFT where possible")
+    ap.add_argument("--pw-transform", default="auto", choices=["auto", "direct", "nufft", "tc"],
+                    help="plane-wave F steps: chosen per level, direct sums on the CUDA cores, the NUFFT "
+                         "where possible, or direct sums with tensor-core products for several RHS")
     ap.add_argument("--eps", type=float, default=0.0, help="accuracy eps (0: the workload's own)")
     ap.add_argument("--aca", type=float, default=0.0, metavar="EPS_T",
                     help="Laplace workloads: transfer matrices as ACA factors to this tolerance (eq. 11)")
@@ -726,7 +727,8 @@ def main():
     u = torch.as_tensor(u_host, device=dev)
     # extra plan arguments: the source normals of the double layer
     kw = {"normals": torch.as_tensor(prob.meta["normals"], device=dev)} if "normals" in prob.meta else {}
-    kw["pw_transform"] = {"auto": ffm.PW_AUTO, "direct": ffm.PW_DIRECT, "nufft": ffm.PW_NUFFT}[args.pw_transform]
+    kw["pw_transform"] = {"auto": ffm.PW_AUTO, "direct": ffm.PW_DIRECT, "nufft": ffm.PW_NUFFT,
+                          "tc": ffm.PW_DIRECT_TC}[args.pw_transform]
     if args.aca > 0:
         kw["aca_eps"] = args.aca
     if args.lagrange_transfer != "default":
