@@ -395,6 +395,14 @@ __device__ __forceinline__ void cp_async16(void *dst, const void *src) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
 }
 
+// bulk copy global -> shared, completion counted in bytes on an mbarrier
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+
 // Bounded wait for the completion of phase `parity` of an mbarrier: at most `tries`
 // try_wait attempts (none for tries <= 0); false if it gave up.
 // With `abort` (the launch's device error flag), the wait also gives up once another CTA has
@@ -662,9 +670,9 @@ __global__ void k_split_pad(const float *__restrict__ src, int64_t nmat, int row
 // of the row's 64 values.  A producer loads its values of the row's source (zero where the
 // row has no partner) from global memory into registers TS_P steps ahead, splits them into
 // TF32 hi and lo parts and writes them into one of TS_NA TMEM operand stages (tcgen05.st),
-// then arrives on that stage's "A full" mbarrier.  It also copies its share of T_t's
-// pre-split image (32 KB in all) with cp.async into one of TS_NB shared stages, TS_DB steps
-// ahead, and arrives on that stage's "B full" mbarrier once the copies land.  One thread of
+// then arrives on that stage's "A full" mbarrier.  The first producer also starts a bulk copy
+// of T_t's pre-split image (32 KB) into one of TS_NB shared stages, TS_DB steps ahead,
+// counted in bytes on that stage's "B full" mbarrier.  One thread of
 // warp 0 waits on both, issues the step's 24 MMAs and commits them to the B stage's "empty"
 // mbarrier; the producers wait on it (TS_NA steps later) before they reuse the A and B
 // stages.  Each barrier round trip thus serves 24 MMAs.
@@ -734,7 +742,7 @@ __global__ void __launch_bounds__(TS_NP + 32, 1) k_lag_gemm_ts(const uint32_t *_
     if (tid == 0) {
         s_bad = 0;
         for (int i = 0; i < TS_NB; ++i) {
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(&s_bfull[i])), "r"(TS_NP));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&s_bfull[i])));
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&s_empty[i])));
         }
         for (int i = 0; i < TS_NA; ++i)
@@ -799,19 +807,18 @@ __global__ void __launch_bounds__(TS_NP + 32, 1) k_lag_gemm_ts(const uint32_t *_
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(&s_drained)) : "memory");
         };
-        // T_t's image of step sp into B stage sp % TS_NB: 2048 segments, 8 per producer; the
-        // arrive fires once this thread's copies (and its earlier ones) have landed
+        // T_t's image of step sp into B stage sp % TS_NB: one bulk copy (32 KB) by the first
+        // producer, counted in bytes on the stage's "B full" barrier
+        int last_b = -1;
         auto copy_b = [&](int sp) {
-            if (sp >= nsteps) return;
-            const float *Bs = Tsp + (size_t)s_tl[sp] * TS_BST;
-            float *B = bring + (size_t)(sp % TS_NB) * TS_BST;
-#pragma unroll
-            for (int i = 0; i < TS_BST / 4 / TS_NP; ++i) {
-                const int e = p + TS_NP * i;
-                cp_async16(B + 4 * e, Bs + 4 * e);
-            }
-            asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_addr(&s_bfull[sp % TS_NB]))
+            if (p != 0 || sp >= nsteps) return;
+            uint64_t *bar = &s_bfull[sp % TS_NB];
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+                         "r"((uint32_t)(TS_BST * sizeof(float)))
                          : "memory");
+            bulk_g2s(bring + (size_t)(sp % TS_NB) * TS_BST, Tsp + (size_t)s_tl[sp] * TS_BST,
+                     (uint32_t)(TS_BST * sizeof(float)), bar);
+            last_b = sp;
         };
         // this row's source values of step sp (zero without a partner), into registers.  The
         // row's next two partners (translation, source) are held in registers and the one after
@@ -906,8 +913,11 @@ __global__ void __launch_bounds__(TS_NP + 32, 1) k_lag_gemm_ts(const uint32_t *_
             const int fills = (nsteps + TS_DRAIN - 1) / TS_DRAIN;
             while (ok && drained < fills) drain(drained++);
         }
-        asm volatile("cp.async.wait_all;" ::: "memory");
-        if (!ok) s_bad = 1;
+        if (!ok) {
+            s_bad = 1;
+            for (int sp = max(0, last_b - TS_NB + 1); sp <= last_b; ++sp)  // copies still in flight
+                mbar_wait(&s_bfull[sp % TS_NB], (uint32_t)((sp / TS_NB) & 1), DRAIN_TRIES);
+        }
         if (ok && x < n_tgt) {
             float *dst = vt + ((size_t)tgt[x] * nrhs + m) * r + qh * 32;
 #pragma unroll
@@ -2079,13 +2089,6 @@ __global__ void k_pw_density_image(const float2 *__restrict__ q, int64_t ny, int
     }
 }
 
-// bulk copy global -> shared, completion counted in bytes on an mbarrier
-__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                     smem_addr(dst)),
-                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
-                 : "memory");
-}
 
 // Leaf factor F_leaf(h) = prod_d E[d][oct_d][h] of one direction (octant path from the
 // leaf's integer coordinates), in the order of leaf_factor.

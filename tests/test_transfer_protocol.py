@@ -1,6 +1,6 @@
 """CPU model of the synchronisation of the pipelined tcgen05 kernels (the target-stationary
-transfer k_lag_gemm_ts, and the plane-wave transforms k_pw_backward_tc, same constants, and
-k_pw_forward_tc, two A stages and no accumulator drains): producers, the MMA thread, and the
+transfer k_lag_gemm_ts and the plane-wave backward transform k_pw_backward_tc, which share
+their constants, and k_pw_forward_tc, two A stages and no accumulator drains): producers, the MMA thread, and the
 asynchronous completions of the copies and of the committed MMAs, over random interleavings.  mbarrier waits follow the hardware's parity
 rule: a wait for phase k succeeds iff the barrier's completed-phase count has a parity other
 than k's, so a barrier two phases ahead of a wait looks incomplete.  The model checks that no
@@ -101,6 +101,12 @@ KERNEL_RULE = lambda s: (s - NA) // DRAIN  # drain a fill once the next fill's f
 def test_transfer_protocol_never_deadlocks_or_aliases(nsteps):
     for seed in range(10):
         run(nsteps, seed, KERNEL_RULE)
+
+
+@pytest.mark.parametrize("nsteps", [2, 3, 16, 17, 33, 64, 214])
+def test_backward_transform_protocol_never_deadlocks_or_aliases(nsteps):
+    for seed in range(10):
+        run(nsteps, seed, KERNEL_RULE, NA=3, DB=2)
 
 
 @pytest.mark.parametrize("nsteps", [1, 2, 3, 5, 8, 9, 31, 214])
