@@ -706,6 +706,13 @@ __device__ __forceinline__ void tmem_st16(uint32_t ta, const uint32_t (&v)[16]) 
         : "memory");
 }
 
+// eight floats from a 32-byte aligned global address, one 256-bit load through the read-only path
+__device__ __forceinline__ void ldg8(const float *p, float4 &a, float4 &b) {
+    asm volatile("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w)
+                 : "l"(p));
+}
+
 // 8 values of one lane into consecutive TMEM columns of the warp's lanes
 __device__ __forceinline__ void tmem_st8(uint32_t ta, const uint32_t (&v)[8]) {
     asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(ta), "r"(v[0]),
@@ -848,9 +855,17 @@ __global__ void __launch_bounds__(TS_NP + 32, 1) k_lag_gemm_ts(const uint32_t *_
                     b1 = adm_src[cur + 1];
                 }
             }
-            const float4 *g = reinterpret_cast<const float4 *>(u + ((size_t)src * nrhs + m) * 64 + qh * 32);
+            // 256-bit loads: half the load instructions (and L1 wavefronts) of 128-bit ones
+            const float *g = u + ((size_t)src * nrhs + m) * 64 + qh * 32;
 #pragma unroll
-            for (int c = 0; c < 8; ++c) dst[c] = use ? __ldg(g + c) : make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int c = 0; c < 4; ++c) {
+                if (use) {
+                    ldg8(g + 8 * c, dst[2 * c], dst[2 * c + 1]);
+                } else {
+                    dst[2 * c] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    dst[2 * c + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+            }
         };
 #pragma unroll
         for (int k = 0; k < TS_P; ++k) load_a(k, ring[k]);
