@@ -205,7 +205,8 @@ typedef struct {
                                   1 tcgen05 GEMM per translation (atomic scatter), 2 tcgen05
                                   target-stationary (one write per target box) */
     int tune_pw[22][3];        /* plane-wave levels: direction pairs per thread (forward), points
-                                  per thread (backward), right-hand sides per thread (several) */
+                                  per thread (backward), right-hand sides per thread (several; 0:
+                                  ffm_autotune picked the tensor-core transforms) */
     int nufft[22];             /* plane-wave levels whose F steps run as type-3 NUFFTs (1) */
     int nufft_w[22];           /* their spreading-kernel width */
     int nufft_n2[22];          /* their FFT grid edge (n2^3 per box) */

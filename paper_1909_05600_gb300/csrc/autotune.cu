@@ -124,9 +124,15 @@ bool parse_near(const std::string &v, int &tch, unsigned &smax) {
     return sscanf(v.c_str(), "%d %u", &tch, &smax) == 2 && tch >= 1 && tch <= P2P_T && smax >= 1;
 }
 bool parse_lag(const std::string &v, int &pick) { return sscanf(v.c_str(), "%d", &pick) == 1 && pick >= 0 && pick <= 2; }
+// c: right-hand sides per thread of the several-RHS kernels, or 0 for the tensor-core transforms
 bool parse_pw(const std::string &v, int &a, int &b, int &c) {
     return sscanf(v.c_str(), "%d %d %d", &a, &b, &c) == 3 && (a == 2 || a == 4) && (b == 2 || b == 4) &&
-           (c == 4 || c == 8);
+           (c == 0 || c == 4 || c == 8);
+}
+
+void set_pw_multi(FarLevel &F, int c) {
+    F.pw_tc = c == 0 ? 1 : 0;
+    if (c != 0) F.pw_mc = c;
 }
 
 void set_items(ffm_plan_s *p, int tch, unsigned smax, Alloc &tmp, cudaStream_t s) {
@@ -174,7 +180,7 @@ void apply_cached_picks(ffm_plan_s *p, const char *cache_path, cudaStream_t s) {
                 F.pw_ppt = b;
             }
             if ((cache.get(pw_key(p, l, dev, 64), v) || cache.get(pw_key(p, l, dev, 8), v)) && parse_pw(v, a, b, c))
-                F.pw_mc = c;
+                set_pw_multi(F, c);
         }
     }
     tmp.release();
@@ -281,8 +287,12 @@ void autotune(ffm_plan_s *p, int nrhs, const char *cache_path, cudaStream_t s) {
                         }
                     }
                 } else {
-                    for (int mc : {8, 4}) {
-                        F.pw_mc = mc;
+                    // CUDA-core kernels with 8 or 4 right-hand sides per thread, and the
+                    // tensor-core transforms where the level has them (c = 0)
+                    const bool tc = F.pw_chunks != nullptr && p->pw_transform == 0;
+                    for (int mc : {8, 4, 0}) {
+                        if (mc == 0 && !tc) continue;
+                        set_pw_multi(F, mc);
                         float ms = T.measure(run_level);
                         if (ms < best) {
                             best = ms;
@@ -294,7 +304,10 @@ void autotune(ffm_plan_s *p, int nrhs, const char *cache_path, cudaStream_t s) {
             }
             F.pw_qpt = a;
             F.pw_ppt = b;
-            F.pw_mc = c;
+            if (nrhs == 1)
+                F.pw_mc = c;
+            else
+                set_pw_multi(F, c);
         }
     }
     p->autotuned = 1;

@@ -2664,7 +2664,8 @@ static void planewave_level(const ffm_plan_s *p, int l, const float2 *q, int nrh
     // and compensated-FP32 levels, the backward transform on FP32 levels (the compensated
     // one carries its rounding error through the direction sum, which the tensor cores do not)
     const bool tc_fwd = f32 && multi && F.pw_chunks != nullptr &&
-                        (p->pw_transform == 3 || (p->pw_transform == 0 && nrhs >= PW_TC_MIN_RHS));
+                        (p->pw_transform == 3 ||
+                         (p->pw_transform == 0 && (F.pw_tc > 0 || (F.pw_tc < 0 && nrhs >= PW_TC_MIN_RHS))));
     const bool tc_bwd = tc_fwd && !COMP;
     if (f32 && F.nufft) {
         if constexpr (f32) nufft_forward(p, l, q, nrhs, ut, tmp, s);

@@ -489,7 +489,7 @@ ffm_status ffm_plan_info(const ffm_plan_t *plan, ffm_info *info) {
         info->tune_tc[l] = act && F.mode == 1 ? (ts ? 2 : tc ? 1 : 0) : 0;
         info->tune_pw[l][0] = act && F.mode == 2 ? F.pw_qpt : 0;
         info->tune_pw[l][1] = act && F.mode == 2 ? F.pw_ppt : 0;
-        info->tune_pw[l][2] = act && F.mode == 2 ? F.pw_mc : 0;
+        info->tune_pw[l][2] = act && F.mode == 2 ? (F.pw_tc == 1 ? 0 : F.pw_mc) : 0;
         info->n_src_boxes[l] = F.n_src;
         info->n_tgt_boxes[l] = F.n_tgt;
     }

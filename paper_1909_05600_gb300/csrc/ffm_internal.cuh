@@ -209,6 +209,8 @@ struct FarLevel {
     // levels): (box, first point) pieces of PW_TC_FCH points of the source boxes and of
     // PW_TC_BCH points of the target boxes
     int64_t n_pw_chunks = 0, n_pw_tchunks = 0;
+    int pw_tc = -1;                 // those transforms: -1 from PW_TC_MIN_RHS right-hand sides on,
+                                    // 0 never, 1 always (ffm_autotune's pick)
     uint2 *pw_chunks = nullptr;
     uint2 *pw_tchunks = nullptr;
 };

@@ -48,11 +48,12 @@ def test_autotune_keeps_results_and_replays_from_cache(case, tmp_path):
     for l in range(after["l_stop"] + 1):
         if after["mode"][l] == 2 and after["n_adm"][l] > 0:
             q, pp, mc = after["tune_pw"][l]
-            assert q in (2, 4) and pp in (2, 4) and mc in (4, 8)
-    # same algorithm and operators: the near-field sums are split differently and the
-    # Lagrange transfer may move between the TF32x3 tensor-core and the FP32 CUDA-core GEMM,
-    # so the results differ by FP32 rounding only
-    assert O.rel_l2(v1, v0) < 5e-6
+            assert q in (2, 4) and pp in (2, 4) and mc in ((0, 4, 8) if nrhs > 1 else (4, 8))
+    # same algorithm and operators: the near-field sums are split differently, and the Lagrange
+    # transfer or the several-RHS plane-wave transforms may move between TF32x3 tensor-core and
+    # FP32 CUDA-core products, so the results differ by rounding only
+    tol = 1e-5 if nrhs > 1 else 5e-6
+    assert O.rel_l2(v1, v0) < tol
     lines = open(cache).read().splitlines()
     assert lines and all(" = " in ln for ln in lines)
     with _plan(prob) as p2:
@@ -66,4 +67,4 @@ def test_autotune_keeps_results_and_replays_from_cache(case, tmp_path):
         v3 = p3.apply(Ud).cpu().numpy()
     if nrhs == 1:
         assert _picks(made) == _picks(after)
-    assert O.rel_l2(v3, v0) < 5e-6
+    assert O.rel_l2(v3, v0) < tol
