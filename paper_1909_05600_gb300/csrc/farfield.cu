@@ -2037,7 +2037,7 @@ __global__ void k_slot_set(const uint32_t *__restrict__ tgt, int64_t n, int *slo
     if (i < n) slot[tgt[i]] = (int)i;
 }
 
-// ---- several right-hand sides on the tensor cores (FP32 plane-wave levels)
+// ---- several right-hand sides on the tensor cores (FP32 and compensated-FP32 plane-wave levels)
 //
 // The forward transform of a source box b is a product of a generated matrix and the
 // densities: for direction pairs h (antipodes h, h + nQ/2) and right-hand sides m,
@@ -2079,7 +2079,7 @@ constexpr size_t PWT_SMEM = sizeof(float) * (size_t)PWT_NB * PWT_BST;  // 128 KB
 // Density image: for every block of 32 consecutive points (Morton order) and every group of
 // 64 right-hand sides, the TF32 hi block then the lo block of the K-major operand (rows n =
 // 2 m + part, part 0 = real, 1 = imaginary; columns = the block's points), zero beyond ny
-// and nrhs.  Shared by every plane-wave level of one apply.
+// and nrhs.  Its layout does not depend on the level; each tensor-core level builds it.
 __global__ void k_pw_density_image(const float2 *__restrict__ q, int64_t ny, int nrhs, int nblk_m,
                                    float *__restrict__ img) {
     const int64_t nimg = (int64_t)((ny + PWT_KC - 1) / PWT_KC) * nblk_m * PWT_BH;
