@@ -2058,8 +2058,8 @@ __global__ void k_slot_set(const uint32_t *__restrict__ tgt, int64_t n, int *slo
 // issues per 8 points hi hi + hi lo + lo hi for P and for Q (6 MMAs, M = 128, N = 128, K =
 // 8, A from TMEM) and commits to the stage's "empty" barrier.  The epilogue reads P and Q
 // from TMEM and adds u~ into the output (atomics: a box may be split over several chunks;
-// the output is zeroed first).  The TF32 x3 products carry about 2^-22 of each term (the
-// dropped lo lo product and the rounding of the lo parts), a few times FP32's rounding.
+// the output is zeroed first).  The TF32 x3 products are off by at most about 2^-21 of each
+// term, 2^-25 typically (the dropped lo lo product and the rounding of the lo parts).
 constexpr int PWT_M = 128;                 // direction pairs per CTA
 constexpr int PWT_KC = 32;                 // points per step
 constexpr int PWT_MC = 64;                 // right-hand sides per CTA
